@@ -1,0 +1,211 @@
+"""FP64 CPU oracle for the G-MAPP hot path (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the bench's CPU-baseline leg
+may import this package.  The product path never does; the CUDA library and
+this oracle share no source, headers or helpers.  Inputs come from the seeded
+generators in ``synth``.
+
+Functions (each cites the paper passage it follows):
+  filter_cloud    Sec. IV-B / V-A   camera cloud -> sorted voxel centres S_W
+  cf_eval         Eq. (mfi), Alg. 1 W, clearance and f_r at given states
+  rollout         Sec. IV-A         N_k-step point-mass rollout + cost sums
+  score_select    Sec. IV-A         weighted cost and argmin selection
+  fd_gradient     --                central finite differences of the cost
+Parity pins for every function live in tests/test_oracle_*.py.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from .build import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(_build())
+        P = C.c_void_p
+        i64 = C.c_int64
+        _lib.oracle_filter.restype = i64
+        _lib.oracle_filter.argtypes = [P, i64, P, P, C.c_float, P, C.c_int32, i64,
+                                       P, P, P, P, P, P]
+        _lib.oracle_cf_eval.restype = None
+        _lib.oracle_cf_eval.argtypes = [i64, P, P, P, C.c_double, i64, P, P, P, P, P, P,
+                                        C.c_double, C.c_double, P, P, P]
+        _lib.oracle_rollout.restype = None
+        _lib.oracle_rollout.argtypes = [i64, P, P, P, C.c_double, i64, P, P, P, P, P, P, P,
+                                        P, P, P, P, P, P, P, P, P]
+        _lib.oracle_max_threads.restype = C.c_int
+        _lib.oracle_set_threads.argtypes = [C.c_int]
+        if hasattr(_lib, "oracle_adjoint"):
+            _lib.oracle_adjoint.restype = None
+    return _lib
+
+
+class _Params(C.Structure):
+    _fields_ = [("goal", C.c_double * 3), ("dt", C.c_double), ("n_steps", C.c_int64),
+                ("damping", C.c_double), ("inv_mass", C.c_double), ("rho", C.c_double),
+                ("eps", C.c_double), ("vel_half", C.c_double),
+                ("clear_margin", C.c_double), ("clear_beta", C.c_double)]
+
+
+def _params(prm) -> _Params:
+    p = _Params()
+    for a in range(3):
+        p.goal[a] = float(prm.goal[a])
+    p.dt, p.n_steps = float(prm.dt), int(prm.n_steps)
+    p.damping, p.inv_mass, p.rho = float(prm.damping), float(prm.inv_mass), float(prm.rho)
+    p.eps, p.vel_half = float(prm.eps), float(prm.vel_half)
+    p.clear_margin, p.clear_beta = float(prm.clear_margin), float(prm.clear_beta)
+    return p
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def set_threads(n: int) -> None:
+    lib().oracle_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().oracle_max_threads())
+
+
+# ---------------------------------------------------------------------------
+# Perception (Sec. IV-B, Sec. V-A)
+# ---------------------------------------------------------------------------
+
+def filter_cloud(xyz: np.ndarray, T, workspace, cap: int | None = None) -> dict:
+    """Transform, crop and voxelise a camera-frame cloud; returns the sorted
+    occupied voxels (keys, counts, smallest point index) and their centres,
+    exactly as the binary32 sequence in ``gmapp_oracle.c`` defines them."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32).reshape(-1, 3)
+    T = np.ascontiguousarray(T, dtype=np.float32).reshape(12)
+    lo = np.ascontiguousarray(workspace.lo, dtype=np.float32)
+    dims = np.ascontiguousarray(workspace.dims, dtype=np.int32)
+    n = xyz.shape[0]
+    cap = n if cap is None else int(cap)
+    keys = np.zeros(max(cap, 1), np.uint32)
+    counts = np.zeros(max(cap, 1), np.uint32)
+    rep = np.zeros(max(cap, 1), np.uint32)
+    cx = np.zeros(max(cap, 1), np.float32)
+    cy = np.zeros(max(cap, 1), np.float32)
+    cz = np.zeros(max(cap, 1), np.float32)
+    n_out = lib().oracle_filter(_ptr(xyz), n, _ptr(T), _ptr(lo), float(np.float32(workspace.voxel)),
+                                _ptr(dims), int(workspace.min_pts), cap, _ptr(keys), _ptr(counts),
+                                _ptr(rep), _ptr(cx), _ptr(cy), _ptr(cz))
+    k = min(n_out, cap)
+    return {"n": int(n_out), "keys": keys[:k], "counts": counts[:k], "rep_idx": rep[:k],
+            "x": cx[:k], "y": cy[:k], "z": cz[:k],
+            "r_O": float(np.float32(workspace.voxel) * np.float32(0.5))}
+
+
+# ---------------------------------------------------------------------------
+# Force (Eq. mfi, Alg. 1) and rollout (Sec. IV-A)
+# ---------------------------------------------------------------------------
+
+def cf_eval(obs_xyz, r_O: float, p, v, agents: dict, rho: float, eps: float) -> dict:
+    """W, clearance m and f_r = rho k_r W g for every agent at state (p, v).
+    ``obs_xyz`` is [3, N_O]; p, v are [3, N_a]."""
+    ox, oy, oz = (_f64(obs_xyz[a]) for a in range(3))
+    p, v = _f64(p), _f64(v)
+    na = p.shape[1]
+    c = _f64(agents["c"])
+    k_r, r_d, r_a = _f64(agents["k_r"]), _f64(agents["r_d"]), _f64(agents["r_a"])
+    W = np.zeros(na)
+    m = np.zeros(na)
+    fr = np.zeros((3, na))
+    lib().oracle_cf_eval(ox.size, _ptr(ox), _ptr(oy), _ptr(oz), float(r_O), na, _ptr(p), _ptr(v),
+                         _ptr(c), _ptr(k_r), _ptr(r_d), _ptr(r_a), float(rho), float(eps),
+                         _ptr(W), _ptr(m), _ptr(fr))
+    return {"W": W, "m": m, "f_r": fr}
+
+
+def rollout(obs_xyz, r_O: float, agents: dict, prm, want_traj: bool = True,
+            want_trace: bool = False) -> dict:
+    """FP64 rollout of all agents; returns the trajectory [N_a, N_k+1, 3],
+    final state, path length, clearance penalty sum and minimum clearance."""
+    ox, oy, oz = (_f64(obs_xyz[a]) for a in range(3))
+    ag = {k: _f64(v) for k, v in agents.items()}
+    na = ag["k_r"].size
+    N = int(prm.n_steps)
+    traj = np.zeros((na, N + 1, 3)) if want_traj else None
+    wtr = np.zeros((na, N)) if want_trace else None
+    mtr = np.zeros((na, N)) if want_trace else None
+    out = {"p_final": np.zeros((3, na)), "v_final": np.zeros((3, na)),
+           "path_len": np.zeros(na), "clear_pen": np.zeros(na), "min_clear": np.zeros(na)}
+    pr = _params(prm)
+    nul = C.c_void_p(0)
+    lib().oracle_rollout(ox.size, _ptr(ox), _ptr(oy), _ptr(oz), float(r_O), na,
+                         _ptr(ag["p0"]), _ptr(ag["v0"]), _ptr(ag["c"]), _ptr(ag["k_r"]),
+                         _ptr(ag["k_a"]), _ptr(ag["r_d"]), _ptr(ag["r_a"]), C.byref(pr),
+                         _ptr(traj) if want_traj else nul, _ptr(out["p_final"]),
+                         _ptr(out["v_final"]), _ptr(out["path_len"]), _ptr(out["clear_pen"]),
+                         _ptr(out["min_clear"]), _ptr(wtr) if want_trace else nul,
+                         _ptr(mtr) if want_trace else nul)
+    if want_traj:
+        out["traj"] = traj
+    if want_trace:
+        out["w_trace"], out["m_trace"] = wtr, mtr
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Cost and selection (Sec. IV-A "Cost Functions", "Selection Mechanism")
+# ---------------------------------------------------------------------------
+
+def costs(ro: dict, prm) -> np.ndarray:
+    """C_i = w_path L_i + w_goal |p_i(N_k) - p_goal| + w_clear sum_k softplus."""
+    g = np.asarray(prm.goal, dtype=np.float64)[:, None]
+    dgoal = np.sqrt(((ro["p_final"] - g) ** 2).sum(axis=0))
+    return prm.w_path * ro["path_len"] + prm.w_goal * dgoal + prm.w_clear * ro["clear_pen"]
+
+
+def select(c: np.ndarray, prev_best_cost: float = math.nan, alpha: float = 1.0) -> int:
+    """i* = argmin_i C_i (ties -> lowest index).  With a previous best cost
+    C_best, only agents with C_i < alpha C_best qualify; -1 when none does
+    (the previous best path is kept)."""
+    c = np.asarray(c, dtype=np.float64)
+    if math.isnan(prev_best_cost):
+        return int(np.argmin(c))
+    ok = np.nonzero(c < alpha * prev_best_cost)[0]
+    if ok.size == 0:
+        return -1
+    return int(ok[np.argmin(c[ok])])
+
+
+def fd_gradient(obs_xyz, r_O, agents: dict, prm, agent_ids, h: float = 1e-6) -> dict:
+    """Central finite differences (step h) of each listed agent's cost with
+    respect to v0 (3), k_r, k_a and c (3), perturbing one agent parameter at
+    a time on a one-agent rollout (agents are independent)."""
+    out = {}
+    names = [("v0", 0), ("v0", 1), ("v0", 2), ("k_r", None), ("k_a", None),
+             ("c", 0), ("c", 1), ("c", 2)]
+    for i in agent_ids:
+        one = {k: (_f64(v)[:, i:i + 1] if _f64(v).ndim == 2 else _f64(v)[i:i + 1])
+               for k, v in agents.items()}
+        g = np.zeros(8)
+        for q, (name, ax) in enumerate(names):
+            vals = []
+            for sgn in (+1, -1):
+                a = {k: v.copy() for k, v in one.items()}
+                if ax is None:
+                    a[name][0] += sgn * h
+                else:
+                    a[name][ax, 0] += sgn * h
+                ro = rollout(obs_xyz, r_O, a, prm, want_traj=False)
+                vals.append(costs(ro, prm)[0])
+            g[q] = (vals[0] - vals[1]) / (2 * h)
+        out[int(i)] = g
+    return out

@@ -1,0 +1,291 @@
+/*
+ * G-MAPP oracle: a plain, slow, obviously correct CPU implementation of the
+ * perception -> rollout -> cost hot path, written from the paper's equations.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path links, loads or
+ * calls this file; only the tests, the smoke check and the bench's CPU
+ * baseline do.  It shares no source with the CUDA library.
+ *
+ * Precision: the rollout, force and cost run in binary64.  The perception
+ * filter is defined as an exact binary32 operation sequence (the paper fixes no
+ * precision for it; the GPU filter must match it bit for bit), so that part is
+ * written with `float` operands.  This file is compiled with
+ * -ffp-contract=off on x86-64 (SSE2, FLT_EVAL_METHOD == 0), so every float
+ * + - * / below is one correctly rounded binary32 operation and no multiply is
+ * fused into an add.
+ *
+ * Section references are to the paper (G-MAPP, arXiv 2606.12579):
+ *   Sec. IV-B / Sec. V-A  perception: transform, workspace crop, voxel grid
+ *                         at edge 2 r_O, voxel centres -> sphere world S_W
+ *   Eq. (mfi)             circular-field (MFI) repulsive force
+ *   Alg. 1                per-obstacle clamp max(d - (r_a + r_O), eps),
+ *                         detection gate d <= r_d, k_f scaling, sum over S_W
+ *   Sec. IV-A             F = f_a + f_r, f_a = K e - D v, vdot = I F,
+ *                         v_k = v_{k-1} + 1/2 dt vdot, p_{k+1} = p_k + dt v_k
+ */
+
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#pragma STDC FP_CONTRACT OFF
+
+/* ------------------------------------------------------------------------ */
+/* Perception filter (Sec. IV-B, Sec. V-A)                                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    uint32_t key;
+    uint32_t idx;
+} key_idx;
+
+static int cmp_key_idx(const void *a, const void *b)
+{
+    const key_idx *x = (const key_idx *)a, *y = (const key_idx *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    if (x->idx != y->idx) return x->idx < y->idx ? -1 : 1;
+    return 0;
+}
+
+/*
+ * Camera-frame cloud -> sorted occupied voxels and their centres.
+ *
+ *   world point   w_a = ((T[a][0] x + T[a][1] y) + T[a][2] z) + T[a][3]
+ *   kept iff      x, y, z finite and, per axis, 0 <= (w_a - lo_a) / voxel < dims_a
+ *   voxel index   i_a = floor((w_a - lo_a) / voxel)
+ *   linear key    (i_z dims_y + i_y) dims_x + i_x
+ *   centre        lo_a + ((float) i_a + 0.5) voxel          (r_O = voxel / 2)
+ *
+ * Points are grouped by key (sort by key, then by index); a voxel is kept when
+ * it holds at least min_pts points.  Output is in ascending key order, with
+ * the number of points and the smallest original point index per voxel.
+ * Returns the number of kept voxels; only the first `cap` are written.
+ */
+int64_t oracle_filter(const float *xyz, int64_t n_raw, const float *T,
+                      const float *lo, float voxel, const int32_t *dims,
+                      int32_t min_pts, int64_t cap, uint32_t *keys,
+                      uint32_t *counts, uint32_t *rep_idx, float *cx,
+                      float *cy, float *cz)
+{
+    key_idx *kv = (key_idx *)malloc((size_t)(n_raw > 0 ? n_raw : 1) * sizeof(key_idx));
+    int64_t m = 0;
+    for (int64_t i = 0; i < n_raw; ++i) {
+        float x = xyz[3 * i + 0], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z)) continue;
+        int64_t ix[3];
+        int inside = 1;
+        for (int a = 0; a < 3; ++a) {
+            float t0 = T[4 * a + 0] * x;
+            float t1 = T[4 * a + 1] * y;
+            float t2 = T[4 * a + 2] * z;
+            float w = ((t0 + t1) + t2) + T[4 * a + 3];
+            float q = (w - lo[a]) / voxel;
+            if (!(q >= 0.0f && q < (float)dims[a])) { inside = 0; break; }
+            ix[a] = (int64_t)floorf(q);
+        }
+        if (!inside) continue;
+        uint64_t key = ((uint64_t)ix[2] * (uint64_t)dims[1] + (uint64_t)ix[1]) * (uint64_t)dims[0]
+                       + (uint64_t)ix[0];
+        kv[m].key = (uint32_t)key;
+        kv[m].idx = (uint32_t)i;
+        ++m;
+    }
+    qsort(kv, (size_t)m, sizeof(key_idx), cmp_key_idx);
+
+    int64_t n_out = 0;
+    int64_t r = 0;
+    while (r < m) {
+        int64_t e = r;
+        while (e < m && kv[e].key == kv[r].key) ++e;
+        uint32_t cnt = (uint32_t)(e - r);
+        if ((int64_t)cnt >= (int64_t)min_pts) {
+            if (n_out < cap) {
+                uint32_t key = kv[r].key;
+                uint32_t i_x = key % (uint32_t)dims[0];
+                uint32_t i_y = (key / (uint32_t)dims[0]) % (uint32_t)dims[1];
+                uint32_t i_z = key / ((uint32_t)dims[0] * (uint32_t)dims[1]);
+                keys[n_out] = key;
+                counts[n_out] = cnt;
+                rep_idx[n_out] = kv[r].idx; /* smallest index: sorted by idx within key */
+                cx[n_out] = lo[0] + ((float)i_x + 0.5f) * voxel;
+                cy[n_out] = lo[1] + ((float)i_y + 0.5f) * voxel;
+                cz[n_out] = lo[2] + ((float)i_z + 0.5f) * voxel;
+            }
+            ++n_out;
+        }
+        r = e;
+    }
+    free(kv);
+    return n_out;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Circular-field repulsion (Eq. mfi, Alg. 1)                                */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Per-agent obstacle sum of Alg. 1 for the MFI heuristic with a fixed current.
+ * For every obstacle j of S_W:
+ *   d_j = |p - p_Oj|,  s_j = max(d_j - (r_a + r_O), eps)
+ *   contributes 1 / s_j when s_j <= r_d (detection gate), else nothing.
+ * W = sum of the contributions.  m = min_j (d_j - r_a - r_O) is the clearance
+ * to the nearest obstacle surface, unclamped.
+ */
+static void cf_weight(const double p[3], int64_t n_obs, const double *ox,
+                      const double *oy, const double *oz, double R, double eps,
+                      double r_d, double *W, double *m)
+{
+    double w = 0.0, mn = INFINITY;
+    for (int64_t j = 0; j < n_obs; ++j) {
+        double dx = p[0] - ox[j], dy = p[1] - oy[j], dz = p[2] - oz[j];
+        double d = sqrt(dx * dx + dy * dy + dz * dz);
+        double s = d - R;
+        if (s < mn) mn = s;
+        if (s < eps) s = eps;
+        if (s <= r_d) w += 1.0 / s;
+    }
+    *W = w;
+    *m = mn;
+}
+
+/*
+ * Direction factor of Eq. (mfi) for static obstacles (d-dot = -v):
+ *   (d-dot / |d-dot|) x (c x d-dot) = v_hat x (c x v) = (|v|^2 c - v (v . c)) / |v|
+ * (the factor is even in d-dot).  Zero when |v|^2 < 1e-30.
+ */
+static void cf_direction(const double v[3], const double c[3], double g[3])
+{
+    double vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    if (vv < 1e-30) { g[0] = g[1] = g[2] = 0.0; return; }
+    double vc = v[0] * c[0] + v[1] * c[1] + v[2] * c[2];
+    double nv = sqrt(vv);
+    for (int a = 0; a < 3; ++a) g[a] = (vv * c[a] - v[a] * vc) / nv;
+}
+
+/*
+ * Repulsive force of each agent at a given state (p, v):
+ *   f_r = rho k_r W g      (k_f = rho k_r)
+ * Layouts: p, v, c, f_r are [3][n_agents] (row per axis); the rest [n_agents].
+ */
+void oracle_cf_eval(int64_t n_obs, const double *ox, const double *oy,
+                    const double *oz, double r_O, int64_t n_agents,
+                    const double *p, const double *v, const double *c,
+                    const double *k_r, const double *r_d, const double *r_a,
+                    double rho, double eps, double *W, double *m, double *f_r)
+{
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t i = 0; i < n_agents; ++i) {
+        double pi[3] = {p[i], p[n_agents + i], p[2 * n_agents + i]};
+        double vi[3] = {v[i], v[n_agents + i], v[2 * n_agents + i]};
+        double ci[3] = {c[i], c[n_agents + i], c[2 * n_agents + i]};
+        double w, mn, g[3];
+        cf_weight(pi, n_obs, ox, oy, oz, r_a[i] + r_O, eps, r_d[i], &w, &mn);
+        cf_direction(vi, ci, g);
+        W[i] = w;
+        m[i] = mn;
+        for (int a = 0; a < 3; ++a) f_r[a * n_agents + i] = rho * k_r[i] * w * g[a];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rollout (Sec. IV-A) with the running cost accumulators                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double goal[3];
+    double dt;            /* delta_t */
+    int64_t n_steps;      /* N_k */
+    double damping;       /* D = damping * I_3 */
+    double inv_mass;      /* inertia tensor = inv_mass * I_3 */
+    double rho;           /* k_f = rho * k_r */
+    double eps;           /* clamp of Alg. 1 */
+    double vel_half;      /* the 1/2 of the velocity update */
+    double clear_margin;  /* softplus clearance penalty margin */
+    double clear_beta;    /* softplus sharpness */
+} oracle_params;
+
+/* softplus_beta(x) = log(1 + exp(beta x)) / beta, evaluated without overflow */
+static double softplus(double x, double beta)
+{
+    double bx = beta * x;
+    if (bx > 0.0) return (bx + log1p(exp(-bx))) / beta;
+    return log1p(exp(bx)) / beta;
+}
+
+/*
+ * N_a independent point-mass agents, N_k steps each.  Step k (0-based):
+ *   W, m  <- Alg. 1 sum at p_k                          (clearance m_k)
+ *   F     = k_a (p_goal - p_k) - D v_{k-1} + rho k_r W g(v_{k-1}, c)
+ *   v_k   = v_{k-1} + vel_half dt inv_mass F
+ *   p_k+1 = p_k + dt v_k
+ *   L    += |p_k+1 - p_k|;   pen += softplus(margin - m_k);   mc = min(mc, m_k)
+ * The trajectory holds p_0 .. p_N_k (N_k + 1 points).
+ * Layouts: agent vectors [3][n_agents]; traj [n_agents][n_steps+1][3];
+ * w_trace, m_trace [n_agents][n_steps].  traj / traces may be NULL.
+ */
+void oracle_rollout(int64_t n_obs, const double *ox, const double *oy,
+                    const double *oz, double r_O, int64_t n_agents,
+                    const double *p0, const double *v0, const double *c,
+                    const double *k_r, const double *k_a, const double *r_d,
+                    const double *r_a, const oracle_params *prm, double *traj,
+                    double *p_final, double *v_final, double *path_len,
+                    double *clear_pen, double *min_clear, double *w_trace,
+                    double *m_trace)
+{
+    const int64_t N = prm->n_steps;
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t i = 0; i < n_agents; ++i) {
+        double p[3] = {p0[i], p0[n_agents + i], p0[2 * n_agents + i]};
+        double v[3] = {v0[i], v0[n_agents + i], v0[2 * n_agents + i]};
+        double ci[3] = {c[i], c[n_agents + i], c[2 * n_agents + i]};
+        double L = 0.0, pen = 0.0, mc = INFINITY;
+        if (traj) for (int a = 0; a < 3; ++a) traj[(i * (N + 1)) * 3 + a] = p[a];
+        for (int64_t k = 0; k < N; ++k) {
+            double w, mn, g[3], F[3], pn[3];
+            cf_weight(p, n_obs, ox, oy, oz, r_a[i] + r_O, prm->eps, r_d[i], &w, &mn);
+            cf_direction(v, ci, g);
+            for (int a = 0; a < 3; ++a)
+                F[a] = k_a[i] * (prm->goal[a] - p[a]) - prm->damping * v[a]
+                       + prm->rho * k_r[i] * w * g[a];
+            for (int a = 0; a < 3; ++a) v[a] = v[a] + prm->vel_half * prm->dt * prm->inv_mass * F[a];
+            for (int a = 0; a < 3; ++a) pn[a] = p[a] + prm->dt * v[a];
+            double dx = pn[0] - p[0], dy = pn[1] - p[1], dz = pn[2] - p[2];
+            L += sqrt(dx * dx + dy * dy + dz * dz);
+            pen += softplus(prm->clear_margin - mn, prm->clear_beta);
+            if (mn < mc) mc = mn;
+            if (w_trace) w_trace[i * N + k] = w;
+            if (m_trace) m_trace[i * N + k] = mn;
+            for (int a = 0; a < 3; ++a) p[a] = pn[a];
+            if (traj) for (int a = 0; a < 3; ++a) traj[(i * (N + 1) + k + 1) * 3 + a] = p[a];
+        }
+        for (int a = 0; a < 3; ++a) {
+            p_final[a * n_agents + i] = p[a];
+            v_final[a * n_agents + i] = v[a];
+        }
+        path_len[i] = L;
+        clear_pen[i] = pen;
+        min_clear[i] = mc;
+    }
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
