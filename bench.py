@@ -1,0 +1,375 @@
+#!/usr/bin/env python3
+"""Benchmark of the B300 G-MAPP hot path.
+
+One step = one planning query of the tabletop workload: a 640x480 depth
+frame (307,200 points, 2 mm noise, 5% NaN) goes through filter_cloud
+(workspace 1 x 1 x 0.8 m, 5 mm voxels -> N_O obstacles), rollout_agents
+(256 agents x 500 steps under the circular field) and score_and_select.
+The metric is agent-obstacle interactions per second, N_a * N_O * N_k per
+step, over the whole job.  The inputs are a ring of distinct frames (sensor
+noise and dropouts differ per frame) larger than L2, resident in HBM before
+timing; ``e2e`` repeats the step through the same public calls with the
+frame copied from pinned host memory and the chosen plan copied back.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs independent queries (replicas: the
+path has no exchange step) on its own frames; the job time is the maximum
+over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "agent-obstacle interactions/s (% FP32 peak) and p50/p99 plan latency vs plain rollout"
+UNIT = "interactions/s"
+FLOPS_PER_INTERACTION = 13      # 3 sub, 5 for |d|^2, rsqrt, mul, sub, rcp, accumulate
+FP32_LANES_PER_SM = 128
+OBS_CAP = 131072
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "rollout_tabletop_256x500.md")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) == 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# Workload
+# ---------------------------------------------------------------------------
+
+def make_workload(n_frames: int, rank: int):
+    import synth
+    base = synth.tabletop_workload()           # scene, agents, params of the tabletop query
+    frames = []
+    for f in range(n_frames):
+        w = synth.tabletop_workload(frame_seed=7_000_000 + 1000 * rank + f, n_agents=1, n_steps=1)
+        frames.append(w["xyz"])
+    return base, frames
+
+
+def oracle_step(base, xyz, n_agents_sample: int):
+    """The oracle on a bounded sample of one step: the full frame's filter,
+    then n_agents_sample agents over all obstacles and all N_k steps."""
+    import oracle
+    f = oracle.filter_cloud(xyz, base["T"], base["workspace"])
+    obs = np.stack([f["x"], f["y"], f["z"]])
+    ag = {k: np.ascontiguousarray(v[..., :n_agents_sample]) for k, v in base["agents"].items()}
+    ro = oracle.rollout(obs, f["r_O"], ag, base["params"], want_traj=True)
+    c = oracle.costs(ro, base["params"])
+    oracle.select(c)
+    return n_agents_sample * f["n"] * int(base["params"].n_steps)
+
+
+def run_reference(args, ws, rank):
+    """--impl reference: the FP64 oracle as it stands on the host cores."""
+    if rank != 0:
+        return 0
+    import oracle
+    base, frames = make_workload(max(2, min(args.frames, 4)), rank)
+    sample = args.ref_agents
+    for i in range(args.warmup):
+        oracle_step(base, frames[i % len(frames)], sample)
+    t0 = time.perf_counter()
+    inter = 0
+    for i in range(args.steps):
+        inter += oracle_step(base, frames[i % len(frames)], sample)
+    dt = time.perf_counter() - t0
+    value = inter / dt
+    cores = oracle.max_threads()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": _config(base, args, ws),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"per step: full-frame filter + {sample} of "
+                                       f"{base['agents']['k_r'].size} agents x all obstacles x "
+                                       f"{base['params'].n_steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(base, args, ws):
+    return {"workload": "tabletop 640x480 depth frame -> 5 mm voxels; 256 agents x 500 steps",
+            "n_raw": int(base["xyz"].shape[0]), "n_agents": int(base["agents"]["k_r"].size),
+            "n_steps": int(base["params"].n_steps), "voxel_m": base["workspace"].voxel,
+            "frames_in_ring": args.frames,
+            "l2": f"inputs larger than L2: a ring of {args.frames} distinct frames "
+                  f"({args.frames * base['xyz'].nbytes / 1e6:.0f} MB) resident in HBM",
+            "parallelism": f"replicas x{ws}"}
+
+
+def _traffic_from_profile():
+    """Per-launch DRAM bytes of the rollout kernel from the committed ncu
+    summary (the line 'traffic_bytes_per_launch: N'), if present."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    with open(PROFILE_SUMMARY) as f:
+        for line in f:
+            if line.strip().startswith("traffic_bytes_per_launch:"):
+                v = line.split(":", 1)[1].strip()
+                return None if v in ("", "null") else float(v)
+    return None
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+    import paper_2606_12579_b300 as gm
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    base, frames_np = make_workload(args.frames, rank)
+    prm = base["params"]
+    na, nk = int(base["agents"]["k_r"].size), int(prm.n_steps)
+    stream = torch.cuda.current_stream()
+    ctx = gm.context(local)
+
+    # inputs resident in HBM
+    frames = torch.from_numpy(np.stack(frames_np)).cuda()
+    pinned = torch.from_numpy(np.stack(frames_np)).pin_memory()
+    agents = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda()
+              for k, v in base["agents"].items()}
+    obs = gm.Obstacles.empty(OBS_CAP)
+    wsp = torch.empty(gm.filter_workspace_bytes(frames.shape[1], base["workspace"]),
+                      dtype=torch.uint8, device="cuda")
+    ro = gm.alloc_rollout_out(na, nk, want_traj=True)
+    sel = gm.score_and_select(gm.rollout_agents(gm.filter_cloud(frames[0], base["T"], base["workspace"],
+                                                                 out=obs, workspace=wsp),
+                                                agents, prm, out=ro), prm)
+    ctx.sync()
+    tuning = gm.pick_tuning(OBS_CAP, na)
+
+    # N_O per frame (for the interaction count), outside any timed region
+    n_obs = []
+    for f in range(args.frames):
+        gm.filter_cloud(frames[f], base["T"], base["workspace"], out=obs, workspace=wsp)
+        n_obs.append(obs.count())
+    ctx.sync()
+
+    def step(f, ev=None):
+        gm.filter_cloud(frames[f], base["T"], base["workspace"], out=obs, workspace=wsp)
+        if ev is not None:
+            ev[0].record(stream)
+        gm.rollout_agents(obs, agents, prm, out=ro, tuning=tuning)
+        if ev is not None:
+            ev[1].record(stream)
+        gm.score_and_select(ro, prm, out=sel)
+
+    for i in range(args.warmup):
+        step(i % args.frames)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.25)
+    ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    ev_roll = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    inter = 0
+    for i in range(args.steps):
+        f = (args.warmup + i) % args.frames
+        ev_step[i][0].record(stream)
+        step(f, ev_roll[i])
+        ev_step[i][1].record(stream)
+        inter += na * n_obs[f] * nk
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ctx.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev_step]
+    roll_ms = [a.elapsed_time(b) for a, b in ev_roll]
+    t_dev = sum(step_ms) / 1e3
+
+    # end to end through the same calls: pinned host frame -> device, plan -> host
+    host_best = torch.empty(1, dtype=torch.int32).pin_memory()
+    host_traj = torch.empty(nk + 1, 3, dtype=torch.float32).pin_memory()
+    dev_frame = torch.empty_like(frames[0])
+    lat = []
+    e2e_inter = 0
+    for i in range(args.warmup + args.steps):
+        f = i % args.frames
+        t0 = time.perf_counter()
+        dev_frame.copy_(pinned[f], non_blocking=True)
+        gm.filter_cloud(dev_frame, base["T"], base["workspace"], out=obs, workspace=wsp)
+        gm.rollout_agents(obs, agents, prm, out=ro, tuning=tuning)
+        gm.score_and_select(ro, prm, out=sel)
+        host_best.copy_(sel["best"], non_blocking=True)
+        host_traj.copy_(sel["best_traj"], non_blocking=True)
+        stream.synchronize()
+        if i >= args.warmup:
+            lat.append(time.perf_counter() - t0)
+            e2e_inter += na * n_obs[f] * nk
+    ctx.sync()
+
+    # max over ranks
+    t_job = t_dev
+    e2e_time = sum(lat)
+    if ws > 1:
+        t = torch.tensor([t_dev, e2e_time], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_job, e2e_time = float(t[0]), float(t[1])
+        it = torch.tensor([inter, e2e_inter], dtype=torch.float64, device="cuda")
+        dist.all_reduce(it, op=dist.ReduceOp.SUM)
+        inter, e2e_inter = float(it[0]), float(it[1])
+
+    result = None
+    if rank == 0:
+        props = torch.cuda.get_device_properties(local)
+        peaks = _measured_peaks()
+        sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2032.0
+        peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        mean_roll = statistics.mean(roll_ms) / 1e3
+        per_launch_inter = na * statistics.mean(
+            [n_obs[(args.warmup + i) % args.frames] for i in range(args.steps)]) * nk
+        achieved = per_launch_inter * FLOPS_PER_INTERACTION / mean_roll / 1e12
+        cpu = cpu_baseline(base, frames_np[0], args.cpu_agents) if not args.no_cpu else None
+        result = {
+            "metric": METRIC, "value": inter / t_job, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_job / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": _config(base, args, ws),
+            "n_obs_mean": float(np.mean(n_obs)), "tuning": list(tuning),
+            "wall_s_timed": t_wall,
+            "roofline": {"bound": "alu", "kernel": "k_rollout", "achieved": achieved,
+                         "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                         "traffic": _traffic_from_profile(),
+                         "flops_per_interaction": FLOPS_PER_INTERACTION,
+                         "peak_source": f"{props.multi_processor_count} SMs x "
+                                        f"{FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                         "rollout_ms_mean": 1e3 * mean_roll},
+            "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
+                           "p99": 1e3 * float(np.percentile(lat, 99))},
+            "e2e": {"value": e2e_inter / e2e_time, "unit": UNIT,
+                    "h2d_bytes_per_step": int(frames[0].numel() * 4),
+                    "d2h_bytes_per_step": int(host_best.numel() * 4 + host_traj.numel() * 4)},
+            "gpu_launches": args.steps * LAUNCHES_PER_STEP,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(result), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+# filter_cloud (zero, keys, bitmap sums, emit, count, publish) + rollout + select
+LAUNCHES_PER_STEP = 6 + 1 + 1
+
+
+def cpu_baseline(base, xyz, n_agents_sample):
+    import oracle
+    t0 = time.perf_counter()
+    inter = oracle_step(base, xyz, n_agents_sample)
+    dt = time.perf_counter() - t0
+    return {"value": inter / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"one step: full-frame filter + {n_agents_sample} of "
+                      f"{base['agents']['k_r'].size} agents x all obstacles x "
+                      f"{base['params'].n_steps} steps (agents are independent)",
+            "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=48)
+    ap.add_argument("--cpu-agents", type=int, default=64)
+    ap.add_argument("--ref-agents", type=int, default=8)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,246 @@
+/*
+ * gmapp.h -- C ABI of the B300 (sm_103a) G-MAPP hot path.
+ *
+ * G-MAPP (arXiv 2606.12579) plans reactive motions by rolling out many
+ * virtual point-mass agents through a sphere-world obstacle set built from a
+ * depth cloud, then picking the cheapest agent.  This library implements
+ * that data-parallel path as hand-written CUDA:
+ *
+ *   filter_cloud      Sec. IV-B, Sec. V-A   depth cloud -> obstacle set S_W
+ *   rollout_agents    Sec. IV-A, Eq. (mfi), Alg. 1
+ *                                           N_a agents x N_k steps under
+ *                                           F = f_a + f_r (CF/MFI field)
+ *   score_and_select  Sec. IV-A (cost, selection)  costs and best agent i*
+ *
+ * Conventions shared by every call:
+ *   - Pointers named "device" point to memory of the context's GPU; "host"
+ *     pointers to ordinary CPU memory.  The caller owns every buffer passed
+ *     in (inputs, outputs, workspaces); the library owns only the context.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *     default stream).  Argument checks are synchronous and return an error
+ *     status without launching anything.
+ *   - Errors found on the device (capacity overflow, a bounded wait that ran
+ *     out) are OR-ed into a device error word of the context; gmapp_sync()
+ *     waits for the stream and reports and clears them.
+ *   - No call throws, exits or traps.  gmapp_last_error() describes the last
+ *     failure on the calling thread.
+ *   - Vectors of agents use the layout [3][N_a] (one row per axis, float32),
+ *     scalars per agent [N_a].
+ */
+#ifndef GMAPP_H
+#define GMAPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *gmapp_stream; /* == cudaStream_t */
+
+typedef enum {
+    GMAPP_OK = 0,
+    GMAPP_ERR_INVALID_ARG = 1, /* a size, pointer, alignment or value is out of range */
+    GMAPP_ERR_CAPACITY = 2,    /* an output or workspace is too small; the needed size is reported */
+    GMAPP_ERR_CUDA = 3,        /* a CUDA runtime call failed (message in gmapp_last_error) */
+    GMAPP_ERR_TIMEOUT = 4,     /* a device-side bounded wait gave up */
+    GMAPP_ERR_NOT_READY = 5    /* the object is busy (serving: no free slot) */
+} gmapp_status;
+
+/* Device error-word bits (reported by gmapp_sync as the status above). */
+#define GMAPP_DEVERR_CAPACITY 0x1u
+#define GMAPP_DEVERR_TIMEOUT 0x2u
+#define GMAPP_DEVERR_BOUNDS 0x4u
+
+typedef struct gmapp_ctx gmapp_ctx;
+
+/* Create a context on CUDA device `device`: allocates the device error word
+ * and reads the device's SM count and cluster limits.  This and
+ * gmapp_destroy are the only calls that allocate or free device memory.
+ * Returns GMAPP_ERR_CUDA when the device cannot be used. */
+gmapp_status gmapp_create(gmapp_ctx **out, int device);
+void gmapp_destroy(gmapp_ctx *ctx);
+
+/* Text of the last failure on the calling thread ("" when none). */
+const char *gmapp_last_error(void);
+
+/* Wait for `stream`, then read and clear the context's device error word:
+ * GMAPP_OK, GMAPP_ERR_CAPACITY, GMAPP_ERR_TIMEOUT or GMAPP_ERR_CUDA. */
+gmapp_status gmapp_sync(gmapp_ctx *ctx, gmapp_stream stream);
+
+/* Raw device error word (bit mask of GMAPP_DEVERR_*), read after a stream
+ * synchronisation, without clearing it. */
+gmapp_status gmapp_peek_device_error(gmapp_ctx *ctx, uint32_t *bits);
+
+/* ------------------------------------------------------------------------ */
+/* Perception: filter_cloud (Sec. IV-B "GPU-accelerated Perception",          */
+/* Sec. V-A: transform, workspace crop, voxel grid of edge 2 r_O, voxel       */
+/* centres form S_W)                                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Workspace voxel grid.  The workspace is the box [lo, lo + dims * voxel).
+ * Constraints: voxel > 0, 1 <= dims[a] <= 2^24, dims[0]*dims[1]*dims[2]
+ * < 2^32 - 1, min_pts >= 1. */
+typedef struct {
+    float lo[3];     /* world-frame lower corner (m) */
+    float voxel;     /* voxel edge (m); the obstacle radius is r_O = voxel / 2 */
+    int32_t dims[3]; /* cells per axis */
+    int32_t min_pts; /* a voxel is an obstacle when it holds >= min_pts points */
+} gmapp_workspace;
+
+/* The sphere world S_W = {(p_Oj, r_O)}: N_O centres in ascending voxel-key
+ * order (SoA float32), with per-voxel key, point count and smallest point
+ * index.  All arrays are device memory of `cap` elements, 16-byte aligned;
+ * `cap` is a multiple of 4.  `n` is ONE device int32 holding N_O (written by
+ * filter_cloud; on overflow it holds the needed size).  keys, counts and
+ * rep_idx may be NULL for obstacle sets that do not come from filter_cloud. */
+typedef struct {
+    float *x, *y, *z;
+    uint32_t *keys;
+    uint32_t *counts;
+    uint32_t *rep_idx;
+    int32_t *n;
+    int64_t cap;
+    float r_O; /* obstacle radius (m); filter_cloud sets it to voxel / 2 */
+} gmapp_obstacles;
+
+/* Bytes of device workspace filter_cloud needs for `n_raw` points. */
+size_t gmapp_filter_workspace_bytes(int64_t n_raw, const gmapp_workspace *ws);
+
+/* Depth cloud -> S_W.
+ *   xyz         device, n_raw x 3 float32 AoS camera-frame points, 16-byte
+ *               aligned; rows with a non-finite coordinate are dropped.
+ *   T           host, 12 float32: row-major 3x4 camera-to-world [R | t].
+ *   ws          host, the voxel grid (above).
+ *   out         host struct of device buffers (above); out->r_O is set.
+ *   workspace   device scratch of at least gmapp_filter_workspace_bytes(),
+ *               256-byte aligned; contents need no initialisation.
+ * Arithmetic is the exact binary32 sequence (no fused multiply-add):
+ *   w_a = ((T[a][0] x + T[a][1] y) + T[a][2] z) + T[a][3]
+ *   q_a = (w_a - lo_a) / voxel (IEEE division); kept iff 0 <= q_a < dims_a
+ *   i_a = floor(q_a); key = (i_z dims_y + i_y) dims_x + i_x
+ *   centre_a = lo_a + ((float) i_a + 0.5) voxel
+ * The result is bit-identical from run to run.  When more than out->cap
+ * voxels qualify, the first cap (by key) are written, *out->n holds the
+ * total and the device error word gets GMAPP_DEVERR_CAPACITY. */
+gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n_raw,
+                          const float T[12], const gmapp_workspace *ws,
+                          gmapp_obstacles *out, void *workspace,
+                          size_t workspace_bytes, gmapp_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Rollout: rollout_agents (Sec. IV-A agent dynamics and agent set;           */
+/* Eq. (mfi) circular-field force; Alg. 1 clamp, detection gate, sum)         */
+/* ------------------------------------------------------------------------ */
+
+/* Agent set A = {A_1 .. A_Na}; device arrays, float32. */
+typedef struct {
+    const float *p0; /* [3][n] start positions (m) */
+    const float *v0; /* [3][n] initial velocities (m/s) */
+    const float *c;  /* [3][n] artificial current vectors (used as given) */
+    const float *k_r; /* [n] field gains; k_f = rho * k_r */
+    const float *k_a; /* [n] attractive stiffness (K = k_a I_3) */
+    const float *r_d; /* [n] detection radii (m); +inf = no gate */
+    const float *r_a; /* [n] agent radii (m) */
+    int32_t n;        /* N_a >= 1 */
+} gmapp_agents;
+
+/* Rollout constants (host struct). */
+typedef struct {
+    float goal[3];      /* p_goal (m) */
+    float dt;           /* delta_t (s), > 0 */
+    int32_t n_steps;    /* N_k >= 1 */
+    float damping;      /* D = damping * I_3 */
+    float inv_mass;     /* inertia tensor = inv_mass * I_3 */
+    float rho;          /* repulsive scale (k_f = rho * k_r) */
+    float eps;          /* minimum acceptable distance of Alg. 1, > 0 */
+    float vel_half;     /* the 1/2 of the velocity update */
+    float clear_margin; /* softplus clearance-penalty margin (m) */
+    float clear_beta;   /* softplus sharpness (1/m), > 0 */
+    int32_t ckpt_every; /* adjoint checkpoint interval (steps); 0 = no checkpoints */
+} gmapp_rollout_params;
+
+/* Rollout outputs: device buffers written by rollout_agents. */
+typedef struct {
+    float *traj;      /* [n][n_steps+1][3] positions p_0..p_Nk, or NULL */
+    float *p_final;   /* [3][n] */
+    float *v_final;   /* [3][n] */
+    float *path_len;  /* [n] sum_k |p_k+1 - p_k| */
+    float *clear_pen; /* [n] sum_k softplus_beta(margin - m_k) */
+    float *min_clear; /* [n] min_k m_k */
+    float *w_trace;   /* [n][n_steps] W_k (sum of Alg. 1), or NULL */
+    float *m_trace;   /* [n][n_steps] clearance m_k, or NULL */
+    float *f_trace;   /* [n][n_steps][3] repulsive force f_r at step k, or NULL */
+    float *ckpt;      /* [n_ckpt][6][n] (p, v) at steps 0, K, 2K, ... (adjoint), or NULL */
+} gmapp_rollout_out;
+
+/* Roll all agents forward N_k steps in ONE launch.  Step k (0-based):
+ *   s_j  = max(|p_k - p_Oj| - (r_a + r_O), eps),  W_k = sum_{s_j <= r_d} 1/s_j
+ *   m_k  = min_j |p_k - p_Oj| - (r_a + r_O)
+ *   g    = (|v|^2 c - v (v . c)) / |v|      (0 when |v|^2 < 1e-30), v = v_{k-1}
+ *   F    = k_a (p_goal - p_k) - damping v + rho k_r W_k g
+ *   v_k  = v_{k-1} + vel_half dt inv_mass F;  p_{k+1} = p_k + dt v_k
+ * N_O is read from obs->n on the device (so the call may follow
+ * filter_cloud on the same stream without a host round trip).  Obstacle
+ * arrays must be 16-byte aligned with obs->cap a multiple of 4.  If N_O
+ * exceeds obs->cap or what the launch can keep on chip, nothing is written
+ * and GMAPP_DEVERR_CAPACITY is set.  FP32 arithmetic; results are
+ * deterministic for a given launch shape. */
+gmapp_status rollout_agents(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                            const gmapp_agents *agents,
+                            const gmapp_rollout_params *prm,
+                            gmapp_rollout_out *out, gmapp_stream stream);
+
+/* Launch shape of the rollout kernel (see rollout_agents_tuned). */
+typedef struct {
+    int32_t cluster;        /* CTAs per cluster, each holding 1/cluster of S_W: 1..16 */
+    int32_t agents_per_cta; /* agents processed together by one cluster: 1..32 */
+    int32_t threads;        /* threads per CTA: 128, 256, 384 or 512 */
+} gmapp_tuning;
+
+/* Same as rollout_agents with an explicit launch shape (used by the
+ * autotuner).  GMAPP_ERR_INVALID_ARG for shapes outside the ranges above or
+ * an obstacle shard that does not fit in shared memory for obs->cap. */
+gmapp_status rollout_agents_tuned(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                                  const gmapp_agents *agents,
+                                  const gmapp_rollout_params *prm,
+                                  gmapp_rollout_out *out, const gmapp_tuning *tune,
+                                  gmapp_stream stream);
+
+/* The launch shape rollout_agents would choose for these sizes. */
+gmapp_status gmapp_pick_tuning(gmapp_ctx *ctx, int64_t obs_cap, int32_t n_agents,
+                               gmapp_tuning *tune);
+
+/* ------------------------------------------------------------------------ */
+/* Cost and selection: score_and_select (Sec. IV-A "Cost Functions" and        */
+/* "Selection Mechanism")                                                     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    float w_path;  /* weight of the path length */
+    float w_goal;  /* weight of the final distance to the goal */
+    float w_clear; /* weight of the clearance-penalty sum */
+} gmapp_cost_weights;
+
+/* C_i = w_path L_i + w_goal |p_i(N_k) - p_goal| + w_clear pen_i for every
+ * agent, then i* = argmin_i C_i with ties to the lowest index.  With a
+ * previous best cost (prev_best_cost not NaN) only agents with
+ * C_i < alpha * prev_best_cost qualify and i* = -1 when none does (keep the
+ * previous path).  Reads ro->p_final, path_len, clear_pen (device).
+ *   costs      device [n_agents] float32 (written)
+ *   best       device, one int32 (written)
+ *   best_traj  device [(n_steps+1) * 3] float32: the selected agent's
+ *              trajectory copied from ro->traj (needs ro->traj), or NULL.
+ *              Left untouched when i* = -1. */
+gmapp_status score_and_select(gmapp_ctx *ctx, const gmapp_rollout_out *ro,
+                              int32_t n_agents, const gmapp_rollout_params *prm,
+                              const gmapp_cost_weights *w, float prev_best_cost,
+                              float alpha, float *costs, int32_t *best,
+                              float *best_traj, gmapp_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMAPP_H */

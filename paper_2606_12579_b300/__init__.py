@@ -1,0 +1,300 @@
+"""B300-native G-MAPP hot path: Python binding of libgmapp.so.
+
+Argument marshalling only: every step of the path runs in the CUDA kernels
+behind the C ABI (include/gmapp.h).  PyTorch supplies device memory and the
+current stream.  There is no CPU fallback: on a machine without the library
+or a CUDA device every compute call raises.
+
+    ctx  = Context(0)
+    obs  = filter_cloud(xyz, T, workspace)               # Sec. IV-B / V-A
+    ro   = rollout_agents(obs, agents, params)           # Sec. IV-A, Eq. (mfi), Alg. 1
+    sel  = score_and_select(ro, params, weights)         # Sec. IV-A cost, selection
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+from dataclasses import dataclass
+
+from . import _abi
+from ._abi import check
+
+__all__ = ["Context", "context", "Obstacles", "filter_cloud", "filter_workspace_bytes",
+           "rollout_agents", "score_and_select", "pick_tuning", "sync", "GmappError"]
+
+GmappError = _abi.GmappError
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream(stream) -> C.c_void_p:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """One library context per CUDA device (owns the device error word)."""
+
+    def __init__(self, device: int = 0):
+        lib = _abi.load()
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2606_12579_b300 needs a CUDA device (no CPU fallback)")
+        torch.cuda.init()
+        h = C.c_void_p()
+        check(lib.gmapp_create(C.byref(h), int(device)), "gmapp_create")
+        self.handle = h
+        self.device = int(device)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _abi._lib is not None:
+            _abi._lib.gmapp_destroy(h)
+            self.handle = None
+
+    def sync(self, stream=None) -> None:
+        """Wait for the stream and raise if a kernel flagged a device error."""
+        check(_abi.load().gmapp_sync(self.handle, _stream(stream)), "gmapp_sync")
+
+    def device_error_bits(self) -> int:
+        b = C.c_uint32()
+        check(_abi.load().gmapp_peek_device_error(self.handle, C.byref(b)), "peek")
+        return int(b.value)
+
+
+_contexts: dict = {}
+
+
+def context(device: int | None = None) -> Context:
+    torch = _torch()
+    d = torch.cuda.current_device() if device is None else int(device)
+    if d not in _contexts:
+        _contexts[d] = Context(d)
+    return _contexts[d]
+
+
+def sync(stream=None, device: int | None = None) -> None:
+    context(device).sync(stream)
+
+
+# ---------------------------------------------------------------------------
+# Obstacles (the sphere world S_W)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Obstacles:
+    x: object
+    y: object
+    z: object
+    keys: object
+    counts: object
+    rep_idx: object
+    n: object          # device int32 [1]
+    cap: int
+    r_O: float
+
+    @staticmethod
+    def empty(cap: int, device=None) -> "Obstacles":
+        torch = _torch()
+        cap = max(4, (int(cap) + 3) // 4 * 4)
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        f = lambda: torch.empty(cap, dtype=torch.float32, device=dev)  # noqa: E731
+        u = lambda: torch.empty(cap, dtype=torch.int32, device=dev)    # noqa: E731
+        return Obstacles(f(), f(), f(), u(), u(), u(), torch.zeros(1, dtype=torch.int32, device=dev),
+                         cap, 0.0)
+
+    @staticmethod
+    def from_points(xyz, r_O: float, cap: int | None = None) -> "Obstacles":
+        """Obstacle set from a [3, N] tensor of centres (copied to device)."""
+        torch = _torch()
+        n = int(xyz.shape[1])
+        o = Obstacles.empty(max(n, 1) if cap is None else cap)
+        if n > o.cap:
+            raise ValueError(f"{n} obstacles exceed cap {o.cap}")
+        src = xyz.to(device=o.x.device, dtype=torch.float32)
+        o.x[:n].copy_(src[0])
+        o.y[:n].copy_(src[1])
+        o.z[:n].copy_(src[2])
+        o.n.fill_(n)
+        o.r_O = float(r_O)
+        return o
+
+    def count(self) -> int:
+        return int(self.n.item())
+
+    def centres(self):
+        """[3, N_O] view of the valid centres (reads N_O from the device)."""
+        torch = _torch()
+        k = min(self.count(), self.cap)
+        return torch.stack([self.x[:k], self.y[:k], self.z[:k]])
+
+    def _struct(self) -> _abi.Obstacles:
+        s = _abi.Obstacles()
+        s.x, s.y, s.z = self.x.data_ptr(), self.y.data_ptr(), self.z.data_ptr()
+        s.keys = self.keys.data_ptr() if self.keys is not None else None
+        s.counts = self.counts.data_ptr() if self.counts is not None else None
+        s.rep_idx = self.rep_idx.data_ptr() if self.rep_idx is not None else None
+        s.n = self.n.data_ptr()
+        s.cap = int(self.cap)
+        s.r_O = float(self.r_O)
+        return s
+
+
+def _ws_struct(ws) -> _abi.Workspace:
+    s = _abi.Workspace()
+    for a in range(3):
+        s.lo[a] = float(ws.lo[a])
+        s.dims[a] = int(ws.dims[a])
+    s.voxel = float(ws.voxel)
+    s.min_pts = int(getattr(ws, "min_pts", 1))
+    return s
+
+
+def filter_workspace_bytes(n_raw: int, ws) -> int:
+    return int(_abi.load().gmapp_filter_workspace_bytes(int(n_raw), C.byref(_ws_struct(ws))))
+
+
+def filter_cloud(xyz, T, ws, out: Obstacles | None = None, cap: int | None = None,
+                 workspace=None, stream=None) -> Obstacles:
+    """Camera-frame cloud [N, 3] (float32, device) -> S_W (Sec. IV-B, V-A).
+
+    ``T`` is the 3x4 row-major camera-to-world transform (12 numbers), ``ws``
+    any object with ``lo``, ``voxel``, ``dims`` (and ``min_pts``).  The
+    obstacle count stays on the device (``out.n``) until asked for."""
+    torch = _torch()
+    ctx = context()
+    n = int(xyz.shape[0])
+    if out is None:
+        out = Obstacles.empty(cap if cap is not None else max(n, 4))
+    wss = _ws_struct(ws)
+    need = int(_abi.load().gmapp_filter_workspace_bytes(n, C.byref(wss)))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=xyz.device)
+    Tc = (C.c_float * 12)(*[float(v) for v in list(T)])
+    ob = out._struct()
+    check(_abi.load().filter_cloud(ctx.handle, _ptr(xyz), n, C.byref(Tc), C.byref(wss),
+                                   C.byref(ob), _ptr(workspace), int(workspace.numel()),
+                                   _stream(stream)), "filter_cloud")
+    out.r_O = float(ob.r_O)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Rollout and selection
+# ---------------------------------------------------------------------------
+
+AGENT_KEYS = ("p0", "v0", "c", "k_r", "k_a", "r_d", "r_a")
+
+
+def _agents_struct(agents: dict) -> _abi.Agents:
+    s = _abi.Agents()
+    for k in AGENT_KEYS:
+        t = agents[k]
+        if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"):
+            raise ValueError(f"agent array {k} must be a contiguous float32 CUDA tensor")
+        setattr(s, k, t.data_ptr())
+    s.n = int(agents["k_r"].numel())
+    return s
+
+
+def _params_struct(prm) -> _abi.RolloutParams:
+    s = _abi.RolloutParams()
+    for a in range(3):
+        s.goal[a] = float(prm.goal[a])
+    s.dt, s.n_steps = float(prm.dt), int(prm.n_steps)
+    s.damping, s.inv_mass, s.rho = float(prm.damping), float(prm.inv_mass), float(prm.rho)
+    s.eps, s.vel_half = float(prm.eps), float(prm.vel_half)
+    s.clear_margin, s.clear_beta = float(prm.clear_margin), float(prm.clear_beta)
+    s.ckpt_every = int(getattr(prm, "ckpt_every", 0))
+    return s
+
+
+def alloc_rollout_out(n_agents: int, n_steps: int, want_traj=True, want_trace=False,
+                      device=None) -> dict:
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    f = lambda *s: torch.empty(*s, dtype=torch.float32, device=dev)  # noqa: E731
+    out = {"p_final": f(3, n_agents), "v_final": f(3, n_agents), "path_len": f(n_agents),
+           "clear_pen": f(n_agents), "min_clear": f(n_agents),
+           "traj": f(n_agents, n_steps + 1, 3) if want_traj else None,
+           "w_trace": f(n_agents, n_steps) if want_trace else None,
+           "m_trace": f(n_agents, n_steps) if want_trace else None,
+           "f_trace": f(n_agents, n_steps, 3) if want_trace else None,
+           "ckpt": None, "n_agents": n_agents, "n_steps": n_steps}
+    return out
+
+
+def _out_struct(out: dict) -> _abi.RolloutOut:
+    s = _abi.RolloutOut()
+    for k in ("traj", "p_final", "v_final", "path_len", "clear_pen", "min_clear", "w_trace",
+              "m_trace", "f_trace", "ckpt"):
+        t = out.get(k)
+        setattr(s, k, t.data_ptr() if t is not None else None)
+    return s
+
+
+def pick_tuning(obs_cap: int, n_agents: int) -> tuple:
+    t = _abi.Tuning()
+    check(_abi.load().gmapp_pick_tuning(context().handle, int(obs_cap), int(n_agents),
+                                        C.byref(t)), "gmapp_pick_tuning")
+    return (t.cluster, t.agents_per_cta, t.threads)
+
+
+def rollout_agents(obs: Obstacles, agents: dict, prm, out: dict | None = None,
+                   want_traj: bool = True, want_trace: bool = False, tuning=None,
+                   stream=None) -> dict:
+    """Roll every agent N_k steps in one launch (Sec. IV-A, Eq. mfi, Alg. 1).
+
+    ``agents``: dict of contiguous float32 CUDA tensors p0, v0, c [3, N_a] and
+    k_r, k_a, r_d, r_a [N_a].  ``prm``: object with goal, dt, n_steps,
+    damping, inv_mass, rho, eps, vel_half, clear_margin, clear_beta.
+    ``tuning``: optional (cluster, agents_per_cta, threads)."""
+    ctx = context()
+    na = int(agents["k_r"].numel())
+    if out is None:
+        out = alloc_rollout_out(na, int(prm.n_steps), want_traj, want_trace)
+    ob, ag, pr, os_ = obs._struct(), _agents_struct(agents), _params_struct(prm), _out_struct(out)
+    lib = _abi.load()
+    if tuning is None:
+        st = lib.rollout_agents(ctx.handle, C.byref(ob), C.byref(ag), C.byref(pr), C.byref(os_),
+                                _stream(stream))
+    else:
+        t = _abi.Tuning(*[int(v) for v in tuning])
+        st = lib.rollout_agents_tuned(ctx.handle, C.byref(ob), C.byref(ag), C.byref(pr),
+                                      C.byref(os_), C.byref(t), _stream(stream))
+    check(st, "rollout_agents")
+    return out
+
+
+def score_and_select(ro: dict, prm, weights=None, prev_best_cost: float = math.nan,
+                     alpha: float = 1.0, best_traj: bool = True, out: dict | None = None,
+                     stream=None) -> dict:
+    """Costs C_i and the selected agent i* (Sec. IV-A cost and selection).
+    Returns device tensors ``costs`` [N_a], ``best`` [1] (int32, -1 = keep
+    the previous path) and ``best_traj`` [N_k+1, 3]."""
+    torch = _torch()
+    ctx = context()
+    na = int(ro["p_final"].shape[1])
+    dev = ro["p_final"].device
+    if out is None:
+        out = {"costs": torch.empty(na, dtype=torch.float32, device=dev),
+               "best": torch.empty(1, dtype=torch.int32, device=dev),
+               "best_traj": (torch.empty(int(prm.n_steps) + 1, 3, dtype=torch.float32, device=dev)
+                             if best_traj and ro.get("traj") is not None else None)}
+    w = weights if weights is not None else prm
+    cw = _abi.CostWeights(float(w.w_path), float(w.w_goal), float(w.w_clear))
+    os_, pr = _out_struct(ro), _params_struct(prm)
+    check(_abi.load().score_and_select(ctx.handle, C.byref(os_), na, C.byref(pr), C.byref(cw),
+                                       float(prev_best_cost), float(alpha), _ptr(out["costs"]),
+                                       _ptr(out["best"]), _ptr(out.get("best_traj")),
+                                       _stream(stream)), "score_and_select")
+    return out

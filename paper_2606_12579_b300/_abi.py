@@ -1,0 +1,106 @@
+"""ctypes mirror of include/gmapp.h: structures, status codes, prototypes.
+
+Loading the library needs no GPU (the CUDA runtime is linked statically and
+binds to the driver on the first CUDA call); every compute call does.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgmapp.so")
+
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_READY = range(6)
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CAPACITY", 3: "CUDA", 4: "TIMEOUT", 5: "NOT_READY"}
+DEVERR_CAPACITY, DEVERR_TIMEOUT, DEVERR_BOUNDS = 0x1, 0x2, 0x4
+
+P = C.c_void_p
+
+
+class Workspace(C.Structure):
+    _fields_ = [("lo", C.c_float * 3), ("voxel", C.c_float), ("dims", C.c_int32 * 3),
+                ("min_pts", C.c_int32)]
+
+
+class Obstacles(C.Structure):
+    _fields_ = [("x", P), ("y", P), ("z", P), ("keys", P), ("counts", P), ("rep_idx", P),
+                ("n", P), ("cap", C.c_int64), ("r_O", C.c_float)]
+
+
+class Agents(C.Structure):
+    _fields_ = [("p0", P), ("v0", P), ("c", P), ("k_r", P), ("k_a", P), ("r_d", P), ("r_a", P),
+                ("n", C.c_int32)]
+
+
+class RolloutParams(C.Structure):
+    _fields_ = [("goal", C.c_float * 3), ("dt", C.c_float), ("n_steps", C.c_int32),
+                ("damping", C.c_float), ("inv_mass", C.c_float), ("rho", C.c_float),
+                ("eps", C.c_float), ("vel_half", C.c_float), ("clear_margin", C.c_float),
+                ("clear_beta", C.c_float), ("ckpt_every", C.c_int32)]
+
+
+class RolloutOut(C.Structure):
+    _fields_ = [("traj", P), ("p_final", P), ("v_final", P), ("path_len", P), ("clear_pen", P),
+                ("min_clear", P), ("w_trace", P), ("m_trace", P), ("f_trace", P), ("ckpt", P)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("cluster", C.c_int32), ("agents_per_cta", C.c_int32), ("threads", C.c_int32)]
+
+
+class CostWeights(C.Structure):
+    _fields_ = [("w_path", C.c_float), ("w_goal", C.c_float), ("w_clear", C.c_float)]
+
+
+# name -> (restype, argtypes); every entry point declared in include/gmapp.h
+PROTOTYPES = {
+    "gmapp_create": (C.c_int, [C.POINTER(P), C.c_int]),
+    "gmapp_destroy": (None, [P]),
+    "gmapp_last_error": (C.c_char_p, []),
+    "gmapp_sync": (C.c_int, [P, P]),
+    "gmapp_peek_device_error": (C.c_int, [P, C.POINTER(C.c_uint32)]),
+    "gmapp_filter_workspace_bytes": (C.c_size_t, [C.c_int64, C.POINTER(Workspace)]),
+    "filter_cloud": (C.c_int, [P, P, C.c_int64, C.POINTER(C.c_float * 12), C.POINTER(Workspace),
+                               C.POINTER(Obstacles), P, C.c_size_t, P]),
+    "rollout_agents": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
+                                 C.POINTER(RolloutParams), C.POINTER(RolloutOut), P]),
+    "rollout_agents_tuned": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
+                                       C.POINTER(RolloutParams), C.POINTER(RolloutOut),
+                                       C.POINTER(Tuning), P]),
+    "gmapp_pick_tuning": (C.c_int, [P, C.c_int64, C.c_int32, C.POINTER(Tuning)]),
+    "score_and_select": (C.c_int, [P, C.POINTER(RolloutOut), C.c_int32, C.POINTER(RolloutParams),
+                                   C.POINTER(CostWeights), C.c_float, C.c_float, P, P, P, P]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libgmapp.so and bind every prototype; raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with paper_2606_12579_b300/build.py "
+                "(there is no CPU fallback)")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in PROTOTYPES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class GmappError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().gmapp_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status: int, where: str) -> None:
+    if status != OK:
+        raise GmappError(status, where)

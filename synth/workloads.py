@@ -103,7 +103,7 @@ def sphere_workload(seed: int = 1001, n_raw: int = 20000, voxel: float = 0.01,
 def tabletop_workload(seed: int = 1002, n_agents: int = 256, n_steps: int = 500,
                       n_points: int | None = None, voxel: float = 0.005,
                       spheres_at: float | None = None, sphere_seed: int | None = None,
-                      scene_seed: int | None = None) -> dict:
+                      scene_seed: int | None = None, frame_seed: int | None = None) -> dict:
     """Tabletop depth frame: 640x480 render of a table, 3 boxes and 2
     cylinders, 2 mm depth noise, 5% NaN dropouts; workspace 1 x 1 x 0.8 m at
     5 mm voxels; 256 agents, 500 steps."""
@@ -111,7 +111,8 @@ def tabletop_workload(seed: int = 1002, n_agents: int = 256, n_steps: int = 500,
     scene = tabletop_scene(s_scene if scene_seed is None else scene_seed)
     if spheres_at is not None:
         scene.spheres = moving_spheres(sphere_seed if sphere_seed is not None else seed)(spheres_at)
-    xyz, T = render_depth_frame(scene, s_frame, n_points=n_points)
+    xyz, T = render_depth_frame(scene, s_frame if frame_seed is None else frame_seed,
+                                n_points=n_points)
     extent = (1.0, 1.0, 0.8)
     dims = tuple(int(math.ceil(e / voxel - 1e-9)) for e in extent)
     ws = Workspace(lo=TABLE_WS.lo, voxel=voxel, dims=dims)

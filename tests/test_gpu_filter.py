@@ -1,0 +1,162 @@
+"""GPU filter_cloud vs the oracle: bit-exact keys, counts, smallest indices
+and voxel centres (Sec. IV-B, Sec. V-A), at full frame sizes and on the edge
+cases (empty, all rejected, ragged sizes, faces and upper edge, capacity
+overflow, min_pts > 1), plus run-to-run determinism."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth.workloads import Workspace
+
+from _helpers import u32, f32_bits
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def gm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2606_12579_b300 as gm
+    gm.context()
+    return gm
+
+
+def _run(gm, xyz, T, ws, cap=None):
+    import torch
+    x = torch.from_numpy(np.ascontiguousarray(xyz, dtype=np.float32)).cuda()
+    return gm.filter_cloud(x, T, ws, cap=cap if cap is not None else max(4, xyz.shape[0]))
+
+
+def _assert_same(obs, ref):
+    n = obs.count()
+    assert n == ref["n"]
+    k = min(n, obs.cap)
+    assert np.array_equal(u32(obs.keys[:k]), ref["keys"][:k])
+    assert np.array_equal(u32(obs.counts[:k]), ref["counts"][:k])
+    assert np.array_equal(u32(obs.rep_idx[:k]), ref["rep_idx"][:k])
+    for a in ("x", "y", "z"):
+        assert np.array_equal(f32_bits(getattr(obs, a)[:k]), ref[a][:k].view(np.uint32)), a
+
+
+@pytest.mark.parametrize("which", ["sphere", "tabletop", "tabletop_200k_1cm"])
+def test_full_frames_bit_exact(gm, which):
+    if which == "sphere":
+        w = synth.sphere_workload()
+    elif which == "tabletop":
+        w = synth.tabletop_workload(n_agents=1, n_steps=1)
+    else:
+        w = synth.tabletop_workload(n_agents=1, n_steps=1, n_points=200000, voxel=0.01,
+                                    spheres_at=0.37, sphere_seed=5)
+    ref = oracle.filter_cloud(w["xyz"], w["T"], w["workspace"])
+    obs = _run(gm, w["xyz"], w["T"], w["workspace"])
+    gm.sync()
+    _assert_same(obs, ref)
+    assert obs.r_O == pytest.approx(w["workspace"].voxel / 2)
+
+
+def test_golden_tiny_frame(gm):
+    g = json.load(open(os.path.join(GOLD, "filter_tiny.json")))
+    xyz = np.array([[float(v) for v in p] for p in g["points"]], np.float32)
+    for mp, key in ((1, "expected_min_pts_1"), (2, "expected_min_pts_2")):
+        ws = Workspace(lo=tuple(g["lo"]), voxel=g["voxel"], dims=tuple(g["dims"]), min_pts=mp)
+        obs = _run(gm, xyz, np.array(g["T"], np.float32), ws)
+        gm.sync()
+        e = g[key]
+        n = obs.count()
+        assert n == len(e["keys"])
+        assert u32(obs.keys[:n]).tolist() == e["keys"]
+        assert u32(obs.counts[:n]).tolist() == e["counts"]
+        assert u32(obs.rep_idx[:n]).tolist() == e["rep_idx"]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_small_clouds_ragged(gm, seed):
+    """Clusters of points (many per voxel), NaN rows, a random rigid
+    transform, and sizes that are not multiples of 4 or of a block."""
+    g = np.random.Generator(np.random.PCG64(100 + seed))
+    n = int(g.integers(1, 5000)) * 4 + int(g.integers(0, 4))
+    centres = g.uniform(0.0, 0.4, size=(16, 3))
+    xyz = (centres[g.integers(0, 16, n)] + g.normal(0, 0.02, (n, 3))).astype(np.float32)
+    xyz[g.random(n) < 0.05] = np.nan
+    xyz[g.random(n) < 0.01, 1] = np.inf
+    ang = g.uniform(0, 2 * np.pi)
+    R = np.array([[np.cos(ang), 0, np.sin(ang)], [0, 1, 0], [-np.sin(ang), 0, np.cos(ang)]])
+    T = np.concatenate([R, g.uniform(-0.1, 0.3, (3, 1))], axis=1).reshape(-1).astype(np.float32)
+    ws = Workspace(lo=(-0.3, -0.2, -0.4), voxel=float(g.uniform(0.005, 0.03)),
+                   dims=(int(g.integers(20, 90)), int(g.integers(20, 90)), int(g.integers(20, 90))),
+                   min_pts=int(g.integers(1, 4)))
+    ref = oracle.filter_cloud(xyz, T, ws)
+    obs = _run(gm, xyz, T, ws)
+    gm.sync()
+    _assert_same(obs, ref)
+
+
+def test_empty_and_all_rejected(gm):
+    ws = Workspace(lo=(0, 0, 0), voxel=0.1, dims=(10, 10, 10))
+    T = np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], np.float32)
+    for xyz in (np.zeros((0, 3), np.float32), np.full((37, 3), 5.0, np.float32),
+                np.full((9, 3), np.nan, np.float32)):
+        obs = _run(gm, xyz, T, ws)
+        gm.sync()
+        assert obs.count() == 0
+
+
+def test_capacity_overflow_reports_total(gm):
+    w = synth.sphere_workload()
+    ref = oracle.filter_cloud(w["xyz"], w["T"], w["workspace"])
+    obs = _run(gm, w["xyz"], w["T"], w["workspace"], cap=256)
+    with pytest.raises(gm.GmappError) as e:
+        gm.sync()
+    assert e.value.status == 2  # GMAPP_ERR_CAPACITY
+    assert obs.count() == ref["n"]
+    assert np.array_equal(u32(obs.keys[:256]), ref["keys"][:256])
+    assert np.array_equal(u32(obs.counts[:256]), ref["counts"][:256])
+    gm.sync()  # the error word was cleared
+
+
+def test_large_grid_and_max_dims(gm):
+    """A grid near the 2^32-cell limit (bitmap of 256 MB) with a ragged cloud."""
+    g = np.random.Generator(np.random.PCG64(7))
+    xyz = g.uniform(-1, 1, (100003, 3)).astype(np.float32)
+    ws = Workspace(lo=(-1.0, -1.0, -1.0), voxel=float(np.float32(2.0 / 1600)), dims=(1600, 1600, 1600))
+    ref = oracle.filter_cloud(xyz, np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], np.float32), ws)
+    obs = _run(gm, xyz, np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], np.float32), ws)
+    gm.sync()
+    _assert_same(obs, ref)
+
+
+def test_invalid_arguments_rejected_on_host(gm):
+    import torch
+    x = torch.zeros(12, 3, device="cuda")
+    T = [1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0]
+    for ws in (Workspace(lo=(0, 0, 0), voxel=0.0, dims=(4, 4, 4)),
+               Workspace(lo=(0, 0, 0), voxel=0.1, dims=(0, 4, 4)),
+               Workspace(lo=(0, 0, 0), voxel=0.1, dims=(4096, 4096, 4096)),
+               Workspace(lo=(0, 0, 0), voxel=0.1, dims=(4, 4, 4), min_pts=0)):
+        with pytest.raises(gm.GmappError) as e:
+            gm.filter_cloud(x, T, ws)
+        assert e.value.status == 1
+    with pytest.raises(gm.GmappError):
+        gm.filter_cloud(x, [1, 0, 0, float("nan"), 0, 1, 0, 0, 0, 0, 1, 0],
+                        Workspace(lo=(0, 0, 0), voxel=0.1, dims=(4, 4, 4)))
+    with pytest.raises(gm.GmappError):
+        gm.filter_cloud(x[1:], T, Workspace(lo=(0, 0, 0), voxel=0.1, dims=(4, 4, 4)))  # misaligned
+
+
+def test_repeat_determinism(gm):
+    w = synth.tabletop_workload(n_agents=1, n_steps=1)
+    a = _run(gm, w["xyz"], w["T"], w["workspace"])
+    b = _run(gm, w["xyz"], w["T"], w["workspace"])
+    gm.sync()
+    n = a.count()
+    assert n == b.count()
+    for f in ("keys", "counts", "rep_idx", "x", "y", "z"):
+        assert np.array_equal(getattr(a, f)[:n].cpu().numpy(), getattr(b, f)[:n].cpu().numpy())
