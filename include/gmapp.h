@@ -129,6 +129,29 @@ gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n_raw,
                           gmapp_obstacles *out, void *workspace,
                           size_t workspace_bytes, gmapp_stream stream);
 
+/* filter_cloud without any allocation or caller workspace.  The paper has
+ * no counterpart: this exists for callers that must not allocate device
+ * memory once running (a fixed-memory real-time control loop, a process
+ * that may not call cudaMalloc at that point).  Same arguments, arithmetic
+ * and results as filter_cloud, but the scratch lives in one fixed 16 MiB
+ * array inside the library's device image, held by every GPU that loads the
+ * library until the process exits.  No context is needed.
+ *   - Sizes whose scratch would exceed 16 MiB (see
+ *     gmapp_filter_workspace_bytes) are rejected with GMAPP_ERR_CAPACITY
+ *     before anything is launched.
+ *   - The call allocates and frees nothing.  Its first call on a device
+ *     looks up the array's device address (cudaGetSymbolAddress) with that
+ *     device current; make that first call before any stream capture.
+ *   - All calls share the one array (the kernels clear what must start at
+ *     zero), so calls whose work overlaps on the GPU -- on different streams
+ *     or devices' threads racing on one device -- race with each other;
+ *     order them on one stream.
+ *   - Output overflow is reported through *out->n > out->cap only (there is
+ *     no context error word). */
+gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, const float T[12],
+                                  const gmapp_workspace *ws, gmapp_obstacles *out,
+                                  gmapp_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* Rollout: rollout_agents (Sec. IV-A agent dynamics and agent set;           */
 /* Eq. (mfi) circular-field force; Alg. 1 clamp, detection gate, sum)         */

@@ -188,6 +188,22 @@ def filter_cloud(xyz, T, ws, out: Obstacles | None = None, cap: int | None = Non
     return out
 
 
+def filter_cloud_noalloc(xyz, T, ws, out: Obstacles, stream=None) -> Obstacles:
+    """filter_cloud whose scratch is the library's fixed 16 MiB device array:
+    no workspace and no allocation inside the call (``out`` is the caller's).
+    For callers that may not allocate once running.  Calls that overlap on
+    the GPU share the array and race; the first call on a device should come
+    before any stream capture."""
+    n = int(xyz.shape[0])
+    Tc = (C.c_float * 12)(*[float(v) for v in list(T)])
+    wss = _ws_struct(ws)
+    ob = out._struct()
+    check(_abi.load().filter_cloud_noalloc(_ptr(xyz), n, C.byref(Tc), C.byref(wss), C.byref(ob),
+                                           _stream(stream)), "filter_cloud_noalloc")
+    out.r_O = float(ob.r_O)
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Rollout and selection
 # ---------------------------------------------------------------------------

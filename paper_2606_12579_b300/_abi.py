@@ -64,6 +64,8 @@ PROTOTYPES = {
     "gmapp_filter_workspace_bytes": (C.c_size_t, [C.c_int64, C.POINTER(Workspace)]),
     "filter_cloud": (C.c_int, [P, P, C.c_int64, C.POINTER(C.c_float * 12), C.POINTER(Workspace),
                                C.POINTER(Obstacles), P, C.c_size_t, P]),
+    "filter_cloud_noalloc": (C.c_int, [P, C.c_int64, C.POINTER(C.c_float * 12),
+                                       C.POINTER(Workspace), C.POINTER(Obstacles), P]),
     "rollout_agents": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
                                  C.POINTER(RolloutParams), C.POINTER(RolloutOut), P]),
     "rollout_agents_tuned": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),

@@ -16,6 +16,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "gmapp_internal.cuh"
 
@@ -533,6 +534,165 @@ extern "C" gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n
         k_keep_sums<<<static_cast<int>(L.n_tblocks), kThreads, 0, stream>>>(
             tcounts, n_occ, ws->min_pts, tsums, toffsets, n_keep_counter, out->n, out->cap,
             ctx->d_err);
+        EmitOut o{out->keys, out->counts, out->rep_idx, out->x, out->y, out->z, out->cap};
+        k_keep_emit<<<static_cast<int>(L.n_tblocks), kThreads, 0, stream>>>(
+            tkeys, tcounts, trep, n_occ, toffsets, ws->min_pts, A, o);
+    }
+    GMAPP_CHECK_CUDA(cudaGetLastError());
+    return GMAPP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// filter_cloud_noalloc: the same kernels with their scratch in a fixed,
+// file-scope device array instead of a caller-provided workspace.
+//
+// For callers that may not allocate device memory once running: a real-time
+// control loop whose memory is fixed at start-up, a process without the
+// right to call cudaMalloc at that point, or code that must not grow the
+// device footprint per call.  The array is part of this library's device
+// image: every GPU that loads the library holds kNoAllocScratchBytes until
+// the process exits.
+// ---------------------------------------------------------------------------
+
+namespace gmapp {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+static __device__ uint32_t g_noalloc_err;
+
+// Device addresses of the two symbols, looked up once per device (host code
+// may not use the symbols' names as addresses).
+struct NoAllocSymbols {
+    void *scratch = nullptr;
+    uint32_t *err = nullptr;
+};
+NoAllocSymbols g_noalloc_syms[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+gmapp_status noalloc_symbols(NoAllocSymbols *out) {
+    int dev = 0;
+    GMAPP_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("filter_cloud_noalloc: device %d beyond the supported %d", dev,
+                  kNoAllocMaxDevices);
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocSymbols &s = g_noalloc_syms[dev];
+    if (!s.scratch) {
+        void *scratch = nullptr, *err = nullptr;
+        GMAPP_CHECK_CUDA(cudaGetSymbolAddress(&scratch, g_noalloc_scratch));
+        GMAPP_CHECK_CUDA(cudaGetSymbolAddress(&err, g_noalloc_err));
+        s.scratch = scratch;
+        s.err = static_cast<uint32_t *>(err);
+    }
+    *out = s;
+    return GMAPP_OK;
+}
+
+}  // namespace
+}  // namespace gmapp
+
+extern "C" gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, const float T[12],
+                                             const gmapp_workspace *ws, gmapp_obstacles *out,
+                                             gmapp_stream stream) {
+    if (!T || !out) {
+        set_error("filter_cloud_noalloc: NULL T or out");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    if (n_raw < 0 || n_raw >= 0xFFFFFFFFll || (n_raw > 0 && !xyz)) {
+        set_error("filter_cloud_noalloc: n_raw %lld out of range or xyz NULL", (long long)n_raw);
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    if (!valid_workspace(ws)) {
+        set_error("filter_cloud_noalloc: invalid workspace grid (voxel > 0, 1 <= dims <= 2^24, "
+                  "cells < 2^32-1, min_pts >= 1)");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    if (reinterpret_cast<uintptr_t>(xyz) % 16) {
+        set_error("filter_cloud_noalloc: xyz must be 16-byte aligned");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    if (!out->x || !out->y || !out->z || !out->keys || !out->counts || !out->rep_idx || !out->n ||
+        out->cap < 0) {
+        set_error("filter_cloud_noalloc: output buffers must all be set and cap >= 0");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < 12; ++i)
+        if (!isfinite(T[i])) {
+            set_error("filter_cloud_noalloc: transform entry %d is not finite", i);
+            return GMAPP_ERR_INVALID_ARG;
+        }
+    Layout L = layout(n_raw, ws);
+    if (L.total > kNoAllocScratchBytes) {
+        set_error("filter_cloud_noalloc: this cloud and grid need %zu bytes of scratch, more than "
+                  "the fixed %zu bytes (use filter_cloud with a workspace)",
+                  L.total, kNoAllocScratchBytes);
+        return GMAPP_ERR_CAPACITY;
+    }
+    NoAllocSymbols sym;
+    gmapp_status st = noalloc_symbols(&sym);
+    if (st != GMAPP_OK) return st;
+    int dev = 0, sms = 0;
+    GMAPP_CHECK_CUDA(cudaGetDevice(&dev));
+    GMAPP_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+
+    FilterArgs A;
+    for (int i = 0; i < 12; ++i) A.T[i] = T[i];
+    for (int a = 0; a < 3; ++a) {
+        A.lo[a] = ws->lo[a];
+        A.dimf[a] = static_cast<float>(ws->dims[a]);
+    }
+    A.voxel = ws->voxel;
+    A.nx = ws->dims[0];
+    A.ny = ws->dims[1];
+    A.nz = ws->dims[2];
+    out->r_O = 0.5f * ws->voxel;
+
+    char *base = static_cast<char *>(sym.scratch);
+    uint32_t *bitmap = reinterpret_cast<uint32_t *>(base + L.off_bitmap);
+    uint32_t *prefix = reinterpret_cast<uint32_t *>(base + L.off_prefix);
+    uint32_t *sums = reinterpret_cast<uint32_t *>(base + L.off_sums);
+    uint32_t *offsets = reinterpret_cast<uint32_t *>(base + L.off_offsets);
+    uint32_t *counters = reinterpret_cast<uint32_t *>(base + L.off_counters);
+    uint32_t *keys = reinterpret_cast<uint32_t *>(base + L.off_keys);
+    uint32_t *n_occ = counters + 1;
+    uint32_t *n_keep_counter = counters + 2;
+
+    const int grid_pts = static_cast<int>(std::max<int64_t>(
+        1, std::min<int64_t>((n_raw / 4 + kThreads - 1) / kThreads, (int64_t)sms * 8)));
+    const int grid_zero = static_cast<int>(
+        std::min<int64_t>((L.n_words / 4 + kThreads - 1) / kThreads, (int64_t)sms * 8));
+
+    // k_zero clears the bitmap and the counters: the array keeps whatever
+    // the previous call left in it.
+    k_zero<<<grid_zero, kThreads, 0, stream>>>(reinterpret_cast<uint4 *>(bitmap), L.n_words / 4,
+                                               counters, 16);
+    k_keys<<<grid_pts, kThreads, 0, stream>>>(xyz, n_raw, A, keys, bitmap);
+    k_bitmap_sums<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, sums, offsets,
+                                                                          counters, n_occ);
+    if (ws->min_pts == 1) {
+        EmitOut o{out->keys, out->counts, out->rep_idx, out->x, out->y, out->z, out->cap};
+        k_emit<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, offsets, prefix, A, o);
+        k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, bitmap, prefix, out->counts,
+                                                   out->rep_idx, out->cap);
+        k_publish<<<1, 1, 0, stream>>>(n_occ, out->n, out->cap, sym.err);
+    } else {
+        uint32_t *tkeys = reinterpret_cast<uint32_t *>(base + L.off_tkeys);
+        uint32_t *tcounts = reinterpret_cast<uint32_t *>(base + L.off_tcounts);
+        uint32_t *trep = reinterpret_cast<uint32_t *>(base + L.off_trep);
+        uint32_t *tsums = reinterpret_cast<uint32_t *>(base + L.off_tsums);
+        uint32_t *toffsets = reinterpret_cast<uint32_t *>(base + L.off_toffsets);
+        EmitOut t{tkeys, tcounts, trep, nullptr, nullptr, nullptr, L.n_tmp};
+        k_emit<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, offsets, prefix, A, t);
+        k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, bitmap, prefix, tcounts, trep,
+                                                   L.n_tmp);
+        k_keep_sums<<<static_cast<int>(L.n_tblocks), kThreads, 0, stream>>>(
+            tcounts, n_occ, ws->min_pts, tsums, toffsets, n_keep_counter, out->n, out->cap,
+            sym.err);
         EmitOut o{out->keys, out->counts, out->rep_idx, out->x, out->y, out->z, out->cap};
         k_keep_emit<<<static_cast<int>(L.n_tblocks), kThreads, 0, stream>>>(
             tkeys, tcounts, trep, n_occ, toffsets, ws->min_pts, A, o);
