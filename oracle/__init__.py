@@ -43,8 +43,9 @@ def lib():
                                         P, P, P, P, P, P, P, P, P]
         _lib.oracle_max_threads.restype = C.c_int
         _lib.oracle_set_threads.argtypes = [C.c_int]
-        if hasattr(_lib, "oracle_adjoint"):
-            _lib.oracle_adjoint.restype = None
+        _lib.oracle_adjoint.restype = None
+        _lib.oracle_adjoint.argtypes = [i64, P, P, P, C.c_double, i64, P, P, P, P, P, P, P, P, P,
+                                        P, P, P, P, P, P]
     return _lib
 
 
@@ -185,27 +186,65 @@ def select(c: np.ndarray, prev_best_cost: float = math.nan, alpha: float = 1.0) 
     return int(ok[np.argmin(c[ok])])
 
 
+class _Weights(C.Structure):
+    _fields_ = [("w_path", C.c_double), ("w_goal", C.c_double), ("w_clear", C.c_double)]
+
+
+def adjoint(obs_xyz, r_O: float, agents: dict, prm) -> dict:
+    """Cost of every agent and its gradient with respect to v0 [3, N_a],
+    k_r, k_a [N_a] and c [3, N_a] by the discrete adjoint (reverse sweep of
+    the stored FP64 rollout), plus each agent's branch signature."""
+    ox, oy, oz = (_f64(obs_xyz[a]) for a in range(3))
+    ag = {k: _f64(v) for k, v in agents.items()}
+    na = ag["k_r"].size
+    out = {"cost": np.zeros(na), "g_v0": np.zeros((3, na)), "g_kr": np.zeros(na),
+           "g_ka": np.zeros(na), "g_c": np.zeros((3, na)), "sig": np.zeros(na, np.uint64)}
+    pr = _params(prm)
+    wt = _Weights(float(prm.w_path), float(prm.w_goal), float(prm.w_clear))
+    lib().oracle_adjoint(ox.size, _ptr(ox), _ptr(oy), _ptr(oz), float(r_O), na, _ptr(ag["p0"]),
+                         _ptr(ag["v0"]), _ptr(ag["c"]), _ptr(ag["k_r"]), _ptr(ag["k_a"]),
+                         _ptr(ag["r_d"]), _ptr(ag["r_a"]), C.byref(pr), C.byref(wt),
+                         _ptr(out["cost"]), _ptr(out["g_v0"]), _ptr(out["g_kr"]),
+                         _ptr(out["g_ka"]), _ptr(out["g_c"]), _ptr(out["sig"]))
+    return out
+
+
+GRAD_NAMES = [("v0", 0), ("v0", 1), ("v0", 2), ("k_r", None), ("k_a", None),
+              ("c", 0), ("c", 1), ("c", 2)]
+
+
+def grad_vector(adj: dict, i: int) -> np.ndarray:
+    """The 8 gradient entries of agent i in GRAD_NAMES order."""
+    return np.array([adj["g_v0"][0, i], adj["g_v0"][1, i], adj["g_v0"][2, i], adj["g_kr"][i],
+                     adj["g_ka"][i], adj["g_c"][0, i], adj["g_c"][1, i], adj["g_c"][2, i]])
+
+
 def fd_gradient(obs_xyz, r_O, agents: dict, prm, agent_ids, h: float = 1e-6) -> dict:
     """Central finite differences (step h) of each listed agent's cost with
     respect to v0 (3), k_r, k_a and c (3), perturbing one agent parameter at
-    a time on a one-agent rollout (agents are independent)."""
+    a time on a one-agent rollout (agents are independent).  Returns per
+    agent (gradient[8], valid[8]); an entry is valid only when both
+    perturbed runs have the unperturbed run's branch signature (no clamp,
+    gate or nearest-obstacle change inside +-h: no kink crossed)."""
     out = {}
-    names = [("v0", 0), ("v0", 1), ("v0", 2), ("k_r", None), ("k_a", None),
-             ("c", 0), ("c", 1), ("c", 2)]
     for i in agent_ids:
         one = {k: (_f64(v)[:, i:i + 1] if _f64(v).ndim == 2 else _f64(v)[i:i + 1])
                for k, v in agents.items()}
+        base_sig = adjoint(obs_xyz, r_O, one, prm)["sig"][0]
         g = np.zeros(8)
-        for q, (name, ax) in enumerate(names):
-            vals = []
+        ok = np.zeros(8, bool)
+        for q, (name, ax) in enumerate(GRAD_NAMES):
+            vals, sigs = [], []
             for sgn in (+1, -1):
                 a = {k: v.copy() for k, v in one.items()}
                 if ax is None:
                     a[name][0] += sgn * h
                 else:
                     a[name][ax, 0] += sgn * h
-                ro = rollout(obs_xyz, r_O, a, prm, want_traj=False)
-                vals.append(costs(ro, prm)[0])
+                r = adjoint(obs_xyz, r_O, a, prm)
+                vals.append(r["cost"][0])
+                sigs.append(r["sig"][0])
             g[q] = (vals[0] - vals[1]) / (2 * h)
-        out[int(i)] = g
+            ok[q] = sigs[0] == base_sig and sigs[1] == base_sig
+        out[int(i)] = (g, ok)
     return out

@@ -272,6 +272,194 @@ void oracle_rollout(int64_t n_obs, const double *ox, const double *oy,
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Discrete adjoint of the rollout and cost (reverse-mode derivative of the  */
+/* step map of Sec. IV-A with the Alg. 1 sum and the cost sums)               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * W, its gradient with respect to p, the clearance m and its gradient.
+ * A pair contributes to the gradient only when it is gated in and not
+ * clamped (the clamp and the gate are flat there); the clearance gradient
+ * is the unit vector from the nearest obstacle centre (first index on ties).
+ * Also counts clamped and gated-in pairs (the branch signature of the step).
+ */
+static void cf_weight_grad(const double p[3], int64_t n_obs, const double *ox,
+                           const double *oy, const double *oz, double R, double eps,
+                           double r_d, double *W, double gW[3], double *m, double gm[3],
+                           int64_t *n_clamped, int64_t *n_gated, int64_t *jstar)
+{
+    double w = 0.0, best = INFINITY;
+    int64_t jb = -1, nc = 0, ng = 0;
+    gW[0] = gW[1] = gW[2] = 0.0;
+    for (int64_t j = 0; j < n_obs; ++j) {
+        double dx = p[0] - ox[j], dy = p[1] - oy[j], dz = p[2] - oz[j];
+        double d = sqrt(dx * dx + dy * dy + dz * dz);
+        double s = d - R;
+        if (d < best) { best = d; jb = j; }
+        int clamped = s < eps;
+        if (clamped) s = eps;
+        if (s <= r_d) {
+            ++ng;
+            w += 1.0 / s;
+            if (!clamped) {
+                double q = -1.0 / (s * s * d);
+                gW[0] += q * dx;
+                gW[1] += q * dy;
+                gW[2] += q * dz;
+            } else {
+                ++nc;
+            }
+        }
+    }
+    *W = w;
+    *m = best - R;
+    gm[0] = gm[1] = gm[2] = 0.0;
+    if (jb >= 0 && best > 0.0) {
+        gm[0] = (p[0] - ox[jb]) / best;
+        gm[1] = (p[1] - oy[jb]) / best;
+        gm[2] = (p[2] - oz[jb]) / best;
+    }
+    if (n_clamped) *n_clamped = nc;
+    if (n_gated) *n_gated = ng;
+    if (jstar) *jstar = jb;
+}
+
+typedef struct {
+    double w_path, w_goal, w_clear;
+} oracle_weights;
+
+/*
+ * Cost C_i = w_path sum_k |p_k+1 - p_k| + w_goal |p_N - p_goal|
+ *          + w_clear sum_k softplus(margin - m_k)
+ * and its gradient with respect to v0 (3), k_r, k_a and c (3) for each
+ * agent, by the reverse sweep of the stored forward rollout:
+ *   a_p <- w_goal (p_N - g)/|p_N - g|,  a_v <- 0
+ *   for k = N-1 .. 0:
+ *     a_vk  = a_v + dt (a_p + w_path e_k),   e_k = unit(p_k+1 - p_k)
+ *     Fbar  = vel_half dt inv_mass a_vk
+ *     a_v   = a_vk - D Fbar + rho k_r W_k J_g^T Fbar
+ *     a_p  += -k_a Fbar + rho k_r (g_k . Fbar) grad W_k
+ *             - w_clear sigmoid(beta (margin - m_k)) grad m_k
+ *     dk_a += Fbar . (g - p_k);  dk_r += rho W_k (g_k . Fbar)
+ *     dc   += rho k_r W_k J_gc^T Fbar
+ *   dv0 = a_v
+ * with g(v, c) = |v| c - (v.c) v/|v|,
+ *   J_g^T F  = u (c.F) - c (u.F) - ((v.c)/|v|) (F - u (u.F)),  u = v/|v|
+ *   J_gc^T F = |v| F - v (u.F).
+ * sig[i] is an order-dependent hash of the per-step branch signature
+ * (clamped pairs, gated-in pairs, nearest obstacle): finite differences of
+ * the cost are only meaningful between runs with equal signatures.
+ * Layouts: [3][n] for vector quantities, [n] for scalars; sig may be NULL.
+ */
+void oracle_adjoint(int64_t n_obs, const double *ox, const double *oy, const double *oz,
+                    double r_O, int64_t n_agents, const double *p0, const double *v0,
+                    const double *c, const double *k_r, const double *k_a, const double *r_d,
+                    const double *r_a, const oracle_params *prm, const oracle_weights *wt,
+                    double *cost, double *g_v0, double *g_kr, double *g_ka, double *g_c,
+                    uint64_t *sig)
+{
+    const int64_t N = prm->n_steps;
+    const double h = prm->vel_half * prm->dt * prm->inv_mass;
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t i = 0; i < n_agents; ++i) {
+        double *P = (double *)malloc((size_t)(N + 1) * 3 * sizeof(double));
+        double *V = (double *)malloc((size_t)N * 3 * sizeof(double)); /* v_{k-1} */
+        double *Wk = (double *)malloc((size_t)N * sizeof(double));
+        double *GW = (double *)malloc((size_t)N * 3 * sizeof(double));
+        double *Mk = (double *)malloc((size_t)N * sizeof(double));
+        double *GM = (double *)malloc((size_t)N * 3 * sizeof(double));
+        double p[3] = {p0[i], p0[n_agents + i], p0[2 * n_agents + i]};
+        double v[3] = {v0[i], v0[n_agents + i], v0[2 * n_agents + i]};
+        double ci[3] = {c[i], c[n_agents + i], c[2 * n_agents + i]};
+        const double R = r_a[i] + r_O;
+        double L = 0.0, pen = 0.0;
+        uint64_t hsh = 1469598103934665603ull;
+        for (int64_t k = 0; k < N; ++k) {
+            double w, gW[3], mn, gm[3], g[3], F[3];
+            int64_t nc, ng, js;
+            cf_weight_grad(p, n_obs, ox, oy, oz, R, prm->eps, r_d[i], &w, gW, &mn, gm, &nc, &ng,
+                           &js);
+            uint64_t ev[3] = {(uint64_t)nc, (uint64_t)ng, (uint64_t)js};
+            for (int t = 0; t < 3; ++t) hsh = (hsh ^ ev[t]) * 1099511628211ull;
+            for (int a = 0; a < 3; ++a) {
+                P[3 * k + a] = p[a];
+                V[3 * k + a] = v[a];
+                GW[3 * k + a] = gW[a];
+                GM[3 * k + a] = gm[a];
+            }
+            Wk[k] = w;
+            Mk[k] = mn;
+            cf_direction(v, ci, g);
+            for (int a = 0; a < 3; ++a)
+                F[a] = k_a[i] * (prm->goal[a] - p[a]) - prm->damping * v[a] + prm->rho * k_r[i] * w * g[a];
+            for (int a = 0; a < 3; ++a) v[a] += h * F[a];
+            double pn[3];
+            for (int a = 0; a < 3; ++a) pn[a] = p[a] + prm->dt * v[a];
+            double dx = pn[0] - p[0], dy = pn[1] - p[1], dz = pn[2] - p[2];
+            L += sqrt(dx * dx + dy * dy + dz * dz);
+            pen += softplus(prm->clear_margin - mn, prm->clear_beta);
+            for (int a = 0; a < 3; ++a) p[a] = pn[a];
+        }
+        for (int a = 0; a < 3; ++a) P[3 * N + a] = p[a];
+        double eg[3] = {p[0] - prm->goal[0], p[1] - prm->goal[1], p[2] - prm->goal[2]};
+        double dg = sqrt(eg[0] * eg[0] + eg[1] * eg[1] + eg[2] * eg[2]);
+        cost[i] = wt->w_path * L + wt->w_goal * dg + wt->w_clear * pen;
+
+        double ap[3], av[3] = {0.0, 0.0, 0.0}, dkr = 0.0, dka = 0.0, dc[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < 3; ++a) ap[a] = dg > 0.0 ? wt->w_goal * eg[a] / dg : 0.0;
+        for (int64_t k = N - 1; k >= 0; --k) {
+            const double *pk = P + 3 * k, *pk1 = P + 3 * (k + 1), *vk = V + 3 * k;
+            double e[3] = {pk1[0] - pk[0], pk1[1] - pk[1], pk1[2] - pk[2]};
+            double le = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+            double avk[3], Fb[3];
+            for (int a = 0; a < 3; ++a) {
+                double ea = le > 0.0 ? e[a] / le : 0.0;
+                avk[a] = av[a] + prm->dt * (ap[a] + wt->w_path * ea);
+                Fb[a] = h * avk[a];
+            }
+            double g[3];
+            cf_direction(vk, ci, g);
+            double gF = g[0] * Fb[0] + g[1] * Fb[1] + g[2] * Fb[2];
+            double JgF[3] = {0.0, 0.0, 0.0}, JcF[3] = {0.0, 0.0, 0.0};
+            double vv = vk[0] * vk[0] + vk[1] * vk[1] + vk[2] * vk[2];
+            if (vv >= 1e-30) {
+                double n = sqrt(vv);
+                double u[3] = {vk[0] / n, vk[1] / n, vk[2] / n};
+                double cF = ci[0] * Fb[0] + ci[1] * Fb[1] + ci[2] * Fb[2];
+                double uF = u[0] * Fb[0] + u[1] * Fb[1] + u[2] * Fb[2];
+                double vc = vk[0] * ci[0] + vk[1] * ci[1] + vk[2] * ci[2];
+                for (int a = 0; a < 3; ++a) {
+                    JgF[a] = u[a] * cF - ci[a] * uF - (vc / n) * (Fb[a] - u[a] * uF);
+                    JcF[a] = n * Fb[a] - vk[a] * uF;
+                }
+            }
+            double sg = 1.0 / (1.0 + exp(-prm->clear_beta * (prm->clear_margin - Mk[k])));
+            for (int a = 0; a < 3; ++a) {
+                av[a] = avk[a] - prm->damping * Fb[a] + prm->rho * k_r[i] * Wk[k] * JgF[a];
+                ap[a] += -k_a[i] * Fb[a] + prm->rho * k_r[i] * gF * GW[3 * k + a]
+                         - wt->w_clear * sg * GM[3 * k + a];
+                dka += Fb[a] * (prm->goal[a] - pk[a]);
+                dc[a] += prm->rho * k_r[i] * Wk[k] * JcF[a];
+            }
+            dkr += prm->rho * Wk[k] * gF;
+        }
+        for (int a = 0; a < 3; ++a) {
+            g_v0[a * n_agents + i] = av[a];
+            g_c[a * n_agents + i] = dc[a];
+        }
+        g_kr[i] = dkr;
+        g_ka[i] = dka;
+        if (sig) sig[i] = hsh;
+        free(P);
+        free(V);
+        free(Wk);
+        free(GW);
+        free(Mk);
+        free(GM);
+    }
+}
+
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP
