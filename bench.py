@@ -205,15 +205,16 @@ def run_ours(args, ws, rank, local):
     pinned = torch.from_numpy(np.stack(frames_np)).pin_memory()
     agents = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda()
               for k, v in base["agents"].items()}
-    obs = gm.Obstacles.empty(OBS_CAP)
+    obs = gm.Obstacles.empty(args.obs_cap)
     wsp = torch.empty(gm.filter_workspace_bytes(frames.shape[1], base["workspace"]),
                       dtype=torch.uint8, device="cuda")
-    ro = gm.alloc_rollout_out(na, nk, want_traj=True)
+    ro = gm.alloc_rollout_out(na, nk, want_traj=True, want_clear=False)
     sel = gm.score_and_select(gm.rollout_agents(gm.filter_cloud(frames[0], base["T"], base["workspace"],
                                                                  out=obs, workspace=wsp),
                                                 agents, prm, out=ro), prm)
     ctx.sync()
-    tuning = gm.pick_tuning(OBS_CAP, na)
+    tuning = (tuple(int(v) for v in args.tuning.split(",")) if args.tuning
+              else gm.pick_tuning(args.obs_cap, na))
 
     # N_O per frame (for the interaction count), outside any timed region
     n_obs = []
@@ -362,6 +363,10 @@ def main():
     ap.add_argument("--cpu-agents", type=int, default=64)
     ap.add_argument("--ref-agents", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--obs-cap", type=int, default=OBS_CAP,
+                    help="obstacle capacity of the S_W buffers (a multiple of 4)")
+    ap.add_argument("--tuning", default="",
+                    help="rollout launch shape 'cluster,agents,threads' (default: library choice)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.warmup < 3:

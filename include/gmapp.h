@@ -190,12 +190,14 @@ typedef struct {
     float *p_final;   /* [3][n] */
     float *v_final;   /* [3][n] */
     float *path_len;  /* [n] sum_k |p_k+1 - p_k| */
-    float *clear_pen; /* [n] sum_k softplus_beta(margin - m_k) */
-    float *min_clear; /* [n] min_k m_k */
+    float *clear_pen; /* [n] sum_k softplus_beta(margin - m_k), or NULL */
+    float *min_clear; /* [n] min_k m_k, or NULL */
     float *w_trace;   /* [n][n_steps] W_k (sum of Alg. 1), or NULL */
     float *m_trace;   /* [n][n_steps] clearance m_k, or NULL */
     float *f_trace;   /* [n][n_steps][3] repulsive force f_r at step k, or NULL */
-    float *ckpt;      /* [n_ckpt][6][n] (p, v) at steps 0, K, 2K, ... (adjoint), or NULL */
+    float *ckpt;      /* [ceil(n_steps/K)][6][n] state (p_k, v_{k-1}) entering steps
+                         k = 0, K, 2K, ... with K = ckpt_every (rows: p x,y,z, v x,y,z),
+                         for rollout_adjoint; or NULL */
 } gmapp_rollout_out;
 
 /* Roll all agents forward N_k steps in ONE launch.  Step k (0-based):
@@ -208,12 +210,55 @@ typedef struct {
  * filter_cloud on the same stream without a host round trip).  Obstacle
  * arrays must be 16-byte aligned with obs->cap a multiple of 4.  If N_O
  * exceeds obs->cap or what the launch can keep on chip, nothing is written
- * and GMAPP_DEVERR_CAPACITY is set.  FP32 arithmetic; results are
- * deterministic for a given launch shape. */
+ * and GMAPP_DEVERR_CAPACITY is set.  The clearance m_k is reduced only
+ * when clear_pen, min_clear or m_trace is requested.  FP32 arithmetic;
+ * results are deterministic for a given launch shape. */
 gmapp_status rollout_agents(gmapp_ctx *ctx, const gmapp_obstacles *obs,
                             const gmapp_agents *agents,
                             const gmapp_rollout_params *prm,
                             gmapp_rollout_out *out, gmapp_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Differentiable rollout: rollout_adjoint (discrete adjoint of the step map  */
+/* of Sec. IV-A with the Alg. 1 sum and the cost; the paper states the field  */
+/* is C^1, Sec. IV-A; the adjoint itself is an addition to the paper)         */
+/* ------------------------------------------------------------------------ */
+
+/* Weights of the plan cost (Sec. IV-A cost; see score_and_select). */
+typedef struct {
+    float w_path;  /* weight of the path length */
+    float w_goal;  /* weight of the final distance to the goal */
+    float w_clear; /* weight of the clearance-penalty sum */
+} gmapp_cost_weights;
+
+/* Gradients per agent (device, float32). */
+typedef struct {
+    float *g_v0; /* [3][n] dC/dv0 */
+    float *g_kr; /* [n]    dC/dk_r */
+    float *g_ka; /* [n]    dC/dk_a */
+    float *g_c;  /* [3][n] dC/dc (c used as given, not renormalised) */
+    float *cost; /* [n] C_i recomputed by the adjoint pass, or NULL */
+} gmapp_adjoint_out;
+
+/* Bytes of device workspace rollout_adjoint needs: one 64-byte record per
+ * agent per step of a checkpoint segment (n_agents x ckpt_every x 64). */
+size_t gmapp_adjoint_workspace_bytes(int32_t n_agents, const gmapp_rollout_params *prm);
+
+/* dC_i/d(v0, k_r, k_a, c) for C_i = w_path L_i + w_goal |p_i(N_k) - goal|
+ * + w_clear sum_k softplus(margin - m_k), scaled per agent by grad_cost[i]
+ * (device [n], NULL = 1).  `ckpt` is the checkpoint array written by a
+ * rollout_agents call with the same obstacles, agents and parameters and
+ * prm->ckpt_every = K >= 1.  The pass recomputes each K-step segment from
+ * its checkpoint (last segment first), storing per-step W, grad W and the
+ * nearest obstacle, then sweeps the segment backwards.  Derivatives are
+ * those of the branch taken: pairs outside the gate or inside the clamp
+ * contribute no gradient, and the clearance gradient follows the nearest
+ * obstacle.  FP32; deterministic for a given launch. */
+gmapp_status rollout_adjoint(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                             const gmapp_agents *agents, const gmapp_rollout_params *prm,
+                             const gmapp_cost_weights *w, const float *ckpt,
+                             const float *grad_cost, gmapp_adjoint_out *out,
+                             void *workspace, size_t workspace_bytes, gmapp_stream stream);
 
 /* Launch shape of the rollout kernel (see rollout_agents_tuned). */
 typedef struct {
@@ -231,26 +276,40 @@ gmapp_status rollout_agents_tuned(gmapp_ctx *ctx, const gmapp_obstacles *obs,
                                   gmapp_rollout_out *out, const gmapp_tuning *tune,
                                   gmapp_stream stream);
 
-/* The launch shape rollout_agents would choose for these sizes. */
+/* Autotuner of the launch shape (for the batched/served pattern: the shape
+ * is picked by measurement).  Ranks every shape that fits obs->cap by the
+ * library's cost model (slowest CTA's pair count, co-resident clusters,
+ * per-step exchange), runs the best `max_candidates` of them on the
+ * caller's own inputs for min(probe_steps, n_steps) steps (CUDA events on
+ * `stream`; each candidate once to warm up, once timed), and stores the
+ * fastest in the context's cache, so later rollout_agents calls with the
+ * same (obs->cap, agents->n, clearance outputs) use it.  Overwrites `out`.
+ * Synchronous (waits for the timing events).  best_ms (may be NULL)
+ * receives the fastest time scaled to the full n_steps. */
+gmapp_status gmapp_autotune_rollout(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                                    const gmapp_agents *agents,
+                                    const gmapp_rollout_params *prm,
+                                    gmapp_rollout_out *out, int32_t max_candidates,
+                                    int32_t probe_steps, gmapp_tuning *best, float *best_ms,
+                                    gmapp_stream stream);
+
+/* The launch shape rollout_agents would choose for these sizes (for a
+ * rollout that requests no clearance output): the autotuned shape if one
+ * is cached, else the cost model's choice. */
 gmapp_status gmapp_pick_tuning(gmapp_ctx *ctx, int64_t obs_cap, int32_t n_agents,
                                gmapp_tuning *tune);
 
 /* ------------------------------------------------------------------------ */
 /* Cost and selection: score_and_select (Sec. IV-A "Cost Functions" and        */
-/* "Selection Mechanism")                                                     */
+/* "Selection Mechanism"; gmapp_cost_weights is declared above)               */
 /* ------------------------------------------------------------------------ */
-
-typedef struct {
-    float w_path;  /* weight of the path length */
-    float w_goal;  /* weight of the final distance to the goal */
-    float w_clear; /* weight of the clearance-penalty sum */
-} gmapp_cost_weights;
 
 /* C_i = w_path L_i + w_goal |p_i(N_k) - p_goal| + w_clear pen_i for every
  * agent, then i* = argmin_i C_i with ties to the lowest index.  With a
  * previous best cost (prev_best_cost not NaN) only agents with
  * C_i < alpha * prev_best_cost qualify and i* = -1 when none does (keep the
- * previous path).  Reads ro->p_final, path_len, clear_pen (device).
+ * previous path).  Reads ro->p_final, path_len and, when w_clear != 0,
+ * clear_pen (device; NULL counts as zero penalty when w_clear == 0).
  *   costs      device [n_agents] float32 (written)
  *   best       device, one int32 (written)
  *   best_traj  device [(n_steps+1) * 3] float32: the selected agent's

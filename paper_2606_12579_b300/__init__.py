@@ -20,8 +20,9 @@ from dataclasses import dataclass
 from . import _abi
 from ._abi import check
 
-__all__ = ["Context", "context", "Obstacles", "filter_cloud", "filter_workspace_bytes",
-           "rollout_agents", "score_and_select", "pick_tuning", "sync", "GmappError"]
+__all__ = ["Context", "context", "Obstacles", "filter_cloud", "filter_cloud_noalloc",
+           "filter_workspace_bytes", "rollout_agents", "score_and_select", "pick_tuning",
+           "autotune_rollout", "rollout_adjoint", "GMappRollout", "sync", "GmappError"]
 
 GmappError = _abi.GmappError
 
@@ -235,12 +236,13 @@ def _params_struct(prm) -> _abi.RolloutParams:
 
 
 def alloc_rollout_out(n_agents: int, n_steps: int, want_traj=True, want_trace=False,
-                      device=None) -> dict:
+                      want_clear=True, device=None) -> dict:
     torch = _torch()
     dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
     f = lambda *s: torch.empty(*s, dtype=torch.float32, device=dev)  # noqa: E731
     out = {"p_final": f(3, n_agents), "v_final": f(3, n_agents), "path_len": f(n_agents),
-           "clear_pen": f(n_agents), "min_clear": f(n_agents),
+           "clear_pen": f(n_agents) if want_clear else None,
+           "min_clear": f(n_agents) if want_clear else None,
            "traj": f(n_agents, n_steps + 1, 3) if want_traj else None,
            "w_trace": f(n_agents, n_steps) if want_trace else None,
            "m_trace": f(n_agents, n_steps) if want_trace else None,
@@ -265,9 +267,28 @@ def pick_tuning(obs_cap: int, n_agents: int) -> tuple:
     return (t.cluster, t.agents_per_cta, t.threads)
 
 
+def autotune_rollout(obs: Obstacles, agents: dict, prm, out: dict | None = None,
+                     candidates: int = 12, probe_steps: int = 60, stream=None):
+    """Measure up to ``candidates`` launch shapes on these inputs and cache
+    the fastest for later rollouts of the same sizes; returns
+    ((cluster, agents_per_cta, threads), ms scaled to the full horizon)."""
+    ctx = context()
+    na = int(agents["k_r"].numel())
+    if out is None:
+        out = alloc_rollout_out(na, int(prm.n_steps))
+    ob, ag, pr, os_ = obs._struct(), _agents_struct(agents), _params_struct(prm), _out_struct(out)
+    t = _abi.Tuning()
+    ms = C.c_float()
+    check(_abi.load().gmapp_autotune_rollout(ctx.handle, C.byref(ob), C.byref(ag), C.byref(pr),
+                                             C.byref(os_), int(candidates), int(probe_steps),
+                                             C.byref(t), C.byref(ms), _stream(stream)),
+          "gmapp_autotune_rollout")
+    return (t.cluster, t.agents_per_cta, t.threads), float(ms.value)
+
+
 def rollout_agents(obs: Obstacles, agents: dict, prm, out: dict | None = None,
-                   want_traj: bool = True, want_trace: bool = False, tuning=None,
-                   stream=None) -> dict:
+                   want_traj: bool = True, want_trace: bool = False, want_clear: bool = True,
+                   tuning=None, stream=None) -> dict:
     """Roll every agent N_k steps in one launch (Sec. IV-A, Eq. mfi, Alg. 1).
 
     ``agents``: dict of contiguous float32 CUDA tensors p0, v0, c [3, N_a] and
@@ -277,7 +298,7 @@ def rollout_agents(obs: Obstacles, agents: dict, prm, out: dict | None = None,
     ctx = context()
     na = int(agents["k_r"].numel())
     if out is None:
-        out = alloc_rollout_out(na, int(prm.n_steps), want_traj, want_trace)
+        out = alloc_rollout_out(na, int(prm.n_steps), want_traj, want_trace, want_clear)
     ob, ag, pr, os_ = obs._struct(), _agents_struct(agents), _params_struct(prm), _out_struct(out)
     lib = _abi.load()
     if tuning is None:
@@ -314,3 +335,86 @@ def score_and_select(ro: dict, prm, weights=None, prev_best_cost: float = math.n
                                        _ptr(out["best"]), _ptr(out.get("best_traj")),
                                        _stream(stream)), "score_and_select")
     return out
+
+
+# ---------------------------------------------------------------------------
+# Differentiable rollout
+# ---------------------------------------------------------------------------
+
+def rollout_adjoint(obs: Obstacles, agents: dict, prm, ckpt, grad_cost=None, weights=None,
+                    want_cost: bool = False, workspace=None, stream=None) -> dict:
+    """dC_i/d(v0, k_r, k_a, c) by the adjoint kernel, from the checkpoints of
+    a forward rollout_agents call (``out["ckpt"]`` with prm.ckpt_every = K).
+    ``grad_cost`` ([N_a], device) scales each agent's gradient."""
+    torch = _torch()
+    ctx = context()
+    na = int(agents["k_r"].numel())
+    dev = agents["k_r"].device
+    f = lambda *s: torch.empty(*s, dtype=torch.float32, device=dev)  # noqa: E731
+    out = {"g_v0": f(3, na), "g_kr": f(na), "g_ka": f(na), "g_c": f(3, na),
+           "cost": f(na) if want_cost else None}
+    pr = _params_struct(prm)
+    need = int(_abi.load().gmapp_adjoint_workspace_bytes(na, C.byref(pr)))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    w = weights if weights is not None else prm
+    cw = _abi.CostWeights(float(w.w_path), float(w.w_goal), float(w.w_clear))
+    ao = _abi.AdjointOut(*[out[k].data_ptr() if out[k] is not None else None
+                           for k in ("g_v0", "g_kr", "g_ka", "g_c", "cost")])
+    if grad_cost is not None:
+        grad_cost = grad_cost.to(dtype=torch.float32).contiguous()
+    check(_abi.load().rollout_adjoint(ctx.handle, C.byref(obs._struct()), C.byref(_agents_struct(agents)),
+                                      C.byref(pr), C.byref(cw), _ptr(ckpt), _ptr(grad_cost),
+                                      C.byref(ao), _ptr(workspace), int(workspace.numel()),
+                                      _stream(stream)), "rollout_adjoint")
+    return out
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class GMappRollout(torch.autograd.Function):
+        """costs = GMappRollout.apply(v0, k_r, k_a, c, obstacles, agents, prm)
+
+        Forward: rollout_agents with checkpoints every prm.ckpt_every steps,
+        then the per-agent plan cost C_i (score_and_select).  Backward:
+        rollout_adjoint with grad_cost = dLoss/dC_i, giving gradients for
+        v0 [3, N_a], k_r, k_a [N_a] and c [3, N_a].  ``agents`` supplies the
+        remaining agent arrays (p0, r_d, r_a)."""
+
+        @staticmethod
+        def forward(fctx, v0, k_r, k_a, c, obstacles, agents, prm):
+            ag = dict(agents)
+            ag.update(v0=v0.detach().contiguous(), k_r=k_r.detach().contiguous(),
+                      k_a=k_a.detach().contiguous(), c=c.detach().contiguous())
+            na, K = int(k_r.numel()), int(prm.ckpt_every)
+            out = alloc_rollout_out(na, int(prm.n_steps), want_traj=True,
+                                    want_clear=float(prm.w_clear) != 0.0)
+            out["ckpt"] = torch.empty((int(prm.n_steps) + K - 1) // K, 6, na,
+                                      dtype=torch.float32, device=v0.device)
+            rollout_agents(obstacles, ag, prm, out=out)
+            sel = score_and_select(out, prm, best_traj=False)
+            fctx.save_for_backward(out["ckpt"])
+            fctx.obstacles, fctx.agents, fctx.prm = obstacles, ag, prm
+            return sel["costs"].clone()
+
+        @staticmethod
+        def backward(fctx, grad_costs):
+            (ckpt,) = fctx.saved_tensors
+            g = rollout_adjoint(fctx.obstacles, fctx.agents, fctx.prm, ckpt,
+                                grad_cost=grad_costs.contiguous())
+            return g["g_v0"], g["g_kr"], g["g_ka"], g["g_c"], None, None, None
+
+    return GMappRollout
+
+
+_GMappRollout = None
+
+
+def __getattr__(name):
+    global _GMappRollout
+    if name == "GMappRollout":
+        if _GMappRollout is None:
+            _GMappRollout = _autograd_function()
+        return _GMappRollout
+    raise AttributeError(name)

@@ -46,6 +46,10 @@ class RolloutOut(C.Structure):
                 ("min_clear", P), ("w_trace", P), ("m_trace", P), ("f_trace", P), ("ckpt", P)]
 
 
+class AdjointOut(C.Structure):
+    _fields_ = [("g_v0", P), ("g_kr", P), ("g_ka", P), ("g_c", P), ("cost", P)]
+
+
 class Tuning(C.Structure):
     _fields_ = [("cluster", C.c_int32), ("agents_per_cta", C.c_int32), ("threads", C.c_int32)]
 
@@ -72,6 +76,14 @@ PROTOTYPES = {
                                        C.POINTER(RolloutParams), C.POINTER(RolloutOut),
                                        C.POINTER(Tuning), P]),
     "gmapp_pick_tuning": (C.c_int, [P, C.c_int64, C.c_int32, C.POINTER(Tuning)]),
+    "gmapp_autotune_rollout": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
+                                         C.POINTER(RolloutParams), C.POINTER(RolloutOut),
+                                         C.c_int32, C.c_int32, C.POINTER(Tuning),
+                                         C.POINTER(C.c_float), P]),
+    "gmapp_adjoint_workspace_bytes": (C.c_size_t, [C.c_int32, C.POINTER(RolloutParams)]),
+    "rollout_adjoint": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
+                                  C.POINTER(RolloutParams), C.POINTER(CostWeights), P, P,
+                                  C.POINTER(AdjointOut), P, C.c_size_t, P]),
     "score_and_select": (C.c_int, [P, C.POINTER(RolloutOut), C.c_int32, C.POINTER(RolloutParams),
                                    C.POINTER(CostWeights), C.c_float, C.c_float, P, P, P, P]),
 }

@@ -112,6 +112,15 @@ __device__ __forceinline__ void st_cluster_v2f32(uint32_t addr, float a, float b
                  : "memory");
 }
 
+// Split cluster barrier: arrive (release: this thread's earlier stores,
+// including DSMEM stores, become visible to the cluster) ... wait (acquire).
+__device__ __forceinline__ void cluster_arrive() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
                  "barrier.cluster.wait.acquire.aligned;" ::

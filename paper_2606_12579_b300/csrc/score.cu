@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(kThreads) k_score_select(const ScoreArgs S) {
         const float dy = S.p_final[S.n + i] - S.goal[1];
         const float dz = S.p_final[2 * S.n + i] - S.goal[2];
         const float dist = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
-        const float C = S.w_path * S.path_len[i] + S.w_goal * dist + S.w_clear * S.clear_pen[i];
+        const float pen = S.clear_pen ? S.clear_pen[i] : 0.0f;
+        const float C = S.w_path * S.path_len[i] + S.w_goal * dist + S.w_clear * pen;
         S.costs[i] = C;
         const bool ok = !isnan(C) && (!has_prev || C < thr);
         if (ok && C < bv) {  // i ascends within a thread: strict < keeps the lowest index
@@ -102,8 +103,10 @@ extern "C" gmapp_status score_and_select(gmapp_ctx *ctx, const gmapp_rollout_out
         set_error("score_and_select: NULL argument or n_agents < 1");
         return GMAPP_ERR_INVALID_ARG;
     }
-    if (!ro->p_final || !ro->path_len || !ro->clear_pen || (best_traj && !ro->traj)) {
-        set_error("score_and_select: rollout outputs missing (best_traj needs ro->traj)");
+    if (!ro->p_final || !ro->path_len || (best_traj && !ro->traj) ||
+        (w->w_clear != 0.0f && !ro->clear_pen)) {
+        set_error("score_and_select: rollout outputs missing (best_traj needs ro->traj, "
+                  "w_clear != 0 needs ro->clear_pen)");
         return GMAPP_ERR_INVALID_ARG;
     }
     if (!isnan(prev_best_cost) && !isfinite(alpha)) {

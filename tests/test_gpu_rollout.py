@@ -139,7 +139,7 @@ def test_tabletop_full_size_sampled_agents(gm):
 
 
 SHAPES = [(1, 8, 256), (1, 3, 128), (2, 4, 256), (3, 5, 384), (4, 8, 512), (5, 2, 256),
-          (8, 1, 128), (8, 16, 256), (16, 7, 256), (16, 16, 512), (7, 11, 384)]
+          (8, 1, 128), (8, 16, 256), (16, 7, 256), (16, 8, 512), (7, 10, 384)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "c%d_a%d_t%d" % s)
@@ -228,3 +228,20 @@ def test_invalid_arguments(gm):
         gm.rollout_agents(o, ag, w["params"], tuning=(17, 4, 256))
     with pytest.raises(gm.GmappError):
         gm.rollout_agents(o, ag, w["params"], tuning=(2, 4, 200))
+
+
+def test_autotuner_picks_a_measured_shape(gm):
+    """The autotuner times candidate shapes on the caller's inputs, caches
+    the fastest, and later rollouts of the same sizes use it."""
+    w = synth.sphere_workload(n_agents=40, n_steps=150)
+    obs, r_O = _filtered(w)
+    o = _gpu_obstacles(gm, obs, r_O, cap=4096)
+    ag = to_dev_agents(w["agents"])
+    out = gm.alloc_rollout_out(40, 150, want_clear=False)
+    shape, ms = gm.autotune_rollout(o, ag, w["params"], out=out, candidates=6, probe_steps=30)
+    assert ms > 0 and len(shape) == 3
+    assert gm.pick_tuning(4096, 40) == shape
+    res = gm.rollout_agents(o, ag, w["params"])
+    gm.sync()
+    ref = oracle.rollout(obs, r_O, w["agents"], w["params"])
+    _compare_rollout(res, ref)
