@@ -321,6 +321,71 @@ gmapp_status score_and_select(gmapp_ctx *ctx, const gmapp_rollout_out *ro,
                               float alpha, float *costs, int32_t *best,
                               float *best_traj, gmapp_stream stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched uneven queries: rollout_batch (the perception -> rollout -> select */
+/* query of Sec. IV for many scenes at once; the paper launches one force     */
+/* kernel per agent per step, Alg. 1 and Sec. IV-D)                           */
+/* ------------------------------------------------------------------------ */
+
+/* One planning query: its cloud and grid, its agents and constants, and the
+ * device buffers its results go to (all owned by the caller). */
+typedef struct {
+    const float *xyz;         /* device, n_raw x 3 camera-frame points, 16-byte aligned */
+    int64_t n_raw;
+    float T[12];              /* camera-to-world, row-major 3x4 */
+    gmapp_workspace ws;       /* voxel grid; min_pts must be 1 in a batch */
+    gmapp_agents agents;      /* device agent arrays */
+    gmapp_rollout_params prm; /* per-query horizon, goal and constants */
+    gmapp_cost_weights w;
+    gmapp_obstacles obs;      /* S_W buffers of this query (cap >= 4, multiple of 4) */
+    gmapp_rollout_out out;    /* p_final, v_final, path_len required; traj,
+                                 clear_pen, min_clear optional; traces and
+                                 checkpoints are not produced in a batch */
+    float *costs;             /* device [N_a] */
+    int32_t *best;            /* device [1] */
+    float *best_traj;         /* device [(n_steps+1)*3] or NULL */
+} gmapp_query;
+
+typedef struct gmapp_batch gmapp_batch;
+
+/* Prepare a batch of n_q queries: validates every query, uploads a device
+ * descriptor table and allocates the queue and the filter scratch of all
+ * queries (the only allocations; runs allocate nothing).  The query
+ * buffers are bound by address: refill them between runs.  Each work item
+ * keeps up to about 18.9k obstacles of its query in one CTA's shared memory;
+ * a larger obstacle set has its remainder read from L2 every step.
+ * Default tuning: 8 agents per work item, 256 threads. */
+gmapp_status gmapp_batch_create(gmapp_ctx *ctx, const gmapp_query *queries, int32_t n_q,
+                                gmapp_batch **out);
+void gmapp_batch_destroy(gmapp_batch *batch);
+
+/* Work-item size (agents per item: 2, 4, 6, 8, 12 or 16) and threads per CTA
+ * (256, 384, 512) of the persistent rollout kernel.  Discards a captured
+ * graph. */
+gmapp_status gmapp_batch_set_tuning(gmapp_batch *batch, int32_t agents_per_item,
+                                    int32_t threads);
+
+/* Enqueue the whole batch on `stream`: batched filter (5 launches over all
+ * queries), the planner (N_O of every query, work items ordered by cost,
+ * largest first), ONE persistent rollout launch whose CTAs pop
+ * (query, agent group) items from a device queue, and a batched
+ * score/select (one CTA per query).  Results equal running each query alone
+ * with the same work-item size, bit for bit: each item's arithmetic depends
+ * only on its own query. */
+gmapp_status rollout_batch(gmapp_batch *batch, gmapp_stream stream);
+
+/* Same as rollout_batch through a CUDA graph: the first call captures the
+ * sequence on `stream` (which must not be the legacy default stream), later
+ * calls replay it. */
+gmapp_status gmapp_batch_launch_graph(gmapp_batch *batch, gmapp_stream stream);
+
+/* Autotuner of the work-item size and thread count: times every supported
+ * (agents per item, threads) pair on the batch's own inputs (one warm-up
+ * and one timed run each, CUDA events on `stream`), keeps the fastest.
+ * Synchronous.  best->cluster is 1. */
+gmapp_status gmapp_batch_autotune(gmapp_batch *batch, gmapp_stream stream, gmapp_tuning *best,
+                                  float *best_ms);
+
 #ifdef __cplusplus
 }
 #endif

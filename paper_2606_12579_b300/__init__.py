@@ -418,3 +418,84 @@ def __getattr__(name):
             _GMappRollout = _autograd_function()
         return _GMappRollout
     raise AttributeError(name)
+
+
+# ---------------------------------------------------------------------------
+# Batched uneven queries
+# ---------------------------------------------------------------------------
+
+class Batch:
+    """Many planning queries through one fixed launch sequence (batched
+    filter, planner, one persistent rollout launch, batched select), with
+    optional CUDA-graph replay and an autotuner of the work-item size.
+
+    ``queries``: list of dicts with ``xyz`` (device [N, 3] float32), ``T``,
+    ``ws``, ``agents`` (device arrays), ``prm`` and optionally ``obs_cap``
+    (default: the raw point count rounded up to 4) and ``want_traj``.
+    Outputs are allocated here; ``results[q]`` holds the query's obstacle
+    set, rollout outputs, ``costs``, ``best`` and ``best_traj``."""
+
+    def __init__(self, queries: list, want_traj: bool = True, want_clear: bool = False):
+        torch = _torch()
+        ctx = context()
+        self._keep = []
+        self.results = []
+        arr = (_abi.Query * len(queries))()
+        for q, spec in enumerate(queries):
+            xyz = spec["xyz"]
+            prm = spec["prm"]
+            na = int(spec["agents"]["k_r"].numel())
+            cap = int(spec.get("obs_cap", max(4, (int(xyz.shape[0]) + 3) // 4 * 4)))
+            obs = Obstacles.empty(cap)
+            obs.r_O = 0.5 * float(spec["ws"].voxel)
+            out = alloc_rollout_out(na, int(prm.n_steps), want_traj=spec.get("want_traj", want_traj),
+                                    want_clear=want_clear)
+            dev = xyz.device
+            res = {"obs": obs, "out": out, "costs": torch.empty(na, dtype=torch.float32, device=dev),
+                   "best": torch.empty(1, dtype=torch.int32, device=dev),
+                   "best_traj": (torch.empty(int(prm.n_steps) + 1, 3, dtype=torch.float32, device=dev)
+                                 if out["traj"] is not None else None)}
+            self.results.append(res)
+            self._keep.append((xyz, spec["agents"]))
+            Q = arr[q]
+            Q.xyz = xyz.data_ptr()
+            Q.n_raw = int(xyz.shape[0])
+            for i, v in enumerate(list(spec["T"])):
+                Q.T[i] = float(v)
+            Q.ws = _ws_struct(spec["ws"])
+            Q.agents = _agents_struct(spec["agents"])
+            Q.prm = _params_struct(prm)
+            Q.w = _abi.CostWeights(float(prm.w_path), float(prm.w_goal), float(prm.w_clear))
+            Q.obs = obs._struct()
+            Q.out = _out_struct(out)
+            Q.costs = res["costs"].data_ptr()
+            Q.best = res["best"].data_ptr()
+            Q.best_traj = res["best_traj"].data_ptr() if res["best_traj"] is not None else None
+        h = C.c_void_p()
+        check(_abi.load().gmapp_batch_create(ctx.handle, arr, len(queries), C.byref(h)),
+              "gmapp_batch_create")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _abi._lib is not None:
+            _abi._lib.gmapp_batch_destroy(h)
+            self.handle = None
+
+    def run(self, stream=None) -> None:
+        check(_abi.load().rollout_batch(self.handle, _stream(stream)), "rollout_batch")
+
+    def launch_graph(self, stream) -> None:
+        check(_abi.load().gmapp_batch_launch_graph(self.handle, _stream(stream)),
+              "gmapp_batch_launch_graph")
+
+    def set_tuning(self, agents_per_item: int, threads: int) -> None:
+        check(_abi.load().gmapp_batch_set_tuning(self.handle, int(agents_per_item), int(threads)),
+              "gmapp_batch_set_tuning")
+
+    def autotune(self, stream=None):
+        t = _abi.Tuning()
+        ms = C.c_float()
+        check(_abi.load().gmapp_batch_autotune(self.handle, _stream(stream), C.byref(t), C.byref(ms)),
+              "gmapp_batch_autotune")
+        return (t.agents_per_cta, t.threads), float(ms.value)

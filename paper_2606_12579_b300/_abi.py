@@ -58,6 +58,13 @@ class CostWeights(C.Structure):
     _fields_ = [("w_path", C.c_float), ("w_goal", C.c_float), ("w_clear", C.c_float)]
 
 
+class Query(C.Structure):
+    _fields_ = [("xyz", P), ("n_raw", C.c_int64), ("T", C.c_float * 12), ("ws", Workspace),
+                ("agents", Agents), ("prm", RolloutParams), ("w", CostWeights),
+                ("obs", Obstacles), ("out", RolloutOut), ("costs", P), ("best", P),
+                ("best_traj", P)]
+
+
 # name -> (restype, argtypes); every entry point declared in include/gmapp.h
 PROTOTYPES = {
     "gmapp_create": (C.c_int, [C.POINTER(P), C.c_int]),
@@ -84,6 +91,12 @@ PROTOTYPES = {
     "rollout_adjoint": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
                                   C.POINTER(RolloutParams), C.POINTER(CostWeights), P, P,
                                   C.POINTER(AdjointOut), P, C.c_size_t, P]),
+    "gmapp_batch_create": (C.c_int, [P, C.POINTER(Query), C.c_int32, C.POINTER(P)]),
+    "gmapp_batch_destroy": (None, [P]),
+    "gmapp_batch_set_tuning": (C.c_int, [P, C.c_int32, C.c_int32]),
+    "rollout_batch": (C.c_int, [P, P]),
+    "gmapp_batch_launch_graph": (C.c_int, [P, P]),
+    "gmapp_batch_autotune": (C.c_int, [P, P, C.POINTER(Tuning), C.POINTER(C.c_float)]),
     "score_and_select": (C.c_int, [P, C.POINTER(RolloutOut), C.c_int32, C.POINTER(RolloutParams),
                                    C.POINTER(CostWeights), C.c_float, C.c_float, P, P, P, P]),
 }

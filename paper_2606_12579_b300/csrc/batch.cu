@@ -1,0 +1,715 @@
+// Batched uneven planning queries (many scenes per launch sequence) for the
+// hot path of Sec. IV-B (perception) and Sec. IV-A/IV-C (rollout, cost,
+// selection); the paper runs one query per kernel launch per agent per step
+// (Alg. 1), this module runs a whole batch of queries in a fixed sequence of
+// eight launches that can be captured once in a CUDA graph:
+//
+//   kb_zero, kb_keys, kb_bitmap_sums, kb_emit, kb_count
+//        the filter stages of every query in one launch each (a block ->
+//        query table maps blocks to queries; same binary32 sequence as
+//        filter_cloud, from filter_device.cuh)
+//   kb_plan   one CTA: publishes each query's N_O and orders the work items
+//        (query, agent group) by their cost N_a,item x N_O x N_k, largest
+//        first (longest-processing-time order), into a device queue
+//   kb_rollout  persistent: every CTA pops items from the queue (one atomic
+//        per item), loads the item's obstacle set into shared memory with
+//        the TMA bulk-copy engine and rolls the item's agents through all
+//        N_k steps of its query (one CTA per item, so no cluster exchange)
+//   kb_score   one CTA per query: costs and selected agent
+//
+// The batch object holds the device descriptor table, the queue and the
+// filter scratch; all of it is allocated once at creation.
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "filter_device.cuh"
+#include "rollout_kernel.cuh"
+#include "score_device.cuh"
+
+namespace gmapp {
+namespace {
+
+constexpr int kMaxItems = 8192;
+constexpr int kMaxPointBlocksPerQuery = 128;
+
+struct QueryDev {
+    // perception
+    const float *xyz;
+    int64_t n_raw;
+    FilterArgs fa;
+    uint32_t *bitmap, *prefix, *sums, *offsets, *counters, *keys;
+    int32_t pt_blk0, pt_nblk, bm_blk0, bm_nblk;
+    // obstacle set S_W of the query
+    float *ox, *oy, *oz;
+    uint32_t *okeys, *ocounts, *orep;
+    int32_t *n_obs;
+    int64_t cap;
+    float r_O;
+    // agents and rollout constants
+    const float *p0, *v0, *c, *k_r, *k_a, *r_d, *r_a;
+    int32_t n_agents, n_groups;
+    float goal[3];
+    float dt;
+    int32_t n_steps;
+    float damping, inv_mass, rho, eps, vel_half, clear_margin, clear_beta;
+    // outputs
+    float *traj, *p_final, *v_final, *path_len, *clear_pen, *min_clear;
+    float w_path, w_goal, w_clear;
+    float *costs;
+    int32_t *best;
+    float *best_traj;
+};
+
+struct BatchDev {
+    const QueryDev *q;
+    int32_t n_q;
+    const int32_t *pt_map, *bm_map;
+    const int32_t *items_static;  // item -> (query << 16) | group, in query order
+    int32_t *items;               // the planned queue
+    int32_t n_items;
+    uint32_t *head;
+    int32_t shard_cap;
+    uint32_t *err;
+};
+
+__global__ void __launch_bounds__(kThreads) kb_zero(const BatchDev B) {
+    const QueryDev &Q = B.q[B.bm_map[blockIdx.x]];
+    const int64_t blk = blockIdx.x - Q.bm_blk0;
+    // one block clears 1024 bitmap words of its query
+    reinterpret_cast<uint4 *>(Q.bitmap)[blk * kThreads + threadIdx.x] = make_uint4(0, 0, 0, 0);
+    if (blk == 0 && threadIdx.x < 16) Q.counters[threadIdx.x] = 0;
+}
+
+__global__ void __launch_bounds__(kThreads) kb_keys(const BatchDev B) {
+    const QueryDev &Q = B.q[B.pt_map[blockIdx.x]];
+    const FilterArgs fa = Q.fa;
+    keys_range(Q.xyz, Q.n_raw, fa, Q.keys, Q.bitmap, blockIdx.x - Q.pt_blk0, Q.pt_nblk);
+}
+
+__global__ void __launch_bounds__(kThreads) kb_bitmap_sums(const BatchDev B) {
+    const QueryDev &Q = B.q[B.bm_map[blockIdx.x]];
+    bitmap_sums_block(Q.bitmap, Q.sums, Q.offsets, Q.counters, Q.counters + 1,
+                      blockIdx.x - Q.bm_blk0, Q.bm_nblk);
+}
+
+__global__ void __launch_bounds__(kThreads) kb_emit(const BatchDev B) {
+    const QueryDev &Q = B.q[B.bm_map[blockIdx.x]];
+    const FilterArgs fa = Q.fa;
+    EmitOut o{Q.okeys, Q.ocounts, Q.orep, Q.ox, Q.oy, Q.oz, Q.cap};
+    emit_block(Q.bitmap, Q.offsets, Q.prefix, fa, o, blockIdx.x - Q.bm_blk0);
+}
+
+__global__ void __launch_bounds__(kThreads) kb_count(const BatchDev B) {
+    const QueryDev &Q = B.q[B.pt_map[blockIdx.x]];
+    count_range(Q.keys, Q.n_raw, Q.bitmap, Q.prefix, Q.ocounts, Q.orep, Q.cap,
+                blockIdx.x - Q.pt_blk0, Q.pt_nblk);
+}
+
+// Publish every query's N_O and order the work items by cost, largest first
+// (ties by item index); resets the queue head.
+__global__ void __launch_bounds__(1024) kb_plan(const BatchDev B, int32_t agents_per_item) {
+    extern __shared__ float cost[];  // [n_items]
+    const int tid = threadIdx.x;
+    for (int q = tid; q < B.n_q; q += 1024) {
+        const QueryDev &Q = B.q[q];
+        const uint32_t t = Q.counters[1];
+        *Q.n_obs = static_cast<int32_t>(t);
+        if (t > Q.cap) raise_error(B.err, GMAPP_DEVERR_CAPACITY);
+    }
+    for (int i = tid; i < B.n_items; i += 1024) {
+        const int packed = B.items_static[i];
+        const QueryDev &Q = B.q[packed >> 16];
+        const int g = packed & 0xffff;
+        const int na = Q.n_agents / Q.n_groups + (g < Q.n_agents % Q.n_groups ? 1 : 0);
+        const int64_t occ = Q.counters[1];
+        const float n_obs = static_cast<float>(occ < Q.cap ? occ : Q.cap);
+        cost[i] = static_cast<float>(na) * fmaxf(n_obs, 1.0f) * static_cast<float>(Q.n_steps);
+    }
+    __syncthreads();
+    for (int i = tid; i < B.n_items; i += 1024) {
+        const float ci = cost[i];
+        int rank = 0;
+        for (int j = 0; j < B.n_items; ++j) {
+            const float cj = cost[j];
+            rank += (cj > ci) || (cj == ci && j < i);
+        }
+        B.items[rank] = B.items_static[i];
+    }
+    if (tid == 0) *B.head = 0;
+    (void)agents_per_item;
+}
+
+template <int AG, int NT, bool CLEAR>
+__global__ void __launch_bounds__(NT, 1) kb_rollout(const BatchDev B) {
+    constexpr int NW = NT / 32;
+    constexpr int NM = sfu_agents(AG);
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_item;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *sx = smem, *sy = smem + B.shard_cap, *sz = smem + 2 * B.shard_cap;
+    float *recv = smem + 3 * B.shard_cap;  // [2][NW][AG] x (W, min |d|^2)
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    for (;;) {
+        if (tid == 0) s_item = static_cast<int>(atomicAdd(B.head, 1u));
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= B.n_items) break;
+        const int packed = B.items[it];
+        const QueryDev &Q = B.q[packed >> 16];
+        int a0, na;
+        group_range(packed & 0xffff, Q.n_agents, Q.n_groups, a0, na);
+        const int32_t n_obs = *Q.n_obs;
+        if (n_obs < 0 || n_obs > Q.cap || na > AG) {
+            if (tid == 0) raise_error(B.err, GMAPP_DEVERR_CAPACITY);
+            continue;  // uniform across the CTA
+        }
+        // the first shard_cap obstacles stay in shared memory, the rest is
+        // read from global memory (L2) every step
+        int32_t cnt = min(n_obs, B.shard_cap);
+        const GlobalTail tail{Q.ox, Q.oy, Q.oz, cnt, n_obs};
+        if (cnt > 0 && tid == 0) {
+            const uint32_t bytes = static_cast<uint32_t>((cnt + 3) & ~3) * 4u;
+            mbar_arrive_expect_tx(&bar, 3 * bytes);
+            bulk_g2s(sx, Q.ox, bytes, &bar);
+            bulk_g2s(sy, Q.oy, bytes, &bar);
+            bulk_g2s(sz, Q.oz, bytes, &bar);
+        }
+        const int n = Q.n_agents, N = Q.n_steps;
+        float p[3] = {0, 0, 0}, v[3] = {0, 0, 0}, cc[3] = {0, 0, 0};
+        float k_r = 0, k_a = 0, R = 0, G2 = -1.0f, L = 0, pen = 0, minc = INFINITY;
+        if (lane < na) {
+            const int i = a0 + lane;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                p[d] = Q.p0[d * n + i];
+                v[d] = Q.v0[d * n + i];
+                cc[d] = Q.c[d * n + i];
+            }
+            k_r = Q.k_r[i];
+            k_a = Q.k_a[i];
+            R = Q.r_a[i] + Q.r_O;
+            const float rd = Q.r_d[i];
+            G2 = rd >= Q.eps ? (rd + R) * (rd + R) : -1.0f;
+            if (warp == 0 && Q.traj) {
+                float *t = Q.traj + (size_t)i * (N + 1) * 3;
+                t[0] = p[0];
+                t[1] = p[1];
+                t[2] = p[2];
+            }
+        }
+        f2 nR2[AG];
+        float G2a[AG];
+#pragma unroll
+        for (int a = 0; a < AG; ++a) {
+            const float r = __shfl_sync(0xffffffffu, R, a);
+            nR2[a] = pk(-r, -r);
+            G2a[a] = __shfl_sync(0xffffffffu, G2, a);
+        }
+        if (cnt > 0) {
+            if (!mbar_wait(&bar, phase)) {
+                if (tid == 0) raise_error(B.err, GMAPP_DEVERR_TIMEOUT);
+                cnt = 0;
+            }
+            phase ^= 1u;
+        }
+        const int32_t cnt_pad = (cnt + 1) & ~1;
+        if (tid == 0 && cnt_pad > cnt) {
+            sx[cnt] = __int_as_float(0x7fc00000);
+            sy[cnt] = __int_as_float(0x7fc00000);
+            sz[cnt] = __int_as_float(0x7fc00000);
+        }
+        __syncthreads();
+        const float h = Q.vel_half * Q.dt * Q.inv_mass;
+        const float goal[3] = {Q.goal[0], Q.goal[1], Q.goal[2]};
+        for (int k = 0; k < N; ++k) {
+            float *rp = recv + (k & 1) * (NW * AG * 2);
+            half_step<AG, AG, 0, NM, NT, CLEAR, true>(sx, sy, sz, cnt_pad, Q.eps, nR2, G2a, p,
+                                                      rp + 2 * (warp * AG), 1u, lane, tail);
+            __syncthreads();
+            float W = 0.0f, md2 = INFINITY;
+            half_combine<AG, AG, 0, CLEAR>(rp, NW, lane, W, md2);
+            if (lane < na) {
+                float g[3], kf, m;
+                agent_step<CLEAR>(p, v, cc, k_r, k_a, R, goal, h, Q.dt, Q.rho, Q.damping,
+                                  Q.clear_margin, Q.clear_beta, W, md2, L, pen, minc, m, g, kf);
+                if (warp == 0 && Q.traj) {
+                    float *t = Q.traj + ((size_t)(a0 + lane) * (N + 1) + k + 1) * 3;
+                    t[0] = p[0];
+                    t[1] = p[1];
+                    t[2] = p[2];
+                }
+            }
+        }
+        if (warp == 0 && lane < na) {
+            const int i = a0 + lane;
+            for (int d = 0; d < 3; ++d) {
+                Q.p_final[d * n + i] = p[d];
+                Q.v_final[d * n + i] = v[d];
+            }
+            Q.path_len[i] = L;
+            if (Q.clear_pen) Q.clear_pen[i] = pen;
+            if (Q.min_clear) Q.min_clear[i] = minc;
+        }
+        __syncthreads();  // the next item's bulk copy overwrites the shard
+    }
+}
+
+__global__ void __launch_bounds__(kScoreThreads) kb_score(const BatchDev B) {
+    const QueryDev &Q = B.q[blockIdx.x];
+    ScoreArgs S;
+    S.p_final = Q.p_final;
+    S.path_len = Q.path_len;
+    S.clear_pen = Q.clear_pen;
+    S.traj = Q.traj;
+    S.n = Q.n_agents;
+    S.n_steps = Q.n_steps;
+    for (int d = 0; d < 3; ++d) S.goal[d] = Q.goal[d];
+    S.w_path = Q.w_path;
+    S.w_goal = Q.w_goal;
+    S.w_clear = Q.w_clear;
+    S.prev_best = __int_as_float(0x7fc00000);
+    S.alpha = 1.0f;
+    S.costs = Q.costs;
+    S.best = Q.best;
+    S.best_traj = Q.best_traj;
+    score_select_block(S);
+}
+
+using BatchKernel = void (*)(const BatchDev);
+
+template <bool CLEAR>
+BatchKernel batch_kernel_for(int ag, int nt) {
+#define GMAPP_BK(AGV)                                             \
+    case AGV:                                                     \
+        switch (nt) {                                             \
+            case 256: return kb_rollout<AGV, 256, CLEAR>;         \
+            case 384: return kb_rollout<AGV, 384, CLEAR>;         \
+            case 512:                                             \
+                if constexpr (AGV <= 8) return kb_rollout<AGV, 512, CLEAR>; \
+                return nullptr;                                   \
+            default: return nullptr;                              \
+        }
+    switch (ag) {
+        GMAPP_BK(2)
+        GMAPP_BK(4)
+        GMAPP_BK(6)
+        GMAPP_BK(8)
+        GMAPP_BK(12)
+        GMAPP_BK(16)
+        default: return nullptr;
+    }
+#undef GMAPP_BK
+}
+
+BatchKernel batch_kernel(int ag, int nt, bool clear) {
+    return clear ? batch_kernel_for<true>(ag, nt) : batch_kernel_for<false>(ag, nt);
+}
+
+}  // namespace
+}  // namespace gmapp
+
+using namespace gmapp;
+
+struct gmapp_batch {
+    gmapp_ctx *ctx = nullptr;
+    int32_t n_q = 0;
+    std::vector<QueryDev> hq;
+    QueryDev *d_q = nullptr;
+    int32_t *d_pt_map = nullptr, *d_bm_map = nullptr;
+    int32_t *d_items_static = nullptr, *d_items = nullptr;
+    uint32_t *d_head = nullptr;
+    void *d_ws = nullptr;
+    int32_t pt_blocks = 0, bm_blocks = 0, n_items = 0, shard_cap = 0;
+    int64_t max_cap = 4;  // largest obstacle capacity over the queries
+    bool clear = false;
+    int32_t agents_per_item = 8, threads = 256;
+    BatchKernel fn = nullptr;
+    size_t smem = 0;
+    int grid = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void release(gmapp_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->d_q);
+    cudaFree(b->d_pt_map);
+    cudaFree(b->d_bm_map);
+    cudaFree(b->d_items_static);
+    cudaFree(b->d_items);
+    cudaFree(b->d_head);
+    cudaFree(b->d_ws);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// (Re)build the item list and the kernel choice for a tuning.
+gmapp_status apply_tuning(gmapp_batch *b, int32_t agents_per_item, int32_t threads) {
+    BatchKernel fn = batch_kernel(agents_per_item, threads, b->clear);
+    if (!fn) {
+        set_error("gmapp_batch: no kernel for %d agents per item and %d threads", agents_per_item,
+                  threads);
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    // resident part of each obstacle set: as much as shared memory holds
+    // after the receive slots (larger sets stream their remainder from L2)
+    cudaFuncAttributes fa;
+    GMAPP_CHECK_CUDA(cudaFuncGetAttributes(&fa, reinterpret_cast<const void *>(fn)));
+    const size_t recv_bytes =
+        static_cast<size_t>(2) * (threads / 32) * agents_per_item * 2 * sizeof(float);
+    const int64_t room = (static_cast<int64_t>(b->ctx->max_smem_optin) -
+                          static_cast<int64_t>(fa.sharedSizeBytes + recv_bytes)) / 12;
+    b->shard_cap = static_cast<int32_t>(std::min<int64_t>((b->max_cap + 3) & ~int64_t(3),
+                                                          room & ~int64_t(3)));
+    if (b->shard_cap < 4) {
+        set_error("gmapp_batch: no shared memory left for obstacles");
+        return GMAPP_ERR_CAPACITY;
+    }
+    const size_t smem = static_cast<size_t>(b->shard_cap) * 3 * sizeof(float) + recv_bytes;
+    std::vector<int32_t> items;
+    for (int q = 0; q < b->n_q; ++q) {
+        const int groups = (b->hq[q].n_agents + agents_per_item - 1) / agents_per_item;
+        b->hq[q].n_groups = groups;
+        if (q > 0xffff || groups > 0xffff) {
+            set_error("gmapp_batch: too many queries or agent groups");
+            return GMAPP_ERR_CAPACITY;
+        }
+        for (int g = 0; g < groups; ++g) items.push_back((q << 16) | g);
+    }
+    if (items.size() > static_cast<size_t>(kMaxItems)) {
+        set_error("gmapp_batch: %zu work items, at most %d (use more agents per item)",
+                  items.size(), kMaxItems);
+        return GMAPP_ERR_CAPACITY;
+    }
+    GMAPP_CHECK_CUDA(cudaMemcpy(b->d_q, b->hq.data(), sizeof(QueryDev) * b->n_q,
+                                cudaMemcpyHostToDevice));
+    GMAPP_CHECK_CUDA(cudaMemcpy(b->d_items_static, items.data(), sizeof(int32_t) * items.size(),
+                                cudaMemcpyHostToDevice));
+    GMAPP_CHECK_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(smem)));
+    GMAPP_CHECK_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void *>(kb_plan),
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kMaxItems * static_cast<int>(sizeof(float))));
+    int per_sm = 0;
+    GMAPP_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, reinterpret_cast<const void *>(fn), threads, smem));
+    if (per_sm < 1) {
+        set_error("gmapp_batch: rollout kernel cannot be resident");
+        return GMAPP_ERR_CAPACITY;
+    }
+    b->n_items = static_cast<int32_t>(items.size());
+    b->grid = std::max(1, std::min(b->n_items, per_sm * b->ctx->sm_count));
+    b->fn = fn;
+    b->smem = smem;
+    b->agents_per_item = agents_per_item;
+    b->threads = threads;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return GMAPP_OK;
+}
+
+BatchDev dev_view(const gmapp_batch *b) {
+    BatchDev B;
+    B.q = b->d_q;
+    B.n_q = b->n_q;
+    B.pt_map = b->d_pt_map;
+    B.bm_map = b->d_bm_map;
+    B.items_static = b->d_items_static;
+    B.items = b->d_items;
+    B.n_items = b->n_items;
+    B.head = b->d_head;
+    B.shard_cap = b->shard_cap;
+    B.err = b->ctx->d_err;
+    return B;
+}
+
+}  // namespace
+
+extern "C" gmapp_status gmapp_batch_create(gmapp_ctx *ctx, const gmapp_query *queries,
+                                           int32_t n_q, gmapp_batch **out) {
+    if (!ctx || !queries || n_q < 1 || !out) {
+        set_error("gmapp_batch_create: invalid argument");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    gmapp_batch *b = new gmapp_batch();
+    b->ctx = ctx;
+    b->n_q = n_q;
+    b->hq.resize(n_q);
+    std::vector<int32_t> pt_map, bm_map;
+    std::vector<size_t> ws_off(n_q);
+    size_t ws_total = 0;
+    int64_t max_cap = 4;
+    for (int q = 0; q < n_q; ++q) {
+        const gmapp_query &Qh = queries[q];
+        if (!valid_workspace(&Qh.ws) || Qh.ws.min_pts != 1 || Qh.n_raw < 0 ||
+            Qh.n_raw >= 0xFFFFFFFFll || (Qh.n_raw > 0 && !Qh.xyz) ||
+            reinterpret_cast<uintptr_t>(Qh.xyz) % 16) {
+            set_error("gmapp_batch_create: query %d: invalid cloud or workspace (batched queries "
+                      "need min_pts == 1 and 16-byte aligned clouds)", q);
+            delete b;
+            return GMAPP_ERR_INVALID_ARG;
+        }
+        const gmapp_obstacles &o = Qh.obs;
+        if (!o.x || !o.y || !o.z || !o.keys || !o.counts || !o.rep_idx || !o.n || o.cap < 4 ||
+            o.cap % 4 ||
+            ((reinterpret_cast<uintptr_t>(o.x) | reinterpret_cast<uintptr_t>(o.y) |
+              reinterpret_cast<uintptr_t>(o.z)) % 16)) {
+            set_error("gmapp_batch_create: query %d: obstacle buffers must be set, 16-byte "
+                      "aligned, cap a multiple of 4", q);
+            delete b;
+            return GMAPP_ERR_INVALID_ARG;
+        }
+        const gmapp_agents &a = Qh.agents;
+        const gmapp_rollout_params &p = Qh.prm;
+        if (a.n < 1 || !a.p0 || !a.v0 || !a.c || !a.k_r || !a.k_a || !a.r_d || !a.r_a ||
+            p.n_steps < 1 || !(p.dt > 0.0f) || !(p.eps > 0.0f) || !(p.clear_beta > 0.0f) ||
+            !Qh.out.p_final || !Qh.out.v_final || !Qh.out.path_len || !Qh.costs || !Qh.best ||
+            (Qh.best_traj && !Qh.out.traj) || (Qh.w.w_clear != 0.0f && !Qh.out.clear_pen)) {
+            set_error("gmapp_batch_create: query %d: invalid agents, parameters or outputs", q);
+            delete b;
+            return GMAPP_ERR_INVALID_ARG;
+        }
+        for (int i = 0; i < 12; ++i)
+            if (!isfinite(Qh.T[i])) {
+                set_error("gmapp_batch_create: query %d: transform not finite", q);
+                delete b;
+                return GMAPP_ERR_INVALID_ARG;
+            }
+        const Layout L = layout(Qh.n_raw, &Qh.ws);
+        ws_off[q] = ws_total;
+        ws_total = align_up(ws_total + L.total, 256);
+        QueryDev &D = b->hq[q];
+        memset(&D, 0, sizeof(D));
+        D.xyz = Qh.xyz;
+        D.n_raw = Qh.n_raw;
+        for (int i = 0; i < 12; ++i) D.fa.T[i] = Qh.T[i];
+        for (int d = 0; d < 3; ++d) {
+            D.fa.lo[d] = Qh.ws.lo[d];
+            D.fa.dimf[d] = static_cast<float>(Qh.ws.dims[d]);
+        }
+        D.fa.voxel = Qh.ws.voxel;
+        D.fa.nx = Qh.ws.dims[0];
+        D.fa.ny = Qh.ws.dims[1];
+        D.fa.nz = Qh.ws.dims[2];
+        D.pt_blk0 = static_cast<int32_t>(pt_map.size());
+        D.pt_nblk = static_cast<int32_t>(std::max<int64_t>(
+            1, std::min<int64_t>((Qh.n_raw / 4 + kThreads - 1) / kThreads, kMaxPointBlocksPerQuery)));
+        for (int i = 0; i < D.pt_nblk; ++i) pt_map.push_back(q);
+        D.bm_blk0 = static_cast<int32_t>(bm_map.size());
+        D.bm_nblk = static_cast<int32_t>(L.n_blocks);
+        for (int i = 0; i < D.bm_nblk; ++i) bm_map.push_back(q);
+        D.ox = o.x;
+        D.oy = o.y;
+        D.oz = o.z;
+        D.okeys = o.keys;
+        D.ocounts = o.counts;
+        D.orep = o.rep_idx;
+        D.n_obs = o.n;
+        D.cap = o.cap;
+        D.r_O = 0.5f * Qh.ws.voxel;
+        max_cap = std::max(max_cap, o.cap);
+        D.p0 = a.p0;
+        D.v0 = a.v0;
+        D.c = a.c;
+        D.k_r = a.k_r;
+        D.k_a = a.k_a;
+        D.r_d = a.r_d;
+        D.r_a = a.r_a;
+        D.n_agents = a.n;
+        for (int d = 0; d < 3; ++d) D.goal[d] = p.goal[d];
+        D.dt = p.dt;
+        D.n_steps = p.n_steps;
+        D.damping = p.damping;
+        D.inv_mass = p.inv_mass;
+        D.rho = p.rho;
+        D.eps = p.eps;
+        D.vel_half = p.vel_half;
+        D.clear_margin = p.clear_margin;
+        D.clear_beta = p.clear_beta;
+        D.traj = Qh.out.traj;
+        D.p_final = Qh.out.p_final;
+        D.v_final = Qh.out.v_final;
+        D.path_len = Qh.out.path_len;
+        D.clear_pen = Qh.out.clear_pen;
+        D.min_clear = Qh.out.min_clear;
+        D.w_path = Qh.w.w_path;
+        D.w_goal = Qh.w.w_goal;
+        D.w_clear = Qh.w.w_clear;
+        D.costs = Qh.costs;
+        D.best = Qh.best;
+        D.best_traj = Qh.best_traj;
+        b->clear = b->clear || Qh.out.clear_pen || Qh.out.min_clear;
+    }
+    b->pt_blocks = static_cast<int32_t>(pt_map.size());
+    b->bm_blocks = static_cast<int32_t>(bm_map.size());
+    b->max_cap = max_cap;
+    cudaError_t e = cudaMalloc(&b->d_ws, std::max<size_t>(ws_total, 256));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_q, sizeof(QueryDev) * n_q);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_pt_map, sizeof(int32_t) * pt_map.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_bm_map, sizeof(int32_t) * bm_map.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items_static, sizeof(int32_t) * kMaxItems);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int32_t) * kMaxItems);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_head, sizeof(uint32_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_pt_map, pt_map.data(), sizeof(int32_t) * pt_map.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_bm_map, bm_map.data(), sizeof(int32_t) * bm_map.size(),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        gmapp_status st = cuda_fail(e, "gmapp_batch_create");
+        release(b);
+        delete b;
+        return st;
+    }
+    char *ws = static_cast<char *>(b->d_ws);
+    for (int q = 0; q < n_q; ++q) {
+        const Layout L = layout(queries[q].n_raw, &queries[q].ws);
+        char *base = ws + ws_off[q];
+        QueryDev &D = b->hq[q];
+        D.bitmap = reinterpret_cast<uint32_t *>(base + L.off_bitmap);
+        D.prefix = reinterpret_cast<uint32_t *>(base + L.off_prefix);
+        D.sums = reinterpret_cast<uint32_t *>(base + L.off_sums);
+        D.offsets = reinterpret_cast<uint32_t *>(base + L.off_offsets);
+        D.counters = reinterpret_cast<uint32_t *>(base + L.off_counters);
+        D.keys = reinterpret_cast<uint32_t *>(base + L.off_keys);
+    }
+    gmapp_status st = apply_tuning(b, 8, 256);
+    if (st != GMAPP_OK) {
+        release(b);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return GMAPP_OK;
+}
+
+extern "C" void gmapp_batch_destroy(gmapp_batch *b) {
+    if (!b) return;
+    release(b);
+    delete b;
+}
+
+extern "C" gmapp_status gmapp_batch_set_tuning(gmapp_batch *b, int32_t agents_per_item,
+                                               int32_t threads) {
+    if (!b) {
+        set_error("gmapp_batch_set_tuning: NULL batch");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    return apply_tuning(b, agents_per_item, threads);
+}
+
+extern "C" gmapp_status rollout_batch(gmapp_batch *b, gmapp_stream stream) {
+    if (!b) {
+        set_error("rollout_batch: NULL batch");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    const BatchDev B = dev_view(b);
+    kb_zero<<<b->bm_blocks, kThreads, 0, stream>>>(B);
+    kb_keys<<<b->pt_blocks, kThreads, 0, stream>>>(B);
+    kb_bitmap_sums<<<b->bm_blocks, kThreads, 0, stream>>>(B);
+    kb_emit<<<b->bm_blocks, kThreads, 0, stream>>>(B);
+    kb_count<<<b->pt_blocks, kThreads, 0, stream>>>(B);
+    kb_plan<<<1, 1024, b->n_items * sizeof(float), stream>>>(B, b->agents_per_item);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b->grid, 1, 1);
+    cfg.blockDim = dim3(b->threads, 1, 1);
+    cfg.dynamicSmemBytes = b->smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;  // a cluster of one CTA
+    attr.val.clusterDim.x = 1;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    GMAPP_CHECK_CUDA(cudaLaunchKernelEx(&cfg, b->fn, B));
+    kb_score<<<b->n_q, kScoreThreads, 0, stream>>>(B);
+    GMAPP_CHECK_CUDA(cudaGetLastError());
+    return GMAPP_OK;
+}
+
+extern "C" gmapp_status gmapp_batch_launch_graph(gmapp_batch *b, gmapp_stream stream) {
+    if (!b || !stream) {
+        set_error("gmapp_batch_launch_graph: needs a batch and a non-default stream");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    if (!b->exec) {
+        GMAPP_CHECK_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        gmapp_status st = rollout_batch(b, stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(stream, &g);
+        if (st != GMAPP_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "gmapp_batch_launch_graph: capture");
+        b->graph = g;
+        GMAPP_CHECK_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
+    }
+    GMAPP_CHECK_CUDA(cudaGraphLaunch(b->exec, stream));
+    return GMAPP_OK;
+}
+
+extern "C" gmapp_status gmapp_batch_autotune(gmapp_batch *b, gmapp_stream stream,
+                                             gmapp_tuning *best, float *best_ms) {
+    if (!b) {
+        set_error("gmapp_batch_autotune: NULL batch");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    const int ags[] = {2, 4, 6, 8, 12, 16};
+    const int nts[] = {256, 384, 512};
+    cudaEvent_t e0, e1;
+    GMAPP_CHECK_CUDA(cudaEventCreate(&e0));
+    GMAPP_CHECK_CUDA(cudaEventCreate(&e1));
+    float best_t = 1e30f;
+    int best_ag = 8, best_nt = 256;
+    for (int ag : ags)
+        for (int nt : nts) {
+            if (apply_tuning(b, ag, nt) != GMAPP_OK) continue;
+            if (rollout_batch(b, stream) != GMAPP_OK) continue;
+            cudaEventRecord(e0, stream);
+            if (rollout_batch(b, stream) != GMAPP_OK) continue;
+            cudaEventRecord(e1, stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(cudaGetLastError(), "gmapp_batch_autotune");
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_t) {
+                best_t = ms;
+                best_ag = ag;
+                best_nt = nt;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    gmapp_status st = apply_tuning(b, best_ag, best_nt);
+    if (st != GMAPP_OK) return st;
+    if (best) *best = gmapp_tuning{1, best_ag, best_nt};
+    if (best_ms) *best_ms = best_t;
+    return GMAPP_OK;
+}

@@ -1,0 +1,461 @@
+// Device-side building blocks of the perception filter (Sec. IV-B, Sec. V-A),
+// shared by the single-query entry points (filter.cu) and the batched
+// queries (batch.cu), so both run the exact same binary32 sequence.
+#pragma once
+
+#include <math.h>
+
+#include <algorithm>
+
+#include "gmapp_internal.cuh"
+
+namespace gmapp {
+namespace {
+
+constexpr uint32_t kInvalid = 0xFFFFFFFFu;
+constexpr int kThreads = 256;
+constexpr int kWordsPerThread = 4;
+constexpr int kWordsPerBlock = kThreads * kWordsPerThread;  // 1024 words = 32768 cells
+
+struct FilterArgs {
+    float T[12];
+    float lo[3];
+    float voxel;
+    float dimf[3];
+    uint32_t nx, ny, nz;
+};
+
+// One point -> its linear voxel key, or kInvalid.  Exact binary32 sequence,
+// no contraction: w = ((T0 x + T1 y) + T2 z) + T3; q = (w - lo) / voxel.
+__device__ __forceinline__ uint32_t voxel_key(float x, float y, float z, const FilterArgs &A) {
+    if (!(isfinite(x) && isfinite(y) && isfinite(z))) return kInvalid;
+    uint32_t idx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float t0 = __fmul_rn(A.T[4 * a + 0], x);
+        float t1 = __fmul_rn(A.T[4 * a + 1], y);
+        float t2 = __fmul_rn(A.T[4 * a + 2], z);
+        float w = __fadd_rn(__fadd_rn(__fadd_rn(t0, t1), t2), A.T[4 * a + 3]);
+        float q = __fdiv_rn(__fsub_rn(w, A.lo[a]), A.voxel);
+        if (!(q >= 0.0f && q < A.dimf[a])) return kInvalid;
+        idx[a] = static_cast<uint32_t>(q);  // q >= 0: truncation is floor
+    }
+    return (idx[2] * A.ny + idx[1]) * A.nx + idx[0];
+}
+
+__device__ __forceinline__ void voxel_centre(uint32_t key, const FilterArgs &A, float &cx,
+                                             float &cy, float &cz) {
+    uint32_t ix = key % A.nx;
+    uint32_t r = key / A.nx;
+    uint32_t iy = r % A.ny;
+    uint32_t iz = r / A.ny;
+    cx = __fadd_rn(A.lo[0], __fmul_rn(__fadd_rn(static_cast<float>(ix), 0.5f), A.voxel));
+    cy = __fadd_rn(A.lo[1], __fmul_rn(__fadd_rn(static_cast<float>(iy), 0.5f), A.voxel));
+    cz = __fadd_rn(A.lo[2], __fmul_rn(__fadd_rn(static_cast<float>(iz), 0.5f), A.voxel));
+}
+
+__global__ void k_zero(uint4 *words, int64_t n_vec, uint32_t *counters, int n_counters) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < n_vec; i += stride) words[i] = make_uint4(0, 0, 0, 0);
+    if (blockIdx.x == 0 && threadIdx.x < n_counters) counters[threadIdx.x] = 0;
+}
+
+// OR a run of bits into the bitmap, merging consecutive points of one thread
+// that fall into the same 32-cell word.
+struct BitMerge {
+    uint32_t word = kInvalid, bits = 0;
+    __device__ __forceinline__ void add(uint32_t key, uint32_t *bitmap) {
+        if (key == kInvalid) return;
+        uint32_t w = key >> 5, b = 1u << (key & 31);
+        if (w == word) {
+            bits |= b;
+            return;
+        }
+        flush(bitmap);
+        word = w;
+        bits = b;
+    }
+    __device__ __forceinline__ void flush(uint32_t *bitmap) {
+        if (word != kInvalid) atomicOr(&bitmap[word], bits);
+        word = kInvalid;
+    }
+};
+
+// Points -> keys (4 points = 48 B per thread per iteration: three 16-byte loads).
+__device__ __forceinline__ void keys_range(const float *__restrict__ xyz, int64_t n,
+                                                    FilterArgs A, uint32_t *__restrict__ keys,
+                                                    uint32_t *__restrict__ bitmap,
+                                           int64_t blk, int64_t nblk) {
+    const int64_t n4 = n / 4;
+    const int64_t stride = nblk * (int64_t)kThreads;
+    for (int64_t g = blk * (int64_t)kThreads + threadIdx.x; g < n4; g += stride) {
+        const float4 *src = reinterpret_cast<const float4 *>(xyz) + 3 * g;
+        float4 a0 = __ldcs(src), a1 = __ldcs(src + 1), a2 = __ldcs(src + 2);
+        uint4 k;
+        k.x = voxel_key(a0.x, a0.y, a0.z, A);
+        k.y = voxel_key(a0.w, a1.x, a1.y, A);
+        k.z = voxel_key(a1.z, a1.w, a2.x, A);
+        k.w = voxel_key(a2.y, a2.z, a2.w, A);
+        reinterpret_cast<uint4 *>(keys)[g] = k;
+        BitMerge m;
+        m.add(k.x, bitmap);
+        m.add(k.y, bitmap);
+        m.add(k.z, bitmap);
+        m.add(k.w, bitmap);
+        m.flush(bitmap);
+    }
+    // ragged tail (n % 4 points)
+    int64_t t = 4 * n4 + blk * (int64_t)kThreads + threadIdx.x;
+    if (t < n) {
+        uint32_t k = voxel_key(xyz[3 * t], xyz[3 * t + 1], xyz[3 * t + 2], A);
+        keys[t] = k;
+        if (k != kInvalid) atomicOr(&bitmap[k >> 5], 1u << (k & 31));
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_keys(const float *__restrict__ xyz, int64_t n,
+                                                    FilterArgs A, uint32_t *__restrict__ keys,
+                                                    uint32_t *__restrict__ bitmap) {
+    keys_range(xyz, n, A, keys, bitmap, blockIdx.x, gridDim.x);
+}
+
+// Block-wide exclusive scan of one uint32 per thread (kThreads threads).
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_tot,
+                                                         uint32_t &block_total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < kThreads / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < kThreads / 32) warp_tot[lane] = t;  // inclusive
+    }
+    __syncthreads();
+    uint32_t before = warp ? warp_tot[warp - 1] : 0;
+    block_total = warp_tot[kThreads / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+// Exclusive scan of `n` block sums by ONE block (the last one to finish);
+// writes offsets[] and returns the grand total to thread 0.
+__device__ uint32_t scan_block_sums(const uint32_t *sums, uint32_t *offsets, int64_t n,
+                                    uint32_t *warp_tot) {
+    const int64_t per = (n + kThreads - 1) / kThreads;
+    const int64_t b0 = threadIdx.x * per;
+    uint32_t local = 0;
+    for (int64_t i = b0; i < b0 + per && i < n; ++i) local += __ldcg(&sums[i]);
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(local, warp_tot, total);
+    for (int64_t i = b0; i < b0 + per && i < n; ++i) {
+        uint32_t s = __ldcg(&sums[i]);
+        offsets[i] = run;
+        run += s;
+    }
+    return total;
+}
+
+// Per block of 1024 bitmap words: popcount sum.  The last block scans all
+// block sums into offsets and publishes the total number of occupied voxels.
+__device__ __forceinline__ void bitmap_sums_block(const uint32_t *__restrict__ bitmap,
+                                                          uint32_t *sums, uint32_t *offsets,
+                                                          uint32_t *counter, uint32_t *n_occ,
+                                                  int64_t blk, int64_t nblk) {
+    __shared__ uint32_t warp_tot[kThreads / 32];
+    __shared__ bool is_last;
+    const uint4 w = reinterpret_cast<const uint4 *>(bitmap)[blk * kThreads + threadIdx.x];
+    uint32_t c = __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
+    uint32_t tot;
+    block_exclusive_scan(c, warp_tot, tot);
+    if (threadIdx.x == 0) {
+        sums[blk] = tot;
+        __threadfence();
+        is_last = atomicAdd(counter, 1u) == nblk - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    uint32_t total = scan_block_sums(sums, offsets, nblk, warp_tot);
+    if (threadIdx.x == 0) {
+        *n_occ = total;
+        *counter = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_bitmap_sums(const uint32_t *__restrict__ bitmap,
+                                                          uint32_t *sums, uint32_t *offsets,
+                                                          uint32_t *counter, uint32_t *n_occ) {
+    bitmap_sums_block(bitmap, sums, offsets, counter, n_occ, blockIdx.x, gridDim.x);
+}
+
+struct EmitOut {
+    uint32_t *keys, *counts, *rep;
+    float *x, *y, *z;  // NULL when centres are computed later (min_pts > 1)
+    int64_t cap;
+};
+
+// Per word: rank of its first set bit = block offset + in-block prefix.
+// Every set bit becomes one output entry (key, centre, count = 0, rep = ~0).
+__device__ __forceinline__ void emit_block(const uint32_t *__restrict__ bitmap,
+                                                   const uint32_t *__restrict__ offsets,
+                                                   uint32_t *__restrict__ word_prefix,
+                                                   FilterArgs A, EmitOut o,
+                                           int64_t blk) {
+    __shared__ uint32_t warp_tot[kThreads / 32];
+    const int64_t wv = blk * (int64_t)kThreads + threadIdx.x;
+    const uint4 w = reinterpret_cast<const uint4 *>(bitmap)[wv];
+    uint32_t c0 = __popc(w.x), c1 = __popc(w.y), c2 = __popc(w.z), c3 = __popc(w.w);
+    uint32_t tot;
+    uint32_t base = offsets[blk] + block_exclusive_scan(c0 + c1 + c2 + c3, warp_tot, tot);
+    uint4 pre = make_uint4(base, base + c0, base + c0 + c1, base + c0 + c1 + c2);
+    reinterpret_cast<uint4 *>(word_prefix)[wv] = pre;
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+    const uint32_t pres[4] = {pre.x, pre.y, pre.z, pre.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t bits = words[j];
+        uint32_t rank = pres[j];
+        const uint32_t key0 = static_cast<uint32_t>((4 * wv + j) * 32);
+        while (bits) {
+            int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            if (rank < o.cap) {
+                uint32_t key = key0 + b;
+                o.keys[rank] = key;
+                o.counts[rank] = 0;
+                o.rep[rank] = kInvalid;
+                if (o.x) {
+                    float cx, cy, cz;
+                    voxel_centre(key, A, cx, cy, cz);
+                    o.x[rank] = cx;
+                    o.y[rank] = cy;
+                    o.z[rank] = cz;
+                }
+            }
+            ++rank;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_emit(const uint32_t *__restrict__ bitmap,
+                                                   const uint32_t *__restrict__ offsets,
+                                                   uint32_t *__restrict__ word_prefix,
+                                                   FilterArgs A, EmitOut o) {
+    emit_block(bitmap, offsets, word_prefix, A, o, blockIdx.x);
+}
+
+// Accumulate count and smallest index of consecutive points with one rank.
+struct RankMerge {
+    uint32_t rank = kInvalid, cnt = 0, first = 0;
+    __device__ __forceinline__ void add(uint32_t r, uint32_t idx, uint32_t *counts, uint32_t *rep) {
+        if (r == rank) {
+            ++cnt;
+            return;
+        }
+        flush(counts, rep);
+        rank = r;
+        cnt = 1;
+        first = idx;
+    }
+    __device__ __forceinline__ void flush(uint32_t *counts, uint32_t *rep) {
+        if (rank != kInvalid) {
+            atomicAdd(&counts[rank], cnt);
+            atomicMin(&rep[rank], first);
+        }
+        rank = kInvalid;
+    }
+};
+
+__device__ __forceinline__ uint32_t rank_of(uint32_t key, const uint32_t *bitmap,
+                                            const uint32_t *word_prefix, int64_t cap) {
+    if (key == kInvalid) return kInvalid;
+    uint32_t w = key >> 5;
+    uint32_t below = __ldg(&bitmap[w]) & ((1u << (key & 31)) - 1u);
+    uint32_t r = __ldg(&word_prefix[w]) + __popc(below);
+    return r < cap ? r : kInvalid;
+}
+
+__device__ __forceinline__ void count_range(const uint32_t *__restrict__ keys, int64_t n,
+                                                    const uint32_t *__restrict__ bitmap,
+                                                    const uint32_t *__restrict__ word_prefix,
+                                                    uint32_t *counts, uint32_t *rep, int64_t cap,
+                                            int64_t blk, int64_t nblk) {
+    const int64_t n4 = n / 4;
+    const int64_t stride = nblk * (int64_t)kThreads;
+    for (int64_t g = blk * (int64_t)kThreads + threadIdx.x; g < n4; g += stride) {
+        uint4 k = __ldcs(reinterpret_cast<const uint4 *>(keys) + g);
+        RankMerge m;
+        uint32_t i0 = static_cast<uint32_t>(4 * g);
+        uint32_t r;
+        if ((r = rank_of(k.x, bitmap, word_prefix, cap)) != kInvalid) m.add(r, i0, counts, rep);
+        if ((r = rank_of(k.y, bitmap, word_prefix, cap)) != kInvalid) m.add(r, i0 + 1, counts, rep);
+        if ((r = rank_of(k.z, bitmap, word_prefix, cap)) != kInvalid) m.add(r, i0 + 2, counts, rep);
+        if ((r = rank_of(k.w, bitmap, word_prefix, cap)) != kInvalid) m.add(r, i0 + 3, counts, rep);
+        m.flush(counts, rep);
+    }
+    int64_t t = 4 * n4 + blk * (int64_t)kThreads + threadIdx.x;
+    if (t < n) {
+        uint32_t r = rank_of(keys[t], bitmap, word_prefix, cap);
+        if (r != kInvalid) {
+            atomicAdd(&counts[r], 1u);
+            atomicMin(&rep[r], static_cast<uint32_t>(t));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_count(const uint32_t *__restrict__ keys, int64_t n,
+                                                    const uint32_t *__restrict__ bitmap,
+                                                    const uint32_t *__restrict__ word_prefix,
+                                                    uint32_t *counts, uint32_t *rep, int64_t cap) {
+    count_range(keys, n, bitmap, word_prefix, counts, rep, cap, blockIdx.x, gridDim.x);
+}
+
+// Publish N_O = min(total, cap) semantics: n_out = total; capacity error if
+// total > cap.  (min_pts == 1 path.)
+__global__ void k_publish(const uint32_t *n_occ, int32_t *n_out, int64_t cap, uint32_t *err) {
+    uint32_t t = *n_occ;
+    *n_out = static_cast<int32_t>(t);
+    if (t > cap) raise_error(err, GMAPP_DEVERR_CAPACITY);
+}
+
+// min_pts > 1: per block of 1024 temporary entries, how many pass; last
+// block scans and publishes the kept total.
+__global__ void __launch_bounds__(kThreads) k_keep_sums(const uint32_t *__restrict__ counts,
+                                                        const uint32_t *__restrict__ n_occ,
+                                                        uint32_t min_pts, uint32_t *sums,
+                                                        uint32_t *offsets, uint32_t *counter,
+                                                        int32_t *n_out, int64_t cap,
+                                                        uint32_t *err) {
+    __shared__ uint32_t warp_tot[kThreads / 32];
+    __shared__ bool is_last;
+    const uint32_t n = *n_occ;
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t i = (blockIdx.x * kThreads + threadIdx.x) * 4 + j;
+        if (i < n && counts[i] >= min_pts) ++c;
+    }
+    uint32_t tot;
+    block_exclusive_scan(c, warp_tot, tot);
+    if (threadIdx.x == 0) {
+        sums[blockIdx.x] = tot;
+        __threadfence();
+        is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    uint32_t total = scan_block_sums(sums, offsets, gridDim.x, warp_tot);
+    if (threadIdx.x == 0) {
+        *n_out = static_cast<int32_t>(total);
+        if (total > cap) raise_error(err, GMAPP_DEVERR_CAPACITY);
+        *counter = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_keep_emit(const uint32_t *__restrict__ tkeys,
+                                                        const uint32_t *__restrict__ tcounts,
+                                                        const uint32_t *__restrict__ trep,
+                                                        const uint32_t *__restrict__ n_occ,
+                                                        const uint32_t *__restrict__ offsets,
+                                                        uint32_t min_pts, FilterArgs A,
+                                                        EmitOut o) {
+    __shared__ uint32_t warp_tot[kThreads / 32];
+    const uint32_t n = *n_occ;
+    bool keep[4];
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t i = (blockIdx.x * kThreads + threadIdx.x) * 4 + j;
+        keep[j] = i < n && tcounts[i] >= min_pts;
+        c += keep[j];
+    }
+    uint32_t tot;
+    uint32_t rank = offsets[blockIdx.x] + block_exclusive_scan(c, warp_tot, tot);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (!keep[j]) continue;
+        uint32_t i = (blockIdx.x * kThreads + threadIdx.x) * 4 + j;
+        if (rank < o.cap) {
+            uint32_t key = tkeys[i];
+            o.keys[rank] = key;
+            o.counts[rank] = tcounts[i];
+            o.rep[rank] = trep[i];
+            float cx, cy, cz;
+            voxel_centre(key, A, cx, cy, cz);
+            o.x[rank] = cx;
+            o.y[rank] = cy;
+            o.z[rank] = cz;
+        }
+        ++rank;
+    }
+}
+
+// Workspace layout (all sections 256-byte aligned).
+struct Layout {
+    int64_t n_words;   // bitmap words, padded to a whole number of k_bitmap_sums blocks
+    int64_t n_blocks;  // k_bitmap_sums / k_emit blocks
+    int64_t n_tmp;     // temporary entries (min_pts > 1), padded to 1024
+    int64_t n_tblocks; // k_keep_* blocks
+    size_t off_bitmap, off_prefix, off_sums, off_offsets, off_counters, off_keys;
+    size_t off_tkeys, off_tcounts, off_trep, off_tsums, off_toffsets;
+    size_t total;
+};
+
+bool valid_workspace(const gmapp_workspace *ws) {
+    if (!ws) return false;
+    if (!(ws->voxel > 0.0f) || !isfinite(ws->voxel) || ws->min_pts < 1) return false;
+    uint64_t cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (ws->dims[a] < 1 || ws->dims[a] > (1 << 24) || !isfinite(ws->lo[a])) return false;
+        cells *= static_cast<uint64_t>(ws->dims[a]);
+    }
+    return cells < 0xFFFFFFFFull;
+}
+
+Layout layout(int64_t n_raw, const gmapp_workspace *ws) {
+    Layout L{};
+    uint64_t cells = (uint64_t)ws->dims[0] * ws->dims[1] * ws->dims[2];
+    int64_t words = static_cast<int64_t>((cells + 31) / 32);
+    L.n_blocks = (words + kWordsPerBlock - 1) / kWordsPerBlock;
+    L.n_words = L.n_blocks * kWordsPerBlock;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    L.off_bitmap = take(L.n_words * 4);
+    L.off_prefix = take(L.n_words * 4);
+    L.off_sums = take(L.n_blocks * 4);
+    L.off_offsets = take(L.n_blocks * 4);
+    L.off_counters = take(64);
+    L.off_keys = take(align_up(n_raw > 0 ? n_raw : 1, 4) * 4);
+    if (ws->min_pts > 1) {
+        int64_t nt = std::min<int64_t>(n_raw, static_cast<int64_t>(cells));
+        L.n_tblocks = std::max<int64_t>(1, (nt + kWordsPerBlock - 1) / kWordsPerBlock);
+        L.n_tmp = L.n_tblocks * kWordsPerBlock;
+        L.off_tkeys = take(L.n_tmp * 4);
+        L.off_tcounts = take(L.n_tmp * 4);
+        L.off_trep = take(L.n_tmp * 4);
+        L.off_tsums = take(L.n_tblocks * 4);
+        L.off_toffsets = take(L.n_tblocks * 4);
+    }
+    L.total = off;
+    return L;
+}
+
+
+}  // namespace
+}  // namespace gmapp

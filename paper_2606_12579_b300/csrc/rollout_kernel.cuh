@@ -120,6 +120,45 @@ __device__ __forceinline__ float softplus_f(float x, float beta) {
     return r / beta;
 }
 
+// One step of Sec. IV-A for one agent, given the Alg. 1 sum W and the
+// smallest squared obstacle distance md2:
+//   g  = (|v|^2 c - v (v.c)) / |v|   (0 when |v|^2 < 1e-30), v = v_{k-1}
+//   F  = k_a (goal - p) - D v + rho k_r W g;  v += h F (h = 1/2 dt inv_mass)
+//   p += dt v;  L += dt |v|;  with CLEAR: m = sqrt(md2) - R,
+//   pen += softplus_beta(margin - m), minc = min(minc, m).
+// Returns g, the field strength kf = rho k_r W and m (inf without CLEAR).
+template <bool CLEAR>
+__device__ __forceinline__ void agent_step(float (&p)[3], float (&v)[3], const float (&cc)[3],
+                                           float k_r, float k_a, float R, const float (&goal)[3],
+                                           float h, float dt, float rho, float damping,
+                                           float clear_margin, float clear_beta, float W,
+                                           float md2, float &L, float &pen, float &minc,
+                                           float &m, float (&g)[3], float &kf) {
+    g[0] = g[1] = g[2] = 0.0f;
+    const float vv = fmaf(v[2], v[2], fmaf(v[1], v[1], v[0] * v[0]));
+    if (vv >= 1e-30f) {
+        const float inv = 1.0f / sqrtf(vv);
+        const float vc = fmaf(v[2], cc[2], fmaf(v[1], cc[1], v[0] * cc[0]));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) g[d] = (vv * cc[d] - v[d] * vc) * inv;
+    }
+    kf = rho * k_r * W;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float F = k_a * (goal[d] - p[d]) - damping * v[d] + kf * g[d];
+        v[d] = fmaf(h, F, v[d]);
+    }
+    L = fmaf(dt, sqrtf(fmaf(v[2], v[2], fmaf(v[1], v[1], v[0] * v[0]))), L);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) p[d] = fmaf(dt, v[d], p[d]);
+    m = INFINITY;
+    if (CLEAR) {
+        m = sqrtf(md2) - R;
+        pen += softplus_f(clear_margin - m, clear_beta);
+        minc = fminf(minc, m);
+    }
+}
+
 // Agent range of cluster q: groups get floor or ceil of N_a / G agents.
 __device__ __forceinline__ void group_range(int q, int n_agents, int n_groups, int &a0, int &na) {
     const int base = n_agents / n_groups, rem = n_agents % n_groups;
@@ -170,11 +209,48 @@ __device__ __forceinline__ int transposed_index(int lane) {
 // Partial Alg. 1 sums of this thread's obstacle pairs for NA agents
 // (agent indices OFF .. OFF+NA-1 of the group), reduced over the warp and
 // stored into every cluster CTA's receive slots recv[h][par][rank][warp][a].
-template <int AG, int NA, int OFF, int NM, int NT, bool CLEAR>
+// The Alg. 1 terms of one obstacle pair (two f32x2 lanes) for NA agents,
+// accumulated into acc (and the squared-distance minimum mn with CLEAR).
+template <int AG, int NA, int OFF, int NM, bool CLEAR>
+__device__ __forceinline__ void pair_terms(f2 ox, f2 oy, f2 oz, const f2 (&X)[NA],
+                                           const f2 (&Y)[NA], const f2 (&Z)[NA], f2 (&acc)[NA],
+                                           float (&mn)[NA], const f2 (&nR2)[AG],
+                                           const float (&G2a)[AG], float eps, f2 one2) {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const f2 dx = sub2(X[a], ox), dy = sub2(Y[a], oy), dz = sub2(Z[a], oz);
+        const f2 d2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        const float d2l = lo_of(d2), d2h = hi_of(d2);
+        const f2 mask = pk(le_mask(d2l, G2a[OFF + a]), le_mask(d2h, G2a[OFF + a]));
+        const f2 r = pk(rsqrt_approx(d2l), rsqrt_approx(d2h));
+        const f2 s = fma2(d2, r, nR2[OFF + a]);  // |d| - R (NaN when d = 0)
+        const float sl = fmaxf(lo_of(s), eps), sh = fmaxf(hi_of(s), eps);
+        if (a < NM) {
+            acc[a] = fma2(mask, pk(rcp_approx(sl), rcp_approx(sh)), acc[a]);
+        } else {
+            const f2 s2 = pk(sl, sh);
+            f2 y = pk(neg_rcp_seed(sl), neg_rcp_seed(sh));
+#pragma unroll
+            for (int it = 0; it < 3; ++it) y = fma2(y, fma2(s2, y, one2), y);
+            acc[a] = fma2(mask, y, acc[a]);
+        }
+        if (CLEAR) mn[a] = fminf(mn[a], fminf(d2l, d2h));
+    }
+}
+
+// Obstacles beyond what shared memory holds, read from global memory
+// (L2-resident): indices [begin, end) of the obstacle arrays.
+struct GlobalTail {
+    const float *x, *y, *z;
+    int begin, end;
+};
+
+template <int AG, int NA, int OFF, int NM, int NT, bool CLEAR, bool TAIL = false>
 __device__ __forceinline__ void half_step(const float *sx, const float *sy, const float *sz,
                                           int cnt_pad, float eps, const f2 (&nR2)[AG],
                                           const float (&G2a)[AG], const float (&p)[3],
-                                          float *recv_slot0, uint32_t C, int lane) {
+                                          float *recv_slot0, uint32_t C, int lane,
+                                          GlobalTail tail = GlobalTail{}) {
     if constexpr (NA > 0) {
         constexpr int P = pow2ceil(NA);
         const int tid = threadIdx.x;
@@ -197,25 +273,22 @@ __device__ __forceinline__ void half_step(const float *sx, const float *sy, cons
             const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
             const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
             const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
-#pragma unroll
-            for (int a = 0; a < NA; ++a) {
-                const f2 dx = sub2(X[a], ox), dy = sub2(Y[a], oy), dz = sub2(Z[a], oz);
-                const f2 d2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-                const float d2l = lo_of(d2), d2h = hi_of(d2);
-                const f2 mask = pk(le_mask(d2l, G2a[OFF + a]), le_mask(d2h, G2a[OFF + a]));
-                const f2 r = pk(rsqrt_approx(d2l), rsqrt_approx(d2h));
-                const f2 s = fma2(d2, r, nR2[OFF + a]);  // |d| - R (NaN when d = 0)
-                const float sl = fmaxf(lo_of(s), eps), sh = fmaxf(hi_of(s), eps);
-                if (a < NM) {
-                    acc[a] = fma2(mask, pk(rcp_approx(sl), rcp_approx(sh)), acc[a]);
-                } else {
-                    const f2 s2 = pk(sl, sh);
-                    f2 y = pk(neg_rcp_seed(sl), neg_rcp_seed(sh));
-#pragma unroll
-                    for (int it = 0; it < 3; ++it) y = fma2(y, fma2(s2, y, one2), y);
-                    acc[a] = fma2(mask, y, acc[a]);
+            pair_terms<AG, NA, OFF, NM, CLEAR>(ox, oy, oz, X, Y, Z, acc, mn, nR2, G2a, eps, one2);
+        }
+        if constexpr (TAIL) {
+            // tail.begin is even; an odd last obstacle is paired with NaN
+            for (int j = tail.begin + 2 * tid; j < tail.end; j += 2 * NT) {
+                f2 ox = __ldg(reinterpret_cast<const f2 *>(tail.x + j));
+                f2 oy = __ldg(reinterpret_cast<const f2 *>(tail.y + j));
+                f2 oz = __ldg(reinterpret_cast<const f2 *>(tail.z + j));
+                if (j + 1 >= tail.end) {
+                    const float nan = __int_as_float(0x7fc00000);
+                    ox = pk(lo_of(ox), nan);
+                    oy = pk(lo_of(oy), nan);
+                    oz = pk(lo_of(oz), nan);
                 }
-                if (CLEAR) mn[a] = fminf(mn[a], fminf(d2l, d2h));
+                pair_terms<AG, NA, OFF, NM, CLEAR>(ox, oy, oz, X, Y, Z, acc, mn, nR2, G2a, eps,
+                                                   one2);
             }
         }
         float vw[P], vm[P];
@@ -393,29 +466,9 @@ __global__ void __launch_bounds__(NT, 1) k_rollout(const RolloutArgs A) {
                 ck[(3 + d) * n] = v[d];
             }
         }
-        float g[3] = {0.0f, 0.0f, 0.0f};
-        const float vv = fmaf(v[2], v[2], fmaf(v[1], v[1], v[0] * v[0]));
-        if (vv >= 1e-30f) {
-            const float inv = 1.0f / sqrtf(vv);
-            const float vc = fmaf(v[2], cc[2], fmaf(v[1], cc[1], v[0] * cc[0]));
-#pragma unroll
-            for (int d = 0; d < 3; ++d) g[d] = (vv * cc[d] - v[d] * vc) * inv;
-        }
-        const float kf = A.rho * k_r * W;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const float F = k_a * (A.goal[d] - p[d]) - A.damping * v[d] + kf * g[d];
-            v[d] = fmaf(h, F, v[d]);
-        }
-        L = fmaf(A.dt, sqrtf(fmaf(v[2], v[2], fmaf(v[1], v[1], v[0] * v[0]))), L);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) p[d] = fmaf(A.dt, v[d], p[d]);
-        float m = INFINITY;
-        if (CLEAR) {
-            m = sqrtf(md2) - R;
-            pen += softplus_f(A.clear_margin - m, A.clear_beta);
-            minc = fminf(minc, m);
-        }
+        float g[3], kf, m;
+        agent_step<CLEAR>(p, v, cc, k_r, k_a, R, A.goal, h, A.dt, A.rho, A.damping,
+                          A.clear_margin, A.clear_beta, W, md2, L, pen, minc, m, g, kf);
         if (rank == 0 && warp == 0) {
             const int i = a0 + lane;
             if (A.traj) {

@@ -7,90 +7,9 @@
 // trajectory so the caller can hand it to the controller with one read.
 #include <math.h>
 
-#include "gmapp_internal.cuh"
+#include "score_device.cuh"
 
-namespace gmapp {
-namespace {
 
-constexpr int kThreads = 1024;
-
-struct ScoreArgs {
-    const float *p_final, *path_len, *clear_pen, *traj;
-    int32_t n, n_steps;
-    float goal[3];
-    float w_path, w_goal, w_clear;
-    float prev_best, alpha;
-    float *costs;
-    int32_t *best;
-    float *best_traj;
-};
-
-__device__ __forceinline__ void better(float &bv, int &bi, float ov, int oi) {
-    if (ov < bv || (ov == bv && oi < bi)) {
-        bv = ov;
-        bi = oi;
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) k_score_select(const ScoreArgs S) {
-    __shared__ float wv[kThreads / 32];
-    __shared__ int wi[kThreads / 32];
-    __shared__ int s_best;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool has_prev = !isnan(S.prev_best);
-    const float thr = S.alpha * S.prev_best;
-    float bv = INFINITY;
-    int bi = INT_MAX;
-    for (int i = tid; i < S.n; i += kThreads) {
-        const float dx = S.p_final[i] - S.goal[0];
-        const float dy = S.p_final[S.n + i] - S.goal[1];
-        const float dz = S.p_final[2 * S.n + i] - S.goal[2];
-        const float dist = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
-        const float pen = S.clear_pen ? S.clear_pen[i] : 0.0f;
-        const float C = S.w_path * S.path_len[i] + S.w_goal * dist + S.w_clear * pen;
-        S.costs[i] = C;
-        const bool ok = !isnan(C) && (!has_prev || C < thr);
-        if (ok && C < bv) {  // i ascends within a thread: strict < keeps the lowest index
-            bv = C;
-            bi = i;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        better(bv, bi, ov, oi);
-    }
-    if (lane == 0) {
-        wv[warp] = bv;
-        wi[warp] = bi;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        bv = lane < kThreads / 32 ? wv[lane] : INFINITY;
-        bi = lane < kThreads / 32 ? wi[lane] : INT_MAX;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            better(bv, bi, ov, oi);
-        }
-        if (lane == 0) {
-            s_best = bi == INT_MAX ? -1 : bi;
-            *S.best = s_best;
-        }
-    }
-    __syncthreads();
-    const int b = s_best;
-    if (b >= 0 && S.best_traj) {
-        const int m = (S.n_steps + 1) * 3;
-        const float *src = S.traj + (size_t)b * m;
-        for (int j = tid; j < m; j += kThreads) S.best_traj[j] = src[j];
-    }
-}
-
-}  // namespace
-}  // namespace gmapp
 
 using namespace gmapp;
 
@@ -129,7 +48,7 @@ extern "C" gmapp_status score_and_select(gmapp_ctx *ctx, const gmapp_rollout_out
     S.costs = costs;
     S.best = best;
     S.best_traj = best_traj;
-    k_score_select<<<1, kThreads, 0, stream>>>(S);
+    k_score_select<<<1, kScoreThreads, 0, stream>>>(S);
     GMAPP_CHECK_CUDA(cudaGetLastError());
     return GMAPP_OK;
 }

@@ -1,0 +1,169 @@
+"""Batched uneven queries (one persistent rollout launch, CUDA-graph replay,
+autotuned work items) vs the oracle and vs each query run alone."""
+
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+from _helpers import to_dev_agents, subset_agents, u32
+
+pytestmark = pytest.mark.gpu
+POS_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def gm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2606_12579_b300 as gm
+    gm.context()
+    return gm
+
+
+def _small_queries(n=9, seed=77):
+    """Uneven sphere scenes, small enough for the oracle."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for q in range(n):
+        w = synth.sphere_workload(seed=int(g.integers(1, 1 << 30)),
+                                  n_raw=int(g.integers(3000, 40000)),
+                                  voxel=float(np.float32(g.uniform(0.006, 0.012))),
+                                  n_agents=int(g.integers(1, 40)), n_steps=int(g.integers(20, 160)))
+        out.append(w)
+    return out
+
+
+def _specs(ws_list, cap=None):
+    import torch
+    specs = []
+    for w in ws_list:
+        specs.append({"xyz": torch.from_numpy(w["xyz"]).cuda(), "T": w["T"], "ws": w["workspace"],
+                      "agents": to_dev_agents(w["agents"]), "prm": w["params"],
+                      "obs_cap": cap if cap is not None else 16384})
+    return specs
+
+
+def test_batch_matches_oracle_per_query(gm):
+    ws_list = _small_queries()
+    b = gm.Batch(_specs(ws_list))
+    b.run()
+    gm.sync()
+    for w, r in zip(ws_list, b.results):
+        ref_f = oracle.filter_cloud(w["xyz"], w["T"], w["workspace"])
+        n = r["obs"].count()
+        assert n == ref_f["n"]
+        assert np.array_equal(u32(r["obs"].keys[:n]), ref_f["keys"])
+        obs = np.stack([ref_f["x"], ref_f["y"], ref_f["z"]])
+        ref = oracle.rollout(obs, ref_f["r_O"], w["agents"], w["params"])
+        err = np.abs(r["out"]["traj"].cpu().numpy() - ref["traj"]).max()
+        assert err <= POS_TOL
+        c_ref = oracle.costs(ref, w["params"])
+        gi, oi = int(r["best"].item()), oracle.select(c_ref)
+        assert gi == oi or abs(c_ref[gi] - c_ref[oi]) < 1e-6
+        assert np.allclose(r["costs"].cpu().numpy(), c_ref, rtol=1e-4, atol=1e-4)
+
+
+def test_query_alone_equals_query_in_batch(gm):
+    """Work items depend only on their own query: bit-identical results."""
+    ws_list = _small_queries(seed=5)
+    big = gm.Batch(_specs(ws_list))
+    big.run()
+    gm.sync()
+    for q in (0, 4, 8):
+        alone = gm.Batch(_specs([ws_list[q]]))
+        alone.run()
+        gm.sync()
+        a, bq = alone.results[0], big.results[q]
+        for k in ("traj", "p_final", "path_len"):
+            assert np.array_equal(a["out"][k].cpu().numpy(), bq["out"][k].cpu().numpy()), k
+        assert np.array_equal(a["costs"].cpu().numpy(), bq["costs"].cpu().numpy())
+        assert int(a["best"].item()) == int(bq["best"].item())
+
+
+def test_graph_replay_equals_direct_run(gm):
+    import torch
+    ws_list = _small_queries(seed=9)
+    b = gm.Batch(_specs(ws_list))
+    b.run()
+    gm.sync()
+    ref = [r["out"]["traj"].clone() for r in b.results]
+    s = torch.cuda.Stream()
+    for _ in range(2):
+        for r in b.results:
+            r["out"]["traj"].zero_()
+        torch.cuda.synchronize()
+        b.launch_graph(s)
+        s.synchronize()
+        gm.sync()
+        for r, t in zip(b.results, ref):
+            assert torch.equal(r["out"]["traj"], t)
+
+
+def test_autotuner_and_every_tuning_agree_with_oracle(gm):
+    ws_list = _small_queries(n=5, seed=21)
+    b = gm.Batch(_specs(ws_list))
+    shape, ms = b.autotune()
+    assert ms > 0 and shape[0] in (2, 4, 6, 8, 12, 16)
+    for tune in ((2, 256), (16, 256), (6, 384), (8, 512)):
+        b.set_tuning(*tune)
+        b.run()
+        gm.sync()
+        for w, r in zip(ws_list, b.results):
+            ref_f = oracle.filter_cloud(w["xyz"], w["T"], w["workspace"])
+            obs = np.stack([ref_f["x"], ref_f["y"], ref_f["z"]])
+            ref = oracle.rollout(obs, ref_f["r_O"], w["agents"], w["params"], want_traj=False)
+            assert np.abs(r["out"]["p_final"].cpu().numpy() - ref["p_final"]).max() <= POS_TOL
+
+
+def test_full_64_scene_batch(gm):
+    """The 64 uneven sphere scenes (raw 5k-300k points, 4-10 mm voxels,
+    32-1024 agents, 100-1000 steps): every filter bit-exact, rollouts of
+    sampled agents within tolerance."""
+    ws_list = synth.batch_workloads()
+    b = gm.Batch(_specs(ws_list, cap=32768), want_traj=False)
+    b.run()
+    gm.sync()
+    rng = np.random.Generator(np.random.PCG64(3))
+    for q, (w, r) in enumerate(zip(ws_list, b.results)):
+        ref_f = oracle.filter_cloud(w["xyz"], w["T"], w["workspace"])
+        n = r["obs"].count()
+        assert n == ref_f["n"], q
+        assert np.array_equal(u32(r["obs"].keys[:n]), ref_f["keys"])
+        if q % 8 == 0:
+            na = w["agents"]["k_r"].size
+            idx = np.sort(rng.choice(na, size=min(3, na), replace=False))
+            obs = np.stack([ref_f["x"], ref_f["y"], ref_f["z"]])
+            ref = oracle.rollout(obs, ref_f["r_O"], subset_agents(w["agents"], idx), w["params"],
+                                 want_traj=False)
+            got = r["out"]["p_final"].cpu().numpy()[:, idx]
+            assert np.abs(got - ref["p_final"]).max() <= POS_TOL
+
+
+def test_capacity_errors(gm):
+    ws_list = _small_queries(n=3, seed=31)
+    b = gm.Batch(_specs(ws_list, cap=64))
+    b.run()
+    with pytest.raises(gm.GmappError) as e:
+        gm.sync()
+    assert e.value.status == 2
+
+
+def test_obstacle_sets_larger_than_shared_memory(gm):
+    """A 2 mm voxel sphere scene holds more obstacles than one CTA's shared
+    memory; the remainder is streamed from L2 with the same arithmetic."""
+    w = synth.sphere_workload(seed=4242, n_raw=120000, voxel=0.003, n_agents=9, n_steps=60)
+    ref_f = oracle.filter_cloud(w["xyz"], w["T"], w["workspace"])
+    assert ref_f["n"] > 19000
+    b = gm.Batch(_specs([w], cap=1 << 16))
+    b.run()
+    gm.sync()
+    r = b.results[0]
+    assert r["obs"].count() == ref_f["n"]
+    obs = np.stack([ref_f["x"], ref_f["y"], ref_f["z"]])
+    ref = oracle.rollout(obs, ref_f["r_O"], w["agents"], w["params"])
+    assert np.abs(r["out"]["traj"].cpu().numpy() - ref["traj"]).max() <= POS_TOL
