@@ -386,6 +386,87 @@ gmapp_status gmapp_batch_launch_graph(gmapp_batch *batch, gmapp_stream stream);
 gmapp_status gmapp_batch_autotune(gmapp_batch *batch, gmapp_stream stream, gmapp_tuning *best,
                                   float *best_ms);
 
+/* ------------------------------------------------------------------------ */
+/* Served control loop with continuous batching (the planning thread of       */
+/* Sec. V-B answers a query per control cycle; here requests overlap)         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t max_slots;       /* requests resident at once */
+    int32_t max_agents;      /* largest N_a of a request */
+    int32_t max_steps;       /* largest N_k of a request */
+    int64_t obs_cap;         /* obstacle capacity of one request (multiple of 4) */
+    int64_t arena_bytes;     /* device memory for admitted requests (allocated once) */
+    int32_t chunk_steps;     /* M: steps every active request advances per tick */
+    int32_t agents_per_item; /* work-item size of the chunk kernel: 4, 8 or 16 */
+    int32_t threads;         /* threads per CTA: 256, 384 or 512 */
+} gmapp_server_config;
+
+/* A request: HOST cloud and agent arrays (kept alive, unmodified, by the
+ * caller until the request is done; pinned memory lets the copies run
+ * asynchronously), the grid and the rollout constants. */
+typedef struct {
+    const float *xyz; /* host, n_raw x 3 camera-frame points */
+    int64_t n_raw;
+    float T[12];
+    gmapp_workspace ws;
+    const float *p0, *v0, *c;                /* host [3][n_agents] */
+    const float *k_r, *k_a, *r_d, *r_a;      /* host [n_agents] */
+    int32_t n_agents;
+    gmapp_rollout_params prm;
+    gmapp_cost_weights w;
+} gmapp_request;
+
+typedef struct {
+    int32_t done;
+    int32_t best;          /* selected agent i* */
+    float best_cost;
+    int32_t n_obs;         /* N_O of the request's S_W */
+    const float *best_traj; /* host [(n_steps+1)*3], valid until release */
+    const float *costs;     /* host [n_agents], valid until release */
+    double t_submit, t_admit, t_done; /* host steady clock, seconds */
+} gmapp_result;
+
+typedef struct {
+    int32_t active, pending;
+    int64_t completed;
+    int64_t arena_free_bytes;
+    int32_t shard_cap;     /* obstacles one CTA keeps in shared memory */
+} gmapp_server_stats_t;
+
+typedef struct gmapp_server gmapp_server;
+
+/* Create a server: one device arena, a compute and a copy stream, a queue of
+ * work items and pinned result staging per slot -- all allocated here;
+ * submit/tick/poll allocate no device memory. */
+gmapp_status gmapp_server_create(gmapp_ctx *ctx, const gmapp_server_config *cfg,
+                                 gmapp_server **out);
+void gmapp_server_destroy(gmapp_server *server);
+
+/* Queue a request (returns at once with a ticket).  GMAPP_ERR_CAPACITY when
+ * the request can never fit the arena. */
+gmapp_status gmapp_server_submit(gmapp_server *server, const gmapp_request *req,
+                                 int64_t *ticket);
+
+/* One scheduling round: waits for the previous round's chunk, retires
+ * requests whose plan reached host memory (freeing their bytes), admits
+ * queued requests in arrival order while their bytes fit (H2D copies on the
+ * copy stream, filter_cloud on the compute stream), advances every active
+ * request by up to chunk_steps steps in ONE persistent launch over
+ * (request, agent group) items, and scores the requests that reached their
+ * horizon (score_and_select, then D2H of i*, the costs and the chosen
+ * trajectory).  *n_active (may be NULL) receives the active count. */
+gmapp_status gmapp_server_tick(gmapp_server *server, int32_t *n_active);
+
+/* Result of a request: GMAPP_ERR_NOT_READY until done.  Identical bit for
+ * bit whether the request ran alone or together with any others. */
+gmapp_status gmapp_server_poll(gmapp_server *server, int64_t ticket, gmapp_result *res);
+
+/* Forget a finished request (its result pointers become invalid). */
+gmapp_status gmapp_server_release(gmapp_server *server, int64_t ticket);
+
+gmapp_status gmapp_server_stats(gmapp_server *server, gmapp_server_stats_t *out);
+
 #ifdef __cplusplus
 }
 #endif

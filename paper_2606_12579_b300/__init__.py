@@ -499,3 +499,92 @@ class Batch:
         check(_abi.load().gmapp_batch_autotune(self.handle, _stream(stream), C.byref(t), C.byref(ms)),
               "gmapp_batch_autotune")
         return (t.agents_per_cta, t.threads), float(ms.value)
+
+
+# ---------------------------------------------------------------------------
+# Served control loop (continuous batching)
+# ---------------------------------------------------------------------------
+
+def _host_ptr(a):
+    """Address of a contiguous float32 host array (numpy or CPU torch)."""
+    import numpy as np
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or not a.is_contiguous() or str(a.dtype) != "torch.float32":
+            raise ValueError("request arrays must be contiguous float32 host tensors")
+        return a.data_ptr()
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]):
+        raise ValueError("request arrays must be contiguous float32 host arrays")
+    return a.ctypes.data
+
+
+class Server:
+    """Control-rate request server: requests (host clouds and agents) are
+    admitted as arena memory frees up, advanced M steps per tick together in
+    one launch, scored and returned; see include/gmapp.h."""
+
+    def __init__(self, max_slots=16, max_agents=1024, max_steps=300, obs_cap=32768,
+                 arena_bytes=4 << 30, chunk_steps=50, agents_per_item=8, threads=256):
+        ctx = context()
+        cfg = _abi.ServerConfig(int(max_slots), int(max_agents), int(max_steps), int(obs_cap),
+                                int(arena_bytes), int(chunk_steps), int(agents_per_item),
+                                int(threads))
+        h = C.c_void_p()
+        check(_abi.load().gmapp_server_create(ctx.handle, C.byref(cfg), C.byref(h)),
+              "gmapp_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _abi._lib is not None:
+            _abi._lib.gmapp_server_destroy(h)
+            self.handle = None
+
+    def submit(self, xyz, T, ws, agents: dict, prm) -> int:
+        r = _abi.Request()
+        r.xyz = _host_ptr(xyz)
+        r.n_raw = int(xyz.shape[0])
+        for i, v in enumerate(list(T)):
+            r.T[i] = float(v)
+        r.ws = _ws_struct(ws)
+        for k in AGENT_KEYS:
+            setattr(r, k, _host_ptr(agents[k]))
+        r.n_agents = int(agents["k_r"].shape[0])
+        r.prm = _params_struct(prm)
+        r.w = _abi.CostWeights(float(prm.w_path), float(prm.w_goal), float(prm.w_clear))
+        t = C.c_int64()
+        check(_abi.load().gmapp_server_submit(self.handle, C.byref(r), C.byref(t)),
+              "gmapp_server_submit")
+        self._keep[t.value] = (xyz, agents, int(prm.n_steps))
+        return int(t.value)
+
+    def tick(self) -> int:
+        n = C.c_int32()
+        check(_abi.load().gmapp_server_tick(self.handle, C.byref(n)), "gmapp_server_tick")
+        return int(n.value)
+
+    def poll(self, ticket: int):
+        """None until done, then a dict with the selected agent, its cost, the
+        costs, the chosen trajectory [N_k+1, 3], N_O and timestamps."""
+        import numpy as np
+        res = _abi.Result()
+        st = _abi.load().gmapp_server_poll(self.handle, int(ticket), C.byref(res))
+        if st == _abi.ERR_NOT_READY:
+            return None
+        check(st, "gmapp_server_poll")
+        _, agents, nk = self._keep[ticket]
+        na = int(agents["k_r"].shape[0])
+        return {"best": int(res.best), "best_cost": float(res.best_cost), "n_obs": int(res.n_obs),
+                "best_traj": np.ctypeslib.as_array(res.best_traj, shape=((nk + 1) * 3,)).reshape(-1, 3).copy(),
+                "costs": np.ctypeslib.as_array(res.costs, shape=(na,)).copy(),
+                "t_submit": res.t_submit, "t_admit": res.t_admit, "t_done": res.t_done}
+
+    def release(self, ticket: int) -> None:
+        check(_abi.load().gmapp_server_release(self.handle, int(ticket)), "gmapp_server_release")
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        s = _abi.ServerStats()
+        check(_abi.load().gmapp_server_stats(self.handle, C.byref(s)), "gmapp_server_stats")
+        return {"active": s.active, "pending": s.pending, "completed": s.completed,
+                "arena_free_bytes": s.arena_free_bytes, "shard_cap": s.shard_cap}

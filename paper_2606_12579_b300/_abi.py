@@ -65,6 +65,30 @@ class Query(C.Structure):
                 ("best_traj", P)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("max_agents", C.c_int32), ("max_steps", C.c_int32),
+                ("obs_cap", C.c_int64), ("arena_bytes", C.c_int64), ("chunk_steps", C.c_int32),
+                ("agents_per_item", C.c_int32), ("threads", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("xyz", P), ("n_raw", C.c_int64), ("T", C.c_float * 12), ("ws", Workspace),
+                ("p0", P), ("v0", P), ("c", P), ("k_r", P), ("k_a", P), ("r_d", P), ("r_a", P),
+                ("n_agents", C.c_int32), ("prm", RolloutParams), ("w", CostWeights)]
+
+
+class Result(C.Structure):
+    _fields_ = [("done", C.c_int32), ("best", C.c_int32), ("best_cost", C.c_float),
+                ("n_obs", C.c_int32), ("best_traj", C.POINTER(C.c_float)),
+                ("costs", C.POINTER(C.c_float)), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("active", C.c_int32), ("pending", C.c_int32), ("completed", C.c_int64),
+                ("arena_free_bytes", C.c_int64), ("shard_cap", C.c_int32)]
+
+
 # name -> (restype, argtypes); every entry point declared in include/gmapp.h
 PROTOTYPES = {
     "gmapp_create": (C.c_int, [C.POINTER(P), C.c_int]),
@@ -97,6 +121,13 @@ PROTOTYPES = {
     "rollout_batch": (C.c_int, [P, P]),
     "gmapp_batch_launch_graph": (C.c_int, [P, P]),
     "gmapp_batch_autotune": (C.c_int, [P, P, C.POINTER(Tuning), C.POINTER(C.c_float)]),
+    "gmapp_server_create": (C.c_int, [P, C.POINTER(ServerConfig), C.POINTER(P)]),
+    "gmapp_server_destroy": (None, [P]),
+    "gmapp_server_submit": (C.c_int, [P, C.POINTER(Request), C.POINTER(C.c_int64)]),
+    "gmapp_server_tick": (C.c_int, [P, C.POINTER(C.c_int32)]),
+    "gmapp_server_poll": (C.c_int, [P, C.c_int64, C.POINTER(Result)]),
+    "gmapp_server_release": (C.c_int, [P, C.c_int64]),
+    "gmapp_server_stats": (C.c_int, [P, C.POINTER(ServerStats)]),
     "score_and_select": (C.c_int, [P, C.POINTER(RolloutOut), C.c_int32, C.POINTER(RolloutParams),
                                    C.POINTER(CostWeights), C.c_float, C.c_float, P, P, P, P]),
 }

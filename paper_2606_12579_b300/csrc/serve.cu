@@ -1,0 +1,707 @@
+// Served control loop with continuous batching (the paper's planning thread
+// answers one query per control cycle, Sec. V-B; here many requests are in
+// flight at once).
+//
+// A gmapp_server owns a device arena.  Requests arrive from the host with
+// host-resident clouds and agents; a request is admitted as soon as its
+// bytes fit in the arena (first fit), its inputs are copied on a copy stream
+// and filtered on the compute stream.  Every tick advances EVERY active
+// request by up to M steps in ONE persistent launch over (request, agent
+// group) work items -- requests that arrived while others run join at the
+// next tick -- and requests that reach their horizon are scored, their plan
+// copied to pinned host memory, and their memory released.  A work item's
+// arithmetic depends only on its own request and the agent state is kept
+// exactly between chunks, so each result is bit-identical whether the
+// request runs alone or in any mix.
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <vector>
+
+#include "rollout_kernel.cuh"
+
+namespace gmapp {
+namespace {
+
+struct SlotDev {
+    const float *ox, *oy, *oz;
+    const int32_t *n_obs;
+    int64_t cap;
+    float r_O;
+    const float *p0, *v0, *c, *k_r, *k_a, *r_d, *r_a;
+    int32_t n_agents, n_groups;
+    float goal[3];
+    float dt;
+    int32_t n_steps;
+    float damping, inv_mass, rho, eps, vel_half, clear_margin, clear_beta;
+    float *sp, *sv, *sL;       // saved state between chunks: p [3][n], v [3][n], L [n]
+    float *traj, *p_final, *v_final, *path_len;
+};
+
+struct ChunkItem {
+    int32_t slot, group, k0, k1;
+};
+
+struct ChunkArgs {
+    const SlotDev *slots;
+    const ChunkItem *items;
+    int32_t n_items;
+    uint32_t *head;
+    int32_t shard_cap;
+    uint32_t *err;
+};
+
+template <int AG, int NT>
+__global__ void __launch_bounds__(NT, 1) ks_chunk(const ChunkArgs A) {
+    constexpr int NW = NT / 32;
+    constexpr int NM = sfu_agents(AG);
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_item;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *sx = smem, *sy = smem + A.shard_cap, *sz = smem + 2 * A.shard_cap;
+    float *recv = smem + 3 * A.shard_cap;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    for (;;) {
+        if (tid == 0) s_item = static_cast<int>(atomicAdd(A.head, 1u));
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= A.n_items) break;
+        const ChunkItem item = A.items[it];
+        const SlotDev &S = A.slots[item.slot];
+        int a0, na;
+        group_range(item.group, S.n_agents, S.n_groups, a0, na);
+        const int32_t n_obs = *S.n_obs;
+        if (n_obs < 0 || n_obs > S.cap || na > AG) {
+            if (tid == 0) raise_error(A.err, GMAPP_DEVERR_CAPACITY);
+            continue;
+        }
+        int32_t cnt = min(n_obs, A.shard_cap);
+        const GlobalTail tail{S.ox, S.oy, S.oz, cnt, n_obs};
+        if (cnt > 0 && tid == 0) {
+            const uint32_t bytes = static_cast<uint32_t>((cnt + 3) & ~3) * 4u;
+            mbar_arrive_expect_tx(&bar, 3 * bytes);
+            bulk_g2s(sx, S.ox, bytes, &bar);
+            bulk_g2s(sy, S.oy, bytes, &bar);
+            bulk_g2s(sz, S.oz, bytes, &bar);
+        }
+        const int n = S.n_agents, N = S.n_steps;
+        float p[3] = {0, 0, 0}, v[3] = {0, 0, 0}, cc[3] = {0, 0, 0};
+        float k_r = 0, k_a = 0, R = 0, G2 = -1.0f, L = 0, pen = 0, minc = INFINITY;
+        if (lane < na) {
+            const int i = a0 + lane;
+            const bool first = item.k0 == 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                p[d] = first ? S.p0[d * n + i] : S.sp[d * n + i];
+                v[d] = first ? S.v0[d * n + i] : S.sv[d * n + i];
+                cc[d] = S.c[d * n + i];
+            }
+            L = first ? 0.0f : S.sL[i];
+            k_r = S.k_r[i];
+            k_a = S.k_a[i];
+            R = S.r_a[i] + S.r_O;
+            const float rd = S.r_d[i];
+            G2 = rd >= S.eps ? (rd + R) * (rd + R) : -1.0f;
+            if (first && warp == 0 && S.traj) {
+                float *t = S.traj + (size_t)i * (N + 1) * 3;
+                t[0] = p[0];
+                t[1] = p[1];
+                t[2] = p[2];
+            }
+        }
+        f2 nR2[AG];
+        float G2a[AG];
+#pragma unroll
+        for (int a = 0; a < AG; ++a) {
+            const float r = __shfl_sync(0xffffffffu, R, a);
+            nR2[a] = pk(-r, -r);
+            G2a[a] = __shfl_sync(0xffffffffu, G2, a);
+        }
+        if (cnt > 0) {
+            if (!mbar_wait(&bar, phase)) {
+                if (tid == 0) raise_error(A.err, GMAPP_DEVERR_TIMEOUT);
+                cnt = 0;
+            }
+            phase ^= 1u;
+        }
+        const int32_t cnt_pad = (cnt + 1) & ~1;
+        if (tid == 0 && cnt_pad > cnt) {
+            sx[cnt] = __int_as_float(0x7fc00000);
+            sy[cnt] = __int_as_float(0x7fc00000);
+            sz[cnt] = __int_as_float(0x7fc00000);
+        }
+        __syncthreads();
+        const float h = S.vel_half * S.dt * S.inv_mass;
+        const float goal[3] = {S.goal[0], S.goal[1], S.goal[2]};
+        for (int k = item.k0; k < item.k1; ++k) {
+            float *rp = recv + (k & 1) * (NW * AG * 2);
+            half_step<AG, AG, 0, NM, NT, false, true>(sx, sy, sz, cnt_pad, S.eps, nR2, G2a, p,
+                                                      rp + 2 * (warp * AG), 1u, lane, tail);
+            __syncthreads();
+            float W = 0.0f, md2 = INFINITY;
+            half_combine<AG, AG, 0, false>(rp, NW, lane, W, md2);
+            if (lane < na) {
+                float g[3], kf, m;
+                agent_step<false>(p, v, cc, k_r, k_a, R, goal, h, S.dt, S.rho, S.damping,
+                                  S.clear_margin, S.clear_beta, W, md2, L, pen, minc, m, g, kf);
+                if (warp == 0 && S.traj) {
+                    float *t = S.traj + ((size_t)(a0 + lane) * (N + 1) + k + 1) * 3;
+                    t[0] = p[0];
+                    t[1] = p[1];
+                    t[2] = p[2];
+                }
+            }
+        }
+        if (warp == 0 && lane < na) {
+            const int i = a0 + lane;
+            for (int d = 0; d < 3; ++d) {
+                S.sp[d * n + i] = p[d];
+                S.sv[d * n + i] = v[d];
+            }
+            S.sL[i] = L;
+            if (item.k1 == N) {
+                for (int d = 0; d < 3; ++d) {
+                    S.p_final[d * n + i] = p[d];
+                    S.v_final[d * n + i] = v[d];
+                }
+                S.path_len[i] = L;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+using ChunkKernel = void (*)(const ChunkArgs);
+
+ChunkKernel chunk_kernel(int ag, int nt) {
+#define GMAPP_CK(AGV)                                             \
+    case AGV:                                                     \
+        switch (nt) {                                             \
+            case 256: return ks_chunk<AGV, 256>;                  \
+            case 384: return ks_chunk<AGV, 384>;                  \
+            case 512:                                             \
+                if constexpr (AGV <= 8) return ks_chunk<AGV, 512>; \
+                return nullptr;                                   \
+            default: return nullptr;                              \
+        }
+    switch (ag) {
+        GMAPP_CK(4)
+        GMAPP_CK(8)
+        GMAPP_CK(16)
+        default: return nullptr;
+    }
+#undef GMAPP_CK
+}
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit byte allocator over the device arena (offsets, 256-aligned).
+class Arena {
+   public:
+    void init(size_t bytes) { free_.assign(1, {0, bytes}); }
+    bool alloc(size_t bytes, size_t *off) {
+        bytes = align_up(bytes, 256);
+        for (size_t i = 0; i < free_.size(); ++i)
+            if (free_[i].second >= bytes) {
+                *off = free_[i].first;
+                free_[i].first += bytes;
+                free_[i].second -= bytes;
+                if (free_[i].second == 0) free_.erase(free_.begin() + i);
+                return true;
+            }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = align_up(bytes, 256);
+        free_.push_back({off, bytes});
+        std::sort(free_.begin(), free_.end());
+        std::vector<std::pair<size_t, size_t>> merged;
+        for (auto &r : free_) {
+            if (!merged.empty() && merged.back().first + merged.back().second == r.first)
+                merged.back().second += r.second;
+            else
+                merged.push_back(r);
+        }
+        free_.swap(merged);
+    }
+    size_t free_bytes() const {
+        size_t s = 0;
+        for (auto &r : free_) s += r.second;
+        return s;
+    }
+
+   private:
+    std::vector<std::pair<size_t, size_t>> free_;
+};
+
+}  // namespace
+}  // namespace gmapp
+
+using namespace gmapp;
+
+struct ServerReq {
+    gmapp_request req;
+    int64_t ticket;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    int slot = -1;
+    size_t off = 0, bytes = 0;
+    int32_t k = 0;  // steps done
+    enum { PENDING, ACTIVE, SCORING, DONE } state = PENDING;
+    // results, copied out of the slot's pinned staging when the request retires
+    int32_t best = -1, n_obs = 0;
+    std::vector<float> costs, traj;
+    // device buffers inside the arena
+    float *d_xyz = nullptr;
+    void *d_fws = nullptr;
+    size_t fws_bytes = 0;
+    gmapp_obstacles obs{};
+    float *d_costs = nullptr, *d_best_traj = nullptr;
+    int32_t *d_best = nullptr;
+    gmapp_rollout_out out{};
+};
+
+struct gmapp_server {
+    gmapp_ctx *ctx = nullptr;
+    gmapp_server_config cfg{};
+    cudaStream_t compute = nullptr, copy = nullptr;
+    char *arena_base = nullptr;
+    Arena arena;
+    SlotDev *d_slots = nullptr;
+    SlotDev *h_slots = nullptr;   // pinned mirror
+    ChunkItem *d_items = nullptr;
+    ChunkItem *h_items = nullptr;  // pinned
+    uint32_t *d_head = nullptr;
+    int max_items = 0;
+    std::vector<int> free_slots;
+    std::deque<int64_t> pending;
+    std::map<int64_t, ServerReq *> reqs;
+    int64_t next_ticket = 1;
+    cudaEvent_t tick_ev = nullptr;
+    bool tick_in_flight = false;
+    // per slot: pinned result staging and events (created once)
+    int32_t *h_best = nullptr, *h_nobs = nullptr;
+    float *h_costs = nullptr, *h_traj = nullptr;
+    std::vector<cudaEvent_t> slot_done, slot_h2d;
+    ChunkKernel fn = nullptr;
+    size_t smem = 0;
+    int shard_cap = 0, resident = 0;
+    int64_t completed = 0;
+};
+
+namespace {
+
+size_t request_bytes(const gmapp_server_config &c, const gmapp_request &r, size_t fws) {
+    const size_t na = r.n_agents, nk = r.prm.n_steps;
+    size_t b = 0;
+    auto add = [&](size_t x) { b += align_up(x, 256); };
+    add(static_cast<size_t>(r.n_raw) * 12);           // cloud
+    add(fws);                                          // filter scratch
+    add(static_cast<size_t>(c.obs_cap) * 24 + 16);     // obstacle set (x,y,z,keys,counts,rep) + n
+    add(na * 13 * 4);                                  // agent arrays
+    add(na * 7 * 4);                                   // saved state p, v, L
+    add(na * 6 * 4 + na * 4);                          // p_final, v_final, path_len
+    add(na * (nk + 1) * 12);                           // trajectories
+    add(na * 4 + 4 + (nk + 1) * 12);                   // costs, best, best trajectory
+    return b;
+}
+
+gmapp_status admit(gmapp_server *s, ServerReq *q) {
+    const gmapp_request &r = q->req;
+    const size_t na = r.n_agents, nk = r.prm.n_steps;
+    char *base = s->arena_base + q->off;
+    size_t o = 0;
+    auto take = [&](size_t x) {
+        char *p = base + o;
+        o = align_up(o + x, 256);
+        return p;
+    };
+    q->d_xyz = reinterpret_cast<float *>(take(static_cast<size_t>(r.n_raw) * 12));
+    q->d_fws = take(q->fws_bytes);
+    const int64_t cap = s->cfg.obs_cap;
+    char *ob = take(static_cast<size_t>(cap) * 24 + 16);
+    q->obs.x = reinterpret_cast<float *>(ob);
+    q->obs.y = q->obs.x + cap;
+    q->obs.z = q->obs.y + cap;
+    q->obs.keys = reinterpret_cast<uint32_t *>(q->obs.z + cap);
+    q->obs.counts = q->obs.keys + cap;
+    q->obs.rep_idx = q->obs.counts + cap;
+    q->obs.n = reinterpret_cast<int32_t *>(q->obs.rep_idx + cap);
+    q->obs.cap = cap;
+    float *ag = reinterpret_cast<float *>(take(na * 13 * 4));
+    float *st = reinterpret_cast<float *>(take(na * 7 * 4));
+    float *fin = reinterpret_cast<float *>(take(na * 6 * 4 + na * 4));
+    q->out.traj = reinterpret_cast<float *>(take(na * (nk + 1) * 12));
+    float *sel = reinterpret_cast<float *>(take(na * 4 + 4 + (nk + 1) * 12));
+    q->out.p_final = fin;
+    q->out.v_final = fin + 3 * na;
+    q->out.path_len = fin + 6 * na;
+    q->d_costs = sel;
+    q->d_best = reinterpret_cast<int32_t *>(sel + na);
+    q->d_best_traj = sel + na + 1;
+    // inputs: host -> device on the copy stream
+    GMAPP_CHECK_CUDA(cudaMemcpyAsync(q->d_xyz, r.xyz, static_cast<size_t>(r.n_raw) * 12,
+                                     cudaMemcpyHostToDevice, s->copy));
+    const float *src[7] = {r.p0, r.v0, r.c, r.k_r, r.k_a, r.r_d, r.r_a};
+    const size_t cnt[7] = {3 * na, 3 * na, 3 * na, na, na, na, na};
+    size_t at = 0;
+    for (int i = 0; i < 7; ++i) {
+        GMAPP_CHECK_CUDA(cudaMemcpyAsync(ag + at, src[i], cnt[i] * 4, cudaMemcpyHostToDevice,
+                                         s->copy));
+        at += cnt[i];
+    }
+    cudaEvent_t ev = s->slot_h2d[q->slot];
+    GMAPP_CHECK_CUDA(cudaEventRecord(ev, s->copy));
+    GMAPP_CHECK_CUDA(cudaStreamWaitEvent(s->compute, ev, 0));
+    gmapp_status st2 = filter_cloud(s->ctx, q->d_xyz, r.n_raw, r.T, &r.ws, &q->obs, q->d_fws,
+                                    q->fws_bytes, s->compute);
+    if (st2 != GMAPP_OK) return st2;
+    // device descriptor of the slot
+    SlotDev &D = s->h_slots[q->slot];
+    memset(&D, 0, sizeof(D));
+    D.ox = q->obs.x;
+    D.oy = q->obs.y;
+    D.oz = q->obs.z;
+    D.n_obs = q->obs.n;
+    D.cap = cap;
+    D.r_O = q->obs.r_O;
+    D.p0 = ag;
+    D.v0 = ag + 3 * na;
+    D.c = ag + 6 * na;
+    D.k_r = ag + 9 * na;
+    D.k_a = ag + 10 * na;
+    D.r_d = ag + 11 * na;
+    D.r_a = ag + 12 * na;
+    D.n_agents = static_cast<int32_t>(na);
+    D.n_groups = static_cast<int32_t>((na + s->cfg.agents_per_item - 1) / s->cfg.agents_per_item);
+    for (int d = 0; d < 3; ++d) D.goal[d] = r.prm.goal[d];
+    D.dt = r.prm.dt;
+    D.n_steps = r.prm.n_steps;
+    D.damping = r.prm.damping;
+    D.inv_mass = r.prm.inv_mass;
+    D.rho = r.prm.rho;
+    D.eps = r.prm.eps;
+    D.vel_half = r.prm.vel_half;
+    D.clear_margin = r.prm.clear_margin;
+    D.clear_beta = r.prm.clear_beta;
+    D.sp = st;
+    D.sv = st + 3 * na;
+    D.sL = st + 6 * na;
+    D.traj = q->out.traj;
+    D.p_final = q->out.p_final;
+    D.v_final = q->out.v_final;
+    D.path_len = q->out.path_len;
+    GMAPP_CHECK_CUDA(cudaMemcpyAsync(s->d_slots + q->slot, &D, sizeof(SlotDev),
+                                     cudaMemcpyHostToDevice, s->compute));
+    return GMAPP_OK;
+}
+
+// The request's plan landed in its slot's pinned staging: keep a copy,
+// free the slot and its arena bytes.
+void retire(gmapp_server *s, ServerReq *q) {
+    const int sl = q->slot;
+    const size_t nk = q->req.prm.n_steps;
+    q->best = s->h_best[sl];
+    q->n_obs = s->h_nobs[sl];
+    const float *c = s->h_costs + (size_t)sl * s->cfg.max_agents;
+    q->costs.assign(c, c + q->req.n_agents);
+    const float *t = s->h_traj + (size_t)sl * (s->cfg.max_steps + 1) * 3;
+    q->traj.assign(t, t + (nk + 1) * 3);
+    q->t_done = now_s();
+    q->state = ServerReq::DONE;
+    s->arena.release(q->off, q->bytes);
+    s->free_slots.push_back(sl);
+    ++s->completed;
+}
+
+}  // namespace
+
+extern "C" gmapp_status gmapp_server_create(gmapp_ctx *ctx, const gmapp_server_config *cfg,
+                                            gmapp_server **out) {
+    if (!ctx || !cfg || !out || cfg->max_slots < 1 || cfg->arena_bytes < (1 << 20) ||
+        cfg->chunk_steps < 1 || cfg->obs_cap < 4 || cfg->obs_cap % 4 ||
+        cfg->max_agents < 1 || cfg->max_steps < 1) {
+        set_error("gmapp_server_create: invalid configuration");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    ChunkKernel fn = chunk_kernel(cfg->agents_per_item, cfg->threads);
+    if (!fn) {
+        set_error("gmapp_server_create: no chunk kernel for %d agents per item, %d threads",
+                  cfg->agents_per_item, cfg->threads);
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    gmapp_server *s = new gmapp_server();
+    s->ctx = ctx;
+    s->cfg = *cfg;
+    s->fn = fn;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void *>(fn));
+    const size_t recv_bytes =
+        static_cast<size_t>(2) * (cfg->threads / 32) * cfg->agents_per_item * 2 * sizeof(float);
+    const int64_t room =
+        (static_cast<int64_t>(ctx->max_smem_optin) - static_cast<int64_t>(fa.sharedSizeBytes + recv_bytes)) / 12;
+    s->shard_cap = static_cast<int>(std::min<int64_t>(cfg->obs_cap, room & ~int64_t(3)));
+    s->smem = static_cast<size_t>(s->shard_cap) * 12 + recv_bytes;
+    const int max_groups = (cfg->max_agents + cfg->agents_per_item - 1) / cfg->agents_per_item;
+    s->max_items = cfg->max_slots * max_groups;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(s->smem));
+    int per_sm = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(fn),
+                                                           cfg->threads, s->smem);
+    s->resident = std::max(1, per_sm) * ctx->sm_count;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&s->arena_base, cfg->arena_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_slots, sizeof(SlotDev) * cfg->max_slots);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_slots, sizeof(SlotDev) * cfg->max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_items, sizeof(ChunkItem) * s->max_items);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_items, sizeof(ChunkItem) * s->max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_head, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->tick_ev, cudaEventDisableTiming);
+    const size_t ms = cfg->max_slots;
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_best, sizeof(int32_t) * ms);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_nobs, sizeof(int32_t) * ms);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_costs, sizeof(float) * ms * cfg->max_agents);
+    if (e == cudaSuccess)
+        e = cudaMallocHost(&s->h_traj, sizeof(float) * ms * (cfg->max_steps + 1) * 3);
+    for (size_t i = 0; i < ms && e == cudaSuccess; ++i) {
+        cudaEvent_t a, b;
+        e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b, cudaEventDisableTiming);
+        if (e == cudaSuccess) {
+            s->slot_done.push_back(a);
+            s->slot_h2d.push_back(b);
+        }
+    }
+    if (e != cudaSuccess) {
+        gmapp_status st = cuda_fail(e, "gmapp_server_create");
+        gmapp_server_destroy(s);
+        return st;
+    }
+    s->arena.init(cfg->arena_bytes);
+    for (int i = cfg->max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+    *out = s;
+    return GMAPP_OK;
+}
+
+extern "C" void gmapp_server_destroy(gmapp_server *s) {
+    if (!s) return;
+    if (s->compute) cudaStreamSynchronize(s->compute);
+    if (s->copy) cudaStreamSynchronize(s->copy);
+    for (auto &kv : s->reqs) delete kv.second;
+    for (cudaEvent_t e : s->slot_done) cudaEventDestroy(e);
+    for (cudaEvent_t e : s->slot_h2d) cudaEventDestroy(e);
+    cudaFreeHost(s->h_best);
+    cudaFreeHost(s->h_nobs);
+    cudaFreeHost(s->h_costs);
+    cudaFreeHost(s->h_traj);
+    if (s->tick_ev) cudaEventDestroy(s->tick_ev);
+    cudaFree(s->arena_base);
+    cudaFree(s->d_slots);
+    cudaFreeHost(s->h_slots);
+    cudaFree(s->d_items);
+    cudaFreeHost(s->h_items);
+    cudaFree(s->d_head);
+    if (s->compute) cudaStreamDestroy(s->compute);
+    if (s->copy) cudaStreamDestroy(s->copy);
+    delete s;
+}
+
+extern "C" gmapp_status gmapp_server_submit(gmapp_server *s, const gmapp_request *r,
+                                            int64_t *ticket) {
+    if (!s || !r || !ticket) {
+        set_error("gmapp_server_submit: NULL argument");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    if (!r->xyz || r->n_raw < 1 || r->n_agents < 1 || r->n_agents > s->cfg.max_agents ||
+        r->prm.n_steps < 1 || r->prm.n_steps > s->cfg.max_steps || !(r->prm.dt > 0.0f) || !(r->prm.eps > 0.0f) || !r->p0 || !r->v0 ||
+        !r->c || !r->k_r || !r->k_a || !r->r_d || !r->r_a || r->ws.min_pts < 1) {
+        set_error("gmapp_server_submit: invalid request (agents and steps within the server's "
+                  "maxima)");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    const size_t fws = gmapp_filter_workspace_bytes(r->n_raw, &r->ws);
+    if (fws == 0) {
+        set_error("gmapp_server_submit: invalid voxel grid");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    ServerReq *q = new ServerReq();
+    q->req = *r;
+    q->ticket = s->next_ticket++;
+    q->t_submit = now_s();
+    q->fws_bytes = fws;
+    q->bytes = request_bytes(s->cfg, *r, fws);
+    if (q->bytes > static_cast<size_t>(s->cfg.arena_bytes)) {
+        delete q;
+        set_error("gmapp_server_submit: request needs more than the whole arena");
+        return GMAPP_ERR_CAPACITY;
+    }
+    s->reqs[q->ticket] = q;
+    s->pending.push_back(q->ticket);
+    *ticket = q->ticket;
+    return GMAPP_OK;
+}
+
+extern "C" gmapp_status gmapp_server_tick(gmapp_server *s, int32_t *n_active) {
+    if (!s) {
+        set_error("gmapp_server_tick: NULL server");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    // 1. the previous tick's chunk is done: its finished requests were
+    //    scored with their results copied; retire those whose copy landed
+    if (s->tick_in_flight) {
+        GMAPP_CHECK_CUDA(cudaEventSynchronize(s->tick_ev));
+        s->tick_in_flight = false;
+    }
+    for (auto &kv : s->reqs) {
+        ServerReq *q = kv.second;
+        if (q->state != ServerReq::SCORING) continue;
+        if (cudaEventQuery(s->slot_done[q->slot]) != cudaSuccess) continue;
+        retire(s, q);
+    }
+    // 2. admit pending requests in arrival order while their bytes fit
+    while (!s->pending.empty() && !s->free_slots.empty()) {
+        ServerReq *q = s->reqs[s->pending.front()];
+        size_t off;
+        if (!s->arena.alloc(q->bytes, &off)) break;
+        s->pending.pop_front();
+        q->off = off;
+        q->slot = s->free_slots.back();
+        s->free_slots.pop_back();
+        q->t_admit = now_s();
+        gmapp_status st = admit(s, q);
+        if (st != GMAPP_OK) return st;
+        q->state = ServerReq::ACTIVE;
+        q->k = 0;
+    }
+    // 3. one chunk of up to M steps for every active request, one launch
+    std::vector<std::pair<int64_t, ChunkItem>> items;
+    int active = 0;
+    for (auto &kv : s->reqs) {
+        ServerReq *q = kv.second;
+        if (q->state != ServerReq::ACTIVE) continue;
+        ++active;
+        const int N = q->req.prm.n_steps;
+        const int k1 = std::min(N, q->k + s->cfg.chunk_steps);
+        const int groups = (q->req.n_agents + s->cfg.agents_per_item - 1) / s->cfg.agents_per_item;
+        for (int g = 0; g < groups; ++g) {
+            const int na = q->req.n_agents / groups + (g < q->req.n_agents % groups ? 1 : 0);
+            const int64_t cost = static_cast<int64_t>(na) * (k1 - q->k);
+            items.push_back({cost, ChunkItem{q->slot, g, q->k, k1}});
+        }
+        q->k = k1;
+    }
+    if (n_active) *n_active = active;
+    if (!items.empty()) {
+        // longest chunks first
+        std::stable_sort(items.begin(), items.end(),
+                         [](const auto &a, const auto &b) { return a.first > b.first; });
+        const int n_items = static_cast<int>(items.size());
+        for (int i = 0; i < n_items; ++i) s->h_items[i] = items[i].second;
+        GMAPP_CHECK_CUDA(cudaMemcpyAsync(s->d_items, s->h_items, sizeof(ChunkItem) * n_items,
+                                         cudaMemcpyHostToDevice, s->compute));
+        GMAPP_CHECK_CUDA(cudaMemsetAsync(s->d_head, 0, sizeof(uint32_t), s->compute));
+        ChunkArgs A{s->d_slots, s->d_items, n_items, s->d_head, s->shard_cap, s->ctx->d_err};
+        const int grid = std::max(1, std::min(n_items, s->resident));
+        s->fn<<<grid, s->cfg.threads, s->smem, s->compute>>>(A);
+        GMAPP_CHECK_CUDA(cudaGetLastError());
+    }
+    // 4. requests that reached their horizon: score, copy the plan out
+    for (auto &kv : s->reqs) {
+        ServerReq *q = kv.second;
+        if (q->state != ServerReq::ACTIVE || q->k < q->req.prm.n_steps) continue;
+        gmapp_status st = score_and_select(s->ctx, &q->out, q->req.n_agents, &q->req.prm,
+                                           &q->req.w, NAN, 1.0f, q->d_costs, q->d_best,
+                                           q->d_best_traj, s->compute);
+        if (st != GMAPP_OK) return st;
+        const size_t nk = q->req.prm.n_steps;
+        const int sl = q->slot;
+        GMAPP_CHECK_CUDA(cudaMemcpyAsync(s->h_best + sl, q->d_best, 4, cudaMemcpyDeviceToHost,
+                                         s->compute));
+        GMAPP_CHECK_CUDA(cudaMemcpyAsync(s->h_costs + (size_t)sl * s->cfg.max_agents, q->d_costs,
+                                         4 * q->req.n_agents, cudaMemcpyDeviceToHost, s->compute));
+        GMAPP_CHECK_CUDA(cudaMemcpyAsync(s->h_traj + (size_t)sl * (s->cfg.max_steps + 1) * 3,
+                                         q->d_best_traj, 12 * (nk + 1), cudaMemcpyDeviceToHost,
+                                         s->compute));
+        GMAPP_CHECK_CUDA(cudaMemcpyAsync(s->h_nobs + sl, q->obs.n, 4, cudaMemcpyDeviceToHost,
+                                         s->compute));
+        GMAPP_CHECK_CUDA(cudaEventRecord(s->slot_done[sl], s->compute));
+        q->state = ServerReq::SCORING;
+    }
+    GMAPP_CHECK_CUDA(cudaEventRecord(s->tick_ev, s->compute));
+    s->tick_in_flight = true;
+    return GMAPP_OK;
+}
+
+extern "C" gmapp_status gmapp_server_poll(gmapp_server *s, int64_t ticket, gmapp_result *res) {
+    if (!s || !res) {
+        set_error("gmapp_server_poll: NULL argument");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) {
+        set_error("gmapp_server_poll: unknown ticket %lld", (long long)ticket);
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    ServerReq *q = it->second;
+    if (q->state == ServerReq::SCORING && cudaEventQuery(s->slot_done[q->slot]) == cudaSuccess)
+        retire(s, q);  // landed between ticks
+    res->done = q->state == ServerReq::DONE;
+    res->t_submit = q->t_submit;
+    res->t_admit = q->t_admit;
+    res->t_done = q->t_done;
+    if (!res->done) return GMAPP_ERR_NOT_READY;
+    res->best = q->best;
+    res->best_cost = q->best >= 0 ? q->costs[q->best] : NAN;
+    res->n_obs = q->n_obs;
+    res->best_traj = q->traj.data();
+    res->costs = q->costs.data();
+    return GMAPP_OK;
+}
+
+extern "C" gmapp_status gmapp_server_release(gmapp_server *s, int64_t ticket) {
+    if (!s) {
+        set_error("gmapp_server_release: NULL server");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end() || it->second->state != ServerReq::DONE) {
+        set_error("gmapp_server_release: ticket %lld is unknown or not done", (long long)ticket);
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    delete it->second;
+    s->reqs.erase(it);
+    return GMAPP_OK;
+}
+
+extern "C" gmapp_status gmapp_server_stats(gmapp_server *s, gmapp_server_stats_t *out) {
+    if (!s || !out) {
+        set_error("gmapp_server_stats: NULL argument");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    int active = 0, pending = static_cast<int>(s->pending.size());
+    for (auto &kv : s->reqs) active += kv.second->state == ServerReq::ACTIVE;
+    out->active = active;
+    out->pending = pending;
+    out->completed = s->completed;
+    out->arena_free_bytes = static_cast<int64_t>(s->arena.free_bytes());
+    out->shard_cap = s->shard_cap;
+    return GMAPP_OK;
+}

@@ -1,0 +1,115 @@
+"""Served control loop with continuous batching: requests admitted by
+memory, advanced together in chunks; each result equals the same request
+served alone (bit for bit) and the oracle's (selection rule, costs and the
+chosen trajectory within tolerance)."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2606_12579_b300 as gm
+    gm.context()
+    return gm
+
+
+def _requests(n=6, seed=3):
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for r in range(n):
+        w = synth.tabletop_workload(seed=int(g.integers(1, 1 << 30)), n_points=30000, voxel=0.01,
+                                    n_agents=int(g.choice([5, 17, 40])), n_steps=int(g.integers(40, 121)),
+                                    spheres_at=0.1 * r, sphere_seed=11, scene_seed=99)
+        out.append(w)
+    return out
+
+
+def _serve(gm, ws, arena=1 << 28, slots=8, stagger=False, chunk=16):
+    srv = gm.Server(max_slots=slots, max_agents=64, max_steps=200, obs_cap=16384,
+                    arena_bytes=arena, chunk_steps=chunk, agents_per_item=8)
+    tickets, results, max_active, max_pending = [], {}, 0, 0
+    for i, w in enumerate(ws):
+        tickets.append(srv.submit(w["xyz"], w["T"], w["workspace"], w["agents"], w["params"]))
+        if stagger:
+            max_active = max(max_active, srv.tick())
+    for _ in range(10000):
+        if len(results) == len(tickets):
+            break
+        max_active = max(max_active, srv.tick())
+        max_pending = max(max_pending, srv.stats()["pending"])
+        for t in tickets:
+            if t not in results:
+                r = srv.poll(t)
+                if r is not None:
+                    results[t] = r
+    assert len(results) == len(tickets)
+    out = [results[t] for t in tickets]
+    for t in tickets:
+        srv.release(t)
+    return out, max_active, max_pending
+
+
+def test_mix_equals_alone_and_oracle(gm):
+    ws = _requests()
+    mixed, max_active, _ = _serve(gm, ws, stagger=True)
+    assert max_active >= 2, "requests must overlap on the device"
+    for w, r in zip(ws, mixed):
+        alone, _, _ = _serve(gm, [w])
+        a = alone[0]
+        assert a["best"] == r["best"]
+        assert np.array_equal(a["costs"], r["costs"])
+        assert np.array_equal(a["best_traj"], r["best_traj"])
+        ref_f = oracle.filter_cloud(w["xyz"], w["T"], w["workspace"])
+        assert r["n_obs"] == ref_f["n"]
+        obs = np.stack([ref_f["x"], ref_f["y"], ref_f["z"]])
+        ref = oracle.rollout(obs, ref_f["r_O"], w["agents"], w["params"])
+        c_ref = oracle.costs(ref, w["params"])
+        oi = oracle.select(c_ref)
+        assert r["best"] == oi or abs(c_ref[r["best"]] - c_ref[oi]) < 1e-6
+        assert np.allclose(r["costs"], c_ref, rtol=1e-4, atol=1e-4)
+        assert np.abs(r["best_traj"] - ref["traj"][r["best"]]).max() <= 1e-3
+        assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
+
+
+def test_admission_by_memory(gm):
+    ws = _requests(n=5, seed=8)
+    # each request needs ~1.1 MB; an arena of 2.4 MB holds two at once
+    mixed, _, max_pending = _serve(gm, ws, arena=2400 << 10, slots=8)
+    assert max_pending >= 1
+    for w, r in zip(ws, mixed):
+        alone, _, _ = _serve(gm, [w])
+        assert np.array_equal(alone[0]["best_traj"], r["best_traj"])
+
+
+def test_chunk_size_does_not_change_results(gm):
+    ws = _requests(n=3, seed=12)
+    a, _, _ = _serve(gm, ws, chunk=7)
+    b, _, _ = _serve(gm, ws, chunk=200)
+    for x, y in zip(a, b):
+        assert np.array_equal(x["best_traj"], y["best_traj"])
+        assert np.array_equal(x["costs"], y["costs"])
+
+
+def test_rejections(gm):
+    w = _requests(n=1)[0]
+    srv = gm.Server(max_slots=2, max_agents=8, max_steps=200, obs_cap=16384,
+                    arena_bytes=1 << 28, chunk_steps=16, agents_per_item=8)
+    with pytest.raises(gm.GmappError) as e:
+        big = dict(w["agents"])
+        big = {k: np.ascontiguousarray(np.repeat(v, 20, axis=-1)) for k, v in w["agents"].items()}
+        srv.submit(w["xyz"], w["T"], w["workspace"], big, w["params"])
+    assert e.value.status == 1
+    tiny = gm.Server(max_slots=2, max_agents=64, max_steps=200, obs_cap=16384,
+                     arena_bytes=1 << 20, chunk_steps=16, agents_per_item=8)
+    with pytest.raises(gm.GmappError) as e:
+        tiny.submit(w["xyz"], w["T"], w["workspace"], w["agents"], w["params"])
+    assert e.value.status == 2
