@@ -205,16 +205,25 @@ def run_ours(args, ws, rank, local):
     pinned = torch.from_numpy(np.stack(frames_np)).pin_memory()
     agents = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda()
               for k, v in base["agents"].items()}
-    obs = gm.Obstacles.empty(args.obs_cap)
     wsp = torch.empty(gm.filter_workspace_bytes(frames.shape[1], base["workspace"]),
                       dtype=torch.uint8, device="cuda")
+    obs_cap = args.obs_cap
+    if obs_cap <= 0:
+        # size S_W to the scene: the first frame's N_O plus 5% (sensor noise
+        # changes N_O by well under that from frame to frame)
+        probe = gm.filter_cloud(frames[0], base["T"], base["workspace"], cap=OBS_CAP, workspace=wsp)
+        obs_cap = (int(probe.count() * 1.05) + 63) // 64 * 64
+        del probe
+    obs = gm.Obstacles.empty(obs_cap)
     ro = gm.alloc_rollout_out(na, nk, want_traj=True, want_clear=False)
     sel = gm.score_and_select(gm.rollout_agents(gm.filter_cloud(frames[0], base["T"], base["workspace"],
                                                                  out=obs, workspace=wsp),
                                                 agents, prm, out=ro), prm)
     ctx.sync()
-    tuning = (tuple(int(v) for v in args.tuning.split(",")) if args.tuning
-              else gm.pick_tuning(args.obs_cap, na))
+    if args.tuning:
+        tuning = tuple(int(v) for v in args.tuning.split(","))
+    else:
+        tuning, _ = gm.autotune_rollout(obs, agents, prm, out=ro, candidates=16, probe_steps=100)
 
     # N_O per frame (for the interaction count), outside any timed region
     n_obs = []
@@ -330,6 +339,13 @@ def run_ours(args, ws, rank, local):
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
+        result["config"]["obs_cap"] = obs_cap
+        if not args.no_patterns:
+            del frames, pinned, wsp, obs, ro, sel
+            torch.cuda.empty_cache()
+            result["patterns"] = {"batched": bench_batched(gm, args),
+                                  "adjoint": bench_adjoint(gm, args),
+                                  "served": bench_served(gm, args)}
         print(json.dumps(result), flush=True)
     if ws > 1:
         dist.barrier()
@@ -339,6 +355,212 @@ def run_ours(args, ws, rank, local):
 
 # filter_cloud (zero, keys, bitmap sums, emit, count, publish) + rollout + select
 LAUNCHES_PER_STEP = 6 + 1 + 1
+
+
+def _events(torch, stream, fn, reps):
+    """Mean device time (s) of fn() over reps runs, CUDA events on stream."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def bench_batched(gm, args, reps=3):
+    """64 uneven sphere scenes: one batched launch sequence replayed from a
+    CUDA graph vs the plain per-query path (filter_cloud, rollout_agents,
+    score_and_select per query, one after another, same stream)."""
+    import torch
+    import synth
+    ws_list = synth.batch_workloads()
+    specs = [{"xyz": torch.from_numpy(w["xyz"]).cuda(), "T": w["T"], "ws": w["workspace"],
+              "agents": {k: torch.from_numpy(v).cuda() for k, v in w["agents"].items()},
+              "prm": w["params"], "obs_cap": 32768} for w in ws_list]
+    b = gm.Batch(specs, want_traj=False)
+    tune, _ = b.autotune()
+    s = torch.cuda.Stream()
+    b.launch_graph(s)
+    s.synchronize()
+    gm.sync()
+    n_obs = [r["obs"].count() for r in b.results]
+    inter = sum(int(w["agents"]["k_r"].size) * n * int(w["params"].n_steps)
+                for w, n in zip(ws_list, n_obs))
+    with torch.cuda.stream(s):
+        t_batch = _events(torch, s, lambda: b.launch_graph(s), reps)
+    gm.sync(s)
+    # plain per-query path
+    outs = []
+    for sp in specs:
+        na = int(sp["agents"]["k_r"].numel())
+        outs.append({"obs": gm.Obstacles.empty(32768),
+                     "ro": gm.alloc_rollout_out(na, int(sp["prm"].n_steps), want_traj=False,
+                                                want_clear=False),
+                     "ws": torch.empty(gm.filter_workspace_bytes(sp["xyz"].shape[0], sp["ws"]),
+                                       dtype=torch.uint8, device="cuda")})
+    cur = torch.cuda.current_stream()
+
+    def plain():
+        for sp, o in zip(specs, outs):
+            gm.filter_cloud(sp["xyz"], sp["T"], sp["ws"], out=o["obs"], workspace=o["ws"])
+            gm.rollout_agents(o["obs"], sp["agents"], sp["prm"], out=o["ro"])
+            gm.score_and_select(o["ro"], sp["prm"], best_traj=False)
+
+    plain()
+    gm.sync()
+    t_plain = _events(torch, cur, plain, reps)
+    gm.sync()
+    return {"workload": "64 sphere scenes: raw 5k-300k points, voxel 4-10 mm, 32-1024 agents, "
+                        "100-1000 steps", "interactions_per_batch": inter,
+            "batched": {"plans_per_s": 64 / t_batch, "interactions_per_s": inter / t_batch,
+                        "ms": 1e3 * t_batch, "tuning_agents_threads": list(tune),
+                        "launches": 8, "graph": True},
+            "plain": {"plans_per_s": 64 / t_plain, "interactions_per_s": inter / t_plain,
+                      "ms": 1e3 * t_plain, "launches": 64 * LAUNCHES_PER_STEP},
+            "speedup": t_plain / t_batch}
+
+
+def bench_adjoint(gm, args, reps=3):
+    """Differentiable rollout: 50,000 obstacles, 512 agents, 1000 steps,
+    checkpoints every 50; forward (with checkpoints) + adjoint vs the plain
+    forward rollout."""
+    import torch
+    import synth
+    w = synth.adjoint_workload()
+    prm = w["params"]
+    o = gm.Obstacles.from_points(torch.from_numpy(w["obstacles"]), w["r_O"])
+    ag = {k: torch.from_numpy(v).cuda() for k, v in w["agents"].items()}
+    na, nk, K = 512, int(prm.n_steps), int(prm.ckpt_every)
+    out = gm.alloc_rollout_out(na, nk, want_traj=False, want_clear=True)
+    out["ckpt"] = torch.empty((nk + K - 1) // K, 6, na, device="cuda")
+    plain_out = gm.alloc_rollout_out(na, nk, want_traj=False, want_clear=True)
+    cur = torch.cuda.current_stream()
+    ws = torch.empty(1 << 24, dtype=torch.uint8, device="cuda")
+    gm.rollout_agents(o, ag, prm, out=out)
+    gm.rollout_adjoint(o, ag, prm, out["ckpt"], workspace=ws)
+    gm.rollout_agents(o, ag, prm, out=plain_out)
+    gm.sync()
+    t_fwd = _events(torch, cur, lambda: gm.rollout_agents(o, ag, prm, out=out), reps)
+    t_adj = _events(torch, cur, lambda: gm.rollout_adjoint(o, ag, prm, out["ckpt"], workspace=ws),
+                    reps)
+    t_plain = _events(torch, cur, lambda: gm.rollout_agents(o, ag, prm, out=plain_out), reps)
+    gm.sync()
+    inter = na * w["obstacles"].shape[1] * nk
+    return {"workload": "50,000 obstacles, 512 agents, 1000 steps, K = 50",
+            "forward_ms": 1e3 * t_fwd, "adjoint_ms": 1e3 * t_adj, "plain_forward_ms": 1e3 * t_plain,
+            "forward_equivalent_interactions_per_s": inter / (t_fwd + t_adj),
+            "gradient_cost_over_plain_forward": (t_fwd + t_adj) / t_plain}
+
+
+def bench_served(gm, args):
+    """1 kHz open-loop request stream (200k-point tabletop frames with 4 moving
+    spheres, 1 cm voxels, N_a in {64, 256, 1024}, N_k = 300) through the
+    continuously batched server vs the same stream served one request at a
+    time through the plain per-query calls.  Frames come from a pool
+    rendered at evenly spaced times of the stream (each frame serves the
+    requests of its 1/pool-th of the stream)."""
+    import torch
+    import synth
+    dur = float(args.serve_seconds)
+    n_req = int(round(dur * 1000))
+    pool = max(4, int(round(dur * 5)))
+    arrivals, na_choice, _ = synth.serve_stream(n_requests=n_req)
+    frames, Ts = [], []
+    for i in range(pool):
+        w = synth.tabletop_workload(seed=1005 + i, n_agents=1, n_steps=1, n_points=200000,
+                                    voxel=0.01, spheres_at=float(arrivals[i * n_req // pool]),
+                                    sphere_seed=1005, scene_seed=1005)
+        frames.append(torch.from_numpy(w["xyz"]).pin_memory())
+        Ts.append(w["T"])
+        ws_grid, prm = w["workspace"], w["params"]
+    import dataclasses
+    prm = dataclasses.replace(prm, n_steps=300)
+    agents = {}
+    for na in (64, 256, 1024):
+        a = synth.agent_set(na, 77 + na, synth.workloads.TABLE_START, synth.workloads.TABLE_GOAL)
+        agents[na] = {k: torch.from_numpy(v).pin_memory() for k, v in a.items()}
+    frame_of = [min(pool - 1, r * pool // n_req) for r in range(n_req)]
+
+    def lat_stats(lat, t_span, inter):
+        lat = np.asarray(lat) * 1e3
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "plans_per_s": len(lat) / t_span, "interactions_per_s": inter / t_span}
+
+    # --- served: continuous batching
+    srv = gm.Server(max_slots=48, max_agents=1024, max_steps=300, obs_cap=32768,
+                    arena_bytes=2 << 30, chunk_steps=50, agents_per_item=8, threads=256)
+    # warm up (kernel loading, first admissions)
+    for r in range(4):
+        t = srv.submit(frames[0], Ts[0], ws_grid, agents[int(na_choice[r])], prm)
+        while srv.poll(t) is None:
+            srv.tick()
+        srv.release(t)
+    lat, inter, done = [], 0, 0
+    outstanding = {}
+    t0 = time.perf_counter()
+    nxt = 0
+    while done < n_req:
+        now = time.perf_counter() - t0
+        while nxt < n_req and arrivals[nxt] <= now:
+            na = int(na_choice[nxt])
+            tk = srv.submit(frames[frame_of[nxt]], Ts[frame_of[nxt]], ws_grid, agents[na], prm)
+            outstanding[tk] = (nxt, na)
+            nxt += 1
+        if not outstanding:
+            while time.perf_counter() - t0 < arrivals[nxt]:
+                pass
+            continue
+        srv.tick()
+        for tk in list(outstanding):
+            res = srv.poll(tk)
+            if res is None:
+                continue
+            r, na = outstanding.pop(tk)
+            lat.append(time.perf_counter() - t0 - arrivals[r])
+            inter += na * res["n_obs"] * prm.n_steps
+            srv.release(tk)
+            done += 1
+    t_span = time.perf_counter() - t0
+    served = lat_stats(lat, t_span, inter)
+    del srv
+
+    # --- plain: one request at a time through the per-query calls
+    cur = torch.cuda.current_stream()
+    dev_frame = torch.empty(200000, 3, device="cuda")
+    obs = gm.Obstacles.empty(32768)
+    wsb = torch.empty(gm.filter_workspace_bytes(200000, ws_grid), dtype=torch.uint8, device="cuda")
+    dev_agents = {na: {k: v.cuda() for k, v in a.items()} for na, a in agents.items()}
+    outs = {na: gm.alloc_rollout_out(na, 300, want_traj=True, want_clear=False) for na in agents}
+    host_best = torch.empty(1, dtype=torch.int32).pin_memory()
+    host_traj = torch.empty(301, 3).pin_memory()
+    for na in agents:  # warm up
+        gm.rollout_agents(gm.filter_cloud(dev_frame.copy_(frames[0]), Ts[0], ws_grid, out=obs,
+                                          workspace=wsb), dev_agents[na], prm, out=outs[na])
+    gm.sync()
+    lat, inter = [], 0
+    t0 = time.perf_counter()
+    for r in range(n_req):
+        while time.perf_counter() - t0 < arrivals[r]:
+            pass
+        na = int(na_choice[r])
+        dev_frame.copy_(frames[frame_of[r]], non_blocking=True)
+        gm.filter_cloud(dev_frame, Ts[frame_of[r]], ws_grid, out=obs, workspace=wsb)
+        gm.rollout_agents(obs, dev_agents[na], prm, out=outs[na])
+        sel = gm.score_and_select(outs[na], prm)
+        host_best.copy_(sel["best"], non_blocking=True)
+        host_traj.copy_(sel["best_traj"], non_blocking=True)
+        cur.synchronize()
+        lat.append(time.perf_counter() - t0 - arrivals[r])
+        inter += na * int(obs.count()) * 300
+    t_span = time.perf_counter() - t0
+    plain = lat_stats(lat, t_span, inter)
+    gm.sync()
+    return {"workload": f"{n_req} requests at 1 kHz: 200k-point tabletop frames + 4 moving spheres, "
+                        "1 cm voxels, N_a in {64, 256, 1024}, N_k = 300",
+            "offered_per_s": 1000.0, "served": served, "plain": plain,
+            "p99_speedup": plain["p99_ms"] / served["p99_ms"],
+            "frames_in_pool": pool}
 
 
 def cpu_baseline(base, xyz, n_agents_sample):
@@ -363,8 +585,12 @@ def main():
     ap.add_argument("--cpu-agents", type=int, default=64)
     ap.add_argument("--ref-agents", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--obs-cap", type=int, default=OBS_CAP,
-                    help="obstacle capacity of the S_W buffers (a multiple of 4)")
+    ap.add_argument("--obs-cap", type=int, default=0,
+                    help="obstacle capacity of the S_W buffers (multiple of 4; 0 = from the scene)")
+    ap.add_argument("--no-patterns", action="store_true",
+                    help="skip the batched / adjoint / served measurements")
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="length of the 1 kHz request stream of the served loop")
     ap.add_argument("--tuning", default="",
                     help="rollout launch shape 'cluster,agents,threads' (default: library choice)")
     args = ap.parse_args()
