@@ -57,8 +57,10 @@ bool resolve(gmapp_ctx *ctx, int64_t cap, int n_agents, const gmapp_tuning &t, b
     if (!s->fn) return false;
     s->shard_cap = shard_cap_for(cap, t.cluster);
     const int nw = t.threads / 32;
-    s->smem = (static_cast<size_t>(s->shard_cap) * 3 +
-               static_cast<size_t>(8) * t.cluster * nw * s->ag) * sizeof(float);
+    // shard + per-warp partials [2][NW][AG] + cluster slots [2][2][C][AG], (W, min d^2) each
+    s->smem = (static_cast<size_t>(s->shard_cap) * 3 + static_cast<size_t>(4) * nw * s->ag +
+               static_cast<size_t>(8) * t.cluster * s->ag) *
+              sizeof(float);
     return s->smem + static_smem(s->fn) <= static_cast<size_t>(ctx->max_smem_optin);
 }
 

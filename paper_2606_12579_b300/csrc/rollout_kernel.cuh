@@ -137,7 +137,7 @@ __device__ __forceinline__ void agent_step(float (&p)[3], float (&v)[3], const f
     g[0] = g[1] = g[2] = 0.0f;
     const float vv = fmaf(v[2], v[2], fmaf(v[1], v[1], v[0] * v[0]));
     if (vv >= 1e-30f) {
-        const float inv = 1.0f / sqrtf(vv);
+        const float inv = rsqrt_approx(vv);  // SFU; ~2^-22 relative error
         const float vc = fmaf(v[2], cc[2], fmaf(v[1], cc[1], v[0] * cc[0]));
 #pragma unroll
         for (int d = 0; d < 3; ++d) g[d] = (vv * cc[d] - v[d] * vc) * inv;
@@ -148,7 +148,8 @@ __device__ __forceinline__ void agent_step(float (&p)[3], float (&v)[3], const f
         const float F = k_a * (goal[d] - p[d]) - damping * v[d] + kf * g[d];
         v[d] = fmaf(h, F, v[d]);
     }
-    L = fmaf(dt, sqrtf(fmaf(v[2], v[2], fmaf(v[1], v[1], v[0] * v[0]))), L);
+    const float vn = fmaf(v[2], v[2], fmaf(v[1], v[1], v[0] * v[0]));
+    L = fmaf(dt, vn > 0.0f ? vn * rsqrt_approx(vn) : 0.0f, L);  // dt |v_k|
 #pragma unroll
     for (int d = 0; d < 3; ++d) p[d] = fmaf(dt, v[d], p[d]);
     m = INFINITY;
@@ -245,7 +246,8 @@ struct GlobalTail {
     int begin, end;
 };
 
-template <int AG, int NA, int OFF, int NM, int NT, bool CLEAR, bool TAIL = false>
+template <int AG, int NA, int OFF, int NM, int NT, bool CLEAR, bool TAIL = false,
+          bool SHIP = true>
 __device__ __forceinline__ void half_step(const float *sx, const float *sy, const float *sz,
                                           int cnt_pad, float eps, const f2 (&nR2)[AG],
                                           const float (&G2a)[AG], const float (&p)[3],
@@ -308,10 +310,58 @@ __device__ __forceinline__ void half_step(const float *sx, const float *sy, cons
         constexpr int REP = (32 >> log2i(P)) - 1;
         const int idx = transposed_index<P>(lane);
         if ((lane & REP) == 0 && idx < NA) {
-            const uint32_t local = smem_u32(recv_slot0 + 2 * (OFF + idx));
+            if constexpr (SHIP) {
+                const uint32_t local = smem_u32(recv_slot0 + 2 * (OFF + idx));
+                for (uint32_t r = 0; r < C; ++r) st_cluster_v2f32(map_smem(local, r), w, m);
+            } else {
+                *reinterpret_cast<float2 *>(recv_slot0 + 2 * (OFF + idx)) = make_float2(w, m);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// CTA-level reduction of a half's per-warp partials part[NW][AG] (float2),
+// one warp per agent (lane l loads warp l's partial, fixed shuffle tree),
+// then lane 0 stores the CTA's partial into slot[rank][a] of every CTA of
+// the cluster.  Call after a barrier that covers all partial stores.
+template <int AG, int NA, int OFF, int NW, bool CLEAR>
+__device__ __forceinline__ void cta_ship(const float *part, float *slot, uint32_t C,
+                                         uint32_t rank, int warp, int lane) {
+    for (int a = warp; a < NA; a += NW) {
+        float w = 0.0f, m = INFINITY;
+        if (lane < NW) {
+            const float2 t = *reinterpret_cast<const float2 *>(part + 2 * (lane * AG + OFF + a));
+            w = t.x;
+            m = t.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            w += __shfl_xor_sync(0xffffffffu, w, o);
+            if (CLEAR) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        }
+        if (lane == 0) {
+            const uint32_t local = smem_u32(slot + 2 * (rank * AG + OFF + a));
             for (uint32_t r = 0; r < C; ++r) st_cluster_v2f32(map_smem(local, r), w, m);
         }
     }
+}
+
+// Sum (min) of the C per-CTA partials of agent `lane` in rank order.
+template <int AG, bool CLEAR>
+__device__ __forceinline__ void cluster_combine(const float *slot, uint32_t C, int lane, float &W,
+                                                float &md2) {
+    float w = 0.0f, m = INFINITY;
+    for (uint32_t r = 0; r < C; ++r) {
+        const float2 t = *reinterpret_cast<const float2 *>(slot + 2 * (r * AG + lane));
+        w += t.x;
+        if (CLEAR) m = fminf(m, t.y);
+    }
+    W = w;
+    md2 = m;
 }
 
 // Sum of the C x NW partials of each agent of a half, in a fixed order;
@@ -362,8 +412,10 @@ __global__ void __launch_bounds__(NT, 1) k_rollout(const RolloutArgs A) {
     constexpr int NW = NT / 32;
     constexpr int H0 = (AG + 1) / 2;  // agents [0, H0) form half 0, [H0, AG) half 1
     constexpr int H1 = AG - H0;
-    constexpr int NM0 = NM < H0 ? NM : H0;  // SFU agents inside each half
-    constexpr int NM1 = NM - NM0;
+    // SFU agents split evenly over the halves (each half's pair loop then
+    // keeps the same SFU/FMA balance)
+    constexpr int NM0 = (NM + 1) / 2 < H0 ? (NM + 1) / 2 : H0;
+    constexpr int NM1 = NM - NM0 < H1 ? NM - NM0 : H1;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar;
 
@@ -385,11 +437,14 @@ __global__ void __launch_bounds__(NT, 1) k_rollout(const RolloutArgs A) {
     const int32_t start = static_cast<int32_t>(rank) * shard_len;
     int32_t cnt = min(shard_len, max(0, n_obs - start));
     float *sx = smem, *sy = smem + A.shard_cap, *sz = smem + 2 * A.shard_cap;
-    // receive slots: [half][parity][rank][warp][AG] x (W, min |d|^2)
-    float *recv = smem + 3 * A.shard_cap;
-    const int nq = static_cast<int>(C) * NW;
-    const int par_stride = 2 * nq * AG;  // floats per (half, parity)
-    auto slot = [&](int h, int par) { return recv + (h * 2 + par) * par_stride; };
+    // per-warp partials of this CTA: [half][NW][AG] x (W, min |d|^2)
+    float *partbuf = smem + 3 * A.shard_cap;
+    // per-CTA partials received from the cluster: [half][parity][rank][AG]
+    float *recv = partbuf + 4 * NW * AG;
+    auto part = [&](int h) { return partbuf + h * (2 * NW * AG); };
+    auto slot = [&](int h, int par) {
+        return recv + (h * 2 + par) * (2 * static_cast<int>(C) * AG);
+    };
 
     if (tid == 0) {
         mbar_init(&bar, 1);
@@ -493,30 +548,38 @@ __global__ void __launch_bounds__(NT, 1) k_rollout(const RolloutArgs A) {
     //   prologue: half0(0) -> arrive
     //   step k:   half1(k) -> wait -> integrate half0(k) -> arrive
     //             half0(k+1) -> wait -> integrate half1(k) -> arrive
-    const int rk = static_cast<int>(rank);
-    half_step<AG, H0, 0, NM0, NT, CLEAR>(sx, sy, sz, cnt_pad, eps, nR2, G2a, p,
-                                         slot(0, 0) + 2 * ((rk * NW + warp) * AG), C, lane);
+    //   each half: per-warp partials -> CTA barrier -> one warp per agent
+    //   reduces the CTA's partial and stores it into every cluster CTA
+    auto compute_half0 = [&](int par) {
+        half_step<AG, H0, 0, NM0, NT, CLEAR, false, false>(sx, sy, sz, cnt_pad, eps, nR2, G2a, p,
+                                                           part(0) + 2 * (warp * AG), C, lane);
+        named_barrier(1, NT);
+        cta_ship<AG, H0, 0, NW, CLEAR>(part(0), slot(0, par), C, rank, warp, lane);
+    };
+    auto compute_half1 = [&](int par) {
+        half_step<AG, H1, H0, NM1, NT, CLEAR, false, false>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
+                                                            p, part(1) + 2 * (warp * AG), C, lane);
+        named_barrier(2, NT);
+        cta_ship<AG, H1, H0, NW, CLEAR>(part(1), slot(1, par), C, rank, warp, lane);
+    };
+    compute_half0(0);
     cluster_arrive();
     for (int k = 0; k < A.n_steps; ++k) {
         const int par = k & 1;
-        half_step<AG, H1, H0, NM1, NT, CLEAR>(sx, sy, sz, cnt_pad, eps, nR2, G2a, p,
-                                              slot(1, par) + 2 * ((rk * NW + warp) * AG), C, lane);
+        compute_half1(par);
         cluster_wait();
-        {
-            float W = 0.0f, md2 = INFINITY;
-            half_combine<AG, H0, 0, CLEAR>(slot(0, par), nq, lane, W, md2);
-            if (lane < H0 && lane < na) integrate(k, W, md2);
+        if (lane < H0 && lane < na) {
+            float W, md2;
+            cluster_combine<AG, CLEAR>(slot(0, par), C, lane, W, md2);
+            integrate(k, W, md2);
         }
         cluster_arrive();
-        if (k + 1 < A.n_steps)
-            half_step<AG, H0, 0, NM0, NT, CLEAR>(sx, sy, sz, cnt_pad, eps, nR2, G2a, p,
-                                                 slot(0, par ^ 1) + 2 * ((rk * NW + warp) * AG), C,
-                                                 lane);
+        if (k + 1 < A.n_steps) compute_half0(par ^ 1);
         cluster_wait();
-        {
-            float W = 0.0f, md2 = INFINITY;
-            half_combine<AG, H1, H0, CLEAR>(slot(1, par), nq, lane, W, md2);
-            if (lane >= H0 && lane < na) integrate(k, W, md2);
+        if (lane >= H0 && lane < na) {
+            float W, md2;
+            cluster_combine<AG, CLEAR>(slot(1, par), C, lane, W, md2);
+            integrate(k, W, md2);
         }
         if (k + 1 < A.n_steps) cluster_arrive();
     }
