@@ -49,6 +49,22 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_over_ranks(times, counts, ws, device):
+    """Whole-job totals of a replicas-only run: every time is the maximum
+    over ranks (the job ends with its slowest rank) and every count of work
+    is the sum over ranks.  A single process returns its own values."""
+    times, counts = [float(v) for v in times], [float(v) for v in counts]
+    if ws <= 1:
+        return times, counts
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(times, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor(counts, dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return t.tolist(), c.tolist()
+
+
 def _measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -294,16 +310,9 @@ def run_ours(args, ws, rank, local):
             e2e_inter += na * n_obs[f] * nk
     ctx.sync()
 
-    # max over ranks
-    t_job = t_dev
-    e2e_time = sum(lat)
-    if ws > 1:
-        t = torch.tensor([t_dev, e2e_time], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_job, e2e_time = float(t[0]), float(t[1])
-        it = torch.tensor([inter, e2e_inter], dtype=torch.float64, device="cuda")
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-        inter, e2e_inter = float(it[0]), float(it[1])
+    # job time = max over ranks, work = sum over ranks
+    (t_job, e2e_time), (inter, e2e_inter) = reduce_over_ranks(
+        [t_dev, sum(lat)], [inter, e2e_inter], ws, "cuda")
 
     result = None
     if rank == 0:
