@@ -263,8 +263,20 @@ gmapp_status rollout_adjoint(gmapp_ctx *ctx, const gmapp_obstacles *obs,
 /* Launch shape of the rollout kernel (see rollout_agents_tuned). */
 typedef struct {
     int32_t cluster;        /* CTAs per cluster, each holding 1/cluster of S_W: 1..16 */
-    int32_t agents_per_cta; /* agents processed together by one cluster: 1..32 */
-    int32_t threads;        /* threads per CTA: 128, 256, 384 or 512 */
+    int32_t agents_per_cta; /* agents processed together by one cluster: 1..16 */
+    int32_t threads;        /* threads of a CTA that evaluate obstacle pairs: 128, 256,
+                               384 or 512 (each CTA has one more warp, which
+                               exchanges partial sums and integrates) */
+    int32_t exchange;       /* how the CTAs of a group combine their partial sums
+                               each step: 0 = a thread-block cluster over
+                               distributed shared memory; 1 = a cooperative
+                               grid (all CTAs co-resident, groups * cluster <=
+                               SM count) over tagged words in global memory,
+                               which is not bound to the GPU's cluster
+                               placement.  Exchange-1 launches of one context
+                               use its exchange slots one at a time: the library
+                               orders them across streams, except inside CUDA
+                               graph capture, where the caller must. */
 } gmapp_tuning;
 
 /* Same as rollout_agents with an explicit launch shape (used by the

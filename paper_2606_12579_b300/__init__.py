@@ -264,14 +264,15 @@ def pick_tuning(obs_cap: int, n_agents: int) -> tuple:
     t = _abi.Tuning()
     check(_abi.load().gmapp_pick_tuning(context().handle, int(obs_cap), int(n_agents),
                                         C.byref(t)), "gmapp_pick_tuning")
-    return (t.cluster, t.agents_per_cta, t.threads)
+    return (t.cluster, t.agents_per_cta, t.threads, t.exchange)
 
 
 def autotune_rollout(obs: Obstacles, agents: dict, prm, out: dict | None = None,
                      candidates: int = 12, probe_steps: int = 60, stream=None):
     """Measure up to ``candidates`` launch shapes on these inputs and cache
     the fastest for later rollouts of the same sizes; returns
-    ((cluster, agents_per_cta, threads), ms scaled to the full horizon)."""
+    ((cluster, agents_per_cta, threads, exchange), ms scaled to the full
+    horizon)."""
     ctx = context()
     na = int(agents["k_r"].numel())
     if out is None:
@@ -283,7 +284,7 @@ def autotune_rollout(obs: Obstacles, agents: dict, prm, out: dict | None = None,
                                              C.byref(os_), int(candidates), int(probe_steps),
                                              C.byref(t), C.byref(ms), _stream(stream)),
           "gmapp_autotune_rollout")
-    return (t.cluster, t.agents_per_cta, t.threads), float(ms.value)
+    return (t.cluster, t.agents_per_cta, t.threads, t.exchange), float(ms.value)
 
 
 def rollout_agents(obs: Obstacles, agents: dict, prm, out: dict | None = None,
@@ -294,7 +295,8 @@ def rollout_agents(obs: Obstacles, agents: dict, prm, out: dict | None = None,
     ``agents``: dict of contiguous float32 CUDA tensors p0, v0, c [3, N_a] and
     k_r, k_a, r_d, r_a [N_a].  ``prm``: object with goal, dt, n_steps,
     damping, inv_mass, rho, eps, vel_half, clear_margin, clear_beta.
-    ``tuning``: optional (cluster, agents_per_cta, threads)."""
+    ``tuning``: optional (cluster, agents_per_cta, threads[, exchange]);
+    exchange 0 = cluster/DSMEM (default), 1 = cooperative grid."""
     ctx = context()
     na = int(agents["k_r"].numel())
     if out is None:

@@ -51,7 +51,8 @@ class AdjointOut(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("cluster", C.c_int32), ("agents_per_cta", C.c_int32), ("threads", C.c_int32)]
+    _fields_ = [("cluster", C.c_int32), ("agents_per_cta", C.c_int32), ("threads", C.c_int32),
+                ("exchange", C.c_int32)]
 
 
 class CostWeights(C.Structure):

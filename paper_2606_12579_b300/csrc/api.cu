@@ -47,8 +47,18 @@ extern "C" gmapp_status gmapp_create(gmapp_ctx **out, int device) {
                                    device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(uint32_t));
+    const size_t xbytes = xbuf_bytes(c->sm_count);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_xbuf, xbytes);
+    if (e == cudaSuccess) e = cudaMemset(c->d_xbuf, 0, xbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_xctl, 2 * sizeof(uint32_t));
+    // epoch 1, counter 0: all-zero slots (epoch 0) never match a tag
+    const uint32_t ctl0[2] = {1u, 0u};
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_xctl, ctl0, sizeof(ctl0), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->x_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         if (c->d_err) cudaFree(c->d_err);
+        if (c->d_xbuf) cudaFree(c->d_xbuf);
+        if (c->d_xctl) cudaFree(c->d_xctl);
         delete c;
         return cuda_fail(e, "gmapp_create");
     }
@@ -59,6 +69,9 @@ extern "C" gmapp_status gmapp_create(gmapp_ctx **out, int device) {
 extern "C" void gmapp_destroy(gmapp_ctx *ctx) {
     if (!ctx) return;
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_xbuf) cudaFree(ctx->d_xbuf);
+    if (ctx->d_xctl) cudaFree(ctx->d_xctl);
+    if (ctx->x_done) cudaEventDestroy(ctx->x_done);
     delete ctx;
 }
 

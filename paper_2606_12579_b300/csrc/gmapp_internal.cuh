@@ -13,6 +13,13 @@ struct gmapp_ctx {
     int sm_count;
     int max_smem_optin;   // bytes of dynamic shared memory one CTA may opt into
     uint32_t *d_err;      // device error word (GMAPP_DEVERR_* bits)
+    // exchange slots of the grid-exchange rollout (one launch at a time):
+    // [sm_count][2 halves][2 parities][kMaxAgents][2] tagged words, and the
+    // launch epoch / finished-CTA counter
+    uint64_t *d_xbuf;
+    uint32_t *d_xctl;
+    cudaEvent_t x_done;   // completion of the last grid-exchange launch
+    bool x_pending;       // x_done has been recorded
 };
 
 namespace gmapp {
@@ -29,6 +36,8 @@ gmapp_status cuda_fail(cudaError_t e, const char *what);
 
 // Bounded-wait limit for every device-side spin (iterations of try_wait).
 constexpr uint32_t kSpinLimit = 1u << 24;
+// Bounded polls of a word in global memory (each an L2 round trip).
+constexpr uint32_t kPollLimit = 1u << 22;
 
 // ---------------------------------------------------------------------------
 // Inline-PTX helpers: shared-memory addresses, mbarriers, 1-D bulk copies
@@ -71,6 +80,63 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
         if (done) return true;
     }
     return false;
+}
+
+// As mbar_wait, with acquire at cluster scope: data that other CTAs of the
+// cluster delivered with st_async_v2f32 on this barrier is visible after it.
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity) {
+    uint32_t addr = smem_u32(bar);
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Asynchronous 8-byte store into the shared memory of a cluster CTA; its
+// byte count completes on that CTA's mbarrier `remote_bar` (both addresses
+// from map_smem).
+__device__ __forceinline__ void st_async_v2f32(uint32_t remote_addr, float a, float b,
+                                               uint32_t remote_bar) {
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(
+            remote_addr),
+        "f"(a), "f"(b), "r"(remote_bar)
+        : "memory");
+}
+
+// 64-bit relaxed accesses at GPU scope (single-copy atomic, never served
+// from a stale L1 line): the grid exchange packs a 32-bit tag and a 32-bit
+// payload into one word, so no other ordering is needed.
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Named CTA barriers for producer/consumer hand-offs between warps: the
+// producers arrive (no wait), the consumers sync; n counts all threads of
+// both sides (a multiple of 32, whole warps).
+__device__ __forceinline__ void named_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int n) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
 // 1-D bulk copy global -> this CTA's shared memory, completing on `bar`.
@@ -144,5 +210,11 @@ __device__ __forceinline__ void raise_error(uint32_t *err, uint32_t bits) {
 }
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bytes of the grid-exchange slots for up to `ctas` CTAs: per CTA
+// [2 halves][2 parities][16 agents][2 words (W, min d^2)].
+inline size_t xbuf_bytes(int ctas) {
+    return static_cast<size_t>(ctas) * 2 * 2 * 16 * 2 * sizeof(uint64_t);
+}
 
 }  // namespace gmapp

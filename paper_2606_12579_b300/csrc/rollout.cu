@@ -16,8 +16,9 @@ namespace {
 
 // A launch shape resolved for concrete sizes.
 struct Shape {
-    int cluster;   // C: CTAs per cluster = obstacle shards
-    int groups;    // G: clusters = agent groups
+    int cluster;   // C: CTAs per group (a cluster, or a grid-exchange group) = obstacle shards
+    int groups;    // G: agent groups
+    bool grid;     // exchange through global memory in a cooperative grid
     int ag;        // agents per group held in registers (max over groups)
     int threads;   // NT
     bool clear;    // clearance reduction compiled in
@@ -31,7 +32,8 @@ int32_t shard_cap_for(int64_t cap, int cluster) {
     return static_cast<int32_t>((s + 3) & ~int64_t(3));
 }
 
-RolloutKernel pick_kernel(int ag, int nt, bool clear) {
+RolloutKernel pick_kernel(int ag, int nt, bool clear, bool grid) {
+    if (grid) return clear ? rollout_kernel_grid_clear(ag, nt) : rollout_kernel_grid_noclear(ag, nt);
     return clear ? rollout_kernel_clear(ag, nt) : rollout_kernel_noclear(ag, nt);
 }
 
@@ -46,20 +48,24 @@ size_t static_smem(RolloutKernel fn) {
 bool resolve(gmapp_ctx *ctx, int64_t cap, int n_agents, const gmapp_tuning &t, bool clear,
              Shape *s) {
     if (t.cluster < 1 || t.cluster > kMaxCluster || t.agents_per_cta < 1 ||
-        t.agents_per_cta > kMaxAgents)
+        t.agents_per_cta > kMaxAgents || t.exchange < 0 || t.exchange > 1)
         return false;
     s->cluster = t.cluster;
+    s->grid = t.exchange == 1;
     s->threads = t.threads;
     s->groups = (n_agents + t.agents_per_cta - 1) / t.agents_per_cta;
     s->ag = (n_agents + s->groups - 1) / s->groups;
     s->clear = clear;
-    s->fn = pick_kernel(s->ag, t.threads, clear);
+    s->fn = pick_kernel(s->ag, t.threads, clear, s->grid);
     if (!s->fn) return false;
+    // grid exchange: one slot set per CTA, at most one CTA per SM
+    if (s->grid && s->groups * s->cluster > ctx->sm_count) return false;
     s->shard_cap = shard_cap_for(cap, t.cluster);
     const int nw = t.threads / 32;
-    // shard + per-warp partials [2][NW][AG] + cluster slots [2][2][C][AG], (W, min d^2) each
+    // shard + per-warp partials [2][NW][AG] + cluster slots [2][2][C][AG], (W, min d^2)
+    // each, + agent positions [3][AG] (4 AG floats keep the 16-byte alignment)
     s->smem = (static_cast<size_t>(s->shard_cap) * 3 + static_cast<size_t>(4) * nw * s->ag +
-               static_cast<size_t>(8) * t.cluster * s->ag) *
+               static_cast<size_t>(8) * t.cluster * s->ag + static_cast<size_t>(4) * s->ag) *
               sizeof(float);
     return s->smem + static_smem(s->fn) <= static_cast<size_t>(ctx->max_smem_optin);
 }
@@ -77,24 +83,39 @@ gmapp_status prepare(const Shape &s) {
 cudaLaunchConfig_t config(const Shape &s, cudaLaunchAttribute *attr, gmapp_stream stream) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(s.groups * s.cluster, 1, 1);
-    cfg.blockDim = dim3(s.threads, 1, 1);
+    cfg.blockDim = dim3(s.threads + 32, 1, 1);  // compute warps + the exchange warp
     cfg.dynamicSmemBytes = s.smem;
     cfg.stream = stream;
-    attr->id = cudaLaunchAttributeClusterDimension;
-    attr->val.clusterDim.x = s.cluster;
-    attr->val.clusterDim.y = 1;
-    attr->val.clusterDim.z = 1;
+    if (s.grid) {
+        // every CTA co-resident: groups poll one another
+        attr->id = cudaLaunchAttributeCooperative;
+        attr->val.cooperative = 1;
+    } else {
+        attr->id = cudaLaunchAttributeClusterDimension;
+        attr->val.clusterDim.x = s.cluster;
+        attr->val.clusterDim.y = 1;
+        attr->val.clusterDim.z = 1;
+    }
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cfg;
 }
 
-// Co-resident clusters of this shape (0 when it cannot be placed).
-int max_active_clusters(const Shape &s) {
+// Co-resident groups of this shape (0 when it cannot be placed).
+int max_active_clusters(gmapp_ctx *ctx, const Shape &s) {
     if (prepare(s) != GMAPP_OK) return 0;
+    int m = 0;
+    if (s.grid) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(s.fn),
+                                                          s.threads + 32, s.smem) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return std::min(per_sm, 1) * ctx->sm_count / s.cluster;
+    }
     cudaLaunchAttribute attr;
     cudaLaunchConfig_t cfg = config(s, &attr, nullptr);
-    int m = 0;
     if (cudaOccupancyMaxActiveClusters(&m, reinterpret_cast<const void *>(s.fn), &cfg) !=
         cudaSuccess) {
         cudaGetLastError();
@@ -111,8 +132,12 @@ double model_cost(const Shape &s, int m, int64_t n_obs_est) {
     const double shard = static_cast<double>((n_obs_est + s.cluster - 1) / s.cluster);
     const double rate = std::min(10.0, 2.0 + 1.5 * s.ag);
     const double sync = 1200.0 + 40.0 * s.cluster + 3.0 * s.cluster * (s.threads / 32) * s.ag;
+    // a grid-exchange launch must fit in one wave (its groups poll one
+    // another); its exchange runs through L2 and costs more latency
+    if (s.grid && s.groups > m) return 1e300;
+    const double xsync = s.grid ? 1.5 * sync : sync;
     const int waves = (s.groups + m - 1) / m;
-    return waves * (s.ag * std::max(shard, 64.0) / rate + sync);
+    return waves * (s.ag * std::max(shard, 64.0) / rate + xsync);
 }
 
 std::mutex g_tune_mu;
@@ -134,25 +159,26 @@ gmapp_status pick_tuning_impl(gmapp_ctx *ctx, int64_t cap, int32_t n_agents, boo
     double best_cost = 1e300;
     bool found = false;
     const int threads_list[] = {256, 384, 512};
-    for (int C = 1; C <= kMaxCluster; ++C) {
-        for (int nt : threads_list) {
-            int last_groups = -1;
-            for (int a = 1; a <= kMaxAgents; ++a) {
-                Shape s;
-                if (!resolve(ctx, cap, n_agents, gmapp_tuning{C, a, nt}, clear, &s)) continue;
-                if (s.groups == last_groups) continue;
-                last_groups = s.groups;
-                const int m = max_active_clusters(s);
-                if (m <= 0) continue;
-                const double cost = model_cost(s, m, cap);
-                if (cost < best_cost) {
-                    best_cost = cost;
-                    *best = gmapp_tuning{C, s.ag, nt};
-                    found = true;
+    for (int x = 0; x <= 1; ++x)
+        for (int C = 1; C <= kMaxCluster; ++C) {
+            for (int nt : threads_list) {
+                int last_groups = -1;
+                for (int a = 1; a <= kMaxAgents; ++a) {
+                    Shape s;
+                    if (!resolve(ctx, cap, n_agents, gmapp_tuning{C, a, nt, x}, clear, &s)) continue;
+                    if (s.groups == last_groups) continue;
+                    last_groups = s.groups;
+                    const int m = max_active_clusters(ctx, s);
+                    if (m <= 0) continue;
+                    const double cost = model_cost(s, m, cap);
+                    if (cost < best_cost) {
+                        best_cost = cost;
+                        *best = gmapp_tuning{C, s.ag, nt, x};
+                        found = true;
+                    }
                 }
             }
         }
-    }
     if (!found) {
         set_error("rollout_agents: no launch shape fits an obstacle capacity of %lld",
                   (long long)cap);
@@ -218,9 +244,9 @@ gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agen
                     const gmapp_tuning &t, gmapp_stream stream) {
     Shape s;
     if (!resolve(ctx, obs->cap, ag->n, t, wants_clear(out), &s)) {
-        set_error("rollout_agents: launch shape (cluster %d, agents %d, threads %d) does not fit "
-                  "an obstacle capacity of %lld",
-                  t.cluster, t.agents_per_cta, t.threads, (long long)obs->cap);
+        set_error("rollout_agents: launch shape (cluster %d, agents %d, threads %d, exchange %d) "
+                  "does not fit an obstacle capacity of %lld",
+                  t.cluster, t.agents_per_cta, t.threads, t.exchange, (long long)obs->cap);
         return GMAPP_ERR_INVALID_ARG;
     }
     gmapp_status st = prepare(s);
@@ -263,11 +289,28 @@ gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agen
     A.ckpt = out->ckpt;
     A.shard_cap = s.shard_cap;
     A.n_groups = s.groups;
-    A.recv_floats = 2 * s.cluster * (s.threads / 32) * s.ag;
+    A.group_ctas = s.cluster;
+    A.xbuf = ctx->d_xbuf;
+    A.xctl = ctx->d_xctl;
     A.err = ctx->d_err;
     cudaLaunchAttribute attr;
     cudaLaunchConfig_t cfg = config(s, &attr, stream);
+    if (!s.grid) {
+        GMAPP_CHECK_CUDA(cudaLaunchKernelEx(&cfg, s.fn, A));
+        return GMAPP_OK;
+    }
+    // The grid exchange uses the context's slots and epoch: launches on
+    // different streams are ordered after one another (outside stream
+    // capture; captured launches are ordered by the caller's graph).
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    GMAPP_CHECK_CUDA(cudaStreamIsCapturing(stream, &cap_status));
+    const bool capturing = cap_status != cudaStreamCaptureStatusNone;
+    if (!capturing && ctx->x_pending) GMAPP_CHECK_CUDA(cudaStreamWaitEvent(stream, ctx->x_done, 0));
     GMAPP_CHECK_CUDA(cudaLaunchKernelEx(&cfg, s.fn, A));
+    if (!capturing) {
+        GMAPP_CHECK_CUDA(cudaEventRecord(ctx->x_done, stream));
+        ctx->x_pending = true;
+    }
     return GMAPP_OK;
 }
 
@@ -296,19 +339,22 @@ extern "C" gmapp_status gmapp_autotune_rollout(gmapp_ctx *ctx, const gmapp_obsta
     };
     std::vector<Cand> cands;
     const int threads_list[] = {256, 384, 512};
-    for (int C = 1; C <= kMaxCluster; ++C)
-        for (int nt : threads_list) {
-            int last_groups = -1;
-            for (int a = 1; a <= kMaxAgents; ++a) {
-                Shape s;
-                if (!resolve(ctx, obs->cap, agents->n, gmapp_tuning{C, a, nt}, clear, &s)) continue;
-                if (s.groups == last_groups) continue;
-                last_groups = s.groups;
-                const int m = max_active_clusters(s);
-                if (m <= 0) continue;
-                cands.push_back({model_cost(s, m, obs->cap), gmapp_tuning{C, s.ag, nt}});
+    for (int x = 0; x <= 1; ++x)
+        for (int C = 1; C <= kMaxCluster; ++C)
+            for (int nt : threads_list) {
+                int last_groups = -1;
+                for (int a = 1; a <= kMaxAgents; ++a) {
+                    Shape s;
+                    if (!resolve(ctx, obs->cap, agents->n, gmapp_tuning{C, a, nt, x}, clear, &s))
+                        continue;
+                    if (s.groups == last_groups) continue;
+                    last_groups = s.groups;
+                    const int m = max_active_clusters(ctx, s);
+                    if (m <= 0) continue;
+                    const double cost = model_cost(s, m, obs->cap);
+                    if (cost < 1e299) cands.push_back({cost, gmapp_tuning{C, s.ag, nt, x}});
+                }
             }
-        }
     if (cands.empty()) {
         set_error("gmapp_autotune_rollout: no launch shape fits an obstacle capacity of %lld",
                   (long long)obs->cap);

@@ -11,21 +11,26 @@
 //   lanes of work): differences, |d|^2, s = |d| - R;
 //   |d|^-1/2 on the SFU (rsqrt), clamp max(s, eps), detection gate as a
 //   0/1 mask from |d|^2 <= (r_d + R)^2 folded into the accumulation FMA;
-//   1/s on the SFU for the first NM agents and by a magic-constant seed plus
+//   1/s on the SFU for NM of the agents and by a magic-constant seed plus
 //   three Newton-Raphson steps on the FMA pipe for the others (Blinn,
 //   "Floating-point tricks", IEEE CG&A 1997; the iteration runs on -1/s so it
 //   needs no negation), which balances the SFU against the FMA pipe.
 //
-// The agents of a group are split into two halves that are kept one phase
-// apart: each warp reduces a half's partial sums with a transposed shuffle
-// butterfly and stores them, over DSMEM, into the double-buffered receive
-// slots of every CTA of the cluster, then arrives on the cluster barrier and
-// computes the other half while the first is in flight; after the wait,
-// every warp sums the C x NW partials of the half in a fixed order (lanes
-// in parallel) and integrates those agents itself (lane a = agent a), so
-// results are bit-identical in every warp and CTA and no other barrier is
-// needed.  Nothing inside the N_k loop touches global memory except the
-// optional trajectory/trace stores.
+// Warp specialisation: the CTA's NT compute warps only evaluate pairs; one
+// more warp (the exchange warp) owns the agents' state.  The agents of a
+// group are split into two halves kept one phase apart.  After a half, each
+// compute warp reduces its partial sums with a transposed shuffle butterfly,
+// stores them to shared memory and arrives on a named barrier, then goes on
+// with the other half.  Meanwhile the exchange warp sums the NW warp
+// partials in warp order, sends the CTA partial into the double-buffered
+// receive slots of every CTA of the cluster with st.async (each store
+// completes bytes on the receiver's mbarrier), waits for the C partials,
+// sums them in rank order, integrates the half's agents (lane a = agent a)
+// and publishes their positions to shared memory behind a second named
+// barrier.  The exchange of one half is thus hidden behind the other half's
+// pair loop; every CTA integrates the same sums in the same order, so all
+// copies of an agent's state are bit-identical.  Nothing inside the N_k loop
+// touches global memory except the optional trajectory/trace stores.
 #pragma once
 
 #include <math.h>
@@ -52,8 +57,10 @@ struct RolloutArgs {
     float *traj, *p_final, *v_final, *path_len, *clear_pen, *min_clear, *w_trace, *m_trace,
         *f_trace, *ckpt;
     int32_t shard_cap;   // obstacles one CTA can hold (multiple of 4)
-    int32_t n_groups;    // clusters in the grid
-    int32_t recv_floats; // size of one parity of the receive buffer
+    int32_t n_groups;    // agent groups (clusters, or CTA groups with the grid exchange)
+    int32_t group_ctas;  // grid exchange: CTAs per group (C)
+    uint64_t *xbuf;      // grid exchange: tagged slots [G][2][2][C][AG][2]
+    uint32_t *xctl;      // grid exchange: launch epoch, finished-CTA counter
     uint32_t *err;
 };
 
@@ -212,6 +219,11 @@ __device__ __forceinline__ int transposed_index(int lane) {
 // stored into every cluster CTA's receive slots recv[h][par][rank][warp][a].
 // The Alg. 1 terms of one obstacle pair (two f32x2 lanes) for NA agents,
 // accumulated into acc (and the squared-distance minimum mn with CLEAR).
+// Agent a of NA uses the SFU reciprocal when it is one of NM agents spread
+// evenly over the NA (Bresenham pattern), so SFU and FMA work interleave in
+// the unrolled pair loop.
+constexpr bool sfu_agent(int a, int NM, int NA) { return ((a + 1) * NM) / NA > (a * NM) / NA; }
+
 template <int AG, int NA, int OFF, int NM, bool CLEAR>
 __device__ __forceinline__ void pair_terms(f2 ox, f2 oy, f2 oz, const f2 (&X)[NA],
                                            const f2 (&Y)[NA], const f2 (&Z)[NA], f2 (&acc)[NA],
@@ -226,7 +238,7 @@ __device__ __forceinline__ void pair_terms(f2 ox, f2 oy, f2 oz, const f2 (&X)[NA
         const f2 r = pk(rsqrt_approx(d2l), rsqrt_approx(d2h));
         const f2 s = fma2(d2, r, nR2[OFF + a]);  // |d| - R (NaN when d = 0)
         const float sl = fmaxf(lo_of(s), eps), sh = fmaxf(hi_of(s), eps);
-        if (a < NM) {
+        if (sfu_agent(a, NM, NA)) {
             acc[a] = fma2(mask, pk(rcp_approx(sl), rcp_approx(sh)), acc[a]);
         } else {
             const f2 s2 = pk(sl, sh);
@@ -246,13 +258,16 @@ struct GlobalTail {
     int begin, end;
 };
 
+// Agent positions come from lane OFF+a of the warp (p), or with POS from
+// shared memory pos[3][AG] (SoA).
 template <int AG, int NA, int OFF, int NM, int NT, bool CLEAR, bool TAIL = false,
-          bool SHIP = true>
+          bool SHIP = true, bool POS = false>
 __device__ __forceinline__ void half_step(const float *sx, const float *sy, const float *sz,
                                           int cnt_pad, float eps, const f2 (&nR2)[AG],
                                           const float (&G2a)[AG], const float (&p)[3],
                                           float *recv_slot0, uint32_t C, int lane,
-                                          GlobalTail tail = GlobalTail{}) {
+                                          GlobalTail tail = GlobalTail{},
+                                          const float *pos = nullptr) {
     if constexpr (NA > 0) {
         constexpr int P = pow2ceil(NA);
         const int tid = threadIdx.x;
@@ -260,9 +275,16 @@ __device__ __forceinline__ void half_step(const float *sx, const float *sy, cons
         float mn[NA];
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
-            const float x = __shfl_sync(0xffffffffu, p[0], OFF + a);
-            const float y = __shfl_sync(0xffffffffu, p[1], OFF + a);
-            const float z = __shfl_sync(0xffffffffu, p[2], OFF + a);
+            float x, y, z;
+            if constexpr (POS) {
+                x = pos[OFF + a];
+                y = pos[AG + OFF + a];
+                z = pos[2 * AG + OFF + a];
+            } else {
+                x = __shfl_sync(0xffffffffu, p[0], OFF + a);
+                y = __shfl_sync(0xffffffffu, p[1], OFF + a);
+                z = __shfl_sync(0xffffffffu, p[2], OFF + a);
+            }
             X[a] = pk(x, x);
             Y[a] = pk(y, y);
             Z[a] = pk(z, z);
@@ -270,7 +292,7 @@ __device__ __forceinline__ void half_step(const float *sx, const float *sy, cons
             mn[a] = INFINITY;
         }
         const f2 one2 = pk(1.0f, 1.0f);
-#pragma unroll 2
+#pragma unroll 3
         for (int j = 2 * tid; j < cnt_pad; j += 2 * NT) {
             const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
             const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
@@ -298,7 +320,7 @@ __device__ __forceinline__ void half_step(const float *sx, const float *sy, cons
         for (int a = 0; a < P; ++a) {
             if (a < NA) {
                 const float w = lo_of(acc[a]) + hi_of(acc[a]);
-                vw[a] = a < NM ? w : -w;
+                vw[a] = sfu_agent(a, NM, NA) ? w : -w;
                 vm[a] = mn[a];
             } else {
                 vw[a] = 0.0f;
@@ -318,50 +340,6 @@ __device__ __forceinline__ void half_step(const float *sx, const float *sy, cons
             }
         }
     }
-}
-
-__device__ __forceinline__ void named_barrier(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-// CTA-level reduction of a half's per-warp partials part[NW][AG] (float2),
-// one warp per agent (lane l loads warp l's partial, fixed shuffle tree),
-// then lane 0 stores the CTA's partial into slot[rank][a] of every CTA of
-// the cluster.  Call after a barrier that covers all partial stores.
-template <int AG, int NA, int OFF, int NW, bool CLEAR>
-__device__ __forceinline__ void cta_ship(const float *part, float *slot, uint32_t C,
-                                         uint32_t rank, int warp, int lane) {
-    for (int a = warp; a < NA; a += NW) {
-        float w = 0.0f, m = INFINITY;
-        if (lane < NW) {
-            const float2 t = *reinterpret_cast<const float2 *>(part + 2 * (lane * AG + OFF + a));
-            w = t.x;
-            m = t.y;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            w += __shfl_xor_sync(0xffffffffu, w, o);
-            if (CLEAR) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        }
-        if (lane == 0) {
-            const uint32_t local = smem_u32(slot + 2 * (rank * AG + OFF + a));
-            for (uint32_t r = 0; r < C; ++r) st_cluster_v2f32(map_smem(local, r), w, m);
-        }
-    }
-}
-
-// Sum (min) of the C per-CTA partials of agent `lane` in rank order.
-template <int AG, bool CLEAR>
-__device__ __forceinline__ void cluster_combine(const float *slot, uint32_t C, int lane, float &W,
-                                                float &md2) {
-    float w = 0.0f, m = INFINITY;
-    for (uint32_t r = 0; r < C; ++r) {
-        const float2 t = *reinterpret_cast<const float2 *>(slot + 2 * (r * AG + lane));
-        w += t.x;
-        if (CLEAR) m = fminf(m, t.y);
-    }
-    W = w;
-    md2 = m;
 }
 
 // Sum of the C x NW partials of each agent of a half, in a fixed order;
@@ -407,31 +385,180 @@ __device__ __forceinline__ void half_combine(const float *recv_par, int nq, int 
     }
 }
 
-template <int AG, int NM, int NT, bool CLEAR>
-__global__ void __launch_bounds__(NT, 1) k_rollout(const RolloutArgs A) {
-    constexpr int NW = NT / 32;
+// Exchange of one agent half for step k, run by the exchange warp (lane a
+// holds agent a of the group): sum the NW per-warp partials of the CTA in
+// warp order, send the CTA partial to slot[rank] of every cluster CTA with
+// st.async (completing on that CTA's receive barrier), wait for the C
+// partials of this half, sum them in rank order and integrate.
+template <int AG, int NA, int OFF, int NW, bool CLEAR>
+__device__ __forceinline__ bool exchange_half(const float *part, float *slot, uint64_t *bar,
+                                              uint32_t C, uint32_t rank, int lane, int k,
+                                              bool ok, float &W, float &md2) {
+    float w = 0.0f, m = INFINITY;
+    if (lane < NA) {
+#pragma unroll 4
+        for (int q = 0; q < NW; ++q) {
+            const float2 t = *reinterpret_cast<const float2 *>(part + 2 * (q * AG + OFF + lane));
+            w += t.x;
+            if (CLEAR) m = fminf(m, t.y);
+        }
+    }
+    if (lane == 0) mbar_arrive_expect_tx(bar, C * NA * 8u);
+    if (lane < NA) {
+        const uint32_t local = smem_u32(slot + 2 * (rank * AG + OFF + lane));
+        const uint32_t lbar = smem_u32(bar);
+        for (uint32_t r = 0; r < C; ++r)
+            st_async_v2f32(map_smem(local, r), w, m, map_smem(lbar, r));
+    }
+    // each (half, parity) barrier completes once every second step
+    if (ok && !mbar_wait_cluster(bar, (k >> 1) & 1)) ok = false;
+    if (lane >= OFF && lane < OFF + NA) {
+        float ws = 0.0f, ms = INFINITY;
+        for (uint32_t r = 0; r < C; ++r) {
+            const float2 t = *reinterpret_cast<const float2 *>(slot + 2 * (r * AG + lane));
+            ws += t.x;
+            if (CLEAR) ms = fminf(ms, t.y);
+        }
+        W = ws;
+        md2 = ms;
+    }
+    return ok;
+}
+
+// Tag of a grid-exchange word: the launch epoch (30 bits) and the step
+// modulo 4 -- a slot is rewritten every second step, so a reader sees either
+// step k or step k - 2 of its own launch, or a word of an older launch.
+__device__ __forceinline__ uint32_t xtag(uint32_t epoch, int k) {
+    return (epoch << 2) | static_cast<uint32_t>(k & 3);
+}
+__device__ __forceinline__ uint64_t xword(uint32_t tag, float v) {
+    return (static_cast<uint64_t>(tag) << 32) | __float_as_uint(v);
+}
+
+// The same exchange between the C CTAs of a group that are not a cluster
+// (a cooperative grid, every CTA co-resident): the CTA partial goes to its
+// slot xs[rank][a] in global memory as tagged 64-bit words; the lanes of the
+// exchange warp poll the C x NA slots of the half between them (bounded)
+// until the tags of step k appear, stage the payloads in the shared-memory
+// slot[rank][a], and the agent's lane sums them in rank order.
+template <int AG, int NA, int OFF, int NW, bool CLEAR>
+__device__ __forceinline__ bool exchange_half_grid(const float *part, uint64_t *xs, float *slot,
+                                                   uint32_t C, uint32_t rank, int lane,
+                                                   uint32_t tag, bool ok, float &W, float &md2) {
+    if (lane < NA) {
+        float w = 0.0f, m = INFINITY;
+#pragma unroll 4
+        for (int q = 0; q < NW; ++q) {
+            const float2 t = *reinterpret_cast<const float2 *>(part + 2 * (q * AG + OFF + lane));
+            w += t.x;
+            if (CLEAR) m = fminf(m, t.y);
+        }
+        uint64_t *dst = xs + 2 * (rank * AG + OFF + lane);
+        st_relaxed_u64(dst, xword(tag, w));
+        if (CLEAR) st_relaxed_u64(dst + 1, xword(tag, m));
+    }
+    // pairs (r, a) = (p / NA, OFF + p % NA), p = lane + 32 j: all loads are
+    // issued before the first tag check
+    constexpr int J = NA > 0 ? (kMaxCluster * NA + 31) / 32 : 1;
+    const int npairs = static_cast<int>(C) * NA;
+    uint64_t vw[J], vm[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int p = lane + 32 * j;
+        if (p < npairs) {
+            const uint64_t *src = xs + 2 * ((p / NA) * AG + OFF + p % NA);
+            vw[j] = ld_relaxed_u64(src);
+            vm[j] = CLEAR ? ld_relaxed_u64(src + 1) : 0;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int p = lane + 32 * j;
+        if (p < npairs) {
+            const int r = p / NA, a = OFF + p % NA;
+            const uint64_t *src = xs + 2 * (r * AG + a);
+            for (uint32_t it = 0; ok && static_cast<uint32_t>(vw[j] >> 32) != tag; ++it) {
+                if (it == kPollLimit) ok = false;
+                else vw[j] = ld_relaxed_u64(src);
+            }
+            if (CLEAR) {
+                for (uint32_t it = 0; ok && static_cast<uint32_t>(vm[j] >> 32) != tag; ++it) {
+                    if (it == kPollLimit) ok = false;
+                    else vm[j] = ld_relaxed_u64(src + 1);
+                }
+            }
+            *reinterpret_cast<float2 *>(slot + 2 * (r * AG + a)) =
+                make_float2(__uint_as_float(static_cast<uint32_t>(vw[j])),
+                            CLEAR ? __uint_as_float(static_cast<uint32_t>(vm[j])) : INFINITY);
+        }
+    }
+    __syncwarp();
+    if (lane >= OFF && lane < OFF + NA) {
+        float ws = 0.0f, ms = INFINITY;
+        for (uint32_t r = 0; r < C; ++r) {
+            const float2 t = *reinterpret_cast<const float2 *>(slot + 2 * (r * AG + lane));
+            ws += t.x;
+            if (CLEAR) ms = fminf(ms, t.y);
+        }
+        W = ws;
+        md2 = ms;
+    }
+    return ok;
+}
+
+// GRID selects the exchange: false -- the C CTAs of a group form a thread-
+// block cluster and exchange over DSMEM; true -- groups of C consecutive
+// CTAs of a cooperative (all co-resident) grid exchange through global
+// memory, which lets groups fill every SM whatever the GPC layout.
+template <int AG, int NM, int NT, bool CLEAR, bool GRID>
+__global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
+    constexpr int NW = NT / 32;       // compute warps; warp NW is the exchange warp
     constexpr int H0 = (AG + 1) / 2;  // agents [0, H0) form half 0, [H0, AG) half 1
     constexpr int H1 = AG - H0;
     // SFU agents split evenly over the halves (each half's pair loop then
     // keeps the same SFU/FMA balance)
     constexpr int NM0 = (NM + 1) / 2 < H0 ? (NM + 1) / 2 : H0;
     constexpr int NM1 = NM - NM0 < H1 ? NM - NM0 : H1;
+    // named barriers: partials of half h ready (compute -> exchange), and
+    // positions of half h ready (exchange -> compute)
+    constexpr int kPart = 1, kPos = 3, kBoth = NT + 32;
     extern __shared__ __align__(128) float smem[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar_tma;
+    __shared__ __align__(8) uint64_t bar_recv[2][2];  // [half][parity]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t rank = cluster_rank();
-    uint32_t C;
-    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(C));
+    const bool exch = warp == NW;
+    uint32_t rank, C, group;
+    if constexpr (GRID) {
+        C = static_cast<uint32_t>(A.group_ctas);
+        rank = blockIdx.x % C;
+        group = blockIdx.x / C;
+    } else {
+        rank = cluster_rank();
+        asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(C));
+        group = cluster_id_x();
+    }
     int a0, na;
-    group_range(static_cast<int>(cluster_id_x()), A.n_agents, A.n_groups, a0, na);
+    group_range(static_cast<int>(group), A.n_agents, A.n_groups, a0, na);
 
     // N_O is read on the device; all CTAs of the cluster see the same value,
     // so an early exit is taken by the whole cluster before any DSMEM access.
     const int32_t n_obs = *A.n_obs;
     const int32_t shard_len = ((n_obs + (int32_t)C - 1) / (int32_t)C + 3) & ~3;
+    // grid exchange: the last CTA to finish (every CTA has read the epoch by
+    // then) advances the epoch for the next launch
+    auto finish_grid = [&](uint32_t epoch) {
+        if (atomicAdd(A.xctl + 1, 1u) == gridDim.x - 1) {
+            A.xctl[1] = 0;
+            const uint32_t next = (epoch + 1) & 0x3fffffffu;
+            A.xctl[0] = next ? next : 1u;
+        }
+    };
     if (n_obs < 0 || n_obs > A.cap || shard_len > A.shard_cap || na > AG || na <= 0) {
         if (tid == 0 && rank == 0) raise_error(A.err, GMAPP_DEVERR_CAPACITY);
+        if constexpr (GRID) {
+            if (tid == NT) finish_grid(ld_relaxed_u32(A.xctl));
+        }
         return;
     }
     const int32_t start = static_cast<int32_t>(rank) * shard_len;
@@ -441,25 +568,29 @@ __global__ void __launch_bounds__(NT, 1) k_rollout(const RolloutArgs A) {
     float *partbuf = smem + 3 * A.shard_cap;
     // per-CTA partials received from the cluster: [half][parity][rank][AG]
     float *recv = partbuf + 4 * NW * AG;
+    // agent positions for the compute warps: [3][AG]
+    float *pos = recv + 8 * static_cast<int>(C) * AG;
     auto part = [&](int h) { return partbuf + h * (2 * NW * AG); };
     auto slot = [&](int h, int par) {
         return recv + (h * 2 + par) * (2 * static_cast<int>(C) * AG);
     };
 
     if (tid == 0) {
-        mbar_init(&bar, 1);
+        mbar_init(&bar_tma, 1);
+        for (int i = 0; i < 4; ++i) mbar_init(&bar_recv[i >> 1][i & 1], 1);
         fence_mbar_init();
     }
     __syncthreads();
     if (cnt > 0 && tid == 0) {
         const uint32_t bytes = static_cast<uint32_t>((cnt + 3) & ~3) * 4u;
-        mbar_arrive_expect_tx(&bar, 3 * bytes);
-        bulk_g2s(sx, A.ox + start, bytes, &bar);
-        bulk_g2s(sy, A.oy + start, bytes, &bar);
-        bulk_g2s(sz, A.oz + start, bytes, &bar);
+        mbar_arrive_expect_tx(&bar_tma, 3 * bytes);
+        bulk_g2s(sx, A.ox + start, bytes, &bar_tma);
+        bulk_g2s(sy, A.oy + start, bytes, &bar_tma);
+        bulk_g2s(sz, A.oz + start, bytes, &bar_tma);
     }
 
-    // Agent state: lane a < na of EVERY warp holds agent a0 + a.
+    // Agent state: lane a < na of every warp reads agent a0 + a; only the
+    // exchange warp integrates, the compute warps keep R and the gate.
     float p[3] = {0, 0, 0}, v[3] = {0, 0, 0}, cc[3] = {0, 0, 0};
     float k_r = 0, k_a = 0, R = 0, G2 = -1.0f, L = 0, pen = 0, minc = INFINITY;
     if (lane < na) {
@@ -476,12 +607,17 @@ __global__ void __launch_bounds__(NT, 1) k_rollout(const RolloutArgs A) {
         const float rd = A.r_d[i];
         // s = max(d - R, eps) <= r_d  <=>  d^2 <= (r_d + R)^2  when r_d >= eps
         G2 = rd >= A.eps ? (rd + R) * (rd + R) : -1.0f;
-        if (rank == 0 && warp == 0 && A.traj) {
+        if (rank == 0 && exch && A.traj) {
             float *t = A.traj + (size_t)i * (A.n_steps + 1) * 3;
             t[0] = p[0];
             t[1] = p[1];
             t[2] = p[2];
         }
+    }
+    if (exch && lane < AG) {
+        pos[lane] = p[0];
+        pos[AG + lane] = p[1];
+        pos[2 * AG + lane] = p[2];
     }
     f2 nR2[AG];
     float G2a[AG];
@@ -492,7 +628,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout(const RolloutArgs A) {
         G2a[a] = __shfl_sync(0xffffffffu, G2, a);
     }
     if (cnt > 0) {
-        if (!mbar_wait(&bar, 0)) {
+        if (!mbar_wait(&bar_tma, 0)) {
             if (tid == 0) raise_error(A.err, GMAPP_DEVERR_TIMEOUT);
             cnt = 0;  // keep the barrier sequence; results are flagged invalid
         }
@@ -505,94 +641,117 @@ __global__ void __launch_bounds__(NT, 1) k_rollout(const RolloutArgs A) {
         sz[cnt] = __int_as_float(0x7fc00000);
     }
     const float eps = A.eps;
-    // every CTA of the cluster is running (and the padding is visible)
-    // before anyone stores into its shared memory
-    cluster_sync_all();
+    // every CTA of the cluster is running (barriers initialised, padding and
+    // positions visible) before anyone stores into its shared memory
+    if constexpr (GRID) __syncthreads();
+    else cluster_sync_all();
 
-    const float h = A.vel_half * A.dt * A.inv_mass;
-    auto integrate = [&](int k, float W, float md2) {
-        if (A.ckpt && rank == 0 && warp == 0 && k % A.ckpt_every == 0) {
-            // adjoint checkpoint: the state (p_k, v_{k-1}) entering step k
-            const int n = A.n_agents, i = a0 + lane;
-            float *ck = A.ckpt + (size_t)(k / A.ckpt_every) * 6 * n + i;
+    if (!exch) {
+        // Compute warps: the two halves back to back; a half's partials are
+        // handed to the exchange warp while the other half is computed, and
+        // its new positions are ready long before they are needed.
+        for (int k = 0; k < A.n_steps; ++k) {
+            if (k > 0) named_sync(kPos + 0, kBoth);
+            half_step<AG, H0, 0, NM0, NT, CLEAR, false, false, true>(
+                sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(0) + 2 * (warp * AG), C, lane,
+                GlobalTail{}, pos);
+            named_arrive(kPart + 0, kBoth);
+            if (k > 0) named_sync(kPos + 1, kBoth);
+            half_step<AG, H1, H0, NM1, NT, CLEAR, false, false, true>(
+                sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(1) + 2 * (warp * AG), C, lane,
+                GlobalTail{}, pos);
+            named_arrive(kPart + 1, kBoth);
+        }
+    } else {
+        const float h = A.vel_half * A.dt * A.inv_mass;
+        auto integrate = [&](int k, float W, float md2) {
+            if (A.ckpt && rank == 0 && k % A.ckpt_every == 0) {
+                // adjoint checkpoint: the state (p_k, v_{k-1}) entering step k
+                const int n = A.n_agents, i = a0 + lane;
+                float *ck = A.ckpt + (size_t)(k / A.ckpt_every) * 6 * n + i;
 #pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    ck[d * n] = p[d];
+                    ck[(3 + d) * n] = v[d];
+                }
+            }
+            float g[3], kf, m;
+            agent_step<CLEAR>(p, v, cc, k_r, k_a, R, A.goal, h, A.dt, A.rho, A.damping,
+                              A.clear_margin, A.clear_beta, W, md2, L, pen, minc, m, g, kf);
+            pos[lane] = p[0];
+            pos[AG + lane] = p[1];
+            pos[2 * AG + lane] = p[2];
+            if (rank == 0) {
+                const int i = a0 + lane;
+                if (A.traj) {
+                    float *t = A.traj + ((size_t)i * (A.n_steps + 1) + k + 1) * 3;
+                    t[0] = p[0];
+                    t[1] = p[1];
+                    t[2] = p[2];
+                }
+                if (A.w_trace) A.w_trace[(size_t)i * A.n_steps + k] = W;
+                if (A.m_trace) A.m_trace[(size_t)i * A.n_steps + k] = m;
+                if (A.f_trace) {
+                    float *f = A.f_trace + ((size_t)i * A.n_steps + k) * 3;
+                    f[0] = kf * g[0];
+                    f[1] = kf * g[1];
+                    f[2] = kf * g[2];
+                }
+            }
+        };
+        // Exchange warp: half 0 of step k is exchanged while the compute
+        // warps work on half 1, and half 1 while they start step k + 1.
+        bool ok = true;
+        uint32_t epoch = 0;
+        uint64_t *xg = nullptr;
+        if constexpr (GRID) {
+            epoch = ld_relaxed_u32(A.xctl);
+            xg = A.xbuf + static_cast<size_t>(group) * 4 * 2 * C * AG;
+        }
+        auto xslot = [&](int h, int par) { return xg + (h * 2 + par) * 2 * C * AG; };
+        for (int k = 0; k < A.n_steps; ++k) {
+            const int par = k & 1;
+            float W = 0.0f, md2 = INFINITY;
+            named_sync(kPart + 0, kBoth);
+            if constexpr (GRID)
+                ok = exchange_half_grid<AG, H0, 0, NW, CLEAR>(part(0), xslot(0, par), slot(0, par),
+                                                              C, rank, lane, xtag(epoch, k), ok, W,
+                                                              md2);
+            else
+                ok = exchange_half<AG, H0, 0, NW, CLEAR>(part(0), slot(0, par), &bar_recv[0][par],
+                                                         C, rank, lane, k, ok, W, md2);
+            if (lane < H0 && lane < na) integrate(k, W, md2);
+            __syncwarp();
+            if (k + 1 < A.n_steps) named_arrive(kPos + 0, kBoth);
+            named_sync(kPart + 1, kBoth);
+            if constexpr (GRID)
+                ok = exchange_half_grid<AG, H1, H0, NW, CLEAR>(part(1), xslot(1, par), slot(1, par),
+                                                               C, rank, lane, xtag(epoch, k), ok, W,
+                                                               md2);
+            else
+                ok = exchange_half<AG, H1, H0, NW, CLEAR>(part(1), slot(1, par), &bar_recv[1][par],
+                                                          C, rank, lane, k, ok, W, md2);
+            if (lane >= H0 && lane < na) integrate(k, W, md2);
+            __syncwarp();
+            if (k + 1 < A.n_steps) named_arrive(kPos + 1, kBoth);
+        }
+        if (!ok) raise_error(A.err, GMAPP_DEVERR_TIMEOUT);
+        if constexpr (GRID) {
+            if (lane == 0) finish_grid(epoch);
+        }
+        if (rank == 0 && lane < na) {
+            const int i = a0 + lane, n = A.n_agents;
             for (int d = 0; d < 3; ++d) {
-                ck[d * n] = p[d];
-                ck[(3 + d) * n] = v[d];
+                A.p_final[d * n + i] = p[d];
+                A.v_final[d * n + i] = v[d];
             }
+            A.path_len[i] = L;
+            if (A.clear_pen) A.clear_pen[i] = pen;
+            if (A.min_clear) A.min_clear[i] = minc;
         }
-        float g[3], kf, m;
-        agent_step<CLEAR>(p, v, cc, k_r, k_a, R, A.goal, h, A.dt, A.rho, A.damping,
-                          A.clear_margin, A.clear_beta, W, md2, L, pen, minc, m, g, kf);
-        if (rank == 0 && warp == 0) {
-            const int i = a0 + lane;
-            if (A.traj) {
-                float *t = A.traj + ((size_t)i * (A.n_steps + 1) + k + 1) * 3;
-                t[0] = p[0];
-                t[1] = p[1];
-                t[2] = p[2];
-            }
-            if (A.w_trace) A.w_trace[(size_t)i * A.n_steps + k] = W;
-            if (A.m_trace) A.m_trace[(size_t)i * A.n_steps + k] = m;
-            if (A.f_trace) {
-                float *f = A.f_trace + ((size_t)i * A.n_steps + k) * 3;
-                f[0] = kf * g[0];
-                f[1] = kf * g[1];
-                f[2] = kf * g[2];
-            }
-        }
-    };
-
-    // Two agent halves in flight: while the partial sums of one half cross
-    // the cluster (split barrier), the other half is being computed.
-    //   prologue: half0(0) -> arrive
-    //   step k:   half1(k) -> wait -> integrate half0(k) -> arrive
-    //             half0(k+1) -> wait -> integrate half1(k) -> arrive
-    //   each half: per-warp partials -> CTA barrier -> one warp per agent
-    //   reduces the CTA's partial and stores it into every cluster CTA
-    auto compute_half0 = [&](int par) {
-        half_step<AG, H0, 0, NM0, NT, CLEAR, false, false>(sx, sy, sz, cnt_pad, eps, nR2, G2a, p,
-                                                           part(0) + 2 * (warp * AG), C, lane);
-        named_barrier(1, NT);
-        cta_ship<AG, H0, 0, NW, CLEAR>(part(0), slot(0, par), C, rank, warp, lane);
-    };
-    auto compute_half1 = [&](int par) {
-        half_step<AG, H1, H0, NM1, NT, CLEAR, false, false>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
-                                                            p, part(1) + 2 * (warp * AG), C, lane);
-        named_barrier(2, NT);
-        cta_ship<AG, H1, H0, NW, CLEAR>(part(1), slot(1, par), C, rank, warp, lane);
-    };
-    compute_half0(0);
-    cluster_arrive();
-    for (int k = 0; k < A.n_steps; ++k) {
-        const int par = k & 1;
-        compute_half1(par);
-        cluster_wait();
-        if (lane < H0 && lane < na) {
-            float W, md2;
-            cluster_combine<AG, CLEAR>(slot(0, par), C, lane, W, md2);
-            integrate(k, W, md2);
-        }
-        cluster_arrive();
-        if (k + 1 < A.n_steps) compute_half0(par ^ 1);
-        cluster_wait();
-        if (lane >= H0 && lane < na) {
-            float W, md2;
-            cluster_combine<AG, CLEAR>(slot(1, par), C, lane, W, md2);
-            integrate(k, W, md2);
-        }
-        if (k + 1 < A.n_steps) cluster_arrive();
     }
-    if (rank == 0 && warp == 0 && lane < na) {
-        const int i = a0 + lane, n = A.n_agents;
-        for (int d = 0; d < 3; ++d) {
-            A.p_final[d * n + i] = p[d];
-            A.v_final[d * n + i] = v[d];
-        }
-        A.path_len[i] = L;
-        if (A.clear_pen) A.clear_pen[i] = pen;
-        if (A.min_clear) A.min_clear[i] = minc;
-    }
+    // no CTA leaves while another may still deliver into its shared memory
+    if constexpr (!GRID) cluster_sync_all();
 }
 
 using RolloutKernel = void (*)(const RolloutArgs);
@@ -600,10 +759,15 @@ using RolloutKernel = void (*)(const RolloutArgs);
 // Instantiation tables (rollout_inst_*.cu).
 RolloutKernel rollout_kernel_noclear(int ag, int nt);
 RolloutKernel rollout_kernel_clear(int ag, int nt);
+RolloutKernel rollout_kernel_grid_noclear(int ag, int nt);
+RolloutKernel rollout_kernel_grid_clear(int ag, int nt);
 
 // SFU share of the reciprocals: NM of AG agents use rcp.approx, the rest the
-// Newton-Raphson path (NM/AG ~ 3/7 balances 16 SFU ops/clk against 128 FMA
-// lanes/clk per SM); tiny groups stay on the SFU, where latency matters more.
-constexpr int sfu_agents(int ag) { return ag <= 2 ? ag : (3 * ag + 3) / 7; }
+// Newton-Raphson path.  Per obstacle pair an SFU agent costs 8 FMA-pipe
+// lane-ops and 2 SFU ops, a Newton-Raphson agent 14 and 1; with 128 FMA
+// lanes and 16 SFU lanes per SM clock the two pipes balance near NM/AG = 1/2
+// (measured best on B300); tiny groups stay on the SFU, where latency
+// matters more.
+constexpr int sfu_agents(int ag) { return ag <= 2 ? ag : (ag + 1) / 2; }
 
 }  // namespace gmapp

@@ -138,11 +138,15 @@ def test_tabletop_full_size_sampled_agents(gm):
     _compare_rollout(out, ref, idx=idx)
 
 
+# (cluster, agents per group, compute threads[, exchange]); exchange 1 = the
+# cooperative-grid exchange through global memory
 SHAPES = [(1, 8, 256), (1, 3, 128), (2, 4, 256), (3, 5, 384), (4, 8, 512), (5, 2, 256),
-          (8, 1, 128), (8, 16, 256), (16, 7, 256), (16, 8, 512), (7, 10, 384)]
+          (8, 1, 128), (8, 16, 256), (16, 7, 256), (16, 8, 512), (7, 10, 384), (2, 14, 384),
+          (3, 10, 512), (5, 10, 384, 1), (1, 8, 256, 1), (3, 5, 128, 1), (16, 3, 512, 1),
+          (2, 16, 256, 1)]
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "c%d_a%d_t%d" % s)
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "c%d_a%d_t%d" % s[:3] + ("_grid" if s[3:] == (1,) else ""))
 def test_launch_shapes(gm, shape):
     w = synth.sphere_workload(n_agents=21, n_steps=120)
     obs, r_O = _filtered(w)
@@ -160,7 +164,7 @@ def test_small_obstacle_counts(gm, n_obs):
                     g.uniform(0.37, 0.43, n_obs)]).astype(np.float32)
     w = synth.sphere_workload(n_agents=5, n_steps=150)
     ref = oracle.rollout(obs, 0.005, w["agents"], w["params"])
-    for shape in ((1, 5, 128), (4, 2, 256), (16, 3, 128)):
+    for shape in ((1, 5, 128), (4, 2, 256), (16, 3, 128), (4, 2, 256, 1), (16, 3, 128, 1)):
         out = gm.rollout_agents(_gpu_obstacles(gm, obs, 0.005, cap=1024), to_dev_agents(w["agents"]),
                                 w["params"], tuning=shape)
         gm.sync()
@@ -230,6 +234,51 @@ def test_invalid_arguments(gm):
         gm.rollout_agents(o, ag, w["params"], tuning=(2, 4, 200))
 
 
+def test_grid_exchange_matches_cluster_bitwise(gm):
+    """Both exchanges sum the same CTA partials in rank order, so a shape
+    gives bit-identical trajectories whichever carries the partials."""
+    w = synth.sphere_workload(n_agents=37, n_steps=160)
+    obs, r_O = _filtered(w)
+    o = _gpu_obstacles(gm, obs, r_O, cap=4096)
+    ag = to_dev_agents(w["agents"])
+    for shape, clear in (((4, 6, 256), True), ((2, 10, 384), False), ((1, 12, 128), True),
+                         ((5, 8, 512), False)):
+        a = gm.rollout_agents(o, ag, w["params"], tuning=shape + (0,), want_clear=clear)
+        b = gm.rollout_agents(o, ag, w["params"], tuning=shape + (1,), want_clear=clear)
+        gm.sync()
+        for k in ("traj", "p_final", "v_final", "path_len", "clear_pen", "min_clear"):
+            if a[k] is not None:
+                assert np.array_equal(a[k].cpu().numpy(), b[k].cpu().numpy()), (shape, k)
+
+
+def test_grid_exchange_repeats_across_streams(gm):
+    """The launch epoch keeps stale slot words of earlier launches from
+    matching: back-to-back grid-exchange launches, alternating between two
+    streams and with changing shapes, all give the same result."""
+    import torch
+    w = synth.sphere_workload(n_agents=40, n_steps=60)
+    obs, r_O = _filtered(w)
+    o = _gpu_obstacles(gm, obs, r_O, cap=4096)
+    ag = to_dev_agents(w["agents"])
+    ref = gm.rollout_agents(o, ag, w["params"], tuning=(4, 8, 256, 1))
+    gm.sync()
+    ref_p = ref["p_final"].cpu().numpy()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for i in range(12):
+        shape = (4, 8, 256, 1) if i % 3 else (5, 5, 128, 1)
+        s = streams[i % 2]
+        with torch.cuda.stream(s):
+            outs.append((shape, gm.rollout_agents(o, ag, w["params"], tuning=shape, stream=s)))
+    torch.cuda.synchronize()
+    gm.sync()
+    for shape, out in outs:
+        if shape == (4, 8, 256, 1):
+            assert np.array_equal(out["p_final"].cpu().numpy(), ref_p)
+        else:
+            assert np.abs(out["p_final"].cpu().numpy() - ref_p).max() < 1e-4
+
+
 def test_autotuner_picks_a_measured_shape(gm):
     """The autotuner times candidate shapes on the caller's inputs, caches
     the fastest, and later rollouts of the same sizes use it."""
@@ -239,7 +288,7 @@ def test_autotuner_picks_a_measured_shape(gm):
     ag = to_dev_agents(w["agents"])
     out = gm.alloc_rollout_out(40, 150, want_clear=False)
     shape, ms = gm.autotune_rollout(o, ag, w["params"], out=out, candidates=6, probe_steps=30)
-    assert ms > 0 and len(shape) == 3
+    assert ms > 0 and len(shape) == 4
     assert gm.pick_tuning(4096, 40) == shape
     res = gm.rollout_agents(o, ag, w["params"])
     gm.sync()
