@@ -124,20 +124,22 @@ int max_active_clusters(gmapp_ctx *ctx, const Shape &s) {
     return m;
 }
 
-// Cost model in SM cycles for the whole rollout of one step: the slowest CTA
-// evaluates ag x shard pairs at ~10 pairs/clk (fewer with few agents in
-// flight), plus a per-step exchange (cluster barrier, partial sums,
-// integration); clusters beyond the co-resident count run in later waves.
+// Cost model in SM cycles for one step of the rollout: the slowest CTA
+// evaluates ag x shard pairs at ~7 pairs/clk (measured on B300 for 9-10
+// agents; fewer with few agents in flight).  The exchange warp hides the
+// per-step exchange behind the pair loop of the other agent half, so a step
+// costs the larger of the pair loop and the exchange latency chain (~3000
+// cycles over DSMEM, ~4700 through L2 for the grid exchange); cluster
+// groups beyond the co-resident count run in later waves, a grid-exchange
+// launch must fit in one wave (its groups poll one another).
 double model_cost(const Shape &s, int m, int64_t n_obs_est) {
     const double shard = static_cast<double>((n_obs_est + s.cluster - 1) / s.cluster);
-    const double rate = std::min(10.0, 2.0 + 1.5 * s.ag);
-    const double sync = 1200.0 + 40.0 * s.cluster + 3.0 * s.cluster * (s.threads / 32) * s.ag;
-    // a grid-exchange launch must fit in one wave (its groups poll one
-    // another); its exchange runs through L2 and costs more latency
+    const double rate = std::min(7.0, 1.5 + 1.2 * s.ag) * (s.threads >= 384 ? 1.0 : 0.95);
+    const double loop = s.ag * std::max(shard, 64.0) / rate;
+    const double chain = (s.grid ? 4700.0 : 3000.0) + 20.0 * s.cluster;
     if (s.grid && s.groups > m) return 1e300;
-    const double xsync = s.grid ? 1.5 * sync : sync;
     const int waves = (s.groups + m - 1) / m;
-    return waves * (s.ag * std::max(shard, 64.0) / rate + xsync);
+    return waves * (std::max(loop, chain) + 0.1 * std::min(loop, chain));
 }
 
 std::mutex g_tune_mu;
