@@ -352,7 +352,8 @@ def run_ours(args, ws, rank, local):
         if not args.no_patterns:
             del frames, pinned, wsp, obs, ro, sel
             torch.cuda.empty_cache()
-            result["patterns"] = {"batched": bench_batched(gm, args),
+            result["patterns"] = {"filter_stream": bench_filter_stream(gm, args),
+                                  "batched": bench_batched(gm, args),
                                   "adjoint": bench_adjoint(gm, args),
                                   "served": bench_served(gm, args)}
         print(json.dumps(result), flush=True)
@@ -362,8 +363,8 @@ def run_ours(args, ws, rank, local):
     return 0
 
 
-# filter_cloud (zero, keys, bitmap sums, emit, count, publish) + rollout + select
-LAUNCHES_PER_STEP = 6 + 1 + 1
+# filter_cloud (zero, keys, bitmap sums, emit, count) + rollout + select
+LAUNCHES_PER_STEP = 5 + 1 + 1
 
 
 def _events(torch, stream, fn, reps):
@@ -375,6 +376,84 @@ def _events(torch, stream, fn, reps):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8):
+    """The perception filter alone (A1-A3) over a stream of 256 tabletop
+    frames (307,200 points each, 944 MB read in total; 64 distinct frames,
+    236 MB, cycled so that no frame is still in L2 when it comes back),
+    issued on 8 CUDA streams with a workspace and an output each, and on one
+    stream back to back.  Algorithmic bytes per frame: 12 B per raw point
+    read + 24 B per obstacle written (centres, key, count, index)."""
+    import torch
+    import synth
+    base_frames = [synth.tabletop_workload(frame_seed=9_000_000 + f, n_agents=1, n_steps=1)
+                   for f in range(8)]
+    w0 = base_frames[0]
+    g = np.random.Generator(np.random.PCG64(4242))
+    host = []
+    for i in range(n_distinct):
+        xyz = base_frames[i % 8]["xyz"]
+        host.append((xyz + g.normal(0.0, 1e-3, xyz.shape)).astype(np.float32))
+    frames = torch.from_numpy(np.stack(host)).cuda()
+    n_raw = frames.shape[1]
+    wbytes = gm.filter_workspace_bytes(n_raw, w0["workspace"])
+    streams = [torch.cuda.Stream() for _ in range(n_streams)]
+    wsp = [torch.empty(wbytes, dtype=torch.uint8, device="cuda") for _ in range(n_streams)]
+    outs = [gm.Obstacles.empty(131072) for _ in range(n_streams)]
+    n_obs = []
+    for i in range(n_distinct):   # N_O per distinct frame, outside timing
+        gm.filter_cloud(frames[i], w0["T"], w0["workspace"], out=outs[0], workspace=wsp[0])
+        n_obs.append(outs[0].count())
+    torch.cuda.synchronize()
+
+    def issue(ns):
+        cur = torch.cuda.current_stream()
+        for s in streams[:ns]:
+            s.wait_stream(cur)
+        for i in range(n_filters):
+            k = i % ns
+            with torch.cuda.stream(streams[k]):
+                gm.filter_cloud(frames[i % n_distinct], w0["T"], w0["workspace"], out=outs[k],
+                                workspace=wsp[k], stream=streams[k])
+        for s in streams[:ns]:
+            cur.wait_stream(s)
+
+    def run(ns):
+        # the 256 calls captured once in a CUDA graph, so the device time is
+        # not bounded by the host issuing 1,280 launches
+        issue(ns)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(graph, stream=side):
+            issue(ns)
+        torch.cuda.synchronize()
+        cur = torch.cuda.current_stream()
+        best = None
+        for _ in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(cur)
+            graph.replay()
+            e1.record(cur)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        return best
+
+    byts = sum(12 * n_raw + 24 * n_obs[i % n_distinct] for i in range(n_filters))
+    peak = _measured_peaks().get("hbm_gbs")
+    res = {"workload": f"{n_filters} tabletop frames x {n_raw} points ({n_distinct} distinct, "
+                       f"{n_distinct * n_raw * 12 / 1e6:.0f} MB), 5 mm voxels",
+           "algorithmic_bytes": byts}
+    for ns in (n_streams, 1):
+        t = run(ns)
+        gbs = byts / t / 1e9
+        res[f"streams_{ns}"] = {"ms": 1e3 * t, "us_per_frame": 1e6 * t / n_filters,
+                                "GB_per_s": gbs, "hbm_frac": gbs / peak if peak else None}
+    res["peak_GB_per_s"] = peak
+    return res
 
 
 def bench_batched(gm, args, reps=3):

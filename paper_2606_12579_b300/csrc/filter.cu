@@ -10,7 +10,8 @@
 //   k_keys          points -> key per point + bitmap bits          (12 B/pt in, 4 B/pt out)
 //   k_bitmap_sums   popcount per block of words; the last block to
 //                   finish scans the block sums (no spin-wait)
-//   k_emit          per word: prefix rank; per set bit: key, centre
+//   k_emit          per word: prefix rank; per set bit (one lane per bit of a
+//                   word, warp-cooperative): key, centre; publishes N_O
 //   k_count         points -> rank -> count (atomicAdd), smallest index (atomicMin)
 //   k_keep_sums / k_keep_emit   only when min_pts > 1: order-preserving compaction
 #include <math.h>
@@ -99,10 +100,10 @@ extern "C" gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n
                                                                           counters, n_occ);
     if (ws->min_pts == 1) {
         EmitOut o{out->keys, out->counts, out->rep_idx, out->x, out->y, out->z, out->cap};
-        k_emit<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, offsets, prefix, A, o);
+        k_emit<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, offsets, prefix, A, o,
+                                                                      n_occ, out->n, ctx->d_err);
         k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, bitmap, prefix, out->counts,
                                                    out->rep_idx, out->cap);
-        k_publish<<<1, 1, 0, stream>>>(n_occ, out->n, out->cap, ctx->d_err);
     } else {
         uint32_t *tkeys = reinterpret_cast<uint32_t *>(base + L.off_tkeys);
         uint32_t *tcounts = reinterpret_cast<uint32_t *>(base + L.off_tcounts);
@@ -110,7 +111,8 @@ extern "C" gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n
         uint32_t *tsums = reinterpret_cast<uint32_t *>(base + L.off_tsums);
         uint32_t *toffsets = reinterpret_cast<uint32_t *>(base + L.off_toffsets);
         EmitOut t{tkeys, tcounts, trep, nullptr, nullptr, nullptr, L.n_tmp};
-        k_emit<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, offsets, prefix, A, t);
+        k_emit<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, offsets, prefix, A, t,
+                                                                      nullptr, nullptr, nullptr);
         k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, bitmap, prefix, tcounts, trep,
                                                    L.n_tmp);
         k_keep_sums<<<static_cast<int>(L.n_tblocks), kThreads, 0, stream>>>(
@@ -258,10 +260,10 @@ extern "C" gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, co
                                                                           counters, n_occ);
     if (ws->min_pts == 1) {
         EmitOut o{out->keys, out->counts, out->rep_idx, out->x, out->y, out->z, out->cap};
-        k_emit<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, offsets, prefix, A, o);
+        k_emit<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, offsets, prefix, A, o,
+                                                                      n_occ, out->n, sym.err);
         k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, bitmap, prefix, out->counts,
                                                    out->rep_idx, out->cap);
-        k_publish<<<1, 1, 0, stream>>>(n_occ, out->n, out->cap, sym.err);
     } else {
         uint32_t *tkeys = reinterpret_cast<uint32_t *>(base + L.off_tkeys);
         uint32_t *tcounts = reinterpret_cast<uint32_t *>(base + L.off_tcounts);
@@ -269,7 +271,8 @@ extern "C" gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, co
         uint32_t *tsums = reinterpret_cast<uint32_t *>(base + L.off_tsums);
         uint32_t *toffsets = reinterpret_cast<uint32_t *>(base + L.off_toffsets);
         EmitOut t{tkeys, tcounts, trep, nullptr, nullptr, nullptr, L.n_tmp};
-        k_emit<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, offsets, prefix, A, t);
+        k_emit<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, offsets, prefix, A, t,
+                                                                      nullptr, nullptr, nullptr);
         k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, bitmap, prefix, tcounts, trep,
                                                    L.n_tmp);
         k_keep_sums<<<static_cast<int>(L.n_tblocks), kThreads, 0, stream>>>(

@@ -207,12 +207,17 @@ struct EmitOut {
 
 // Per word: rank of its first set bit = block offset + in-block prefix.
 // Every set bit becomes one output entry (key, centre, count = 0, rep = ~0).
+// Emission is warp-cooperative: each warp walks its 128 words of the block
+// (staged in shared memory), skips empty ones by ballot, and lane b writes
+// the entry of bit b, so a fully occupied word costs one pass of 32 lanes
+// with consecutive (coalesced) ranks instead of 32 serial iterations.
 __device__ __forceinline__ void emit_block(const uint32_t *__restrict__ bitmap,
-                                                   const uint32_t *__restrict__ offsets,
-                                                   uint32_t *__restrict__ word_prefix,
-                                                   FilterArgs A, EmitOut o,
-                                           int64_t blk) {
+                                           const uint32_t *__restrict__ offsets,
+                                           uint32_t *__restrict__ word_prefix, FilterArgs A,
+                                           EmitOut o, int64_t blk) {
     __shared__ uint32_t warp_tot[kThreads / 32];
+    __shared__ __align__(16) uint32_t s_words[kWordsPerBlock];
+    __shared__ __align__(16) uint32_t s_pre[kWordsPerBlock];
     const int64_t wv = blk * (int64_t)kThreads + threadIdx.x;
     const uint4 w = reinterpret_cast<const uint4 *>(bitmap)[wv];
     uint32_t c0 = __popc(w.x), c1 = __popc(w.y), c2 = __popc(w.z), c3 = __popc(w.w);
@@ -220,38 +225,55 @@ __device__ __forceinline__ void emit_block(const uint32_t *__restrict__ bitmap,
     uint32_t base = offsets[blk] + block_exclusive_scan(c0 + c1 + c2 + c3, warp_tot, tot);
     uint4 pre = make_uint4(base, base + c0, base + c0 + c1, base + c0 + c1 + c2);
     reinterpret_cast<uint4 *>(word_prefix)[wv] = pre;
-    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
-    const uint32_t pres[4] = {pre.x, pre.y, pre.z, pre.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        uint32_t bits = words[j];
-        uint32_t rank = pres[j];
-        const uint32_t key0 = static_cast<uint32_t>((4 * wv + j) * 32);
-        while (bits) {
-            int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            if (rank < o.cap) {
-                uint32_t key = key0 + b;
-                o.keys[rank] = key;
-                o.counts[rank] = 0;
-                o.rep[rank] = kInvalid;
-                if (o.x) {
-                    float cx, cy, cz;
-                    voxel_centre(key, A, cx, cy, cz);
-                    o.x[rank] = cx;
-                    o.y[rank] = cy;
-                    o.z[rank] = cz;
+    reinterpret_cast<uint4 *>(s_words)[threadIdx.x] = w;
+    reinterpret_cast<uint4 *>(s_pre)[threadIdx.x] = pre;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t below = (1u << lane) - 1u;
+    constexpr int kWordsPerWarp = kWordsPerBlock / (kThreads / 32);
+#pragma unroll 1
+    for (int c = 0; c < kWordsPerWarp; c += 32) {
+        const int i0 = warp * kWordsPerWarp + c;
+        uint32_t nz = __ballot_sync(0xffffffffu, s_words[i0 + lane] != 0u);
+        while (nz) {
+            const int i = i0 + __ffs(nz) - 1;
+            nz &= nz - 1;
+            const uint32_t bits = s_words[i];
+            if ((bits >> lane) & 1u) {
+                const uint32_t rank = s_pre[i] + __popc(bits & below);
+                if (rank < o.cap) {
+                    const uint32_t key =
+                        static_cast<uint32_t>((blk * kWordsPerBlock + i) * 32 + lane);
+                    o.keys[rank] = key;
+                    o.counts[rank] = 0;
+                    o.rep[rank] = kInvalid;
+                    if (o.x) {
+                        float cx, cy, cz;
+                        voxel_centre(key, A, cx, cy, cz);
+                        o.x[rank] = cx;
+                        o.y[rank] = cy;
+                        o.z[rank] = cz;
+                    }
                 }
             }
-            ++rank;
         }
     }
 }
 
+// With n_out set (min_pts == 1), block 0 also publishes N_O = the number of
+// occupied voxels (and a capacity error when it exceeds o.cap), which the
+// later kernels of the stream read on the device.
 __global__ void __launch_bounds__(kThreads) k_emit(const uint32_t *__restrict__ bitmap,
                                                    const uint32_t *__restrict__ offsets,
                                                    uint32_t *__restrict__ word_prefix,
-                                                   FilterArgs A, EmitOut o) {
+                                                   FilterArgs A, EmitOut o,
+                                                   const uint32_t *n_occ, int32_t *n_out,
+                                                   uint32_t *err) {
+    if (n_out && blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint32_t t = *n_occ;
+        *n_out = static_cast<int32_t>(t);
+        if (t > o.cap) raise_error(err, GMAPP_DEVERR_CAPACITY);
+    }
     emit_block(bitmap, offsets, word_prefix, A, o, blockIdx.x);
 }
 
@@ -319,14 +341,6 @@ __global__ void __launch_bounds__(kThreads) k_count(const uint32_t *__restrict__
                                                     const uint32_t *__restrict__ word_prefix,
                                                     uint32_t *counts, uint32_t *rep, int64_t cap) {
     count_range(keys, n, bitmap, word_prefix, counts, rep, cap, blockIdx.x, gridDim.x);
-}
-
-// Publish N_O = min(total, cap) semantics: n_out = total; capacity error if
-// total > cap.  (min_pts == 1 path.)
-__global__ void k_publish(const uint32_t *n_occ, int32_t *n_out, int64_t cap, uint32_t *err) {
-    uint32_t t = *n_occ;
-    *n_out = static_cast<int32_t>(t);
-    if (t > cap) raise_error(err, GMAPP_DEVERR_CAPACITY);
 }
 
 // min_pts > 1: per block of 1024 temporary entries, how many pass; last

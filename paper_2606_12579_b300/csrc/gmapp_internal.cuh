@@ -212,9 +212,29 @@ __device__ __forceinline__ void raise_error(uint32_t *err, uint32_t bits) {
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Bytes of the grid-exchange slots for up to `ctas` CTAs: per CTA
-// [2 halves][2 parities][16 agents][2 words (W, min d^2)].
+// [2 halves][2 parities][16 agents][6 words] -- the rollout uses 2 words
+// per agent (W, min d^2), the adjoint 6 (W, grad W, min d^2, argmin).
 inline size_t xbuf_bytes(int ctas) {
-    return static_cast<size_t>(ctas) * 2 * 2 * 16 * 2 * sizeof(uint64_t);
+    return static_cast<size_t>(ctas) * 2 * 2 * 16 * 6 * sizeof(uint64_t);
+}
+
+// Launches that exchange through the context's grid slots use them one at
+// a time: outside stream capture, each waits for the previous one (on any
+// stream) and records its own completion; inside capture the caller's graph
+// orders them.
+inline gmapp_status grid_exchange_begin(gmapp_ctx *ctx, cudaStream_t stream, bool *capturing) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    GMAPP_CHECK_CUDA(cudaStreamIsCapturing(stream, &cs));
+    *capturing = cs != cudaStreamCaptureStatusNone;
+    if (!*capturing && ctx->x_pending) GMAPP_CHECK_CUDA(cudaStreamWaitEvent(stream, ctx->x_done, 0));
+    return GMAPP_OK;
+}
+inline gmapp_status grid_exchange_end(gmapp_ctx *ctx, cudaStream_t stream, bool capturing) {
+    if (!capturing) {
+        GMAPP_CHECK_CUDA(cudaEventRecord(ctx->x_done, stream));
+        ctx->x_pending = true;
+    }
+    return GMAPP_OK;
 }
 
 }  // namespace gmapp

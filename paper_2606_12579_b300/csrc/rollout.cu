@@ -132,10 +132,14 @@ int max_active_clusters(gmapp_ctx *ctx, const Shape &s) {
 // cycles over DSMEM, ~4700 through L2 for the grid exchange); cluster
 // groups beyond the co-resident count run in later waves, a grid-exchange
 // launch must fit in one wave (its groups poll one another).
-double model_cost(const Shape &s, int m, int64_t n_obs_est) {
+// CTAs that share an SM (when the occupancy allows more than one) share its
+// pipes, so the pair loop slows by the number of co-resident CTAs per SM.
+double model_cost(const Shape &s, int m, int64_t n_obs_est, int sm_count) {
     const double shard = static_cast<double>((n_obs_est + s.cluster - 1) / s.cluster);
     const double rate = std::min(7.0, 1.5 + 1.2 * s.ag) * (s.threads >= 384 ? 1.0 : 0.95);
-    const double loop = s.ag * std::max(shard, 64.0) / rate;
+    const double share =
+        std::max(1.0, static_cast<double>(std::min(s.groups, m)) * s.cluster / sm_count);
+    const double loop = s.ag * std::max(shard, 64.0) / rate * share;
     const double chain = (s.grid ? 4700.0 : 3000.0) + 20.0 * s.cluster;
     if (s.grid && s.groups > m) return 1e300;
     const int waves = (s.groups + m - 1) / m;
@@ -172,7 +176,7 @@ gmapp_status pick_tuning_impl(gmapp_ctx *ctx, int64_t cap, int32_t n_agents, boo
                     last_groups = s.groups;
                     const int m = max_active_clusters(ctx, s);
                     if (m <= 0) continue;
-                    const double cost = model_cost(s, m, cap);
+                    const double cost = model_cost(s, m, cap, ctx->sm_count);
                     if (cost < best_cost) {
                         best_cost = cost;
                         *best = gmapp_tuning{C, s.ag, nt, x};
@@ -301,19 +305,12 @@ gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agen
         GMAPP_CHECK_CUDA(cudaLaunchKernelEx(&cfg, s.fn, A));
         return GMAPP_OK;
     }
-    // The grid exchange uses the context's slots and epoch: launches on
-    // different streams are ordered after one another (outside stream
-    // capture; captured launches are ordered by the caller's graph).
-    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
-    GMAPP_CHECK_CUDA(cudaStreamIsCapturing(stream, &cap_status));
-    const bool capturing = cap_status != cudaStreamCaptureStatusNone;
-    if (!capturing && ctx->x_pending) GMAPP_CHECK_CUDA(cudaStreamWaitEvent(stream, ctx->x_done, 0));
+    // the grid exchange uses the context's slots and epoch
+    bool capturing = false;
+    st = grid_exchange_begin(ctx, stream, &capturing);
+    if (st != GMAPP_OK) return st;
     GMAPP_CHECK_CUDA(cudaLaunchKernelEx(&cfg, s.fn, A));
-    if (!capturing) {
-        GMAPP_CHECK_CUDA(cudaEventRecord(ctx->x_done, stream));
-        ctx->x_pending = true;
-    }
-    return GMAPP_OK;
+    return grid_exchange_end(ctx, stream, capturing);
 }
 
 }  // namespace
@@ -353,7 +350,7 @@ extern "C" gmapp_status gmapp_autotune_rollout(gmapp_ctx *ctx, const gmapp_obsta
                     last_groups = s.groups;
                     const int m = max_active_clusters(ctx, s);
                     if (m <= 0) continue;
-                    const double cost = model_cost(s, m, obs->cap);
+                    const double cost = model_cost(s, m, obs->cap, ctx->sm_count);
                     if (cost < 1e299) cands.push_back({cost, gmapp_tuning{C, s.ag, nt, x}});
                 }
             }

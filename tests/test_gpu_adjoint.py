@@ -93,6 +93,48 @@ def test_full_size_sampled_agents_and_fd(gm):
     assert np.all(np.abs(got - gf)[ok] <= GRAD_TOL * scale)
 
 
+def test_many_agents_loop_over_groups(gm):
+    """More agents than the co-resident CTA groups hold at once (2,000 agents
+    on a small obstacle set: every group of CTAs works through several agent
+    groups in one launch); sampled agents vs the oracle adjoint."""
+    w = synth.adjoint_workload(n_obs=600, n_agents=2000, n_steps=64)
+    prm = dataclasses.replace(w["params"], ckpt_every=16)
+    g, _ = _gpu_forward_adjoint(gm, w["obstacles"], w["r_O"], w["agents"], prm)
+    idx = [0, 1, 777, 1500, 1998, 1999]
+    ref = oracle.adjoint(w["obstacles"], w["r_O"], subset_agents(w["agents"], idx), prm)
+    assert _rel_l2(_stack(g, idx), _stack(ref)) <= GRAD_TOL
+    assert np.allclose(g["cost"][idx], ref["cost"], rtol=1e-4, atol=1e-5)
+
+
+@pytest.mark.parametrize("n_obs", [1, 3, 17])
+def test_tiny_obstacle_sets(gm, n_obs):
+    w = synth.adjoint_workload(n_obs=n_obs, n_agents=5, n_steps=45)
+    prm = dataclasses.replace(w["params"], ckpt_every=10)
+    g, _ = _gpu_forward_adjoint(gm, w["obstacles"], w["r_O"], w["agents"], prm)
+    ref = oracle.adjoint(w["obstacles"], w["r_O"], w["agents"], prm)
+    assert _rel_l2(_stack(g), _stack(ref)) <= GRAD_TOL
+    assert np.allclose(g["cost"], ref["cost"], rtol=1e-4, atol=1e-5)
+
+
+def test_adjoint_repeats_bitwise(gm):
+    """Two adjoint passes over the same checkpoints give the same bits (the
+    launch epoch separates their exchange words)."""
+    import torch
+    w = synth.adjoint_workload(n_obs=3000, n_agents=40, n_steps=90)
+    o = gm.Obstacles.from_points(torch.from_numpy(w["obstacles"]), w["r_O"])
+    ag = to_dev_agents(w["agents"])
+    prm = w["params"]
+    out = gm.alloc_rollout_out(40, prm.n_steps)
+    K = int(prm.ckpt_every)
+    out["ckpt"] = torch.empty((prm.n_steps + K - 1) // K, 6, 40, device="cuda")
+    gm.rollout_agents(o, ag, prm, out=out)
+    a = gm.rollout_adjoint(o, ag, prm, out["ckpt"], want_cost=True)
+    b = gm.rollout_adjoint(o, ag, prm, out["ckpt"], want_cost=True)
+    gm.sync()
+    for k in ("g_v0", "g_kr", "g_ka", "g_c", "cost"):
+        assert torch.equal(a[k], b[k]), k
+
+
 def test_autograd_function_matches_adjoint(gm):
     import torch
     w = synth.adjoint_workload(n_obs=4000, n_agents=12, n_steps=120)
