@@ -381,10 +381,12 @@ def _events(torch, stream, fn, reps):
 def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8):
     """The perception filter alone (A1-A3) over a stream of 256 tabletop
     frames (307,200 points each, 944 MB read in total; 64 distinct frames,
-    236 MB, cycled so that no frame is still in L2 when it comes back),
-    issued on 8 CUDA streams with a workspace and an output each, and on one
-    stream back to back.  Algorithmic bytes per frame: 12 B per raw point
-    read + 24 B per obstacle written (centres, key, count, index)."""
+    236 MB, cycled so that no frame is still in L2 when it comes back):
+    through filter_cloud_batch, 32 frames per batch; and frame by frame
+    through filter_cloud, on 8 CUDA streams with a workspace and an output
+    each, and on one stream back to back (both graph-captured).  Algorithmic
+    bytes per frame: 12 B per raw point read + 24 B per obstacle written
+    (centres, key, count, index)."""
     import torch
     import synth
     base_frames = [synth.tabletop_workload(frame_seed=9_000_000 + f, n_agents=1, n_steps=1)
@@ -446,13 +448,39 @@ def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8):
     peak = _measured_peaks().get("hbm_gbs")
     res = {"workload": f"{n_filters} tabletop frames x {n_raw} points ({n_distinct} distinct, "
                        f"{n_distinct * n_raw * 12 / 1e6:.0f} MB), 5 mm voxels",
-           "algorithmic_bytes": byts}
-    for ns in (n_streams, 1):
-        t = run(ns)
+           "algorithmic_bytes": byts, "peak_GB_per_s": peak}
+
+    def entry(t):
         gbs = byts / t / 1e9
-        res[f"streams_{ns}"] = {"ms": 1e3 * t, "us_per_frame": 1e6 * t / n_filters,
-                                "GB_per_s": gbs, "hbm_frac": gbs / peak if peak else None}
-    res["peak_GB_per_s"] = peak
+        return {"ms": 1e3 * t, "us_per_frame": 1e6 * t / n_filters, "GB_per_s": gbs,
+                "hbm_frac": gbs / peak if peak else None}
+
+    # filter_cloud_batch: 32 frames per batch (four launches for all of
+    # them), two batches over the 64 distinct frames, run alternately
+    per = 32
+    batches = [gm.FilterBatch([frames[i] for i in range(b, b + per)], w0["T"], w0["workspace"],
+                              caps=[131072] * per) for b in range(0, n_distinct, per)]
+    cur = torch.cuda.current_stream()
+    for fb in batches:
+        fb.run()
+    torch.cuda.synchronize()
+    for fb, b in zip(batches, range(0, n_distinct, per)):   # N_O agrees with filter_cloud
+        assert [o.count() for o in fb.outs] == n_obs[b:b + per]
+    best = None
+    for _ in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for r in range(n_filters // per):
+            batches[r % len(batches)].run()
+        e1.record(cur)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    res["batched_32"] = entry(best)
+    res["batched_32"]["launches"] = 4 * (n_filters // per)
+    for ns in (n_streams, 1):
+        res[f"per_frame_streams_{ns}"] = entry(run(ns))
+    gm.sync()
     return res
 
 
@@ -503,7 +531,7 @@ def bench_batched(gm, args, reps=3):
                         "100-1000 steps", "interactions_per_batch": inter,
             "batched": {"plans_per_s": 64 / t_batch, "interactions_per_s": inter / t_batch,
                         "ms": 1e3 * t_batch, "tuning_agents_threads": list(tune),
-                        "launches": 8, "graph": True},
+                        "launches": 7, "graph": True},
             "plain": {"plans_per_s": 64 / t_plain, "interactions_per_s": inter / t_plain,
                       "ms": 1e3 * t_plain, "launches": 64 * LAUNCHES_PER_STEP},
             "speedup": t_plain / t_batch}

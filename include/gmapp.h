@@ -152,6 +152,33 @@ gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, const float T
                                   const gmapp_workspace *ws, gmapp_obstacles *out,
                                   gmapp_stream stream);
 
+/* Batched filter: many clouds (a stream of frames, or several sensors) through
+ * one sequence of four launches (Sec. IV-B, Sec. V-A, as filter_cloud).  The
+ * jobs are fixed at creation (their device pointers are kept); each run
+ * filters every job's cloud into its obstacle buffers with results
+ * bit-identical to filter_cloud on the same cloud. */
+typedef struct {
+    const float *xyz;     /* device, n_raw x 3 float32 AoS, 16-byte aligned */
+    int64_t n_raw;        /* >= 0 points */
+    float T[12];          /* camera-to-world transform, row-major 3x4 */
+    gmapp_workspace ws;   /* voxel grid; min_pts must be 1 */
+    gmapp_obstacles out;  /* caller-owned output buffers; out.n receives N_O */
+} gmapp_cloud_job;
+
+typedef struct gmapp_filter_batch gmapp_filter_batch;
+
+/* Checks every job (GMAPP_ERR_INVALID_ARG names the first bad one), keeps the
+ * job table on the device and allocates the jobs' scratch once (the library
+ * owns it; freed by gmapp_filter_batch_destroy).  Synchronous. */
+gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cloud_job *jobs,
+                                       int32_t n_jobs, gmapp_filter_batch **out);
+void gmapp_filter_batch_destroy(gmapp_filter_batch *fb);
+
+/* Filters every job's cloud: four launches on `stream` whatever the number of
+ * jobs (graph-capturable; allocates nothing).  Output overflow of a job sets
+ * GMAPP_DEVERR_CAPACITY and its out.n > out.cap. */
+gmapp_status filter_cloud_batch(gmapp_filter_batch *fb, gmapp_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* Rollout: rollout_agents (Sec. IV-A agent dynamics and agent set;           */
 /* Eq. (mfi) circular-field force; Alg. 1 clamp, detection gate, sum)         */

@@ -22,7 +22,8 @@ from ._abi import check
 
 __all__ = ["Context", "context", "Obstacles", "filter_cloud", "filter_cloud_noalloc",
            "filter_workspace_bytes", "rollout_agents", "score_and_select", "pick_tuning",
-           "autotune_rollout", "rollout_adjoint", "GMappRollout", "sync", "GmappError"]
+           "autotune_rollout", "rollout_adjoint", "GMappRollout", "sync", "GmappError",
+           "FilterBatch", "Batch", "Server"]
 
 GmappError = _abi.GmappError
 
@@ -425,6 +426,49 @@ def __getattr__(name):
 # ---------------------------------------------------------------------------
 # Batched uneven queries
 # ---------------------------------------------------------------------------
+
+class FilterBatch:
+    """Many clouds through one batched filter (four launches for all of them,
+    results bit-identical to filter_cloud per cloud).  ``clouds``: list of
+    device [N, 3] float32 tensors (kept, not copied: refill them in place
+    between runs); ``T`` and ``ws`` are shared by all clouds, or lists of one
+    per cloud.  ``outs[q]`` is cloud q's obstacle set after run()."""
+
+    def __init__(self, clouds: list, T, ws, caps=None):
+        ctx = context()
+        n = len(clouds)
+        import numpy as np
+        Ts = list(T) if np.ndim(T) == 2 else [T] * n
+        wss = ws if isinstance(ws, (list, tuple)) else [ws] * n
+        self._keep = list(clouds)
+        self.outs = []
+        arr = (_abi.CloudJob * n)()
+        for q, xyz in enumerate(clouds):
+            cap = int(caps[q]) if caps is not None else max(4, (int(xyz.shape[0]) + 3) // 4 * 4)
+            out = Obstacles.empty(cap)
+            out.r_O = 0.5 * float(wss[q].voxel)
+            self.outs.append(out)
+            J = arr[q]
+            J.xyz = xyz.data_ptr()
+            J.n_raw = int(xyz.shape[0])
+            for i, v in enumerate(list(Ts[q])):
+                J.T[i] = float(v)
+            J.ws = _ws_struct(wss[q])
+            J.out = out._struct()
+        h = C.c_void_p()
+        check(_abi.load().gmapp_filter_batch_create(ctx.handle, arr, n, C.byref(h)),
+              "gmapp_filter_batch_create")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _abi._lib is not None:
+            _abi._lib.gmapp_filter_batch_destroy(h)
+            self.handle = None
+
+    def run(self, stream=None) -> None:
+        check(_abi.load().filter_cloud_batch(self.handle, _stream(stream)), "filter_cloud_batch")
+
 
 class Batch:
     """Many planning queries through one fixed launch sequence (batched

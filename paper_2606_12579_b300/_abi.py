@@ -29,6 +29,11 @@ class Obstacles(C.Structure):
                 ("n", P), ("cap", C.c_int64), ("r_O", C.c_float)]
 
 
+class CloudJob(C.Structure):
+    _fields_ = [("xyz", P), ("n_raw", C.c_int64), ("T", C.c_float * 12), ("ws", Workspace),
+                ("out", Obstacles)]
+
+
 class Agents(C.Structure):
     _fields_ = [("p0", P), ("v0", P), ("c", P), ("k_r", P), ("k_a", P), ("r_d", P), ("r_a", P),
                 ("n", C.c_int32)]
@@ -116,6 +121,9 @@ PROTOTYPES = {
     "rollout_adjoint": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
                                   C.POINTER(RolloutParams), C.POINTER(CostWeights), P, P,
                                   C.POINTER(AdjointOut), P, C.c_size_t, P]),
+    "gmapp_filter_batch_create": (C.c_int, [P, C.POINTER(CloudJob), C.c_int32, C.POINTER(P)]),
+    "gmapp_filter_batch_destroy": (None, [P]),
+    "filter_cloud_batch": (C.c_int, [P, P]),
     "gmapp_batch_create": (C.c_int, [P, C.POINTER(Query), C.c_int32, C.POINTER(P)]),
     "gmapp_batch_destroy": (None, [P]),
     "gmapp_batch_set_tuning": (C.c_int, [P, C.c_int32, C.c_int32]),

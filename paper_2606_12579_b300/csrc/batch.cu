@@ -2,12 +2,13 @@
 // hot path of Sec. IV-B (perception) and Sec. IV-A/IV-C (rollout, cost,
 // selection); the paper runs one query per kernel launch per agent per step
 // (Alg. 1), this module runs a whole batch of queries in a fixed sequence of
-// eight launches that can be captured once in a CUDA graph:
+// seven launches that can be captured once in a CUDA graph:
 //
-//   kb_zero, kb_keys, kb_bitmap_sums, kb_emit, kb_count
+//   kb_keys, kb_bitmap_sums, kb_emit, kb_count
 //        the filter stages of every query in one launch each (a block ->
 //        query table maps blocks to queries; same binary32 sequence as
-//        filter_cloud, from filter_device.cuh)
+//        filter_cloud, from filter_device.cuh; the scratch is zeroed at
+//        creation and kb_emit leaves it clear, so no clearing launch)
 //   kb_plan   one CTA: publishes each query's N_O and orders the work items
 //        (query, agent group) by their cost N_a,item x N_O x N_k, largest
 //        first (longest-processing-time order), into a device queue
@@ -40,8 +41,9 @@ struct QueryDev {
     const float *xyz;
     int64_t n_raw;
     FilterArgs fa;
-    uint32_t *bitmap, *prefix, *sums, *offsets, *counters, *keys;
-    int32_t pt_blk0, pt_nblk, bm_blk0, bm_nblk;
+    uint32_t *bitmap, *chunk, *sums, *offsets, *counters, *keys;
+    uint2 *pw;
+    int32_t pt_blk0, pt_nblk, bm_blk0, bm_nblk, sb_blk0, sb_nblk;
     // obstacle set S_W of the query
     float *ox, *oy, *oz;
     uint32_t *okeys, *ocounts, *orep;
@@ -66,7 +68,7 @@ struct QueryDev {
 struct BatchDev {
     const QueryDev *q;
     int32_t n_q;
-    const int32_t *pt_map, *bm_map;
+    const int32_t *pt_map, *bm_map, *sb_map;
     const int32_t *items_static;  // item -> (query << 16) | group, in query order
     int32_t *items;               // the planned queue
     int32_t n_items;
@@ -75,36 +77,28 @@ struct BatchDev {
     uint32_t *err;
 };
 
-__global__ void __launch_bounds__(kThreads) kb_zero(const BatchDev B) {
-    const QueryDev &Q = B.q[B.bm_map[blockIdx.x]];
-    const int64_t blk = blockIdx.x - Q.bm_blk0;
-    // one block clears 1024 bitmap words of its query
-    reinterpret_cast<uint4 *>(Q.bitmap)[blk * kThreads + threadIdx.x] = make_uint4(0, 0, 0, 0);
-    if (blk == 0 && threadIdx.x < 16) Q.counters[threadIdx.x] = 0;
-}
-
 __global__ void __launch_bounds__(kThreads) kb_keys(const BatchDev B) {
     const QueryDev &Q = B.q[B.pt_map[blockIdx.x]];
     const FilterArgs fa = Q.fa;
     keys_range(Q.xyz, Q.n_raw, fa, Q.keys, Q.bitmap, blockIdx.x - Q.pt_blk0, Q.pt_nblk);
 }
 
-__global__ void __launch_bounds__(kThreads) kb_bitmap_sums(const BatchDev B) {
-    const QueryDev &Q = B.q[B.bm_map[blockIdx.x]];
-    bitmap_sums_block(Q.bitmap, Q.sums, Q.offsets, Q.counters, Q.counters + 1,
-                      blockIdx.x - Q.bm_blk0, Q.bm_nblk);
+__global__ void __launch_bounds__(kBmThreads) kb_bitmap_sums(const BatchDev B) {
+    const QueryDev &Q = B.q[B.sb_map[blockIdx.x]];
+    bitmap_sums_block(Q.bitmap, Q.chunk, Q.sums, Q.offsets, Q.counters, Q.counters + 1,
+                      blockIdx.x - Q.sb_blk0, Q.sb_nblk);
 }
 
-__global__ void __launch_bounds__(kThreads) kb_emit(const BatchDev B) {
+__global__ void __launch_bounds__(kBmThreads) kb_emit(const BatchDev B) {
     const QueryDev &Q = B.q[B.bm_map[blockIdx.x]];
     const FilterArgs fa = Q.fa;
     EmitOut o{Q.okeys, Q.ocounts, Q.orep, Q.ox, Q.oy, Q.oz, Q.cap};
-    emit_block(Q.bitmap, Q.offsets, Q.prefix, fa, o, blockIdx.x - Q.bm_blk0);
+    emit_block(Q.bitmap, Q.offsets, Q.chunk, Q.pw, fa, o, blockIdx.x - Q.bm_blk0, true);
 }
 
 __global__ void __launch_bounds__(kThreads) kb_count(const BatchDev B) {
     const QueryDev &Q = B.q[B.pt_map[blockIdx.x]];
-    count_range(Q.keys, Q.n_raw, Q.bitmap, Q.prefix, Q.ocounts, Q.orep, Q.cap,
+    count_range(Q.keys, Q.n_raw, Q.pw, Q.ocounts, Q.orep, Q.cap,
                 blockIdx.x - Q.pt_blk0, Q.pt_nblk);
 }
 
@@ -325,11 +319,11 @@ struct gmapp_batch {
     int32_t n_q = 0;
     std::vector<QueryDev> hq;
     QueryDev *d_q = nullptr;
-    int32_t *d_pt_map = nullptr, *d_bm_map = nullptr;
+    int32_t *d_pt_map = nullptr, *d_bm_map = nullptr, *d_sb_map = nullptr;
     int32_t *d_items_static = nullptr, *d_items = nullptr;
     uint32_t *d_head = nullptr;
     void *d_ws = nullptr;
-    int32_t pt_blocks = 0, bm_blocks = 0, n_items = 0, shard_cap = 0;
+    int32_t pt_blocks = 0, bm_blocks = 0, sb_blocks = 0, n_items = 0, shard_cap = 0;
     int64_t max_cap = 4;  // largest obstacle capacity over the queries
     bool clear = false;
     int32_t agents_per_item = 8, threads = 256;
@@ -348,6 +342,7 @@ void release(gmapp_batch *b) {
     cudaFree(b->d_q);
     cudaFree(b->d_pt_map);
     cudaFree(b->d_bm_map);
+    cudaFree(b->d_sb_map);
     cudaFree(b->d_items_static);
     cudaFree(b->d_items);
     cudaFree(b->d_head);
@@ -434,6 +429,7 @@ BatchDev dev_view(const gmapp_batch *b) {
     B.n_q = b->n_q;
     B.pt_map = b->d_pt_map;
     B.bm_map = b->d_bm_map;
+    B.sb_map = b->d_sb_map;
     B.items_static = b->d_items_static;
     B.items = b->d_items;
     B.n_items = b->n_items;
@@ -456,7 +452,7 @@ extern "C" gmapp_status gmapp_batch_create(gmapp_ctx *ctx, const gmapp_query *qu
     b->ctx = ctx;
     b->n_q = n_q;
     b->hq.resize(n_q);
-    std::vector<int32_t> pt_map, bm_map;
+    std::vector<int32_t> pt_map, bm_map, sb_map;
     std::vector<size_t> ws_off(n_q);
     size_t ws_total = 0;
     int64_t max_cap = 4;
@@ -519,6 +515,9 @@ extern "C" gmapp_status gmapp_batch_create(gmapp_ctx *ctx, const gmapp_query *qu
         D.bm_blk0 = static_cast<int32_t>(bm_map.size());
         D.bm_nblk = static_cast<int32_t>(L.n_blocks);
         for (int i = 0; i < D.bm_nblk; ++i) bm_map.push_back(q);
+        D.sb_blk0 = static_cast<int32_t>(sb_map.size());
+        D.sb_nblk = static_cast<int32_t>(L.n_sblocks);
+        for (int i = 0; i < D.sb_nblk; ++i) sb_map.push_back(q);
         D.ox = o.x;
         D.oy = o.y;
         D.oz = o.z;
@@ -563,11 +562,16 @@ extern "C" gmapp_status gmapp_batch_create(gmapp_ctx *ctx, const gmapp_query *qu
     }
     b->pt_blocks = static_cast<int32_t>(pt_map.size());
     b->bm_blocks = static_cast<int32_t>(bm_map.size());
+    b->sb_blocks = static_cast<int32_t>(sb_map.size());
     b->max_cap = max_cap;
     cudaError_t e = cudaMalloc(&b->d_ws, std::max<size_t>(ws_total, 256));
+    // zero filter scratch: bitmaps and counters start clear, and each run
+    // leaves them clear again (kb_emit clears the bitmap behind it)
+    if (e == cudaSuccess) e = cudaMemset(b->d_ws, 0, std::max<size_t>(ws_total, 256));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_q, sizeof(QueryDev) * n_q);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_pt_map, sizeof(int32_t) * pt_map.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->d_bm_map, sizeof(int32_t) * bm_map.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sb_map, sizeof(int32_t) * sb_map.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items_static, sizeof(int32_t) * kMaxItems);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int32_t) * kMaxItems);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_head, sizeof(uint32_t));
@@ -576,6 +580,9 @@ extern "C" gmapp_status gmapp_batch_create(gmapp_ctx *ctx, const gmapp_query *qu
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_bm_map, bm_map.data(), sizeof(int32_t) * bm_map.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_sb_map, sb_map.data(), sizeof(int32_t) * sb_map.size(),
                        cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         gmapp_status st = cuda_fail(e, "gmapp_batch_create");
@@ -589,7 +596,8 @@ extern "C" gmapp_status gmapp_batch_create(gmapp_ctx *ctx, const gmapp_query *qu
         char *base = ws + ws_off[q];
         QueryDev &D = b->hq[q];
         D.bitmap = reinterpret_cast<uint32_t *>(base + L.off_bitmap);
-        D.prefix = reinterpret_cast<uint32_t *>(base + L.off_prefix);
+        D.pw = reinterpret_cast<uint2 *>(base + L.off_pw);
+        D.chunk = reinterpret_cast<uint32_t *>(base + L.off_chunk);
         D.sums = reinterpret_cast<uint32_t *>(base + L.off_sums);
         D.offsets = reinterpret_cast<uint32_t *>(base + L.off_offsets);
         D.counters = reinterpret_cast<uint32_t *>(base + L.off_counters);
@@ -626,10 +634,9 @@ extern "C" gmapp_status rollout_batch(gmapp_batch *b, gmapp_stream stream) {
         return GMAPP_ERR_INVALID_ARG;
     }
     const BatchDev B = dev_view(b);
-    kb_zero<<<b->bm_blocks, kThreads, 0, stream>>>(B);
     kb_keys<<<b->pt_blocks, kThreads, 0, stream>>>(B);
-    kb_bitmap_sums<<<b->bm_blocks, kThreads, 0, stream>>>(B);
-    kb_emit<<<b->bm_blocks, kThreads, 0, stream>>>(B);
+    kb_bitmap_sums<<<b->sb_blocks, kBmThreads, 0, stream>>>(B);
+    kb_emit<<<b->bm_blocks, kBmThreads, 0, stream>>>(B);
     kb_count<<<b->pt_blocks, kThreads, 0, stream>>>(B);
     kb_plan<<<1, 1024, b->n_items * sizeof(float), stream>>>(B, b->agents_per_item);
     cudaLaunchConfig_t cfg = {};

@@ -80,7 +80,8 @@ extern "C" gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n
 
     char *base = static_cast<char *>(workspace);
     uint32_t *bitmap = reinterpret_cast<uint32_t *>(base + L.off_bitmap);
-    uint32_t *prefix = reinterpret_cast<uint32_t *>(base + L.off_prefix);
+    uint2 *pw = reinterpret_cast<uint2 *>(base + L.off_pw);
+    uint32_t *chunk = reinterpret_cast<uint32_t *>(base + L.off_chunk);
     uint32_t *sums = reinterpret_cast<uint32_t *>(base + L.off_sums);
     uint32_t *offsets = reinterpret_cast<uint32_t *>(base + L.off_offsets);
     uint32_t *counters = reinterpret_cast<uint32_t *>(base + L.off_counters);
@@ -96,13 +97,13 @@ extern "C" gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n
     k_zero<<<grid_zero, kThreads, 0, stream>>>(reinterpret_cast<uint4 *>(bitmap), L.n_words / 4,
                                                counters, 16);
     k_keys<<<grid_pts, kThreads, 0, stream>>>(xyz, n_raw, A, keys, bitmap);
-    k_bitmap_sums<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, sums, offsets,
+    k_bitmap_sums<<<static_cast<int>(L.n_sblocks), kBmThreads, 0, stream>>>(bitmap, chunk, sums, offsets,
                                                                           counters, n_occ);
     if (ws->min_pts == 1) {
         EmitOut o{out->keys, out->counts, out->rep_idx, out->x, out->y, out->z, out->cap};
-        k_emit<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, offsets, prefix, A, o,
+        k_emit<<<static_cast<int>(L.n_blocks), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, o,
                                                                       n_occ, out->n, ctx->d_err);
-        k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, bitmap, prefix, out->counts,
+        k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, pw, out->counts,
                                                    out->rep_idx, out->cap);
     } else {
         uint32_t *tkeys = reinterpret_cast<uint32_t *>(base + L.off_tkeys);
@@ -111,9 +112,9 @@ extern "C" gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n
         uint32_t *tsums = reinterpret_cast<uint32_t *>(base + L.off_tsums);
         uint32_t *toffsets = reinterpret_cast<uint32_t *>(base + L.off_toffsets);
         EmitOut t{tkeys, tcounts, trep, nullptr, nullptr, nullptr, L.n_tmp};
-        k_emit<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, offsets, prefix, A, t,
+        k_emit<<<static_cast<int>(L.n_blocks), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, t,
                                                                       nullptr, nullptr, nullptr);
-        k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, bitmap, prefix, tcounts, trep,
+        k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, pw, tcounts, trep,
                                                    L.n_tmp);
         k_keep_sums<<<static_cast<int>(L.n_tblocks), kThreads, 0, stream>>>(
             tcounts, n_occ, ws->min_pts, tsums, toffsets, n_keep_counter, out->n, out->cap,
@@ -238,7 +239,8 @@ extern "C" gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, co
 
     char *base = static_cast<char *>(sym.scratch);
     uint32_t *bitmap = reinterpret_cast<uint32_t *>(base + L.off_bitmap);
-    uint32_t *prefix = reinterpret_cast<uint32_t *>(base + L.off_prefix);
+    uint2 *pw = reinterpret_cast<uint2 *>(base + L.off_pw);
+    uint32_t *chunk = reinterpret_cast<uint32_t *>(base + L.off_chunk);
     uint32_t *sums = reinterpret_cast<uint32_t *>(base + L.off_sums);
     uint32_t *offsets = reinterpret_cast<uint32_t *>(base + L.off_offsets);
     uint32_t *counters = reinterpret_cast<uint32_t *>(base + L.off_counters);
@@ -256,13 +258,13 @@ extern "C" gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, co
     k_zero<<<grid_zero, kThreads, 0, stream>>>(reinterpret_cast<uint4 *>(bitmap), L.n_words / 4,
                                                counters, 16);
     k_keys<<<grid_pts, kThreads, 0, stream>>>(xyz, n_raw, A, keys, bitmap);
-    k_bitmap_sums<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, sums, offsets,
+    k_bitmap_sums<<<static_cast<int>(L.n_sblocks), kBmThreads, 0, stream>>>(bitmap, chunk, sums, offsets,
                                                                           counters, n_occ);
     if (ws->min_pts == 1) {
         EmitOut o{out->keys, out->counts, out->rep_idx, out->x, out->y, out->z, out->cap};
-        k_emit<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, offsets, prefix, A, o,
+        k_emit<<<static_cast<int>(L.n_blocks), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, o,
                                                                       n_occ, out->n, sym.err);
-        k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, bitmap, prefix, out->counts,
+        k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, pw, out->counts,
                                                    out->rep_idx, out->cap);
     } else {
         uint32_t *tkeys = reinterpret_cast<uint32_t *>(base + L.off_tkeys);
@@ -271,9 +273,9 @@ extern "C" gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, co
         uint32_t *tsums = reinterpret_cast<uint32_t *>(base + L.off_tsums);
         uint32_t *toffsets = reinterpret_cast<uint32_t *>(base + L.off_toffsets);
         EmitOut t{tkeys, tcounts, trep, nullptr, nullptr, nullptr, L.n_tmp};
-        k_emit<<<static_cast<int>(L.n_blocks), kThreads, 0, stream>>>(bitmap, offsets, prefix, A, t,
+        k_emit<<<static_cast<int>(L.n_blocks), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, t,
                                                                       nullptr, nullptr, nullptr);
-        k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, bitmap, prefix, tcounts, trep,
+        k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, pw, tcounts, trep,
                                                    L.n_tmp);
         k_keep_sums<<<static_cast<int>(L.n_tblocks), kThreads, 0, stream>>>(
             tcounts, n_occ, ws->min_pts, tsums, toffsets, n_keep_counter, out->n, out->cap,

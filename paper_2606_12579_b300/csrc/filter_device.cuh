@@ -14,8 +14,21 @@ namespace {
 
 constexpr uint32_t kInvalid = 0xFFFFFFFFu;
 constexpr int kThreads = 256;
-constexpr int kWordsPerThread = 4;
-constexpr int kWordsPerBlock = kThreads * kWordsPerThread;  // 1024 words = 32768 cells
+// Bitmap kernels.  A chunk is 32 words (one warp, one word per lane).
+// k_bitmap_sums: 256 threads x 16 words = 4096 words (128 chunks) per
+// block; per-chunk popcount offsets within the block and the block total.
+// k_emit: 1024 words per block, 4 chunks per warp, warps independent (no
+// block barrier), so empty stretches cost one load and a dense stretch (a
+// table plane fills whole words) spreads over many warps.
+constexpr int kBmThreads = 256;
+constexpr int kChunkWords = 32;
+constexpr int kChunksPerWarp = 4;
+constexpr int kWordsPerBlock = kBmThreads * kChunksPerWarp;  // emit block: 1024 words
+constexpr int kWordsPerSumBlock = 4096;
+constexpr int kChunksPerSumBlock = kWordsPerSumBlock / kChunkWords;
+static_assert(kWordsPerSumBlock % kWordsPerBlock == 0, "emit blocks tile the sum blocks");
+// min_pts > 1 compaction: 4 temporary entries per thread.
+constexpr int kKeepPerBlock = kThreads * 4;
 
 struct FilterArgs {
     float T[12];
@@ -43,15 +56,22 @@ __device__ __forceinline__ uint32_t voxel_key(float x, float y, float z, const F
     return (idx[2] * A.ny + idx[1]) * A.nx + idx[0];
 }
 
-__device__ __forceinline__ void voxel_centre(uint32_t key, const FilterArgs &A, float &cx,
-                                             float &cy, float &cz) {
-    uint32_t ix = key % A.nx;
-    uint32_t r = key / A.nx;
-    uint32_t iy = r % A.ny;
-    uint32_t iz = r / A.ny;
+// Centre of cell (ix, iy, iz): lo + ((float)i + 0.5) voxel per axis, exact
+// binary32 sequence.
+__device__ __forceinline__ void cell_centre(uint32_t ix, uint32_t iy, uint32_t iz,
+                                            const FilterArgs &A, float &cx, float &cy, float &cz) {
     cx = __fadd_rn(A.lo[0], __fmul_rn(__fadd_rn(static_cast<float>(ix), 0.5f), A.voxel));
     cy = __fadd_rn(A.lo[1], __fmul_rn(__fadd_rn(static_cast<float>(iy), 0.5f), A.voxel));
     cz = __fadd_rn(A.lo[2], __fmul_rn(__fadd_rn(static_cast<float>(iz), 0.5f), A.voxel));
+}
+
+__device__ __forceinline__ void voxel_centre(uint32_t key, const FilterArgs &A, float &cx,
+                                             float &cy, float &cz) {
+    const uint32_t r = key / A.nx;
+    const uint32_t ix = key - r * A.nx;
+    const uint32_t iz = r / A.ny;
+    const uint32_t iy = r - iz * A.ny;
+    cell_centre(ix, iy, iz, A, cx, cy, cz);
 }
 
 __global__ void k_zero(uint4 *words, int64_t n_vec, uint32_t *counters, int n_counters) {
@@ -89,6 +109,7 @@ __device__ __forceinline__ void keys_range(const float *__restrict__ xyz, int64_
                                            int64_t blk, int64_t nblk) {
     const int64_t n4 = n / 4;
     const int64_t stride = nblk * (int64_t)kThreads;
+#pragma unroll 2
     for (int64_t g = blk * (int64_t)kThreads + threadIdx.x; g < n4; g += stride) {
         const float4 *src = reinterpret_cast<const float4 *>(xyz) + 3 * g;
         float4 a0 = __ldcs(src), a1 = __ldcs(src + 1), a2 = __ldcs(src + 2);
@@ -120,7 +141,8 @@ __global__ void __launch_bounds__(kThreads) k_keys(const float *__restrict__ xyz
     keys_range(xyz, n, A, keys, bitmap, blockIdx.x, gridDim.x);
 }
 
-// Block-wide exclusive scan of one uint32 per thread (kThreads threads).
+// Block-wide exclusive scan of one uint32 per thread (NTH threads).
+template <int NTH>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_tot,
                                                          uint32_t &block_total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -133,31 +155,32 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *w
     if (lane == 31) warp_tot[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        uint32_t t = lane < kThreads / 32 ? warp_tot[lane] : 0;
+        uint32_t t = lane < NTH / 32 ? warp_tot[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
             if (lane >= o) t += y;
         }
-        if (lane < kThreads / 32) warp_tot[lane] = t;  // inclusive
+        if (lane < NTH / 32) warp_tot[lane] = t;  // inclusive
     }
     __syncthreads();
     uint32_t before = warp ? warp_tot[warp - 1] : 0;
-    block_total = warp_tot[kThreads / 32 - 1];
+    block_total = warp_tot[NTH / 32 - 1];
     __syncthreads();
     return before + x - v;
 }
 
 // Exclusive scan of `n` block sums by ONE block (the last one to finish);
 // writes offsets[] and returns the grand total to thread 0.
+template <int NTH>
 __device__ uint32_t scan_block_sums(const uint32_t *sums, uint32_t *offsets, int64_t n,
                                     uint32_t *warp_tot) {
-    const int64_t per = (n + kThreads - 1) / kThreads;
+    const int64_t per = (n + NTH - 1) / NTH;
     const int64_t b0 = threadIdx.x * per;
     uint32_t local = 0;
     for (int64_t i = b0; i < b0 + per && i < n; ++i) local += __ldcg(&sums[i]);
     uint32_t total;
-    uint32_t run = block_exclusive_scan(local, warp_tot, total);
+    uint32_t run = block_exclusive_scan<NTH>(local, warp_tot, total);
     for (int64_t i = b0; i < b0 + per && i < n; ++i) {
         uint32_t s = __ldcg(&sums[i]);
         offsets[i] = run;
@@ -166,19 +189,30 @@ __device__ uint32_t scan_block_sums(const uint32_t *sums, uint32_t *offsets, int
     return total;
 }
 
-// Per block of 1024 bitmap words: popcount sum.  The last block scans all
-// block sums into offsets and publishes the total number of occupied voxels.
+// Per block of kWordsPerSumBlock bitmap words: each 32-word chunk's
+// exclusive popcount prefix within the block (chunk_off) and the block
+// total.  The last block to finish scans all block totals into offsets and
+// publishes the total number of occupied voxels.
 __device__ __forceinline__ void bitmap_sums_block(const uint32_t *__restrict__ bitmap,
-                                                          uint32_t *sums, uint32_t *offsets,
-                                                          uint32_t *counter, uint32_t *n_occ,
-                                                  int64_t blk, int64_t nblk) {
-    __shared__ uint32_t warp_tot[kThreads / 32];
+                                                  uint32_t *chunk_off, uint32_t *sums,
+                                                  uint32_t *offsets, uint32_t *counter,
+                                                  uint32_t *n_occ, int64_t blk, int64_t nblk) {
+    __shared__ uint32_t warp_tot[kBmThreads / 32];
     __shared__ bool is_last;
-    const uint4 w = reinterpret_cast<const uint4 *>(bitmap)[blk * kThreads + threadIdx.x];
-    uint32_t c = __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
+    const int t = threadIdx.x;
+    const uint4 *src = reinterpret_cast<const uint4 *>(bitmap + blk * kWordsPerSumBlock + 16 * t);
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint4 w = src[k];
+        c += __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
+    }
+    // a chunk is two consecutive threads: the even one carries its sum
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
     uint32_t tot;
-    block_exclusive_scan(c, warp_tot, tot);
-    if (threadIdx.x == 0) {
+    const uint32_t excl = block_exclusive_scan<kBmThreads>((t & 1) ? 0u : c, warp_tot, tot);
+    if (!(t & 1)) chunk_off[blk * kChunksPerSumBlock + (t >> 1)] = excl;
+    if (t == 0) {
         sums[blk] = tot;
         __threadfence();
         is_last = atomicAdd(counter, 1u) == nblk - 1;
@@ -186,17 +220,18 @@ __device__ __forceinline__ void bitmap_sums_block(const uint32_t *__restrict__ b
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    uint32_t total = scan_block_sums(sums, offsets, nblk, warp_tot);
-    if (threadIdx.x == 0) {
+    uint32_t total = scan_block_sums<kBmThreads>(sums, offsets, nblk, warp_tot);
+    if (t == 0) {
         *n_occ = total;
         *counter = 0;
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_bitmap_sums(const uint32_t *__restrict__ bitmap,
-                                                          uint32_t *sums, uint32_t *offsets,
-                                                          uint32_t *counter, uint32_t *n_occ) {
-    bitmap_sums_block(bitmap, sums, offsets, counter, n_occ, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(kBmThreads) k_bitmap_sums(const uint32_t *__restrict__ bitmap,
+                                                            uint32_t *chunk_off, uint32_t *sums,
+                                                            uint32_t *offsets, uint32_t *counter,
+                                                            uint32_t *n_occ) {
+    bitmap_sums_block(bitmap, chunk_off, sums, offsets, counter, n_occ, blockIdx.x, gridDim.x);
 }
 
 struct EmitOut {
@@ -205,51 +240,80 @@ struct EmitOut {
     int64_t cap;
 };
 
-// Per word: rank of its first set bit = block offset + in-block prefix.
-// Every set bit becomes one output entry (key, centre, count = 0, rep = ~0).
-// Emission is warp-cooperative: each warp walks its 128 words of the block
-// (staged in shared memory), skips empty ones by ballot, and lane b writes
-// the entry of bit b, so a fully occupied word costs one pass of 32 lanes
-// with consecutive (coalesced) ranks instead of 32 serial iterations.
-__device__ __forceinline__ void emit_block(const uint32_t *__restrict__ bitmap,
+// Per word: rank of its first set bit = sum-block offset + chunk offset +
+// in-chunk prefix (a warp scan), stored with the word itself as
+// pw[w] = (rank, bits) for k_count (occupied words only: no point maps to
+// an empty one).  Every set bit becomes one output entry (key, centre,
+// count = 0, rep = ~0).  With `zero`, the occupied words are
+// cleared after use (library-owned scratch stays ready for the next run
+// without a clearing launch).
+__device__ __forceinline__ void emit_block(uint32_t *__restrict__ bitmap,
                                            const uint32_t *__restrict__ offsets,
-                                           uint32_t *__restrict__ word_prefix, FilterArgs A,
-                                           EmitOut o, int64_t blk) {
-    __shared__ uint32_t warp_tot[kThreads / 32];
-    __shared__ __align__(16) uint32_t s_words[kWordsPerBlock];
-    __shared__ __align__(16) uint32_t s_pre[kWordsPerBlock];
-    const int64_t wv = blk * (int64_t)kThreads + threadIdx.x;
-    const uint4 w = reinterpret_cast<const uint4 *>(bitmap)[wv];
-    uint32_t c0 = __popc(w.x), c1 = __popc(w.y), c2 = __popc(w.z), c3 = __popc(w.w);
-    uint32_t tot;
-    uint32_t base = offsets[blk] + block_exclusive_scan(c0 + c1 + c2 + c3, warp_tot, tot);
-    uint4 pre = make_uint4(base, base + c0, base + c0 + c1, base + c0 + c1 + c2);
-    reinterpret_cast<uint4 *>(word_prefix)[wv] = pre;
-    reinterpret_cast<uint4 *>(s_words)[threadIdx.x] = w;
-    reinterpret_cast<uint4 *>(s_pre)[threadIdx.x] = pre;
-    __syncthreads();
+                                           const uint32_t *__restrict__ chunk_off,
+                                           uint2 *__restrict__ pw, FilterArgs A, EmitOut o,
+                                           int64_t blk, bool zero) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t below = (1u << lane) - 1u;
-    constexpr int kWordsPerWarp = kWordsPerBlock / (kThreads / 32);
+    const int64_t c0 = (blk * (kBmThreads / 32) + warp) * kChunksPerWarp;
+    uint32_t w[kChunksPerWarp];
+#pragma unroll
+    for (int j = 0; j < kChunksPerWarp; ++j) w[j] = bitmap[(c0 + j) * kChunkWords + lane];
 #pragma unroll 1
-    for (int c = 0; c < kWordsPerWarp; c += 32) {
-        const int i0 = warp * kWordsPerWarp + c;
-        uint32_t nz = __ballot_sync(0xffffffffu, s_words[i0 + lane] != 0u);
+    for (int j = 0; j < kChunksPerWarp; ++j) {
+        if (!__ballot_sync(0xffffffffu, w[j] != 0u)) continue;
+        const int64_t c = c0 + j;
+        const uint32_t cnt = __popc(w[j]);
+        uint32_t x = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        const uint32_t pre = offsets[c / kChunksPerSumBlock] + chunk_off[c] + x - cnt;
+        const int64_t wv = c * kChunkWords + lane;
+        if (w[j]) {
+            pw[wv] = make_uint2(pre, w[j]);
+            if (zero) bitmap[wv] = 0u;
+        }
+        // lane per bit: for each occupied word (warp-uniform loop), lane b
+        // writes the entry of bit b, so the ranks of a word are consecutive
+        // and its stores coalesce; each lane first finds the cell
+        // coordinates of its own word's first cell (one division chain per
+        // word), which the loop broadcasts
+        uint32_t ix0 = 0, iy0 = 0, iz0 = 0;
+        if (w[j]) {
+            const uint32_t key0 = static_cast<uint32_t>(wv) * 32u;
+            const uint32_t q = key0 / A.nx;
+            ix0 = key0 - q * A.nx;
+            iz0 = q / A.ny;
+            iy0 = q - iz0 * A.ny;
+        }
+        const uint32_t below = (1u << lane) - 1u;
+        uint32_t nz = __ballot_sync(0xffffffffu, w[j] != 0u);
         while (nz) {
-            const int i = i0 + __ffs(nz) - 1;
+            const int i = __ffs(nz) - 1;
             nz &= nz - 1;
-            const uint32_t bits = s_words[i];
+            const uint32_t bits = __shfl_sync(0xffffffffu, w[j], i);
+            const uint32_t p0 = __shfl_sync(0xffffffffu, pre, i);
+            const uint32_t bx = __shfl_sync(0xffffffffu, ix0, i);
+            const uint32_t by = __shfl_sync(0xffffffffu, iy0, i);
+            const uint32_t bz = __shfl_sync(0xffffffffu, iz0, i);
             if ((bits >> lane) & 1u) {
-                const uint32_t rank = s_pre[i] + __popc(bits & below);
+                const uint32_t rank = p0 + __popc(bits & below);
                 if (rank < o.cap) {
-                    const uint32_t key =
-                        static_cast<uint32_t>((blk * kWordsPerBlock + i) * 32 + lane);
-                    o.keys[rank] = key;
+                    o.keys[rank] = static_cast<uint32_t>((c * kChunkWords + i) * 32 + lane);
                     o.counts[rank] = 0;
                     o.rep[rank] = kInvalid;
                     if (o.x) {
+                        uint32_t ix = bx + lane, iy = by, iz = bz;
+                        while (ix >= A.nx) {  // the word crosses a row (and plane) end
+                            ix -= A.nx;
+                            if (++iy == A.ny) {
+                                iy = 0;
+                                ++iz;
+                            }
+                        }
                         float cx, cy, cz;
-                        voxel_centre(key, A, cx, cy, cz);
+                        cell_centre(ix, iy, iz, A, cx, cy, cz);
                         o.x[rank] = cx;
                         o.y[rank] = cy;
                         o.z[rank] = cz;
@@ -263,18 +327,18 @@ __device__ __forceinline__ void emit_block(const uint32_t *__restrict__ bitmap,
 // With n_out set (min_pts == 1), block 0 also publishes N_O = the number of
 // occupied voxels (and a capacity error when it exceeds o.cap), which the
 // later kernels of the stream read on the device.
-__global__ void __launch_bounds__(kThreads) k_emit(const uint32_t *__restrict__ bitmap,
-                                                   const uint32_t *__restrict__ offsets,
-                                                   uint32_t *__restrict__ word_prefix,
-                                                   FilterArgs A, EmitOut o,
-                                                   const uint32_t *n_occ, int32_t *n_out,
-                                                   uint32_t *err) {
+__global__ void __launch_bounds__(kBmThreads) k_emit(uint32_t *__restrict__ bitmap,
+                                                     const uint32_t *__restrict__ offsets,
+                                                     const uint32_t *__restrict__ chunk_off,
+                                                     uint2 *__restrict__ pw, FilterArgs A,
+                                                     EmitOut o, const uint32_t *n_occ,
+                                                     int32_t *n_out, uint32_t *err) {
     if (n_out && blockIdx.x == 0 && threadIdx.x == 0) {
         const uint32_t t = *n_occ;
         *n_out = static_cast<int32_t>(t);
         if (t > o.cap) raise_error(err, GMAPP_DEVERR_CAPACITY);
     }
-    emit_block(bitmap, offsets, word_prefix, A, o, blockIdx.x);
+    emit_block(bitmap, offsets, chunk_off, pw, A, o, blockIdx.x, false);
 }
 
 // Accumulate count and smallest index of consecutive points with one rank.
@@ -299,36 +363,34 @@ struct RankMerge {
     }
 };
 
-__device__ __forceinline__ uint32_t rank_of(uint32_t key, const uint32_t *bitmap,
-                                            const uint32_t *word_prefix, int64_t cap) {
+__device__ __forceinline__ uint32_t rank_of(uint32_t key, const uint2 *pw, int64_t cap) {
     if (key == kInvalid) return kInvalid;
-    uint32_t w = key >> 5;
-    uint32_t below = __ldg(&bitmap[w]) & ((1u << (key & 31)) - 1u);
-    uint32_t r = __ldg(&word_prefix[w]) + __popc(below);
+    const uint2 p = __ldg(&pw[key >> 5]);  // (rank of the word's first bit, bits)
+    const uint32_t r = p.x + __popc(p.y & ((1u << (key & 31)) - 1u));
     return r < cap ? r : kInvalid;
 }
 
 __device__ __forceinline__ void count_range(const uint32_t *__restrict__ keys, int64_t n,
-                                                    const uint32_t *__restrict__ bitmap,
-                                                    const uint32_t *__restrict__ word_prefix,
-                                                    uint32_t *counts, uint32_t *rep, int64_t cap,
-                                            int64_t blk, int64_t nblk) {
+                                            const uint2 *__restrict__ pw, uint32_t *counts,
+                                            uint32_t *rep, int64_t cap, int64_t blk,
+                                            int64_t nblk) {
     const int64_t n4 = n / 4;
     const int64_t stride = nblk * (int64_t)kThreads;
+#pragma unroll 2
     for (int64_t g = blk * (int64_t)kThreads + threadIdx.x; g < n4; g += stride) {
         uint4 k = __ldcs(reinterpret_cast<const uint4 *>(keys) + g);
         RankMerge m;
         uint32_t i0 = static_cast<uint32_t>(4 * g);
         uint32_t r;
-        if ((r = rank_of(k.x, bitmap, word_prefix, cap)) != kInvalid) m.add(r, i0, counts, rep);
-        if ((r = rank_of(k.y, bitmap, word_prefix, cap)) != kInvalid) m.add(r, i0 + 1, counts, rep);
-        if ((r = rank_of(k.z, bitmap, word_prefix, cap)) != kInvalid) m.add(r, i0 + 2, counts, rep);
-        if ((r = rank_of(k.w, bitmap, word_prefix, cap)) != kInvalid) m.add(r, i0 + 3, counts, rep);
+        if ((r = rank_of(k.x, pw, cap)) != kInvalid) m.add(r, i0, counts, rep);
+        if ((r = rank_of(k.y, pw, cap)) != kInvalid) m.add(r, i0 + 1, counts, rep);
+        if ((r = rank_of(k.z, pw, cap)) != kInvalid) m.add(r, i0 + 2, counts, rep);
+        if ((r = rank_of(k.w, pw, cap)) != kInvalid) m.add(r, i0 + 3, counts, rep);
         m.flush(counts, rep);
     }
     int64_t t = 4 * n4 + blk * (int64_t)kThreads + threadIdx.x;
     if (t < n) {
-        uint32_t r = rank_of(keys[t], bitmap, word_prefix, cap);
+        uint32_t r = rank_of(keys[t], pw, cap);
         if (r != kInvalid) {
             atomicAdd(&counts[r], 1u);
             atomicMin(&rep[r], static_cast<uint32_t>(t));
@@ -337,10 +399,9 @@ __device__ __forceinline__ void count_range(const uint32_t *__restrict__ keys, i
 }
 
 __global__ void __launch_bounds__(kThreads) k_count(const uint32_t *__restrict__ keys, int64_t n,
-                                                    const uint32_t *__restrict__ bitmap,
-                                                    const uint32_t *__restrict__ word_prefix,
-                                                    uint32_t *counts, uint32_t *rep, int64_t cap) {
-    count_range(keys, n, bitmap, word_prefix, counts, rep, cap, blockIdx.x, gridDim.x);
+                                                    const uint2 *__restrict__ pw, uint32_t *counts,
+                                                    uint32_t *rep, int64_t cap) {
+    count_range(keys, n, pw, counts, rep, cap, blockIdx.x, gridDim.x);
 }
 
 // min_pts > 1: per block of 1024 temporary entries, how many pass; last
@@ -357,11 +418,11 @@ __global__ void __launch_bounds__(kThreads) k_keep_sums(const uint32_t *__restri
     uint32_t c = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        uint32_t i = (blockIdx.x * kThreads + threadIdx.x) * 4 + j;
+        uint32_t i = (blockIdx.x * kThreads + threadIdx.x) * 4 + j;  // kKeepPerBlock per block
         if (i < n && counts[i] >= min_pts) ++c;
     }
     uint32_t tot;
-    block_exclusive_scan(c, warp_tot, tot);
+    block_exclusive_scan<kThreads>(c, warp_tot, tot);
     if (threadIdx.x == 0) {
         sums[blockIdx.x] = tot;
         __threadfence();
@@ -370,7 +431,7 @@ __global__ void __launch_bounds__(kThreads) k_keep_sums(const uint32_t *__restri
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    uint32_t total = scan_block_sums(sums, offsets, gridDim.x, warp_tot);
+    uint32_t total = scan_block_sums<kThreads>(sums, offsets, gridDim.x, warp_tot);
     if (threadIdx.x == 0) {
         *n_out = static_cast<int32_t>(total);
         if (total > cap) raise_error(err, GMAPP_DEVERR_CAPACITY);
@@ -396,7 +457,7 @@ __global__ void __launch_bounds__(kThreads) k_keep_emit(const uint32_t *__restri
         c += keep[j];
     }
     uint32_t tot;
-    uint32_t rank = offsets[blockIdx.x] + block_exclusive_scan(c, warp_tot, tot);
+    uint32_t rank = offsets[blockIdx.x] + block_exclusive_scan<kThreads>(c, warp_tot, tot);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (!keep[j]) continue;
@@ -418,11 +479,12 @@ __global__ void __launch_bounds__(kThreads) k_keep_emit(const uint32_t *__restri
 
 // Workspace layout (all sections 256-byte aligned).
 struct Layout {
-    int64_t n_words;   // bitmap words, padded to a whole number of k_bitmap_sums blocks
-    int64_t n_blocks;  // k_bitmap_sums / k_emit blocks
-    int64_t n_tmp;     // temporary entries (min_pts > 1), padded to 1024
+    int64_t n_words;   // bitmap words, padded to whole k_bitmap_sums blocks
+    int64_t n_blocks;  // k_emit blocks (kWordsPerBlock words)
+    int64_t n_sblocks; // k_bitmap_sums blocks (4096 words)
+    int64_t n_tmp;     // temporary entries (min_pts > 1), padded to kKeepPerBlock
     int64_t n_tblocks; // k_keep_* blocks
-    size_t off_bitmap, off_prefix, off_sums, off_offsets, off_counters, off_keys;
+    size_t off_bitmap, off_pw, off_chunk, off_sums, off_offsets, off_counters, off_keys;
     size_t off_tkeys, off_tcounts, off_trep, off_tsums, off_toffsets;
     size_t total;
 };
@@ -442,8 +504,9 @@ Layout layout(int64_t n_raw, const gmapp_workspace *ws) {
     Layout L{};
     uint64_t cells = (uint64_t)ws->dims[0] * ws->dims[1] * ws->dims[2];
     int64_t words = static_cast<int64_t>((cells + 31) / 32);
-    L.n_blocks = (words + kWordsPerBlock - 1) / kWordsPerBlock;
-    L.n_words = L.n_blocks * kWordsPerBlock;
+    L.n_sblocks = (words + kWordsPerSumBlock - 1) / kWordsPerSumBlock;
+    L.n_words = L.n_sblocks * kWordsPerSumBlock;  // a multiple of kWordsPerBlock too
+    L.n_blocks = L.n_words / kWordsPerBlock;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -451,15 +514,16 @@ Layout layout(int64_t n_raw, const gmapp_workspace *ws) {
         return o;
     };
     L.off_bitmap = take(L.n_words * 4);
-    L.off_prefix = take(L.n_words * 4);
-    L.off_sums = take(L.n_blocks * 4);
-    L.off_offsets = take(L.n_blocks * 4);
+    L.off_pw = take(L.n_words * 8);
+    L.off_chunk = take(L.n_words / kChunkWords * 4);
+    L.off_sums = take(L.n_sblocks * 4);
+    L.off_offsets = take(L.n_sblocks * 4);
     L.off_counters = take(64);
     L.off_keys = take(align_up(n_raw > 0 ? n_raw : 1, 4) * 4);
     if (ws->min_pts > 1) {
         int64_t nt = std::min<int64_t>(n_raw, static_cast<int64_t>(cells));
-        L.n_tblocks = std::max<int64_t>(1, (nt + kWordsPerBlock - 1) / kWordsPerBlock);
-        L.n_tmp = L.n_tblocks * kWordsPerBlock;
+        L.n_tblocks = std::max<int64_t>(1, (nt + kKeepPerBlock - 1) / kKeepPerBlock);
+        L.n_tmp = L.n_tblocks * kKeepPerBlock;
         L.off_tkeys = take(L.n_tmp * 4);
         L.off_tcounts = take(L.n_tmp * 4);
         L.off_trep = take(L.n_tmp * 4);
