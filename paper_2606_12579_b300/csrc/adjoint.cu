@@ -142,10 +142,7 @@ __device__ __forceinline__ void adj_pair(f2 ox, f2 oy, f2 oz, int jg, const f2 (
         if (sfu_agent(a, NM, NA)) {
             u = pk(rcp_approx(sl), rcp_approx(sh));
         } else {
-            const f2 s2 = pk(sl, sh);
-            u = pk(neg_rcp_seed(sl), neg_rcp_seed(sh));
-#pragma unroll
-            for (int it = 0; it < 3; ++it) u = fma2(u, fma2(s2, u, one2), u);
+            u = neg_rcp2(pk(sl, sh), sl, sh, one2);
         }
         W[a] = add2(W[a], pk(and_bits(lo_of(u), gl), and_bits(hi_of(u), gh)));
         const f2 t = mul2(mul2(u, u), r);  // u^2 / |d|
