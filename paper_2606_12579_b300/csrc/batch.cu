@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kBmThreads) kb_emit(const BatchDev B) {
     const QueryDev &Q = B.q[B.bm_map[blockIdx.x]];
     const FilterArgs fa = Q.fa;
     EmitOut o{Q.okeys, Q.ocounts, Q.orep, Q.ox, Q.oy, Q.oz, Q.cap};
-    emit_block(Q.bitmap, Q.offsets, Q.chunk, Q.pw, fa, o, blockIdx.x - Q.bm_blk0, true);
+    emit_block<kChunksPerWarp>(Q.bitmap, Q.offsets, Q.chunk, Q.pw, fa, o, blockIdx.x - Q.bm_blk0, true);
 }
 
 __global__ void __launch_bounds__(kThreads) kb_count(const BatchDev B) {

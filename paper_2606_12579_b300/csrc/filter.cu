@@ -101,7 +101,7 @@ extern "C" gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n
                                                                           counters, n_occ);
     if (ws->min_pts == 1) {
         EmitOut o{out->keys, out->counts, out->rep_idx, out->x, out->y, out->z, out->cap};
-        k_emit<<<static_cast<int>(L.n_blocks), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, o,
+        k_emit<<<static_cast<int>(L.n_words / kBmThreads), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, o,
                                                                       n_occ, out->n, ctx->d_err);
         k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, pw, out->counts,
                                                    out->rep_idx, out->cap);
@@ -112,7 +112,7 @@ extern "C" gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n
         uint32_t *tsums = reinterpret_cast<uint32_t *>(base + L.off_tsums);
         uint32_t *toffsets = reinterpret_cast<uint32_t *>(base + L.off_toffsets);
         EmitOut t{tkeys, tcounts, trep, nullptr, nullptr, nullptr, L.n_tmp};
-        k_emit<<<static_cast<int>(L.n_blocks), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, t,
+        k_emit<<<static_cast<int>(L.n_words / kBmThreads), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, t,
                                                                       nullptr, nullptr, nullptr);
         k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, pw, tcounts, trep,
                                                    L.n_tmp);
@@ -262,7 +262,7 @@ extern "C" gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, co
                                                                           counters, n_occ);
     if (ws->min_pts == 1) {
         EmitOut o{out->keys, out->counts, out->rep_idx, out->x, out->y, out->z, out->cap};
-        k_emit<<<static_cast<int>(L.n_blocks), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, o,
+        k_emit<<<static_cast<int>(L.n_words / kBmThreads), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, o,
                                                                       n_occ, out->n, sym.err);
         k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, pw, out->counts,
                                                    out->rep_idx, out->cap);
@@ -273,7 +273,7 @@ extern "C" gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, co
         uint32_t *tsums = reinterpret_cast<uint32_t *>(base + L.off_tsums);
         uint32_t *toffsets = reinterpret_cast<uint32_t *>(base + L.off_toffsets);
         EmitOut t{tkeys, tcounts, trep, nullptr, nullptr, nullptr, L.n_tmp};
-        k_emit<<<static_cast<int>(L.n_blocks), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, t,
+        k_emit<<<static_cast<int>(L.n_words / kBmThreads), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, t,
                                                                       nullptr, nullptr, nullptr);
         k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, pw, tcounts, trep,
                                                    L.n_tmp);

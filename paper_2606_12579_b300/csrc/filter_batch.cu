@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kBmThreads) kf_emit(const FilterJob *J, const 
         if (t > o.cap) raise_error(err, GMAPP_DEVERR_CAPACITY);
     }
     const FilterArgs fa = Q.fa;
-    emit_block(Q.bitmap, Q.offsets, Q.chunk, Q.pw, fa, o, blk, true);
+    emit_block<kChunksPerWarp>(Q.bitmap, Q.offsets, Q.chunk, Q.pw, fa, o, blk, true);
 }
 
 __global__ void __launch_bounds__(kThreads) kf_count(const FilterJob *J, const int32_t *pt_map) {

@@ -22,8 +22,8 @@ constexpr int kThreads = 256;
 // table plane fills whole words) spreads over many warps.
 constexpr int kBmThreads = 256;
 constexpr int kChunkWords = 32;
-constexpr int kChunksPerWarp = 4;
-constexpr int kWordsPerBlock = kBmThreads * kChunksPerWarp;  // emit block: 1024 words
+constexpr int kChunksPerWarp = 4;  // batched paths; a single cloud uses 1 (more warps)
+constexpr int kWordsPerBlock = kBmThreads * kChunksPerWarp;  // batched emit block: 1024 words
 constexpr int kWordsPerSumBlock = 4096;
 constexpr int kChunksPerSumBlock = kWordsPerSumBlock / kChunkWords;
 static_assert(kWordsPerSumBlock % kWordsPerBlock == 0, "emit blocks tile the sum blocks");
@@ -246,19 +246,20 @@ struct EmitOut {
 // an empty one).  Every set bit becomes one output entry (key, centre,
 // count = 0, rep = ~0).  With `zero`, the occupied words are
 // cleared after use (library-owned scratch stays ready for the next run
-// without a clearing launch).
+// without a clearing launch).  CPW: 32-word chunks per warp (warps independent).
+template <int CPW>
 __device__ __forceinline__ void emit_block(uint32_t *__restrict__ bitmap,
                                            const uint32_t *__restrict__ offsets,
                                            const uint32_t *__restrict__ chunk_off,
                                            uint2 *__restrict__ pw, FilterArgs A, EmitOut o,
                                            int64_t blk, bool zero) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t c0 = (blk * (kBmThreads / 32) + warp) * kChunksPerWarp;
-    uint32_t w[kChunksPerWarp];
+    const int64_t c0 = (blk * (kBmThreads / 32) + warp) * CPW;
+    uint32_t w[CPW];
 #pragma unroll
-    for (int j = 0; j < kChunksPerWarp; ++j) w[j] = bitmap[(c0 + j) * kChunkWords + lane];
+    for (int j = 0; j < CPW; ++j) w[j] = bitmap[(c0 + j) * kChunkWords + lane];
 #pragma unroll 1
-    for (int j = 0; j < kChunksPerWarp; ++j) {
+    for (int j = 0; j < CPW; ++j) {
         if (!__ballot_sync(0xffffffffu, w[j] != 0u)) continue;
         const int64_t c = c0 + j;
         const uint32_t cnt = __popc(w[j]);
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(kBmThreads) k_emit(uint32_t *__restrict__ bitm
         *n_out = static_cast<int32_t>(t);
         if (t > o.cap) raise_error(err, GMAPP_DEVERR_CAPACITY);
     }
-    emit_block(bitmap, offsets, chunk_off, pw, A, o, blockIdx.x, false);
+    emit_block<1>(bitmap, offsets, chunk_off, pw, A, o, blockIdx.x, false);
 }
 
 // Accumulate count and smallest index of consecutive points with one rank.
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(kThreads) k_keep_emit(const uint32_t *__restri
 // Workspace layout (all sections 256-byte aligned).
 struct Layout {
     int64_t n_words;   // bitmap words, padded to whole k_bitmap_sums blocks
-    int64_t n_blocks;  // k_emit blocks (kWordsPerBlock words)
+    int64_t n_blocks;  // batched emit blocks (kWordsPerBlock words)
     int64_t n_sblocks; // k_bitmap_sums blocks (4096 words)
     int64_t n_tmp;     // temporary entries (min_pts > 1), padded to kKeepPerBlock
     int64_t n_tblocks; // k_keep_* blocks
