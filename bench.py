@@ -352,10 +352,7 @@ def run_ours(args, ws, rank, local):
         if not args.no_patterns:
             del frames, pinned, wsp, obs, ro, sel
             torch.cuda.empty_cache()
-            result["patterns"] = {"filter_stream": bench_filter_stream(gm, args),
-                                  "batched": bench_batched(gm, args),
-                                  "adjoint": bench_adjoint(gm, args),
-                                  "served": bench_served(gm, args)}
+            result["patterns"] = {name: fn(gm, args) for name, fn in PATTERNS.items()}
         print(json.dumps(result), flush=True)
     if ws > 1:
         dist.barrier()
@@ -708,14 +705,30 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="length of the 1 kHz request stream of the served loop")
     ap.add_argument("--tuning", default="",
-                    help="rollout launch shape 'cluster,agents,threads' (default: library choice)")
+                    help="rollout launch shape 'cluster,agents,threads[,exchange]' "
+                         "(default: autotuned)")
+    ap.add_argument("--pattern", choices=sorted(PATTERNS), default=None,
+                    help="run only this pattern measurement and print its JSON")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.pattern:
+        import torch
+        import paper_2606_12579_b300 as gm
+        torch.cuda.set_device(local)
+        gm.context(local)
+        print(json.dumps({args.pattern: PATTERNS[args.pattern](gm, args)}), flush=True)
+        return 0
     return run_ours(args, ws, rank, local)
+
+
+PATTERNS = {"filter_stream": lambda gm, a: bench_filter_stream(gm, a),
+            "batched": lambda gm, a: bench_batched(gm, a),
+            "adjoint": lambda gm, a: bench_adjoint(gm, a),
+            "served": lambda gm, a: bench_served(gm, a)}
 
 
 if __name__ == "__main__":
