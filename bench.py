@@ -369,7 +369,7 @@ def run_ours(args, ws, rank, local):
         per_launch_inter = na * statistics.mean(
             [n_obs[(args.warmup + i) % args.frames] for i in range(args.steps)]) * nk
         achieved = per_launch_inter * FLOPS_PER_INTERACTION / mean_roll / 1e12
-        cpu = cpu_baseline(base, frames_np[0], args.cpu_agents) if not args.no_cpu else None
+        cpu = cpu_baseline(base, frames_np, args.cpu_agents) if not args.no_cpu else None
         result = {
             "metric": METRIC, "value": inter / t_job, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_job / args.steps,
@@ -725,16 +725,33 @@ def bench_served(gm, args):
             "frames_in_pool": pool}
 
 
-def cpu_baseline(base, xyz, n_agents_sample):
+def cpu_baseline(base, frames, n_agents_sample, min_seconds=10.0, max_steps=8):
+    """The oracle as it stands on the host cores (OpenMP over agents): whole
+    steps (the frame's filter, then n_agents_sample agents x all obstacles x
+    N_k) on successive frames until min_seconds have passed; and one thread
+    on a sixteenth of the agents of one step."""
     import oracle
+    cores = oracle.max_threads()
     t0 = time.perf_counter()
-    inter = oracle_step(base, xyz, n_agents_sample)
+    inter, steps = 0, 0
+    while steps < max_steps and (steps == 0 or time.perf_counter() - t0 < min_seconds):
+        inter += oracle_step(base, frames[steps % len(frames)], n_agents_sample)
+        steps += 1
     dt = time.perf_counter() - t0
-    return {"value": inter / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"one step: full-frame filter + {n_agents_sample} of "
-                      f"{base['agents']['k_r'].size} agents x all obstacles x "
-                      f"{base['params'].n_steps} steps (agents are independent)",
-            "seconds": dt}
+    one = max(1, n_agents_sample // 16)
+    oracle.set_threads(1)
+    try:
+        t1 = time.perf_counter()
+        inter1 = oracle_step(base, frames[0], one)
+        dt1 = time.perf_counter() - t1
+    finally:
+        oracle.set_threads(cores)
+    return {"value": inter / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} steps on distinct frames, each: full-frame filter + "
+                      f"{n_agents_sample} of {base['agents']['k_r'].size} agents x all obstacles x "
+                      f"{base['params'].n_steps} steps",
+            "seconds": dt,
+            "single_thread": {"value": inter1 / dt1, "agents": one, "seconds": dt1}}
 
 
 def main():
@@ -744,7 +761,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--frames", type=int, default=48)
-    ap.add_argument("--cpu-agents", type=int, default=64)
+    ap.add_argument("--cpu-agents", type=int, default=256,
+                    help="agents per step of the oracle's cpu_baseline")
     ap.add_argument("--ref-agents", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--obs-cap", type=int, default=0,
