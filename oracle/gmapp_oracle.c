@@ -18,6 +18,7 @@
  *   Sec. IV-B / Sec. V-A  perception: transform, workspace crop, voxel grid
  *                         at edge 2 r_O, voxel centres -> sphere world S_W
  *   Eq. (mfi)             circular-field (MFI) repulsive force
+ *   Eq. (apf)             artificial-potential-field (APF) repulsive force
  *   Alg. 1                per-obstacle clamp max(d - (r_a + r_O), eps),
  *                         detection gate d <= r_d, k_f scaling, sum over S_W
  *   Sec. IV-A             F = f_a + f_r, f_a = K e - D v, vdot = I F,
@@ -191,6 +192,62 @@ void oracle_cf_eval(int64_t n_obs, const double *ox, const double *oy,
     }
 }
 
+/*
+ * Per-agent obstacle sum of the APF heuristic, Eq. (apf), in the reading of
+ * this implementation: for every obstacle j of S_W, with d_j = p - p_Oj and
+ * the surface distance d_O = |d_j| - (r_a + r_O),
+ *   gate      d_O < r_d (strict, as printed);
+ *   distance  rho_j = max(|d_j|, r_a + r_O + eps) -- the clamp of Alg. 1
+ *             applied to the surface distance, so a penetrating pair stays
+ *             finite; for d_O >= eps, rho_j = |d_j| exactly as printed;
+ *   term      (1/rho_j - 1/r_d) rho_j^-2 d_j / |d_j|   (0 when |d_j| = 0),
+ * which for d_O >= eps is (1/|d| - 1/r_d) |d|^-3 d of Eq. (apf).
+ * f = sum of the terms (the gain k_f is applied by the caller); m as in
+ * cf_weight (clearance to the nearest surface, unclamped).
+ */
+static void apf_force(const double p[3], int64_t n_obs, const double *ox,
+                      const double *oy, const double *oz, double R, double eps,
+                      double r_d, double f[3], double *m)
+{
+    double fx = 0.0, fy = 0.0, fz = 0.0, mn = INFINITY;
+    for (int64_t j = 0; j < n_obs; ++j) {
+        double dx = p[0] - ox[j], dy = p[1] - oy[j], dz = p[2] - oz[j];
+        double d = sqrt(dx * dx + dy * dy + dz * dz);
+        double dO = d - R;
+        if (dO < mn) mn = dO;
+        if (!(dO < r_d) || d == 0.0) continue;
+        double rho = d > R + eps ? d : R + eps;
+        double coef = (1.0 / rho - 1.0 / r_d) / (rho * rho) / d;
+        fx += coef * dx;
+        fy += coef * dy;
+        fz += coef * dz;
+    }
+    f[0] = fx;
+    f[1] = fy;
+    f[2] = fz;
+    *m = mn;
+}
+
+/*
+ * APF repulsive force of each agent at positions p:
+ *   f_r = rho k_r f      (k_f = rho k_r)
+ * Layouts: p, f_r are [3][n_agents]; the rest [n_agents].
+ */
+void oracle_apf_eval(int64_t n_obs, const double *ox, const double *oy,
+                     const double *oz, double r_O, int64_t n_agents,
+                     const double *p, const double *k_r, const double *r_d,
+                     const double *r_a, double rho, double eps, double *m, double *f_r)
+{
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t i = 0; i < n_agents; ++i) {
+        double pi[3] = {p[i], p[n_agents + i], p[2 * n_agents + i]};
+        double f[3], mn;
+        apf_force(pi, n_obs, ox, oy, oz, r_a[i] + r_O, eps, r_d[i], f, &mn);
+        m[i] = mn;
+        for (int a = 0; a < 3; ++a) f_r[a * n_agents + i] = rho * k_r[i] * f[a];
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Rollout (Sec. IV-A) with the running cost accumulators                    */
 /* ------------------------------------------------------------------------ */
@@ -224,6 +281,9 @@ static double softplus(double x, double beta)
  *   p_k+1 = p_k + dt v_k
  *   L    += |p_k+1 - p_k|;   pen += softplus(margin - m_k);   mc = min(mc, m_k)
  * The trajectory holds p_0 .. p_N_k (N_k + 1 points).
+ * Heterogeneous ensemble: the last n_apf agents use the APF heuristic
+ * instead, F = k_a (p_goal - p_k) - D v_{k-1} + rho k_r f_apf(p_k), with
+ * |f_apf| in the w trace.
  * Layouts: agent vectors [3][n_agents]; traj [n_agents][n_steps+1][3];
  * w_trace, m_trace [n_agents][n_steps].  traj / traces may be NULL.
  */
@@ -234,7 +294,7 @@ void oracle_rollout(int64_t n_obs, const double *ox, const double *oy,
                     const double *r_a, const oracle_params *prm, double *traj,
                     double *p_final, double *v_final, double *path_len,
                     double *clear_pen, double *min_clear, double *w_trace,
-                    double *m_trace)
+                    double *m_trace, int64_t n_apf)
 {
     const int64_t N = prm->n_steps;
 #pragma omp parallel for schedule(dynamic)
@@ -244,13 +304,22 @@ void oracle_rollout(int64_t n_obs, const double *ox, const double *oy,
         double ci[3] = {c[i], c[n_agents + i], c[2 * n_agents + i]};
         double L = 0.0, pen = 0.0, mc = INFINITY;
         if (traj) for (int a = 0; a < 3; ++a) traj[(i * (N + 1)) * 3 + a] = p[a];
+        const int apf = i >= n_agents - n_apf;
         for (int64_t k = 0; k < N; ++k) {
             double w, mn, g[3], F[3], pn[3];
-            cf_weight(p, n_obs, ox, oy, oz, r_a[i] + r_O, prm->eps, r_d[i], &w, &mn);
-            cf_direction(v, ci, g);
-            for (int a = 0; a < 3; ++a)
-                F[a] = k_a[i] * (prm->goal[a] - p[a]) - prm->damping * v[a]
-                       + prm->rho * k_r[i] * w * g[a];
+            if (apf) {
+                apf_force(p, n_obs, ox, oy, oz, r_a[i] + r_O, prm->eps, r_d[i], g, &mn);
+                w = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+                for (int a = 0; a < 3; ++a)
+                    F[a] = k_a[i] * (prm->goal[a] - p[a]) - prm->damping * v[a]
+                           + prm->rho * k_r[i] * g[a];
+            } else {
+                cf_weight(p, n_obs, ox, oy, oz, r_a[i] + r_O, prm->eps, r_d[i], &w, &mn);
+                cf_direction(v, ci, g);
+                for (int a = 0; a < 3; ++a)
+                    F[a] = k_a[i] * (prm->goal[a] - p[a]) - prm->damping * v[a]
+                           + prm->rho * k_r[i] * w * g[a];
+            }
             for (int a = 0; a < 3; ++a) v[a] = v[a] + prm->vel_half * prm->dt * prm->inv_mass * F[a];
             for (int a = 0; a < 3; ++a) pn[a] = p[a] + prm->dt * v[a];
             double dx = pn[0] - p[0], dy = pn[1] - p[1], dz = pn[2] - p[2];
