@@ -339,6 +339,37 @@ gmapp_status gmapp_pick_tuning(gmapp_ctx *ctx, int64_t obs_cap, int32_t n_agents
                                gmapp_tuning *tune);
 
 /* ------------------------------------------------------------------------ */
+/* Heterogeneous ensemble: rollout_ensemble (Sec. IV-A vector-field           */
+/* heuristics: Heuristic 1, APF, Eq. (apf); Heuristic 2, MFI, Eq. (mfi);      */
+/* "Other Heuristics": agents with different heuristics and large or small    */
+/* detection radii form one ensemble; Sec. IV-D: agents grouped by heuristic) */
+/* ------------------------------------------------------------------------ */
+
+/* rollout_agents for an ensemble in which the LAST n_apf agents (indices
+ * n - n_apf .. n - 1) follow the APF heuristic and the others the MFI field
+ * above.  Callers order their agents by heuristic.  Per-agent r_d gives each
+ * agent a large or small detection radius.  An APF agent's force at step k:
+ *   d_j  = p_k - p_Oj,  rho_j = max(|d_j|, r_a + r_O + eps)
+ *   f    = sum over j with |d_j| - (r_a + r_O) < r_d (strict) of
+ *          (1/rho_j - 1/r_d) rho_j^-2 d_j / |d_j|   (a pair with d_j = 0 adds 0)
+ *   F    = k_a (p_goal - p_k) - damping v_{k-1} + rho k_r f
+ * The rest of the step, the outputs and the error behaviour are those of
+ * rollout_agents.  For APF agents, w_trace holds |f| and f_trace rho k_r f.
+ * APF agents need r_d > 0 (+inf = no gate).
+ * All agents run in ONE launch: the agent groups of the launch are
+ * homogeneous (each holds only MFI or only APF agents), with groups shared
+ * in proportion to the two counts.  `tune` selects the launch shape as in
+ * rollout_agents_tuned (agents_per_cta is an upper bound per group; at most
+ * 12 agents per group and 384 threads), or NULL for the library's choice.
+ * n_apf = 0 is rollout_agents.  GMAPP_ERR_INVALID_ARG for n_apf outside
+ * [0, n], for adjoint checkpoints (out->ckpt) with n_apf > 0, or for a shape
+ * that does not fit. */
+gmapp_status rollout_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                              const gmapp_agents *agents, int32_t n_apf,
+                              const gmapp_rollout_params *prm, gmapp_rollout_out *out,
+                              const gmapp_tuning *tune, gmapp_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* Cost and selection: score_and_select (Sec. IV-A "Cost Functions" and        */
 /* "Selection Mechanism"; gmapp_cost_weights is declared above)               */
 /* ------------------------------------------------------------------------ */

@@ -43,7 +43,7 @@ def lib():
                                         P, P, P, P, P, P, P, P, P, i64]
         _lib.oracle_apf_eval.restype = None
         _lib.oracle_apf_eval.argtypes = [i64, P, P, P, C.c_double, i64, P, P, P, P,
-                                         C.c_double, C.c_double, P, P]
+                                         C.c_double, C.c_double, P, P, P]
         _lib.oracle_max_threads.restype = C.c_int
         _lib.oracle_set_threads.argtypes = [C.c_int]
         _lib.oracle_adjoint.restype = None
@@ -138,17 +138,19 @@ def cf_eval(obs_xyz, r_O: float, p, v, agents: dict, rho: float, eps: float) -> 
 
 def apf_eval(obs_xyz, r_O: float, p, agents: dict, rho: float, eps: float) -> dict:
     """Clearance m and the APF force f_r = rho k_r f (Eq. apf) for every agent
-    at positions p [3, N_a]."""
+    at positions p [3, N_a]; f_abs = |rho k_r| times the sum of the term
+    magnitudes (the scale of the rounding error of the vector sum)."""
     ox, oy, oz = (_f64(obs_xyz[a]) for a in range(3))
     p = _f64(p)
     na = p.shape[1]
     k_r, r_d, r_a = _f64(agents["k_r"]), _f64(agents["r_d"]), _f64(agents["r_a"])
     m = np.zeros(na)
     fr = np.zeros((3, na))
+    fa = np.zeros(na)
     lib().oracle_apf_eval(ox.size, _ptr(ox), _ptr(oy), _ptr(oz), float(r_O), na, _ptr(p),
                           _ptr(k_r), _ptr(r_d), _ptr(r_a), float(rho), float(eps), _ptr(m),
-                          _ptr(fr))
-    return {"m": m, "f_r": fr}
+                          _ptr(fr), _ptr(fa))
+    return {"m": m, "f_r": fr, "f_abs": fa}
 
 
 def rollout(obs_xyz, r_O: float, agents: dict, prm, want_traj: bool = True,

@@ -203,13 +203,15 @@ void oracle_cf_eval(int64_t n_obs, const double *ox, const double *oy,
  *   term      (1/rho_j - 1/r_d) rho_j^-2 d_j / |d_j|   (0 when |d_j| = 0),
  * which for d_O >= eps is (1/|d| - 1/r_d) |d|^-3 d of Eq. (apf).
  * f = sum of the terms (the gain k_f is applied by the caller); m as in
- * cf_weight (clearance to the nearest surface, unclamped).
+ * cf_weight (clearance to the nearest surface, unclamped); sabs (may be
+ * NULL) = sum of the term magnitudes |term_j|, the scale of the rounding
+ * error of any evaluation of the sum.
  */
 static void apf_force(const double p[3], int64_t n_obs, const double *ox,
                       const double *oy, const double *oz, double R, double eps,
-                      double r_d, double f[3], double *m)
+                      double r_d, double f[3], double *m, double *sabs)
 {
-    double fx = 0.0, fy = 0.0, fz = 0.0, mn = INFINITY;
+    double fx = 0.0, fy = 0.0, fz = 0.0, mn = INFINITY, sa = 0.0;
     for (int64_t j = 0; j < n_obs; ++j) {
         double dx = p[0] - ox[j], dy = p[1] - oy[j], dz = p[2] - oz[j];
         double d = sqrt(dx * dx + dy * dy + dz * dz);
@@ -221,29 +223,34 @@ static void apf_force(const double p[3], int64_t n_obs, const double *ox,
         fx += coef * dx;
         fy += coef * dy;
         fz += coef * dz;
+        sa += fabs(coef) * d;
     }
     f[0] = fx;
     f[1] = fy;
     f[2] = fz;
     *m = mn;
+    if (sabs) *sabs = sa;
 }
 
 /*
  * APF repulsive force of each agent at positions p:
  *   f_r = rho k_r f      (k_f = rho k_r)
+ * and f_abs = |rho k_r| sum_j |term_j| (f_abs may be NULL).
  * Layouts: p, f_r are [3][n_agents]; the rest [n_agents].
  */
 void oracle_apf_eval(int64_t n_obs, const double *ox, const double *oy,
                      const double *oz, double r_O, int64_t n_agents,
                      const double *p, const double *k_r, const double *r_d,
-                     const double *r_a, double rho, double eps, double *m, double *f_r)
+                     const double *r_a, double rho, double eps, double *m, double *f_r,
+                     double *f_abs)
 {
 #pragma omp parallel for schedule(dynamic)
     for (int64_t i = 0; i < n_agents; ++i) {
         double pi[3] = {p[i], p[n_agents + i], p[2 * n_agents + i]};
-        double f[3], mn;
-        apf_force(pi, n_obs, ox, oy, oz, r_a[i] + r_O, eps, r_d[i], f, &mn);
+        double f[3], mn, sa;
+        apf_force(pi, n_obs, ox, oy, oz, r_a[i] + r_O, eps, r_d[i], f, &mn, &sa);
         m[i] = mn;
+        if (f_abs) f_abs[i] = fabs(rho * k_r[i]) * sa;
         for (int a = 0; a < 3; ++a) f_r[a * n_agents + i] = rho * k_r[i] * f[a];
     }
 }
@@ -308,7 +315,7 @@ void oracle_rollout(int64_t n_obs, const double *ox, const double *oy,
         for (int64_t k = 0; k < N; ++k) {
             double w, mn, g[3], F[3], pn[3];
             if (apf) {
-                apf_force(p, n_obs, ox, oy, oz, r_a[i] + r_O, prm->eps, r_d[i], g, &mn);
+                apf_force(p, n_obs, ox, oy, oz, r_a[i] + r_O, prm->eps, r_d[i], g, &mn, NULL);
                 w = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
                 for (int a = 0; a < 3; ++a)
                     F[a] = k_a[i] * (prm->goal[a] - p[a]) - prm->damping * v[a]

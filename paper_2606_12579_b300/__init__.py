@@ -21,8 +21,8 @@ from . import _abi
 from ._abi import check
 
 __all__ = ["Context", "context", "Obstacles", "filter_cloud", "filter_cloud_noalloc",
-           "filter_workspace_bytes", "rollout_agents", "score_and_select", "pick_tuning",
-           "autotune_rollout", "rollout_adjoint", "GMappRollout", "sync", "GmappError",
+           "filter_workspace_bytes", "rollout_agents", "rollout_ensemble", "score_and_select",
+           "pick_tuning", "autotune_rollout", "rollout_adjoint", "GMappRollout", "sync", "GmappError",
            "FilterBatch", "Batch", "Server"]
 
 GmappError = _abi.GmappError
@@ -312,6 +312,24 @@ def rollout_agents(obs: Obstacles, agents: dict, prm, out: dict | None = None,
         st = lib.rollout_agents_tuned(ctx.handle, C.byref(ob), C.byref(ag), C.byref(pr),
                                       C.byref(os_), C.byref(t), _stream(stream))
     check(st, "rollout_agents")
+    return out
+
+
+def rollout_ensemble(obs: Obstacles, agents: dict, n_apf: int, prm, out: dict | None = None,
+                     want_traj: bool = True, want_trace: bool = False, want_clear: bool = True,
+                     tuning=None, stream=None) -> dict:
+    """Heterogeneous ensemble in one launch: the last ``n_apf`` agents follow
+    the APF heuristic (Eq. apf), the others the MFI field (Eq. mfi); agent
+    groups are homogeneous.  Arguments and outputs as rollout_agents."""
+    ctx = context()
+    na = int(agents["k_r"].numel())
+    if out is None:
+        out = alloc_rollout_out(na, int(prm.n_steps), want_traj, want_trace, want_clear)
+    ob, ag, pr, os_ = obs._struct(), _agents_struct(agents), _params_struct(prm), _out_struct(out)
+    t = C.byref(_abi.Tuning(*[int(v) for v in tuning])) if tuning is not None else None
+    check(_abi.load().rollout_ensemble(ctx.handle, C.byref(ob), C.byref(ag), int(n_apf),
+                                       C.byref(pr), C.byref(os_), t, _stream(stream)),
+          "rollout_ensemble")
     return out
 
 

@@ -112,6 +112,9 @@ PROTOTYPES = {
     "rollout_agents_tuned": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
                                        C.POINTER(RolloutParams), C.POINTER(RolloutOut),
                                        C.POINTER(Tuning), P]),
+    "rollout_ensemble": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents), C.c_int32,
+                                   C.POINTER(RolloutParams), C.POINTER(RolloutOut),
+                                   C.POINTER(Tuning), P]),
     "gmapp_pick_tuning": (C.c_int, [P, C.c_int64, C.c_int32, C.POINTER(Tuning)]),
     "gmapp_autotune_rollout": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
                                          C.POINTER(RolloutParams), C.POINTER(RolloutOut),

@@ -22,6 +22,8 @@ struct Shape {
     int ag;        // agents per group held in registers (max over groups)
     int threads;   // NT
     bool clear;    // clearance reduction compiled in
+    int n_apf;     // heterogeneous ensemble: the last n_apf agents use APF (0 = MFI only)
+    int groups_apf;  // ... forming the last groups_apf groups
     RolloutKernel fn;
     int32_t shard_cap;
     size_t smem;   // dynamic shared memory bytes
@@ -32,7 +34,11 @@ int32_t shard_cap_for(int64_t cap, int cluster) {
     return static_cast<int32_t>((s + 3) & ~int64_t(3));
 }
 
-RolloutKernel pick_kernel(int ag, int nt, bool clear, bool grid) {
+RolloutKernel pick_kernel(int ag, int nt, bool clear, bool grid, bool ens) {
+    if (ens) {
+        if (grid) return clear ? rollout_kernel_ens_grid_clear(ag, nt) : rollout_kernel_ens_grid_noclear(ag, nt);
+        return clear ? rollout_kernel_ens_clear(ag, nt) : rollout_kernel_ens_noclear(ag, nt);
+    }
     if (grid) return clear ? rollout_kernel_grid_clear(ag, nt) : rollout_kernel_grid_noclear(ag, nt);
     return clear ? rollout_kernel_clear(ag, nt) : rollout_kernel_noclear(ag, nt);
 }
@@ -44,9 +50,12 @@ size_t static_smem(RolloutKernel fn) {
 }
 
 // Resolve (cluster, agents per group, threads) for N_a agents and an
-// obstacle capacity; false when the shape cannot run.
+// obstacle capacity; false when the shape cannot run.  With n_apf > 0 the
+// groups are split by heuristic (homogeneous groups, in proportion to the
+// agent counts, at least one of each kind present) and the ensemble kernel
+// is used.
 bool resolve(gmapp_ctx *ctx, int64_t cap, int n_agents, const gmapp_tuning &t, bool clear,
-             Shape *s) {
+             Shape *s, int n_apf = 0) {
     if (t.cluster < 1 || t.cluster > kMaxCluster || t.agents_per_cta < 1 ||
         t.agents_per_cta > kMaxAgents || t.exchange < 0 || t.exchange > 1)
         return false;
@@ -56,16 +65,32 @@ bool resolve(gmapp_ctx *ctx, int64_t cap, int n_agents, const gmapp_tuning &t, b
     s->groups = (n_agents + t.agents_per_cta - 1) / t.agents_per_cta;
     s->ag = (n_agents + s->groups - 1) / s->groups;
     s->clear = clear;
-    s->fn = pick_kernel(s->ag, t.threads, clear, s->grid);
+    s->n_apf = n_apf;
+    s->groups_apf = 0;
+    if (n_apf > 0) {
+        const int n_mfi = n_agents - n_apf;
+        if (n_mfi > 0 && s->groups < 2) s->groups = 2;
+        const int g = s->groups;
+        int ga = static_cast<int>((static_cast<int64_t>(g) * n_apf + n_agents / 2) / n_agents);
+        ga = std::max(1, std::min(ga, n_mfi > 0 ? g - 1 : g));
+        s->groups_apf = ga;
+        const int gm = g - ga;
+        s->ag = (n_apf + ga - 1) / ga;
+        if (gm > 0) s->ag = std::max(s->ag, (n_mfi + gm - 1) / gm);
+        if (s->ag > kMaxEnsembleAgents) return false;
+    }
+    s->fn = pick_kernel(s->ag, t.threads, clear, s->grid, n_apf > 0);
     if (!s->fn) return false;
     // grid exchange: one slot set per CTA, at most one CTA per SM
     if (s->grid && s->groups * s->cluster > ctx->sm_count) return false;
     s->shard_cap = shard_cap_for(cap, t.cluster);
     const int nw = t.threads / 32;
-    // shard + per-warp partials [2][NW][AG] + cluster slots [2][2][C][AG], (W, min d^2)
-    // each, + agent positions [3][AG] (4 AG floats keep the 16-byte alignment)
-    s->smem = (static_cast<size_t>(s->shard_cap) * 3 + static_cast<size_t>(4) * nw * s->ag +
-               static_cast<size_t>(8) * t.cluster * s->ag + static_cast<size_t>(4) * s->ag) *
+    // shard + per-warp partials [2][NW][AG] + cluster slots [2][2][C][AG] of
+    // one record each ((W, min d^2); (f_x, f_y, f_z, min d^2) in an ensemble)
+    // + agent positions [3][AG] (4 AG floats keep the 16-byte alignment)
+    const size_t rec = n_apf > 0 ? 4 : 2;
+    s->smem = (static_cast<size_t>(s->shard_cap) * 3 + 2 * rec * nw * s->ag +
+               4 * rec * t.cluster * s->ag + static_cast<size_t>(4) * s->ag) *
               sizeof(float);
     return s->smem + static_smem(s->fn) <= static_cast<size_t>(ctx->max_smem_optin);
 }
@@ -147,13 +172,14 @@ double model_cost(const Shape &s, int m, int64_t n_obs_est, int sm_count) {
 }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int64_t, int, bool>, gmapp_tuning> g_tune_cache;
+// (device, obstacle capacity, N_a, clearance outputs, APF agents of an ensemble)
+std::map<std::tuple<int, int64_t, int, bool, int>, gmapp_tuning> g_tune_cache;
 
 }  // namespace
 
 gmapp_status pick_tuning_impl(gmapp_ctx *ctx, int64_t cap, int32_t n_agents, bool clear,
-                              gmapp_tuning *best) {
-    const auto key = std::make_tuple(ctx->device, cap, n_agents, clear);
+                              gmapp_tuning *best, int32_t n_apf = 0) {
+    const auto key = std::make_tuple(ctx->device, cap, n_agents, clear, n_apf);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -171,7 +197,8 @@ gmapp_status pick_tuning_impl(gmapp_ctx *ctx, int64_t cap, int32_t n_agents, boo
                 int last_groups = -1;
                 for (int a = 1; a <= kMaxAgents; ++a) {
                     Shape s;
-                    if (!resolve(ctx, cap, n_agents, gmapp_tuning{C, a, nt, x}, clear, &s)) continue;
+                    if (!resolve(ctx, cap, n_agents, gmapp_tuning{C, a, nt, x}, clear, &s, n_apf))
+                        continue;
                     if (s.groups == last_groups) continue;
                     last_groups = s.groups;
                     const int m = max_active_clusters(ctx, s);
@@ -179,7 +206,7 @@ gmapp_status pick_tuning_impl(gmapp_ctx *ctx, int64_t cap, int32_t n_agents, boo
                     const double cost = model_cost(s, m, cap, ctx->sm_count);
                     if (cost < best_cost) {
                         best_cost = cost;
-                        *best = gmapp_tuning{C, s.ag, nt, x};
+                        *best = gmapp_tuning{C, n_apf > 0 ? a : s.ag, nt, x};
                         found = true;
                     }
                 }
@@ -247,9 +274,9 @@ bool wants_clear(const gmapp_rollout_out *out) {
 
 gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agents *ag,
                     const gmapp_rollout_params *prm, gmapp_rollout_out *out,
-                    const gmapp_tuning &t, gmapp_stream stream) {
+                    const gmapp_tuning &t, gmapp_stream stream, int n_apf = 0) {
     Shape s;
-    if (!resolve(ctx, obs->cap, ag->n, t, wants_clear(out), &s)) {
+    if (!resolve(ctx, obs->cap, ag->n, t, wants_clear(out), &s, n_apf)) {
         set_error("rollout_agents: launch shape (cluster %d, agents %d, threads %d, exchange %d) "
                   "does not fit an obstacle capacity of %lld",
                   t.cluster, t.agents_per_cta, t.threads, t.exchange, (long long)obs->cap);
@@ -295,6 +322,8 @@ gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agen
     A.ckpt = out->ckpt;
     A.shard_cap = s.shard_cap;
     A.n_groups = s.groups;
+    A.n_apf = s.n_apf;
+    A.n_groups_apf = s.groups_apf;
     A.group_ctas = s.cluster;
     A.xbuf = ctx->d_xbuf;
     A.xctl = ctx->d_xctl;
@@ -396,7 +425,7 @@ extern "C" gmapp_status gmapp_autotune_rollout(gmapp_ctx *ctx, const gmapp_obsta
     }
     if (best_ms) *best_ms = best_t * static_cast<float>(prm->n_steps) / probe.n_steps;
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[std::make_tuple(ctx->device, obs->cap, agents->n, clear)] = *best;
+    g_tune_cache[std::make_tuple(ctx->device, obs->cap, agents->n, clear, 0)] = *best;
     return GMAPP_OK;
 }
 
@@ -442,4 +471,37 @@ extern "C" gmapp_status rollout_agents(gmapp_ctx *ctx, const gmapp_obstacles *ob
     st = pick_tuning_impl(ctx, obs->cap, agents->n, wants_clear(out), &t);
     if (st != GMAPP_OK) return st;
     return launch(ctx, obs, agents, prm, out, t, stream);
+}
+
+extern "C" gmapp_status rollout_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                                         const gmapp_agents *agents, int32_t n_apf,
+                                         const gmapp_rollout_params *prm, gmapp_rollout_out *out,
+                                         const gmapp_tuning *tune, gmapp_stream stream) {
+    if (!ctx) {
+        set_error("rollout_ensemble: NULL ctx");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    gmapp_status st = validate(obs, agents, prm, out);
+    if (st != GMAPP_OK) return st;
+    if (n_apf < 0 || n_apf > agents->n) {
+        set_error("rollout_ensemble: n_apf must lie in [0, n] (n_apf %d, n %d)", n_apf, agents->n);
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    if (n_apf > 0 && out->ckpt) {
+        set_error("rollout_ensemble: adjoint checkpoints cover MFI agents only");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    gmapp_tuning t;
+    if (tune) {
+        if (!(tune->threads == 128 || tune->threads == 256 || tune->threads == 384 ||
+              tune->threads == 512)) {
+            set_error("rollout_ensemble: threads must be 128, 256, 384 or 512");
+            return GMAPP_ERR_INVALID_ARG;
+        }
+        t = *tune;
+    } else {
+        st = pick_tuning_impl(ctx, obs->cap, agents->n, wants_clear(out), &t, n_apf);
+        if (st != GMAPP_OK) return st;
+    }
+    return launch(ctx, obs, agents, prm, out, t, stream, n_apf);
 }

@@ -1,0 +1,8 @@
+// Rollout kernel instantiations: heterogeneous ensemble, CLEAR = true, GRID = false.
+#include "rollout_inst.cuh"
+
+namespace gmapp {
+RolloutKernel rollout_kernel_ens_clear(int ag, int nt) {
+    return rollout_table<true, false, true>(ag, nt);
+}
+}  // namespace gmapp

@@ -1,0 +1,8 @@
+// Rollout kernel instantiations: heterogeneous ensemble, CLEAR = true, GRID = true.
+#include "rollout_inst.cuh"
+
+namespace gmapp {
+RolloutKernel rollout_kernel_ens_grid_clear(int ag, int nt) {
+    return rollout_table<true, true, true>(ag, nt);
+}
+}  // namespace gmapp

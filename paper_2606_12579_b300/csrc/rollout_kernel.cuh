@@ -36,12 +36,16 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 #include "gmapp_internal.cuh"
 
 namespace gmapp {
 
 constexpr int kMaxCluster = 16;
 constexpr int kMaxAgents = 16;
+// agents per group of the heterogeneous-ensemble kernel
+constexpr int kMaxEnsembleAgents = 12;
 
 struct RolloutArgs {
     const float *ox, *oy, *oz;
@@ -59,6 +63,8 @@ struct RolloutArgs {
         *f_trace, *ckpt;
     int32_t shard_cap;   // obstacles one CTA can hold (multiple of 4)
     int32_t n_groups;    // agent groups (clusters, or CTA groups with the grid exchange)
+    int32_t n_apf;       // ensemble kernel: the last n_apf agents use APF (Eq. (apf))
+    int32_t n_groups_apf;  // ensemble kernel: ... and form the last n_groups_apf groups
     int32_t group_ctas;  // grid exchange: CTAs per group (C)
     uint64_t *xbuf;      // grid exchange: tagged slots [G][2][2][C][AG][2]
     uint32_t *xctl;      // grid exchange: launch epoch, finished-CTA counter
@@ -520,11 +526,245 @@ __device__ __forceinline__ bool exchange_half_grid(const float *part, uint64_t *
     return ok;
 }
 
+// ---- APF heuristic (Eq. (apf)) of a heterogeneous ensemble -----------------
+//
+// For every obstacle j, with d = p - p_Oj and r = 1/|d|:
+//   gate   surface distance |d| - R < r_d, i.e. |d|^2 < (r_d + R)^2
+//   clamp  1/rho = min(r, 1/(R + eps))   (rho = max(|d|, R + eps), Alg. 1's
+//          clamp of the surface distance at eps)
+//   term   (1/rho - 1/r_d) rho^-2 r d    ((1/|d| - 1/r_d)|d|^-3 d unclamped)
+// A pair outside the gate takes 1/rho = 1/r_d, so its coefficient is exactly
+// zero; r comes from rsqrt(max(|d|^2, 1e-30)), so a pair at d = 0 has a
+// finite coefficient times d = 0.  Shard padding for APF groups is a far
+// finite point (kApfPad), never NaN (NaN times a zero coefficient is NaN).
+// Per pair: 13 FMA-pipe lane-ops (3 sub, 3 for |d|^2, 4 for the
+// coefficient, 3 accumulating FMAs), one SFU rsqrt, clamp/gate on the ALU.
+constexpr float kApfPad = 1e18f;
+
+template <int AG, int NA, int OFF, bool CLEAR>
+__device__ __forceinline__ void apf_pair_terms(f2 ox, f2 oy, f2 oz, const f2 (&X)[NA],
+                                               const f2 (&Y)[NA], const f2 (&Z)[NA],
+                                               f2 (&fx)[NA], f2 (&fy)[NA], f2 (&fz)[NA],
+                                               float (&mn)[NA], const float (&cRa)[AG],
+                                               const f2 (&ird2)[AG], const float (&G2a)[AG]) {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const f2 dx = sub2(X[a], ox), dy = sub2(Y[a], oy), dz = sub2(Z[a], oz);
+        const f2 d2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        const float d2l = lo_of(d2), d2h = hi_of(d2);
+        const float rl = rsqrt_approx(fmaxf(d2l, 1e-30f));
+        const float rh = rsqrt_approx(fmaxf(d2h, 1e-30f));
+        const float ird = lo_of(ird2[OFF + a]);
+        const float il = d2l < G2a[OFF + a] ? fminf(rl, cRa[OFF + a]) : ird;
+        const float ih = d2h < G2a[OFF + a] ? fminf(rh, cRa[OFF + a]) : ird;
+        const f2 ir = pk(il, ih);
+        const f2 cf = mul2(mul2(sub2(ir, ird2[OFF + a]), mul2(ir, ir)), pk(rl, rh));
+        fx[a] = fma2(cf, dx, fx[a]);
+        fy[a] = fma2(cf, dy, fy[a]);
+        fz[a] = fma2(cf, dz, fz[a]);
+        if (CLEAR) mn[a] = fminf(mn[a], fminf(d2l, d2h));
+    }
+}
+
+// APF counterpart of half_step (positions from shared memory pos[3][AG]):
+// partial force sums of this thread's obstacle pairs, reduced over the warp
+// (one transposed butterfly per component) and stored as one record
+// (f_x, f_y, f_z, min |d|^2) per agent at part_slot0[4 (OFF + a)].
+template <int AG, int NA, int OFF, int NT, bool CLEAR>
+__device__ __forceinline__ void half_step_apf(const float *sx, const float *sy, const float *sz,
+                                              int cnt_pad, const float (&cRa)[AG],
+                                              const f2 (&ird2)[AG], const float (&G2a)[AG],
+                                              float *part_slot0, int lane, const float *pos) {
+    if constexpr (NA > 0) {
+        constexpr int P = pow2ceil(NA);
+        const int tid = threadIdx.x;
+        f2 X[NA], Y[NA], Z[NA], fx[NA], fy[NA], fz[NA];
+        float mn[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            const float x = pos[OFF + a], y = pos[AG + OFF + a], z = pos[2 * AG + OFF + a];
+            X[a] = pk(x, x);
+            Y[a] = pk(y, y);
+            Z[a] = pk(z, z);
+            fx[a] = fy[a] = fz[a] = 0ull;
+            mn[a] = INFINITY;
+        }
+#pragma unroll 2
+        for (int j = 2 * tid; j < cnt_pad; j += 2 * NT) {
+            const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
+            const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
+            const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
+            apf_pair_terms<AG, NA, OFF, CLEAR>(ox, oy, oz, X, Y, Z, fx, fy, fz, mn, cRa, ird2, G2a);
+        }
+        float v0[P], v1[P], v2[P], vm[P];
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            if (a < NA) {
+                v0[a] = lo_of(fx[a]) + hi_of(fx[a]);
+                v1[a] = lo_of(fy[a]) + hi_of(fy[a]);
+                v2[a] = lo_of(fz[a]) + hi_of(fz[a]);
+                vm[a] = mn[a];
+            } else {
+                v0[a] = v1[a] = v2[a] = 0.0f;
+                vm[a] = INFINITY;
+            }
+        }
+        const float rx = transposed_reduce<P, false>(v0, lane);
+        const float ry = transposed_reduce<P, false>(v1, lane);
+        const float rz = transposed_reduce<P, false>(v2, lane);
+        const float m = CLEAR ? transposed_reduce<P, true>(vm, lane) : INFINITY;
+        constexpr int REP = (32 >> log2i(P)) - 1;
+        const int idx = transposed_index<P>(lane);
+        if ((lane & REP) == 0 && idx < NA)
+            *reinterpret_cast<float4 *>(part_slot0 + 4 * (OFF + idx)) = make_float4(rx, ry, rz, m);
+    }
+}
+
+// Sum of the NW per-warp APF records of agent OFF + lane in warp order.
+template <int AG, int OFF, int NW, bool CLEAR>
+__device__ __forceinline__ float4 sum_warp_records(const float *part, int lane) {
+    float4 s = make_float4(0.0f, 0.0f, 0.0f, INFINITY);
+#pragma unroll 4
+    for (int q = 0; q < NW; ++q) {
+        const float4 t = *reinterpret_cast<const float4 *>(part + 4 * (q * AG + OFF + lane));
+        s.x += t.x;
+        s.y += t.y;
+        s.z += t.z;
+        if (CLEAR) s.w = fminf(s.w, t.w);
+    }
+    return s;
+}
+
+// Sum of the C per-CTA records of agent `lane` in rank order.
+template <int AG, bool CLEAR>
+__device__ __forceinline__ void sum_rank_records(const float *slot, uint32_t C, int lane,
+                                                 float (&F)[3], float &md2) {
+    float fx = 0.0f, fy = 0.0f, fz = 0.0f, ms = INFINITY;
+    for (uint32_t r = 0; r < C; ++r) {
+        const float4 t = *reinterpret_cast<const float4 *>(slot + 4 * (r * AG + lane));
+        fx += t.x;
+        fy += t.y;
+        fz += t.z;
+        if (CLEAR) ms = fminf(ms, t.w);
+    }
+    F[0] = fx;
+    F[1] = fy;
+    F[2] = fz;
+    md2 = ms;
+}
+
+__device__ __forceinline__ void st_async_v4f32(uint32_t remote_addr, float4 v, uint32_t remote_bar) {
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+            remote_addr),
+        "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(remote_bar)
+        : "memory");
+}
+
+// exchange_half for APF records (16 bytes per agent and CTA).
+template <int AG, int NA, int OFF, int NW, bool CLEAR>
+__device__ __forceinline__ bool exchange_half_apf(const float *part, float *slot, uint64_t *bar,
+                                                  uint32_t C, uint32_t rank, int lane, int k,
+                                                  bool ok, float (&F)[3], float &md2) {
+    float4 s = make_float4(0.0f, 0.0f, 0.0f, INFINITY);
+    if (lane < NA) s = sum_warp_records<AG, OFF, NW, CLEAR>(part, lane);
+    if (lane == 0) mbar_arrive_expect_tx(bar, C * NA * 16u);
+    if (lane < NA) {
+        const uint32_t local = smem_u32(slot + 4 * (rank * AG + OFF + lane));
+        const uint32_t lbar = smem_u32(bar);
+        for (uint32_t r = 0; r < C; ++r) st_async_v4f32(map_smem(local, r), s, map_smem(lbar, r));
+    }
+    if (ok && !mbar_wait_cluster(bar, (k >> 1) & 1)) ok = false;
+    if (lane >= OFF && lane < OFF + NA) sum_rank_records<AG, CLEAR>(slot, C, lane, F, md2);
+    return ok;
+}
+
+// exchange_half_grid for APF records: 3 tagged words per agent and CTA
+// (f_x, f_y, f_z), a fourth (min |d|^2) with CLEAR.
+template <int AG, int NA, int OFF, int NW, bool CLEAR>
+__device__ __forceinline__ bool exchange_half_grid_apf(const float *part, uint64_t *xs,
+                                                       float *slot, uint32_t C, uint32_t rank,
+                                                       int lane, uint32_t tag, bool ok,
+                                                       float (&F)[3], float &md2) {
+    constexpr int NV = CLEAR ? 4 : 3;
+    if (lane < NA) {
+        const float4 s = sum_warp_records<AG, OFF, NW, CLEAR>(part, lane);
+        uint64_t *dst = xs + 4 * (rank * AG + OFF + lane);
+        st_relaxed_u64(dst, xword(tag, s.x));
+        st_relaxed_u64(dst + 1, xword(tag, s.y));
+        st_relaxed_u64(dst + 2, xword(tag, s.z));
+        if (CLEAR) st_relaxed_u64(dst + 3, xword(tag, s.w));
+    }
+    constexpr int J = NA > 0 ? (kMaxCluster * NA + 31) / 32 : 1;
+    const int npairs = static_cast<int>(C) * NA;
+    uint64_t w[J][NV];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int p = lane + 32 * j;
+        if (p < npairs) {
+            const uint64_t *src = xs + 4 * ((p / NA) * AG + OFF + p % NA);
+#pragma unroll
+            for (int c = 0; c < NV; ++c) w[j][c] = ld_relaxed_u64(src + c);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int p = lane + 32 * j;
+        if (p < npairs) {
+            const int r = p / NA, a = OFF + p % NA;
+            const uint64_t *src = xs + 4 * (r * AG + a);
+            float val[4] = {0.0f, 0.0f, 0.0f, INFINITY};
+#pragma unroll
+            for (int c = 0; c < NV; ++c) {
+                for (uint32_t it = 0; ok && static_cast<uint32_t>(w[j][c] >> 32) != tag; ++it) {
+                    if (it == kPollLimit) ok = false;
+                    else w[j][c] = ld_relaxed_u64(src + c);
+                }
+                val[c] = __uint_as_float(static_cast<uint32_t>(w[j][c]));
+            }
+            *reinterpret_cast<float4 *>(slot + 4 * (r * AG + a)) =
+                make_float4(val[0], val[1], val[2], val[3]);
+        }
+    }
+    __syncwarp();
+    if (lane >= OFF && lane < OFF + NA) sum_rank_records<AG, CLEAR>(slot, C, lane, F, md2);
+    return ok;
+}
+
+// One step of Sec. IV-A for an APF agent: F = k_a (goal - p) - D v + kf f
+// with kf = rho k_r and f the Eq. (apf) sum; the rest as agent_step.
+template <bool CLEAR>
+__device__ __forceinline__ void agent_step_apf(float (&p)[3], float (&v)[3], float kf, float k_a,
+                                               float R, const float (&goal)[3], float h, float dt,
+                                               float damping, float clear_margin,
+                                               float clear_beta, const float (&f)[3], float md2,
+                                               float &L, float &pen, float &minc, float &m) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float F = k_a * (goal[d] - p[d]) - damping * v[d] + kf * f[d];
+        v[d] = fmaf(h, F, v[d]);
+    }
+    const float vn = fmaf(v[2], v[2], fmaf(v[1], v[1], v[0] * v[0]));
+    L = fmaf(dt, vn > 0.0f ? vn * rsqrt_approx(vn) : 0.0f, L);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) p[d] = fmaf(dt, v[d], p[d]);
+    m = INFINITY;
+    if (CLEAR) {
+        m = sqrtf(md2) - R;
+        pen += softplus_f(clear_margin - m, clear_beta);
+        minc = fminf(minc, m);
+    }
+}
+
 // GRID selects the exchange: false -- the C CTAs of a group form a thread-
 // block cluster and exchange over DSMEM; true -- groups of C consecutive
 // CTAs of a cooperative (all co-resident) grid exchange through global
 // memory, which lets groups fill every SM whatever the GPC layout.
-template <int AG, int NM, int NT, bool CLEAR, bool GRID>
+// ENS compiles the heterogeneous ensemble (Sec. IV-A agent set with the
+// heuristics of Eq. (apf) and Eq. (mfi)): the last n_apf agents form the
+// last n_groups_apf groups and use APF, the others MFI; every group is
+// homogeneous, so the branch between the two pair loops is uniform per CTA.
+template <int AG, int NM, int NT, bool CLEAR, bool GRID, bool ENS = false>
 __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
     constexpr int NW = NT / 32;       // compute warps; warp NW is the exchange warp
     constexpr int H0 = (AG + 1) / 2;  // agents [0, H0) form half 0, [H0, AG) half 1
@@ -553,7 +793,22 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
         group = cluster_id_x();
     }
     int a0, na;
-    group_range(static_cast<int>(group), A.n_agents, A.n_groups, a0, na);
+    bool apf = false;
+    if constexpr (ENS) {
+        const int gm = A.n_groups - A.n_groups_apf, nm = A.n_agents - A.n_apf;
+        if (static_cast<int>(group) < gm) {
+            group_range(static_cast<int>(group), nm, gm, a0, na);
+        } else {
+            apf = true;
+            group_range(static_cast<int>(group) - gm, A.n_apf, A.n_groups_apf, a0, na);
+            a0 += nm;
+        }
+    } else {
+        group_range(static_cast<int>(group), A.n_agents, A.n_groups, a0, na);
+    }
+    // floats per agent record exchanged each step: (W, min |d|^2) for MFI,
+    // (f_x, f_y, f_z, min |d|^2) for APF
+    const int SR = apf ? 4 : 2;
 
     // N_O is read on the device; all CTAs of the cluster see the same value,
     // so an early exit is taken by the whole cluster before any DSMEM access.
@@ -578,15 +833,15 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
     const int32_t start = static_cast<int32_t>(rank) * shard_len;
     int32_t cnt = min(shard_len, max(0, n_obs - start));
     float *sx = smem, *sy = smem + A.shard_cap, *sz = smem + 2 * A.shard_cap;
-    // per-warp partials of this CTA: [half][NW][AG] x (W, min |d|^2)
+    // per-warp partials of this CTA: [half][NW][AG] records
     float *partbuf = smem + 3 * A.shard_cap;
-    // per-CTA partials received from the cluster: [half][parity][rank][AG]
-    float *recv = partbuf + 4 * NW * AG;
+    // per-CTA partials received from the cluster: [half][parity][rank][AG] records
+    float *recv = partbuf + 2 * SR * NW * AG;
     // agent positions for the compute warps: [3][AG]
-    float *pos = recv + 8 * static_cast<int>(C) * AG;
-    auto part = [&](int h) { return partbuf + h * (2 * NW * AG); };
+    float *pos = recv + 4 * SR * static_cast<int>(C) * AG;
+    auto part = [&](int h) { return partbuf + h * (SR * NW * AG); };
     auto slot = [&](int h, int par) {
-        return recv + (h * 2 + par) * (2 * static_cast<int>(C) * AG);
+        return recv + (h * 2 + par) * (SR * static_cast<int>(C) * AG);
     };
 
     if (tid == 0) {
@@ -606,7 +861,7 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
     // Agent state: lane a < na of every warp reads agent a0 + a; only the
     // exchange warp integrates, the compute warps keep R and the gate.
     float p[3] = {0, 0, 0}, v[3] = {0, 0, 0}, cc[3] = {0, 0, 0};
-    float k_r = 0, k_a = 0, R = 0, G2 = -1.0f, L = 0, pen = 0, minc = INFINITY;
+    float k_r = 0, k_a = 0, R = 0, rd = 0, G2 = -1.0f, L = 0, pen = 0, minc = INFINITY;
     if (lane < na) {
         const int i = a0 + lane, n = A.n_agents;
 #pragma unroll
@@ -618,7 +873,7 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
         k_r = A.k_r[i];
         k_a = A.k_a[i];
         R = A.r_a[i] + A.r_O;
-        const float rd = A.r_d[i];
+        rd = A.r_d[i];
         // s = max(d - R, eps) <= r_d  <=>  d^2 <= (r_d + R)^2  when r_d >= eps
         G2 = rd >= A.eps ? (rd + R) * (rd + R) : -1.0f;
         if (rank == 0 && exch && A.traj) {
@@ -647,12 +902,14 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
             cnt = 0;  // keep the barrier sequence; results are flagged invalid
         }
     }
-    // pad the shard to an even length with NaN (contributes nothing)
+    // pad the shard to an even length with NaN (contributes nothing to the
+    // MFI sum), or a far point for APF groups
     const int32_t cnt_pad = (cnt + 1) & ~1;
     if (tid == 0 && cnt_pad > cnt) {
-        sx[cnt] = __int_as_float(0x7fc00000);
-        sy[cnt] = __int_as_float(0x7fc00000);
-        sz[cnt] = __int_as_float(0x7fc00000);
+        const float pad = apf ? kApfPad : __int_as_float(0x7fc00000);
+        sx[cnt] = pad;
+        sy[cnt] = pad;
+        sz[cnt] = pad;
     }
     const float eps = A.eps;
     // every CTA of the cluster is running (barriers initialised, padding and
@@ -660,25 +917,55 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
     if constexpr (GRID) __syncthreads();
     else cluster_sync_all();
 
-    if (!exch) {
-        // Compute warps: the two halves back to back; a half's partials are
-        // handed to the exchange warp while the other half is computed, and
-        // its new positions are ready long before they are needed.
-        for (int k = 0; k < A.n_steps; ++k) {
-            if (k > 0) named_sync(kPos + 0, kBoth);
-            half_step<AG, H0, 0, NM0, NT, CLEAR, false, false, true>(
-                sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(0) + 2 * (warp * AG), C, lane,
-                GlobalTail{}, pos);
-            named_arrive(kPart + 0, kBoth);
-            if (k > 0) named_sync(kPos + 1, kBoth);
-            half_step<AG, H1, H0, NM1, NT, CLEAR, false, false, true>(
-                sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(1) + 2 * (warp * AG), C, lane,
-                GlobalTail{}, pos);
-            named_arrive(kPart + 1, kBoth);
+    // The step loops of one group kind (MFI or APF).
+    auto run = [&](auto kind) {
+        constexpr bool APF = decltype(kind)::value;
+        // APF per-agent constants: 1/(R + eps), 1/r_d and the strict gate
+        // |d|^2 < (r_d + R)^2 (never when r_d + R <= 0)
+        float cRa[AG], G2s[AG];
+        f2 ird2[AG];
+        if constexpr (APF) {
+            const float cR = __fdiv_rn(1.0f, R + eps);
+            const float ird = lane < na ? __fdiv_rn(1.0f, rd) : 0.0f;
+            const float G2l = rd + R > 0.0f ? (rd + R) * (rd + R) : -1.0f;
+#pragma unroll
+            for (int a = 0; a < AG; ++a) {
+                cRa[a] = __shfl_sync(0xffffffffu, cR, a);
+                const float t = __shfl_sync(0xffffffffu, ird, a);
+                ird2[a] = pk(t, t);
+                G2s[a] = __shfl_sync(0xffffffffu, lane < na ? G2l : -1.0f, a);
+            }
         }
-    } else {
+        if (!exch) {
+            // Compute warps: the two halves back to back; a half's partials
+            // are handed to the exchange warp while the other half is
+            // computed, and its new positions are ready long before they are
+            // needed.
+            for (int k = 0; k < A.n_steps; ++k) {
+                if (k > 0) named_sync(kPos + 0, kBoth);
+                if constexpr (APF)
+                    half_step_apf<AG, H0, 0, NT, CLEAR>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
+                                                        part(0) + 4 * (warp * AG), lane, pos);
+                else
+                    half_step<AG, H0, 0, NM0, NT, CLEAR, false, false, true>(
+                        sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(0) + 2 * (warp * AG), C,
+                        lane, GlobalTail{}, pos);
+                named_arrive(kPart + 0, kBoth);
+                if (k > 0) named_sync(kPos + 1, kBoth);
+                if constexpr (APF)
+                    half_step_apf<AG, H1, H0, NT, CLEAR>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
+                                                         part(1) + 4 * (warp * AG), lane, pos);
+                else
+                    half_step<AG, H1, H0, NM1, NT, CLEAR, false, false, true>(
+                        sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(1) + 2 * (warp * AG), C,
+                        lane, GlobalTail{}, pos);
+                named_arrive(kPart + 1, kBoth);
+            }
+            return;
+        }
         const float h = A.vel_half * A.dt * A.inv_mass;
-        auto integrate = [&](int k, float W, float md2) {
+        // rec: W (MFI) or the force sum f (APF) of this lane's agent
+        auto integrate = [&](int k, const float (&rec)[3], float md2) {
             if (A.ckpt && rank == 0 && k % A.ckpt_every == 0) {
                 // adjoint checkpoint: the state (p_k, v_{k-1}) entering step k
                 const int n = A.n_agents, i = a0 + lane;
@@ -689,9 +976,22 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
                     ck[(3 + d) * n] = v[d];
                 }
             }
-            float g[3], kf, m;
-            agent_step<CLEAR>(p, v, cc, k_r, k_a, R, A.goal, h, A.dt, A.rho, A.damping,
-                              A.clear_margin, A.clear_beta, W, md2, L, pen, minc, m, g, kf);
+            float fr[3], w, m;
+            if constexpr (APF) {
+                const float kf = A.rho * k_r;
+                agent_step_apf<CLEAR>(p, v, kf, k_a, R, A.goal, h, A.dt, A.damping,
+                                      A.clear_margin, A.clear_beta, rec, md2, L, pen, minc, m);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) fr[d] = kf * rec[d];
+                w = sqrtf(fmaf(rec[2], rec[2], fmaf(rec[1], rec[1], rec[0] * rec[0])));
+            } else {
+                float g[3], kf;
+                w = rec[0];
+                agent_step<CLEAR>(p, v, cc, k_r, k_a, R, A.goal, h, A.dt, A.rho, A.damping,
+                                  A.clear_margin, A.clear_beta, w, md2, L, pen, minc, m, g, kf);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) fr[d] = kf * g[d];
+            }
             pos[lane] = p[0];
             pos[AG + lane] = p[1];
             pos[2 * AG + lane] = p[2];
@@ -703,13 +1003,13 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
                     t[1] = p[1];
                     t[2] = p[2];
                 }
-                if (A.w_trace) A.w_trace[(size_t)i * A.n_steps + k] = W;
+                if (A.w_trace) A.w_trace[(size_t)i * A.n_steps + k] = w;
                 if (A.m_trace) A.m_trace[(size_t)i * A.n_steps + k] = m;
                 if (A.f_trace) {
                     float *f = A.f_trace + ((size_t)i * A.n_steps + k) * 3;
-                    f[0] = kf * g[0];
-                    f[1] = kf * g[1];
-                    f[2] = kf * g[2];
+                    f[0] = fr[0];
+                    f[1] = fr[1];
+                    f[2] = fr[2];
                 }
             }
         };
@@ -718,34 +1018,49 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
         bool ok = true;
         uint32_t epoch = 0;
         uint64_t *xg = nullptr;
+        // grid slots of a group: [half][parity][rank][AG] records of SR
+        // words; the ensemble kernel spaces groups for the larger record
+        constexpr int kGroupRec = ENS ? 4 : 2;
         if constexpr (GRID) {
             epoch = ld_relaxed_u32(A.xctl);
-            xg = A.xbuf + static_cast<size_t>(group) * 4 * 2 * C * AG;
+            xg = A.xbuf + static_cast<size_t>(group) * 4 * kGroupRec * C * AG;
         }
-        auto xslot = [&](int h, int par) { return xg + (h * 2 + par) * 2 * C * AG; };
+        auto xslot = [&](int hh, int par) { return xg + (hh * 2 + par) * SR * C * AG; };
+        auto exchange = [&](auto half, int k, int par, float (&rec)[3], float &md2) {
+            constexpr int HH = decltype(half)::value;
+            constexpr int NA = HH ? H1 : H0, OFF = HH ? H0 : 0;
+            if constexpr (APF) {
+                if constexpr (GRID)
+                    ok = exchange_half_grid_apf<AG, NA, OFF, NW, CLEAR>(
+                        part(HH), xslot(HH, par), slot(HH, par), C, rank, lane, xtag(epoch, k), ok,
+                        rec, md2);
+                else
+                    ok = exchange_half_apf<AG, NA, OFF, NW, CLEAR>(part(HH), slot(HH, par),
+                                                                   &bar_recv[HH][par], C, rank,
+                                                                   lane, k, ok, rec, md2);
+            } else {
+                if constexpr (GRID)
+                    ok = exchange_half_grid<AG, NA, OFF, NW, CLEAR>(part(HH), xslot(HH, par),
+                                                                    slot(HH, par), C, rank, lane,
+                                                                    xtag(epoch, k), ok, rec[0],
+                                                                    md2);
+                else
+                    ok = exchange_half<AG, NA, OFF, NW, CLEAR>(part(HH), slot(HH, par),
+                                                               &bar_recv[HH][par], C, rank, lane,
+                                                               k, ok, rec[0], md2);
+            }
+        };
         for (int k = 0; k < A.n_steps; ++k) {
             const int par = k & 1;
-            float W = 0.0f, md2 = INFINITY;
+            float rec[3] = {0.0f, 0.0f, 0.0f}, md2 = INFINITY;
             named_sync(kPart + 0, kBoth);
-            if constexpr (GRID)
-                ok = exchange_half_grid<AG, H0, 0, NW, CLEAR>(part(0), xslot(0, par), slot(0, par),
-                                                              C, rank, lane, xtag(epoch, k), ok, W,
-                                                              md2);
-            else
-                ok = exchange_half<AG, H0, 0, NW, CLEAR>(part(0), slot(0, par), &bar_recv[0][par],
-                                                         C, rank, lane, k, ok, W, md2);
-            if (lane < H0 && lane < na) integrate(k, W, md2);
+            exchange(std::integral_constant<int, 0>{}, k, par, rec, md2);
+            if (lane < H0 && lane < na) integrate(k, rec, md2);
             __syncwarp();
             if (k + 1 < A.n_steps) named_arrive(kPos + 0, kBoth);
             named_sync(kPart + 1, kBoth);
-            if constexpr (GRID)
-                ok = exchange_half_grid<AG, H1, H0, NW, CLEAR>(part(1), xslot(1, par), slot(1, par),
-                                                               C, rank, lane, xtag(epoch, k), ok, W,
-                                                               md2);
-            else
-                ok = exchange_half<AG, H1, H0, NW, CLEAR>(part(1), slot(1, par), &bar_recv[1][par],
-                                                          C, rank, lane, k, ok, W, md2);
-            if (lane >= H0 && lane < na) integrate(k, W, md2);
+            exchange(std::integral_constant<int, 1>{}, k, par, rec, md2);
+            if (lane >= H0 && lane < na) integrate(k, rec, md2);
             __syncwarp();
             if (k + 1 < A.n_steps) named_arrive(kPos + 1, kBoth);
         }
@@ -763,6 +1078,12 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
             if (A.clear_pen) A.clear_pen[i] = pen;
             if (A.min_clear) A.min_clear[i] = minc;
         }
+    };
+    if constexpr (ENS) {
+        if (apf) run(std::true_type{});
+        else run(std::false_type{});
+    } else {
+        run(std::false_type{});
     }
     // no CTA leaves while another may still deliver into its shared memory
     if constexpr (!GRID) cluster_sync_all();
@@ -775,6 +1096,10 @@ RolloutKernel rollout_kernel_noclear(int ag, int nt);
 RolloutKernel rollout_kernel_clear(int ag, int nt);
 RolloutKernel rollout_kernel_grid_noclear(int ag, int nt);
 RolloutKernel rollout_kernel_grid_clear(int ag, int nt);
+RolloutKernel rollout_kernel_ens_noclear(int ag, int nt);
+RolloutKernel rollout_kernel_ens_clear(int ag, int nt);
+RolloutKernel rollout_kernel_ens_grid_noclear(int ag, int nt);
+RolloutKernel rollout_kernel_ens_grid_clear(int ag, int nt);
 
 // SFU share of the reciprocals: NM of AG agents use rcp.approx, the rest the
 // Newton-Raphson path.  Per obstacle pair an SFU agent costs 8 FMA-pipe

@@ -21,4 +21,5 @@ from .workloads import (  # noqa: F401
     batch_workloads,
     adjoint_workload,
     serve_stream,
+    ensemble_agents,
 )

@@ -124,6 +124,29 @@ def tabletop_workload(seed: int = 1002, n_agents: int = 256, n_steps: int = 500,
             "scene": scene}
 
 
+# Heterogeneous ensemble (the paper's multi-agent runs: two agents per
+# heuristic, one with a large and one with a small detection radius).  The
+# APF term grows as |d|^-3 where the MFI weight grows as 1/|d|, so APF gains
+# are scaled down to give forces of the same order near the obstacles.
+APF_GAIN = 1e-3
+R_D_SMALL, R_D_LARGE = 0.05, 0.10
+
+
+def ensemble_agents(agents: dict, n_apf: int, apf_gain: float = APF_GAIN,
+                    r_d=(R_D_SMALL, R_D_LARGE)) -> dict:
+    """An agent set turned into a heterogeneous ensemble: the last ``n_apf``
+    agents are the APF ones (gains k_r scaled by ``apf_gain``), the others
+    MFI; within each heuristic the detection radius alternates small, large."""
+    ag = {k: np.array(v, copy=True) for k, v in agents.items()}
+    n = ag["k_r"].size
+    nm = n - n_apf
+    idx = np.arange(n)
+    local = np.where(idx < nm, idx, idx - nm)
+    ag["r_d"] = np.where(local % 2 == 0, r_d[0], r_d[1]).astype(np.float32)
+    ag["k_r"][nm:] = (ag["k_r"][nm:].astype(np.float64) * apf_gain).astype(np.float32)
+    return ag
+
+
 def batch_workloads(seed: int = 1003, n_scenes: int = 64) -> list:
     """64 uneven sphere-cloud queries: raw points log-uniform in [5k, 300k],
     voxel U[4, 10] mm, agents log-uniform in {32..1024}, steps U{100..1000}."""

@@ -65,6 +65,12 @@ def test_mirrored_obstacles_cancel_and_permutation():
     out = _f(obs, 0.005, p, _ag(1.0, 0.06))
     single = _f(obs[:, :40], 0.005, p, _ag(1.0, 0.06))
     assert np.abs(out["f_r"]).max() <= 1e-12 * np.abs(single["f_r"]).max()
+    # the term-magnitude sum does not cancel: it doubles, and for one
+    # obstacle it equals the force magnitude
+    assert out["f_abs"][0] == pytest.approx(2.0 * single["f_abs"][0], rel=1e-13)
+    one = _f(obs[:, :1], 0.005, p, _ag(1.0, np.inf), rho=3.0)
+    assert one["f_abs"][0] == pytest.approx(np.linalg.norm(one["f_r"][:, 0]), rel=1e-14)
+    assert single["f_abs"][0] >= np.linalg.norm(single["f_r"][:, 0])
     perm = g.permutation(40)
     a = _f(obs[:, :40], 0.005, p, _ag(1.0, 0.06))["f_r"]
     b = _f(obs[:, :40][:, perm], 0.005, p, _ag(1.0, 0.06))["f_r"]
