@@ -40,6 +40,9 @@ sys.path.insert(0, ROOT)
 METRIC = "agent-obstacle interactions/s (% FP32 peak) and p50/p99 plan latency vs plain rollout"
 UNIT = "interactions/s"
 FLOPS_PER_INTERACTION = 13      # 3 sub, 5 for |d|^2, rsqrt, mul, sub, rcp, accumulate
+# APF pair (Eq. apf): 3 sub, 5 for |d|^2, rsqrt, 1/rho - 1/r_d, 3 mul for the
+# coefficient, 3 accumulating FMAs (6); clamp/gate selects not counted
+APF_FLOPS_PER_INTERACTION = 19
 FP32_LANES_PER_SM = 128
 OBS_CAP = 131072
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "rollout_tabletop_256x500.md")
@@ -615,6 +618,65 @@ def bench_adjoint(gm, args, reps=3):
             "gradient_cost_over_plain_forward": (t_fwd + t_adj) / t_plain}
 
 
+def bench_ensemble(gm, args, reps=5):
+    """Heterogeneous ensemble (Eq. apf + Eq. mfi) on the tabletop query:
+    256 agents x 500 steps, the last 128 on APF, in one launch; beside it the
+    plain MFI rollout of the same 256 agents and an all-APF launch, all in
+    the launch shape the autotuner picks for the MFI rollout."""
+    import torch
+    import synth
+    w = synth.tabletop_workload()
+    prm = w["params"]
+    na, nk, n_apf = 256, int(prm.n_steps), 128
+    xyz = torch.from_numpy(w["xyz"]).cuda()
+    probe = gm.filter_cloud(xyz, w["T"], w["workspace"], cap=OBS_CAP)
+    cap = (int(probe.count() * 1.05) + 63) // 64 * 64
+    obs = gm.filter_cloud(xyz, w["T"], w["workspace"], cap=cap)
+    n_o = obs.count()
+    dev = lambda a: {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda()  # noqa: E731
+                     for k, v in a.items()}
+    mixed = dev(synth.ensemble_agents(w["agents"], n_apf))
+    all_apf = dev(synth.ensemble_agents(w["agents"], na))
+    mfi = dev(w["agents"])
+    out = gm.alloc_rollout_out(na, nk, want_traj=True, want_clear=False)
+    shapes = {"ensemble": gm.autotune_ensemble(obs, mixed, n_apf, prm, out=out, candidates=16,
+                                               probe_steps=100)[0],
+              "mfi": gm.autotune_rollout(obs, mfi, prm, out=out, candidates=16, probe_steps=100)[0],
+              "apf": gm.autotune_ensemble(obs, all_apf, na, prm, out=out, candidates=16,
+                                          probe_steps=100)[0]}
+    cur = torch.cuda.current_stream()
+    runs = {"ensemble": lambda: gm.rollout_ensemble(obs, mixed, n_apf, prm, out=out,
+                                                    tuning=shapes["ensemble"]),
+            "mfi": lambda: gm.rollout_agents(obs, mfi, prm, out=out, tuning=shapes["mfi"]),
+            "apf": lambda: gm.rollout_ensemble(obs, all_apf, na, prm, out=out,
+                                               tuning=shapes["apf"])}
+    for k, fn in runs.items():   # warm-up launches, one NVTX range each (for ncu)
+        torch.cuda.nvtx.range_push(f"warm_{k}")
+        fn()
+        torch.cuda.nvtx.range_pop()
+    gm.sync()
+    times = {k: _events(torch, cur, fn, reps) for k, fn in runs.items()}
+    gm.sync()
+    peaks = _measured_peaks()
+    sm_max = peaks.get("sm_max_mhz") or 2032.0
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    pairs = n_o * nk
+    flops = {"ensemble": pairs * ((na - n_apf) * FLOPS_PER_INTERACTION +
+                                  n_apf * APF_FLOPS_PER_INTERACTION),
+             "mfi": pairs * na * FLOPS_PER_INTERACTION,
+             "apf": pairs * na * APF_FLOPS_PER_INTERACTION}
+    res = {"workload": f"tabletop 640x480 -> 5 mm voxels (N_O = {n_o}); 256 agents x 500 steps; "
+                       f"ensemble = last {n_apf} agents APF (gain x 1e-3), r_d alternating 5/10 cm",
+           "tuning": {k: list(v) for k, v in shapes.items()}, "peak_TFLOP_per_s": peak,
+           "flops_per_interaction": {"mfi": FLOPS_PER_INTERACTION,
+                                     "apf": APF_FLOPS_PER_INTERACTION}}
+    for k, s in times.items():
+        res[k] = {"ms": 1e3 * s, "interactions_per_s": na * pairs / s,
+                  "TFLOP_per_s": flops[k] / s / 1e12, "fp32_frac": flops[k] / s / 1e12 / peak}
+    return res
+
+
 def bench_served(gm, args):
     """1 kHz open-loop request stream (200k-point tabletop frames with 4 moving
     spheres, 1 cm voxels, N_a in {64, 256, 1024}, N_k = 300) through the
@@ -795,6 +857,7 @@ def main():
 PATTERNS = {"filter_stream": lambda gm, a: bench_filter_stream(gm, a),
             "batched": lambda gm, a: bench_batched(gm, a),
             "adjoint": lambda gm, a: bench_adjoint(gm, a),
+            "ensemble": lambda gm, a: bench_ensemble(gm, a),
             "served": lambda gm, a: bench_served(gm, a)}
 
 

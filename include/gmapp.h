@@ -361,6 +361,8 @@ gmapp_status gmapp_pick_tuning(gmapp_ctx *ctx, int64_t obs_cap, int32_t n_agents
  * in proportion to the two counts.  `tune` selects the launch shape as in
  * rollout_agents_tuned (agents_per_cta is an upper bound per group; at most
  * 12 agents per group and 384 threads), or NULL for the library's choice.
+ * With tune = NULL the shape is the one gmapp_autotune_ensemble cached
+ * for these sizes, else the cost model's choice among ensemble shapes.
  * n_apf = 0 is rollout_agents.  GMAPP_ERR_INVALID_ARG for n_apf outside
  * [0, n], for adjoint checkpoints (out->ckpt) with n_apf > 0, or for a shape
  * that does not fit. */
@@ -368,6 +370,19 @@ gmapp_status rollout_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *obs,
                               const gmapp_agents *agents, int32_t n_apf,
                               const gmapp_rollout_params *prm, gmapp_rollout_out *out,
                               const gmapp_tuning *tune, gmapp_stream stream);
+
+/* gmapp_autotune_rollout for an ensemble with n_apf APF agents: ranks the
+ * shapes that fit the ensemble (groups split by heuristic), times the best
+ * `max_candidates` on the caller's inputs and caches the fastest for later
+ * rollout_ensemble calls with tune = NULL and the same (obs->cap,
+ * agents->n, n_apf, clearance outputs).  Same arguments, errors and
+ * synchronous behaviour as gmapp_autotune_rollout; n_apf = 0 is that call. */
+gmapp_status gmapp_autotune_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                                     const gmapp_agents *agents, int32_t n_apf,
+                                     const gmapp_rollout_params *prm,
+                                     gmapp_rollout_out *out, int32_t max_candidates,
+                                     int32_t probe_steps, gmapp_tuning *best, float *best_ms,
+                                     gmapp_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Cost and selection: score_and_select (Sec. IV-A "Cost Functions" and        */

@@ -22,7 +22,7 @@ from ._abi import check
 
 __all__ = ["Context", "context", "Obstacles", "filter_cloud", "filter_cloud_noalloc",
            "filter_workspace_bytes", "rollout_agents", "rollout_ensemble", "score_and_select",
-           "pick_tuning", "autotune_rollout", "rollout_adjoint", "GMappRollout", "sync", "GmappError",
+           "pick_tuning", "autotune_rollout", "autotune_ensemble", "rollout_adjoint", "GMappRollout", "sync", "GmappError",
            "FilterBatch", "Batch", "Server"]
 
 GmappError = _abi.GmappError
@@ -285,6 +285,26 @@ def autotune_rollout(obs: Obstacles, agents: dict, prm, out: dict | None = None,
                                              C.byref(os_), int(candidates), int(probe_steps),
                                              C.byref(t), C.byref(ms), _stream(stream)),
           "gmapp_autotune_rollout")
+    return (t.cluster, t.agents_per_cta, t.threads, t.exchange), float(ms.value)
+
+
+def autotune_ensemble(obs: Obstacles, agents: dict, n_apf: int, prm, out: dict | None = None,
+                      candidates: int = 12, probe_steps: int = 60, stream=None):
+    """autotune_rollout for an ensemble whose last ``n_apf`` agents use APF;
+    later rollout_ensemble calls of the same sizes without ``tuning`` use
+    the shape it caches."""
+    ctx = context()
+    na = int(agents["k_r"].numel())
+    if out is None:
+        out = alloc_rollout_out(na, int(prm.n_steps))
+    ob, ag, pr, os_ = obs._struct(), _agents_struct(agents), _params_struct(prm), _out_struct(out)
+    t = _abi.Tuning()
+    ms = C.c_float()
+    check(_abi.load().gmapp_autotune_ensemble(ctx.handle, C.byref(ob), C.byref(ag), int(n_apf),
+                                              C.byref(pr), C.byref(os_), int(candidates),
+                                              int(probe_steps), C.byref(t), C.byref(ms),
+                                              _stream(stream)),
+          "gmapp_autotune_ensemble")
     return (t.cluster, t.agents_per_cta, t.threads, t.exchange), float(ms.value)
 
 

@@ -120,6 +120,10 @@ PROTOTYPES = {
                                          C.POINTER(RolloutParams), C.POINTER(RolloutOut),
                                          C.c_int32, C.c_int32, C.POINTER(Tuning),
                                          C.POINTER(C.c_float), P]),
+    "gmapp_autotune_ensemble": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents), C.c_int32,
+                                          C.POINTER(RolloutParams), C.POINTER(RolloutOut),
+                                          C.c_int32, C.c_int32, C.POINTER(Tuning),
+                                          C.POINTER(C.c_float), P]),
     "gmapp_adjoint_workspace_bytes": (C.c_size_t, [C.c_int32, C.POINTER(RolloutParams)]),
     "rollout_adjoint": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
                                   C.POINTER(RolloutParams), C.POINTER(CostWeights), P, P,

@@ -159,9 +159,12 @@ int max_active_clusters(gmapp_ctx *ctx, const Shape &s) {
 // launch must fit in one wave (its groups poll one another).
 // CTAs that share an SM (when the occupancy allows more than one) share its
 // pipes, so the pair loop slows by the number of co-resident CTAs per SM.
+// In an ensemble every group runs AG agent slots and the APF groups set
+// the pace: an APF pair costs ~1.32 MFI pairs (measured on B300, tabletop).
 double model_cost(const Shape &s, int m, int64_t n_obs_est, int sm_count) {
     const double shard = static_cast<double>((n_obs_est + s.cluster - 1) / s.cluster);
-    const double rate = std::min(7.0, 1.5 + 1.2 * s.ag) * (s.threads >= 384 ? 1.0 : 0.95);
+    const double rate = std::min(7.0, 1.5 + 1.2 * s.ag) * (s.threads >= 384 ? 1.0 : 0.95) /
+                        (s.n_apf > 0 ? 1.32 : 1.0);
     const double share =
         std::max(1.0, static_cast<double>(std::min(s.groups, m)) * s.cluster / sm_count);
     const double loop = s.ag * std::max(shard, 64.0) / rate * share;
@@ -347,18 +350,25 @@ gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agen
 
 using namespace gmapp;
 
-extern "C" gmapp_status gmapp_autotune_rollout(gmapp_ctx *ctx, const gmapp_obstacles *obs,
-                                               const gmapp_agents *agents,
-                                               const gmapp_rollout_params *prm,
-                                               gmapp_rollout_out *out, int32_t max_candidates,
-                                               int32_t probe_steps, gmapp_tuning *best,
-                                               float *best_ms, gmapp_stream stream) {
+namespace {
+
+// Measured choice of the launch shape (MFI rollout, or an ensemble with
+// n_apf APF agents): rank by the model, time the best candidates on the
+// caller's inputs, cache the fastest.
+gmapp_status autotune_impl(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agents *agents,
+                           int32_t n_apf, const gmapp_rollout_params *prm,
+                           gmapp_rollout_out *out, int32_t max_candidates, int32_t probe_steps,
+                           gmapp_tuning *best, float *best_ms, gmapp_stream stream) {
     if (!ctx || !best || max_candidates < 1 || probe_steps < 1) {
         set_error("gmapp_autotune_rollout: invalid argument");
         return GMAPP_ERR_INVALID_ARG;
     }
     gmapp_status st = validate(obs, agents, prm, out);
     if (st != GMAPP_OK) return st;
+    if (n_apf < 0 || n_apf > agents->n || (n_apf > 0 && out->ckpt)) {
+        set_error("gmapp_autotune_ensemble: n_apf outside [0, n], or checkpoints with n_apf > 0");
+        return GMAPP_ERR_INVALID_ARG;
+    }
     const bool clear = wants_clear(out);
     // 1. candidates ranked by the model, one per (cluster, groups, threads)
     struct Cand {
@@ -373,14 +383,16 @@ extern "C" gmapp_status gmapp_autotune_rollout(gmapp_ctx *ctx, const gmapp_obsta
                 int last_groups = -1;
                 for (int a = 1; a <= kMaxAgents; ++a) {
                     Shape s;
-                    if (!resolve(ctx, obs->cap, agents->n, gmapp_tuning{C, a, nt, x}, clear, &s))
+                    if (!resolve(ctx, obs->cap, agents->n, gmapp_tuning{C, a, nt, x}, clear, &s,
+                                 n_apf))
                         continue;
                     if (s.groups == last_groups) continue;
                     last_groups = s.groups;
                     const int m = max_active_clusters(ctx, s);
                     if (m <= 0) continue;
                     const double cost = model_cost(s, m, obs->cap, ctx->sm_count);
-                    if (cost < 1e299) cands.push_back({cost, gmapp_tuning{C, s.ag, nt, x}});
+                    if (cost < 1e299)
+                        cands.push_back({cost, gmapp_tuning{C, n_apf > 0 ? a : s.ag, nt, x}});
                 }
             }
     if (cands.empty()) {
@@ -400,9 +412,9 @@ extern "C" gmapp_status gmapp_autotune_rollout(gmapp_ctx *ctx, const gmapp_obsta
     float best_t = 1e30f;
     gmapp_status result = GMAPP_OK;
     for (const Cand &c : cands) {
-        if ((st = launch(ctx, obs, agents, &probe, out, c.t, stream)) != GMAPP_OK) continue;
+        if ((st = launch(ctx, obs, agents, &probe, out, c.t, stream, n_apf)) != GMAPP_OK) continue;
         cudaEventRecord(e0, stream);
-        st = launch(ctx, obs, agents, &probe, out, c.t, stream);
+        st = launch(ctx, obs, agents, &probe, out, c.t, stream, n_apf);
         cudaEventRecord(e1, stream);
         if (st != GMAPP_OK) continue;
         if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -425,8 +437,30 @@ extern "C" gmapp_status gmapp_autotune_rollout(gmapp_ctx *ctx, const gmapp_obsta
     }
     if (best_ms) *best_ms = best_t * static_cast<float>(prm->n_steps) / probe.n_steps;
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[std::make_tuple(ctx->device, obs->cap, agents->n, clear, 0)] = *best;
+    g_tune_cache[std::make_tuple(ctx->device, obs->cap, agents->n, clear, n_apf)] = *best;
     return GMAPP_OK;
+}
+
+}  // namespace
+
+extern "C" gmapp_status gmapp_autotune_rollout(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                                               const gmapp_agents *agents,
+                                               const gmapp_rollout_params *prm,
+                                               gmapp_rollout_out *out, int32_t max_candidates,
+                                               int32_t probe_steps, gmapp_tuning *best,
+                                               float *best_ms, gmapp_stream stream) {
+    return autotune_impl(ctx, obs, agents, 0, prm, out, max_candidates, probe_steps, best,
+                         best_ms, stream);
+}
+
+extern "C" gmapp_status gmapp_autotune_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                                                const gmapp_agents *agents, int32_t n_apf,
+                                                const gmapp_rollout_params *prm,
+                                                gmapp_rollout_out *out, int32_t max_candidates,
+                                                int32_t probe_steps, gmapp_tuning *best,
+                                                float *best_ms, gmapp_stream stream) {
+    return autotune_impl(ctx, obs, agents, n_apf, prm, out, max_candidates, probe_steps, best,
+                         best_ms, stream);
 }
 
 extern "C" gmapp_status gmapp_pick_tuning(gmapp_ctx *ctx, int64_t obs_cap, int32_t n_agents,

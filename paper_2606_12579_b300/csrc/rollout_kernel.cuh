@@ -534,11 +534,12 @@ __device__ __forceinline__ bool exchange_half_grid(const float *part, uint64_t *
 //          clamp of the surface distance at eps)
 //   term   (1/rho - 1/r_d) rho^-2 r d    ((1/|d| - 1/r_d)|d|^-3 d unclamped)
 // A pair outside the gate takes 1/rho = 1/r_d, so its coefficient is exactly
-// zero; r comes from rsqrt(max(|d|^2, 1e-30)), so a pair at d = 0 has a
-// finite coefficient times d = 0.  Shard padding for APF groups is a far
-// finite point (kApfPad), never NaN (NaN times a zero coefficient is NaN).
-// Per pair: 13 FMA-pipe lane-ops (3 sub, 3 for |d|^2, 4 for the
-// coefficient, 3 accumulating FMAs), one SFU rsqrt, clamp/gate on the ALU.
+// zero; |d|^2 carries an added 1e-30 (below the rounding of any |d| above
+// 1e-11 m), so a pair at d = 0 has a finite coefficient times d = 0.  Shard
+// padding for APF groups is a far finite point (kApfPad), never NaN (NaN
+// times a zero coefficient is NaN).  Per pair: 13 FMA-pipe lane-ops (3 sub,
+// 3 for |d|^2, 4 for the coefficient, 3 accumulating FMAs), one SFU rsqrt,
+// and the clamp and gate select on the ALU.
 constexpr float kApfPad = 1e18f;
 
 template <int AG, int NA, int OFF, bool CLEAR>
@@ -546,14 +547,14 @@ __device__ __forceinline__ void apf_pair_terms(f2 ox, f2 oy, f2 oz, const f2 (&X
                                                const f2 (&Y)[NA], const f2 (&Z)[NA],
                                                f2 (&fx)[NA], f2 (&fy)[NA], f2 (&fz)[NA],
                                                float (&mn)[NA], const float (&cRa)[AG],
-                                               const f2 (&ird2)[AG], const float (&G2a)[AG]) {
+                                               const f2 (&ird2)[AG], const float (&G2a)[AG],
+                                               f2 tiny2) {
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
         const f2 dx = sub2(X[a], ox), dy = sub2(Y[a], oy), dz = sub2(Z[a], oz);
-        const f2 d2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        const f2 d2 = fma2(dz, dz, fma2(dy, dy, fma2(dx, dx, tiny2)));
         const float d2l = lo_of(d2), d2h = hi_of(d2);
-        const float rl = rsqrt_approx(fmaxf(d2l, 1e-30f));
-        const float rh = rsqrt_approx(fmaxf(d2h, 1e-30f));
+        const float rl = rsqrt_approx(d2l), rh = rsqrt_approx(d2h);
         const float ird = lo_of(ird2[OFF + a]);
         const float il = d2l < G2a[OFF + a] ? fminf(rl, cRa[OFF + a]) : ird;
         const float ih = d2h < G2a[OFF + a] ? fminf(rh, cRa[OFF + a]) : ird;
@@ -589,12 +590,14 @@ __device__ __forceinline__ void half_step_apf(const float *sx, const float *sy, 
             fx[a] = fy[a] = fz[a] = 0ull;
             mn[a] = INFINITY;
         }
+        const f2 tiny2 = pk(1e-30f, 1e-30f);
 #pragma unroll 2
         for (int j = 2 * tid; j < cnt_pad; j += 2 * NT) {
             const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
             const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
             const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
-            apf_pair_terms<AG, NA, OFF, CLEAR>(ox, oy, oz, X, Y, Z, fx, fy, fz, mn, cRa, ird2, G2a);
+            apf_pair_terms<AG, NA, OFF, CLEAR>(ox, oy, oz, X, Y, Z, fx, fy, fz, mn, cRa, ird2, G2a,
+                                               tiny2);
         }
         float v0[P], v1[P], v2[P], vm[P];
 #pragma unroll

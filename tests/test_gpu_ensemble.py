@@ -248,3 +248,22 @@ def test_ensemble_invalid_arguments(gm):
     with pytest.raises(gm.GmappError) as e:
         gm.rollout_ensemble(o, big, 2, w["params"], tuning=(1, 16, 256, 0))
     assert e.value.status == 1
+
+
+def test_ensemble_autotuner(gm):
+    """gmapp_autotune_ensemble times ensemble shapes on the caller's inputs;
+    a later rollout_ensemble of the same sizes without a shape uses the
+    cached one and still matches the oracle."""
+    w = _sphere_ensemble(n_agents=40, n_apf=16, n_steps=150)
+    obs, r_O = _filtered(w)
+    o = _gpu_obstacles(gm, obs, r_O, cap=4096)
+    ag = to_dev_agents(w["agents"])
+    out = gm.alloc_rollout_out(40, 150)
+    shape, ms = gm.autotune_ensemble(o, ag, 16, w["params"], out=out, candidates=6, probe_steps=30)
+    assert ms > 0 and len(shape) == 4 and shape[1] <= 12
+    a = gm.rollout_ensemble(o, ag, 16, w["params"])
+    b = gm.rollout_ensemble(o, ag, 16, w["params"], tuning=shape)
+    gm.sync()
+    assert np.array_equal(a["traj"].cpu().numpy(), b["traj"].cpu().numpy())
+    ref = oracle.rollout(obs, r_O, w["agents"], w["params"], n_apf=16)
+    _compare(a, ref)
