@@ -8,8 +8,11 @@ generators in ``synth``.
 Functions (each cites the paper passage it follows):
   filter_cloud    Sec. IV-B / V-A   camera cloud -> sorted voxel centres S_W
   cf_eval         Eq. (mfi), Alg. 1 W, clearance and f_r at given states
+  apf_eval        Eq. (apf)         APF force and clearance at given states
   rollout         Sec. IV-A         N_k-step point-mass rollout + cost sums
-  score_select    Sec. IV-A         weighted cost and argmin selection
+                                    (MFI agents, and APF agents of an ensemble)
+  costs, select   Sec. IV-A         weighted cost and argmin selection
+  four_term_costs Eq. (cost_function) goal, obstacle, path, smoothness terms
   fd_gradient     --                central finite differences of the cost
 Parity pins for every function live in tests/test_oracle_*.py.
 """
@@ -193,6 +196,47 @@ def costs(ro: dict, prm) -> np.ndarray:
     g = np.asarray(prm.goal, dtype=np.float64)[:, None]
     dgoal = np.sqrt(((ro["p_final"] - g) ** 2).sum(axis=0))
     return prm.w_path * ro["path_len"] + prm.w_goal * dgoal + prm.w_clear * ro["clear_pen"]
+
+
+def four_term_costs(traj, m_trace, goal, dt: float, r_c: float, a_max: float,
+                    w=(1.0, 1.0, 1.0, 1.0)) -> dict:
+    """Eq. (cost_function): C_i = sum_j w_j C_ij with the four terms of
+    Sec. IV-A "Cost Functions", per agent, in FP64.
+
+    The candidate trajectory is the N_k states at which the field is
+    evaluated, xi^(k) = p_(k-1) for k = 1..N_k (so d^(1) is the distance of
+    the start to the goal), taken from ``traj`` [N_a, N_k+1, 3]; the
+    obstacle distance at xi^(k) is the clearance m_(k-1) of ``m_trace``
+    [N_a, N_k] (inf without obstacles); r_c is the radius of Eqs. (cost_goal)
+    and (cost_obs), one value for all agents.
+      C_goal   = 1/N_k sum_k min(|xi^k - g|, r_c) / r_c                 Eq. (cost_goal)
+      C_obs    = 1/N_k sum_k (1 - min(m^k, r_c) / r_c)                   Eq. (cost_obs)
+      L        = sum_{k=2}^{N_k} |xi^k - xi^(k-1)|,  d1 = |xi^1 - g|
+      C_path   = 1 - d1 / L  if L >= d1,  else 1 - L / d1  (0 when L = d1 = 0)   Eq. (cost_path)
+      J        = sum_{k=4}^{N_k} |xi^k - 3 xi^(k-1) + 3 xi^(k-2) - xi^(k-3)|^2
+      C_smooth = min(1, J / (N_k dt^4 a_max^2))                          Eq. (cost_smooth)
+    Returns the four terms, L, J, d1 and the weighted total C."""
+    traj = _f64(traj)
+    xi = traj[:, :-1, :]
+    nk = xi.shape[1]
+    g = np.asarray(goal, dtype=np.float64)
+    dg = np.sqrt(((xi - g) ** 2).sum(axis=2))
+    c_goal = (np.minimum(dg, r_c) / r_c).sum(axis=1) / nk
+    c_obs = (1.0 - np.minimum(_f64(m_trace), r_c) / r_c).sum(axis=1) / nk
+    L = np.sqrt((np.diff(xi, axis=1) ** 2).sum(axis=2)).sum(axis=1)
+    d1 = dg[:, 0]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        c_path = np.where(L >= d1, 1.0 - d1 / L, 1.0 - L / d1)
+    c_path = np.where((L == 0.0) & (d1 == 0.0), 0.0, c_path)
+    if nk >= 4:
+        j3 = xi[:, 3:] - 3.0 * xi[:, 2:-1] + 3.0 * xi[:, 1:-2] - xi[:, :-3]
+        J = (j3 ** 2).sum(axis=(1, 2))
+    else:
+        J = np.zeros(xi.shape[0])
+    c_smooth = np.minimum(1.0, J / (nk * dt ** 4 * a_max ** 2))
+    C = w[0] * c_goal + w[1] * c_obs + w[2] * c_path + w[3] * c_smooth
+    return {"goal": c_goal, "obs": c_obs, "path": c_path, "smooth": c_smooth, "L": L, "J": J,
+            "d1": d1, "C": C}
 
 
 def select(c: np.ndarray, prev_best_cost: float = math.nan, alpha: float = 1.0) -> int:
