@@ -209,6 +209,9 @@ typedef struct {
     float clear_margin; /* softplus clearance-penalty margin (m) */
     float clear_beta;   /* softplus sharpness (1/m), > 0 */
     int32_t ckpt_every; /* adjoint checkpoint interval (steps); 0 = no checkpoints */
+    float cost_radius;  /* r_c of the goal and obstacle terms of the four-term
+                           cost (Eq. cost_goal, Eq. cost_obs), > 0 when
+                           gmapp_rollout_out.cost_terms is requested */
 } gmapp_rollout_params;
 
 /* Rollout outputs: device buffers written by rollout_agents. */
@@ -225,6 +228,17 @@ typedef struct {
     float *ckpt;      /* [ceil(n_steps/K)][6][n] state (p_k, v_{k-1}) entering steps
                          k = 0, K, 2K, ... with K = ckpt_every (rows: p x,y,z, v x,y,z),
                          for rollout_adjoint; or NULL */
+    float *cost_terms; /* [5][n] sums of the four-term cost (Eq. cost_function) over the
+                          candidate trajectory xi^(k) = p_{k-1}, k = 1..N_k (the N_k
+                          states where the field is evaluated), for score_and_select4;
+                          or NULL.  Rows: S_goal = sum_k min(|p_k - goal|, r_c) / r_c;
+                          S_obs = sum_k max(r_c - m_k, 0) / r_c; L = sum_{k=1}^{N_k-1}
+                          |p_k - p_{k-1}|; J = sum_{k=3}^{N_k-1} |p_k - 3 p_{k-1} +
+                          3 p_{k-2} - p_{k-3}|^2, accumulated as (dt h)^2 |F_{k-1} -
+                          F_{k-2}|^2 (h = vel_half dt inv_mass), the same quantity by
+                          the step rule; d1 = |p_0 - goal|.  Needs cost_radius > 0 and
+                          computes the clearance m_k.  rollout_agents and
+                          rollout_ensemble only. */
 } gmapp_rollout_out;
 
 /* Roll all agents forward N_k steps in ONE launch.  Step k (0-based):
@@ -405,6 +419,39 @@ gmapp_status score_and_select(gmapp_ctx *ctx, const gmapp_rollout_out *ro,
                               const gmapp_cost_weights *w, float prev_best_cost,
                               float alpha, float *costs, int32_t *best,
                               float *best_traj, gmapp_stream stream);
+
+/* Weights of the paper's four-term cost (Eq. cost_function). */
+typedef struct {
+    float w_goal;   /* w_1: goal distance term, Eq. (cost_goal) */
+    float w_obs;    /* w_2: obstacle distance term, Eq. (cost_obs) */
+    float w_path;   /* w_3: path length term, Eq. (cost_path) */
+    float w_smooth; /* w_4: smoothness term, Eq. (cost_smooth) */
+    float a_max;    /* maximum acceleration (m/s^2) normalising the jerk, > 0 */
+} gmapp_cost4;
+
+/* The paper's cost C_i = w_1 C_goal + w_2 C_obs + w_3 C_path + w_4 C_smooth
+ * (Sec. IV-A "Cost Functions") from the sums a rollout wrote to
+ * ro->cost_terms (see gmapp_rollout_out), with N_k = prm->n_steps:
+ *   C_goal = S_goal / N_k,  C_obs = S_obs / N_k,
+ *   C_path = 1 - d1 / L if L >= d1, else 1 - L / d1 (0 when L = d1 = 0),
+ *   C_smooth = min(1, J / (N_k dt^4 a_max^2)),
+ * then the selection of "Selection Mechanism": i* = argmin {C_i : C_i <
+ * alpha C_best} with ties to the lowest index.  C_best is the cost of the
+ * plan currently followed, kept on the device so a re-planning loop needs
+ * no host round trip:
+ *   c_best     device, one float32, in/out, or NULL.  NaN (or NULL) = no
+ *              current plan: plain argmin over the agents with a finite
+ *              cost.  When an agent is selected, *c_best becomes its cost;
+ *              when none qualifies, *best = -1 and *c_best is unchanged
+ *              (the caller keeps following the previous plan).
+ *   costs, best, best_traj  as in score_and_select.
+ * GMAPP_ERR_INVALID_ARG when ro->cost_terms is NULL, a weight or alpha is
+ * not finite, or a_max <= 0. */
+gmapp_status score_and_select4(gmapp_ctx *ctx, const gmapp_rollout_out *ro,
+                               int32_t n_agents, const gmapp_rollout_params *prm,
+                               const gmapp_cost4 *w, float *c_best, float alpha,
+                               float *costs, int32_t *best, float *best_traj,
+                               gmapp_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Batched uneven queries: rollout_batch (the perception -> rollout -> select */

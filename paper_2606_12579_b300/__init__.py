@@ -22,6 +22,7 @@ from ._abi import check
 
 __all__ = ["Context", "context", "Obstacles", "filter_cloud", "filter_cloud_noalloc",
            "filter_workspace_bytes", "rollout_agents", "rollout_ensemble", "score_and_select",
+           "score_and_select4",
            "pick_tuning", "autotune_rollout", "autotune_ensemble", "rollout_adjoint", "GMappRollout", "sync", "GmappError",
            "FilterBatch", "Batch", "Server"]
 
@@ -233,11 +234,12 @@ def _params_struct(prm) -> _abi.RolloutParams:
     s.eps, s.vel_half = float(prm.eps), float(prm.vel_half)
     s.clear_margin, s.clear_beta = float(prm.clear_margin), float(prm.clear_beta)
     s.ckpt_every = int(getattr(prm, "ckpt_every", 0))
+    s.cost_radius = float(getattr(prm, "cost_radius", 0.05))
     return s
 
 
 def alloc_rollout_out(n_agents: int, n_steps: int, want_traj=True, want_trace=False,
-                      want_clear=True, device=None) -> dict:
+                      want_clear=True, device=None, want_cost4=False) -> dict:
     torch = _torch()
     dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
     f = lambda *s: torch.empty(*s, dtype=torch.float32, device=dev)  # noqa: E731
@@ -248,14 +250,15 @@ def alloc_rollout_out(n_agents: int, n_steps: int, want_traj=True, want_trace=Fa
            "w_trace": f(n_agents, n_steps) if want_trace else None,
            "m_trace": f(n_agents, n_steps) if want_trace else None,
            "f_trace": f(n_agents, n_steps, 3) if want_trace else None,
-           "ckpt": None, "n_agents": n_agents, "n_steps": n_steps}
+           "ckpt": None, "cost_terms": f(5, n_agents) if want_cost4 else None,
+           "n_agents": n_agents, "n_steps": n_steps}
     return out
 
 
 def _out_struct(out: dict) -> _abi.RolloutOut:
     s = _abi.RolloutOut()
     for k in ("traj", "p_final", "v_final", "path_len", "clear_pen", "min_clear", "w_trace",
-              "m_trace", "f_trace", "ckpt"):
+              "m_trace", "f_trace", "ckpt", "cost_terms"):
         t = out.get(k)
         setattr(s, k, t.data_ptr() if t is not None else None)
     return s
@@ -375,6 +378,32 @@ def score_and_select(ro: dict, prm, weights=None, prev_best_cost: float = math.n
                                        float(prev_best_cost), float(alpha), _ptr(out["costs"]),
                                        _ptr(out["best"]), _ptr(out.get("best_traj")),
                                        _stream(stream)), "score_and_select")
+    return out
+
+
+def score_and_select4(ro: dict, prm, c_best=None, alpha: float = 1.0, best_traj: bool = True,
+                      out: dict | None = None, stream=None) -> dict:
+    """The paper's four-term cost (Eq. cost_function) from ``ro["cost_terms"]``
+    (a rollout with ``want_cost4``) and the selection against the cost of
+    the current plan: ``c_best`` is a device float32 tensor [1] (NaN = no
+    plan), updated in place when an agent is selected; None = plain argmin.
+    Weights from prm.w4 = (w_goal, w_obs, w_path, w_smooth) and prm.a_max."""
+    torch = _torch()
+    ctx = context()
+    na = int(ro["p_final"].shape[1])
+    dev = ro["p_final"].device
+    if out is None:
+        out = {"costs": torch.empty(na, dtype=torch.float32, device=dev),
+               "best": torch.empty(1, dtype=torch.int32, device=dev),
+               "best_traj": (torch.empty(int(prm.n_steps) + 1, 3, dtype=torch.float32, device=dev)
+                             if best_traj and ro.get("traj") is not None else None)}
+    w4 = tuple(float(v) for v in prm.w4)
+    cw = _abi.Cost4(w4[0], w4[1], w4[2], w4[3], float(prm.a_max))
+    os_, pr = _out_struct(ro), _params_struct(prm)
+    check(_abi.load().score_and_select4(ctx.handle, C.byref(os_), na, C.byref(pr), C.byref(cw),
+                                        _ptr(c_best), float(alpha), _ptr(out["costs"]),
+                                        _ptr(out["best"]), _ptr(out.get("best_traj")),
+                                        _stream(stream)), "score_and_select4")
     return out
 
 

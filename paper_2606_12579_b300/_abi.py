@@ -43,12 +43,13 @@ class RolloutParams(C.Structure):
     _fields_ = [("goal", C.c_float * 3), ("dt", C.c_float), ("n_steps", C.c_int32),
                 ("damping", C.c_float), ("inv_mass", C.c_float), ("rho", C.c_float),
                 ("eps", C.c_float), ("vel_half", C.c_float), ("clear_margin", C.c_float),
-                ("clear_beta", C.c_float), ("ckpt_every", C.c_int32)]
+                ("clear_beta", C.c_float), ("ckpt_every", C.c_int32), ("cost_radius", C.c_float)]
 
 
 class RolloutOut(C.Structure):
     _fields_ = [("traj", P), ("p_final", P), ("v_final", P), ("path_len", P), ("clear_pen", P),
-                ("min_clear", P), ("w_trace", P), ("m_trace", P), ("f_trace", P), ("ckpt", P)]
+                ("min_clear", P), ("w_trace", P), ("m_trace", P), ("f_trace", P), ("ckpt", P),
+                ("cost_terms", P)]
 
 
 class AdjointOut(C.Structure):
@@ -62,6 +63,11 @@ class Tuning(C.Structure):
 
 class CostWeights(C.Structure):
     _fields_ = [("w_path", C.c_float), ("w_goal", C.c_float), ("w_clear", C.c_float)]
+
+
+class Cost4(C.Structure):
+    _fields_ = [("w_goal", C.c_float), ("w_obs", C.c_float), ("w_path", C.c_float),
+                ("w_smooth", C.c_float), ("a_max", C.c_float)]
 
 
 class Query(C.Structure):
@@ -146,6 +152,8 @@ PROTOTYPES = {
     "gmapp_server_stats": (C.c_int, [P, C.POINTER(ServerStats)]),
     "score_and_select": (C.c_int, [P, C.POINTER(RolloutOut), C.c_int32, C.POINTER(RolloutParams),
                                    C.POINTER(CostWeights), C.c_float, C.c_float, P, P, P, P]),
+    "score_and_select4": (C.c_int, [P, C.POINTER(RolloutOut), C.c_int32, C.POINTER(RolloutParams),
+                                    C.POINTER(Cost4), P, C.c_float, P, P, P, P]),
 }
 
 _lib = None

@@ -88,9 +88,10 @@ bool resolve(gmapp_ctx *ctx, int64_t cap, int n_agents, const gmapp_tuning &t, b
     // shard + per-warp partials [2][NW][AG] + cluster slots [2][2][C][AG] of
     // one record each ((W, min d^2); (f_x, f_y, f_z, min d^2) in an ensemble)
     // + agent positions [3][AG] (4 AG floats keep the 16-byte alignment)
+    // + the four-term cost sums [kCostAcc][AG]
     const size_t rec = n_apf > 0 ? 4 : 2;
     s->smem = (static_cast<size_t>(s->shard_cap) * 3 + 2 * rec * nw * s->ag +
-               4 * rec * t.cluster * s->ag + static_cast<size_t>(4) * s->ag) *
+               4 * rec * t.cluster * s->ag + static_cast<size_t>(4 + kCostAcc) * s->ag) *
               sizeof(float);
     return s->smem + static_smem(s->fn) <= static_cast<size_t>(ctx->max_smem_optin);
 }
@@ -268,11 +269,15 @@ gmapp_status validate(const gmapp_obstacles *obs, const gmapp_agents *ag,
         set_error("rollout_agents: checkpoints need ckpt_every >= 1");
         return GMAPP_ERR_INVALID_ARG;
     }
+    if (out->cost_terms && !(prm->cost_radius > 0.0f && isfinite(prm->cost_radius))) {
+        set_error("rollout_agents: cost_terms need a finite cost_radius > 0");
+        return GMAPP_ERR_INVALID_ARG;
+    }
     return GMAPP_OK;
 }
 
 bool wants_clear(const gmapp_rollout_out *out) {
-    return out->clear_pen || out->min_clear || out->m_trace;
+    return out->clear_pen || out->min_clear || out->m_trace || out->cost_terms;
 }
 
 gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agents *ag,
@@ -323,6 +328,8 @@ gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agen
     A.m_trace = out->m_trace;
     A.f_trace = out->f_trace;
     A.ckpt = out->ckpt;
+    A.cost_terms = out->cost_terms;
+    A.cost_radius = prm->cost_radius;
     A.shard_cap = s.shard_cap;
     A.n_groups = s.groups;
     A.n_apf = s.n_apf;

@@ -46,6 +46,8 @@ constexpr int kMaxCluster = 16;
 constexpr int kMaxAgents = 16;
 // agents per group of the heterogeneous-ensemble kernel
 constexpr int kMaxEnsembleAgents = 12;
+// rows of the per-agent four-term cost sums kept in shared memory
+constexpr int kCostAcc = 11;
 
 struct RolloutArgs {
     const float *ox, *oy, *oz;
@@ -61,6 +63,8 @@ struct RolloutArgs {
     int32_t ckpt_every;
     float *traj, *p_final, *v_final, *path_len, *clear_pen, *min_clear, *w_trace, *m_trace,
         *f_trace, *ckpt;
+    float *cost_terms;  // [5][N_a] sums of the four-term cost, or NULL
+    float cost_radius;  // r_c of its goal and obstacle terms
     int32_t shard_cap;   // obstacles one CTA can hold (multiple of 4)
     int32_t n_groups;    // agent groups (clusters, or CTA groups with the grid exchange)
     int32_t n_apf;       // ensemble kernel: the last n_apf agents use APF (Eq. (apf))
@@ -156,14 +160,16 @@ __device__ __forceinline__ float softplus_f(float x, float beta) {
 //   F  = k_a (goal - p) - D v + rho k_r W g;  v += h F (h = 1/2 dt inv_mass)
 //   p += dt v;  L += dt |v|;  with CLEAR: m = sqrt(md2) - R,
 //   pen += softplus_beta(margin - m), minc = min(minc, m).
-// Returns g, the field strength kf = rho k_r W and m (inf without CLEAR).
+// Returns g, the field strength kf = rho k_r W and m (inf without CLEAR);
+// with Fo, also the total force F.
 template <bool CLEAR>
 __device__ __forceinline__ void agent_step(float (&p)[3], float (&v)[3], const float (&cc)[3],
                                            float k_r, float k_a, float R, const float (&goal)[3],
                                            float h, float dt, float rho, float damping,
                                            float clear_margin, float clear_beta, float W,
                                            float md2, float &L, float &pen, float &minc,
-                                           float &m, float (&g)[3], float &kf) {
+                                           float &m, float (&g)[3], float &kf,
+                                           float *Fo = nullptr) {
     g[0] = g[1] = g[2] = 0.0f;
     const float vv = fmaf(v[2], v[2], fmaf(v[1], v[1], v[0] * v[0]));
     if (vv >= 1e-30f) {
@@ -176,6 +182,7 @@ __device__ __forceinline__ void agent_step(float (&p)[3], float (&v)[3], const f
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const float F = k_a * (goal[d] - p[d]) - damping * v[d] + kf * g[d];
+        if (Fo) Fo[d] = F;
         v[d] = fmaf(h, F, v[d]);
     }
     const float vn = fmaf(v[2], v[2], fmaf(v[1], v[1], v[0] * v[0]));
@@ -741,10 +748,12 @@ __device__ __forceinline__ void agent_step_apf(float (&p)[3], float (&v)[3], flo
                                                float R, const float (&goal)[3], float h, float dt,
                                                float damping, float clear_margin,
                                                float clear_beta, const float (&f)[3], float md2,
-                                               float &L, float &pen, float &minc, float &m) {
+                                               float &L, float &pen, float &minc, float &m,
+                                               float *Fo = nullptr) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const float F = k_a * (goal[d] - p[d]) - damping * v[d] + kf * f[d];
+        if (Fo) Fo[d] = F;
         v[d] = fmaf(h, F, v[d]);
     }
     const float vn = fmaf(v[2], v[2], fmaf(v[1], v[1], v[0] * v[0]));
@@ -842,6 +851,8 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
     float *recv = partbuf + 2 * SR * NW * AG;
     // agent positions for the compute warps: [3][AG]
     float *pos = recv + 4 * SR * static_cast<int>(C) * AG;
+    // four-term cost sums of the exchange warp (lane = agent): [kCostAcc][AG]
+    float *cacc = pos + 4 * AG;
     auto part = [&](int h) { return partbuf + h * (SR * NW * AG); };
     auto slot = [&](int h, int par) {
         return recv + (h * 2 + par) * (SR * static_cast<int>(C) * AG);
@@ -967,6 +978,21 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
             return;
         }
         const float h = A.vel_half * A.dt * A.inv_mass;
+        // Sums of the four-term cost (Eq. cost_function) over the candidate
+        // trajectory p_0 .. p_{N_k-1} (only with the clearance compiled in):
+        // sum min(|p_k - goal|, r_c), sum max(r_c - m_k, 0), the path length
+        // of its N_k - 1 segments, the jerk sum and |p_0 - goal|.  The third
+        // difference p_k - 3 p_{k-1} + 3 p_{k-2} - p_{k-3} equals
+        // dt h (F_{k-1} - F_{k-2}) by the step rule, and F_k - F_{k-1} =
+        // -k_a dt v_{k-1} - D h F_{k-1} + (f_r,k - f_r,k-1): small terms only,
+        // where differencing FP32 positions (or forces) would cancel.
+        // The sums live in shared memory, column `lane` of cacc: rows 0-4 the
+        // five outputs, 5-7 F_{k-1}, 8-10 f_r,k-1.
+        float *cs = cacc + lane;
+        auto cv = [&](int row) -> float & { return cs[row * AG]; };
+        if (CLEAR && A.cost_terms && lane < AG) {
+            for (int r = 0; r < kCostAcc; ++r) cv(r) = 0.0f;
+        }
         // rec: W (MFI) or the force sum f (APF) of this lane's agent
         auto integrate = [&](int k, const float (&rec)[3], float md2) {
             if (A.ckpt && rank == 0 && k % A.ckpt_every == 0) {
@@ -979,11 +1005,23 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
                     ck[(3 + d) * n] = v[d];
                 }
             }
-            float fr[3], w, m;
+            float vprev[3] = {v[0], v[1], v[2]};
+            if constexpr (CLEAR) {
+                if (A.cost_terms) {
+                    const float gx = p[0] - A.goal[0], gy = p[1] - A.goal[1], gz = p[2] - A.goal[2];
+                    const float dg = sqrtf(fmaf(gz, gz, fmaf(gy, gy, gx * gx)));
+                    cv(0) += fminf(dg, A.cost_radius);
+                    if (k == 0) cv(4) = dg;
+                    if (k == A.n_steps - 1) cv(2) = L;  // before the last segment
+                }
+            }
+            float fr[3], w, m, F[3];
+            float *Fo = CLEAR && A.cost_terms ? F : nullptr;
             if constexpr (APF) {
                 const float kf = A.rho * k_r;
                 agent_step_apf<CLEAR>(p, v, kf, k_a, R, A.goal, h, A.dt, A.damping,
-                                      A.clear_margin, A.clear_beta, rec, md2, L, pen, minc, m);
+                                      A.clear_margin, A.clear_beta, rec, md2, L, pen, minc, m,
+                                      Fo);
 #pragma unroll
                 for (int d = 0; d < 3; ++d) fr[d] = kf * rec[d];
                 w = sqrtf(fmaf(rec[2], rec[2], fmaf(rec[1], rec[1], rec[0] * rec[0])));
@@ -991,9 +1029,30 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
                 float g[3], kf;
                 w = rec[0];
                 agent_step<CLEAR>(p, v, cc, k_r, k_a, R, A.goal, h, A.dt, A.rho, A.damping,
-                                  A.clear_margin, A.clear_beta, w, md2, L, pen, minc, m, g, kf);
+                                  A.clear_margin, A.clear_beta, w, md2, L, pen, minc, m, g, kf,
+                                  Fo);
 #pragma unroll
                 for (int d = 0; d < 3; ++d) fr[d] = kf * g[d];
+            }
+            if constexpr (CLEAR) {
+                if (A.cost_terms) {
+                    cv(1) += fmaxf(A.cost_radius - m, 0.0f);
+                    if (k >= 2 && k <= A.n_steps - 2) {
+                        float s = 0.0f;
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            const float dF = fmaf(-k_a * A.dt, vprev[d],
+                                                  fmaf(-A.damping * h, cv(5 + d), fr[d] - cv(8 + d)));
+                            s = fmaf(dF, dF, s);
+                        }
+                        cv(3) += s;
+                    }
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        cv(5 + d) = F[d];
+                        cv(8 + d) = fr[d];
+                    }
+                }
             }
             pos[lane] = p[0];
             pos[AG + lane] = p[1];
@@ -1080,6 +1139,16 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
             A.path_len[i] = L;
             if (A.clear_pen) A.clear_pen[i] = pen;
             if (A.min_clear) A.min_clear[i] = minc;
+            if constexpr (CLEAR) {
+                if (A.cost_terms) {
+                    const float rc = A.cost_radius, dh = A.dt * h;
+                    A.cost_terms[i] = cv(0) / rc;
+                    A.cost_terms[n + i] = cv(1) / rc;
+                    A.cost_terms[2 * n + i] = cv(2);
+                    A.cost_terms[3 * n + i] = dh * dh * cv(3);
+                    A.cost_terms[4 * n + i] = cv(4);
+                }
+            }
         }
     };
     if constexpr (ENS) {

@@ -52,3 +52,44 @@ extern "C" gmapp_status score_and_select(gmapp_ctx *ctx, const gmapp_rollout_out
     GMAPP_CHECK_CUDA(cudaGetLastError());
     return GMAPP_OK;
 }
+
+extern "C" gmapp_status score_and_select4(gmapp_ctx *ctx, const gmapp_rollout_out *ro,
+                                          int32_t n_agents, const gmapp_rollout_params *prm,
+                                          const gmapp_cost4 *w, float *c_best, float alpha,
+                                          float *costs, int32_t *best, float *best_traj,
+                                          gmapp_stream stream) {
+    if (!ctx || !ro || !prm || !w || !costs || !best || n_agents < 1 || prm->n_steps < 1) {
+        set_error("score_and_select4: NULL argument, n_agents < 1 or n_steps < 1");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    if (!ro->cost_terms || (best_traj && !ro->traj)) {
+        set_error("score_and_select4: needs ro->cost_terms (and ro->traj for best_traj)");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    if (!(w->a_max > 0.0f) || !isfinite(w->a_max) || !(prm->dt > 0.0f) || !isfinite(alpha) ||
+        !isfinite(w->w_goal) || !isfinite(w->w_obs) || !isfinite(w->w_path) ||
+        !isfinite(w->w_smooth)) {
+        set_error("score_and_select4: weights, alpha must be finite, a_max and dt > 0");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    ScoreArgs S{};
+    S.traj = ro->traj;
+    S.n = n_agents;
+    S.n_steps = prm->n_steps;
+    S.prev_best = __builtin_nanf("");
+    S.alpha = alpha;
+    S.costs = costs;
+    S.best = best;
+    S.best_traj = best_traj;
+    S.terms = ro->cost_terms;
+    S.w4[0] = w->w_goal;
+    S.w4[1] = w->w_obs;
+    S.w4[2] = w->w_path;
+    S.w4[3] = w->w_smooth;
+    const double dt = prm->dt, am = w->a_max;
+    S.smooth_scale = static_cast<float>(1.0 / (prm->n_steps * dt * dt * dt * dt * am * am));
+    S.c_best = c_best;
+    k_score_select<<<1, kScoreThreads, 0, stream>>>(S);
+    GMAPP_CHECK_CUDA(cudaGetLastError());
+    return GMAPP_OK;
+}

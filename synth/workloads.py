@@ -58,6 +58,12 @@ class PhysicsParams:
     w_path: float = 1.0
     w_goal: float = 10.0
     w_clear: float = 0.0
+    # four-term cost (Eq. cost_function): weights of the goal, obstacle, path
+    # and smoothness terms, the radius r_c of the goal/obstacle terms and the
+    # acceleration bound a_max normalising the jerk
+    w4: tuple = (1.0, 1.0, 1.0, 1.0)
+    cost_radius: float = 0.05
+    a_max: float = 50.0
 
     def as_dict(self) -> dict:
         return asdict(self)
