@@ -677,6 +677,75 @@ def bench_ensemble(gm, args, reps=5):
     return res
 
 
+def bench_replan(gm, args, n_frames=16, ticks=32, alpha=0.95):
+    """Re-planning loop with the paper's four-term cost (Eq. cost_function)
+    and hysteresis: per tick a new tabletop frame (a ring of distinct frames
+    resident in HBM) -> filter_cloud -> rollout_agents accumulating the cost
+    sums (256 agents x 500 steps, clearance reduced) -> score_and_select4
+    against the device-resident C_best (alpha = 0.95), no host round trip
+    inside a tick.  Beside it the same ticks with the plain cost (the
+    headline step: no clearance, score_and_select)."""
+    import dataclasses
+    import torch
+    base, frames_np = make_workload(n_frames, 0)
+    prm = dataclasses.replace(base["params"], cost_radius=0.05, a_max=50.0)
+    na, nk = int(base["agents"]["k_r"].size), int(prm.n_steps)
+    frames = torch.from_numpy(np.stack(frames_np)).cuda()
+    agents = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda()
+              for k, v in base["agents"].items()}
+    wsp = torch.empty(gm.filter_workspace_bytes(frames.shape[1], base["workspace"]),
+                      dtype=torch.uint8, device="cuda")
+    n_obs = []
+    probe = gm.Obstacles.empty(OBS_CAP)
+    for f in range(n_frames):
+        gm.filter_cloud(frames[f], base["T"], base["workspace"], out=probe, workspace=wsp)
+        n_obs.append(probe.count())
+    cap = (int(max(n_obs) * 1.05) + 63) // 64 * 64
+    del probe
+    obs = gm.Obstacles.empty(cap)
+    gm.filter_cloud(frames[0], base["T"], base["workspace"], out=obs, workspace=wsp)
+    out4 = gm.alloc_rollout_out(na, nk, want_traj=True, want_cost4=True)
+    out = gm.alloc_rollout_out(na, nk, want_traj=True, want_clear=False)
+    t4, _ = gm.autotune_rollout(obs, agents, prm, out=out4, candidates=16, probe_steps=100)
+    t0, _ = gm.autotune_rollout(obs, agents, prm, out=out, candidates=16, probe_steps=100)
+    c_best = torch.full((1,), float("nan"), dtype=torch.float32, device="cuda")
+    picks = torch.empty(ticks, dtype=torch.int32, device="cuda")
+    sel4 = gm.score_and_select4(out4, prm)       # output buffers, reused
+    sel = gm.score_and_select(out, prm)
+
+    def tick4(i):
+        gm.filter_cloud(frames[i % n_frames], base["T"], base["workspace"], out=obs, workspace=wsp)
+        gm.rollout_agents(obs, agents, prm, out=out4, tuning=t4)
+        gm.score_and_select4(out4, prm, c_best=c_best, alpha=alpha, out=sel4)
+        picks[i % ticks].copy_(sel4["best"][0])
+
+    def tick(i):
+        gm.filter_cloud(frames[i % n_frames], base["T"], base["workspace"], out=obs, workspace=wsp)
+        gm.rollout_agents(obs, agents, prm, out=out, tuning=t0)
+        gm.score_and_select(out, prm, out=sel)
+
+    cur = torch.cuda.current_stream()
+    for i in range(3):
+        tick4(i)
+        tick(i)
+    gm.sync()
+    c_best.fill_(float("nan"))
+    t_4 = _events(torch, cur, lambda it=iter(range(ticks)): tick4(next(it)), ticks)
+    t_0 = _events(torch, cur, lambda it=iter(range(ticks)): tick(next(it)), ticks)
+    gm.sync()
+    pk = picks.cpu().numpy()
+    inter = sum(na * n_obs[i % n_frames] * nk for i in range(ticks)) / ticks
+    return {"workload": f"{ticks} ticks over {n_frames} tabletop frames; 256 agents x 500 steps; "
+                        f"four-term cost (r_c 5 cm, a_max 50 m/s^2, w = 1,1,1,1), alpha = {alpha}",
+            "tuning": {"four_term": list(t4), "plain": list(t0)},
+            "four_term": {"ms_per_tick": 1e3 * t_4, "plans_per_s": 1.0 / t_4,
+                          "interactions_per_s": inter / t_4,
+                          "plan_switches": int((pk >= 0).sum()), "kept_plan": int((pk < 0).sum())},
+            "plain_cost": {"ms_per_tick": 1e3 * t_0, "plans_per_s": 1.0 / t_0,
+                           "interactions_per_s": inter / t_0},
+            "overhead_of_four_term_cost": t_4 / t_0 - 1.0}
+
+
 def bench_served(gm, args):
     """1 kHz open-loop request stream (200k-point tabletop frames with 4 moving
     spheres, 1 cm voxels, N_a in {64, 256, 1024}, N_k = 300) through the
@@ -858,6 +927,7 @@ PATTERNS = {"filter_stream": lambda gm, a: bench_filter_stream(gm, a),
             "batched": lambda gm, a: bench_batched(gm, a),
             "adjoint": lambda gm, a: bench_adjoint(gm, a),
             "ensemble": lambda gm, a: bench_ensemble(gm, a),
+            "replan": lambda gm, a: bench_replan(gm, a),
             "served": lambda gm, a: bench_served(gm, a)}
 
 
