@@ -43,7 +43,10 @@ def lib():
                                         C.c_double, C.c_double, P, P, P]
         _lib.oracle_rollout.restype = None
         _lib.oracle_rollout.argtypes = [i64, P, P, P, C.c_double, i64, P, P, P, P, P, P, P,
-                                        P, P, P, P, P, P, P, P, P, i64]
+                                        P, P, P, P, P, P, P, P, P, i64, i64]
+        _lib.oracle_proj_eval.restype = None
+        _lib.oracle_proj_eval.argtypes = [i64, P, P, P, C.c_double, i64, P, P, P, P, P,
+                                          C.c_double, C.c_double, P, P]
         _lib.oracle_apf_eval.restype = None
         _lib.oracle_apf_eval.argtypes = [i64, P, P, P, C.c_double, i64, P, P, P, P,
                                          C.c_double, C.c_double, P, P, P]
@@ -156,12 +159,29 @@ def apf_eval(obs_xyz, r_O: float, p, agents: dict, rho: float, eps: float) -> di
     return {"m": m, "f_r": fr, "f_abs": fa}
 
 
+def proj_eval(obs_xyz, r_O: float, p, v, agents: dict, rho: float, eps: float) -> dict:
+    """Clearance m and the projected-current MFI force f_r = rho k_r f (Eq.
+    mfi with the per-obstacle current c_j) for every agent at states (p, v),
+    [3, N_a] each."""
+    ox, oy, oz = (_f64(obs_xyz[a]) for a in range(3))
+    p, v = _f64(p), _f64(v)
+    na = p.shape[1]
+    k_r, r_d, r_a = _f64(agents["k_r"]), _f64(agents["r_d"]), _f64(agents["r_a"])
+    m = np.zeros(na)
+    fr = np.zeros((3, na))
+    lib().oracle_proj_eval(ox.size, _ptr(ox), _ptr(oy), _ptr(oz), float(r_O), na, _ptr(p),
+                           _ptr(v), _ptr(k_r), _ptr(r_d), _ptr(r_a), float(rho), float(eps),
+                           _ptr(m), _ptr(fr))
+    return {"m": m, "f_r": fr}
+
+
 def rollout(obs_xyz, r_O: float, agents: dict, prm, want_traj: bool = True,
-            want_trace: bool = False, n_apf: int = 0) -> dict:
+            want_trace: bool = False, n_apf: int = 0, n_proj: int = 0) -> dict:
     """FP64 rollout of all agents; returns the trajectory [N_a, N_k+1, 3],
     final state, path length, clearance penalty sum and minimum clearance.
-    The last ``n_apf`` agents use the APF heuristic (Eq. apf), the others
-    the MFI / circular field (Eq. mfi)."""
+    The last ``n_apf`` agents use the APF heuristic (Eq. apf), the ``n_proj``
+    before them MFI with the per-obstacle projected current, the others the
+    MFI / circular field with the agent's own current (Eq. mfi)."""
     ox, oy, oz = (_f64(obs_xyz[a]) for a in range(3))
     ag = {k: _f64(v) for k, v in agents.items()}
     na = ag["k_r"].size
@@ -179,7 +199,7 @@ def rollout(obs_xyz, r_O: float, agents: dict, prm, want_traj: bool = True,
                          _ptr(traj) if want_traj else nul, _ptr(out["p_final"]),
                          _ptr(out["v_final"]), _ptr(out["path_len"]), _ptr(out["clear_pen"]),
                          _ptr(out["min_clear"]), _ptr(wtr) if want_trace else nul,
-                         _ptr(mtr) if want_trace else nul, int(n_apf))
+                         _ptr(mtr) if want_trace else nul, int(n_apf), int(n_proj))
     if want_traj:
         out["traj"] = traj
     if want_trace:

@@ -233,6 +233,79 @@ static void apf_force(const double p[3], int64_t n_obs, const double *ox,
 }
 
 /*
+ * MFI with the current projected per obstacle (Eq. (mfi) with the current
+ * of the equation that follows it), static obstacles, so the relative
+ * velocity is d' = -v.  For every obstacle j, with d_j = p - p_Oj:
+ *   n_j   = d_j / |d_j|                      surface normal (the term is even in n_j)
+ *   c_j   = d' - n_j (n_j . d')              current projected onto the surface
+ *   s_j   = max(|d_j| - (r_a + r_O), eps)    clamp of Alg. 1
+ *   term  = (1 / s_j) (d' / |d'|) x (c_j x d')   when s_j <= r_d (gate of Alg. 1)
+ * written out with the two cross products.  f = sum of the terms (k_f is
+ * applied by the caller); f = 0 when |v|^2 < 1e-30; a pair with d_j = 0 has
+ * no normal and adds nothing.  m as in cf_weight.
+ */
+static void cross3(const double a[3], const double b[3], double o[3])
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static void proj_force(const double p[3], const double v[3], int64_t n_obs, const double *ox,
+                       const double *oy, const double *oz, double R, double eps, double r_d,
+                       double f[3], double *m)
+{
+    const double dd[3] = {-v[0], -v[1], -v[2]};
+    const double vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const double ndd = sqrt(vv);
+    double fx = 0.0, fy = 0.0, fz = 0.0, mn = INFINITY;
+    for (int64_t j = 0; j < n_obs; ++j) {
+        double d[3] = {p[0] - ox[j], p[1] - oy[j], p[2] - oz[j]};
+        double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double s = dn - R;
+        if (s < mn) mn = s;
+        if (s < eps) s = eps;
+        if (!(s <= r_d) || dn == 0.0 || vv < 1e-30) continue;
+        double n[3] = {d[0] / dn, d[1] / dn, d[2] / dn};
+        double nd = n[0] * dd[0] + n[1] * dd[1] + n[2] * dd[2];
+        double c[3] = {dd[0] - n[0] * nd, dd[1] - n[1] * nd, dd[2] - n[2] * nd};
+        double u[3] = {dd[0] / ndd, dd[1] / ndd, dd[2] / ndd};
+        double cxd[3], t[3];
+        cross3(c, dd, cxd);
+        cross3(u, cxd, t);
+        fx += t[0] / s;
+        fy += t[1] / s;
+        fz += t[2] / s;
+    }
+    f[0] = fx;
+    f[1] = fy;
+    f[2] = fz;
+    *m = mn;
+}
+
+/*
+ * Projected-current MFI force of each agent at states (p, v):
+ *   f_r = rho k_r f      (k_f = rho k_r)
+ * Layouts: p, v, f_r are [3][n_agents]; the rest [n_agents].
+ */
+void oracle_proj_eval(int64_t n_obs, const double *ox, const double *oy,
+                      const double *oz, double r_O, int64_t n_agents,
+                      const double *p, const double *v, const double *k_r,
+                      const double *r_d, const double *r_a, double rho, double eps,
+                      double *m, double *f_r)
+{
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t i = 0; i < n_agents; ++i) {
+        double pi[3] = {p[i], p[n_agents + i], p[2 * n_agents + i]};
+        double vi[3] = {v[i], v[n_agents + i], v[2 * n_agents + i]};
+        double f[3], mn;
+        proj_force(pi, vi, n_obs, ox, oy, oz, r_a[i] + r_O, eps, r_d[i], f, &mn);
+        m[i] = mn;
+        for (int a = 0; a < 3; ++a) f_r[a * n_agents + i] = rho * k_r[i] * f[a];
+    }
+}
+
+/*
  * APF repulsive force of each agent at positions p:
  *   f_r = rho k_r f      (k_f = rho k_r)
  * and f_abs = |rho k_r| sum_j |term_j| (f_abs may be NULL).
@@ -290,7 +363,9 @@ static double softplus(double x, double beta)
  * The trajectory holds p_0 .. p_N_k (N_k + 1 points).
  * Heterogeneous ensemble: the last n_apf agents use the APF heuristic
  * instead, F = k_a (p_goal - p_k) - D v_{k-1} + rho k_r f_apf(p_k), with
- * |f_apf| in the w trace.
+ * |f_apf| in the w trace; the n_proj agents before them use MFI with the
+ * projected current, F = ... + rho k_r f_proj(p_k, v_{k-1}), |f_proj| in the
+ * w trace.
  * Layouts: agent vectors [3][n_agents]; traj [n_agents][n_steps+1][3];
  * w_trace, m_trace [n_agents][n_steps].  traj / traces may be NULL.
  */
@@ -301,7 +376,7 @@ void oracle_rollout(int64_t n_obs, const double *ox, const double *oy,
                     const double *r_a, const oracle_params *prm, double *traj,
                     double *p_final, double *v_final, double *path_len,
                     double *clear_pen, double *min_clear, double *w_trace,
-                    double *m_trace, int64_t n_apf)
+                    double *m_trace, int64_t n_apf, int64_t n_proj)
 {
     const int64_t N = prm->n_steps;
 #pragma omp parallel for schedule(dynamic)
@@ -312,9 +387,16 @@ void oracle_rollout(int64_t n_obs, const double *ox, const double *oy,
         double L = 0.0, pen = 0.0, mc = INFINITY;
         if (traj) for (int a = 0; a < 3; ++a) traj[(i * (N + 1)) * 3 + a] = p[a];
         const int apf = i >= n_agents - n_apf;
+        const int proj = !apf && i >= n_agents - n_apf - n_proj;
         for (int64_t k = 0; k < N; ++k) {
             double w, mn, g[3], F[3], pn[3];
-            if (apf) {
+            if (proj) {
+                proj_force(p, v, n_obs, ox, oy, oz, r_a[i] + r_O, prm->eps, r_d[i], g, &mn);
+                w = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+                for (int a = 0; a < 3; ++a)
+                    F[a] = k_a[i] * (prm->goal[a] - p[a]) - prm->damping * v[a]
+                           + prm->rho * k_r[i] * g[a];
+            } else if (apf) {
                 apf_force(p, n_obs, ox, oy, oz, r_a[i] + r_O, prm->eps, r_d[i], g, &mn, NULL);
                 w = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
                 for (int a = 0; a < 3; ++a)
