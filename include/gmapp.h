@@ -359,17 +359,26 @@ gmapp_status gmapp_pick_tuning(gmapp_ctx *ctx, int64_t obs_cap, int32_t n_agents
 /* detection radii form one ensemble; Sec. IV-D: agents grouped by heuristic) */
 /* ------------------------------------------------------------------------ */
 
-/* rollout_agents for an ensemble in which the LAST n_apf agents (indices
- * n - n_apf .. n - 1) follow the APF heuristic and the others the MFI field
- * above.  Callers order their agents by heuristic.  Per-agent r_d gives each
- * agent a large or small detection radius.  An APF agent's force at step k:
- *   d_j  = p_k - p_Oj,  rho_j = max(|d_j|, r_a + r_O + eps)
- *   f    = sum over j with |d_j| - (r_a + r_O) < r_d (strict) of
- *          (1/rho_j - 1/r_d) rho_j^-2 d_j / |d_j|   (a pair with d_j = 0 adds 0)
- *   F    = k_a (p_goal - p_k) - damping v_{k-1} + rho k_r f
+/* rollout_agents for an ensemble of three heuristics, agents ordered by
+ * heuristic: indices 0 .. n - n_proj - n_apf - 1 follow the MFI field above
+ * (the agent's own current c); the next n_proj agents MFI with the current
+ * projected per obstacle (Eq. (mfi) with the equation after it); the LAST
+ * n_apf agents (n - n_apf .. n - 1) the APF heuristic.  Per-agent r_d gives
+ * each agent a large or small detection radius.  At step k, with
+ * d_j = p_k - p_Oj and R = r_a + r_O:
+ *   APF:        rho_j = max(|d_j|, R + eps),
+ *               f = sum over j with |d_j| - R < r_d (strict) of
+ *               (1/rho_j - 1/r_d) rho_j^-2 d_j / |d_j|   (a pair with d_j = 0 adds 0)
+ *   projected:  s_j = max(|d_j| - R, eps), n_j = d_j / |d_j|, d' = -v_{k-1},
+ *               c_j = d' - n_j (n_j . d'),
+ *               f = sum over j with s_j <= r_d of (1/s_j) (d'/|d'|) x (c_j x d')
+ *                 = (|v|^2 S - v B) / |v|,  S = sum a_j d_j,  B = sum a_j (d_j . v),
+ *               a_j = (d_j . v) / (s_j |d_j|^2)   (f = 0 when |v|^2 < 1e-30;
+ *               a pair with d_j = 0 adds 0)
+ *   both:       F = k_a (p_goal - p_k) - damping v_{k-1} + rho k_r f
  * The rest of the step, the outputs and the error behaviour are those of
- * rollout_agents.  For APF agents, w_trace holds |f| and f_trace rho k_r f.
- * APF agents need r_d > 0 (+inf = no gate).
+ * rollout_agents.  For APF and projected agents, w_trace holds |f| and
+ * f_trace rho k_r f.  APF agents need r_d > 0 (+inf = no gate).
  * All agents run in ONE launch: the agent groups of the launch are
  * homogeneous (each holds only MFI or only APF agents), with groups shared
  * in proportion to the two counts.  `tune` selects the launch shape as in
@@ -377,22 +386,24 @@ gmapp_status gmapp_pick_tuning(gmapp_ctx *ctx, int64_t obs_cap, int32_t n_agents
  * 12 agents per group and 384 threads), or NULL for the library's choice.
  * With tune = NULL the shape is the one gmapp_autotune_ensemble cached
  * for these sizes, else the cost model's choice among ensemble shapes.
- * n_apf = 0 is rollout_agents.  GMAPP_ERR_INVALID_ARG for n_apf outside
- * [0, n], for adjoint checkpoints (out->ckpt) with n_apf > 0, or for a shape
- * that does not fit. */
+ * n_proj = n_apf = 0 is rollout_agents.  GMAPP_ERR_INVALID_ARG for negative
+ * counts or n_proj + n_apf > n, for adjoint checkpoints (out->ckpt) in an
+ * ensemble, or for a shape that does not fit. */
 gmapp_status rollout_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *obs,
-                              const gmapp_agents *agents, int32_t n_apf,
+                              const gmapp_agents *agents, int32_t n_proj, int32_t n_apf,
                               const gmapp_rollout_params *prm, gmapp_rollout_out *out,
                               const gmapp_tuning *tune, gmapp_stream stream);
 
-/* gmapp_autotune_rollout for an ensemble with n_apf APF agents: ranks the
+/* gmapp_autotune_rollout for an ensemble (n_proj, n_apf as in
+ * rollout_ensemble): ranks the
  * shapes that fit the ensemble (groups split by heuristic), times the best
  * `max_candidates` on the caller's inputs and caches the fastest for later
  * rollout_ensemble calls with tune = NULL and the same (obs->cap,
- * agents->n, n_apf, clearance outputs).  Same arguments, errors and
- * synchronous behaviour as gmapp_autotune_rollout; n_apf = 0 is that call. */
+ * agents->n, n_proj, n_apf, clearance outputs).  Same arguments, errors and
+ * synchronous behaviour as gmapp_autotune_rollout; n_proj = n_apf = 0 is
+ * that call. */
 gmapp_status gmapp_autotune_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *obs,
-                                     const gmapp_agents *agents, int32_t n_apf,
+                                     const gmapp_agents *agents, int32_t n_proj, int32_t n_apf,
                                      const gmapp_rollout_params *prm,
                                      gmapp_rollout_out *out, int32_t max_candidates,
                                      int32_t probe_steps, gmapp_tuning *best, float *best_ms,

@@ -292,7 +292,7 @@ def autotune_rollout(obs: Obstacles, agents: dict, prm, out: dict | None = None,
 
 
 def autotune_ensemble(obs: Obstacles, agents: dict, n_apf: int, prm, out: dict | None = None,
-                      candidates: int = 12, probe_steps: int = 60, stream=None):
+                      candidates: int = 12, probe_steps: int = 60, stream=None, n_proj: int = 0):
     """autotune_rollout for an ensemble whose last ``n_apf`` agents use APF;
     later rollout_ensemble calls of the same sizes without ``tuning`` use
     the shape it caches."""
@@ -303,7 +303,8 @@ def autotune_ensemble(obs: Obstacles, agents: dict, n_apf: int, prm, out: dict |
     ob, ag, pr, os_ = obs._struct(), _agents_struct(agents), _params_struct(prm), _out_struct(out)
     t = _abi.Tuning()
     ms = C.c_float()
-    check(_abi.load().gmapp_autotune_ensemble(ctx.handle, C.byref(ob), C.byref(ag), int(n_apf),
+    check(_abi.load().gmapp_autotune_ensemble(ctx.handle, C.byref(ob), C.byref(ag), int(n_proj),
+                                              int(n_apf),
                                               C.byref(pr), C.byref(os_), int(candidates),
                                               int(probe_steps), C.byref(t), C.byref(ms),
                                               _stream(stream)),
@@ -340,17 +341,19 @@ def rollout_agents(obs: Obstacles, agents: dict, prm, out: dict | None = None,
 
 def rollout_ensemble(obs: Obstacles, agents: dict, n_apf: int, prm, out: dict | None = None,
                      want_traj: bool = True, want_trace: bool = False, want_clear: bool = True,
-                     tuning=None, stream=None) -> dict:
+                     tuning=None, stream=None, n_proj: int = 0) -> dict:
     """Heterogeneous ensemble in one launch: the last ``n_apf`` agents follow
-    the APF heuristic (Eq. apf), the others the MFI field (Eq. mfi); agent
-    groups are homogeneous.  Arguments and outputs as rollout_agents."""
+    the APF heuristic (Eq. apf), the ``n_proj`` before them MFI with the
+    per-obstacle projected current, the others the MFI field with their own
+    current (Eq. mfi); agent groups are homogeneous.  Arguments and outputs
+    as rollout_agents."""
     ctx = context()
     na = int(agents["k_r"].numel())
     if out is None:
         out = alloc_rollout_out(na, int(prm.n_steps), want_traj, want_trace, want_clear)
     ob, ag, pr, os_ = obs._struct(), _agents_struct(agents), _params_struct(prm), _out_struct(out)
     t = C.byref(_abi.Tuning(*[int(v) for v in tuning])) if tuning is not None else None
-    check(_abi.load().rollout_ensemble(ctx.handle, C.byref(ob), C.byref(ag), int(n_apf),
+    check(_abi.load().rollout_ensemble(ctx.handle, C.byref(ob), C.byref(ag), int(n_proj), int(n_apf),
                                        C.byref(pr), C.byref(os_), t, _stream(stream)),
           "rollout_ensemble")
     return out

@@ -118,7 +118,7 @@ PROTOTYPES = {
     "rollout_agents_tuned": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
                                        C.POINTER(RolloutParams), C.POINTER(RolloutOut),
                                        C.POINTER(Tuning), P]),
-    "rollout_ensemble": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents), C.c_int32,
+    "rollout_ensemble": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents), C.c_int32, C.c_int32,
                                    C.POINTER(RolloutParams), C.POINTER(RolloutOut),
                                    C.POINTER(Tuning), P]),
     "gmapp_pick_tuning": (C.c_int, [P, C.c_int64, C.c_int32, C.POINTER(Tuning)]),
@@ -127,6 +127,7 @@ PROTOTYPES = {
                                          C.c_int32, C.c_int32, C.POINTER(Tuning),
                                          C.POINTER(C.c_float), P]),
     "gmapp_autotune_ensemble": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents), C.c_int32,
+                                          C.c_int32,
                                           C.POINTER(RolloutParams), C.POINTER(RolloutOut),
                                           C.c_int32, C.c_int32, C.POINTER(Tuning),
                                           C.POINTER(C.c_float), P]),

@@ -14,6 +14,14 @@ namespace gmapp {
 
 namespace {
 
+// Agent kinds of a heterogeneous ensemble (agents ordered MFI, projected
+// current, APF); all zero for a plain MFI rollout.
+struct Kinds {
+    int n_proj = 0, n_apf = 0;
+    // ensemble level of the kernel: 0 MFI only, 1 + APF, 2 + projected current
+    int level() const { return n_proj > 0 ? 2 : n_apf > 0 ? 1 : 0; }
+};
+
 // A launch shape resolved for concrete sizes.
 struct Shape {
     int cluster;   // C: CTAs per group (a cluster, or a grid-exchange group) = obstacle shards
@@ -22,8 +30,8 @@ struct Shape {
     int ag;        // agents per group held in registers (max over groups)
     int threads;   // NT
     bool clear;    // clearance reduction compiled in
-    int n_apf;     // heterogeneous ensemble: the last n_apf agents use APF (0 = MFI only)
-    int groups_apf;  // ... forming the last groups_apf groups
+    Kinds kinds;   // heterogeneous ensemble (all zero: MFI only)
+    int groups_proj, groups_apf;  // groups of projected-current and APF agents
     RolloutKernel fn;
     int32_t shard_cap;
     size_t smem;   // dynamic shared memory bytes
@@ -34,8 +42,12 @@ int32_t shard_cap_for(int64_t cap, int cluster) {
     return static_cast<int32_t>((s + 3) & ~int64_t(3));
 }
 
-RolloutKernel pick_kernel(int ag, int nt, bool clear, bool grid, bool ens) {
-    if (ens) {
+RolloutKernel pick_kernel(int ag, int nt, bool clear, bool grid, int level) {
+    if (level == 2) {
+        if (grid) return clear ? rollout_kernel_ens3_grid_clear(ag, nt) : rollout_kernel_ens3_grid_noclear(ag, nt);
+        return clear ? rollout_kernel_ens3_clear(ag, nt) : rollout_kernel_ens3_noclear(ag, nt);
+    }
+    if (level == 1) {
         if (grid) return clear ? rollout_kernel_ens_grid_clear(ag, nt) : rollout_kernel_ens_grid_noclear(ag, nt);
         return clear ? rollout_kernel_ens_clear(ag, nt) : rollout_kernel_ens_noclear(ag, nt);
     }
@@ -49,13 +61,42 @@ size_t static_smem(RolloutKernel fn) {
     return fa.sharedSizeBytes;
 }
 
+// Groups per kind of an ensemble: in proportion to the agent counts, at
+// least one per kind present, the remainder to the kinds with the most
+// agents per group; returns the largest number of agents in a group.
+int split_groups(const int (&count)[3], int groups, int (&g)[3]) {
+    int sum = 0, total = count[0] + count[1] + count[2];
+    for (int i = 0; i < 3; ++i) {
+        g[i] = count[i] > 0 ? std::max(1, static_cast<int>(static_cast<int64_t>(groups) *
+                                                           count[i] / total)) : 0;
+        sum += g[i];
+    }
+    auto per = [&](int i) { return g[i] > 0 ? (count[i] + g[i] - 1) / g[i] : 0; };
+    while (sum > groups) {  // only when a small kind got its one group
+        int j = -1;
+        for (int i = 0; i < 3; ++i)
+            if (g[i] > 1 && (j < 0 || per(i) < per(j))) j = i;
+        if (j < 0) break;
+        --g[j];
+        --sum;
+    }
+    while (sum < groups) {
+        int j = -1;
+        for (int i = 0; i < 3; ++i)
+            if (count[i] > g[i] && (j < 0 || per(i) > per(j))) j = i;
+        if (j < 0) break;
+        ++g[j];
+        ++sum;
+    }
+    return std::max(per(0), std::max(per(1), per(2)));
+}
+
 // Resolve (cluster, agents per group, threads) for N_a agents and an
-// obstacle capacity; false when the shape cannot run.  With n_apf > 0 the
-// groups are split by heuristic (homogeneous groups, in proportion to the
-// agent counts, at least one of each kind present) and the ensemble kernel
-// is used.
+// obstacle capacity; false when the shape cannot run.  For an ensemble the
+// groups are split by heuristic (homogeneous groups; split_groups) and the
+// ensemble kernel of the matching level is used.
 bool resolve(gmapp_ctx *ctx, int64_t cap, int n_agents, const gmapp_tuning &t, bool clear,
-             Shape *s, int n_apf = 0) {
+             Shape *s, Kinds kinds = Kinds{}) {
     if (t.cluster < 1 || t.cluster > kMaxCluster || t.agents_per_cta < 1 ||
         t.agents_per_cta > kMaxAgents || t.exchange < 0 || t.exchange > 1)
         return false;
@@ -65,33 +106,32 @@ bool resolve(gmapp_ctx *ctx, int64_t cap, int n_agents, const gmapp_tuning &t, b
     s->groups = (n_agents + t.agents_per_cta - 1) / t.agents_per_cta;
     s->ag = (n_agents + s->groups - 1) / s->groups;
     s->clear = clear;
-    s->n_apf = n_apf;
-    s->groups_apf = 0;
-    if (n_apf > 0) {
-        const int n_mfi = n_agents - n_apf;
-        if (n_mfi > 0 && s->groups < 2) s->groups = 2;
-        const int g = s->groups;
-        int ga = static_cast<int>((static_cast<int64_t>(g) * n_apf + n_agents / 2) / n_agents);
-        ga = std::max(1, std::min(ga, n_mfi > 0 ? g - 1 : g));
-        s->groups_apf = ga;
-        const int gm = g - ga;
-        s->ag = (n_apf + ga - 1) / ga;
-        if (gm > 0) s->ag = std::max(s->ag, (n_mfi + gm - 1) / gm);
+    s->kinds = kinds;
+    s->groups_proj = s->groups_apf = 0;
+    if (kinds.level() > 0) {
+        const int count[3] = {n_agents - kinds.n_proj - kinds.n_apf, kinds.n_proj, kinds.n_apf};
+        const int present = (count[0] > 0) + (count[1] > 0) + (count[2] > 0);
+        if (s->groups < present) s->groups = present;
+        int g[3];
+        s->ag = split_groups(count, s->groups, g);
+        s->groups_proj = g[1];
+        s->groups_apf = g[2];
         if (s->ag > kMaxEnsembleAgents) return false;
     }
-    s->fn = pick_kernel(s->ag, t.threads, clear, s->grid, n_apf > 0);
+    s->fn = pick_kernel(s->ag, t.threads, clear, s->grid, kinds.level());
     if (!s->fn) return false;
     // grid exchange: one slot set per CTA, at most one CTA per SM
     if (s->grid && s->groups * s->cluster > ctx->sm_count) return false;
     s->shard_cap = shard_cap_for(cap, t.cluster);
     const int nw = t.threads / 32;
     // shard + per-warp partials [2][NW][AG] + cluster slots [2][2][C][AG] of
-    // one record each ((W, min d^2); (f_x, f_y, f_z, min d^2) in an ensemble)
-    // + agent positions [3][AG] (4 AG floats keep the 16-byte alignment)
-    // + the four-term cost sums [kCostAcc][AG]
-    const size_t rec = n_apf > 0 ? 4 : 2;
+    // one record each ((W, min d^2); APF (f, min d^2): 4 floats; projected
+    // current (S, B, min d^2, -): 6) + agent positions and velocities [3][AG]
+    // each (4 AG floats apart, keeping the 16-byte alignment) + the
+    // four-term cost sums [kCostAcc][AG]
+    const size_t rec = kinds.level() == 2 ? 6 : kinds.level() == 1 ? 4 : 2;
     s->smem = (static_cast<size_t>(s->shard_cap) * 3 + 2 * rec * nw * s->ag +
-               4 * rec * t.cluster * s->ag + static_cast<size_t>(4 + kCostAcc) * s->ag) *
+               4 * rec * t.cluster * s->ag + static_cast<size_t>(8 + kCostAcc) * s->ag) *
               sizeof(float);
     return s->smem + static_smem(s->fn) <= static_cast<size_t>(ctx->max_smem_optin);
 }
@@ -160,12 +200,13 @@ int max_active_clusters(gmapp_ctx *ctx, const Shape &s) {
 // launch must fit in one wave (its groups poll one another).
 // CTAs that share an SM (when the occupancy allows more than one) share its
 // pipes, so the pair loop slows by the number of co-resident CTAs per SM.
-// In an ensemble every group runs AG agent slots and the APF groups set
-// the pace: an APF pair costs ~1.32 MFI pairs (measured on B300, tabletop).
+// In an ensemble every group runs AG agent slots and the costliest kind sets
+// the pace: an APF pair costs ~1.32 MFI pairs (measured on B300, tabletop),
+// a projected-current pair ~1.6 (17 FMA-pipe lane-ops and 2 SFU ops).
 double model_cost(const Shape &s, int m, int64_t n_obs_est, int sm_count) {
     const double shard = static_cast<double>((n_obs_est + s.cluster - 1) / s.cluster);
     const double rate = std::min(7.0, 1.5 + 1.2 * s.ag) * (s.threads >= 384 ? 1.0 : 0.95) /
-                        (s.n_apf > 0 ? 1.32 : 1.0);
+                        (s.kinds.n_proj > 0 ? 1.6 : s.kinds.n_apf > 0 ? 1.32 : 1.0);
     const double share =
         std::max(1.0, static_cast<double>(std::min(s.groups, m)) * s.cluster / sm_count);
     const double loop = s.ag * std::max(shard, 64.0) / rate * share;
@@ -176,14 +217,15 @@ double model_cost(const Shape &s, int m, int64_t n_obs_est, int sm_count) {
 }
 
 std::mutex g_tune_mu;
-// (device, obstacle capacity, N_a, clearance outputs, APF agents of an ensemble)
-std::map<std::tuple<int, int64_t, int, bool, int>, gmapp_tuning> g_tune_cache;
+// (device, obstacle capacity, N_a, clearance outputs, projected-current and
+// APF agents of an ensemble)
+std::map<std::tuple<int, int64_t, int, bool, int, int>, gmapp_tuning> g_tune_cache;
 
 }  // namespace
 
 gmapp_status pick_tuning_impl(gmapp_ctx *ctx, int64_t cap, int32_t n_agents, bool clear,
-                              gmapp_tuning *best, int32_t n_apf = 0) {
-    const auto key = std::make_tuple(ctx->device, cap, n_agents, clear, n_apf);
+                              gmapp_tuning *best, Kinds kinds = Kinds{}) {
+    const auto key = std::make_tuple(ctx->device, cap, n_agents, clear, kinds.n_proj, kinds.n_apf);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -201,7 +243,7 @@ gmapp_status pick_tuning_impl(gmapp_ctx *ctx, int64_t cap, int32_t n_agents, boo
                 int last_groups = -1;
                 for (int a = 1; a <= kMaxAgents; ++a) {
                     Shape s;
-                    if (!resolve(ctx, cap, n_agents, gmapp_tuning{C, a, nt, x}, clear, &s, n_apf))
+                    if (!resolve(ctx, cap, n_agents, gmapp_tuning{C, a, nt, x}, clear, &s, kinds))
                         continue;
                     if (s.groups == last_groups) continue;
                     last_groups = s.groups;
@@ -210,7 +252,7 @@ gmapp_status pick_tuning_impl(gmapp_ctx *ctx, int64_t cap, int32_t n_agents, boo
                     const double cost = model_cost(s, m, cap, ctx->sm_count);
                     if (cost < best_cost) {
                         best_cost = cost;
-                        *best = gmapp_tuning{C, n_apf > 0 ? a : s.ag, nt, x};
+                        *best = gmapp_tuning{C, kinds.level() > 0 ? a : s.ag, nt, x};
                         found = true;
                     }
                 }
@@ -282,9 +324,9 @@ bool wants_clear(const gmapp_rollout_out *out) {
 
 gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agents *ag,
                     const gmapp_rollout_params *prm, gmapp_rollout_out *out,
-                    const gmapp_tuning &t, gmapp_stream stream, int n_apf = 0) {
+                    const gmapp_tuning &t, gmapp_stream stream, Kinds kinds = Kinds{}) {
     Shape s;
-    if (!resolve(ctx, obs->cap, ag->n, t, wants_clear(out), &s, n_apf)) {
+    if (!resolve(ctx, obs->cap, ag->n, t, wants_clear(out), &s, kinds)) {
         set_error("rollout_agents: launch shape (cluster %d, agents %d, threads %d, exchange %d) "
                   "does not fit an obstacle capacity of %lld",
                   t.cluster, t.agents_per_cta, t.threads, t.exchange, (long long)obs->cap);
@@ -332,8 +374,10 @@ gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agen
     A.cost_radius = prm->cost_radius;
     A.shard_cap = s.shard_cap;
     A.n_groups = s.groups;
-    A.n_apf = s.n_apf;
+    A.n_apf = s.kinds.n_apf;
     A.n_groups_apf = s.groups_apf;
+    A.n_proj = s.kinds.n_proj;
+    A.n_groups_proj = s.groups_proj;
     A.group_ctas = s.cluster;
     A.xbuf = ctx->d_xbuf;
     A.xctl = ctx->d_xctl;
@@ -359,11 +403,27 @@ using namespace gmapp;
 
 namespace {
 
-// Measured choice of the launch shape (MFI rollout, or an ensemble with
-// n_apf APF agents): rank by the model, time the best candidates on the
-// caller's inputs, cache the fastest.
+// Checks of an ensemble's agent counts (the kinds are ordered MFI,
+// projected current, APF; the adjoint covers MFI agents only).
+gmapp_status check_kinds(const char *who, const gmapp_agents *agents, int32_t n_proj,
+                         int32_t n_apf, const gmapp_rollout_out *out) {
+    if (n_proj < 0 || n_apf < 0 || static_cast<int64_t>(n_proj) + n_apf > agents->n) {
+        set_error("%s: n_proj, n_apf must be >= 0 with n_proj + n_apf <= n (%d, %d, n %d)", who,
+                  n_proj, n_apf, agents->n);
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    if (n_proj + n_apf > 0 && out->ckpt) {
+        set_error("%s: adjoint checkpoints cover MFI agents only", who);
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    return GMAPP_OK;
+}
+
+// Measured choice of the launch shape (MFI rollout, or an ensemble): rank
+// by the model, time the best candidates on the caller's inputs, cache the
+// fastest.
 gmapp_status autotune_impl(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agents *agents,
-                           int32_t n_apf, const gmapp_rollout_params *prm,
+                           Kinds kinds, const gmapp_rollout_params *prm,
                            gmapp_rollout_out *out, int32_t max_candidates, int32_t probe_steps,
                            gmapp_tuning *best, float *best_ms, gmapp_stream stream) {
     if (!ctx || !best || max_candidates < 1 || probe_steps < 1) {
@@ -372,10 +432,9 @@ gmapp_status autotune_impl(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gma
     }
     gmapp_status st = validate(obs, agents, prm, out);
     if (st != GMAPP_OK) return st;
-    if (n_apf < 0 || n_apf > agents->n || (n_apf > 0 && out->ckpt)) {
-        set_error("gmapp_autotune_ensemble: n_apf outside [0, n], or checkpoints with n_apf > 0");
-        return GMAPP_ERR_INVALID_ARG;
-    }
+    if ((st = check_kinds("gmapp_autotune_ensemble", agents, kinds.n_proj, kinds.n_apf, out)) !=
+        GMAPP_OK)
+        return st;
     const bool clear = wants_clear(out);
     // 1. candidates ranked by the model, one per (cluster, groups, threads)
     struct Cand {
@@ -391,7 +450,7 @@ gmapp_status autotune_impl(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gma
                 for (int a = 1; a <= kMaxAgents; ++a) {
                     Shape s;
                     if (!resolve(ctx, obs->cap, agents->n, gmapp_tuning{C, a, nt, x}, clear, &s,
-                                 n_apf))
+                                 kinds))
                         continue;
                     if (s.groups == last_groups) continue;
                     last_groups = s.groups;
@@ -399,7 +458,7 @@ gmapp_status autotune_impl(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gma
                     if (m <= 0) continue;
                     const double cost = model_cost(s, m, obs->cap, ctx->sm_count);
                     if (cost < 1e299)
-                        cands.push_back({cost, gmapp_tuning{C, n_apf > 0 ? a : s.ag, nt, x}});
+                        cands.push_back({cost, gmapp_tuning{C, kinds.level() > 0 ? a : s.ag, nt, x}});
                 }
             }
     if (cands.empty()) {
@@ -419,9 +478,9 @@ gmapp_status autotune_impl(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gma
     float best_t = 1e30f;
     gmapp_status result = GMAPP_OK;
     for (const Cand &c : cands) {
-        if ((st = launch(ctx, obs, agents, &probe, out, c.t, stream, n_apf)) != GMAPP_OK) continue;
+        if ((st = launch(ctx, obs, agents, &probe, out, c.t, stream, kinds)) != GMAPP_OK) continue;
         cudaEventRecord(e0, stream);
-        st = launch(ctx, obs, agents, &probe, out, c.t, stream, n_apf);
+        st = launch(ctx, obs, agents, &probe, out, c.t, stream, kinds);
         cudaEventRecord(e1, stream);
         if (st != GMAPP_OK) continue;
         if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -444,7 +503,8 @@ gmapp_status autotune_impl(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gma
     }
     if (best_ms) *best_ms = best_t * static_cast<float>(prm->n_steps) / probe.n_steps;
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[std::make_tuple(ctx->device, obs->cap, agents->n, clear, n_apf)] = *best;
+    g_tune_cache[std::make_tuple(ctx->device, obs->cap, agents->n, clear, kinds.n_proj,
+                                 kinds.n_apf)] = *best;
     return GMAPP_OK;
 }
 
@@ -456,18 +516,19 @@ extern "C" gmapp_status gmapp_autotune_rollout(gmapp_ctx *ctx, const gmapp_obsta
                                                gmapp_rollout_out *out, int32_t max_candidates,
                                                int32_t probe_steps, gmapp_tuning *best,
                                                float *best_ms, gmapp_stream stream) {
-    return autotune_impl(ctx, obs, agents, 0, prm, out, max_candidates, probe_steps, best,
+    return autotune_impl(ctx, obs, agents, Kinds{}, prm, out, max_candidates, probe_steps, best,
                          best_ms, stream);
 }
 
 extern "C" gmapp_status gmapp_autotune_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *obs,
-                                                const gmapp_agents *agents, int32_t n_apf,
+                                                const gmapp_agents *agents, int32_t n_proj,
+                                                int32_t n_apf,
                                                 const gmapp_rollout_params *prm,
                                                 gmapp_rollout_out *out, int32_t max_candidates,
                                                 int32_t probe_steps, gmapp_tuning *best,
                                                 float *best_ms, gmapp_stream stream) {
-    return autotune_impl(ctx, obs, agents, n_apf, prm, out, max_candidates, probe_steps, best,
-                         best_ms, stream);
+    return autotune_impl(ctx, obs, agents, Kinds{n_proj, n_apf}, prm, out, max_candidates,
+                         probe_steps, best, best_ms, stream);
 }
 
 extern "C" gmapp_status gmapp_pick_tuning(gmapp_ctx *ctx, int64_t obs_cap, int32_t n_agents,
@@ -515,7 +576,8 @@ extern "C" gmapp_status rollout_agents(gmapp_ctx *ctx, const gmapp_obstacles *ob
 }
 
 extern "C" gmapp_status rollout_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *obs,
-                                         const gmapp_agents *agents, int32_t n_apf,
+                                         const gmapp_agents *agents, int32_t n_proj,
+                                         int32_t n_apf,
                                          const gmapp_rollout_params *prm, gmapp_rollout_out *out,
                                          const gmapp_tuning *tune, gmapp_stream stream) {
     if (!ctx) {
@@ -524,14 +586,7 @@ extern "C" gmapp_status rollout_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *
     }
     gmapp_status st = validate(obs, agents, prm, out);
     if (st != GMAPP_OK) return st;
-    if (n_apf < 0 || n_apf > agents->n) {
-        set_error("rollout_ensemble: n_apf must lie in [0, n] (n_apf %d, n %d)", n_apf, agents->n);
-        return GMAPP_ERR_INVALID_ARG;
-    }
-    if (n_apf > 0 && out->ckpt) {
-        set_error("rollout_ensemble: adjoint checkpoints cover MFI agents only");
-        return GMAPP_ERR_INVALID_ARG;
-    }
+    if ((st = check_kinds("rollout_ensemble", agents, n_proj, n_apf, out)) != GMAPP_OK) return st;
     gmapp_tuning t;
     if (tune) {
         if (!(tune->threads == 128 || tune->threads == 256 || tune->threads == 384 ||
@@ -541,8 +596,8 @@ extern "C" gmapp_status rollout_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *
         }
         t = *tune;
     } else {
-        st = pick_tuning_impl(ctx, obs->cap, agents->n, wants_clear(out), &t, n_apf);
+        st = pick_tuning_impl(ctx, obs->cap, agents->n, wants_clear(out), &t, Kinds{n_proj, n_apf});
         if (st != GMAPP_OK) return st;
     }
-    return launch(ctx, obs, agents, prm, out, t, stream, n_apf);
+    return launch(ctx, obs, agents, prm, out, t, stream, Kinds{n_proj, n_apf});
 }

@@ -1,8 +1,8 @@
-// Rollout kernel instantiations: heterogeneous ensemble, CLEAR = true, GRID = true.
+// Rollout kernel instantiations: heterogeneous ensemble (MFI + APF), CLEAR = true, GRID = true.
 #include "rollout_inst.cuh"
 
 namespace gmapp {
 RolloutKernel rollout_kernel_ens_grid_clear(int ag, int nt) {
-    return rollout_table<true, true, true>(ag, nt);
+    return rollout_table<true, true, 1>(ag, nt);
 }
 }  // namespace gmapp

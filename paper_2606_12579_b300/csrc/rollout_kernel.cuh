@@ -46,6 +46,8 @@ constexpr int kMaxCluster = 16;
 constexpr int kMaxAgents = 16;
 // agents per group of the heterogeneous-ensemble kernel
 constexpr int kMaxEnsembleAgents = 12;
+// heuristic kinds of an agent group
+constexpr int kMfi = 0, kApf = 1, kProj = 2;
 // rows of the per-agent four-term cost sums kept in shared memory
 constexpr int kCostAcc = 11;
 
@@ -69,6 +71,8 @@ struct RolloutArgs {
     int32_t n_groups;    // agent groups (clusters, or CTA groups with the grid exchange)
     int32_t n_apf;       // ensemble kernel: the last n_apf agents use APF (Eq. (apf))
     int32_t n_groups_apf;  // ensemble kernel: ... and form the last n_groups_apf groups
+    int32_t n_proj;      // ensemble kernel: the n_proj agents before them use the
+    int32_t n_groups_proj;  // projected current, in n_groups_proj groups
     int32_t group_ctas;  // grid exchange: CTAs per group (C)
     uint64_t *xbuf;      // grid exchange: tagged slots [G][2][2][C][AG][2]
     uint32_t *xctl;      // grid exchange: launch epoch, finished-CTA counter
@@ -630,80 +634,88 @@ __device__ __forceinline__ void half_step_apf(const float *sx, const float *sy, 
     }
 }
 
-// Sum of the NW per-warp APF records of agent OFF + lane in warp order.
-template <int AG, int OFF, int NW, bool CLEAR>
-__device__ __forceinline__ float4 sum_warp_records(const float *part, int lane) {
-    float4 s = make_float4(0.0f, 0.0f, 0.0f, INFINITY);
+// ---- per-agent records of the vector heuristics ---------------------------
+// An APF or projected-current agent exchanges a record of RS floats per step:
+// NF summed components, then (with CLEAR) the smallest |d|^2 at index NF.
+//   APF (Eq. apf):               NF = 3 (f_x, f_y, f_z),       RS = 4
+//   projected current (Eq. mfi): NF = 4 (S_x, S_y, S_z, B),    RS = 6
+// RS is even: records move as float2 pieces (8-byte aligned).
+
+// Sum of the NW per-warp records of agent OFF + lane in warp order.
+template <int AG, int OFF, int NW, bool CLEAR, int NF, int RS>
+__device__ __forceinline__ void sum_warp_rec(const float *part, int lane, float (&s)[RS]) {
+#pragma unroll
+    for (int c = 0; c < RS; ++c) s[c] = c < NF ? 0.0f : INFINITY;
 #pragma unroll 4
     for (int q = 0; q < NW; ++q) {
-        const float4 t = *reinterpret_cast<const float4 *>(part + 4 * (q * AG + OFF + lane));
-        s.x += t.x;
-        s.y += t.y;
-        s.z += t.z;
-        if (CLEAR) s.w = fminf(s.w, t.w);
+        const float *src = part + RS * (q * AG + OFF + lane);
+#pragma unroll
+        for (int c = 0; c < RS; c += 2) {
+            const float2 t = *reinterpret_cast<const float2 *>(src + c);
+            if (c < NF) s[c] += t.x;
+            if (c + 1 < NF) s[c + 1] += t.y;
+            if (CLEAR && c == NF) s[c] = fminf(s[c], t.x);
+            if (CLEAR && c + 1 == NF) s[c + 1] = fminf(s[c + 1], t.y);
+        }
     }
-    return s;
 }
 
 // Sum of the C per-CTA records of agent `lane` in rank order.
-template <int AG, bool CLEAR>
-__device__ __forceinline__ void sum_rank_records(const float *slot, uint32_t C, int lane,
-                                                 float (&F)[3], float &md2) {
-    float fx = 0.0f, fy = 0.0f, fz = 0.0f, ms = INFINITY;
+template <int AG, bool CLEAR, int NF, int RS>
+__device__ __forceinline__ void sum_rank_rec(const float *slot, uint32_t C, int lane,
+                                             float (&F)[4], float &md2) {
+    float acc[NF];
+#pragma unroll
+    for (int c = 0; c < NF; ++c) acc[c] = 0.0f;
+    float ms = INFINITY;
     for (uint32_t r = 0; r < C; ++r) {
-        const float4 t = *reinterpret_cast<const float4 *>(slot + 4 * (r * AG + lane));
-        fx += t.x;
-        fy += t.y;
-        fz += t.z;
-        if (CLEAR) ms = fminf(ms, t.w);
+        const float *src = slot + RS * (r * AG + lane);
+#pragma unroll
+        for (int c = 0; c < NF; ++c) acc[c] += src[c];
+        if (CLEAR) ms = fminf(ms, src[NF]);
     }
-    F[0] = fx;
-    F[1] = fy;
-    F[2] = fz;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) F[c] = c < NF ? acc[c] : 0.0f;
     md2 = ms;
 }
 
-__device__ __forceinline__ void st_async_v4f32(uint32_t remote_addr, float4 v, uint32_t remote_bar) {
-    asm volatile(
-        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
-            remote_addr),
-        "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(remote_bar)
-        : "memory");
-}
-
-// exchange_half for APF records (16 bytes per agent and CTA).
-template <int AG, int NA, int OFF, int NW, bool CLEAR>
-__device__ __forceinline__ bool exchange_half_apf(const float *part, float *slot, uint64_t *bar,
+// exchange_half for records: the CTA record goes to slot[rank][agent] of
+// every cluster CTA with st.async (RS / 2 pieces of 8 bytes each).
+template <int AG, int NA, int OFF, int NW, bool CLEAR, int NF, int RS>
+__device__ __forceinline__ bool exchange_half_rec(const float *part, float *slot, uint64_t *bar,
                                                   uint32_t C, uint32_t rank, int lane, int k,
-                                                  bool ok, float (&F)[3], float &md2) {
-    float4 s = make_float4(0.0f, 0.0f, 0.0f, INFINITY);
-    if (lane < NA) s = sum_warp_records<AG, OFF, NW, CLEAR>(part, lane);
-    if (lane == 0) mbar_arrive_expect_tx(bar, C * NA * 16u);
+                                                  bool ok, float (&F)[4], float &md2) {
+    float s[RS];
+    if (lane < NA) sum_warp_rec<AG, OFF, NW, CLEAR, NF, RS>(part, lane, s);
+    if (lane == 0) mbar_arrive_expect_tx(bar, C * NA * RS * 4u);
     if (lane < NA) {
-        const uint32_t local = smem_u32(slot + 4 * (rank * AG + OFF + lane));
+        const uint32_t local = smem_u32(slot + RS * (rank * AG + OFF + lane));
         const uint32_t lbar = smem_u32(bar);
-        for (uint32_t r = 0; r < C; ++r) st_async_v4f32(map_smem(local, r), s, map_smem(lbar, r));
+        for (uint32_t r = 0; r < C; ++r) {
+            const uint32_t dst = map_smem(local, r), rb = map_smem(lbar, r);
+#pragma unroll
+            for (int c = 0; c < RS; c += 2) st_async_v2f32(dst + 4u * c, s[c], s[c + 1], rb);
+        }
     }
     if (ok && !mbar_wait_cluster(bar, (k >> 1) & 1)) ok = false;
-    if (lane >= OFF && lane < OFF + NA) sum_rank_records<AG, CLEAR>(slot, C, lane, F, md2);
+    if (lane >= OFF && lane < OFF + NA) sum_rank_rec<AG, CLEAR, NF, RS>(slot, C, lane, F, md2);
     return ok;
 }
 
-// exchange_half_grid for APF records: 3 tagged words per agent and CTA
-// (f_x, f_y, f_z), a fourth (min |d|^2) with CLEAR.
-template <int AG, int NA, int OFF, int NW, bool CLEAR>
-__device__ __forceinline__ bool exchange_half_grid_apf(const float *part, uint64_t *xs,
+// exchange_half_grid for records: NF tagged words per agent and CTA, one
+// more (min |d|^2) with CLEAR, at xs[RS (rank AG + agent) + c].
+template <int AG, int NA, int OFF, int NW, bool CLEAR, int NF, int RS>
+__device__ __forceinline__ bool exchange_half_grid_rec(const float *part, uint64_t *xs,
                                                        float *slot, uint32_t C, uint32_t rank,
                                                        int lane, uint32_t tag, bool ok,
-                                                       float (&F)[3], float &md2) {
-    constexpr int NV = CLEAR ? 4 : 3;
+                                                       float (&F)[4], float &md2) {
+    constexpr int NV = CLEAR ? NF + 1 : NF;
     if (lane < NA) {
-        const float4 s = sum_warp_records<AG, OFF, NW, CLEAR>(part, lane);
-        uint64_t *dst = xs + 4 * (rank * AG + OFF + lane);
-        st_relaxed_u64(dst, xword(tag, s.x));
-        st_relaxed_u64(dst + 1, xword(tag, s.y));
-        st_relaxed_u64(dst + 2, xword(tag, s.z));
-        if (CLEAR) st_relaxed_u64(dst + 3, xword(tag, s.w));
+        float s[RS];
+        sum_warp_rec<AG, OFF, NW, CLEAR, NF, RS>(part, lane, s);
+        uint64_t *dst = xs + RS * (rank * AG + OFF + lane);
+#pragma unroll
+        for (int c = 0; c < NV; ++c) st_relaxed_u64(dst + c, xword(tag, s[c]));
     }
     constexpr int J = NA > 0 ? (kMaxCluster * NA + 31) / 32 : 1;
     const int npairs = static_cast<int>(C) * NA;
@@ -712,7 +724,7 @@ __device__ __forceinline__ bool exchange_half_grid_apf(const float *part, uint64
     for (int j = 0; j < J; ++j) {
         const int p = lane + 32 * j;
         if (p < npairs) {
-            const uint64_t *src = xs + 4 * ((p / NA) * AG + OFF + p % NA);
+            const uint64_t *src = xs + RS * ((p / NA) * AG + OFF + p % NA);
 #pragma unroll
             for (int c = 0; c < NV; ++c) w[j][c] = ld_relaxed_u64(src + c);
         }
@@ -722,23 +734,128 @@ __device__ __forceinline__ bool exchange_half_grid_apf(const float *part, uint64
         const int p = lane + 32 * j;
         if (p < npairs) {
             const int r = p / NA, a = OFF + p % NA;
-            const uint64_t *src = xs + 4 * (r * AG + a);
-            float val[4] = {0.0f, 0.0f, 0.0f, INFINITY};
+            const uint64_t *src = xs + RS * (r * AG + a);
+            float *dst = slot + RS * (r * AG + a);
 #pragma unroll
             for (int c = 0; c < NV; ++c) {
                 for (uint32_t it = 0; ok && static_cast<uint32_t>(w[j][c] >> 32) != tag; ++it) {
                     if (it == kPollLimit) ok = false;
                     else w[j][c] = ld_relaxed_u64(src + c);
                 }
-                val[c] = __uint_as_float(static_cast<uint32_t>(w[j][c]));
+                dst[c] = __uint_as_float(static_cast<uint32_t>(w[j][c]));
             }
-            *reinterpret_cast<float4 *>(slot + 4 * (r * AG + a)) =
-                make_float4(val[0], val[1], val[2], val[3]);
         }
     }
     __syncwarp();
-    if (lane >= OFF && lane < OFF + NA) sum_rank_records<AG, CLEAR>(slot, C, lane, F, md2);
+    if (lane >= OFF && lane < OFF + NA) sum_rank_rec<AG, CLEAR, NF, RS>(slot, C, lane, F, md2);
     return ok;
+}
+
+// ---- MFI with the per-obstacle projected current ---------------------------
+//
+// Eq. (mfi) with the current c_j = d' - n_j (n_j . d') of each obstacle
+// (static obstacles, d' = -v, n_j = d_j / |d_j|, d_j = p - p_Oj) and Alg. 1's
+// clamp and gate.  The cross products reduce to
+//   (d'/|d'|) x (c_j x d') = (n_j . v) / |v| (|v|^2 n_j - (n_j . v) v),
+// so with t_j = d_j . v, a_j = w_j t_j / |d_j|^2 and w_j = [s_j <= r_d] / s_j
+//   f = (|v|^2 S - v B) / |v|,  S = sum_j a_j d_j,  B = sum_j a_j t_j;
+// the pair loop accumulates S and B (one record per agent), the exchange warp
+// forms f.  |d|^2 carries an added 1e-30, so a pair at d = 0 (no normal)
+// adds a_j d_j = 0.  Per pair: 17 FMA-pipe lane-ops (3 sub, 3 for |d|^2, 1
+// for s, 3 for t, 3 for a, 4 accumulating FMAs), rsqrt and rcp on the SFU,
+// clamp and gate select on the ALU.  The FMA pipe bounds it (an NR
+// reciprocal would only add FMA work), so every agent takes rcp.approx.
+template <int AG, int NA, int OFF, bool CLEAR>
+__device__ __forceinline__ void proj_pair_terms(f2 ox, f2 oy, f2 oz, const f2 (&X)[NA],
+                                                const f2 (&Y)[NA], const f2 (&Z)[NA],
+                                                const f2 (&VX)[NA], const f2 (&VY)[NA],
+                                                const f2 (&VZ)[NA], f2 (&sx)[NA], f2 (&sy)[NA],
+                                                f2 (&sz)[NA], f2 (&sb)[NA], float (&mn)[NA],
+                                                const f2 (&nR2)[AG], const float (&G2a)[AG],
+                                                float eps, f2 tiny2) {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const f2 dx = sub2(X[a], ox), dy = sub2(Y[a], oy), dz = sub2(Z[a], oz);
+        const f2 d2 = fma2(dz, dz, fma2(dy, dy, fma2(dx, dx, tiny2)));
+        const float d2l = lo_of(d2), d2h = hi_of(d2);
+        const float rl = rsqrt_approx(d2l), rh = rsqrt_approx(d2h);
+        const f2 r = pk(rl, rh);
+        const f2 s = fma2(d2, r, nR2[OFF + a]);  // |d| - R
+        const float wl = d2l <= G2a[OFF + a] ? rcp_approx(fmaxf(lo_of(s), eps)) : 0.0f;
+        const float wh = d2h <= G2a[OFF + a] ? rcp_approx(fmaxf(hi_of(s), eps)) : 0.0f;
+        const f2 t = fma2(dz, VZ[a], fma2(dy, VY[a], mul2(dx, VX[a])));
+        const f2 q = mul2(mul2(pk(wl, wh), mul2(r, r)), t);
+        sx[a] = fma2(q, dx, sx[a]);
+        sy[a] = fma2(q, dy, sy[a]);
+        sz[a] = fma2(q, dz, sz[a]);
+        sb[a] = fma2(q, t, sb[a]);
+        if (CLEAR) mn[a] = fminf(mn[a], fminf(d2l, d2h));
+    }
+}
+
+// Projected-current counterpart of half_step: positions and velocities of
+// the half's agents from shared memory (pos, vel: [3][AG]); the record
+// (S_x, S_y, S_z, B, min |d|^2, 0) of each agent goes to part_slot0[6 a'].
+template <int AG, int NA, int OFF, int NT, bool CLEAR>
+__device__ __forceinline__ void half_step_proj(const float *sx, const float *sy, const float *sz,
+                                               int cnt_pad, float eps, const f2 (&nR2)[AG],
+                                               const float (&G2a)[AG], float *part_slot0,
+                                               int lane, const float *pos, const float *vel) {
+    if constexpr (NA > 0) {
+        constexpr int P = pow2ceil(NA);
+        const int tid = threadIdx.x;
+        f2 X[NA], Y[NA], Z[NA], VX[NA], VY[NA], VZ[NA], ax[NA], ay[NA], az[NA], ab[NA];
+        float mn[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            const float x = pos[OFF + a], y = pos[AG + OFF + a], z = pos[2 * AG + OFF + a];
+            const float u = vel[OFF + a], v = vel[AG + OFF + a], w = vel[2 * AG + OFF + a];
+            X[a] = pk(x, x);
+            Y[a] = pk(y, y);
+            Z[a] = pk(z, z);
+            VX[a] = pk(u, u);
+            VY[a] = pk(v, v);
+            VZ[a] = pk(w, w);
+            ax[a] = ay[a] = az[a] = ab[a] = 0ull;
+            mn[a] = INFINITY;
+        }
+        const f2 tiny2 = pk(1e-30f, 1e-30f);
+#pragma unroll 2
+        for (int j = 2 * tid; j < cnt_pad; j += 2 * NT) {
+            const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
+            const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
+            const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
+            proj_pair_terms<AG, NA, OFF, CLEAR>(ox, oy, oz, X, Y, Z, VX, VY, VZ, ax, ay, az, ab,
+                                                mn, nR2, G2a, eps, tiny2);
+        }
+        float v0[P], v1[P], v2[P], v3[P], vm[P];
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            if (a < NA) {
+                v0[a] = lo_of(ax[a]) + hi_of(ax[a]);
+                v1[a] = lo_of(ay[a]) + hi_of(ay[a]);
+                v2[a] = lo_of(az[a]) + hi_of(az[a]);
+                v3[a] = lo_of(ab[a]) + hi_of(ab[a]);
+                vm[a] = mn[a];
+            } else {
+                v0[a] = v1[a] = v2[a] = v3[a] = 0.0f;
+                vm[a] = INFINITY;
+            }
+        }
+        const float r0 = transposed_reduce<P, false>(v0, lane);
+        const float r1 = transposed_reduce<P, false>(v1, lane);
+        const float r2 = transposed_reduce<P, false>(v2, lane);
+        const float r3 = transposed_reduce<P, false>(v3, lane);
+        const float m = CLEAR ? transposed_reduce<P, true>(vm, lane) : INFINITY;
+        constexpr int REP = (32 >> log2i(P)) - 1;
+        const int idx = transposed_index<P>(lane);
+        if ((lane & REP) == 0 && idx < NA) {
+            float2 *dst = reinterpret_cast<float2 *>(part_slot0 + 6 * (OFF + idx));
+            dst[0] = make_float2(r0, r1);
+            dst[1] = make_float2(r2, r3);
+            dst[2] = make_float2(m, 0.0f);
+        }
+    }
 }
 
 // One step of Sec. IV-A for an APF agent: F = k_a (goal - p) - D v + kf f
@@ -772,11 +889,13 @@ __device__ __forceinline__ void agent_step_apf(float (&p)[3], float (&v)[3], flo
 // block cluster and exchange over DSMEM; true -- groups of C consecutive
 // CTAs of a cooperative (all co-resident) grid exchange through global
 // memory, which lets groups fill every SM whatever the GPC layout.
-// ENS compiles the heterogeneous ensemble (Sec. IV-A agent set with the
-// heuristics of Eq. (apf) and Eq. (mfi)): the last n_apf agents form the
-// last n_groups_apf groups and use APF, the others MFI; every group is
-// homogeneous, so the branch between the two pair loops is uniform per CTA.
-template <int AG, int NM, int NT, bool CLEAR, bool GRID, bool ENS = false>
+// EK compiles the heterogeneous ensemble (Sec. IV-A agent set with the
+// heuristics of Eq. (apf) and Eq. (mfi)): EK = 0 -- MFI only; EK = 1 -- the
+// last n_apf agents form the last n_groups_apf groups and use APF; EK = 2 --
+// in addition the n_proj agents before them form n_groups_proj groups of
+// MFI with the per-obstacle projected current.  Every group is homogeneous,
+// so the branch between the pair loops is uniform per CTA.
+template <int AG, int NM, int NT, bool CLEAR, bool GRID, int EK = 0>
 __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
     constexpr int NW = NT / 32;       // compute warps; warp NW is the exchange warp
     constexpr int H0 = (AG + 1) / 2;  // agents [0, H0) form half 0, [H0, AG) half 1
@@ -805,22 +924,29 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
         group = cluster_id_x();
     }
     int a0, na;
-    bool apf = false;
-    if constexpr (ENS) {
-        const int gm = A.n_groups - A.n_groups_apf, nm = A.n_agents - A.n_apf;
-        if (static_cast<int>(group) < gm) {
-            group_range(static_cast<int>(group), nm, gm, a0, na);
-        } else {
-            apf = true;
-            group_range(static_cast<int>(group) - gm, A.n_apf, A.n_groups_apf, a0, na);
+    int kind = kMfi;  // heuristic of this CTA's group
+    if constexpr (EK > 0) {
+        const int gp = EK > 1 ? A.n_groups_proj : 0, np = EK > 1 ? A.n_proj : 0;
+        const int gm = A.n_groups - A.n_groups_apf - gp, nm = A.n_agents - A.n_apf - np;
+        const int g = static_cast<int>(group);
+        if (g < gm) {
+            group_range(g, nm, gm, a0, na);
+        } else if (g < gm + gp) {
+            kind = kProj;
+            group_range(g - gm, np, gp, a0, na);
             a0 += nm;
+        } else {
+            kind = kApf;
+            group_range(g - gm - gp, A.n_apf, A.n_groups_apf, a0, na);
+            a0 += nm + np;
         }
     } else {
         group_range(static_cast<int>(group), A.n_agents, A.n_groups, a0, na);
     }
     // floats per agent record exchanged each step: (W, min |d|^2) for MFI,
-    // (f_x, f_y, f_z, min |d|^2) for APF
-    const int SR = apf ? 4 : 2;
+    // (f_x, f_y, f_z, min |d|^2) for APF, (S_x, S_y, S_z, B, min |d|^2, -)
+    // for the projected current
+    const int SR = kind == kApf ? 4 : kind == kProj ? 6 : 2;
 
     // N_O is read on the device; all CTAs of the cluster see the same value,
     // so an early exit is taken by the whole cluster before any DSMEM access.
@@ -849,10 +975,12 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
     float *partbuf = smem + 3 * A.shard_cap;
     // per-CTA partials received from the cluster: [half][parity][rank][AG] records
     float *recv = partbuf + 2 * SR * NW * AG;
-    // agent positions for the compute warps: [3][AG]
+    // agent positions and (projected current) velocities for the compute
+    // warps: [3][AG] each, 4 AG floats apart
     float *pos = recv + 4 * SR * static_cast<int>(C) * AG;
+    float *vel = pos + 4 * AG;
     // four-term cost sums of the exchange warp (lane = agent): [kCostAcc][AG]
-    float *cacc = pos + 4 * AG;
+    float *cacc = vel + 4 * AG;
     auto part = [&](int h) { return partbuf + h * (SR * NW * AG); };
     auto slot = [&](int h, int par) {
         return recv + (h * 2 + par) * (SR * static_cast<int>(C) * AG);
@@ -901,6 +1029,11 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
         pos[lane] = p[0];
         pos[AG + lane] = p[1];
         pos[2 * AG + lane] = p[2];
+        if (EK > 1) {
+            vel[lane] = v[0];
+            vel[AG + lane] = v[1];
+            vel[2 * AG + lane] = v[2];
+        }
     }
     f2 nR2[AG];
     float G2a[AG];
@@ -920,7 +1053,7 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
     // MFI sum), or a far point for APF groups
     const int32_t cnt_pad = (cnt + 1) & ~1;
     if (tid == 0 && cnt_pad > cnt) {
-        const float pad = apf ? kApfPad : __int_as_float(0x7fc00000);
+        const float pad = kind != kMfi ? kApfPad : __int_as_float(0x7fc00000);
         sx[cnt] = pad;
         sy[cnt] = pad;
         sz[cnt] = pad;
@@ -931,9 +1064,10 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
     if constexpr (GRID) __syncthreads();
     else cluster_sync_all();
 
-    // The step loops of one group kind (MFI or APF).
-    auto run = [&](auto kind) {
-        constexpr bool APF = decltype(kind)::value;
+    // The step loops of one group kind (kMfi, kApf or kProj).
+    auto run = [&](auto kind_tag) {
+        constexpr int KIND = decltype(kind_tag)::value;
+        constexpr bool APF = KIND == kApf, PROJ = KIND == kProj;
         // APF per-agent constants: 1/(R + eps), 1/r_d and the strict gate
         // |d|^2 < (r_d + R)^2 (never when r_d + R <= 0)
         float cRa[AG], G2s[AG];
@@ -960,6 +1094,10 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
                 if constexpr (APF)
                     half_step_apf<AG, H0, 0, NT, CLEAR>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
                                                         part(0) + 4 * (warp * AG), lane, pos);
+                else if constexpr (PROJ)
+                    half_step_proj<AG, H0, 0, NT, CLEAR>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
+                                                         part(0) + 6 * (warp * AG), lane, pos,
+                                                         vel);
                 else
                     half_step<AG, H0, 0, NM0, NT, CLEAR, false, false, true>(
                         sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(0) + 2 * (warp * AG), C,
@@ -969,6 +1107,10 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
                 if constexpr (APF)
                     half_step_apf<AG, H1, H0, NT, CLEAR>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
                                                          part(1) + 4 * (warp * AG), lane, pos);
+                else if constexpr (PROJ)
+                    half_step_proj<AG, H1, H0, NT, CLEAR>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
+                                                          part(1) + 6 * (warp * AG), lane, pos,
+                                                          vel);
                 else
                     half_step<AG, H1, H0, NM1, NT, CLEAR, false, false, true>(
                         sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(1) + 2 * (warp * AG), C,
@@ -993,8 +1135,9 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
         if (CLEAR && A.cost_terms && lane < AG) {
             for (int r = 0; r < kCostAcc; ++r) cv(r) = 0.0f;
         }
-        // rec: W (MFI) or the force sum f (APF) of this lane's agent
-        auto integrate = [&](int k, const float (&rec)[3], float md2) {
+        // rec: W (MFI), the force sum f (APF), or S and B (projected
+        // current) of this lane's agent
+        auto integrate = [&](int k, const float (&rec)[4], float md2) {
             if (A.ckpt && rank == 0 && k % A.ckpt_every == 0) {
                 // adjoint checkpoint: the state (p_k, v_{k-1}) entering step k
                 const int n = A.n_agents, i = a0 + lane;
@@ -1017,14 +1160,22 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
             }
             float fr[3], w, m, F[3];
             float *Fo = CLEAR && A.cost_terms ? F : nullptr;
-            if constexpr (APF) {
+            if constexpr (APF || PROJ) {
                 const float kf = A.rho * k_r;
+                float f3[3] = {rec[0], rec[1], rec[2]};
+                if constexpr (PROJ) {
+                    // f = (|v|^2 S - v B) / |v| with v = v_{k-1}; 0 at rest
+                    const float vv = fmaf(v[2], v[2], fmaf(v[1], v[1], v[0] * v[0]));
+                    const float inv = vv >= 1e-30f ? rsqrt_approx(vv) : 0.0f;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) f3[d] = (vv * rec[d] - v[d] * rec[3]) * inv;
+                }
                 agent_step_apf<CLEAR>(p, v, kf, k_a, R, A.goal, h, A.dt, A.damping,
-                                      A.clear_margin, A.clear_beta, rec, md2, L, pen, minc, m,
+                                      A.clear_margin, A.clear_beta, f3, md2, L, pen, minc, m,
                                       Fo);
 #pragma unroll
-                for (int d = 0; d < 3; ++d) fr[d] = kf * rec[d];
-                w = sqrtf(fmaf(rec[2], rec[2], fmaf(rec[1], rec[1], rec[0] * rec[0])));
+                for (int d = 0; d < 3; ++d) fr[d] = kf * f3[d];
+                w = sqrtf(fmaf(f3[2], f3[2], fmaf(f3[1], f3[1], f3[0] * f3[0])));
             } else {
                 float g[3], kf;
                 w = rec[0];
@@ -1057,6 +1208,11 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
             pos[lane] = p[0];
             pos[AG + lane] = p[1];
             pos[2 * AG + lane] = p[2];
+            if constexpr (PROJ) {
+                vel[lane] = v[0];
+                vel[AG + lane] = v[1];
+                vel[2 * AG + lane] = v[2];
+            }
             if (rank == 0) {
                 const int i = a0 + lane;
                 if (A.traj) {
@@ -1082,24 +1238,25 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
         uint64_t *xg = nullptr;
         // grid slots of a group: [half][parity][rank][AG] records of SR
         // words; the ensemble kernel spaces groups for the larger record
-        constexpr int kGroupRec = ENS ? 4 : 2;
+        constexpr int kGroupRec = EK > 1 ? 6 : EK == 1 ? 4 : 2;
         if constexpr (GRID) {
             epoch = ld_relaxed_u32(A.xctl);
             xg = A.xbuf + static_cast<size_t>(group) * 4 * kGroupRec * C * AG;
         }
         auto xslot = [&](int hh, int par) { return xg + (hh * 2 + par) * SR * C * AG; };
-        auto exchange = [&](auto half, int k, int par, float (&rec)[3], float &md2) {
+        auto exchange = [&](auto half, int k, int par, float (&rec)[4], float &md2) {
             constexpr int HH = decltype(half)::value;
             constexpr int NA = HH ? H1 : H0, OFF = HH ? H0 : 0;
-            if constexpr (APF) {
+            if constexpr (APF || PROJ) {
+                constexpr int NF = APF ? 3 : 4, RS = APF ? 4 : 6;
                 if constexpr (GRID)
-                    ok = exchange_half_grid_apf<AG, NA, OFF, NW, CLEAR>(
+                    ok = exchange_half_grid_rec<AG, NA, OFF, NW, CLEAR, NF, RS>(
                         part(HH), xslot(HH, par), slot(HH, par), C, rank, lane, xtag(epoch, k), ok,
                         rec, md2);
                 else
-                    ok = exchange_half_apf<AG, NA, OFF, NW, CLEAR>(part(HH), slot(HH, par),
-                                                                   &bar_recv[HH][par], C, rank,
-                                                                   lane, k, ok, rec, md2);
+                    ok = exchange_half_rec<AG, NA, OFF, NW, CLEAR, NF, RS>(
+                        part(HH), slot(HH, par), &bar_recv[HH][par], C, rank, lane, k, ok, rec,
+                        md2);
             } else {
                 if constexpr (GRID)
                     ok = exchange_half_grid<AG, NA, OFF, NW, CLEAR>(part(HH), xslot(HH, par),
@@ -1114,7 +1271,7 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
         };
         for (int k = 0; k < A.n_steps; ++k) {
             const int par = k & 1;
-            float rec[3] = {0.0f, 0.0f, 0.0f}, md2 = INFINITY;
+            float rec[4] = {0.0f, 0.0f, 0.0f, 0.0f}, md2 = INFINITY;
             named_sync(kPart + 0, kBoth);
             exchange(std::integral_constant<int, 0>{}, k, par, rec, md2);
             if (lane < H0 && lane < na) integrate(k, rec, md2);
@@ -1151,11 +1308,15 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
             }
         }
     };
-    if constexpr (ENS) {
-        if (apf) run(std::true_type{});
-        else run(std::false_type{});
+    if constexpr (EK == 0) {
+        run(std::integral_constant<int, kMfi>{});
+    } else if constexpr (EK == 1) {
+        if (kind == kApf) run(std::integral_constant<int, kApf>{});
+        else run(std::integral_constant<int, kMfi>{});
     } else {
-        run(std::false_type{});
+        if (kind == kApf) run(std::integral_constant<int, kApf>{});
+        else if (kind == kProj) run(std::integral_constant<int, kProj>{});
+        else run(std::integral_constant<int, kMfi>{});
     }
     // no CTA leaves while another may still deliver into its shared memory
     if constexpr (!GRID) cluster_sync_all();
@@ -1172,6 +1333,10 @@ RolloutKernel rollout_kernel_ens_noclear(int ag, int nt);
 RolloutKernel rollout_kernel_ens_clear(int ag, int nt);
 RolloutKernel rollout_kernel_ens_grid_noclear(int ag, int nt);
 RolloutKernel rollout_kernel_ens_grid_clear(int ag, int nt);
+RolloutKernel rollout_kernel_ens3_noclear(int ag, int nt);
+RolloutKernel rollout_kernel_ens3_clear(int ag, int nt);
+RolloutKernel rollout_kernel_ens3_grid_noclear(int ag, int nt);
+RolloutKernel rollout_kernel_ens3_grid_clear(int ag, int nt);
 
 // SFU share of the reciprocals: NM of AG agents use rcp.approx, the rest the
 // Newton-Raphson path.  Per obstacle pair an SFU agent costs 8 FMA-pipe

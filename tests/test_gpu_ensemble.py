@@ -267,3 +267,101 @@ def test_ensemble_autotuner(gm):
     assert np.array_equal(a["traj"].cpu().numpy(), b["traj"].cpu().numpy())
     ref = oracle.rollout(obs, r_O, w["agents"], w["params"], n_apf=16)
     _compare(a, ref)
+
+
+# ---- MFI with the per-obstacle projected current (the third kind) ----------
+
+def test_projected_force_parity_at_oracle_states(gm):
+    """f_r of projected-current agents evaluated once (N_k = 1) at states of
+    the oracle's trajectories.  Each term of f = (|v|^2 S - v B) / |v| is at
+    most 2 w_j |v| (w_j = 1/s_j inside the gate), so the FP32 bound is
+    1e-5 |f| + 4e-6 k_f |v| W, W = sum_j w_j, plus 2 k_f |v| / r_d per
+    gate-ambiguous pair."""
+    w = _sphere_ensemble(n_agents=12, n_apf=0)
+    obs, r_O = _filtered(w)
+    prm = w["params"]
+    ref = oracle.rollout(obs, r_O, w["agents"], prm, n_proj=12)
+    ps, vs = [], []
+    for k in (1, 40, 80, 110, 140, 170, 199):
+        ps.append(ref["traj"][:, k].T)
+        vs.append((ref["traj"][:, k] - ref["traj"][:, k - 1]).T / prm.dt)
+    P = np.concatenate(ps, axis=1).astype(np.float32)
+    V = np.concatenate(vs, axis=1).astype(np.float32)
+    n = P.shape[1]
+    ag = subset_agents(w["agents"], np.tile(np.arange(12), 7))
+    ag["p0"], ag["v0"] = np.ascontiguousarray(P), np.ascontiguousarray(V)
+    one = dataclasses.replace(prm, n_steps=1)
+    out = gm.rollout_ensemble(_gpu_obstacles(gm, obs, r_O), to_dev_agents(ag), 0, one,
+                              want_trace=True, n_proj=n)
+    gm.sync()
+    f_gpu = out["f_trace"][:, 0, :].cpu().numpy().T.astype(np.float64)
+    P64, V64 = P.astype(np.float64), V.astype(np.float64)
+    r = oracle.proj_eval(obs, r_O, P64, V64, ag, prm.rho, prm.eps)
+    W = oracle.cf_eval(obs, r_O, P64, V64, ag, prm.rho, prm.eps)["W"]
+    R = ag["r_a"].astype(np.float64) + r_O
+    r_d = ag["r_d"].astype(np.float64)
+    kf = prm.rho * ag["k_r"].astype(np.float64)
+    vn = np.linalg.norm(V64, axis=0)
+    amb = gate_allowance(obs.astype(np.float64), P64, R, r_d)
+    fn = np.linalg.norm(r["f_r"], axis=0)
+    err = np.linalg.norm(f_gpu - r["f_r"], axis=0)
+    tol = FORCE_TOL * fn + 4e-6 * kf * vn * W + amb * 2.0 * kf * vn / r_d
+    assert (fn > 0).sum() >= 20
+    assert np.all(err <= tol), (err / np.maximum(fn, 1e-30)).max()
+    assert np.all(np.abs((f_gpu * V64).sum(axis=0)) <= 1e-5 * fn * vn + 4e-6 * kf * vn * vn * W)
+    m_gpu = out["m_trace"][:, 0].cpu().numpy()
+    assert np.abs(m_gpu - r["m"]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("clear", [True, False], ids=["clear", "noclear"])
+@pytest.mark.parametrize("shape", [(1, 4, 256, 0), (3, 3, 256, 0), (2, 4, 128, 1), (5, 2, 256, 1)],
+                         ids=lambda s: "c%d_a%d_t%d_x%d" % s)
+def test_three_kind_ensemble_launch_shapes(gm, shape, clear):
+    """4 MFI + 4 projected-current + 4 APF agents in one launch."""
+    w = _sphere_ensemble(n_agents=12, n_apf=4, n_steps=160)
+    obs, r_O = _filtered(w)
+    obs = obs[:, :-1]   # odd N_O: odd shards take the far padding
+    ref = oracle.rollout(obs, r_O, w["agents"], w["params"], n_apf=4, n_proj=4)
+    out = gm.rollout_ensemble(_gpu_obstacles(gm, obs, r_O, cap=4096), to_dev_agents(w["agents"]),
+                              4, w["params"], tuning=shape, want_clear=clear, n_proj=4)
+    gm.sync()
+    _compare(out, ref, clear=clear)
+
+
+@pytest.mark.parametrize("n_proj", [1, 12])
+def test_projected_only_and_single(gm, n_proj):
+    w = _sphere_ensemble(n_agents=12, n_apf=0, n_steps=150)
+    obs, r_O = _filtered(w)
+    ref = oracle.rollout(obs, r_O, w["agents"], w["params"], n_proj=n_proj)
+    for shape in (None, (2, 5, 256, 0), (3, 4, 128, 1)):
+        out = gm.rollout_ensemble(_gpu_obstacles(gm, obs, r_O), to_dev_agents(w["agents"]), 0,
+                                  w["params"], tuning=shape, n_proj=n_proj)
+        gm.sync()
+        _compare(out, ref)
+
+
+def test_tabletop_three_kinds_sampled_agents(gm):
+    """256 agents x 500 steps: 86 MFI, 85 projected-current, 85 APF in the
+    library's shape; 6 of each kind checked against the oracle."""
+    import torch
+    w = synth.tabletop_workload()
+    ag = synth.ensemble_agents(w["agents"], 85)
+    xyz = torch.from_numpy(w["xyz"]).cuda()
+    gobs = gm.filter_cloud(xyz, w["T"], w["workspace"], cap=131072)
+    out = gm.rollout_ensemble(gobs, to_dev_agents(ag), 85, w["params"], n_proj=85)
+    gm.sync()
+    idx = np.r_[np.arange(0, 86, 15), np.arange(86, 171, 15), np.arange(171, 256, 15)]
+    obs, r_O = _filtered(w)
+    ref = oracle.rollout(obs, r_O, subset_agents(ag, idx), w["params"], n_apf=6, n_proj=6)
+    _compare(out, ref, idx=idx)
+
+
+def test_projected_invalid_counts(gm):
+    w = _sphere_ensemble(n_agents=4, n_apf=1, n_steps=5)
+    obs, r_O = _filtered(w)
+    o = _gpu_obstacles(gm, obs, r_O)
+    ag = to_dev_agents(w["agents"])
+    for n_proj, n_apf in ((-1, 1), (4, 1), (3, 2)):
+        with pytest.raises(gm.GmappError) as e:
+            gm.rollout_ensemble(o, ag, n_apf, w["params"], n_proj=n_proj)
+        assert e.value.status == 1
