@@ -43,6 +43,9 @@ FLOPS_PER_INTERACTION = 13      # 3 sub, 5 for |d|^2, rsqrt, mul, sub, rcp, accu
 # APF pair (Eq. apf): 3 sub, 5 for |d|^2, rsqrt, 1/rho - 1/r_d, 3 mul for the
 # coefficient, 3 accumulating FMAs (6); clamp/gate selects not counted
 APF_FLOPS_PER_INTERACTION = 19
+# projected-current MFI pair: 3 sub, 5 for |d|^2, rsqrt, 2 for s = |d|^2 r - R,
+# rcp, 5 for t = d . v, 3 mul for a = w r^2 t, 4 accumulating FMAs (8)
+PROJ_FLOPS_PER_INTERACTION = 28
 FP32_LANES_PER_SM = 128
 OBS_CAP = 131072
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "rollout_tabletop_256x500.md")
@@ -620,9 +623,11 @@ def bench_adjoint(gm, args, reps=3):
 
 def bench_ensemble(gm, args, reps=5):
     """Heterogeneous ensemble (Eq. apf + Eq. mfi) on the tabletop query:
-    256 agents x 500 steps, the last 128 on APF, in one launch; beside it the
-    plain MFI rollout of the same 256 agents and an all-APF launch, all in
-    the launch shape the autotuner picks for the MFI rollout."""
+    256 agents x 500 steps, the last 128 on APF, in one launch; beside it
+    the plain MFI rollout of the same 256 agents, an all-APF launch, an
+    all-projected-current launch and a three-kind ensemble (86 MFI, 85
+    projected, 85 APF), each in the launch shape the autotuner measures best
+    for it."""
     import torch
     import synth
     w = synth.tabletop_workload()
@@ -638,18 +643,28 @@ def bench_ensemble(gm, args, reps=5):
     mixed = dev(synth.ensemble_agents(w["agents"], n_apf))
     all_apf = dev(synth.ensemble_agents(w["agents"], na))
     mfi = dev(w["agents"])
+    n3 = na // 3   # three kinds: 86 MFI, 85 projected current, 85 APF
+    three = dev(synth.ensemble_agents(w["agents"], n3))
     out = gm.alloc_rollout_out(na, nk, want_traj=True, want_clear=False)
     shapes = {"ensemble": gm.autotune_ensemble(obs, mixed, n_apf, prm, out=out, candidates=16,
                                                probe_steps=100)[0],
               "mfi": gm.autotune_rollout(obs, mfi, prm, out=out, candidates=16, probe_steps=100)[0],
               "apf": gm.autotune_ensemble(obs, all_apf, na, prm, out=out, candidates=16,
-                                          probe_steps=100)[0]}
+                                          probe_steps=100)[0],
+              "proj": gm.autotune_ensemble(obs, mfi, 0, prm, out=out, candidates=16,
+                                           probe_steps=100, n_proj=na)[0],
+              "three_kinds": gm.autotune_ensemble(obs, three, n3, prm, out=out, candidates=16,
+                                                  probe_steps=100, n_proj=n3)[0]}
     cur = torch.cuda.current_stream()
     runs = {"ensemble": lambda: gm.rollout_ensemble(obs, mixed, n_apf, prm, out=out,
                                                     tuning=shapes["ensemble"]),
             "mfi": lambda: gm.rollout_agents(obs, mfi, prm, out=out, tuning=shapes["mfi"]),
             "apf": lambda: gm.rollout_ensemble(obs, all_apf, na, prm, out=out,
-                                               tuning=shapes["apf"])}
+                                               tuning=shapes["apf"]),
+            "proj": lambda: gm.rollout_ensemble(obs, mfi, 0, prm, out=out, tuning=shapes["proj"],
+                                                n_proj=na),
+            "three_kinds": lambda: gm.rollout_ensemble(obs, three, n3, prm, out=out,
+                                                       tuning=shapes["three_kinds"], n_proj=n3)}
     for k, fn in runs.items():   # warm-up launches, one NVTX range each (for ncu)
         torch.cuda.nvtx.range_push(f"warm_{k}")
         fn()
@@ -665,12 +680,17 @@ def bench_ensemble(gm, args, reps=5):
     flops = {"ensemble": pairs * ((na - n_apf) * FLOPS_PER_INTERACTION +
                                   n_apf * APF_FLOPS_PER_INTERACTION),
              "mfi": pairs * na * FLOPS_PER_INTERACTION,
-             "apf": pairs * na * APF_FLOPS_PER_INTERACTION}
+             "apf": pairs * na * APF_FLOPS_PER_INTERACTION,
+             "proj": pairs * na * PROJ_FLOPS_PER_INTERACTION,
+             "three_kinds": pairs * ((na - 2 * n3) * FLOPS_PER_INTERACTION +
+                                     n3 * PROJ_FLOPS_PER_INTERACTION +
+                                     n3 * APF_FLOPS_PER_INTERACTION)}
     res = {"workload": f"tabletop 640x480 -> 5 mm voxels (N_O = {n_o}); 256 agents x 500 steps; "
                        f"ensemble = last {n_apf} agents APF (gain x 1e-3), r_d alternating 5/10 cm",
            "tuning": {k: list(v) for k, v in shapes.items()}, "peak_TFLOP_per_s": peak,
            "flops_per_interaction": {"mfi": FLOPS_PER_INTERACTION,
-                                     "apf": APF_FLOPS_PER_INTERACTION}}
+                                     "apf": APF_FLOPS_PER_INTERACTION,
+                                     "proj": PROJ_FLOPS_PER_INTERACTION}}
     for k, s in times.items():
         res[k] = {"ms": 1e3 * s, "interactions_per_s": na * pairs / s,
                   "TFLOP_per_s": flops[k] / s / 1e12, "fp32_frac": flops[k] / s / 1e12 / peak}
