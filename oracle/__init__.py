@@ -7,6 +7,7 @@ generators in ``synth``.
 
 Functions (each cites the paper passage it follows):
   filter_cloud    Sec. IV-B / V-A   camera cloud -> sorted voxel centres S_W
+  filter_clouds   Sec. IV-B         several sensors' clouds fused into one S_W
   cf_eval         Eq. (mfi), Alg. 1 W, clearance and f_r at given states
   apf_eval        Eq. (apf)         APF force and clearance at given states
   rollout         Sec. IV-A         N_k-step point-mass rollout + cost sums
@@ -38,6 +39,9 @@ def lib():
         _lib.oracle_filter.restype = i64
         _lib.oracle_filter.argtypes = [P, i64, P, P, C.c_float, P, C.c_int32, i64,
                                        P, P, P, P, P, P]
+        _lib.oracle_filter_fused.restype = i64
+        _lib.oracle_filter_fused.argtypes = [P, P, P, C.c_int32, P, C.c_float, P, C.c_int32, i64,
+                                             P, P, P, P, P, P]
         _lib.oracle_cf_eval.restype = None
         _lib.oracle_cf_eval.argtypes = [i64, P, P, P, C.c_double, i64, P, P, P, P, P, P,
                                         C.c_double, C.c_double, P, P, P]
@@ -118,6 +122,30 @@ def filter_cloud(xyz: np.ndarray, T, workspace, cap: int | None = None) -> dict:
     k = min(n_out, cap)
     return {"n": int(n_out), "keys": keys[:k], "counts": counts[:k], "rep_idx": rep[:k],
             "x": cx[:k], "y": cy[:k], "z": cz[:k],
+            "r_O": float(np.float32(workspace.voxel) * np.float32(0.5))}
+
+
+def filter_clouds(clouds, workspace, cap: int | None = None) -> dict:
+    """Several sensors' clouds [(xyz, T), ...] fused into one obstacle set
+    (Sec. IV-B); point i of cloud s has the index n_0 + ... + n_{s-1} + i."""
+    xyzs = [np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 3) for x, _ in clouds]
+    ns = np.array([x.shape[0] for x in xyzs], dtype=np.int64)
+    xyz = np.ascontiguousarray(np.concatenate(xyzs, axis=0) if xyzs else np.zeros((0, 3), np.float32))
+    T = np.ascontiguousarray(np.stack([np.asarray(t, np.float32).reshape(12) for _, t in clouds]))
+    lo = np.ascontiguousarray(workspace.lo, dtype=np.float32)
+    dims = np.ascontiguousarray(workspace.dims, dtype=np.int32)
+    n = int(ns.sum())
+    cap = n if cap is None else int(cap)
+    out = {k: np.zeros(max(cap, 1), np.uint32) for k in ("keys", "counts", "rep_idx")}
+    cs = [np.zeros(max(cap, 1), np.float32) for _ in range(3)]
+    n_out = lib().oracle_filter_fused(_ptr(xyz), _ptr(ns), _ptr(T), len(clouds), _ptr(lo),
+                                      float(np.float32(workspace.voxel)), _ptr(dims),
+                                      int(workspace.min_pts), cap, _ptr(out["keys"]),
+                                      _ptr(out["counts"]), _ptr(out["rep_idx"]), _ptr(cs[0]),
+                                      _ptr(cs[1]), _ptr(cs[2]))
+    k = min(n_out, cap)
+    return {"n": int(n_out), "keys": out["keys"][:k], "counts": out["counts"][:k],
+            "rep_idx": out["rep_idx"][:k], "x": cs[0][:k], "y": cs[1][:k], "z": cs[2][:k],
             "r_O": float(np.float32(workspace.voxel) * np.float32(0.5))}
 
 

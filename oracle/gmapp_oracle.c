@@ -66,13 +66,12 @@ static int cmp_key_idx(const void *a, const void *b)
  * the number of points and the smallest original point index per voxel.
  * Returns the number of kept voxels; only the first `cap` are written.
  */
-int64_t oracle_filter(const float *xyz, int64_t n_raw, const float *T,
-                      const float *lo, float voxel, const int32_t *dims,
-                      int32_t min_pts, int64_t cap, uint32_t *keys,
-                      uint32_t *counts, uint32_t *rep_idx, float *cx,
-                      float *cy, float *cz)
+
+/* Append (key, idx0 + i) of every kept point of one cloud to kv; returns the
+ * number appended. */
+static int64_t collect_keys(const float *xyz, int64_t n_raw, const float *T, const float *lo,
+                            float voxel, const int32_t *dims, uint32_t idx0, key_idx *kv)
 {
-    key_idx *kv = (key_idx *)malloc((size_t)(n_raw > 0 ? n_raw : 1) * sizeof(key_idx));
     int64_t m = 0;
     for (int64_t i = 0; i < n_raw; ++i) {
         float x = xyz[3 * i + 0], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
@@ -92,11 +91,18 @@ int64_t oracle_filter(const float *xyz, int64_t n_raw, const float *T,
         uint64_t key = ((uint64_t)ix[2] * (uint64_t)dims[1] + (uint64_t)ix[1]) * (uint64_t)dims[0]
                        + (uint64_t)ix[0];
         kv[m].key = (uint32_t)key;
-        kv[m].idx = (uint32_t)i;
+        kv[m].idx = idx0 + (uint32_t)i;
         ++m;
     }
-    qsort(kv, (size_t)m, sizeof(key_idx), cmp_key_idx);
+    return m;
+}
 
+/* Sort the m (key, index) pairs and emit the voxels with >= min_pts points. */
+static int64_t group_voxels(key_idx *kv, int64_t m, const float *lo, float voxel,
+                            const int32_t *dims, int32_t min_pts, int64_t cap, uint32_t *keys,
+                            uint32_t *counts, uint32_t *rep_idx, float *cx, float *cy, float *cz)
+{
+    qsort(kv, (size_t)m, sizeof(key_idx), cmp_key_idx);
     int64_t n_out = 0;
     int64_t r = 0;
     while (r < m) {
@@ -120,6 +126,48 @@ int64_t oracle_filter(const float *xyz, int64_t n_raw, const float *T,
         }
         r = e;
     }
+    return n_out;
+}
+
+int64_t oracle_filter(const float *xyz, int64_t n_raw, const float *T,
+                      const float *lo, float voxel, const int32_t *dims,
+                      int32_t min_pts, int64_t cap, uint32_t *keys,
+                      uint32_t *counts, uint32_t *rep_idx, float *cx,
+                      float *cy, float *cz)
+{
+    key_idx *kv = (key_idx *)malloc((size_t)(n_raw > 0 ? n_raw : 1) * sizeof(key_idx));
+    int64_t m = collect_keys(xyz, n_raw, T, lo, voxel, dims, 0u, kv);
+    int64_t n_out = group_voxels(kv, m, lo, voxel, dims, min_pts, cap, keys, counts, rep_idx,
+                                 cx, cy, cz);
+    free(kv);
+    return n_out;
+}
+
+/*
+ * Several sensors into one obstacle set (Sec. IV-B: the clouds of N_S
+ * sensors, each with its own camera-to-world transform, fused into one
+ * voxel grid).  xyz holds the clouds one after another ([sum n_s][3]); point
+ * i of sensor s has the index offset_s + i (offset_s = n_0 + ... + n_{s-1}),
+ * so a voxel's smallest index is taken over all sensors.  T holds one 3x4
+ * transform per sensor ([n_sensors][12]).  Everything else as oracle_filter.
+ */
+int64_t oracle_filter_fused(const float *xyz, const int64_t *n_s, const float *T,
+                            int32_t n_sensors, const float *lo, float voxel,
+                            const int32_t *dims, int32_t min_pts, int64_t cap,
+                            uint32_t *keys, uint32_t *counts, uint32_t *rep_idx, float *cx,
+                            float *cy, float *cz)
+{
+    int64_t total = 0;
+    for (int32_t s = 0; s < n_sensors; ++s) total += n_s[s];
+    key_idx *kv = (key_idx *)malloc((size_t)(total > 0 ? total : 1) * sizeof(key_idx));
+    int64_t m = 0, off = 0;
+    for (int32_t s = 0; s < n_sensors; ++s) {
+        m += collect_keys(xyz + 3 * off, n_s[s], T + 12 * s, lo, voxel, dims, (uint32_t)off,
+                          kv + m);
+        off += n_s[s];
+    }
+    int64_t n_out = group_voxels(kv, m, lo, voxel, dims, min_pts, cap, keys, counts, rep_idx,
+                                 cx, cy, cz);
     free(kv);
     return n_out;
 }

@@ -22,4 +22,5 @@ from .workloads import (  # noqa: F401
     adjoint_workload,
     serve_stream,
     ensemble_agents,
+    multi_sensor_frames,
 )

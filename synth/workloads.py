@@ -153,6 +153,28 @@ def ensemble_agents(agents: dict, n_apf: int, apf_gain: float = APF_GAIN,
     return ag
 
 
+# Depth cameras of the multi-sensor frames (the paper's real-world runs use
+# two RealSense cameras at 848x480); all look at the table centre.
+SENSOR_POSITIONS = ((0.5, -0.4, 1.2), (0.5, 0.45, 1.1), (-0.3, 0.0, 1.0))
+
+
+def multi_sensor_frames(seed: int = 1006, n_sensors: int = 2, width: int = 848,
+                        height: int = 480, fx: float = 425.0, n_points: int | None = None) -> dict:
+    """The tabletop scene seen by ``n_sensors`` depth cameras at once: one
+    organised cloud per sensor in its own camera frame with its
+    camera-to-world transform, 2 mm depth noise and 5% dropouts each."""
+    subs = _sub_seeds(seed, 1 + n_sensors)
+    scene = tabletop_scene(subs[0])
+    clouds = []
+    for s in range(n_sensors):
+        xyz, T = render_depth_frame(scene, subs[1 + s], width=width, height=height, fx=fx, fy=fx,
+                                    cx=(width - 1) / 2.0, cy=(height - 1) / 2.0,
+                                    cam_position=SENSOR_POSITIONS[s % len(SENSOR_POSITIONS)],
+                                    n_points=n_points)
+        clouds.append((xyz, T))
+    return {"clouds": clouds, "workspace": TABLE_WS, "scene": scene}
+
+
 def batch_workloads(seed: int = 1003, n_scenes: int = 64) -> list:
     """64 uneven sphere-cloud queries: raw points log-uniform in [5k, 300k],
     voxel U[4, 10] mm, agents log-uniform in {32..1024}, steps U{100..1000}."""

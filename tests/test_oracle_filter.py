@@ -144,3 +144,47 @@ def test_empty_and_all_rejected():
     assert oracle.filter_cloud(np.zeros((0, 3), np.float32), T, ws)["n"] == 0
     far = np.full((50, 3), 5.0, np.float32)
     assert oracle.filter_cloud(far, T, ws)["n"] == 0
+
+
+# ---- several sensors fused into one obstacle set (Sec. IV-B) --------------
+
+def _ws_small():
+    return synth.Workspace(lo=(0.0, -0.5, -0.02), voxel=0.01, dims=(100, 100, 80))
+
+
+def test_fusion_of_one_sensor_is_the_single_filter():
+    m = synth.multi_sensor_frames(n_sensors=1, n_points=20000)
+    xyz, T = m["clouds"][0]
+    a = oracle.filter_clouds(m["clouds"], _ws_small())
+    b = oracle.filter_cloud(xyz, T, _ws_small())
+    for k in ("keys", "counts", "rep_idx", "x", "y", "z"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_fusion_with_identity_transforms_is_the_concatenated_cloud():
+    g = np.random.Generator(np.random.PCG64(4))
+    c1 = g.uniform([0, -0.5, 0], [1, 0.5, 0.8], (3001, 3)).astype(np.float32)
+    c2 = g.uniform([0.2, -0.2, 0], [0.6, 0.3, 0.5], (1999, 3)).astype(np.float32)
+    I = synth.workloads.IDENTITY_T
+    a = oracle.filter_clouds([(c1, I), (c2, I)], _ws_small())
+    b = oracle.filter_cloud(np.concatenate([c1, c2]), I, _ws_small())
+    for k in ("keys", "counts", "rep_idx", "x", "y", "z"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_fusion_is_the_union_with_summed_counts_and_global_indices():
+    m = synth.multi_sensor_frames(n_sensors=3, n_points=30000)
+    ws = _ws_small()
+    fused = oracle.filter_clouds(m["clouds"], ws)
+    singles = [oracle.filter_cloud(x, T, ws) for x, T in m["clouds"]]
+    offsets = np.cumsum([0] + [x.shape[0] for x, _ in m["clouds"]])[:-1]
+    count, rep = {}, {}
+    for s, f in enumerate(singles):
+        for k, c, r in zip(f["keys"], f["counts"], f["rep_idx"]):
+            count[int(k)] = count.get(int(k), 0) + int(c)
+            rep[int(k)] = min(rep.get(int(k), 1 << 40), int(r) + int(offsets[s]))
+    keys = np.array(sorted(count), dtype=np.uint32)
+    assert np.array_equal(fused["keys"], keys)
+    assert np.array_equal(fused["counts"], np.array([count[int(k)] for k in keys], np.uint32))
+    assert np.array_equal(fused["rep_idx"], np.array([rep[int(k)] for k in keys], np.uint32))
+    assert len(set(singles[0]["keys"].tolist()) & set(singles[1]["keys"].tolist())) > 100
