@@ -179,6 +179,32 @@ void gmapp_filter_batch_destroy(gmapp_filter_batch *fb);
  * GMAPP_DEVERR_CAPACITY and its out.n > out.cap. */
 gmapp_status filter_cloud_batch(gmapp_filter_batch *fb, gmapp_stream stream);
 
+/* One sensor's cloud for filter_clouds. */
+typedef struct {
+    const float *xyz; /* device, n_raw x 3 float32 AoS in the sensor's camera frame,
+                         16-byte aligned */
+    int64_t n_raw;    /* points (>= 0) */
+    float T[12];      /* camera -> world, row-major 3x4 [R | t] */
+} gmapp_sensor_cloud;
+
+/* Workspace bytes filter_clouds needs for these clouds (0 when invalid). */
+size_t gmapp_filter_clouds_workspace_bytes(const gmapp_sensor_cloud *clouds, int32_t n_sensors,
+                                           const gmapp_workspace *ws);
+
+/* Several sensors fused into one obstacle set (Sec. IV-B: the clouds of N_S
+ * depth sensors, each with its own camera-to-world transform, voxelised
+ * into one grid).  Every point of every sensor goes through the exact
+ * binary32 sequence of filter_cloud with its sensor's T; a voxel is occupied
+ * when any sensor's point falls in it; counts add over the sensors and the
+ * smallest index is taken over all of them, point i of sensor s having the
+ * index n_0 + ... + n_{s-1} + i (the clouds' concatenation).  clouds: host
+ * array [n_sensors] (n_sensors >= 1; n_sensors = 1 is filter_cloud).  Sum of
+ * n_raw below 2^32 - 1.  Output, workspace (gmapp_filter_clouds_workspace_
+ * bytes) and errors as filter_cloud. */
+gmapp_status filter_clouds(gmapp_ctx *ctx, const gmapp_sensor_cloud *clouds, int32_t n_sensors,
+                           const gmapp_workspace *ws, gmapp_obstacles *out, void *workspace,
+                           size_t workspace_bytes, gmapp_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* Rollout: rollout_agents (Sec. IV-A agent dynamics and agent set;           */
 /* Eq. (mfi) circular-field force; Alg. 1 clamp, detection gate, sum)         */

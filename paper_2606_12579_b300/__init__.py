@@ -20,7 +20,8 @@ from dataclasses import dataclass
 from . import _abi
 from ._abi import check
 
-__all__ = ["Context", "context", "Obstacles", "filter_cloud", "filter_cloud_noalloc",
+__all__ = ["Context", "context", "Obstacles", "filter_cloud", "filter_clouds",
+           "filter_cloud_noalloc",
            "filter_workspace_bytes", "rollout_agents", "rollout_ensemble", "score_and_select",
            "score_and_select4",
            "pick_tuning", "autotune_rollout", "autotune_ensemble", "rollout_adjoint", "GMappRollout", "sync", "GmappError",
@@ -187,6 +188,35 @@ def filter_cloud(xyz, T, ws, out: Obstacles | None = None, cap: int | None = Non
     check(_abi.load().filter_cloud(ctx.handle, _ptr(xyz), n, C.byref(Tc), C.byref(wss),
                                    C.byref(ob), _ptr(workspace), int(workspace.numel()),
                                    _stream(stream)), "filter_cloud")
+    out.r_O = float(ob.r_O)
+    return out
+
+
+def filter_clouds(clouds, ws, out: Obstacles | None = None, cap: int | None = None,
+                  workspace=None, stream=None) -> Obstacles:
+    """Several sensors fused into one S_W (Sec. IV-B): ``clouds`` is a list
+    of (xyz [N_s, 3] float32 device tensor, T 12 numbers) pairs; point i of
+    sensor s has the index N_0 + ... + N_{s-1} + i."""
+    torch = _torch()
+    ctx = context()
+    arr = (_abi.SensorCloud * len(clouds))()
+    for s, (xyz, T) in enumerate(clouds):
+        arr[s].xyz = xyz.data_ptr() if xyz.numel() else None
+        arr[s].n_raw = int(xyz.shape[0])
+        for i, v in enumerate(list(T)):
+            arr[s].T[i] = float(v)
+    total = sum(int(x.shape[0]) for x, _ in clouds)
+    if out is None:
+        out = Obstacles.empty(cap if cap is not None else max(total, 4))
+    wss = _ws_struct(ws)
+    lib = _abi.load()
+    need = int(lib.gmapp_filter_clouds_workspace_bytes(arr, len(clouds), C.byref(wss)))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=out.x.device)
+    ob = out._struct()
+    check(lib.filter_clouds(ctx.handle, arr, len(clouds), C.byref(wss), C.byref(ob),
+                            _ptr(workspace), int(workspace.numel()), _stream(stream)),
+          "filter_clouds")
     out.r_O = float(ob.r_O)
     return out
 

@@ -29,6 +29,10 @@ class Obstacles(C.Structure):
                 ("n", P), ("cap", C.c_int64), ("r_O", C.c_float)]
 
 
+class SensorCloud(C.Structure):
+    _fields_ = [("xyz", P), ("n_raw", C.c_int64), ("T", C.c_float * 12)]
+
+
 class CloudJob(C.Structure):
     _fields_ = [("xyz", P), ("n_raw", C.c_int64), ("T", C.c_float * 12), ("ws", Workspace),
                 ("out", Obstacles)]
@@ -111,6 +115,10 @@ PROTOTYPES = {
     "gmapp_filter_workspace_bytes": (C.c_size_t, [C.c_int64, C.POINTER(Workspace)]),
     "filter_cloud": (C.c_int, [P, P, C.c_int64, C.POINTER(C.c_float * 12), C.POINTER(Workspace),
                                C.POINTER(Obstacles), P, C.c_size_t, P]),
+    "gmapp_filter_clouds_workspace_bytes": (C.c_size_t, [C.POINTER(SensorCloud), C.c_int32,
+                                                         C.POINTER(Workspace)]),
+    "filter_clouds": (C.c_int, [P, C.POINTER(SensorCloud), C.c_int32, C.POINTER(Workspace),
+                                C.POINTER(Obstacles), P, C.c_size_t, P]),
     "filter_cloud_noalloc": (C.c_int, [P, C.c_int64, C.POINTER(C.c_float * 12),
                                        C.POINTER(Workspace), C.POINTER(Obstacles), P]),
     "rollout_agents": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),

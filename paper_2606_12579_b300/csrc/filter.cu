@@ -30,44 +30,69 @@ extern "C" size_t gmapp_filter_workspace_bytes(int64_t n_raw, const gmapp_worksp
     return layout(n_raw, ws).total;
 }
 
-extern "C" gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n_raw,
-                                     const float T[12], const gmapp_workspace *ws,
-                                     gmapp_obstacles *out, void *workspace,
-                                     size_t workspace_bytes, gmapp_stream stream) {
-    if (!ctx || !T || !out || !workspace) {
-        set_error("filter_cloud: NULL ctx, T, out or workspace");
+namespace {
+
+// Key slots of the sensors in the workspace's key array: sensor s starts at
+// the sum of the earlier clouds rounded up to 4 (16-byte aligned stores).
+int64_t key_slots(const gmapp_sensor_cloud *clouds, int32_t n_sensors) {
+    int64_t tot = 0;
+    for (int32_t s = 0; s < n_sensors; ++s) tot += (clouds[s].n_raw + 3) & ~int64_t(3);
+    return tot;
+}
+
+// filter_cloud / filter_clouds: every sensor's points set bits in one bitmap
+// (k_keys with its own transform) and are counted with their global index
+// (k_count with the sensor's index base); bitmap sums and emit run once.
+gmapp_status filter_impl(const char *who, gmapp_ctx *ctx, const gmapp_sensor_cloud *clouds,
+                         int32_t n_sensors, const gmapp_workspace *ws, gmapp_obstacles *out,
+                         void *workspace, size_t workspace_bytes, gmapp_stream stream) {
+    if (!ctx || !clouds || n_sensors < 1 || !out || !workspace) {
+        set_error("%s: NULL ctx, clouds, out or workspace, or no sensor", who);
         return GMAPP_ERR_INVALID_ARG;
     }
-    if (n_raw < 0 || n_raw >= 0xFFFFFFFFll || (n_raw > 0 && !xyz)) {
-        set_error("filter_cloud: n_raw %lld out of range or xyz NULL", (long long)n_raw);
+    int64_t total = 0;
+    for (int32_t s = 0; s < n_sensors; ++s) {
+        const gmapp_sensor_cloud &c = clouds[s];
+        if (c.n_raw < 0 || c.n_raw >= 0xFFFFFFFFll || (c.n_raw > 0 && !c.xyz)) {
+            set_error("%s: n_raw %lld of sensor %d out of range or xyz NULL", who,
+                      (long long)c.n_raw, s);
+            return GMAPP_ERR_INVALID_ARG;
+        }
+        if (reinterpret_cast<uintptr_t>(c.xyz) % 16) {
+            set_error("%s: xyz of sensor %d must be 16-byte aligned", who, s);
+            return GMAPP_ERR_INVALID_ARG;
+        }
+        for (int i = 0; i < 12; ++i)
+            if (!isfinite(c.T[i])) {
+                set_error("%s: transform entry %d of sensor %d is not finite", who, i, s);
+                return GMAPP_ERR_INVALID_ARG;
+            }
+        total += c.n_raw;
+    }
+    if (total >= 0xFFFFFFFFll) {
+        set_error("%s: %lld points in all, at most 2^32 - 2", who, (long long)total);
         return GMAPP_ERR_INVALID_ARG;
     }
     if (!valid_workspace(ws)) {
-        set_error("filter_cloud: invalid workspace grid (voxel > 0, 1 <= dims <= 2^24, "
-                  "cells < 2^32-1, min_pts >= 1)");
+        set_error("%s: invalid workspace grid (voxel > 0, 1 <= dims <= 2^24, "
+                  "cells < 2^32-1, min_pts >= 1)", who);
         return GMAPP_ERR_INVALID_ARG;
     }
-    if (reinterpret_cast<uintptr_t>(xyz) % 16 || reinterpret_cast<uintptr_t>(workspace) % 256) {
-        set_error("filter_cloud: xyz must be 16-byte and workspace 256-byte aligned");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256) {
+        set_error("%s: workspace must be 256-byte aligned", who);
         return GMAPP_ERR_INVALID_ARG;
     }
     if (!out->x || !out->y || !out->z || !out->keys || !out->counts || !out->rep_idx || !out->n ||
         out->cap < 0) {
-        set_error("filter_cloud: output buffers must all be set and cap >= 0");
+        set_error("%s: output buffers must all be set and cap >= 0", who);
         return GMAPP_ERR_INVALID_ARG;
     }
-    for (int i = 0; i < 12; ++i)
-        if (!isfinite(T[i])) {
-            set_error("filter_cloud: transform entry %d is not finite", i);
-            return GMAPP_ERR_INVALID_ARG;
-        }
-    Layout L = layout(n_raw, ws);
+    Layout L = layout(key_slots(clouds, n_sensors), ws);
     if (workspace_bytes < L.total) {
-        set_error("filter_cloud: workspace of %zu bytes, %zu needed", workspace_bytes, L.total);
+        set_error("%s: workspace of %zu bytes, %zu needed", who, workspace_bytes, L.total);
         return GMAPP_ERR_CAPACITY;
     }
     FilterArgs A;
-    for (int i = 0; i < 12; ++i) A.T[i] = T[i];
     for (int a = 0; a < 3; ++a) {
         A.lo[a] = ws->lo[a];
         A.dimf[a] = static_cast<float>(ws->dims[a]);
@@ -89,22 +114,41 @@ extern "C" gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n
     uint32_t *n_occ = counters + 1;
     uint32_t *n_keep_counter = counters + 2;
 
-    const int grid_pts = static_cast<int>(std::max<int64_t>(
-        1, std::min<int64_t>((n_raw / 4 + kThreads - 1) / kThreads, (int64_t)ctx->sm_count * 8)));
+    auto grid_for = [&](int64_t n) {
+        return static_cast<int>(std::max<int64_t>(
+            1, std::min<int64_t>((n / 4 + kThreads - 1) / kThreads, (int64_t)ctx->sm_count * 8)));
+    };
     const int grid_zero = static_cast<int>(
         std::min<int64_t>((L.n_words / 4 + kThreads - 1) / kThreads, (int64_t)ctx->sm_count * 8));
 
     k_zero<<<grid_zero, kThreads, 0, stream>>>(reinterpret_cast<uint4 *>(bitmap), L.n_words / 4,
                                                counters, 16);
-    k_keys<<<grid_pts, kThreads, 0, stream>>>(xyz, n_raw, A, keys, bitmap);
+    {
+        int64_t slot = 0;
+        for (int32_t s = 0; s < n_sensors; ++s) {
+            for (int i = 0; i < 12; ++i) A.T[i] = clouds[s].T[i];
+            k_keys<<<grid_for(clouds[s].n_raw), kThreads, 0, stream>>>(
+                clouds[s].xyz, clouds[s].n_raw, A, keys + slot, bitmap);
+            slot += (clouds[s].n_raw + 3) & ~int64_t(3);
+        }
+    }
     k_bitmap_sums<<<static_cast<int>(L.n_sblocks), kBmThreads, 0, stream>>>(bitmap, chunk, sums, offsets,
                                                                           counters, n_occ);
+    // per-sensor counts: points of sensor s carry the indices idx0 + i
+    auto count_all = [&](uint32_t *cnt, uint32_t *rep, int64_t cap) {
+        int64_t slot = 0, idx0 = 0;
+        for (int32_t s = 0; s < n_sensors; ++s) {
+            k_count<<<grid_for(clouds[s].n_raw), kThreads, 0, stream>>>(
+                keys + slot, clouds[s].n_raw, pw, cnt, rep, cap, static_cast<uint32_t>(idx0));
+            slot += (clouds[s].n_raw + 3) & ~int64_t(3);
+            idx0 += clouds[s].n_raw;
+        }
+    };
     if (ws->min_pts == 1) {
         EmitOut o{out->keys, out->counts, out->rep_idx, out->x, out->y, out->z, out->cap};
         k_emit<<<static_cast<int>(L.n_words / kBmThreads), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, o,
                                                                       n_occ, out->n, ctx->d_err);
-        k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, pw, out->counts,
-                                                   out->rep_idx, out->cap);
+        count_all(out->counts, out->rep_idx, out->cap);
     } else {
         uint32_t *tkeys = reinterpret_cast<uint32_t *>(base + L.off_tkeys);
         uint32_t *tcounts = reinterpret_cast<uint32_t *>(base + L.off_tcounts);
@@ -114,8 +158,7 @@ extern "C" gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n
         EmitOut t{tkeys, tcounts, trep, nullptr, nullptr, nullptr, L.n_tmp};
         k_emit<<<static_cast<int>(L.n_words / kBmThreads), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, t,
                                                                       nullptr, nullptr, nullptr);
-        k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, pw, tcounts, trep,
-                                                   L.n_tmp);
+        count_all(tcounts, trep, L.n_tmp);
         k_keep_sums<<<static_cast<int>(L.n_tblocks), kThreads, 0, stream>>>(
             tcounts, n_occ, ws->min_pts, tsums, toffsets, n_keep_counter, out->n, out->cap,
             ctx->d_err);
@@ -125,6 +168,40 @@ extern "C" gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n
     }
     GMAPP_CHECK_CUDA(cudaGetLastError());
     return GMAPP_OK;
+}
+
+}  // namespace
+
+extern "C" gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n_raw,
+                                     const float T[12], const gmapp_workspace *ws,
+                                     gmapp_obstacles *out, void *workspace,
+                                     size_t workspace_bytes, gmapp_stream stream) {
+    if (!T) {
+        set_error("filter_cloud: NULL T");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    gmapp_sensor_cloud c;
+    c.xyz = xyz;
+    c.n_raw = n_raw;
+    for (int i = 0; i < 12; ++i) c.T[i] = T[i];
+    return filter_impl("filter_cloud", ctx, &c, 1, ws, out, workspace, workspace_bytes, stream);
+}
+
+extern "C" size_t gmapp_filter_clouds_workspace_bytes(const gmapp_sensor_cloud *clouds,
+                                                      int32_t n_sensors,
+                                                      const gmapp_workspace *ws) {
+    if (!clouds || n_sensors < 1 || !valid_workspace(ws)) return 0;
+    for (int32_t s = 0; s < n_sensors; ++s)
+        if (clouds[s].n_raw < 0) return 0;
+    return layout(key_slots(clouds, n_sensors), ws).total;
+}
+
+extern "C" gmapp_status filter_clouds(gmapp_ctx *ctx, const gmapp_sensor_cloud *clouds,
+                                      int32_t n_sensors, const gmapp_workspace *ws,
+                                      gmapp_obstacles *out, void *workspace,
+                                      size_t workspace_bytes, gmapp_stream stream) {
+    return filter_impl("filter_clouds", ctx, clouds, n_sensors, ws, out, workspace,
+                       workspace_bytes, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -265,7 +342,7 @@ extern "C" gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, co
         k_emit<<<static_cast<int>(L.n_words / kBmThreads), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, o,
                                                                       n_occ, out->n, sym.err);
         k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, pw, out->counts,
-                                                   out->rep_idx, out->cap);
+                                                   out->rep_idx, out->cap, 0u);
     } else {
         uint32_t *tkeys = reinterpret_cast<uint32_t *>(base + L.off_tkeys);
         uint32_t *tcounts = reinterpret_cast<uint32_t *>(base + L.off_tcounts);
@@ -276,7 +353,7 @@ extern "C" gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, co
         k_emit<<<static_cast<int>(L.n_words / kBmThreads), kBmThreads, 0, stream>>>(bitmap, offsets, chunk, pw, A, t,
                                                                       nullptr, nullptr, nullptr);
         k_count<<<grid_pts, kThreads, 0, stream>>>(keys, n_raw, pw, tcounts, trep,
-                                                   L.n_tmp);
+                                                   L.n_tmp, 0u);
         k_keep_sums<<<static_cast<int>(L.n_tblocks), kThreads, 0, stream>>>(
             tcounts, n_occ, ws->min_pts, tsums, toffsets, n_keep_counter, out->n, out->cap,
             sym.err);

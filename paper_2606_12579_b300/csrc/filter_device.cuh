@@ -371,17 +371,19 @@ __device__ __forceinline__ uint32_t rank_of(uint32_t key, const uint2 *pw, int64
     return r < cap ? r : kInvalid;
 }
 
+// Point t of the range has the index idx0 + t (several sensors share one
+// index space).
 __device__ __forceinline__ void count_range(const uint32_t *__restrict__ keys, int64_t n,
                                             const uint2 *__restrict__ pw, uint32_t *counts,
                                             uint32_t *rep, int64_t cap, int64_t blk,
-                                            int64_t nblk) {
+                                            int64_t nblk, uint32_t idx0 = 0) {
     const int64_t n4 = n / 4;
     const int64_t stride = nblk * (int64_t)kThreads;
 #pragma unroll 2
     for (int64_t g = blk * (int64_t)kThreads + threadIdx.x; g < n4; g += stride) {
         uint4 k = __ldcs(reinterpret_cast<const uint4 *>(keys) + g);
         RankMerge m;
-        uint32_t i0 = static_cast<uint32_t>(4 * g);
+        uint32_t i0 = idx0 + static_cast<uint32_t>(4 * g);
         uint32_t r;
         if ((r = rank_of(k.x, pw, cap)) != kInvalid) m.add(r, i0, counts, rep);
         if ((r = rank_of(k.y, pw, cap)) != kInvalid) m.add(r, i0 + 1, counts, rep);
@@ -394,15 +396,15 @@ __device__ __forceinline__ void count_range(const uint32_t *__restrict__ keys, i
         uint32_t r = rank_of(keys[t], pw, cap);
         if (r != kInvalid) {
             atomicAdd(&counts[r], 1u);
-            atomicMin(&rep[r], static_cast<uint32_t>(t));
+            atomicMin(&rep[r], idx0 + static_cast<uint32_t>(t));
         }
     }
 }
 
 __global__ void __launch_bounds__(kThreads) k_count(const uint32_t *__restrict__ keys, int64_t n,
                                                     const uint2 *__restrict__ pw, uint32_t *counts,
-                                                    uint32_t *rep, int64_t cap) {
-    count_range(keys, n, pw, counts, rep, cap, blockIdx.x, gridDim.x);
+                                                    uint32_t *rep, int64_t cap, uint32_t idx0) {
+    count_range(keys, n, pw, counts, rep, cap, blockIdx.x, gridDim.x, idx0);
 }
 
 // min_pts > 1: per block of 1024 temporary entries, how many pass; last
