@@ -533,7 +533,54 @@ def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8):
     for ns in (n_streams, 1):
         res[f"per_frame_streams_{ns}"] = entry(run(ns))
     gm.sync()
+    del batches, frames
+    torch.cuda.empty_cache()
+    res["fused_2_sensors"] = bench_fused(gm)
     return res
+
+
+def bench_fused(gm, n_sets=24, reps=3):
+    """filter_clouds: two 848x480 depth cameras fused into one obstacle set
+    per call (Sec. IV-B), over a ring of n_sets distinct frame pairs resident
+    in HBM (larger than L2); algorithmic bytes = 12 B per raw point + 24 B per
+    obstacle."""
+    import torch
+    import synth
+    sets = []
+    n_obs = []
+    for s in range(n_sets):
+        m = synth.multi_sensor_frames(seed=9_000_000 + s, n_sensors=2)
+        sets.append([(torch.from_numpy(x).cuda(), T) for x, T in m["clouds"]])
+    ws = m["workspace"]
+    out = gm.Obstacles.empty(262144)
+    wsp = None
+    for c in sets:
+        gm.filter_clouds(c, ws, out=out)
+        n_obs.append(out.count())
+    need = sum(int(x.shape[0]) for x, _ in sets[0]) + 8
+    wsp = torch.empty(int(gm.filter_workspace_bytes(need, ws)), dtype=torch.uint8, device="cuda")
+    cur = torch.cuda.current_stream()
+    for c in sets[:3]:
+        gm.filter_clouds(c, ws, out=out, workspace=wsp)
+    gm.sync()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for c in sets:
+            gm.filter_clouds(c, ws, out=out, workspace=wsp)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / n_sets
+        best = t if best is None else min(best, t)
+    n_raw = sum(int(x.shape[0]) for x, _ in sets[0])
+    byts = 12 * n_raw + 24 * float(np.mean(n_obs))
+    peak = _measured_peaks().get("hbm_gbs")
+    return {"workload": f"2 sensors x 848x480 ({n_raw} points), 5 mm voxels, {n_sets} distinct "
+                        f"pairs ({n_sets * n_raw * 12 / 1e6:.0f} MB)",
+            "n_obs_mean": float(np.mean(n_obs)), "us_per_call": 1e6 * best,
+            "GB_per_s": byts / best / 1e9, "hbm_frac": byts / best / 1e9 / peak if peak else None,
+            "launches_per_call": 7}
 
 
 def bench_batched(gm, args, reps=3):

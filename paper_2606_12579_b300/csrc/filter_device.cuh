@@ -38,9 +38,30 @@ struct FilterArgs {
     uint32_t nx, ny, nz;
 };
 
+// The correctly rounded quotient x / voxel from the correctly rounded
+// reciprocal y = RN(1 / voxel) by Markstein's theorem (P. Markstein,
+// "Computation of elementary functions on the IBM RISC System/6000
+// processor", IBM J. Res. Dev. 34(1), 1990): when q is within one ulp of
+// x / voxel, r = x - q voxel is exact (one FMA) and RN(q + r y) = RN(x /
+// voxel).  q0 = RN(x y) may be up to 1.5 ulp off (the errors of y and of
+// the product add), so one correction first makes it faithful (error
+// below 1/2 ulp plus a few units of 2^-46) and a second one, now under the
+// theorem, rounds correctly: one multiply and four FMAs.  Outside the
+// normal range (a quotient that overflows becomes NaN, a subnormal one may
+// differ in its last bit) the crop and floor decisions are those of the
+// IEEE quotient: an overflowing quotient lies beyond the grid, a tiny one
+// floors to 0 with its sign kept.
+__device__ __forceinline__ float voxel_quotient(float x, float voxel, float y) {
+    const float q0 = __fmul_rn(x, y);
+    const float q1 = __fmaf_rn(__fmaf_rn(-q0, voxel, x), y, q0);
+    return __fmaf_rn(__fmaf_rn(-q1, voxel, x), y, q1);
+}
+
 // One point -> its linear voxel key, or kInvalid.  Exact binary32 sequence,
-// no contraction: w = ((T0 x + T1 y) + T2 z) + T3; q = (w - lo) / voxel.
-__device__ __forceinline__ uint32_t voxel_key(float x, float y, float z, const FilterArgs &A) {
+// no contraction: w = ((T0 x + T1 y) + T2 z) + T3; q = RN((w - lo) / voxel);
+// inv_voxel = RN(1 / voxel).
+__device__ __forceinline__ uint32_t voxel_key(float x, float y, float z, const FilterArgs &A,
+                                              float inv_voxel) {
     if (!(isfinite(x) && isfinite(y) && isfinite(z))) return kInvalid;
     uint32_t idx[3];
 #pragma unroll
@@ -49,7 +70,7 @@ __device__ __forceinline__ uint32_t voxel_key(float x, float y, float z, const F
         float t1 = __fmul_rn(A.T[4 * a + 1], y);
         float t2 = __fmul_rn(A.T[4 * a + 2], z);
         float w = __fadd_rn(__fadd_rn(__fadd_rn(t0, t1), t2), A.T[4 * a + 3]);
-        float q = __fdiv_rn(__fsub_rn(w, A.lo[a]), A.voxel);
+        float q = voxel_quotient(__fsub_rn(w, A.lo[a]), A.voxel, inv_voxel);
         if (!(q >= 0.0f && q < A.dimf[a])) return kInvalid;
         idx[a] = static_cast<uint32_t>(q);  // q >= 0: truncation is floor
     }
@@ -109,15 +130,16 @@ __device__ __forceinline__ void keys_range(const float *__restrict__ xyz, int64_
                                            int64_t blk, int64_t nblk) {
     const int64_t n4 = n / 4;
     const int64_t stride = nblk * (int64_t)kThreads;
+    const float inv_voxel = __frcp_rn(A.voxel);
 #pragma unroll 2
     for (int64_t g = blk * (int64_t)kThreads + threadIdx.x; g < n4; g += stride) {
         const float4 *src = reinterpret_cast<const float4 *>(xyz) + 3 * g;
         float4 a0 = __ldcs(src), a1 = __ldcs(src + 1), a2 = __ldcs(src + 2);
         uint4 k;
-        k.x = voxel_key(a0.x, a0.y, a0.z, A);
-        k.y = voxel_key(a0.w, a1.x, a1.y, A);
-        k.z = voxel_key(a1.z, a1.w, a2.x, A);
-        k.w = voxel_key(a2.y, a2.z, a2.w, A);
+        k.x = voxel_key(a0.x, a0.y, a0.z, A, inv_voxel);
+        k.y = voxel_key(a0.w, a1.x, a1.y, A, inv_voxel);
+        k.z = voxel_key(a1.z, a1.w, a2.x, A, inv_voxel);
+        k.w = voxel_key(a2.y, a2.z, a2.w, A, inv_voxel);
         reinterpret_cast<uint4 *>(keys)[g] = k;
         BitMerge m;
         m.add(k.x, bitmap);
@@ -129,7 +151,7 @@ __device__ __forceinline__ void keys_range(const float *__restrict__ xyz, int64_
     // ragged tail (n % 4 points)
     int64_t t = 4 * n4 + blk * (int64_t)kThreads + threadIdx.x;
     if (t < n) {
-        uint32_t k = voxel_key(xyz[3 * t], xyz[3 * t + 1], xyz[3 * t + 2], A);
+        uint32_t k = voxel_key(xyz[3 * t], xyz[3 * t + 1], xyz[3 * t + 2], A, inv_voxel);
         keys[t] = k;
         if (k != kInvalid) atomicOr(&bitmap[k >> 5], 1u << (k & 31));
     }

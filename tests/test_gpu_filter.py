@@ -196,3 +196,33 @@ def test_batched_filter_matches_filter_cloud_and_oracle(gm):
                 for a in ("x", "y", "z", "keys", "counts", "rep_idx"):
                     n = single.count()
                     assert torch.equal(getattr(single, a)[:n], getattr(fb.outs[q], a)[:n])
+
+
+def test_voxel_faces_stress_bit_exact(gm):
+    """Quotients (w - lo) / voxel at and around every integer of the grid:
+    points within +-8 ulp of each voxel face along x (and the faces of the
+    upper edge), plus random offsets; the GPU's voxel quotient must decide
+    floor and crop exactly as the IEEE quotient of the oracle."""
+    ws = Workspace(lo=(0.0, -0.5, 0.0), voxel=0.0043, dims=(232, 232, 186))
+    v = np.float32(ws.voxel)
+    k = np.arange(0, 233, dtype=np.float32)
+    face = (k * v).astype(np.float32)
+    steps = np.arange(-8, 9)
+    x = np.concatenate([np.nextafter(face, np.float32(np.inf) if s > 0 else np.float32(-np.inf))
+                        if s else face for s in [0]] +
+                       [face + s * np.spacing(face) for s in steps])
+    g = np.random.Generator(np.random.PCG64(8))
+    x = np.concatenate([x, g.uniform(-0.01, 1.01, 200000).astype(np.float32)]).astype(np.float32)
+    n = x.size
+    y = np.full(n, np.float32(0.5 * v) - np.float32(0.5), np.float32)     # a cell centre in y
+    z = g.uniform(0.0, 0.79, n).astype(np.float32)
+    pts = np.stack([x, y, z], axis=1).astype(np.float32)
+    I = np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], np.float32)
+    # also through a rotation: the transform's products and sums feed the quotient
+    c, s = np.float32(np.cos(0.3)), np.float32(np.sin(0.3))
+    Rz = np.array([c, -s, 0, 0.2, s, c, 0, -0.1, 0, 0, 1, 0.05], np.float32)
+    for T in (I, Rz):
+        ref = oracle.filter_cloud(pts, T, ws)
+        obs = _run(gm, pts, T, ws)
+        gm.sync()
+        _assert_same(obs, ref)
