@@ -66,7 +66,9 @@ void gmapp_destroy(gmapp_ctx *ctx);
 const char *gmapp_last_error(void);
 
 /* Wait for `stream`, then read and clear the context's device error word:
- * GMAPP_OK, GMAPP_ERR_CAPACITY, GMAPP_ERR_TIMEOUT or GMAPP_ERR_CUDA. */
+ * GMAPP_OK, GMAPP_ERR_CAPACITY, GMAPP_ERR_TIMEOUT, GMAPP_ERR_INVALID_ARG (an
+ * input that is only read on the device was out of range, e.g. an agent
+ * without a gate in rollout_agents_culled) or GMAPP_ERR_CUDA. */
 gmapp_status gmapp_sync(gmapp_ctx *ctx, gmapp_stream stream);
 
 /* Raw device error word (bit mask of GMAPP_DEVERR_*), read after a stream
@@ -434,6 +436,40 @@ gmapp_status gmapp_autotune_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *obs,
                                      gmapp_rollout_out *out, int32_t max_candidates,
                                      int32_t probe_steps, gmapp_tuning *best, float *best_ms,
                                      gmapp_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Rollout with spatial culling (Alg. 1's detection gate; the voxel grid of  */
+/* Sec. IV-B as a neighbour grid)                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of the neighbour index of a grid: (ceil(cells / 32) + 1) x 4. */
+size_t gmapp_grid_index_bytes(const gmapp_workspace *ws);
+
+/* Neighbour index of an obstacle set that filter_cloud (or filter_clouds)
+ * built on the grid `ws`: index[w] = the number of obstacles whose key is
+ * below 32 w, for w = 0 .. ceil(cells / 32) (device, uint32, written).
+ * Reads obs->keys and N_O (obs->n) on the device; asynchronous. */
+gmapp_status gmapp_grid_index(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                              const gmapp_workspace *ws, uint32_t *index, size_t index_bytes,
+                              gmapp_stream stream);
+
+/* rollout_agents (MFI field) visiting only the obstacles within each
+ * agent's reach r_d + r_a + r_O: the grid rows around the agent give index
+ * ranges of S_W through `index` (gmapp_grid_index of the same obstacles and
+ * grid).  Alg. 1's gate makes every farther pair contribute nothing, so W,
+ * the force and the trajectory are those of rollout_agents (FP32 sums in
+ * another order).  The clearance m_k is exact when the nearest obstacle is
+ * within the reach, else the smallest distance among the visited obstacles
+ * (at least r_d) or +inf when none was visited; clear_pen and min_clear
+ * follow it.  Every r_d must be finite (an agent without a gate sets
+ * GMAPP_DEVERR_BOUNDS and its outputs are not written).  One CTA of 128
+ * threads per agent.  traj, p_final, v_final, path_len, clear_pen,
+ * min_clear, w_trace, m_trace as in rollout_agents; checkpoints, f_trace
+ * and cost_terms must be NULL (GMAPP_ERR_INVALID_ARG). */
+gmapp_status rollout_agents_culled(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                                   const gmapp_workspace *ws, const uint32_t *index,
+                                   const gmapp_agents *agents, const gmapp_rollout_params *prm,
+                                   gmapp_rollout_out *out, gmapp_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Cost and selection: score_and_select (Sec. IV-A "Cost Functions" and        */

@@ -23,7 +23,7 @@ from ._abi import check
 __all__ = ["Context", "context", "Obstacles", "filter_cloud", "filter_clouds",
            "filter_cloud_noalloc",
            "filter_workspace_bytes", "rollout_agents", "rollout_ensemble", "score_and_select",
-           "score_and_select4",
+           "score_and_select4", "grid_index", "rollout_agents_culled",
            "pick_tuning", "autotune_rollout", "autotune_ensemble", "rollout_adjoint", "GMappRollout", "sync", "GmappError",
            "FilterBatch", "Batch", "Server"]
 
@@ -386,6 +386,41 @@ def rollout_ensemble(obs: Obstacles, agents: dict, n_apf: int, prm, out: dict | 
     check(_abi.load().rollout_ensemble(ctx.handle, C.byref(ob), C.byref(ag), int(n_proj), int(n_apf),
                                        C.byref(pr), C.byref(os_), t, _stream(stream)),
           "rollout_ensemble")
+    return out
+
+
+def grid_index(obs: Obstacles, ws, index=None, stream=None):
+    """Neighbour index of ``obs`` on the grid ``ws`` (device uint32 tensor
+    [ceil(cells/32) + 1]) for rollout_agents_culled."""
+    torch = _torch()
+    ctx = context()
+    wss = _ws_struct(ws)
+    lib = _abi.load()
+    need = int(lib.gmapp_grid_index_bytes(C.byref(wss)))
+    if index is None or index.numel() * 4 < need:
+        index = torch.empty(need // 4, dtype=torch.int32, device=obs.x.device)
+    ob = obs._struct()
+    check(lib.gmapp_grid_index(ctx.handle, C.byref(ob), C.byref(wss), _ptr(index),
+                               int(index.numel() * 4), _stream(stream)), "gmapp_grid_index")
+    return index
+
+
+def rollout_agents_culled(obs: Obstacles, ws, index, agents: dict, prm, out: dict | None = None,
+                          want_traj: bool = True, want_trace: bool = False,
+                          want_clear: bool = True, stream=None) -> dict:
+    """rollout_agents visiting only the obstacles within each agent's gate
+    (the voxel grid ``ws`` of ``obs`` as a neighbour grid; ``index`` from
+    grid_index)."""
+    ctx = context()
+    na = int(agents["k_r"].numel())
+    if out is None:
+        out = alloc_rollout_out(na, int(prm.n_steps), want_traj, want_trace, want_clear)
+        out["f_trace"] = None
+    ob, ag, pr, os_ = obs._struct(), _agents_struct(agents), _params_struct(prm), _out_struct(out)
+    wss = _ws_struct(ws)
+    check(_abi.load().rollout_agents_culled(ctx.handle, C.byref(ob), C.byref(wss), _ptr(index),
+                                            C.byref(ag), C.byref(pr), C.byref(os_),
+                                            _stream(stream)), "rollout_agents_culled")
     return out
 
 

@@ -130,6 +130,11 @@ PROTOTYPES = {
                                    C.POINTER(RolloutParams), C.POINTER(RolloutOut),
                                    C.POINTER(Tuning), P]),
     "gmapp_pick_tuning": (C.c_int, [P, C.c_int64, C.c_int32, C.POINTER(Tuning)]),
+    "gmapp_grid_index_bytes": (C.c_size_t, [C.POINTER(Workspace)]),
+    "gmapp_grid_index": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Workspace), P, C.c_size_t, P]),
+    "rollout_agents_culled": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Workspace), P,
+                                        C.POINTER(Agents), C.POINTER(RolloutParams),
+                                        C.POINTER(RolloutOut), P]),
     "gmapp_autotune_rollout": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
                                          C.POINTER(RolloutParams), C.POINTER(RolloutOut),
                                          C.c_int32, C.c_int32, C.POINTER(Tuning),

@@ -101,6 +101,10 @@ extern "C" gmapp_status gmapp_sync(gmapp_ctx *ctx, gmapp_stream stream) {
         set_error("device: capacity exceeded (error bits 0x%x)", bits);
         return GMAPP_ERR_CAPACITY;
     }
+    if (bits & GMAPP_DEVERR_BOUNDS) {
+        set_error("device: an input read on the device is out of range (error bits 0x%x)", bits);
+        return GMAPP_ERR_INVALID_ARG;
+    }
     if (bits) {
         set_error("device: error bits 0x%x", bits);
         return GMAPP_ERR_CUDA;
