@@ -813,6 +813,69 @@ def bench_replan(gm, args, n_frames=16, ticks=32, alpha=0.95):
             "overhead_of_four_term_cost": t_4 / t_0 - 1.0}
 
 
+def bench_culled(gm, args, n_frames=16, ticks=32):
+    """Plans with spatial culling vs the all-pairs plan on the tabletop
+    query: per plan a new frame (a ring of distinct frames in HBM) ->
+    filter_cloud -> [gmapp_grid_index -> rollout_agents_culled |
+    rollout_agents] -> score_and_select, 256 agents x 500 steps, r_d = 5 cm.
+    Culling skips the pairs beyond the gate, so it is reported as plans/s
+    (interactions/s counts all pairs)."""
+    import torch
+    base, frames_np = make_workload(n_frames, 0)
+    prm, ws = base["params"], base["workspace"]
+    na, nk = int(base["agents"]["k_r"].size), int(prm.n_steps)
+    frames = torch.from_numpy(np.stack(frames_np)).cuda()
+    agents = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda()
+              for k, v in base["agents"].items()}
+    wsp = torch.empty(gm.filter_workspace_bytes(frames.shape[1], ws), dtype=torch.uint8,
+                      device="cuda")
+    probe = gm.filter_cloud(frames[0], base["T"], ws, cap=OBS_CAP, workspace=wsp)
+    cap = (int(probe.count() * 1.05) + 63) // 64 * 64
+    del probe
+    obs = gm.Obstacles.empty(cap)
+    index = gm.grid_index(gm.filter_cloud(frames[0], base["T"], ws, out=obs, workspace=wsp), ws)
+    out_c = gm.alloc_rollout_out(na, nk, want_traj=True, want_clear=False)
+    out_c["f_trace"] = None
+    out_a = gm.alloc_rollout_out(na, nk, want_traj=True, want_clear=False)
+    tun, _ = gm.autotune_rollout(obs, agents, prm, out=out_a, candidates=16, probe_steps=100)
+    sel_c, sel_a = gm.score_and_select(out_c, prm), gm.score_and_select(out_a, prm)
+
+    def plan_culled(i):
+        gm.filter_cloud(frames[i % n_frames], base["T"], ws, out=obs, workspace=wsp)
+        gm.grid_index(obs, ws, index=index)
+        gm.rollout_agents_culled(obs, ws, index, agents, prm, out=out_c)
+        gm.score_and_select(out_c, prm, out=sel_c)
+
+    def plan_all(i):
+        gm.filter_cloud(frames[i % n_frames], base["T"], ws, out=obs, workspace=wsp)
+        gm.rollout_agents(obs, agents, prm, out=out_a, tuning=tun)
+        gm.score_and_select(out_a, prm, out=sel_a)
+
+    for i in range(3):
+        plan_culled(i)
+        plan_all(i)
+    gm.sync()
+    cur = torch.cuda.current_stream()
+    t_c = _events(torch, cur, lambda it=iter(range(ticks)): plan_culled(next(it)), ticks)
+    t_a = _events(torch, cur, lambda it=iter(range(ticks)): plan_all(next(it)), ticks)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    ev[0].record(cur)
+    for _ in range(5):
+        gm.rollout_agents_culled(obs, ws, index, agents, prm, out=out_c)
+    ev[1].record(cur)
+    torch.cuda.synchronize()
+    t_roll = ev[0].elapsed_time(ev[1]) / 1e3 / 5
+    gm.sync()
+    same = int((sel_c["best"] == sel_a["best"]).item())
+    return {"workload": f"{ticks} plans over {n_frames} tabletop frames; 256 agents x 500 steps, "
+                        "r_d = 5 cm",
+            "culled": {"ms_per_plan": 1e3 * t_c, "plans_per_s": 1.0 / t_c,
+                       "rollout_ms": 1e3 * t_roll},
+            "all_pairs": {"ms_per_plan": 1e3 * t_a, "plans_per_s": 1.0 / t_a,
+                          "tuning": list(tun)},
+            "speedup": t_a / t_c, "last_plan_same_agent": bool(same)}
+
+
 def bench_served(gm, args):
     """1 kHz open-loop request stream (200k-point tabletop frames with 4 moving
     spheres, 1 cm voxels, N_a in {64, 256, 1024}, N_k = 300) through the
@@ -995,6 +1058,7 @@ PATTERNS = {"filter_stream": lambda gm, a: bench_filter_stream(gm, a),
             "adjoint": lambda gm, a: bench_adjoint(gm, a),
             "ensemble": lambda gm, a: bench_ensemble(gm, a),
             "replan": lambda gm, a: bench_replan(gm, a),
+            "culled": lambda gm, a: bench_culled(gm, a),
             "served": lambda gm, a: bench_served(gm, a)}
 
 
