@@ -71,6 +71,18 @@ const char *gmapp_last_error(void);
  * without a gate in rollout_agents_culled) or GMAPP_ERR_CUDA. */
 gmapp_status gmapp_sync(gmapp_ctx *ctx, gmapp_stream stream);
 
+/* Cap on the polls of the grid-exchange waits (launch shapes with
+ * exchange = 1) of rollout_agents, rollout_ensemble and their autotuners,
+ * for later launches of this context: a wait that gives up sets
+ * GMAPP_DEVERR_TIMEOUT, its CTA skips its later waits and every CTA still
+ * finishes, so the failure path can be exercised without a hang (polls = 1
+ * makes the exchanges give up).  Only these global-memory polls are capped:
+ * the mbarrier waits for TMA copies and DSMEM deliveries keep their bound
+ * (2^24 polls), since a CTA that stopped waiting for them could leave
+ * while data is still in flight into its shared memory.  0 restores the
+ * default (2^22 polls of an exchange word). */
+gmapp_status gmapp_set_wait_limit(gmapp_ctx *ctx, uint32_t polls);
+
 /* Raw device error word (bit mask of GMAPP_DEVERR_*), read after a stream
  * synchronisation, without clearing it. */
 gmapp_status gmapp_peek_device_error(gmapp_ctx *ctx, uint32_t *bits);

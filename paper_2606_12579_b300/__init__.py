@@ -69,6 +69,11 @@ class Context:
         """Wait for the stream and raise if a kernel flagged a device error."""
         check(_abi.load().gmapp_sync(self.handle, _stream(stream)), "gmapp_sync")
 
+    def set_wait_limit(self, polls: int) -> None:
+        """Cap the polls of the rollout kernels' bounded waits (0 = defaults);
+        a wait that gives up is reported as GMAPP_ERR_TIMEOUT by sync()."""
+        check(_abi.load().gmapp_set_wait_limit(self.handle, int(polls)), "gmapp_set_wait_limit")
+
     def device_error_bits(self) -> int:
         b = C.c_uint32()
         check(_abi.load().gmapp_peek_device_error(self.handle, C.byref(b)), "peek")

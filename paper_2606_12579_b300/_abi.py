@@ -111,6 +111,7 @@ PROTOTYPES = {
     "gmapp_destroy": (None, [P]),
     "gmapp_last_error": (C.c_char_p, []),
     "gmapp_sync": (C.c_int, [P, P]),
+    "gmapp_set_wait_limit": (C.c_int, [P, C.c_uint32]),
     "gmapp_peek_device_error": (C.c_int, [P, C.POINTER(C.c_uint32)]),
     "gmapp_filter_workspace_bytes": (C.c_size_t, [C.c_int64, C.POINTER(Workspace)]),
     "filter_cloud": (C.c_int, [P, P, C.c_int64, C.POINTER(C.c_float * 12), C.POINTER(Workspace),

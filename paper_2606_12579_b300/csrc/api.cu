@@ -84,6 +84,15 @@ extern "C" gmapp_status gmapp_peek_device_error(gmapp_ctx *ctx, uint32_t *bits) 
     return GMAPP_OK;
 }
 
+extern "C" gmapp_status gmapp_set_wait_limit(gmapp_ctx *ctx, uint32_t polls) {
+    if (!ctx) {
+        set_error("gmapp_set_wait_limit: ctx is NULL");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    ctx->wait_limit = polls;
+    return GMAPP_OK;
+}
+
 extern "C" gmapp_status gmapp_sync(gmapp_ctx *ctx, gmapp_stream stream) {
     if (!ctx) {
         set_error("gmapp_sync: ctx is NULL");

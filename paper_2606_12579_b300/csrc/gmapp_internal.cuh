@@ -20,6 +20,7 @@ struct gmapp_ctx {
     uint32_t *d_xctl;
     cudaEvent_t x_done;   // completion of the last grid-exchange launch
     bool x_pending;       // x_done has been recorded
+    uint32_t wait_limit;  // cap on the polls of a bounded rollout wait (0 = defaults)
 };
 
 namespace gmapp {
@@ -66,9 +67,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
 
 // Wait until the mbarrier phase with parity `parity` completes; gives up
 // after kSpinLimit polls and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          uint32_t limit = kSpinLimit) {
     uint32_t addr = smem_u32(bar);
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -84,9 +86,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 
 // As mbar_wait, with acquire at cluster scope: data that other CTAs of the
 // cluster delivered with st_async_v2f32 on this barrier is visible after it.
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity,
+                                                  uint32_t limit = kSpinLimit) {
     uint32_t addr = smem_u32(bar);
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

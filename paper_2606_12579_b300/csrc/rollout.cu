@@ -381,6 +381,11 @@ gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agen
     A.group_ctas = s.cluster;
     A.xbuf = ctx->d_xbuf;
     A.xctl = ctx->d_xctl;
+    // the test knob caps only the grid-exchange polls (global-memory words,
+    // nothing in flight into shared memory when a CTA gives up); mbarrier
+    // waits (TMA copies, DSMEM deliveries) keep their full bound
+    A.spin_limit = kSpinLimit;
+    A.poll_limit = ctx->wait_limit ? ctx->wait_limit : kPollLimit;
     A.err = ctx->d_err;
     cudaLaunchAttribute attr;
     cudaLaunchConfig_t cfg = config(s, &attr, stream);

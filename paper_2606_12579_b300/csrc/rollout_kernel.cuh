@@ -76,6 +76,8 @@ struct RolloutArgs {
     int32_t group_ctas;  // grid exchange: CTAs per group (C)
     uint64_t *xbuf;      // grid exchange: tagged slots [G][2][2][C][AG][2]
     uint32_t *xctl;      // grid exchange: launch epoch, finished-CTA counter
+    uint32_t spin_limit;  // polls of an mbarrier wait before it gives up
+    uint32_t poll_limit;  // polls of a grid-exchange word before it gives up
     uint32_t *err;
 };
 
@@ -424,7 +426,7 @@ __device__ __forceinline__ void half_combine(const float *recv_par, int nq, int 
 template <int AG, int NA, int OFF, int NW, bool CLEAR>
 __device__ __forceinline__ bool exchange_half(const float *part, float *slot, uint64_t *bar,
                                               uint32_t C, uint32_t rank, int lane, int k,
-                                              bool ok, float &W, float &md2) {
+                                              bool ok, float &W, float &md2, uint32_t limit) {
     float w = 0.0f, m = INFINITY;
     if (lane < NA) {
 #pragma unroll 4
@@ -442,7 +444,7 @@ __device__ __forceinline__ bool exchange_half(const float *part, float *slot, ui
             st_async_v2f32(map_smem(local, r), w, m, map_smem(lbar, r));
     }
     // each (half, parity) barrier completes once every second step
-    if (ok && !mbar_wait_cluster(bar, (k >> 1) & 1)) ok = false;
+    if (ok && !mbar_wait_cluster(bar, (k >> 1) & 1, limit)) ok = false;
     if (lane >= OFF && lane < OFF + NA) {
         float ws = 0.0f, ms = INFINITY;
         for (uint32_t r = 0; r < C; ++r) {
@@ -475,7 +477,8 @@ __device__ __forceinline__ uint64_t xword(uint32_t tag, float v) {
 template <int AG, int NA, int OFF, int NW, bool CLEAR>
 __device__ __forceinline__ bool exchange_half_grid(const float *part, uint64_t *xs, float *slot,
                                                    uint32_t C, uint32_t rank, int lane,
-                                                   uint32_t tag, bool ok, float &W, float &md2) {
+                                                   uint32_t tag, bool ok, float &W, float &md2,
+                                                   uint32_t limit) {
     if (lane < NA) {
         float w = 0.0f, m = INFINITY;
 #pragma unroll 4
@@ -509,12 +512,12 @@ __device__ __forceinline__ bool exchange_half_grid(const float *part, uint64_t *
             const int r = p / NA, a = OFF + p % NA;
             const uint64_t *src = xs + 2 * (r * AG + a);
             for (uint32_t it = 0; ok && static_cast<uint32_t>(vw[j] >> 32) != tag; ++it) {
-                if (it == kPollLimit) ok = false;
+                if (it == limit) ok = false;
                 else vw[j] = ld_relaxed_u64(src);
             }
             if (CLEAR) {
                 for (uint32_t it = 0; ok && static_cast<uint32_t>(vm[j] >> 32) != tag; ++it) {
-                    if (it == kPollLimit) ok = false;
+                    if (it == limit) ok = false;
                     else vm[j] = ld_relaxed_u64(src + 1);
                 }
             }
@@ -684,7 +687,8 @@ __device__ __forceinline__ void sum_rank_rec(const float *slot, uint32_t C, int 
 template <int AG, int NA, int OFF, int NW, bool CLEAR, int NF, int RS>
 __device__ __forceinline__ bool exchange_half_rec(const float *part, float *slot, uint64_t *bar,
                                                   uint32_t C, uint32_t rank, int lane, int k,
-                                                  bool ok, float (&F)[4], float &md2) {
+                                                  bool ok, float (&F)[4], float &md2,
+                                                  uint32_t limit) {
     float s[RS];
     if (lane < NA) sum_warp_rec<AG, OFF, NW, CLEAR, NF, RS>(part, lane, s);
     if (lane == 0) mbar_arrive_expect_tx(bar, C * NA * RS * 4u);
@@ -697,7 +701,7 @@ __device__ __forceinline__ bool exchange_half_rec(const float *part, float *slot
             for (int c = 0; c < RS; c += 2) st_async_v2f32(dst + 4u * c, s[c], s[c + 1], rb);
         }
     }
-    if (ok && !mbar_wait_cluster(bar, (k >> 1) & 1)) ok = false;
+    if (ok && !mbar_wait_cluster(bar, (k >> 1) & 1, limit)) ok = false;
     if (lane >= OFF && lane < OFF + NA) sum_rank_rec<AG, CLEAR, NF, RS>(slot, C, lane, F, md2);
     return ok;
 }
@@ -708,7 +712,7 @@ template <int AG, int NA, int OFF, int NW, bool CLEAR, int NF, int RS>
 __device__ __forceinline__ bool exchange_half_grid_rec(const float *part, uint64_t *xs,
                                                        float *slot, uint32_t C, uint32_t rank,
                                                        int lane, uint32_t tag, bool ok,
-                                                       float (&F)[4], float &md2) {
+                                                       float (&F)[4], float &md2, uint32_t limit) {
     constexpr int NV = CLEAR ? NF + 1 : NF;
     if (lane < NA) {
         float s[RS];
@@ -739,7 +743,7 @@ __device__ __forceinline__ bool exchange_half_grid_rec(const float *part, uint64
 #pragma unroll
             for (int c = 0; c < NV; ++c) {
                 for (uint32_t it = 0; ok && static_cast<uint32_t>(w[j][c] >> 32) != tag; ++it) {
-                    if (it == kPollLimit) ok = false;
+                    if (it == limit) ok = false;
                     else w[j][c] = ld_relaxed_u64(src + c);
                 }
                 dst[c] = __uint_as_float(static_cast<uint32_t>(w[j][c]));
@@ -1044,7 +1048,7 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
         G2a[a] = __shfl_sync(0xffffffffu, G2, a);
     }
     if (cnt > 0) {
-        if (!mbar_wait(&bar_tma, 0)) {
+        if (!mbar_wait(&bar_tma, 0, A.spin_limit)) {
             if (tid == 0) raise_error(A.err, GMAPP_DEVERR_TIMEOUT);
             cnt = 0;  // keep the barrier sequence; results are flagged invalid
         }
@@ -1252,21 +1256,21 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
                 if constexpr (GRID)
                     ok = exchange_half_grid_rec<AG, NA, OFF, NW, CLEAR, NF, RS>(
                         part(HH), xslot(HH, par), slot(HH, par), C, rank, lane, xtag(epoch, k), ok,
-                        rec, md2);
+                        rec, md2, A.poll_limit);
                 else
                     ok = exchange_half_rec<AG, NA, OFF, NW, CLEAR, NF, RS>(
                         part(HH), slot(HH, par), &bar_recv[HH][par], C, rank, lane, k, ok, rec,
-                        md2);
+                        md2, A.spin_limit);
             } else {
                 if constexpr (GRID)
                     ok = exchange_half_grid<AG, NA, OFF, NW, CLEAR>(part(HH), xslot(HH, par),
                                                                     slot(HH, par), C, rank, lane,
                                                                     xtag(epoch, k), ok, rec[0],
-                                                                    md2);
+                                                                    md2, A.poll_limit);
                 else
                     ok = exchange_half<AG, NA, OFF, NW, CLEAR>(part(HH), slot(HH, par),
                                                                &bar_recv[HH][par], C, rank, lane,
-                                                               k, ok, rec[0], md2);
+                                                               k, ok, rec[0], md2, A.spin_limit);
             }
         };
         for (int k = 0; k < A.n_steps; ++k) {
