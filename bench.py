@@ -880,7 +880,9 @@ def bench_served(gm, args):
     """1 kHz open-loop request stream (200k-point tabletop frames with 4 moving
     spheres, 1 cm voxels, N_a in {64, 256, 1024}, N_k = 300) through the
     continuously batched server vs the same stream served one request at a
-    time through the plain per-query calls.  Frames come from a pool
+    time through the plain per-query calls, both with all pairs and with
+    spatial culling (each agent visits the obstacles within its reach).
+    Frames come from a pool
     rendered at evenly spaced times of the stream (each frame serves the
     requests of its 1/pool-th of the stream)."""
     import torch
@@ -888,11 +890,11 @@ def bench_served(gm, args):
     dur = float(args.serve_seconds)
     n_req = int(round(dur * 1000))
     pool = max(4, int(round(dur * 5)))
-    arrivals, na_choice, _ = synth.serve_stream(n_requests=n_req)
+    arrivals_1k, na_choice, _ = synth.serve_stream(n_requests=n_req)
     frames, Ts = [], []
     for i in range(pool):
         w = synth.tabletop_workload(seed=1005 + i, n_agents=1, n_steps=1, n_points=200000,
-                                    voxel=0.01, spheres_at=float(arrivals[i * n_req // pool]),
+                                    voxel=0.01, spheres_at=float(arrivals_1k[i * n_req // pool]),
                                     sphere_seed=1005, scene_seed=1005)
         frames.append(torch.from_numpy(w["xyz"]).pin_memory())
         Ts.append(w["T"])
@@ -910,79 +912,107 @@ def bench_served(gm, args):
         return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "plans_per_s": len(lat) / t_span, "interactions_per_s": inter / t_span}
 
-    # --- served: continuous batching
-    srv = gm.Server(max_slots=48, max_agents=1024, max_steps=300, obs_cap=32768,
-                    arena_bytes=2 << 30, chunk_steps=50, agents_per_item=8, threads=256)
-    # warm up (kernel loading, first admissions)
-    for r in range(4):
-        t = srv.submit(frames[0], Ts[0], ws_grid, agents[int(na_choice[r])], prm)
-        while srv.poll(t) is None:
-            srv.tick()
-        srv.release(t)
-    lat, inter, done = [], 0, 0
-    outstanding = {}
-    t0 = time.perf_counter()
-    nxt = 0
-    while done < n_req:
-        now = time.perf_counter() - t0
-        while nxt < n_req and arrivals[nxt] <= now:
-            na = int(na_choice[nxt])
-            tk = srv.submit(frames[frame_of[nxt]], Ts[frame_of[nxt]], ws_grid, agents[na], prm)
-            outstanding[tk] = (nxt, na)
-            nxt += 1
-        if not outstanding:
-            while time.perf_counter() - t0 < arrivals[nxt]:
-                pass
-            continue
-        srv.tick()
-        for tk in list(outstanding):
-            res = srv.poll(tk)
-            if res is None:
+    def run_served(culled, rate=1000.0, chunk=50):
+        """The stream, offered at ``rate`` requests/s, through the continuously
+        batched server (``chunk`` steps of every active plan per tick)."""
+        arrivals = arrivals_1k * (1000.0 / rate)
+        srv = gm.Server(max_slots=48, max_agents=1024, max_steps=300, obs_cap=32768,
+                        arena_bytes=2 << 30, chunk_steps=chunk, agents_per_item=8, threads=256,
+                        culled=culled)
+        for r in range(4):   # warm up (kernel loading, first admissions)
+            t = srv.submit(frames[0], Ts[0], ws_grid, agents[int(na_choice[r])], prm)
+            while srv.poll(t) is None:
+                srv.tick()
+            srv.release(t)
+        lat, inter, done = [], 0, 0
+        outstanding = {}
+        t0 = time.perf_counter()
+        nxt = 0
+        while done < n_req:
+            now = time.perf_counter() - t0
+            while nxt < n_req and arrivals[nxt] <= now:
+                na = int(na_choice[nxt])
+                tk = srv.submit(frames[frame_of[nxt]], Ts[frame_of[nxt]], ws_grid, agents[na], prm)
+                outstanding[tk] = (nxt, na)
+                nxt += 1
+            if not outstanding:
+                while time.perf_counter() - t0 < arrivals[nxt]:
+                    pass
                 continue
-            r, na = outstanding.pop(tk)
-            lat.append(time.perf_counter() - t0 - arrivals[r])
-            inter += na * res["n_obs"] * prm.n_steps
-            srv.release(tk)
-            done += 1
-    t_span = time.perf_counter() - t0
-    served = lat_stats(lat, t_span, inter)
-    del srv
+            srv.tick()
+            for tk in list(outstanding):
+                res = srv.poll(tk)
+                if res is None:
+                    continue
+                r, na = outstanding.pop(tk)
+                lat.append(time.perf_counter() - t0 - arrivals[r])
+                inter += na * res["n_obs"] * prm.n_steps
+                srv.release(tk)
+                done += 1
+        t_span = time.perf_counter() - t0
+        del srv
+        return lat_stats(lat, t_span, inter)
 
-    # --- plain: one request at a time through the per-query calls
     cur = torch.cuda.current_stream()
     dev_frame = torch.empty(200000, 3, device="cuda")
     obs = gm.Obstacles.empty(32768)
     wsb = torch.empty(gm.filter_workspace_bytes(200000, ws_grid), dtype=torch.uint8, device="cuda")
+    index = gm.grid_index(gm.filter_cloud(dev_frame.copy_(frames[0]), Ts[0], ws_grid, out=obs,
+                                          workspace=wsb), ws_grid)
     dev_agents = {na: {k: v.cuda() for k, v in a.items()} for na, a in agents.items()}
     outs = {na: gm.alloc_rollout_out(na, 300, want_traj=True, want_clear=False) for na in agents}
+    for o in outs.values():
+        o["f_trace"] = None
     host_best = torch.empty(1, dtype=torch.int32).pin_memory()
     host_traj = torch.empty(301, 3).pin_memory()
-    for na in agents:  # warm up
-        gm.rollout_agents(gm.filter_cloud(dev_frame.copy_(frames[0]), Ts[0], ws_grid, out=obs,
-                                          workspace=wsb), dev_agents[na], prm, out=outs[na])
-    gm.sync()
-    lat, inter = [], 0
-    t0 = time.perf_counter()
-    for r in range(n_req):
-        while time.perf_counter() - t0 < arrivals[r]:
-            pass
-        na = int(na_choice[r])
-        dev_frame.copy_(frames[frame_of[r]], non_blocking=True)
-        gm.filter_cloud(dev_frame, Ts[frame_of[r]], ws_grid, out=obs, workspace=wsb)
-        gm.rollout_agents(obs, dev_agents[na], prm, out=outs[na])
-        sel = gm.score_and_select(outs[na], prm)
-        host_best.copy_(sel["best"], non_blocking=True)
-        host_traj.copy_(sel["best_traj"], non_blocking=True)
-        cur.synchronize()
-        lat.append(time.perf_counter() - t0 - arrivals[r])
-        inter += na * int(obs.count()) * 300
-    t_span = time.perf_counter() - t0
-    plain = lat_stats(lat, t_span, inter)
-    gm.sync()
+
+    def plan(na, culled):
+        if culled:
+            gm.grid_index(obs, ws_grid, index=index)
+            gm.rollout_agents_culled(obs, ws_grid, index, dev_agents[na], prm, out=outs[na])
+        else:
+            gm.rollout_agents(obs, dev_agents[na], prm, out=outs[na])
+        return gm.score_and_select(outs[na], prm)
+
+    def run_plain(culled, rate=1000.0):
+        """The stream, offered at ``rate`` requests/s, one request at a time
+        through the per-query calls."""
+        arrivals = arrivals_1k * (1000.0 / rate)
+        for na in agents:  # warm up
+            gm.filter_cloud(dev_frame.copy_(frames[0]), Ts[0], ws_grid, out=obs, workspace=wsb)
+            plan(na, culled)
+        gm.sync()
+        lat, inter = [], 0
+        t0 = time.perf_counter()
+        for r in range(n_req):
+            while time.perf_counter() - t0 < arrivals[r]:
+                pass
+            na = int(na_choice[r])
+            dev_frame.copy_(frames[frame_of[r]], non_blocking=True)
+            gm.filter_cloud(dev_frame, Ts[frame_of[r]], ws_grid, out=obs, workspace=wsb)
+            sel = plan(na, culled)
+            host_best.copy_(sel["best"], non_blocking=True)
+            host_traj.copy_(sel["best_traj"], non_blocking=True)
+            cur.synchronize()
+            lat.append(time.perf_counter() - t0 - arrivals[r])
+            inter += na * int(obs.count()) * 300
+        t_span = time.perf_counter() - t0
+        gm.sync()
+        return lat_stats(lat, t_span, inter)
+
+    served, plain = run_served(False), run_plain(False)
+    culled = {}
+    for rate in (float(r) for r in str(args.serve_cull_rates).split(",")):
+        s, p = run_served(True, rate, int(args.serve_cull_chunk)), run_plain(True, rate)
+        culled[f"{rate:g}_per_s"] = {"served": s, "plain": p, "p99_speedup": p["p99_ms"] / s["p99_ms"]}
     return {"workload": f"{n_req} requests at 1 kHz: 200k-point tabletop frames + 4 moving spheres, "
                         "1 cm voxels, N_a in {64, 256, 1024}, N_k = 300",
             "offered_per_s": 1000.0, "served": served, "plain": plain,
             "p99_speedup": plain["p99_ms"] / served["p99_ms"],
+            "culled": {"note": "every agent visits only the obstacles within its reach "
+                               "(interactions/s still counts all pairs); the same frames "
+                               "and N_a offered at each rate",
+                       "chunk_steps": int(args.serve_cull_chunk), **culled},
             "frames_in_pool": pool}
 
 
@@ -1030,6 +1060,10 @@ def main():
                     help="obstacle capacity of the S_W buffers (multiple of 4; 0 = from the scene)")
     ap.add_argument("--no-patterns", action="store_true",
                     help="skip the batched / adjoint / served measurements")
+    ap.add_argument("--serve-cull-rates", default="1000,2000,4000",
+                    help="offered request rates (Hz) of the culled serving comparison")
+    ap.add_argument("--serve-cull-chunk", type=int, default=300,
+                    help="steps per tick of the culled server")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="length of the 1 kHz request stream of the served loop")
     ap.add_argument("--tuning", default="",

@@ -617,6 +617,11 @@ typedef struct {
     int32_t chunk_steps;     /* M: steps every active request advances per tick */
     int32_t agents_per_item; /* work-item size of the chunk kernel: 4, 8 or 16 */
     int32_t threads;         /* threads per CTA: 256, 384 or 512 */
+    int32_t culled;          /* 1: every agent visits only the obstacles within its reach
+                                r_d + r_a + r_O (the voxel grid as a neighbour grid, as in
+                                rollout_agents_culled; one agent per work item, 128 threads;
+                                agents_per_item and threads are then unused and every r_d
+                                must be finite); 0: all pairs */
 } gmapp_server_config;
 
 /* A request: HOST cloud and agent arrays (kept alive, unmodified, by the

@@ -709,11 +709,12 @@ class Server:
     one launch, scored and returned; see include/gmapp.h."""
 
     def __init__(self, max_slots=16, max_agents=1024, max_steps=300, obs_cap=32768,
-                 arena_bytes=4 << 30, chunk_steps=50, agents_per_item=8, threads=256):
+                 arena_bytes=4 << 30, chunk_steps=50, agents_per_item=8, threads=256,
+                 culled=False):
         ctx = context()
         cfg = _abi.ServerConfig(int(max_slots), int(max_agents), int(max_steps), int(obs_cap),
                                 int(arena_bytes), int(chunk_steps), int(agents_per_item),
-                                int(threads))
+                                int(threads), int(bool(culled)))
         h = C.c_void_p()
         check(_abi.load().gmapp_server_create(ctx.handle, C.byref(cfg), C.byref(h)),
               "gmapp_server_create")

@@ -84,7 +84,7 @@ class Query(C.Structure):
 class ServerConfig(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("max_agents", C.c_int32), ("max_steps", C.c_int32),
                 ("obs_cap", C.c_int64), ("arena_bytes", C.c_int64), ("chunk_steps", C.c_int32),
-                ("agents_per_item", C.c_int32), ("threads", C.c_int32)]
+                ("agents_per_item", C.c_int32), ("threads", C.c_int32), ("culled", C.c_int32)]
 
 
 class Request(C.Structure):

@@ -9,13 +9,9 @@
 // within the visited rows; otherwise it is the smallest distance among the
 // visited obstacles (at least r_d, or +inf when none was visited).
 //
-// Neighbour index: S_W comes out of filter_cloud sorted by its linear key
-// (i_z dims_y + i_y) dims_x + i_x, so the obstacles of a grid row (fixed
-// i_y, i_z) with i_x in [a, b] lie in one index range.  wr[w] = the number of
-// obstacles whose key is below 32 w (one binary search per 32-cell word of
-// the grid, k_grid_index); a row's range is [wr[klo / 32], wr[khi / 32 + 1])
-// with klo, khi the keys of its end cells -- at most 31 cells of slack at
-// each end, which the gate rejects.
+// Neighbour index (culled_device.cuh): wr[w] = the number of obstacles whose
+// key is below 32 w, one binary search per 32-cell word of the grid
+// (k_grid_index).
 //
 // k_rollout_culled: one CTA per agent.  Each step its threads take the grid
 // rows of the box around the agent (rows whose (y, z) cell is farther than
@@ -26,7 +22,7 @@
 
 #include <algorithm>
 
-#include "rollout_kernel.cuh"
+#include "culled_device.cuh"
 
 namespace gmapp {
 namespace {
@@ -55,9 +51,7 @@ struct CulledArgs {
     const int32_t *n_obs;
     int64_t cap;
     float r_O;
-    const uint32_t *wr;  // [n_words + 1]
-    float lo[3], voxel;
-    int32_t nx, ny, nz;
+    NeighbourGrid grid;
     const float *p0, *v0, *c, *k_r, *k_a, *r_d, *r_a;
     int32_t n_agents;
     float goal[3];
@@ -68,21 +62,12 @@ struct CulledArgs {
     uint32_t *err;
 };
 
-// Index range [i0, i1] of the cells whose extent meets [c - r, c + r] along
-// one axis (clamped to the grid); empty when i0 > i1.
-__device__ __forceinline__ void cell_span(float c, float r, float lo, float voxel, int n, int &i0,
-                                          int &i1) {
-    const float a = floorf((c - r - lo) / voxel), b = floorf((c + r - lo) / voxel);
-    i0 = a < 0.0f ? 0 : (a >= static_cast<float>(n) ? n : static_cast<int>(a));
-    i1 = b < 0.0f ? -1 : (b >= static_cast<float>(n) ? n - 1 : static_cast<int>(b));
-}
-
 template <bool CLEAR>
 __global__ void __launch_bounds__(kCullThreads) k_rollout_culled(const CulledArgs A) {
     constexpr int NW = kCullThreads / 32;
     __shared__ float s_w[NW], s_m[NW];
     __shared__ float s_p[3];
-    const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i = blockIdx.x, tid = threadIdx.x;
     const int n = A.n_agents;
     const int32_t n_obs = *A.n_obs;
     if (n_obs < 0 || n_obs > A.cap) {
@@ -94,10 +79,9 @@ __global__ void __launch_bounds__(kCullThreads) k_rollout_culled(const CulledArg
         if (tid == 0) raise_error(A.err, GMAPP_DEVERR_BOUNDS);
         return;
     }
-    // gate s <= r_d  <=>  d^2 <= (r_d + R)^2 (as in the all-pairs kernel);
-    // rows are taken within r_d + R plus a margin far above FP32 rounding
+    // gate s <= r_d  <=>  d^2 <= (r_d + R)^2 (as in the all-pairs kernel)
     const float G2 = rd >= A.eps ? (rd + R) * (rd + R) : -1.0f;
-    const float reach = rd >= A.eps ? (rd + R) + 1e-3f * A.voxel : -1.0f;
+    const float reach = culled_reach(rd, R, A.eps, A.grid.voxel);
     float p[3], v[3], cc[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -115,56 +99,14 @@ __global__ void __launch_bounds__(kCullThreads) k_rollout_culled(const CulledArg
         t[2] = p[2];
     }
     for (int k = 0; k < A.n_steps; ++k) {
-        float W = 0.0f, md2 = INFINITY;
-        if (reach > 0.0f) {
-            int x0, x1, y0, y1, z0, z1;
-            cell_span(p[0], reach, A.lo[0], A.voxel, A.nx, x0, x1);
-            cell_span(p[1], reach, A.lo[1], A.voxel, A.ny, y0, y1);
-            cell_span(p[2], reach, A.lo[2], A.voxel, A.nz, z0, z1);
-            const int ny_r = y1 - y0 + 1, nz_r = z1 - z0 + 1;
-            const int rows = (x0 <= x1 && ny_r > 0 && nz_r > 0) ? ny_r * nz_r : 0;
-            const float r2 = reach * reach;
-            for (int r = tid; r < rows; r += kCullThreads) {
-                const int iy = y0 + r % ny_r, iz = z0 + r / ny_r;
-                // distance from p to the row's cells in (y, z)
-                const float cy = A.lo[1] + static_cast<float>(iy) * A.voxel;
-                const float cz = A.lo[2] + static_cast<float>(iz) * A.voxel;
-                const float dy = fmaxf(fmaxf(cy - p[1], p[1] - (cy + A.voxel)), 0.0f);
-                const float dz = fmaxf(fmaxf(cz - p[2], p[2] - (cz + A.voxel)), 0.0f);
-                if (dy * dy + dz * dz > r2) continue;
-                const uint32_t row = static_cast<uint32_t>(iz) * static_cast<uint32_t>(A.ny) +
-                                     static_cast<uint32_t>(iy);
-                const uint32_t klo = row * static_cast<uint32_t>(A.nx) + static_cast<uint32_t>(x0);
-                const uint32_t khi = row * static_cast<uint32_t>(A.nx) + static_cast<uint32_t>(x1);
-                const uint32_t j0 = __ldg(A.wr + (klo >> 5)), j1 = __ldg(A.wr + (khi >> 5) + 1);
-                for (uint32_t j = j0; j < j1; ++j) {
-                    const float dx = p[0] - __ldg(A.ox + j), ex = p[1] - __ldg(A.oy + j),
-                                ez = p[2] - __ldg(A.oz + j);
-                    const float d2 = fmaf(ez, ez, fmaf(ex, ex, dx * dx));
-                    const float s = fmaxf(fmaf(d2, rsqrt_approx(d2), -R), A.eps);
-                    if (d2 <= G2) W += rcp_approx(s);
-                    if (CLEAR) md2 = fminf(md2, d2);
-                }
-            }
-        }
-        // fixed-order CTA reduction: warp butterfly, then warps in order
-        W = warp_sum(W);
-        if (CLEAR) md2 = warp_min(md2);
-        if (lane == 0) {
-            s_w[warp] = W;
-            s_m[warp] = md2;
-        }
-        __syncthreads();
+        float W, md2;
+        culled_terms<kCullThreads, CLEAR>(p, reach, G2, R, A.eps, A.grid, A.ox, A.oy, A.oz, tid,
+                                          W, md2);
+        culled_reduce<kCullThreads, CLEAR>(W, md2, s_w, s_m);
         if (tid == 0) {
-            float Wt = 0.0f, mt = INFINITY;
-#pragma unroll
-            for (int q = 0; q < NW; ++q) {
-                Wt += s_w[q];
-                mt = fminf(mt, s_m[q]);
-            }
             float g[3], kf, m;
             agent_step<CLEAR>(p, v, cc, k_r, k_a, R, A.goal, h, A.dt, A.rho, A.damping,
-                              A.clear_margin, A.clear_beta, Wt, mt, L, pen, minc, m, g, kf);
+                              A.clear_margin, A.clear_beta, W, md2, L, pen, minc, m, g, kf);
             s_p[0] = p[0];
             s_p[1] = p[1];
             s_p[2] = p[2];
@@ -174,7 +116,7 @@ __global__ void __launch_bounds__(kCullThreads) k_rollout_culled(const CulledArg
                 t[1] = p[1];
                 t[2] = p[2];
             }
-            if (A.w_trace) A.w_trace[static_cast<size_t>(i) * A.n_steps + k] = Wt;
+            if (A.w_trace) A.w_trace[static_cast<size_t>(i) * A.n_steps + k] = W;
             if (A.m_trace) A.m_trace[static_cast<size_t>(i) * A.n_steps + k] = m;
         }
         __syncthreads();
@@ -273,12 +215,12 @@ extern "C" gmapp_status rollout_agents_culled(gmapp_ctx *ctx, const gmapp_obstac
     A.n_obs = obs->n;
     A.cap = obs->cap;
     A.r_O = obs->r_O;
-    A.wr = index;
-    for (int a = 0; a < 3; ++a) A.lo[a] = ws->lo[a];
-    A.voxel = ws->voxel;
-    A.nx = ws->dims[0];
-    A.ny = ws->dims[1];
-    A.nz = ws->dims[2];
+    A.grid.wr = index;
+    for (int a = 0; a < 3; ++a) A.grid.lo[a] = ws->lo[a];
+    A.grid.voxel = ws->voxel;
+    A.grid.nx = ws->dims[0];
+    A.grid.ny = ws->dims[1];
+    A.grid.nz = ws->dims[2];
     A.p0 = ag->p0;
     A.v0 = ag->v0;
     A.c = ag->c;

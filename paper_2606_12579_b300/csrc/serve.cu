@@ -13,6 +13,11 @@
 // arithmetic depends only on its own request and the agent state is kept
 // exactly between chunks, so each result is bit-identical whether the
 // request runs alone or in any mix.
+//
+// With cfg.culled the server visits, for every agent, only the obstacles
+// within its reach (the voxel grid as a neighbour grid, culled_device.cuh):
+// each request gets its grid index after its filter, and the chunk kernel
+// takes one agent per work item (ks_chunk_culled).
 #include <math.h>
 
 #include <algorithm>
@@ -22,7 +27,7 @@
 #include <map>
 #include <vector>
 
-#include "rollout_kernel.cuh"
+#include "culled_device.cuh"
 
 namespace gmapp {
 namespace {
@@ -40,6 +45,7 @@ struct SlotDev {
     float damping, inv_mass, rho, eps, vel_half, clear_margin, clear_beta;
     float *sp, *sv, *sL;       // saved state between chunks: p [3][n], v [3][n], L [n]
     float *traj, *p_final, *v_final, *path_len;
+    NeighbourGrid grid;        // culled server: the request's neighbour index
 };
 
 struct ChunkItem {
@@ -182,6 +188,99 @@ __global__ void __launch_bounds__(NT, 1) ks_chunk(const ChunkArgs A) {
     }
 }
 
+// Culled chunks (cfg.culled): one agent of one request per work item
+// (ChunkItem.group is the agent index), its CTA deals the agent's grid rows
+// to its threads every step (culled_terms), reduces in a fixed order and
+// thread 0 integrates; the state is saved exactly between chunks as in
+// ks_chunk.
+constexpr int kServeCullThreads = 128;
+
+__global__ void __launch_bounds__(kServeCullThreads) ks_chunk_culled(const ChunkArgs A) {
+    constexpr int NT = kServeCullThreads, NW = NT / 32;
+    __shared__ float s_w[NW], s_m[NW], s_p[3];
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) s_item = static_cast<int>(atomicAdd(A.head, 1u));
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= A.n_items) break;
+        const ChunkItem item = A.items[it];
+        const SlotDev &S = A.slots[item.slot];
+        const int i = item.group, n = S.n_agents, N = S.n_steps;
+        const int32_t n_obs = *S.n_obs;
+        if (n_obs < 0 || n_obs > S.cap) {
+            if (tid == 0) raise_error(A.err, GMAPP_DEVERR_CAPACITY);
+            continue;  // uniform across the CTA
+        }
+        const float R = S.r_a[i] + S.r_O, rd = S.r_d[i];
+        if (!isfinite(rd)) {  // no gate: nothing to cull by
+            if (tid == 0) raise_error(A.err, GMAPP_DEVERR_BOUNDS);
+            continue;
+        }
+        const float G2 = rd >= S.eps ? (rd + R) * (rd + R) : -1.0f;
+        const float reach = culled_reach(rd, R, S.eps, S.grid.voxel);
+        const bool first = item.k0 == 0;
+        float p[3], v[3], cc[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            p[d] = first ? S.p0[d * n + i] : S.sp[d * n + i];
+            v[d] = first ? S.v0[d * n + i] : S.sv[d * n + i];
+            cc[d] = S.c[d * n + i];
+        }
+        float L = first ? 0.0f : S.sL[i], pen = 0.0f, minc = INFINITY;
+        const float k_r = S.k_r[i], k_a = S.k_a[i];
+        const float h = S.vel_half * S.dt * S.inv_mass;
+        const float goal[3] = {S.goal[0], S.goal[1], S.goal[2]};
+        if (first && tid == 0 && S.traj) {
+            float *t = S.traj + static_cast<size_t>(i) * (N + 1) * 3;
+            t[0] = p[0];
+            t[1] = p[1];
+            t[2] = p[2];
+        }
+        for (int k = item.k0; k < item.k1; ++k) {
+            float W, md2;
+            culled_terms<NT, false>(p, reach, G2, R, S.eps, S.grid, S.ox, S.oy, S.oz, tid, W,
+                                    md2);
+            culled_reduce<NT, false>(W, md2, s_w, s_m);
+            if (tid == 0) {
+                float g[3], kf, m;
+                agent_step<false>(p, v, cc, k_r, k_a, R, goal, h, S.dt, S.rho, S.damping,
+                                  S.clear_margin, S.clear_beta, W, md2, L, pen, minc, m, g, kf);
+                s_p[0] = p[0];
+                s_p[1] = p[1];
+                s_p[2] = p[2];
+                if (S.traj) {
+                    float *t = S.traj + (static_cast<size_t>(i) * (N + 1) + k + 1) * 3;
+                    t[0] = p[0];
+                    t[1] = p[1];
+                    t[2] = p[2];
+                }
+            }
+            __syncthreads();
+            p[0] = s_p[0];
+            p[1] = s_p[1];
+            p[2] = s_p[2];
+        }
+        if (tid == 0) {
+            for (int d = 0; d < 3; ++d) {
+                S.sp[d * n + i] = p[d];
+                S.sv[d * n + i] = v[d];
+            }
+            S.sL[i] = L;
+            if (item.k1 == N) {
+                for (int d = 0; d < 3; ++d) {
+                    S.p_final[d * n + i] = p[d];
+                    S.v_final[d * n + i] = v[d];
+                }
+                S.path_len[i] = L;
+            }
+        }
+    }
+}
+
+
 using ChunkKernel = void (*)(const ChunkArgs);
 
 ChunkKernel chunk_kernel(int ag, int nt) {
@@ -316,6 +415,7 @@ size_t request_bytes(const gmapp_server_config &c, const gmapp_request &r, size_
     add(na * 6 * 4 + na * 4);                          // p_final, v_final, path_len
     add(na * (nk + 1) * 12);                           // trajectories
     add(na * 4 + 4 + (nk + 1) * 12);                   // costs, best, best trajectory
+    if (c.culled) add(gmapp_grid_index_bytes(&r.ws));  // neighbour index
     return b;
 }
 
@@ -346,6 +446,8 @@ gmapp_status admit(gmapp_server *s, ServerReq *q) {
     float *fin = reinterpret_cast<float *>(take(na * 6 * 4 + na * 4));
     q->out.traj = reinterpret_cast<float *>(take(na * (nk + 1) * 12));
     float *sel = reinterpret_cast<float *>(take(na * 4 + 4 + (nk + 1) * 12));
+    const size_t index_bytes = s->cfg.culled ? gmapp_grid_index_bytes(&r.ws) : 0;
+    uint32_t *index = s->cfg.culled ? reinterpret_cast<uint32_t *>(take(index_bytes)) : nullptr;
     q->out.p_final = fin;
     q->out.v_final = fin + 3 * na;
     q->out.path_len = fin + 6 * na;
@@ -369,6 +471,10 @@ gmapp_status admit(gmapp_server *s, ServerReq *q) {
     gmapp_status st2 = filter_cloud(s->ctx, q->d_xyz, r.n_raw, r.T, &r.ws, &q->obs, q->d_fws,
                                     q->fws_bytes, s->compute);
     if (st2 != GMAPP_OK) return st2;
+    if (index) {
+        st2 = gmapp_grid_index(s->ctx, &q->obs, &r.ws, index, index_bytes, s->compute);
+        if (st2 != GMAPP_OK) return st2;
+    }
     // device descriptor of the slot
     SlotDev &D = s->h_slots[q->slot];
     memset(&D, 0, sizeof(D));
@@ -404,6 +510,14 @@ gmapp_status admit(gmapp_server *s, ServerReq *q) {
     D.p_final = q->out.p_final;
     D.v_final = q->out.v_final;
     D.path_len = q->out.path_len;
+    if (index) {
+        D.grid.wr = index;
+        for (int a = 0; a < 3; ++a) D.grid.lo[a] = r.ws.lo[a];
+        D.grid.voxel = r.ws.voxel;
+        D.grid.nx = r.ws.dims[0];
+        D.grid.ny = r.ws.dims[1];
+        D.grid.nz = r.ws.dims[2];
+    }
     GMAPP_CHECK_CUDA(cudaMemcpyAsync(s->d_slots + q->slot, &D, sizeof(SlotDev),
                                      cudaMemcpyHostToDevice, s->compute));
     return GMAPP_OK;
@@ -438,7 +552,7 @@ extern "C" gmapp_status gmapp_server_create(gmapp_ctx *ctx, const gmapp_server_c
         return GMAPP_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    ChunkKernel fn = chunk_kernel(cfg->agents_per_item, cfg->threads);
+    ChunkKernel fn = cfg->culled ? ks_chunk_culled : chunk_kernel(cfg->agents_per_item, cfg->threads);
     if (!fn) {
         set_error("gmapp_server_create: no chunk kernel for %d agents per item, %d threads",
                   cfg->agents_per_item, cfg->threads);
@@ -454,9 +568,12 @@ extern "C" gmapp_status gmapp_server_create(gmapp_ctx *ctx, const gmapp_server_c
         static_cast<size_t>(2) * (cfg->threads / 32) * cfg->agents_per_item * 2 * sizeof(float);
     const int64_t room =
         (static_cast<int64_t>(ctx->max_smem_optin) - static_cast<int64_t>(fa.sharedSizeBytes + recv_bytes)) / 12;
-    s->shard_cap = static_cast<int>(std::min<int64_t>(cfg->obs_cap, room & ~int64_t(3)));
-    s->smem = static_cast<size_t>(s->shard_cap) * 12 + recv_bytes;
-    const int max_groups = (cfg->max_agents + cfg->agents_per_item - 1) / cfg->agents_per_item;
+    // the culled kernel reads obstacles through the neighbour index (no shard)
+    s->shard_cap = cfg->culled ? 0 : static_cast<int>(std::min<int64_t>(cfg->obs_cap, room & ~int64_t(3)));
+    s->smem = cfg->culled ? 0 : static_cast<size_t>(s->shard_cap) * 12 + recv_bytes;
+    const int threads = cfg->culled ? kServeCullThreads : cfg->threads;
+    const int max_groups =
+        cfg->culled ? cfg->max_agents : (cfg->max_agents + cfg->agents_per_item - 1) / cfg->agents_per_item;
     s->max_items = cfg->max_slots * max_groups;
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
@@ -464,7 +581,7 @@ extern "C" gmapp_status gmapp_server_create(gmapp_ctx *ctx, const gmapp_server_c
     int per_sm = 0;
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(fn),
-                                                           cfg->threads, s->smem);
+                                                           threads, s->smem);
     s->resident = std::max(1, per_sm) * ctx->sm_count;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
@@ -600,7 +717,10 @@ extern "C" gmapp_status gmapp_server_tick(gmapp_server *s, int32_t *n_active) {
         ++active;
         const int N = q->req.prm.n_steps;
         const int k1 = std::min(N, q->k + s->cfg.chunk_steps);
-        const int groups = (q->req.n_agents + s->cfg.agents_per_item - 1) / s->cfg.agents_per_item;
+        // culled: one agent per item (group = agent index)
+        const int groups = s->cfg.culled
+                               ? q->req.n_agents
+                               : (q->req.n_agents + s->cfg.agents_per_item - 1) / s->cfg.agents_per_item;
         for (int g = 0; g < groups; ++g) {
             const int na = q->req.n_agents / groups + (g < q->req.n_agents % groups ? 1 : 0);
             const int64_t cost = static_cast<int64_t>(na) * (k1 - q->k);
@@ -620,7 +740,7 @@ extern "C" gmapp_status gmapp_server_tick(gmapp_server *s, int32_t *n_active) {
         GMAPP_CHECK_CUDA(cudaMemsetAsync(s->d_head, 0, sizeof(uint32_t), s->compute));
         ChunkArgs A{s->d_slots, s->d_items, n_items, s->d_head, s->shard_cap, s->ctx->d_err};
         const int grid = std::max(1, std::min(n_items, s->resident));
-        s->fn<<<grid, s->cfg.threads, s->smem, s->compute>>>(A);
+        s->fn<<<grid, s->cfg.culled ? kServeCullThreads : s->cfg.threads, s->smem, s->compute>>>(A);
         GMAPP_CHECK_CUDA(cudaGetLastError());
     }
     // 4. requests that reached their horizon: score, copy the plan out

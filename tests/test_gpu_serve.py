@@ -33,9 +33,9 @@ def _requests(n=6, seed=3):
     return out
 
 
-def _serve(gm, ws, arena=1 << 28, slots=8, stagger=False, chunk=16):
+def _serve(gm, ws, arena=1 << 28, slots=8, stagger=False, chunk=16, culled=False):
     srv = gm.Server(max_slots=slots, max_agents=64, max_steps=200, obs_cap=16384,
-                    arena_bytes=arena, chunk_steps=chunk, agents_per_item=8)
+                    arena_bytes=arena, chunk_steps=chunk, agents_per_item=8, culled=culled)
     tickets, results, max_active, max_pending = [], {}, 0, 0
     for i, w in enumerate(ws):
         tickets.append(srv.submit(w["xyz"], w["T"], w["workspace"], w["agents"], w["params"]))
@@ -113,3 +113,47 @@ def test_rejections(gm):
     with pytest.raises(gm.GmappError) as e:
         tiny.submit(w["xyz"], w["T"], w["workspace"], w["agents"], w["params"])
     assert e.value.status == 2
+
+
+# ---- the culled server (each agent visits the obstacles within its reach) --
+
+def test_culled_mix_equals_alone_equals_single_query_and_oracle(gm):
+    """Culled serving: every result is bit-identical alone and in the mix,
+    and bit-identical to rollout_agents_culled of the same request (same
+    per-step arithmetic, state kept exactly between chunks); within the
+    rollout tolerance of the oracle's all-pairs definition."""
+    import torch
+    ws = _requests(n=5, seed=21)
+    mixed, max_active, _ = _serve(gm, ws, stagger=True, culled=True)
+    assert max_active >= 2
+    for w, r in zip(ws, mixed):
+        alone, _, _ = _serve(gm, [w], culled=True)
+        assert np.array_equal(alone[0]["costs"], r["costs"])
+        assert np.array_equal(alone[0]["best_traj"], r["best_traj"])
+        obs = gm.filter_cloud(torch.from_numpy(w["xyz"]).cuda(), w["T"], w["workspace"],
+                              cap=16384)
+        index = gm.grid_index(obs, w["workspace"])
+        ag = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda()
+              for k, v in w["agents"].items()}
+        single = gm.rollout_agents_culled(obs, w["workspace"], index, ag, w["params"],
+                                          want_clear=False)
+        sel = gm.score_and_select(single, w["params"])
+        gm.sync()
+        assert np.array_equal(sel["costs"].cpu().numpy(), r["costs"])
+        assert np.array_equal(single["traj"][r["best"]].cpu().numpy(), r["best_traj"])
+        ref_f = oracle.filter_cloud(w["xyz"], w["T"], w["workspace"])
+        o = np.stack([ref_f["x"], ref_f["y"], ref_f["z"]])
+        ref = oracle.rollout(o, ref_f["r_O"], w["agents"], w["params"])
+        c_ref = oracle.costs(ref, w["params"])
+        oi = oracle.select(c_ref)
+        assert r["best"] == oi or abs(c_ref[r["best"]] - c_ref[oi]) < 1e-6
+        assert np.abs(r["best_traj"] - ref["traj"][r["best"]]).max() <= 1e-3
+
+
+def test_culled_chunk_size_does_not_change_results(gm):
+    ws = _requests(n=3, seed=13)
+    a, _, _ = _serve(gm, ws, chunk=5, culled=True)
+    b, _, _ = _serve(gm, ws, chunk=200, culled=True)
+    for x, y in zip(a, b):
+        assert np.array_equal(x["best_traj"], y["best_traj"])
+        assert np.array_equal(x["costs"], y["costs"])
