@@ -279,6 +279,15 @@ typedef struct {
                           the step rule; d1 = |p_0 - goal|.  Needs cost_radius > 0 and
                           computes the clearance m_k.  rollout_agents and
                           rollout_ensemble only. */
+    unsigned long long *heur_pairs; /* device counter, or NULL: the launch adds the number
+                          of MFI agent-obstacle pairs whose heuristic terms (rsqrt, clamp,
+                          reciprocal, accumulation) it evaluated.  Every pair's |d|^2 and
+                          gate are evaluated; a warp evaluates the heuristic terms of its
+                          block of 64 obstacles only when one of the block's pairs passes
+                          an agent's gate (Alg. 1's branch), so this is a multiple of 64
+                          and at least the number of pairs within the gates.  For
+                          accounting only (results do not depend on it); rollout_agents and
+                          rollout_ensemble only (other calls leave it untouched). */
 } gmapp_rollout_out;
 
 /* Roll all agents forward N_k steps in ONE launch.  Step k (0-based):

@@ -293,7 +293,7 @@ def alloc_rollout_out(n_agents: int, n_steps: int, want_traj=True, want_trace=Fa
 def _out_struct(out: dict) -> _abi.RolloutOut:
     s = _abi.RolloutOut()
     for k in ("traj", "p_final", "v_final", "path_len", "clear_pen", "min_clear", "w_trace",
-              "m_trace", "f_trace", "ckpt", "cost_terms"):
+              "m_trace", "f_trace", "ckpt", "cost_terms", "heur_pairs"):
         t = out.get(k)
         setattr(s, k, t.data_ptr() if t is not None else None)
     return s

@@ -53,7 +53,7 @@ class RolloutParams(C.Structure):
 class RolloutOut(C.Structure):
     _fields_ = [("traj", P), ("p_final", P), ("v_final", P), ("path_len", P), ("clear_pen", P),
                 ("min_clear", P), ("w_trace", P), ("m_trace", P), ("f_trace", P), ("ckpt", P),
-                ("cost_terms", P)]
+                ("cost_terms", P), ("heur_pairs", P)]
 
 
 class AdjointOut(C.Structure):

@@ -38,8 +38,9 @@ struct Shape {
 };
 
 int32_t shard_cap_for(int64_t cap, int cluster) {
+    // a multiple of 128: the pair loop pads every shard to whole 128-obstacle blocks
     int64_t s = (cap + cluster - 1) / cluster;
-    return static_cast<int32_t>((s + 3) & ~int64_t(3));
+    return static_cast<int32_t>((s + 127) & ~int64_t(127));
 }
 
 RolloutKernel pick_kernel(int ag, int nt, bool clear, bool grid, int level) {
@@ -371,6 +372,7 @@ gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agen
     A.f_trace = out->f_trace;
     A.ckpt = out->ckpt;
     A.cost_terms = out->cost_terms;
+    A.heur_pairs = out->heur_pairs;
     A.cost_radius = prm->cost_radius;
     A.shard_cap = s.shard_cap;
     A.n_groups = s.groups;
@@ -477,15 +479,18 @@ gmapp_status autotune_impl(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gma
     // 2. time each on the caller's inputs with a shortened horizon
     gmapp_rollout_params probe = *prm;
     probe.n_steps = std::min(prm->n_steps, probe_steps);
+    gmapp_rollout_out probe_out = *out;  // the probes add nothing to the caller's counter
+    probe_out.heur_pairs = nullptr;
     cudaEvent_t e0, e1;
     GMAPP_CHECK_CUDA(cudaEventCreate(&e0));
     GMAPP_CHECK_CUDA(cudaEventCreate(&e1));
     float best_t = 1e30f;
     gmapp_status result = GMAPP_OK;
     for (const Cand &c : cands) {
-        if ((st = launch(ctx, obs, agents, &probe, out, c.t, stream, kinds)) != GMAPP_OK) continue;
+        if ((st = launch(ctx, obs, agents, &probe, &probe_out, c.t, stream, kinds)) != GMAPP_OK)
+            continue;
         cudaEventRecord(e0, stream);
-        st = launch(ctx, obs, agents, &probe, out, c.t, stream, kinds);
+        st = launch(ctx, obs, agents, &probe, &probe_out, c.t, stream, kinds);
         cudaEventRecord(e1, stream);
         if (st != GMAPP_OK) continue;
         if (cudaEventSynchronize(e1) != cudaSuccess) {

@@ -2,9 +2,10 @@
 // circular-field force, Alg. 1 clamp, gate and obstacle sum).
 //
 // Layout of the work: a thread-block cluster of C CTAs owns a group of up to
-// AG agents for the whole rollout; CTA r keeps obstacle shard r of S_W in
-// shared memory (SoA float32, loaded once by the TMA bulk-copy engine, padded
-// with NaN, which contributes exactly nothing).  Each thread walks pairs of
+// AG agents for the whole rollout; CTA r keeps obstacle shard r of S_W (the
+// blocks r, r + C, ... of 128 obstacles) in shared memory (SoA float32,
+// loaded once by the TMA bulk-copy engine, padded with NaN, which
+// contributes exactly nothing).  Each thread walks pairs of
 // obstacles of its shard against all AG agents of the group:
 //
 //   packed f32x2 arithmetic over the obstacle pair (one instruction, two
@@ -66,8 +67,9 @@ struct RolloutArgs {
     float *traj, *p_final, *v_final, *path_len, *clear_pen, *min_clear, *w_trace, *m_trace,
         *f_trace, *ckpt;
     float *cost_terms;  // [5][N_a] sums of the four-term cost, or NULL
+    unsigned long long *heur_pairs;  // MFI pairs whose heuristic terms ran (added), or NULL
     float cost_radius;  // r_c of its goal and obstacle terms
-    int32_t shard_cap;   // obstacles one CTA can hold (multiple of 4)
+    int32_t shard_cap;   // obstacles one CTA can hold (multiple of 128)
     int32_t n_groups;    // agent groups (clusters, or CTA groups with the grid exchange)
     int32_t n_apf;       // ensemble kernel: the last n_apf agents use APF (Eq. (apf))
     int32_t n_groups_apf;  // ensemble kernel: ... and form the last n_groups_apf groups
@@ -260,19 +262,40 @@ __device__ __forceinline__ int transposed_index(int lane) {
 // the unrolled pair loop.
 constexpr bool sfu_agent(int a, int NM, int NA) { return ((a + 1) * NM) / NA > (a * NM) / NA; }
 
-template <int AG, int NA, int OFF, int NM, bool CLEAR>
-__device__ __forceinline__ void pair_terms(f2 ox, f2 oy, f2 oz, const f2 (&X)[NA],
-                                           const f2 (&Y)[NA], const f2 (&Z)[NA], f2 (&acc)[NA],
-                                           float (&mn)[NA], const f2 (&nR2)[AG],
-                                           const float (&G2a)[AG], float eps, f2 one2) {
+//
+// The terms are split in two parts: pair_dist forms |d|^2 of every pair (and
+// the clearance minimum) and tells whether one of the thread's pairs passes
+// the gate of one of the NA agents; pair_heur evaluates the gated heuristic
+// terms (Alg. 1's branch) from |d|^2.  A pair outside the gate adds its
+// mask 0 times a finite term, i.e. a signed zero, which leaves a sum that is
+// never -0 unchanged; evaluating pair_heur only for blocks where some pair
+// passes the gate therefore gives bit-identical sums.
+template <int AG, int NA, int OFF, bool CLEAR>
+__device__ __forceinline__ bool pair_dist(f2 ox, f2 oy, f2 oz, const f2 (&X)[NA],
+                                          const f2 (&Y)[NA], const f2 (&Z)[NA], f2 (&d2)[NA],
+                                          float (&mn)[NA], const float (&G2a)[AG]) {
+    bool hit = false;
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
         const f2 dx = sub2(X[a], ox), dy = sub2(Y[a], oy), dz = sub2(Z[a], oz);
-        const f2 d2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-        const float d2l = lo_of(d2), d2h = hi_of(d2);
+        d2[a] = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        // min ignores a NaN lane, so m <= G2 iff one of the two lanes passes
+        const float m = fminf(lo_of(d2[a]), hi_of(d2[a]));
+        hit |= m <= G2a[OFF + a];
+        if (CLEAR) mn[a] = fminf(mn[a], m);
+    }
+    return hit;
+}
+
+template <int AG, int NA, int OFF, int NM>
+__device__ __forceinline__ void pair_heur(const f2 (&d2)[NA], f2 (&acc)[NA], const f2 (&nR2)[AG],
+                                          const float (&G2a)[AG], float eps, f2 one2) {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const float d2l = lo_of(d2[a]), d2h = hi_of(d2[a]);
         const f2 mask = pk(le_mask(d2l, G2a[OFF + a]), le_mask(d2h, G2a[OFF + a]));
         const f2 r = pk(rsqrt_approx(d2l), rsqrt_approx(d2h));
-        const f2 s = fma2(d2, r, nR2[OFF + a]);  // |d| - R (NaN when d = 0)
+        const f2 s = fma2(d2[a], r, nR2[OFF + a]);  // |d| - R (NaN when d = 0)
         const float sl = fmaxf(lo_of(s), eps), sh = fmaxf(hi_of(s), eps);
         if (sfu_agent(a, NM, NA)) {
             acc[a] = fma2(mask, pk(rcp_approx(sl), rcp_approx(sh)), acc[a]);
@@ -280,8 +303,17 @@ __device__ __forceinline__ void pair_terms(f2 ox, f2 oy, f2 oz, const f2 (&X)[NA
             const f2 y = neg_rcp2(pk(sl, sh), sl, sh, one2);
             acc[a] = fma2(mask, y, acc[a]);
         }
-        if (CLEAR) mn[a] = fminf(mn[a], fminf(d2l, d2h));
     }
+}
+
+template <int AG, int NA, int OFF, int NM, bool CLEAR>
+__device__ __forceinline__ void pair_terms(f2 ox, f2 oy, f2 oz, const f2 (&X)[NA],
+                                           const f2 (&Y)[NA], const f2 (&Z)[NA], f2 (&acc)[NA],
+                                           float (&mn)[NA], const f2 (&nR2)[AG],
+                                           const float (&G2a)[AG], float eps, f2 one2) {
+    f2 d2[NA];
+    pair_dist<AG, NA, OFF, CLEAR>(ox, oy, oz, X, Y, Z, d2, mn, G2a);
+    pair_heur<AG, NA, OFF, NM>(d2, acc, nR2, G2a, eps, one2);
 }
 
 // Obstacles beyond what shared memory holds, read from global memory
@@ -292,15 +324,32 @@ struct GlobalTail {
 };
 
 // Agent positions come from lane OFF+a of the warp (p), or with POS from
-// shared memory pos[3][AG] (SoA).
+// shared memory pos[3][AG] (SoA).  With VOTE the shard is padded to a
+// multiple of 128 obstacles (cnt_pad), so every lane of a warp runs the same
+// iterations; a lane takes 4 consecutive obstacles per iteration (two packed
+// pairs), the warp a block of 128, and the warp evaluates the heuristic
+// terms of the block only when one of its pairs passes an agent's gate
+// (Alg. 1's branch, taken per warp).  *nheur counts those blocks in units of
+// 64 pairs per agent.
+//
+// Without the clearance the test of a block uses the expanded distance
+// |d|^2 - |p|^2 = |o|^2 - 2 p.o (|o|^2 once per obstacle, then three FMAs
+// per pair instead of six) against G2 - |p|^2 + delta.  Its rounding
+// error (a few ulp of |o|^2 + 2|p||o| + |p|^2 <= 2 (|p|^2 + omax2), plus
+// those of the exact |d|^2 and of the threshold) stays below
+// 32 u (G2 + |p|^2 + omax2) with u = 2^-24; delta is eight times that, so
+// every pair the exact |d|^2 puts inside the gate passes the test (a few
+// more blocks than needed may run the heuristic terms, which then add
+// signed zeros).  omax2 bounds |o|^2 over the shard.
 template <int AG, int NA, int OFF, int NM, int NT, bool CLEAR, bool TAIL = false,
-          bool SHIP = true, bool POS = false>
+          bool SHIP = true, bool POS = false, bool VOTE = false>
 __device__ __forceinline__ void half_step(const float *sx, const float *sy, const float *sz,
                                           int cnt_pad, float eps, const f2 (&nR2)[AG],
                                           const float (&G2a)[AG], const float (&p)[3],
                                           float *recv_slot0, uint32_t C, int lane,
                                           GlobalTail tail = GlobalTail{},
-                                          const float *pos = nullptr) {
+                                          const float *pos = nullptr,
+                                          uint32_t *nheur = nullptr, float omax2 = 0.0f) {
     if constexpr (NA > 0) {
         constexpr int P = pow2ceil(NA);
         const int tid = threadIdx.x;
@@ -325,12 +374,66 @@ __device__ __forceinline__ void half_step(const float *sx, const float *sy, cons
             mn[a] = INFINITY;
         }
         const f2 one2 = pk(1.0f, 1.0f);
+        if constexpr (VOTE) {
+            // block test of the expanded distance (no clearance): -2p and
+            // the threshold G2 - |p|^2 + delta per agent
+            f2 QX[NA], QY[NA], QZ[NA];
+            float T[NA];
+            if constexpr (!CLEAR) {
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    const float x = lo_of(X[a]), y = lo_of(Y[a]), z = lo_of(Z[a]);
+                    QX[a] = pk(-2.0f * x, -2.0f * x);
+                    QY[a] = pk(-2.0f * y, -2.0f * y);
+                    QZ[a] = pk(-2.0f * z, -2.0f * z);
+                    const float pp = fmaf(x, x, fmaf(y, y, z * z)), g = G2a[OFF + a];
+                    T[a] = (g - pp) + 0x1p-16f * (fabsf(g) + pp + omax2);
+                }
+            }
+            uint32_t blocks = 0;
+#pragma unroll 2
+            for (int j = 4 * tid; j < cnt_pad; j += 4 * NT) {
+                const float4 x4 = *reinterpret_cast<const float4 *>(sx + j);
+                const float4 y4 = *reinterpret_cast<const float4 *>(sy + j);
+                const float4 z4 = *reinterpret_cast<const float4 *>(sz + j);
+                const f2 ox0 = pk(x4.x, x4.y), oy0 = pk(y4.x, y4.y), oz0 = pk(z4.x, z4.y);
+                const f2 ox1 = pk(x4.z, x4.w), oy1 = pk(y4.z, y4.w), oz1 = pk(z4.z, z4.w);
+                f2 d20[NA], d21[NA];
+                bool hit = false;
+                if constexpr (CLEAR) {
+                    hit = pair_dist<AG, NA, OFF, true>(ox0, oy0, oz0, X, Y, Z, d20, mn, G2a);
+                    hit |= pair_dist<AG, NA, OFF, true>(ox1, oy1, oz1, X, Y, Z, d21, mn, G2a);
+                } else {
+                    const f2 oo0 = fma2(ox0, ox0, fma2(oy0, oy0, mul2(oz0, oz0)));
+                    const f2 oo1 = fma2(ox1, ox1, fma2(oy1, oy1, mul2(oz1, oz1)));
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) {
+                        const f2 e0 = fma2(QX[a], ox0, fma2(QY[a], oy0, fma2(QZ[a], oz0, oo0)));
+                        const f2 e1 = fma2(QX[a], ox1, fma2(QY[a], oy1, fma2(QZ[a], oz1, oo1)));
+                        hit |= fminf(fminf(lo_of(e0), hi_of(e0)), fminf(lo_of(e1), hi_of(e1))) <=
+                               T[a];
+                    }
+                }
+                if (__any_sync(0xffffffffu, hit)) {
+                    if constexpr (!CLEAR) {
+                        pair_dist<AG, NA, OFF, false>(ox0, oy0, oz0, X, Y, Z, d20, mn, G2a);
+                        pair_dist<AG, NA, OFF, false>(ox1, oy1, oz1, X, Y, Z, d21, mn, G2a);
+                    }
+                    pair_heur<AG, NA, OFF, NM>(d20, acc, nR2, G2a, eps, one2);
+                    pair_heur<AG, NA, OFF, NM>(d21, acc, nR2, G2a, eps, one2);
+                    ++blocks;
+                }
+            }
+            if (nheur) *nheur += 2 * blocks * NA;  // blocks of 128 obstacles
+        } else {
 #pragma unroll 3
-        for (int j = 2 * tid; j < cnt_pad; j += 2 * NT) {
-            const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
-            const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
-            const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
-            pair_terms<AG, NA, OFF, NM, CLEAR>(ox, oy, oz, X, Y, Z, acc, mn, nR2, G2a, eps, one2);
+            for (int j = 2 * tid; j < cnt_pad; j += 2 * NT) {
+                const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
+                const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
+                const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
+                pair_terms<AG, NA, OFF, NM, CLEAR>(ox, oy, oz, X, Y, Z, acc, mn, nR2, G2a, eps,
+                                                   one2);
+            }
         }
         if constexpr (TAIL) {
             // tail.begin is even; an odd last obstacle is paired with NaN
@@ -914,6 +1017,7 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar_tma;
     __shared__ __align__(8) uint64_t bar_recv[2][2];  // [half][parity]
+    __shared__ int s_omax2;  // bits of max |o|^2 over the shard
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool exch = warp == NW;
@@ -955,7 +1059,14 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
     // N_O is read on the device; all CTAs of the cluster see the same value,
     // so an early exit is taken by the whole cluster before any DSMEM access.
     const int32_t n_obs = *A.n_obs;
-    const int32_t shard_len = ((n_obs + (int32_t)C - 1) / (int32_t)C + 3) & ~3;
+    // Shards interleave blocks of 128 obstacles: CTA r of a group holds the
+    // blocks r, r + C, r + 2C, ... of S_W, consecutive in its shared memory.
+    // S_W is sorted by voxel key, so the obstacles near a group's agents form
+    // runs of consecutive blocks, which this spreads evenly over the C CTAs
+    // (each CTA's share of the gated pairs, and so its time per step, is
+    // then about the same).  Only the last block of S_W may be partial.
+    const int32_t n_blk = (max(n_obs, 0) + 127) / 128;
+    const int32_t shard_len = (n_blk + (int32_t)C - 1) / (int32_t)C * 128;
     // grid exchange: the last CTA to finish (every CTA has read the epoch by
     // then) advances the epoch for the next launch
     auto finish_grid = [&](uint32_t epoch) {
@@ -965,15 +1076,19 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
             A.xctl[0] = next ? next : 1u;
         }
     };
-    if (n_obs < 0 || n_obs > A.cap || shard_len > A.shard_cap || na > AG || na <= 0) {
+    if (n_obs < 0 || n_obs > A.cap || shard_len > A.shard_cap || (A.shard_cap & 127) ||
+        na > AG || na <= 0) {
         if (tid == 0 && rank == 0) raise_error(A.err, GMAPP_DEVERR_CAPACITY);
         if constexpr (GRID) {
             if (tid == NT) finish_grid(ld_relaxed_u32(A.xctl));
         }
         return;
     }
-    const int32_t start = static_cast<int32_t>(rank) * shard_len;
-    int32_t cnt = min(shard_len, max(0, n_obs - start));
+    const int32_t n_loc = static_cast<int32_t>(rank) < n_blk
+                              ? (n_blk - 1 - static_cast<int32_t>(rank)) / (int32_t)C + 1
+                              : 0;
+    int32_t cnt = n_loc * 128;
+    if (n_loc > 0 && static_cast<uint32_t>(n_blk - 1) % C == rank) cnt -= n_blk * 128 - n_obs;
     float *sx = smem, *sy = smem + A.shard_cap, *sz = smem + 2 * A.shard_cap;
     // per-warp partials of this CTA: [half][NW][AG] records
     float *partbuf = smem + 3 * A.shard_cap;
@@ -991,17 +1106,26 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
     };
 
     if (tid == 0) {
+        s_omax2 = 0;
         mbar_init(&bar_tma, 1);
         for (int i = 0; i < 4; ++i) mbar_init(&bar_recv[i >> 1][i & 1], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    if (cnt > 0 && tid == 0) {
-        const uint32_t bytes = static_cast<uint32_t>((cnt + 3) & ~3) * 4u;
-        mbar_arrive_expect_tx(&bar_tma, 3 * bytes);
-        bulk_g2s(sx, A.ox + start, bytes, &bar_tma);
-        bulk_g2s(sy, A.oy + start, bytes, &bar_tma);
-        bulk_g2s(sz, A.oz + start, bytes, &bar_tma);
+    if (cnt > 0 && tid < 32) {
+        // one bulk copy per block and array, issued by the lanes of warp 0
+        // after the expected byte count (whole blocks, the partial one
+        // rounded up to 4 obstacles: within obs->cap, a multiple of 4)
+        if (tid == 0) mbar_arrive_expect_tx(&bar_tma, 3u * 4u * static_cast<uint32_t>((cnt + 3) & ~3));
+        __syncwarp();
+        for (int32_t i = tid; i < n_loc; i += 32) {
+            const int64_t g = static_cast<int64_t>(rank) + static_cast<int64_t>(i) * C;
+            const int32_t valid = min(128, n_obs - static_cast<int32_t>(128 * g));
+            const uint32_t bytes = static_cast<uint32_t>((valid + 3) & ~3) * 4u;
+            bulk_g2s(sx + 128 * i, A.ox + 128 * g, bytes, &bar_tma);
+            bulk_g2s(sy + 128 * i, A.oy + 128 * g, bytes, &bar_tma);
+            bulk_g2s(sz + 128 * i, A.oz + 128 * g, bytes, &bar_tma);
+        }
     }
 
     // Agent state: lane a < na of every warp reads agent a0 + a; only the
@@ -1053,14 +1177,26 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
             cnt = 0;  // keep the barrier sequence; results are flagged invalid
         }
     }
-    // pad the shard to an even length with NaN (contributes nothing to the
-    // MFI sum), or a far point for APF groups
-    const int32_t cnt_pad = (cnt + 1) & ~1;
-    if (tid == 0 && cnt_pad > cnt) {
+    // pad the shard to a multiple of 128 (shard_cap is one) with NaN
+    // (contributes nothing to the MFI sum), or a far point for APF and
+    // projected-current groups: every warp of the MFI pair loop then runs
+    // the same iterations over whole blocks of 128 obstacles
+    const int32_t cnt_pad = (cnt + 127) & ~127;
+    {
         const float pad = kind != kMfi ? kApfPad : __int_as_float(0x7fc00000);
-        sx[cnt] = pad;
-        sy[cnt] = pad;
-        sz[cnt] = pad;
+        for (int32_t i = cnt + tid; i < cnt_pad; i += blockDim.x) {
+            sx[i] = pad;
+            sy[i] = pad;
+            sz[i] = pad;
+        }
+        // omax2 = max |o|^2 over the shard (bounds the rounding of the
+        // expanded distance of the pair loop's block test)
+        float m = 0.0f;
+        for (int32_t i = tid; i < cnt; i += blockDim.x)
+            m = fmaxf(m, fmaf(sx[i], sx[i], fmaf(sy[i], sy[i], sz[i] * sz[i])));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) atomicMax(&s_omax2, __float_as_int(m));  // m >= 0: ordered as ints
     }
     const float eps = A.eps;
     // every CTA of the cluster is running (barriers initialised, padding and
@@ -1093,6 +1229,8 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
             // are handed to the exchange warp while the other half is
             // computed, and its new positions are ready long before they are
             // needed.
+            uint32_t nheur = 0;  // heuristic pairs of the MFI pair loop, in units of 64
+            const float omax2 = __int_as_float(s_omax2);
             for (int k = 0; k < A.n_steps; ++k) {
                 if (k > 0) named_sync(kPos + 0, kBoth);
                 if constexpr (APF)
@@ -1103,9 +1241,9 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
                                                          part(0) + 6 * (warp * AG), lane, pos,
                                                          vel);
                 else
-                    half_step<AG, H0, 0, NM0, NT, CLEAR, false, false, true>(
+                    half_step<AG, H0, 0, NM0, NT, CLEAR, false, false, true, true>(
                         sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(0) + 2 * (warp * AG), C,
-                        lane, GlobalTail{}, pos);
+                        lane, GlobalTail{}, pos, &nheur, omax2);
                 named_arrive(kPart + 0, kBoth);
                 if (k > 0) named_sync(kPos + 1, kBoth);
                 if constexpr (APF)
@@ -1116,11 +1254,13 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
                                                           part(1) + 6 * (warp * AG), lane, pos,
                                                           vel);
                 else
-                    half_step<AG, H1, H0, NM1, NT, CLEAR, false, false, true>(
+                    half_step<AG, H1, H0, NM1, NT, CLEAR, false, false, true, true>(
                         sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(1) + 2 * (warp * AG), C,
-                        lane, GlobalTail{}, pos);
+                        lane, GlobalTail{}, pos, &nheur, omax2);
                 named_arrive(kPart + 1, kBoth);
             }
+            if (A.heur_pairs && lane == 0 && nheur)
+                atomicAdd(A.heur_pairs, 64ull * nheur);
             return;
         }
         const float h = A.vel_half * A.dt * A.inv_mass;
