@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(NT, 1) kb_rollout(const BatchDev B) {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_item;
+    __shared__ int s_om;  // bits of max |o|^2 of the resident obstacles
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *sx = smem, *sy = smem + B.shard_cap, *sz = smem + 2 * B.shard_cap;
     float *recv = smem + 3 * B.shard_cap;  // [2][NW][AG] x (W, min |d|^2)
@@ -153,7 +154,10 @@ __global__ void __launch_bounds__(NT, 1) kb_rollout(const BatchDev B) {
     __syncthreads();
     uint32_t phase = 0;
     for (;;) {
-        if (tid == 0) s_item = static_cast<int>(atomicAdd(B.head, 1u));
+        if (tid == 0) {
+            s_item = static_cast<int>(atomicAdd(B.head, 1u));
+            s_om = 0;
+        }
         __syncthreads();
         const int it = s_item;
         __syncthreads();
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(NT, 1) kb_rollout(const BatchDev B) {
         int a0, na;
         group_range(packed & 0xffff, Q.n_agents, Q.n_groups, a0, na);
         const int32_t n_obs = *Q.n_obs;
-        if (n_obs < 0 || n_obs > Q.cap || na > AG) {
+        if (n_obs < 0 || n_obs > Q.cap || na > AG || (B.shard_cap & 127)) {
             if (tid == 0) raise_error(B.err, GMAPP_DEVERR_CAPACITY);
             continue;  // uniform across the CTA
         }
@@ -216,19 +220,32 @@ __global__ void __launch_bounds__(NT, 1) kb_rollout(const BatchDev B) {
             }
             phase ^= 1u;
         }
-        const int32_t cnt_pad = (cnt + 1) & ~1;
-        if (tid == 0 && cnt_pad > cnt) {
-            sx[cnt] = __int_as_float(0x7fc00000);
-            sy[cnt] = __int_as_float(0x7fc00000);
-            sz[cnt] = __int_as_float(0x7fc00000);
+        // pad the resident part to whole blocks of 128 (shard_cap is a
+        // multiple of 128) with NaN, which contributes nothing: the pair
+        // loop tests a block per warp; omax2 = max |o|^2 of the resident part
+        const int32_t cnt_pad = (cnt + 127) & ~127;
+        for (int32_t i = cnt + tid; i < cnt_pad; i += NT) {
+            sx[i] = __int_as_float(0x7fc00000);
+            sy[i] = __int_as_float(0x7fc00000);
+            sz[i] = __int_as_float(0x7fc00000);
+        }
+        {
+            float m = 0.0f;
+            for (int32_t i = tid; i < cnt; i += NT)
+                m = fmaxf(m, fmaf(sx[i], sx[i], fmaf(sy[i], sy[i], sz[i] * sz[i])));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) atomicMax(&s_om, __float_as_int(m));  // m >= 0: ordered as ints
         }
         __syncthreads();
+        const float omax2 = __int_as_float(s_om);
         const float h = Q.vel_half * Q.dt * Q.inv_mass;
         const float goal[3] = {Q.goal[0], Q.goal[1], Q.goal[2]};
         for (int k = 0; k < N; ++k) {
             float *rp = recv + (k & 1) * (NW * AG * 2);
-            half_step<AG, AG, 0, NM, NT, CLEAR, true>(sx, sy, sz, cnt_pad, Q.eps, nR2, G2a, p,
-                                                      rp + 2 * (warp * AG), 1u, lane, tail);
+            half_step<AG, AG, 0, NM, NT, CLEAR, true, true, false, true>(
+                sx, sy, sz, cnt_pad, Q.eps, nR2, G2a, p, rp + 2 * (warp * AG), 1u, lane, tail,
+                nullptr, nullptr, omax2);
             __syncthreads();
             float W = 0.0f, md2 = INFINITY;
             half_combine<AG, AG, 0, CLEAR>(rp, NW, lane, W, md2);
@@ -367,9 +384,10 @@ gmapp_status apply_tuning(gmapp_batch *b, int32_t agents_per_item, int32_t threa
         static_cast<size_t>(2) * (threads / 32) * agents_per_item * 2 * sizeof(float);
     const int64_t room = (static_cast<int64_t>(b->ctx->max_smem_optin) -
                           static_cast<int64_t>(fa.sharedSizeBytes + recv_bytes)) / 12;
-    b->shard_cap = static_cast<int32_t>(std::min<int64_t>((b->max_cap + 3) & ~int64_t(3),
-                                                          room & ~int64_t(3)));
-    if (b->shard_cap < 4) {
+    // a multiple of 128: the pair loop tests whole blocks of 128 obstacles
+    b->shard_cap = static_cast<int32_t>(std::min<int64_t>((b->max_cap + 127) & ~int64_t(127),
+                                                          room & ~int64_t(127)));
+    if (b->shard_cap < 128) {
         set_error("gmapp_batch: no shared memory left for obstacles");
         return GMAPP_ERR_CAPACITY;
     }

@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(NT, 1) ks_chunk(const ChunkArgs A) {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_item;
+    __shared__ int s_om;  // bits of max |o|^2 of the resident obstacles
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *sx = smem, *sy = smem + A.shard_cap, *sz = smem + 2 * A.shard_cap;
     float *recv = smem + 3 * A.shard_cap;
@@ -78,7 +79,10 @@ __global__ void __launch_bounds__(NT, 1) ks_chunk(const ChunkArgs A) {
     __syncthreads();
     uint32_t phase = 0;
     for (;;) {
-        if (tid == 0) s_item = static_cast<int>(atomicAdd(A.head, 1u));
+        if (tid == 0) {
+            s_item = static_cast<int>(atomicAdd(A.head, 1u));
+            s_om = 0;
+        }
         __syncthreads();
         const int it = s_item;
         __syncthreads();
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(NT, 1) ks_chunk(const ChunkArgs A) {
         int a0, na;
         group_range(item.group, S.n_agents, S.n_groups, a0, na);
         const int32_t n_obs = *S.n_obs;
-        if (n_obs < 0 || n_obs > S.cap || na > AG) {
+        if (n_obs < 0 || n_obs > S.cap || na > AG || (A.shard_cap & 127)) {
             if (tid == 0) raise_error(A.err, GMAPP_DEVERR_CAPACITY);
             continue;
         }
@@ -141,19 +145,32 @@ __global__ void __launch_bounds__(NT, 1) ks_chunk(const ChunkArgs A) {
             }
             phase ^= 1u;
         }
-        const int32_t cnt_pad = (cnt + 1) & ~1;
-        if (tid == 0 && cnt_pad > cnt) {
-            sx[cnt] = __int_as_float(0x7fc00000);
-            sy[cnt] = __int_as_float(0x7fc00000);
-            sz[cnt] = __int_as_float(0x7fc00000);
+        // pad the resident part to whole blocks of 128 (shard_cap is a
+        // multiple of 128) with NaN, which contributes nothing: the pair
+        // loop tests a block per warp; omax2 = max |o|^2 of the resident part
+        const int32_t cnt_pad = (cnt + 127) & ~127;
+        for (int32_t i = cnt + tid; i < cnt_pad; i += NT) {
+            sx[i] = __int_as_float(0x7fc00000);
+            sy[i] = __int_as_float(0x7fc00000);
+            sz[i] = __int_as_float(0x7fc00000);
+        }
+        {
+            float m = 0.0f;
+            for (int32_t i = tid; i < cnt; i += NT)
+                m = fmaxf(m, fmaf(sx[i], sx[i], fmaf(sy[i], sy[i], sz[i] * sz[i])));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) atomicMax(&s_om, __float_as_int(m));  // m >= 0: ordered as ints
         }
         __syncthreads();
+        const float omax2 = __int_as_float(s_om);
         const float h = S.vel_half * S.dt * S.inv_mass;
         const float goal[3] = {S.goal[0], S.goal[1], S.goal[2]};
         for (int k = item.k0; k < item.k1; ++k) {
             float *rp = recv + (k & 1) * (NW * AG * 2);
-            half_step<AG, AG, 0, NM, NT, false, true>(sx, sy, sz, cnt_pad, S.eps, nR2, G2a, p,
-                                                      rp + 2 * (warp * AG), 1u, lane, tail);
+            half_step<AG, AG, 0, NM, NT, false, true, true, false, true>(
+                sx, sy, sz, cnt_pad, S.eps, nR2, G2a, p, rp + 2 * (warp * AG), 1u, lane, tail,
+                nullptr, nullptr, omax2);
             __syncthreads();
             float W = 0.0f, md2 = INFINITY;
             half_combine<AG, AG, 0, false>(rp, NW, lane, W, md2);
@@ -569,7 +586,11 @@ extern "C" gmapp_status gmapp_server_create(gmapp_ctx *ctx, const gmapp_server_c
     const int64_t room =
         (static_cast<int64_t>(ctx->max_smem_optin) - static_cast<int64_t>(fa.sharedSizeBytes + recv_bytes)) / 12;
     // the culled kernel reads obstacles through the neighbour index (no shard)
-    s->shard_cap = cfg->culled ? 0 : static_cast<int>(std::min<int64_t>(cfg->obs_cap, room & ~int64_t(3)));
+    // a multiple of 128: the pair loop tests whole blocks of 128 obstacles
+    s->shard_cap = cfg->culled ? 0
+                               : static_cast<int>(std::min<int64_t>(
+                                     (static_cast<int64_t>(cfg->obs_cap) + 127) & ~int64_t(127),
+                                     room & ~int64_t(127)));
     s->smem = cfg->culled ? 0 : static_cast<size_t>(s->shard_cap) * 12 + recv_bytes;
     const int threads = cfg->culled ? kServeCullThreads : cfg->threads;
     const int max_groups =
