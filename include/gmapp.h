@@ -280,8 +280,8 @@ typedef struct {
                           computes the clearance m_k.  rollout_agents and
                           rollout_ensemble only. */
     unsigned long long *heur_pairs; /* device counter, or NULL: the launch adds the number
-                          of MFI agent-obstacle pairs whose heuristic terms (rsqrt, clamp,
-                          reciprocal, accumulation) it evaluated.  Every pair's |d|^2 and
+                          of agent-obstacle pairs (of every heuristic) whose heuristic terms
+                          (rsqrt, clamp, reciprocal, accumulation) it evaluated.  Every pair's |d|^2 and
                           gate are evaluated; a warp evaluates the heuristic terms of its
                           block of 64 obstacles only when one of the block's pairs passes
                           an agent's gate (Alg. 1's branch), so this is a multiple of 64

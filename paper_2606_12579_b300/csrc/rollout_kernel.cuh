@@ -67,7 +67,7 @@ struct RolloutArgs {
     float *traj, *p_final, *v_final, *path_len, *clear_pen, *min_clear, *w_trace, *m_trace,
         *f_trace, *ckpt;
     float *cost_terms;  // [5][N_a] sums of the four-term cost, or NULL
-    unsigned long long *heur_pairs;  // MFI pairs whose heuristic terms ran (added), or NULL
+    unsigned long long *heur_pairs;  // pairs whose heuristic terms ran (added), or NULL
     float cost_radius;  // r_c of its goal and obstacle terms
     int32_t shard_cap;   // obstacles one CTA can hold (multiple of 128)
     int32_t n_groups;    // agent groups (clusters, or CTA groups with the grid exchange)
@@ -684,6 +684,100 @@ __device__ __forceinline__ void apf_pair_terms(f2 ox, f2 oy, f2 oz, const f2 (&X
     }
 }
 
+// Block gate test of the APF and projected-current pair loops (the MFI loop
+// in half_step does the same): a lane takes 4 consecutive obstacles (two
+// packed pairs), a warp a block of 128.  Without the clearance the block is
+// tested on the expanded distance |o|^2 - 2 p.o against G2 - |p|^2 + delta
+// (block_setup); with it, on the exact |d|^2 (+1e-30, as the terms compute
+// it) of every pair, which also updates the clearance minimum.  The
+// heuristic terms then run only for blocks with a pair inside a gate;
+// outside the gate they add exact signed zeros, so the sums are unchanged.
+template <int AG, int NA, int OFF>
+__device__ __forceinline__ void block_setup(const f2 (&X)[NA], const f2 (&Y)[NA],
+                                            const f2 (&Z)[NA], const float (&G2a)[AG],
+                                            float omax2, f2 (&QX)[NA], f2 (&QY)[NA],
+                                            f2 (&QZ)[NA], float (&T)[NA]) {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const float x = lo_of(X[a]), y = lo_of(Y[a]), z = lo_of(Z[a]);
+        QX[a] = pk(-2.0f * x, -2.0f * x);
+        QY[a] = pk(-2.0f * y, -2.0f * y);
+        QZ[a] = pk(-2.0f * z, -2.0f * z);
+        const float pp = fmaf(x, x, fmaf(y, y, z * z)), g = G2a[OFF + a];
+        T[a] = (g - pp) + 0x1p-16f * (fabsf(g) + pp + omax2);
+    }
+}
+
+template <int NA>
+__device__ __forceinline__ bool block_test_expanded(f2 ox0, f2 oy0, f2 oz0, f2 ox1, f2 oy1,
+                                                    f2 oz1, const f2 (&QX)[NA],
+                                                    const f2 (&QY)[NA], const f2 (&QZ)[NA],
+                                                    const float (&T)[NA]) {
+    const f2 oo0 = fma2(ox0, ox0, fma2(oy0, oy0, mul2(oz0, oz0)));
+    const f2 oo1 = fma2(ox1, ox1, fma2(oy1, oy1, mul2(oz1, oz1)));
+    bool hit = false;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const f2 e0 = fma2(QX[a], ox0, fma2(QY[a], oy0, fma2(QZ[a], oz0, oo0)));
+        const f2 e1 = fma2(QX[a], ox1, fma2(QY[a], oy1, fma2(QZ[a], oz1, oo1)));
+        hit |= fminf(fminf(lo_of(e0), hi_of(e0)), fminf(lo_of(e1), hi_of(e1))) <= T[a];
+    }
+    return hit;
+}
+
+template <int AG, int NA, int OFF>
+__device__ __forceinline__ bool block_test_exact(f2 ox, f2 oy, f2 oz, const f2 (&X)[NA],
+                                                 const f2 (&Y)[NA], const f2 (&Z)[NA],
+                                                 float (&mn)[NA], const float (&G2a)[AG],
+                                                 f2 tiny2) {
+    bool hit = false;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const f2 dx = sub2(X[a], ox), dy = sub2(Y[a], oy), dz = sub2(Z[a], oz);
+        const f2 d2 = fma2(dz, dz, fma2(dy, dy, fma2(dx, dx, tiny2)));
+        const float m = fminf(lo_of(d2), hi_of(d2));
+        hit |= m <= G2a[OFF + a];
+        mn[a] = fminf(mn[a], m);
+    }
+    return hit;
+}
+
+// The voting pair loop over the shard (cnt_pad a multiple of 128): terms(ox,
+// oy, oz) evaluates and accumulates the heuristic terms of one packed pair.
+// Returns the number of blocks whose terms ran.
+template <int AG, int NA, int OFF, int NT, bool CLEAR, class Terms>
+__device__ __forceinline__ uint32_t vote_loop(const float *sx, const float *sy, const float *sz,
+                                          int cnt_pad, const f2 (&X)[NA], const f2 (&Y)[NA],
+                                          const f2 (&Z)[NA], float (&mn)[NA],
+                                          const float (&G2a)[AG], float omax2, f2 tiny2,
+                                          Terms &&terms) {
+    f2 QX[NA], QY[NA], QZ[NA];
+    float T[NA];
+    if constexpr (!CLEAR) block_setup<AG, NA, OFF>(X, Y, Z, G2a, omax2, QX, QY, QZ, T);
+    uint32_t blocks = 0;
+#pragma unroll 2
+    for (int j = 4 * threadIdx.x; j < cnt_pad; j += 4 * NT) {
+        const float4 x4 = *reinterpret_cast<const float4 *>(sx + j);
+        const float4 y4 = *reinterpret_cast<const float4 *>(sy + j);
+        const float4 z4 = *reinterpret_cast<const float4 *>(sz + j);
+        const f2 ox0 = pk(x4.x, x4.y), oy0 = pk(y4.x, y4.y), oz0 = pk(z4.x, z4.y);
+        const f2 ox1 = pk(x4.z, x4.w), oy1 = pk(y4.z, y4.w), oz1 = pk(z4.z, z4.w);
+        bool hit;
+        if constexpr (CLEAR) {
+            hit = block_test_exact<AG, NA, OFF>(ox0, oy0, oz0, X, Y, Z, mn, G2a, tiny2);
+            hit |= block_test_exact<AG, NA, OFF>(ox1, oy1, oz1, X, Y, Z, mn, G2a, tiny2);
+        } else {
+            hit = block_test_expanded<NA>(ox0, oy0, oz0, ox1, oy1, oz1, QX, QY, QZ, T);
+        }
+        if (__any_sync(0xffffffffu, hit)) {
+            terms(ox0, oy0, oz0);
+            terms(ox1, oy1, oz1);
+            ++blocks;
+        }
+    }
+    return blocks;
+}
+
 // APF counterpart of half_step (positions from shared memory pos[3][AG]):
 // partial force sums of this thread's obstacle pairs, reduced over the warp
 // (one transposed butterfly per component) and stored as one record
@@ -692,7 +786,8 @@ template <int AG, int NA, int OFF, int NT, bool CLEAR>
 __device__ __forceinline__ void half_step_apf(const float *sx, const float *sy, const float *sz,
                                               int cnt_pad, const float (&cRa)[AG],
                                               const f2 (&ird2)[AG], const float (&G2a)[AG],
-                                              float *part_slot0, int lane, const float *pos) {
+                                              float *part_slot0, int lane, const float *pos,
+                                              float omax2, uint32_t *nheur) {
     if constexpr (NA > 0) {
         constexpr int P = pow2ceil(NA);
         const int tid = threadIdx.x;
@@ -708,14 +803,14 @@ __device__ __forceinline__ void half_step_apf(const float *sx, const float *sy, 
             mn[a] = INFINITY;
         }
         const f2 tiny2 = pk(1e-30f, 1e-30f);
-#pragma unroll 2
-        for (int j = 2 * tid; j < cnt_pad; j += 2 * NT) {
-            const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
-            const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
-            const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
-            apf_pair_terms<AG, NA, OFF, CLEAR>(ox, oy, oz, X, Y, Z, fx, fy, fz, mn, cRa, ird2, G2a,
-                                               tiny2);
-        }
+        (void)tid;
+        *nheur += 2 * NA * vote_loop<AG, NA, OFF, NT, CLEAR>(
+                                   sx, sy, sz, cnt_pad, X, Y, Z, mn, G2a, omax2, tiny2,
+                                          [&](f2 ox, f2 oy, f2 oz) {
+                                              apf_pair_terms<AG, NA, OFF, false>(
+                                                  ox, oy, oz, X, Y, Z, fx, fy, fz, mn, cRa, ird2,
+                                                  G2a, tiny2);
+                                          });
         float v0[P], v1[P], v2[P], vm[P];
 #pragma unroll
         for (int a = 0; a < P; ++a) {
@@ -907,7 +1002,8 @@ template <int AG, int NA, int OFF, int NT, bool CLEAR>
 __device__ __forceinline__ void half_step_proj(const float *sx, const float *sy, const float *sz,
                                                int cnt_pad, float eps, const f2 (&nR2)[AG],
                                                const float (&G2a)[AG], float *part_slot0,
-                                               int lane, const float *pos, const float *vel) {
+                                               int lane, const float *pos, const float *vel,
+                                               float omax2, uint32_t *nheur) {
     if constexpr (NA > 0) {
         constexpr int P = pow2ceil(NA);
         const int tid = threadIdx.x;
@@ -927,14 +1023,14 @@ __device__ __forceinline__ void half_step_proj(const float *sx, const float *sy,
             mn[a] = INFINITY;
         }
         const f2 tiny2 = pk(1e-30f, 1e-30f);
-#pragma unroll 2
-        for (int j = 2 * tid; j < cnt_pad; j += 2 * NT) {
-            const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
-            const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
-            const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
-            proj_pair_terms<AG, NA, OFF, CLEAR>(ox, oy, oz, X, Y, Z, VX, VY, VZ, ax, ay, az, ab,
-                                                mn, nR2, G2a, eps, tiny2);
-        }
+        (void)tid;
+        *nheur += 2 * NA * vote_loop<AG, NA, OFF, NT, CLEAR>(
+                                   sx, sy, sz, cnt_pad, X, Y, Z, mn, G2a, omax2, tiny2,
+                                          [&](f2 ox, f2 oy, f2 oz) {
+                                              proj_pair_terms<AG, NA, OFF, false>(
+                                                  ox, oy, oz, X, Y, Z, VX, VY, VZ, ax, ay, az, ab,
+                                                  mn, nR2, G2a, eps, tiny2);
+                                          });
         float v0[P], v1[P], v2[P], v3[P], vm[P];
 #pragma unroll
         for (int a = 0; a < P; ++a) {
@@ -1229,17 +1325,18 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
             // are handed to the exchange warp while the other half is
             // computed, and its new positions are ready long before they are
             // needed.
-            uint32_t nheur = 0;  // heuristic pairs of the MFI pair loop, in units of 64
+            uint32_t nheur = 0;  // heuristic pairs of the pair loops, in units of 64
             const float omax2 = __int_as_float(s_omax2);
             for (int k = 0; k < A.n_steps; ++k) {
                 if (k > 0) named_sync(kPos + 0, kBoth);
                 if constexpr (APF)
                     half_step_apf<AG, H0, 0, NT, CLEAR>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
-                                                        part(0) + 4 * (warp * AG), lane, pos);
+                                                        part(0) + 4 * (warp * AG), lane, pos,
+                                                        omax2, &nheur);
                 else if constexpr (PROJ)
                     half_step_proj<AG, H0, 0, NT, CLEAR>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
                                                          part(0) + 6 * (warp * AG), lane, pos,
-                                                         vel);
+                                                         vel, omax2, &nheur);
                 else
                     half_step<AG, H0, 0, NM0, NT, CLEAR, false, false, true, true>(
                         sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(0) + 2 * (warp * AG), C,
@@ -1248,11 +1345,12 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
                 if (k > 0) named_sync(kPos + 1, kBoth);
                 if constexpr (APF)
                     half_step_apf<AG, H1, H0, NT, CLEAR>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
-                                                         part(1) + 4 * (warp * AG), lane, pos);
+                                                         part(1) + 4 * (warp * AG), lane, pos,
+                                                         omax2, &nheur);
                 else if constexpr (PROJ)
                     half_step_proj<AG, H1, H0, NT, CLEAR>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
                                                           part(1) + 6 * (warp * AG), lane, pos,
-                                                          vel);
+                                                          vel, omax2, &nheur);
                 else
                     half_step<AG, H1, H0, NM1, NT, CLEAR, false, false, true, true>(
                         sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(1) + 2 * (warp * AG), C,

@@ -131,3 +131,28 @@ def test_heuristic_pair_count_covers_the_gated_pairs(gm):
     far["p0"] = np.ascontiguousarray(ag["p0"] + np.float32(5.0))
     f, _ = _both(gm, obs, to_dev_agents(far), w["params"], TABLE)
     assert int(f["heur_pairs"].item()) == 0
+
+
+@pytest.mark.parametrize("n_proj,n_apf", [(0, 48), (48, 0), (24, 24)])
+def test_ensemble_identical_with_and_without_clearance(gm, n_proj, n_apf):
+    """APF and projected-current groups (and MFI beside them): the block
+    test of the clearance variant (exact |d|^2) and of the plain one
+    (expanded distance) give bit-identical force records and trajectories."""
+    import torch
+    w = synth.tabletop_workload(n_agents=96, n_steps=200)
+    ag = synth.ensemble_agents(w["agents"], n_apf)
+    obs = gm.filter_cloud(torch.from_numpy(w["xyz"]).cuda(), w["T"], w["workspace"], cap=80000)
+    dev = to_dev_agents(ag)
+    outs = []
+    for clear in (False, True):
+        o = gm.alloc_rollout_out(96, 200, want_traj=True, want_trace=True, want_clear=clear)
+        if not clear:
+            o["m_trace"] = None
+        gm.rollout_ensemble(obs, dev, n_apf, w["params"], out=o, tuning=TABLE, n_proj=n_proj)
+        outs.append(o)
+    gm.sync()
+    a, b = outs
+    for key in ("traj", "w_trace", "f_trace"):
+        assert np.array_equal(a[key].cpu().numpy().view(np.uint32),
+                              b[key].cpu().numpy().view(np.uint32)), key
+    assert np.count_nonzero(b["w_trace"].cpu().numpy()) > 1000
