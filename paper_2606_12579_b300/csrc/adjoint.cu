@@ -120,7 +120,7 @@ __device__ __forceinline__ float and_bits(float v, uint32_t m) {
 // jg, jg + 1) for NA agents: W += [gate] u, grad += [gate, unclamped]
 // u^2/|d| (p - o) (negated later), nearest obstacle.  TAIL: the pair holds
 // the shard's odd last obstacle twice and its hi lane counts for nothing.
-template <int NA, int NM, bool TAIL>
+template <int NA, int NM, bool TAIL, bool ARGMIN = true, bool MASKD = false>
 __device__ __forceinline__ void adj_pair(f2 ox, f2 oy, f2 oz, int jg, const f2 (&X)[NA],
                                          const f2 (&Y)[NA], const f2 (&Z)[NA],
                                          const f2 (&nR2)[NA], const float (&G2)[NA], float eps,
@@ -147,18 +147,56 @@ __device__ __forceinline__ void adj_pair(f2 ox, f2 oy, f2 oz, int jg, const f2 (
         W[a] = add2(W[a], pk(and_bits(lo_of(u), gl), and_bits(hi_of(u), gh)));
         const f2 t = mul2(mul2(u, u), r);  // u^2 / |d|
         const f2 q = pk(and_bits(lo_of(t), ql), and_bits(hi_of(t), qh));
-        GX[a] = fma2(q, dx, GX[a]);
-        GY[a] = fma2(q, dy, GY[a]);
-        GZ[a] = fma2(q, dz, GZ[a]);
-        if (d2l < bd[a]) {  // ascending index per thread: strict < keeps the lowest
+        if (MASKD) {
+            // d masked like q: a NaN pad obstacle has a NaN direction, and a
+            // zero weight times NaN would still be NaN
+            GX[a] = fma2(q, pk(and_bits(lo_of(dx), ql), and_bits(hi_of(dx), qh)), GX[a]);
+            GY[a] = fma2(q, pk(and_bits(lo_of(dy), ql), and_bits(hi_of(dy), qh)), GY[a]);
+            GZ[a] = fma2(q, pk(and_bits(lo_of(dz), ql), and_bits(hi_of(dz), qh)), GZ[a]);
+        } else {
+            GX[a] = fma2(q, dx, GX[a]);
+            GY[a] = fma2(q, dy, GY[a]);
+            GZ[a] = fma2(q, dz, GZ[a]);
+        }
+        if (ARGMIN) {
+            if (d2l < bd[a]) {  // ascending index per thread: strict < keeps the lowest
+                bd[a] = d2l;
+                bj[a] = jg;
+            }
+            if (!TAIL && d2h < bd[a]) {
+                bd[a] = d2h;
+                bj[a] = jg + 1;
+            }
+        }
+    }
+}
+
+// Block gate test of one packed pair (Alg. 1's branch, taken per warp for a
+// block of 128 obstacles): the exact |d|^2 of each pair (as adj_pair forms
+// it), the nearest obstacle, and whether a pair passes an agent's gate.
+// Outside the gate adj_pair adds masked zeros (W, gradient), so evaluating
+// it only for blocks with a pair inside leaves the sums unchanged.
+template <int NA>
+__device__ __forceinline__ bool adj_test(f2 ox, f2 oy, f2 oz, int jg, const f2 (&X)[NA],
+                                         const f2 (&Y)[NA], const f2 (&Z)[NA],
+                                         const float (&G2)[NA], float (&bd)[NA], int (&bj)[NA]) {
+    bool hit = false;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const f2 dx = sub2(X[a], ox), dy = sub2(Y[a], oy), dz = sub2(Z[a], oz);
+        const f2 d2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        const float d2l = lo_of(d2), d2h = hi_of(d2);
+        hit |= fminf(d2l, d2h) <= G2[a];
+        if (d2l < bd[a]) {
             bd[a] = d2l;
             bj[a] = jg;
         }
-        if (!TAIL && d2h < bd[a]) {
+        if (d2h < bd[a]) {
             bd[a] = d2h;
             bj[a] = jg + 1;
         }
     }
+    return hit;
 }
 
 // One half step of the recompute for NA agents (OFF .. OFF+NA-1 of the
@@ -190,19 +228,54 @@ __device__ __forceinline__ void adj_half(const float *sx, const float *sy, const
             bj[a] = INT_MAX;
         }
         const f2 one2 = pk(1.0f, 1.0f);
-        const int cnt_even = cnt & ~1;
+        // the shard is padded with NaN to whole blocks of 128 (a lane takes 4
+        // consecutive obstacles, a warp a block); NaN pairs add nothing and
+        // never become the nearest obstacle
+        const int cnt_pad = (cnt + 127) & ~127;
+        // an agent without a gate (r_d = inf) passes every block: then every
+        // block's terms run without the test
+        bool every = false;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) every |= G2[a] == INFINITY;
+        if (every) {
+            // the real obstacles only (no NaN pads): pairs, then an odd last one
+            const int cnt_even = cnt & ~1;
 #pragma unroll 2
-        for (int j = 2 * tid; j < cnt_even; j += 2 * NT) {
-            const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
-            const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
-            const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
-            adj_pair<NA, NM, false>(ox, oy, oz, j0 + j, X, Y, Z, nR2, G2, eps, one2, W, GX, GY,
-                                    GZ, bd, bj);
+            for (int j = 2 * tid; j < cnt_even; j += 2 * NT) {
+                const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
+                const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
+                const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
+                adj_pair<NA, NM, false>(ox, oy, oz, j0 + j, X, Y, Z, nR2, G2, eps, one2, W, GX,
+                                        GY, GZ, bd, bj);
+            }
+            if ((cnt & 1) && tid == (cnt_even / 2) % NT) {
+                const float x = sx[cnt_even], y = sy[cnt_even], z = sz[cnt_even];
+                adj_pair<NA, NM, true>(pk(x, x), pk(y, y), pk(z, z), j0 + cnt_even, X, Y, Z, nR2,
+                                       G2, eps, one2, W, GX, GY, GZ, bd, bj);
+            }
         }
-        if ((cnt & 1) && tid == (cnt_even / 2) % NT) {
-            const float x = sx[cnt_even], y = sy[cnt_even], z = sz[cnt_even];
-            adj_pair<NA, NM, true>(pk(x, x), pk(y, y), pk(z, z), j0 + cnt_even, X, Y, Z, nR2,
-                                   G2, eps, one2, W, GX, GY, GZ, bd, bj);
+#pragma unroll 1
+        for (int j = every ? cnt_pad : 4 * tid; j < cnt_pad; j += 4 * NT) {
+            const float4 x4 = *reinterpret_cast<const float4 *>(sx + j);
+            const float4 y4 = *reinterpret_cast<const float4 *>(sy + j);
+            const float4 z4 = *reinterpret_cast<const float4 *>(sz + j);
+            const f2 ox0 = pk(x4.x, x4.y), oy0 = pk(y4.x, y4.y), oz0 = pk(z4.x, z4.y);
+            const f2 ox1 = pk(x4.z, x4.w), oy1 = pk(y4.z, y4.w), oz1 = pk(z4.z, z4.w);
+            bool hit = adj_test<NA>(ox0, oy0, oz0, j0 + j, X, Y, Z, G2, bd, bj);
+            hit |= adj_test<NA>(ox1, oy1, oz1, j0 + j + 2, X, Y, Z, G2, bd, bj);
+            if (__any_sync(0xffffffffu, hit)) {
+                // reloaded from shared memory: keeps the block's coordinates
+                // out of registers across the test
+                const float4 u4 = *reinterpret_cast<const float4 *>(sx + j);
+                const float4 v4 = *reinterpret_cast<const float4 *>(sy + j);
+                const float4 w4 = *reinterpret_cast<const float4 *>(sz + j);
+                adj_pair<NA, NM, false, false, true>(pk(u4.x, u4.y), pk(v4.x, v4.y),
+                                                     pk(w4.x, w4.y), j0 + j, X, Y, Z, nR2, G2,
+                                                     eps, one2, W, GX, GY, GZ, bd, bj);
+                adj_pair<NA, NM, false, false, true>(pk(u4.z, u4.w), pk(v4.z, v4.w),
+                                                     pk(w4.z, w4.w), j0 + j + 2, X, Y, Z, nR2,
+                                                     G2, eps, one2, W, GX, GY, GZ, bd, bj);
+            }
         }
         float vw[P], vx[P], vy[P], vz[P], vd[P];
         int vj[P];
@@ -341,7 +414,7 @@ __global__ void __launch_bounds__(NT + 32, 1) k_adjoint(const AdjArgs A) {
             A.xctl[0] = next ? next : 1u;
         }
     };
-    if (n_obs < 0 || n_obs > A.cap || shard_len > A.shard_cap) {
+    if (n_obs < 0 || n_obs > A.cap || shard_len > A.shard_cap || (A.shard_cap & 127)) {
         if (tid == 0 && rank == 0 && group == 0) raise_error(A.err, GMAPP_DEVERR_CAPACITY);
         if (tid == NT) finish_grid(ld_relaxed_u32(A.xctl));
         return;
@@ -365,6 +438,14 @@ __global__ void __launch_bounds__(NT + 32, 1) k_adjoint(const AdjArgs A) {
         if (tid == 0) raise_error(A.err, GMAPP_DEVERR_TIMEOUT);
         cnt = 0;
     }
+    // pad the shard to whole blocks of 128 with NaN (shard_cap is a multiple
+    // of 128)
+    for (int32_t i = cnt + tid; i < ((cnt + 127) & ~127); i += blockDim.x) {
+        sx[i] = __int_as_float(0x7fc00000);
+        sy[i] = __int_as_float(0x7fc00000);
+        sz[i] = __int_as_float(0x7fc00000);
+    }
+    __syncthreads();
     const float eps = A.eps;
     const int N = A.n_steps, K = A.K, nseg = (N + K - 1) / K;
     const int n = A.n_agents;
@@ -650,7 +731,7 @@ extern "C" gmapp_status rollout_adjoint(gmapp_ctx *ctx, const gmapp_obstacles *o
     int C = 0, agp = 1, G = 0;
     size_t dyn = 0;
     for (int c = 1; c <= kMaxCluster && !fn; ++c) {
-        const int64_t shard = ((obs->cap + c - 1) / c + 3) & ~int64_t(3);
+        const int64_t shard = ((obs->cap + c - 1) / c + 127) & ~int64_t(127);
         const size_t bytes = static_cast<size_t>(shard) * 3 * sizeof(float);
         cudaFuncAttributes fa;
         GMAPP_CHECK_CUDA(cudaFuncGetAttributes(
@@ -709,7 +790,8 @@ extern "C" gmapp_status rollout_adjoint(gmapp_ctx *ctx, const gmapp_obstacles *o
     A.g_c = out->g_c;
     A.cost = out->cost;
     A.rec = static_cast<float *>(workspace);
-    A.shard_cap = static_cast<int32_t>(((obs->cap + C - 1) / C + 3) & ~int64_t(3));
+    // a multiple of 128: the recompute loop tests whole blocks of 128 obstacles
+    A.shard_cap = static_cast<int32_t>(((obs->cap + C - 1) / C + 127) & ~int64_t(127));
     A.n_agent_groups = n_agent_groups;
     A.group_ctas = C;
     A.xbuf = ctx->d_xbuf;

@@ -391,6 +391,8 @@ __device__ __forceinline__ void half_step(const float *sx, const float *sy, cons
                 }
             }
             uint32_t blocks = 0;
+            // an agent without a gate (r_d = inf) passes every block: then
+            // every pair runs the terms, in the plain loop (no test)
 #pragma unroll 2
             for (int j = 4 * tid; j < cnt_pad; j += 4 * NT) {
                 const float4 x4 = *reinterpret_cast<const float4 *>(sx + j);
@@ -426,6 +428,7 @@ __device__ __forceinline__ void half_step(const float *sx, const float *sy, cons
             }
             if (nheur) *nheur += 2 * blocks * NA;  // blocks of 128 obstacles
         } else {
+            uint32_t its = 0;
 #pragma unroll 3
             for (int j = 2 * tid; j < cnt_pad; j += 2 * NT) {
                 const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
@@ -433,7 +436,9 @@ __device__ __forceinline__ void half_step(const float *sx, const float *sy, cons
                 const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
                 pair_terms<AG, NA, OFF, NM, CLEAR>(ox, oy, oz, X, Y, Z, acc, mn, nR2, G2a, eps,
                                                    one2);
+                ++its;
             }
+            if (nheur) *nheur += its * NA;  // every pair, 64 per iteration and agent
         }
         if constexpr (TAIL) {
             // tail.begin is even; an odd last obstacle is paired with NaN
@@ -755,6 +760,23 @@ __device__ __forceinline__ uint32_t vote_loop(const float *sx, const float *sy, 
     float T[NA];
     if constexpr (!CLEAR) block_setup<AG, NA, OFF>(X, Y, Z, G2a, omax2, QX, QY, QZ, T);
     uint32_t blocks = 0;
+    // an agent without a gate (r_d = inf) passes every block: then every
+    // pair runs the terms, in the plain loop (no test)
+    bool every = false;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) every |= G2a[OFF + a] == INFINITY;
+    if (every) {
+#pragma unroll 2
+        for (int j = 2 * threadIdx.x; j < cnt_pad; j += 2 * NT) {
+            const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
+            const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
+            const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
+            if constexpr (CLEAR)  // the clearance minimum of every pair
+                block_test_exact<AG, NA, OFF>(ox, oy, oz, X, Y, Z, mn, G2a, tiny2);
+            terms(ox, oy, oz);
+        }
+        return static_cast<uint32_t>(cnt_pad / 128 / (NT / 32));
+    }
 #pragma unroll 2
     for (int j = 4 * threadIdx.x; j < cnt_pad; j += 4 * NT) {
         const float4 x4 = *reinterpret_cast<const float4 *>(sx + j);
@@ -1327,35 +1349,49 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
             // needed.
             uint32_t nheur = 0;  // heuristic pairs of the pair loops, in units of 64
             const float omax2 = __int_as_float(s_omax2);
-            for (int k = 0; k < A.n_steps; ++k) {
-                if (k > 0) named_sync(kPos + 0, kBoth);
-                if constexpr (APF)
-                    half_step_apf<AG, H0, 0, NT, CLEAR>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
-                                                        part(0) + 4 * (warp * AG), lane, pos,
-                                                        omax2, &nheur);
-                else if constexpr (PROJ)
-                    half_step_proj<AG, H0, 0, NT, CLEAR>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
-                                                         part(0) + 6 * (warp * AG), lane, pos,
-                                                         vel, omax2, &nheur);
-                else
-                    half_step<AG, H0, 0, NM0, NT, CLEAR, false, false, true, true>(
-                        sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(0) + 2 * (warp * AG), C,
-                        lane, GlobalTail{}, pos, &nheur, omax2);
-                named_arrive(kPart + 0, kBoth);
-                if (k > 0) named_sync(kPos + 1, kBoth);
-                if constexpr (APF)
-                    half_step_apf<AG, H1, H0, NT, CLEAR>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
-                                                         part(1) + 4 * (warp * AG), lane, pos,
-                                                         omax2, &nheur);
-                else if constexpr (PROJ)
-                    half_step_proj<AG, H1, H0, NT, CLEAR>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
-                                                          part(1) + 6 * (warp * AG), lane, pos,
-                                                          vel, omax2, &nheur);
-                else
-                    half_step<AG, H1, H0, NM1, NT, CLEAR, false, false, true, true>(
-                        sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(1) + 2 * (warp * AG), C,
-                        lane, GlobalTail{}, pos, &nheur, omax2);
-                named_arrive(kPart + 1, kBoth);
+            auto steps = [&](auto vote_tag) {
+                constexpr bool VOTE = decltype(vote_tag)::value;
+                for (int k = 0; k < A.n_steps; ++k) {
+                    if (k > 0) named_sync(kPos + 0, kBoth);
+                    if constexpr (APF)
+                        half_step_apf<AG, H0, 0, NT, CLEAR>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
+                                                            part(0) + 4 * (warp * AG), lane, pos,
+                                                            omax2, &nheur);
+                    else if constexpr (PROJ)
+                        half_step_proj<AG, H0, 0, NT, CLEAR>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
+                                                             part(0) + 6 * (warp * AG), lane, pos,
+                                                             vel, omax2, &nheur);
+                    else
+                        half_step<AG, H0, 0, NM0, NT, CLEAR, false, false, true, VOTE>(
+                            sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(0) + 2 * (warp * AG), C,
+                            lane, GlobalTail{}, pos, &nheur, omax2);
+                    named_arrive(kPart + 0, kBoth);
+                    if (k > 0) named_sync(kPos + 1, kBoth);
+                    if constexpr (APF)
+                        half_step_apf<AG, H1, H0, NT, CLEAR>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
+                                                             part(1) + 4 * (warp * AG), lane, pos,
+                                                             omax2, &nheur);
+                    else if constexpr (PROJ)
+                        half_step_proj<AG, H1, H0, NT, CLEAR>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
+                                                              part(1) + 6 * (warp * AG), lane, pos,
+                                                              vel, omax2, &nheur);
+                    else
+                        half_step<AG, H1, H0, NM1, NT, CLEAR, false, false, true, VOTE>(
+                            sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(1) + 2 * (warp * AG), C,
+                            lane, GlobalTail{}, pos, &nheur, omax2);
+                    named_arrive(kPart + 1, kBoth);
+                }
+            };
+            // an MFI group with an agent without a gate (r_d = inf) passes
+            // every block: its pair loops run without the block test
+            bool every = false;
+#pragma unroll
+            for (int a = 0; a < AG; ++a) every |= G2a[a] == INFINITY;
+            if constexpr (!APF && !PROJ) {
+                if (every) steps(std::false_type{});
+                else steps(std::true_type{});
+            } else {
+                steps(std::true_type{});
             }
             if (A.heur_pairs && lane == 0 && nheur)
                 atomicAdd(A.heur_pairs, 64ull * nheur);
