@@ -156,3 +156,31 @@ def test_ensemble_identical_with_and_without_clearance(gm, n_proj, n_apf):
         assert np.array_equal(a[key].cpu().numpy().view(np.uint32),
                               b[key].cpu().numpy().view(np.uint32)), key
     assert np.count_nonzero(b["w_trace"].cpu().numpy()) > 1000
+
+
+def test_clearance_equals_the_batched_kernel_without_gated_pairs(gm):
+    """The clearance minimum of the rollout kernel (per-block exact test,
+    blocks dealt round-robin over the CTAs) against the batched kernel (one
+    CTA, resident obstacles in order).  With r_d below eps no pair passes a
+    gate (W = 0), so the trajectories are the attractor's alone and equal in
+    both kernels: the clearance sums and minima must then be equal bit for
+    bit, as the minimum of the same exact |d|^2 values."""
+    import torch
+    w = synth.tabletop_workload(n_agents=40, n_steps=300)
+    ag = dict(w["agents"])
+    ag["r_d"] = np.full(40, 0.5e-3, np.float32)          # below eps: no gate
+    rng = np.random.default_rng(11)
+    ag["p0"] = (ag["p0"] + rng.normal(scale=0.05, size=ag["p0"].shape)).astype(np.float32)
+    dev = to_dev_agents(ag)
+    xyz = torch.from_numpy(w["xyz"]).cuda()
+    obs = gm.filter_cloud(xyz, w["T"], w["workspace"], cap=80000)
+    a = gm.rollout_agents(obs, dev, w["params"], tuning=TABLE, want_clear=True)
+    b = gm.Batch([{"xyz": xyz, "T": w["T"], "ws": w["workspace"], "agents": dev,
+                   "prm": w["params"], "obs_cap": 80000}], want_clear=True)
+    b.run()
+    gm.sync()
+    o = b.results[0]["out"]
+    for key in ("traj", "clear_pen", "min_clear"):
+        assert np.array_equal(a[key].cpu().numpy().view(np.uint32),
+                              o[key].cpu().numpy().view(np.uint32)), key
+    assert np.all(np.isfinite(a["min_clear"].cpu().numpy()))
