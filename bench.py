@@ -868,9 +868,10 @@ def bench_culled(gm, args, n_frames=16, ticks=32):
     """Plans with spatial culling vs the all-pairs plan on the tabletop
     query: per plan a new frame (a ring of distinct frames in HBM) ->
     filter_cloud -> [gmapp_grid_index -> rollout_agents_culled |
-    rollout_agents] -> score_and_select, 256 agents x 500 steps, r_d = 5 cm.
-    Culling skips the pairs beyond the gate, so it is reported as plans/s
-    (interactions/s counts all pairs)."""
+    rollout_agents_blockcull | rollout_agents] -> score_and_select, 256
+    agents x 500 steps, r_d = 5 cm.  Culling skips the pairs beyond the
+    gate, so it is reported as plans/s (interactions/s counts all pairs).
+    The block-culled rollout takes the fastest of a few launch shapes."""
     import torch
     base, frames_np = make_workload(n_frames, 0)
     prm, ws = base["params"], base["workspace"]
@@ -902,13 +903,38 @@ def bench_culled(gm, args, n_frames=16, ticks=32):
         gm.rollout_agents(obs, agents, prm, out=out_a, tuning=tun)
         gm.score_and_select(out_a, prm, out=sel_a)
 
+    # block culling: the per-step exchange sets its pace, so shapes with the
+    # cluster exchange and more agents per group are among the candidates
+    out_b = gm.alloc_rollout_out(na, nk, want_traj=True, want_clear=False)
+    sel_b = gm.score_and_select(out_a, prm)
+    cur = torch.cuda.current_stream()
+    best_b = None
+    for cand in [tuple(tun), (5, 9, 384, 0), (5, 10, 384, 0), (4, 8, 384, 0), (6, 11, 384, 1),
+                 (8, 16, 256, 0), (8, 16, 256, 1)]:
+        try:
+            gm.rollout_agents_blockcull(obs, agents, prm, out=out_b, tuning=cand)
+            gm.sync()
+        except gm.GmappError:
+            continue
+        tb = _events(torch, cur, lambda c=cand: gm.rollout_agents_blockcull(
+            obs, agents, prm, out=out_b, tuning=c), 3)
+        if best_b is None or tb < best_b[0]:
+            best_b = (tb, cand)
+    tun_b = best_b[1]
+
+    def plan_block(i):
+        gm.filter_cloud(frames[i % n_frames], base["T"], ws, out=obs, workspace=wsp)
+        gm.rollout_agents_blockcull(obs, agents, prm, out=out_b, tuning=tun_b)
+        gm.score_and_select(out_b, prm, out=sel_b)
+
     for i in range(3):
         plan_culled(i)
         plan_all(i)
+        plan_block(i)
     gm.sync()
-    cur = torch.cuda.current_stream()
     t_c = _events(torch, cur, lambda it=iter(range(ticks)): plan_culled(next(it)), ticks)
     t_a = _events(torch, cur, lambda it=iter(range(ticks)): plan_all(next(it)), ticks)
+    t_b = _events(torch, cur, lambda it=iter(range(ticks)): plan_block(next(it)), ticks)
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     ev[0].record(cur)
     for _ in range(5):
@@ -918,10 +944,15 @@ def bench_culled(gm, args, n_frames=16, ticks=32):
     t_roll = ev[0].elapsed_time(ev[1]) / 1e3 / 5
     gm.sync()
     same = int((sel_c["best"] == sel_a["best"]).item())
+    same_b = int((sel_b["best"] == sel_a["best"]).item())
     return {"workload": f"{ticks} plans over {n_frames} tabletop frames; 256 agents x 500 steps, "
                         "r_d = 5 cm",
             "culled": {"ms_per_plan": 1e3 * t_c, "plans_per_s": 1.0 / t_c,
                        "rollout_ms": 1e3 * t_roll},
+            "block_culled": {"ms_per_plan": 1e3 * t_b, "plans_per_s": 1.0 / t_b,
+                             "rollout_ms": 1e3 * best_b[0], "tuning": list(tun_b),
+                             "speedup_vs_all_pairs": t_a / t_b,
+                             "last_plan_same_agent": bool(same_b)},
             "all_pairs": {"ms_per_plan": 1e3 * t_a, "plans_per_s": 1.0 / t_a,
                           "tuning": list(tun)},
             "speedup": t_a / t_c, "last_plan_same_agent": bool(same)}

@@ -378,6 +378,27 @@ gmapp_status rollout_agents_tuned(gmapp_ctx *ctx, const gmapp_obstacles *obs,
                                   gmapp_rollout_out *out, const gmapp_tuning *tune,
                                   gmapp_stream stream);
 
+/* rollout_agents with spatial culling over the key-sorted obstacle set
+ * (Alg. 1's gate: pairs with s_j > r_d contribute nothing).  Each CTA keeps
+ * the bounding box of every block of 128 consecutive obstacles of its
+ * shard; each step, a warp visits only the blocks whose box lies within an
+ * agent's gate radius r_d + R (widened by 2^-12 for rounding) and evaluates
+ * their pairs exactly as rollout_agents does, in the same order.  So W, the
+ * forces, the trajectories and the path lengths equal those of
+ * rollout_agents at the same launch shape bit for bit.  The clearance m_k
+ * is exact when the nearest obstacle lies within the agent's reach r_d + R,
+ * else it is the smallest distance among the visited obstacles (>= r_d) or
+ * +inf when none was visited.  Obstacles sorted by voxel key (filter_cloud's
+ * order) make the blocks compact; any order gives the same results, culling
+ * less.  An agent with r_d = inf cannot be culled: its group evaluates
+ * every pair.  tune: the launch shape, or NULL for the one rollout_agents
+ * would pick.  Arguments, outputs and errors as for rollout_agents. */
+gmapp_status rollout_agents_blockcull(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                                      const gmapp_agents *agents,
+                                      const gmapp_rollout_params *prm,
+                                      gmapp_rollout_out *out, const gmapp_tuning *tune,
+                                      gmapp_stream stream);
+
 /* Autotuner of the launch shape (for the batched/served pattern: the shape
  * is picked by measurement).  Ranks every shape that fits obs->cap by the
  * library's cost model (slowest CTA's pair count, co-resident clusters,

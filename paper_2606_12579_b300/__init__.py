@@ -374,6 +374,25 @@ def rollout_agents(obs: Obstacles, agents: dict, prm, out: dict | None = None,
     return out
 
 
+def rollout_agents_blockcull(obs: Obstacles, agents: dict, prm, out: dict | None = None,
+                             want_traj: bool = True, want_trace: bool = False,
+                             want_clear: bool = True, tuning=None, stream=None) -> dict:
+    """rollout_agents visiting, each step, only the blocks of 128
+    key-sorted obstacles whose bounding box lies within an agent's gate
+    (spatial culling, Alg. 1's gate); W and the trajectories equal
+    rollout_agents' at the same launch shape bit for bit."""
+    ctx = context()
+    na = int(agents["k_r"].numel())
+    if out is None:
+        out = alloc_rollout_out(na, int(prm.n_steps), want_traj, want_trace, want_clear)
+    ob, ag, pr, os_ = obs._struct(), _agents_struct(agents), _params_struct(prm), _out_struct(out)
+    t = _abi.Tuning(*[int(v) for v in tuning]) if tuning is not None else None
+    check(_abi.load().rollout_agents_blockcull(ctx.handle, C.byref(ob), C.byref(ag), C.byref(pr),
+                                               C.byref(os_), C.byref(t) if t is not None else None,
+                                               _stream(stream)), "rollout_agents_blockcull")
+    return out
+
+
 def rollout_ensemble(obs: Obstacles, agents: dict, n_apf: int, prm, out: dict | None = None,
                      want_traj: bool = True, want_trace: bool = False, want_clear: bool = True,
                      tuning=None, stream=None, n_proj: int = 0) -> dict:

@@ -131,8 +131,10 @@ bool resolve(gmapp_ctx *ctx, int64_t cap, int n_agents, const gmapp_tuning &t, b
     // each (4 AG floats apart, keeping the 16-byte alignment) + the
     // four-term cost sums [kCostAcc][AG]
     const size_t rec = kinds.level() == 2 ? 6 : kinds.level() == 1 ? 4 : 2;
+    // + the per-block bounding boxes of the shard [shard_cap / 128][6]
     s->smem = (static_cast<size_t>(s->shard_cap) * 3 + 2 * rec * nw * s->ag +
-               4 * rec * t.cluster * s->ag + static_cast<size_t>(8 + kCostAcc) * s->ag) *
+               4 * rec * t.cluster * s->ag + static_cast<size_t>(8 + kCostAcc) * s->ag +
+               6 * static_cast<size_t>(s->shard_cap / 128)) *
               sizeof(float);
     return s->smem + static_smem(s->fn) <= static_cast<size_t>(ctx->max_smem_optin);
 }
@@ -325,7 +327,8 @@ bool wants_clear(const gmapp_rollout_out *out) {
 
 gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agents *ag,
                     const gmapp_rollout_params *prm, gmapp_rollout_out *out,
-                    const gmapp_tuning &t, gmapp_stream stream, Kinds kinds = Kinds{}) {
+                    const gmapp_tuning &t, gmapp_stream stream, Kinds kinds = Kinds{},
+                    bool box_cull = false) {
     Shape s;
     if (!resolve(ctx, obs->cap, ag->n, t, wants_clear(out), &s, kinds)) {
         set_error("rollout_agents: launch shape (cluster %d, agents %d, threads %d, exchange %d) "
@@ -373,6 +376,7 @@ gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agen
     A.ckpt = out->ckpt;
     A.cost_terms = out->cost_terms;
     A.heur_pairs = out->heur_pairs;
+    A.box_cull = box_cull ? 1 : 0;
     A.cost_radius = prm->cost_radius;
     A.shard_cap = s.shard_cap;
     A.n_groups = s.groups;
@@ -583,6 +587,26 @@ extern "C" gmapp_status rollout_agents(gmapp_ctx *ctx, const gmapp_obstacles *ob
     st = pick_tuning_impl(ctx, obs->cap, agents->n, wants_clear(out), &t);
     if (st != GMAPP_OK) return st;
     return launch(ctx, obs, agents, prm, out, t, stream);
+}
+
+extern "C" gmapp_status rollout_agents_blockcull(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                                                 const gmapp_agents *agents,
+                                                 const gmapp_rollout_params *prm,
+                                                 gmapp_rollout_out *out, const gmapp_tuning *tune,
+                                                 gmapp_stream stream) {
+    if (!ctx) {
+        set_error("rollout_agents_blockcull: NULL ctx");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    gmapp_status st = validate(obs, agents, prm, out);
+    if (st != GMAPP_OK) return st;
+    gmapp_tuning t;
+    if (tune) {
+        t = *tune;
+    } else if ((st = pick_tuning_impl(ctx, obs->cap, agents->n, wants_clear(out), &t)) != GMAPP_OK) {
+        return st;
+    }
+    return launch(ctx, obs, agents, prm, out, t, stream, Kinds{}, true);
 }
 
 extern "C" gmapp_status rollout_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *obs,

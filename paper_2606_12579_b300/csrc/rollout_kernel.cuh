@@ -68,6 +68,7 @@ struct RolloutArgs {
         *f_trace, *ckpt;
     float *cost_terms;  // [5][N_a] sums of the four-term cost, or NULL
     unsigned long long *heur_pairs;  // pairs whose heuristic terms ran (added), or NULL
+    int32_t box_cull;    // MFI groups visit only the blocks whose bounding box meets a gate
     float cost_radius;  // r_c of its goal and obstacle terms
     int32_t shard_cap;   // obstacles one CTA can hold (multiple of 128)
     int32_t n_groups;    // agent groups (clusters, or CTA groups with the grid exchange)
@@ -342,14 +343,15 @@ struct GlobalTail {
 // more blocks than needed may run the heuristic terms, which then add
 // signed zeros).  omax2 bounds |o|^2 over the shard.
 template <int AG, int NA, int OFF, int NM, int NT, bool CLEAR, bool TAIL = false,
-          bool SHIP = true, bool POS = false, bool VOTE = false>
+          bool SHIP = true, bool POS = false, bool VOTE = false, bool BOX = false>
 __device__ __forceinline__ void half_step(const float *sx, const float *sy, const float *sz,
                                           int cnt_pad, float eps, const f2 (&nR2)[AG],
                                           const float (&G2a)[AG], const float (&p)[3],
                                           float *recv_slot0, uint32_t C, int lane,
                                           GlobalTail tail = GlobalTail{},
                                           const float *pos = nullptr,
-                                          uint32_t *nheur = nullptr, float omax2 = 0.0f) {
+                                          uint32_t *nheur = nullptr, float omax2 = 0.0f,
+                                          const float *boxes = nullptr) {
     if constexpr (NA > 0) {
         constexpr int P = pow2ceil(NA);
         const int tid = threadIdx.x;
@@ -374,7 +376,56 @@ __device__ __forceinline__ void half_step(const float *sx, const float *sy, cons
             mn[a] = INFINITY;
         }
         const f2 one2 = pk(1.0f, 1.0f);
-        if constexpr (VOTE) {
+        if constexpr (VOTE && BOX) {
+            // Culled: a lane tests one block's bounding box (boxes[6 b]: lo
+            // xyz, hi xyz) against the gates of the half's agents, and the
+            // warp visits only the blocks whose box meets a gate, in the same
+            // order and lane layout as the voting loop (a skipped block could
+            // only add signed zeros).  The gate radius is widened by 2^-12
+            // (relative) against the rounding of the box and pair distances.
+            float TB[NA];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) TB[a] = fmaf(G2a[OFF + a], 1.0f + 0x1p-12f, 1e-12f);
+            constexpr int NWc = NT / 32;
+            const int w = tid >> 5;
+            const int n_it = (cnt_pad / 128 - w + NWc - 1) / NWc;  // blocks w, w + NWc, ...
+            uint32_t blocks = 0;
+            for (int base = 0; base < n_it; base += 32) {
+                const int i = base + lane;
+                bool near = false;
+                if (i < n_it) {
+                    const float *bx = boxes + 6 * (w + i * NWc);
+                    const float lx = bx[0], ly = bx[1], lz = bx[2], hx = bx[3], hy = bx[4],
+                                hz = bx[5];
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) {
+                        const float px = lo_of(X[a]), py = lo_of(Y[a]), pz = lo_of(Z[a]);
+                        const float dx = fmaxf(fmaxf(lx - px, px - hx), 0.0f);
+                        const float dy = fmaxf(fmaxf(ly - py, py - hy), 0.0f);
+                        const float dz = fmaxf(fmaxf(lz - pz, pz - hz), 0.0f);
+                        near |= fmaf(dz, dz, fmaf(dy, dy, dx * dx)) <= TB[a];
+                    }
+                }
+                uint32_t m = __ballot_sync(0xffffffffu, near);
+                while (m) {
+                    const int l = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int j = (w + (base + l) * NWc) * 128 + 4 * lane;
+                    const float4 x4 = *reinterpret_cast<const float4 *>(sx + j);
+                    const float4 y4 = *reinterpret_cast<const float4 *>(sy + j);
+                    const float4 z4 = *reinterpret_cast<const float4 *>(sz + j);
+                    f2 d20[NA], d21[NA];
+                    pair_dist<AG, NA, OFF, CLEAR>(pk(x4.x, x4.y), pk(y4.x, y4.y), pk(z4.x, z4.y),
+                                                  X, Y, Z, d20, mn, G2a);
+                    pair_dist<AG, NA, OFF, CLEAR>(pk(x4.z, x4.w), pk(y4.z, y4.w), pk(z4.z, z4.w),
+                                                  X, Y, Z, d21, mn, G2a);
+                    pair_heur<AG, NA, OFF, NM>(d20, acc, nR2, G2a, eps, one2);
+                    pair_heur<AG, NA, OFF, NM>(d21, acc, nR2, G2a, eps, one2);
+                    ++blocks;
+                }
+            }
+            if (nheur) *nheur += 2 * blocks * NA;
+        } else if constexpr (VOTE) {
             // block test of the expanded distance (no clearance): -2p and
             // the threshold G2 - |p|^2 + delta per agent
             f2 QX[NA], QY[NA], QZ[NA];
@@ -1218,6 +1269,8 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
     float *vel = pos + 4 * AG;
     // four-term cost sums of the exchange warp (lane = agent): [kCostAcc][AG]
     float *cacc = vel + 4 * AG;
+    // per-block bounding boxes of the shard (culled rollouts): [blocks][6]
+    float *boxes = cacc + kCostAcc * AG;
     auto part = [&](int h) { return partbuf + h * (SR * NW * AG); };
     auto slot = [&](int h, int par) {
         return recv + (h * 2 + par) * (SR * static_cast<int>(C) * AG);
@@ -1315,6 +1368,33 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) atomicMax(&s_omax2, __float_as_int(m));  // m >= 0: ordered as ints
+        if (A.box_cull) {
+            // bounding box of every block (NaN pads ignored; an all-pad
+            // block gets an empty box), one warp per block
+            const int nwt = static_cast<int>(blockDim.x) / 32;
+            for (int b = warp; b < cnt_pad / 128; b += nwt) {
+                float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = b * 128 + 4 * lane + q;
+                    lo[0] = fminf(lo[0], sx[i]);
+                    lo[1] = fminf(lo[1], sy[i]);
+                    lo[2] = fminf(lo[2], sz[i]);
+                    hi[0] = fmaxf(hi[0], sx[i]);
+                    hi[1] = fmaxf(hi[1], sy[i]);
+                    hi[2] = fmaxf(hi[2], sz[i]);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+                        hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+                    }
+                }
+                if (lane < 6) boxes[6 * b + lane] = lane < 3 ? lo[lane] : hi[lane - 3];
+            }
+        }
     }
     const float eps = A.eps;
     // every CTA of the cluster is running (barriers initialised, padding and
@@ -1349,8 +1429,9 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
             // needed.
             uint32_t nheur = 0;  // heuristic pairs of the pair loops, in units of 64
             const float omax2 = __int_as_float(s_omax2);
-            auto steps = [&](auto vote_tag) {
+            auto steps = [&](auto vote_tag, auto box_tag) {
                 constexpr bool VOTE = decltype(vote_tag)::value;
+                constexpr bool BOX = decltype(box_tag)::value;
                 for (int k = 0; k < A.n_steps; ++k) {
                     if (k > 0) named_sync(kPos + 0, kBoth);
                     if constexpr (APF)
@@ -1362,9 +1443,9 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
                                                              part(0) + 6 * (warp * AG), lane, pos,
                                                              vel, omax2, &nheur);
                     else
-                        half_step<AG, H0, 0, NM0, NT, CLEAR, false, false, true, VOTE>(
+                        half_step<AG, H0, 0, NM0, NT, CLEAR, false, false, true, VOTE, BOX>(
                             sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(0) + 2 * (warp * AG), C,
-                            lane, GlobalTail{}, pos, &nheur, omax2);
+                            lane, GlobalTail{}, pos, &nheur, omax2, boxes);
                     named_arrive(kPart + 0, kBoth);
                     if (k > 0) named_sync(kPos + 1, kBoth);
                     if constexpr (APF)
@@ -1376,9 +1457,9 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
                                                               part(1) + 6 * (warp * AG), lane, pos,
                                                               vel, omax2, &nheur);
                     else
-                        half_step<AG, H1, H0, NM1, NT, CLEAR, false, false, true, VOTE>(
+                        half_step<AG, H1, H0, NM1, NT, CLEAR, false, false, true, VOTE, BOX>(
                             sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(1) + 2 * (warp * AG), C,
-                            lane, GlobalTail{}, pos, &nheur, omax2);
+                            lane, GlobalTail{}, pos, &nheur, omax2, boxes);
                     named_arrive(kPart + 1, kBoth);
                 }
             };
@@ -1388,10 +1469,11 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
 #pragma unroll
             for (int a = 0; a < AG; ++a) every |= G2a[a] == INFINITY;
             if constexpr (!APF && !PROJ) {
-                if (every) steps(std::false_type{});
-                else steps(std::true_type{});
+                if (every) steps(std::false_type{}, std::false_type{});
+                else if (A.box_cull) steps(std::true_type{}, std::true_type{});
+                else steps(std::true_type{}, std::false_type{});
             } else {
-                steps(std::true_type{});
+                steps(std::true_type{}, std::false_type{});
             }
             if (A.heur_pairs && lane == 0 && nheur)
                 atomicAdd(A.heur_pairs, 64ull * nheur);
