@@ -152,7 +152,7 @@ gmapp_status prepare(const Shape &s) {
 cudaLaunchConfig_t config(const Shape &s, cudaLaunchAttribute *attr, gmapp_stream stream) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(s.groups * s.cluster, 1, 1);
-    cfg.blockDim = dim3(s.threads + 32, 1, 1);  // compute warps + the exchange warp
+    cfg.blockDim = dim3(s.threads + 32 * kExchWarps, 1, 1);  // compute + exchange warps
     cfg.dynamicSmemBytes = s.smem;
     cfg.stream = stream;
     if (s.grid) {
@@ -177,7 +177,7 @@ int max_active_clusters(gmapp_ctx *ctx, const Shape &s) {
     if (s.grid) {
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void *>(s.fn),
-                                                          s.threads + 32, s.smem) != cudaSuccess) {
+                                                          s.threads + 32 * kExchWarps, s.smem) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }

@@ -51,6 +51,8 @@ constexpr int kMaxEnsembleAgents = 12;
 constexpr int kMfi = 0, kApf = 1, kProj = 2;
 // rows of the per-agent four-term cost sums kept in shared memory
 constexpr int kCostAcc = 11;
+// exchange warps of a rollout CTA: one per agent half
+constexpr int kExchWarps = 2;
 
 struct RolloutArgs {
     const float *ox, *oy, *oz;
@@ -1172,24 +1174,26 @@ __device__ __forceinline__ void agent_step_apf(float (&p)[3], float (&v)[3], flo
 // MFI with the per-obstacle projected current.  Every group is homogeneous,
 // so the branch between the pair loops is uniform per CTA.
 template <int AG, int NM, int NT, bool CLEAR, bool GRID, int EK = 0>
-__global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
-    constexpr int NW = NT / 32;       // compute warps; warp NW is the exchange warp
+__global__ void __launch_bounds__(NT + 32 * kExchWarps, 1) k_rollout(const RolloutArgs A) {
+    constexpr int NW = NT / 32;       // compute warps; warps NW + h exchange half h
     constexpr int H0 = (AG + 1) / 2;  // agents [0, H0) form half 0, [H0, AG) half 1
     constexpr int H1 = AG - H0;
     // SFU agents split evenly over the halves (each half's pair loop then
     // keeps the same SFU/FMA balance)
     constexpr int NM0 = (NM + 1) / 2 < H0 ? (NM + 1) / 2 : H0;
     constexpr int NM1 = NM - NM0 < H1 ? NM - NM0 : H1;
-    // named barriers: partials of half h ready (compute -> exchange), and
-    // positions of half h ready (exchange -> compute)
-    constexpr int kPart = 1, kPos = 3, kBoth = NT + 32;
+    // named barriers: partials of half h ready (compute -> exchange warp h),
+    // and positions of half h ready (exchange warp h -> compute); the two
+    // exchange warps join on kJoin before the grid's epoch is advanced
+    constexpr int kPart = 1, kPos = 3, kJoin = 5, kBoth = NT + 32;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar_tma;
     __shared__ __align__(8) uint64_t bar_recv[2][2];  // [half][parity]
     __shared__ int s_omax2;  // bits of max |o|^2 over the shard
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool exch = warp == NW;
+    const bool exch = warp >= NW;
+    const int xh = warp - NW;  // exchange warps: the half they own
     uint32_t rank, C, group;
     if constexpr (GRID) {
         C = static_cast<uint32_t>(A.group_ctas);
@@ -1317,14 +1321,14 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
         rd = A.r_d[i];
         // s = max(d - R, eps) <= r_d  <=>  d^2 <= (r_d + R)^2  when r_d >= eps
         G2 = rd >= A.eps ? (rd + R) * (rd + R) : -1.0f;
-        if (rank == 0 && exch && A.traj) {
+        if (rank == 0 && xh == 0 && A.traj) {
             float *t = A.traj + (size_t)i * (A.n_steps + 1) * 3;
             t[0] = p[0];
             t[1] = p[1];
             t[2] = p[2];
         }
     }
-    if (exch && lane < AG) {
+    if (xh == 0 && lane < AG) {
         pos[lane] = p[0];
         pos[AG + lane] = p[1];
         pos[2 * AG + lane] = p[2];
@@ -1492,7 +1496,9 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
         // five outputs, 5-7 F_{k-1}, 8-10 f_r,k-1.
         float *cs = cacc + lane;
         auto cv = [&](int row) -> float & { return cs[row * AG]; };
-        if (CLEAR && A.cost_terms && lane < AG) {
+        // this exchange warp's agents: lanes of its half
+        const bool mine = xh == 0 ? lane < H0 : (lane >= H0 && lane < AG);
+        if (CLEAR && A.cost_terms && mine) {
             for (int r = 0; r < kCostAcc; ++r) cv(r) = 0.0f;
         }
         // rec: W (MFI), the force sum f (APF), or S and B (projected
@@ -1629,25 +1635,28 @@ __global__ void __launch_bounds__(NT + 32, 1) k_rollout(const RolloutArgs A) {
                                                                k, ok, rec[0], md2, A.spin_limit);
             }
         };
-        for (int k = 0; k < A.n_steps; ++k) {
-            const int par = k & 1;
-            float rec[4] = {0.0f, 0.0f, 0.0f, 0.0f}, md2 = INFINITY;
-            named_sync(kPart + 0, kBoth);
-            exchange(std::integral_constant<int, 0>{}, k, par, rec, md2);
-            if (lane < H0 && lane < na) integrate(k, rec, md2);
-            __syncwarp();
-            if (k + 1 < A.n_steps) named_arrive(kPos + 0, kBoth);
-            named_sync(kPart + 1, kBoth);
-            exchange(std::integral_constant<int, 1>{}, k, par, rec, md2);
-            if (lane >= H0 && lane < na) integrate(k, rec, md2);
-            __syncwarp();
-            if (k + 1 < A.n_steps) named_arrive(kPos + 1, kBoth);
-        }
+        // exchange warp h: half h of every step, one phase apart from the
+        // other half's warp (the two halves' exchanges overlap)
+        auto xloop = [&](auto half) {
+            constexpr int HH = decltype(half)::value;
+            for (int k = 0; k < A.n_steps; ++k) {
+                const int par = k & 1;
+                float rec[4] = {0.0f, 0.0f, 0.0f, 0.0f}, md2 = INFINITY;
+                named_sync(kPart + HH, kBoth);
+                exchange(half, k, par, rec, md2);
+                if (mine && lane < na) integrate(k, rec, md2);
+                __syncwarp();
+                if (k + 1 < A.n_steps) named_arrive(kPos + HH, kBoth);
+            }
+        };
+        if (xh == 0) xloop(std::integral_constant<int, 0>{});
+        else xloop(std::integral_constant<int, 1>{});
         if (!ok) raise_error(A.err, GMAPP_DEVERR_TIMEOUT);
+        named_sync(kJoin, 32 * kExchWarps);
         if constexpr (GRID) {
-            if (lane == 0) finish_grid(epoch);
+            if (xh == 0 && lane == 0) finish_grid(epoch);
         }
-        if (rank == 0 && lane < na) {
+        if (rank == 0 && mine && lane < na) {
             const int i = a0 + lane, n = A.n_agents;
             for (int d = 0; d < 3; ++d) {
                 A.p_final[d * n + i] = p[d];
