@@ -10,7 +10,10 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libgmapp.so")
+# GMAPP_BOUNDS_CHECK=1 selects the bounds-checked build (index checks that
+# set GMAPP_DEVERR_BOUNDS; see build.py)
+LIB_PATH = os.path.join(HERE, "libgmapp_bc.so" if os.environ.get("GMAPP_BOUNDS_CHECK") == "1"
+                        else "libgmapp.so")
 
 OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_READY = range(6)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CAPACITY", 3: "CUDA", 4: "TIMEOUT", 5: "NOT_READY"}

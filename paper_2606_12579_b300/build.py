@@ -3,6 +3,11 @@
 Each ``csrc/*.cu`` is compiled to an object in ``_build/`` (in parallel),
 then linked into ``paper_2606_12579_b300/libgmapp.so``.  The CUDA runtime is
 linked statically, so the library needs only the driver at run time.
+
+``build(bounds_check=True)`` builds the bounds-checked variant
+``libgmapp_bc.so`` (objects in ``_build_bc/``, compiled with
+-DGMAPP_BOUNDS_CHECK: index checks that set GMAPP_DEVERR_BOUNDS in the
+device error word); the package loads it when GMAPP_BOUNDS_CHECK=1.
 """
 
 from __future__ import annotations
@@ -17,6 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libgmapp.so")
+LIB_BC = os.path.join(HERE, "libgmapp_bc.so")
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -32,9 +38,9 @@ def _deps():
         os.path.join(os.path.dirname(HERE), "include", "gmapp.h")]
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-    cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj]
+def _compile(src: str, verbose: bool, bdir: str = BUILD, extra=()) -> str:
+    obj = os.path.join(bdir, os.path.basename(src) + ".o")
+    cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -45,18 +51,22 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= max(os.path.getmtime(p) for p in _deps())):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, bounds_check: bool = False) -> str:
+    lib = LIB_BC if bounds_check else LIB
+    bdir = BUILD + "_bc" if bounds_check else BUILD
+    extra = ("-DGMAPP_BOUNDS_CHECK",) if bounds_check else ()
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= max(os.path.getmtime(p) for p in _deps())):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), _sources()))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, verbose, bdir, extra), _sources()))
+    tmp = lib + ".tmp"
     subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                bounds_check="--bounds-check" in sys.argv))

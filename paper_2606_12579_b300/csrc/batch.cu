@@ -526,6 +526,7 @@ extern "C" gmapp_status gmapp_batch_create(gmapp_ctx *ctx, const gmapp_query *qu
         D.fa.nx = Qh.ws.dims[0];
         D.fa.ny = Qh.ws.dims[1];
         D.fa.nz = Qh.ws.dims[2];
+        D.fa.err = ctx->d_err;
         D.pt_blk0 = static_cast<int32_t>(pt_map.size());
         D.pt_nblk = static_cast<int32_t>(std::max<int64_t>(
             1, std::min<int64_t>((Qh.n_raw / 4 + kThreads - 1) / kThreads, kMaxPointBlocksPerQuery)));

@@ -101,6 +101,7 @@ gmapp_status filter_impl(const char *who, gmapp_ctx *ctx, const gmapp_sensor_clo
     A.nx = ws->dims[0];
     A.ny = ws->dims[1];
     A.nz = ws->dims[2];
+    A.err = ctx->d_err;
     out->r_O = 0.5f * ws->voxel;  // exact: scaling by a power of two
 
     char *base = static_cast<char *>(workspace);
@@ -312,6 +313,7 @@ extern "C" gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, co
     A.nx = ws->dims[0];
     A.ny = ws->dims[1];
     A.nz = ws->dims[2];
+    A.err = nullptr;  // no context: index checks of the bounds-checked build are silent here
     out->r_O = 0.5f * ws->voxel;
 
     char *base = static_cast<char *>(sym.scratch);

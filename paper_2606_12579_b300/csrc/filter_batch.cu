@@ -140,6 +140,7 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
         D.fa.nx = J.ws.dims[0];
         D.fa.ny = J.ws.dims[1];
         D.fa.nz = J.ws.dims[2];
+        D.fa.err = ctx->d_err;
         D.pt_blk0 = static_cast<int32_t>(pt_map.size());
         D.pt_nblk = static_cast<int32_t>(std::max<int64_t>(
             1, std::min<int64_t>((J.n_raw / 4 + kThreads - 1) / kThreads, kMaxPointBlocksPerJob)));

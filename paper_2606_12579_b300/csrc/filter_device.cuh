@@ -36,6 +36,7 @@ struct FilterArgs {
     float voxel;
     float dimf[3];
     uint32_t nx, ny, nz;
+    uint32_t *err;  // device error word (index checks of the bounds-checked build)
 };
 
 // The correctly rounded quotient x / voxel from the correctly rounded
@@ -131,15 +132,21 @@ __device__ __forceinline__ void keys_range(const float *__restrict__ xyz, int64_
     const int64_t n4 = n / 4;
     const int64_t stride = nblk * (int64_t)kThreads;
     const float inv_voxel = __frcp_rn(A.voxel);
+    // every later bitmap word, rank and output index derives from a key:
+    // the bounds-checked build checks each key against the grid
+    const int64_t cells = static_cast<int64_t>(A.nx) * A.ny * A.nz;
+    auto chk = [&](uint32_t k) {
+        return k == kInvalid || bc_ok(k, cells, A.err) ? k : kInvalid;
+    };
 #pragma unroll 2
     for (int64_t g = blk * (int64_t)kThreads + threadIdx.x; g < n4; g += stride) {
         const float4 *src = reinterpret_cast<const float4 *>(xyz) + 3 * g;
         float4 a0 = __ldcs(src), a1 = __ldcs(src + 1), a2 = __ldcs(src + 2);
         uint4 k;
-        k.x = voxel_key(a0.x, a0.y, a0.z, A, inv_voxel);
-        k.y = voxel_key(a0.w, a1.x, a1.y, A, inv_voxel);
-        k.z = voxel_key(a1.z, a1.w, a2.x, A, inv_voxel);
-        k.w = voxel_key(a2.y, a2.z, a2.w, A, inv_voxel);
+        k.x = chk(voxel_key(a0.x, a0.y, a0.z, A, inv_voxel));
+        k.y = chk(voxel_key(a0.w, a1.x, a1.y, A, inv_voxel));
+        k.z = chk(voxel_key(a1.z, a1.w, a2.x, A, inv_voxel));
+        k.w = chk(voxel_key(a2.y, a2.z, a2.w, A, inv_voxel));
         reinterpret_cast<uint4 *>(keys)[g] = k;
         BitMerge m;
         m.add(k.x, bitmap);
@@ -151,7 +158,7 @@ __device__ __forceinline__ void keys_range(const float *__restrict__ xyz, int64_
     // ragged tail (n % 4 points)
     int64_t t = 4 * n4 + blk * (int64_t)kThreads + threadIdx.x;
     if (t < n) {
-        uint32_t k = voxel_key(xyz[3 * t], xyz[3 * t + 1], xyz[3 * t + 2], A, inv_voxel);
+        uint32_t k = chk(voxel_key(xyz[3 * t], xyz[3 * t + 1], xyz[3 * t + 2], A, inv_voxel));
         keys[t] = k;
         if (k != kInvalid) atomicOr(&bitmap[k >> 5], 1u << (k & 31));
     }

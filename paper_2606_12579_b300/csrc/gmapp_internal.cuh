@@ -212,6 +212,20 @@ __device__ __forceinline__ void raise_error(uint32_t *err, uint32_t bits) {
     if (err) atomicOr(err, bits);
 }
 
+// Index checks of the bounds-checked build (compiled with
+// -DGMAPP_BOUNDS_CHECK): an index outside [0, n) sets GMAPP_DEVERR_BOUNDS
+// in the device error word and the caller skips the access.  In the normal
+// build the check is the constant true and compiles to nothing.
+#ifdef GMAPP_BOUNDS_CHECK
+__device__ __forceinline__ bool bc_ok(int64_t i, int64_t n, uint32_t *err) {
+    if (i >= 0 && i < n) return true;
+    raise_error(err, GMAPP_DEVERR_BOUNDS);
+    return false;
+}
+#else
+__device__ __forceinline__ constexpr bool bc_ok(int64_t, int64_t, uint32_t *) { return true; }
+#endif
+
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Bytes of the grid-exchange slots for up to `ctas` CTAs: per CTA

@@ -376,6 +376,7 @@ gmapp_status launch(gmapp_ctx *ctx, const gmapp_obstacles *obs, const gmapp_agen
     A.ckpt = out->ckpt;
     A.cost_terms = out->cost_terms;
     A.heur_pairs = out->heur_pairs;
+    A.xbuf_words = static_cast<int64_t>(xbuf_bytes(ctx->sm_count) / sizeof(uint64_t));
     A.box_cull = box_cull ? 1 : 0;
     A.cost_radius = prm->cost_radius;
     A.shard_cap = s.shard_cap;

@@ -81,6 +81,7 @@ struct RolloutArgs {
     int32_t group_ctas;  // grid exchange: CTAs per group (C)
     uint64_t *xbuf;      // grid exchange: tagged slots [G][2][2][C][AG][2]
     uint32_t *xctl;      // grid exchange: launch epoch, finished-CTA counter
+    int64_t xbuf_words;   // grid exchange: 64-bit words of xbuf
     uint32_t spin_limit;  // polls of an mbarrier wait before it gives up
     uint32_t poll_limit;  // polls of a grid-exchange word before it gives up
     uint32_t *err;
@@ -1279,6 +1280,24 @@ __global__ void __launch_bounds__(NT + 32 * kExchWarps, 1) k_rollout(const Rollo
     auto slot = [&](int h, int par) {
         return recv + (h * 2 + par) * (SR * static_cast<int>(C) * AG);
     };
+    {
+        // bounds-checked build: the invariants the index arithmetic below
+        // relies on (uniform over the group's CTAs, so they leave together)
+        uint32_t dyn;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        constexpr int kGroupWords = 4 * (EK > 1 ? 6 : EK == 1 ? 4 : 2);
+        const bool in = bc_ok(cnt > 0 ? ((cnt + 127) & ~127) - 1 : 0, A.shard_cap, A.err) &&
+                        bc_ok(a0 + na - 1, A.n_agents, A.err) &&
+                        bc_ok((boxes + 6 * (A.shard_cap / 128)) - smem - 1, dyn / 4, A.err) &&
+                        (!GRID || bc_ok((static_cast<int64_t>(group) + 1) * kGroupWords * C * AG - 1,
+                                        A.xbuf_words, A.err));
+        if (!in) {
+            if constexpr (GRID) {
+                if (tid == NT) finish_grid(ld_relaxed_u32(A.xctl));
+            }
+            return;
+        }
+    }
 
     if (tid == 0) {
         s_omax2 = 0;
@@ -1297,6 +1316,7 @@ __global__ void __launch_bounds__(NT + 32 * kExchWarps, 1) k_rollout(const Rollo
             const int64_t g = static_cast<int64_t>(rank) + static_cast<int64_t>(i) * C;
             const int32_t valid = min(128, n_obs - static_cast<int32_t>(128 * g));
             const uint32_t bytes = static_cast<uint32_t>((valid + 3) & ~3) * 4u;
+            if (!bc_ok(128 * g + bytes / 4 - 1, A.cap, A.err)) continue;  // (the wait then times out)
             bulk_g2s(sx + 128 * i, A.ox + 128 * g, bytes, &bar_tma);
             bulk_g2s(sy + 128 * i, A.oy + 128 * g, bytes, &bar_tma);
             bulk_g2s(sz + 128 * i, A.oz + 128 * g, bytes, &bar_tma);
