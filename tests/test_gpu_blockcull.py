@@ -101,3 +101,27 @@ def test_ungated_agent_and_sphere_oracle(gm):
     near = rm < rd
     assert np.abs(mc[near] - rm[near]).max(initial=0) <= POS_TOL
     assert np.all(mc[~near] >= rd[~near] - POS_TOL)
+
+
+def test_four_term_cost_sums_equal_all_pairs(gm):
+    """The four-term cost sums (goal, obstacle, path, jerk, d1) depend on the
+    positions, the forces and -- through the obstacle term max(r_c - m, 0)
+    -- on the clearance only where it is below r_c <= r_d, where the culled
+    clearance is exact.  So they, and the agent score_and_select4 picks,
+    equal rollout_agents' bit for bit."""
+    import dataclasses
+    import torch
+    w = synth.tabletop_workload(n_agents=60, n_steps=300)
+    prm = dataclasses.replace(w["params"], cost_radius=0.05)
+    assert prm.cost_radius <= float(np.min(w["agents"]["r_d"]))
+    obs = gm.filter_cloud(torch.from_numpy(w["xyz"]).cuda(), w["T"], w["workspace"], cap=80000)
+    dev = to_dev_agents(w["agents"])
+    outs, sels = [], []
+    for fn in (gm.rollout_agents, gm.rollout_agents_blockcull):
+        o = gm.alloc_rollout_out(60, 300, want_traj=True, want_clear=True, want_cost4=True)
+        fn(obs, dev, prm, out=o, tuning=TABLE)
+        outs.append(o)
+        sels.append(gm.score_and_select4(o, prm))
+    gm.sync()
+    assert np.array_equal(_bits(outs[0]["cost_terms"]), _bits(outs[1]["cost_terms"]))
+    assert int(sels[0]["best"].item()) == int(sels[1]["best"].item())
