@@ -445,8 +445,6 @@ __device__ __forceinline__ void half_step(const float *sx, const float *sy, cons
                 }
             }
             uint32_t blocks = 0;
-            // an agent without a gate (r_d = inf) passes every block: then
-            // every pair runs the terms, in the plain loop (no test)
 #pragma unroll 2
             for (int j = 4 * tid; j < cnt_pad; j += 4 * NT) {
                 const float4 x4 = *reinterpret_cast<const float4 *>(sx + j);
@@ -814,23 +812,6 @@ __device__ __forceinline__ uint32_t vote_loop(const float *sx, const float *sy, 
     float T[NA];
     if constexpr (!CLEAR) block_setup<AG, NA, OFF>(X, Y, Z, G2a, omax2, QX, QY, QZ, T);
     uint32_t blocks = 0;
-    // an agent without a gate (r_d = inf) passes every block: then every
-    // pair runs the terms, in the plain loop (no test)
-    bool every = false;
-#pragma unroll
-    for (int a = 0; a < NA; ++a) every |= G2a[OFF + a] == INFINITY;
-    if (every) {
-#pragma unroll 2
-        for (int j = 2 * threadIdx.x; j < cnt_pad; j += 2 * NT) {
-            const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
-            const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
-            const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
-            if constexpr (CLEAR)  // the clearance minimum of every pair
-                block_test_exact<AG, NA, OFF>(ox, oy, oz, X, Y, Z, mn, G2a, tiny2);
-            terms(ox, oy, oz);
-        }
-        return static_cast<uint32_t>(cnt_pad / 128 / (NT / 32));
-    }
 #pragma unroll 2
     for (int j = 4 * threadIdx.x; j < cnt_pad; j += 4 * NT) {
         const float4 x4 = *reinterpret_cast<const float4 *>(sx + j);
@@ -858,7 +839,7 @@ __device__ __forceinline__ uint32_t vote_loop(const float *sx, const float *sy, 
 // partial force sums of this thread's obstacle pairs, reduced over the warp
 // (one transposed butterfly per component) and stored as one record
 // (f_x, f_y, f_z, min |d|^2) per agent at part_slot0[4 (OFF + a)].
-template <int AG, int NA, int OFF, int NT, bool CLEAR>
+template <int AG, int NA, int OFF, int NT, bool CLEAR, bool VOTE = true>
 __device__ __forceinline__ void half_step_apf(const float *sx, const float *sy, const float *sz,
                                               int cnt_pad, const float (&cRa)[AG],
                                               const f2 (&ird2)[AG], const float (&G2a)[AG],
@@ -880,13 +861,22 @@ __device__ __forceinline__ void half_step_apf(const float *sx, const float *sy, 
         }
         const f2 tiny2 = pk(1e-30f, 1e-30f);
         (void)tid;
-        *nheur += 2 * NA * vote_loop<AG, NA, OFF, NT, CLEAR>(
-                                   sx, sy, sz, cnt_pad, X, Y, Z, mn, G2a, omax2, tiny2,
-                                          [&](f2 ox, f2 oy, f2 oz) {
-                                              apf_pair_terms<AG, NA, OFF, false>(
-                                                  ox, oy, oz, X, Y, Z, fx, fy, fz, mn, cRa, ird2,
-                                                  G2a, tiny2);
-                                          });
+        if constexpr (VOTE) {
+            *nheur += 2 * NA * vote_loop<AG, NA, OFF, NT, CLEAR>(
+                sx, sy, sz, cnt_pad, X, Y, Z, mn, G2a, omax2, tiny2, [&](f2 ox, f2 oy, f2 oz) {
+                    apf_pair_terms<AG, NA, OFF, false>(ox, oy, oz, X, Y, Z, fx, fy, fz, mn, cRa,
+                                                       ird2, G2a, tiny2);
+                });
+        } else {  // a group with an agent without a gate: every pair, no test
+            uint32_t its = 0;
+#pragma unroll 2
+            for (int j = 2 * tid; j < cnt_pad; j += 2 * NT, ++its)
+                apf_pair_terms<AG, NA, OFF, CLEAR>(*reinterpret_cast<const f2 *>(sx + j),
+                                                   *reinterpret_cast<const f2 *>(sy + j),
+                                                   *reinterpret_cast<const f2 *>(sz + j), X, Y, Z,
+                                                   fx, fy, fz, mn, cRa, ird2, G2a, tiny2);
+            *nheur += its * NA;
+        }
         float v0[P], v1[P], v2[P], vm[P];
 #pragma unroll
         for (int a = 0; a < P; ++a) {
@@ -1074,7 +1064,7 @@ __device__ __forceinline__ void proj_pair_terms(f2 ox, f2 oy, f2 oz, const f2 (&
 // Projected-current counterpart of half_step: positions and velocities of
 // the half's agents from shared memory (pos, vel: [3][AG]); the record
 // (S_x, S_y, S_z, B, min |d|^2, 0) of each agent goes to part_slot0[6 a'].
-template <int AG, int NA, int OFF, int NT, bool CLEAR>
+template <int AG, int NA, int OFF, int NT, bool CLEAR, bool VOTE = true>
 __device__ __forceinline__ void half_step_proj(const float *sx, const float *sy, const float *sz,
                                                int cnt_pad, float eps, const f2 (&nR2)[AG],
                                                const float (&G2a)[AG], float *part_slot0,
@@ -1100,13 +1090,23 @@ __device__ __forceinline__ void half_step_proj(const float *sx, const float *sy,
         }
         const f2 tiny2 = pk(1e-30f, 1e-30f);
         (void)tid;
-        *nheur += 2 * NA * vote_loop<AG, NA, OFF, NT, CLEAR>(
-                                   sx, sy, sz, cnt_pad, X, Y, Z, mn, G2a, omax2, tiny2,
-                                          [&](f2 ox, f2 oy, f2 oz) {
-                                              proj_pair_terms<AG, NA, OFF, false>(
-                                                  ox, oy, oz, X, Y, Z, VX, VY, VZ, ax, ay, az, ab,
-                                                  mn, nR2, G2a, eps, tiny2);
-                                          });
+        if constexpr (VOTE) {
+            *nheur += 2 * NA * vote_loop<AG, NA, OFF, NT, CLEAR>(
+                sx, sy, sz, cnt_pad, X, Y, Z, mn, G2a, omax2, tiny2, [&](f2 ox, f2 oy, f2 oz) {
+                    proj_pair_terms<AG, NA, OFF, false>(ox, oy, oz, X, Y, Z, VX, VY, VZ, ax, ay,
+                                                        az, ab, mn, nR2, G2a, eps, tiny2);
+                });
+        } else {  // a group with an agent without a gate: every pair, no test
+            uint32_t its = 0;
+#pragma unroll 2
+            for (int j = 2 * tid; j < cnt_pad; j += 2 * NT, ++its)
+                proj_pair_terms<AG, NA, OFF, CLEAR>(*reinterpret_cast<const f2 *>(sx + j),
+                                                    *reinterpret_cast<const f2 *>(sy + j),
+                                                    *reinterpret_cast<const f2 *>(sz + j), X, Y, Z,
+                                                    VX, VY, VZ, ax, ay, az, ab, mn, nR2, G2a, eps,
+                                                    tiny2);
+            *nheur += its * NA;
+        }
         float v0[P], v1[P], v2[P], v3[P], vm[P];
 #pragma unroll
         for (int a = 0; a < P; ++a) {
@@ -1459,11 +1459,11 @@ __global__ void __launch_bounds__(NT + 32 * kExchWarps, 1) k_rollout(const Rollo
                 for (int k = 0; k < A.n_steps; ++k) {
                     if (k > 0) named_sync(kPos + 0, kBoth);
                     if constexpr (APF)
-                        half_step_apf<AG, H0, 0, NT, CLEAR>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
+                        half_step_apf<AG, H0, 0, NT, CLEAR, VOTE>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
                                                             part(0) + 4 * (warp * AG), lane, pos,
                                                             omax2, &nheur);
                     else if constexpr (PROJ)
-                        half_step_proj<AG, H0, 0, NT, CLEAR>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
+                        half_step_proj<AG, H0, 0, NT, CLEAR, VOTE>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
                                                              part(0) + 6 * (warp * AG), lane, pos,
                                                              vel, omax2, &nheur);
                     else
@@ -1473,11 +1473,11 @@ __global__ void __launch_bounds__(NT + 32 * kExchWarps, 1) k_rollout(const Rollo
                     named_arrive(kPart + 0, kBoth);
                     if (k > 0) named_sync(kPos + 1, kBoth);
                     if constexpr (APF)
-                        half_step_apf<AG, H1, H0, NT, CLEAR>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
+                        half_step_apf<AG, H1, H0, NT, CLEAR, VOTE>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
                                                              part(1) + 4 * (warp * AG), lane, pos,
                                                              omax2, &nheur);
                     else if constexpr (PROJ)
-                        half_step_proj<AG, H1, H0, NT, CLEAR>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
+                        half_step_proj<AG, H1, H0, NT, CLEAR, VOTE>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
                                                               part(1) + 6 * (warp * AG), lane, pos,
                                                               vel, omax2, &nheur);
                     else
@@ -1487,14 +1487,15 @@ __global__ void __launch_bounds__(NT + 32 * kExchWarps, 1) k_rollout(const Rollo
                     named_arrive(kPart + 1, kBoth);
                 }
             };
-            // an MFI group with an agent without a gate (r_d = inf) passes
-            // every block: its pair loops run without the block test
+            // a group with an agent without a gate (r_d = inf) passes every
+            // block: its pair loops run without the block test
             bool every = false;
 #pragma unroll
-            for (int a = 0; a < AG; ++a) every |= G2a[a] == INFINITY;
-            if constexpr (!APF && !PROJ) {
-                if (every) steps(std::false_type{}, std::false_type{});
-                else if (A.box_cull) steps(std::true_type{}, std::true_type{});
+            for (int a = 0; a < AG; ++a) every |= (APF ? G2s[a] : G2a[a]) == INFINITY;
+            if (every) {
+                steps(std::false_type{}, std::false_type{});
+            } else if constexpr (!APF && !PROJ) {
+                if (A.box_cull) steps(std::true_type{}, std::true_type{});
                 else steps(std::true_type{}, std::false_type{});
             } else {
                 steps(std::true_type{}, std::false_type{});
