@@ -401,6 +401,7 @@ def run_ours(args, ws, rank, local):
         result = {
             "metric": METRIC, "value": inter / t_job, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_job / args.steps,
+            "ms_per_step_median": float(np.median(step_ms)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": _config(base, args, ws),
             "n_obs_mean": float(np.mean(n_obs)), "tuning": list(tuning),
@@ -412,6 +413,7 @@ def run_ours(args, ws, rank, local):
                          "peak_source": f"{props.multi_processor_count} SMs x "
                                         f"{FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
                          "rollout_ms_mean": 1e3 * mean_roll,
+                         "rollout_ms_median": float(np.median(roll_ms)),
                          "executed": {
                              "note": "FP32 flops the kernel executes: the heuristic terms only "
                                      "for blocks of 64 obstacles where a pair passes the gate",
