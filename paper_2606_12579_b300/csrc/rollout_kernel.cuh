@@ -18,21 +18,22 @@
 //   runs on -1/s so it needs no negation), which balances the SFU against
 //   the FMA pipe.
 //
-// Warp specialisation: the CTA's NT compute warps only evaluate pairs; one
-// more warp (the exchange warp) owns the agents' state.  The agents of a
-// group are split into two halves kept one phase apart.  After a half, each
-// compute warp reduces its partial sums with a transposed shuffle butterfly,
-// stores them to shared memory and arrives on a named barrier, then goes on
-// with the other half.  Meanwhile the exchange warp sums the NW warp
-// partials in warp order, sends the CTA partial into the double-buffered
-// receive slots of every CTA of the cluster with st.async (each store
-// completes bytes on the receiver's mbarrier), waits for the C partials,
-// sums them in rank order, integrates the half's agents (lane a = agent a)
-// and publishes their positions to shared memory behind a second named
-// barrier.  The exchange of one half is thus hidden behind the other half's
-// pair loop; every CTA integrates the same sums in the same order, so all
-// copies of an agent's state are bit-identical.  Nothing inside the N_k loop
-// touches global memory except the optional trajectory/trace stores.
+// Warp specialisation: the CTA's NT compute warps only evaluate pairs; two
+// more warps (the exchange warps, one per agent half) own the agents' state.
+// The agents of a group are split into two halves kept one phase apart.
+// After a half, each compute warp reduces its partial sums with a transposed
+// shuffle butterfly, stores them to shared memory and arrives on a named
+// barrier, then goes on with the other half.  Meanwhile the half's exchange
+// warp sums the NW warp partials in warp order, sends the CTA partial into
+// the double-buffered receive slots of every CTA of the cluster with st.async
+// (each store completes bytes on the receiver's mbarrier), waits for the C
+// partials, sums them in rank order, integrates the half's agents (lane a =
+// agent a) and publishes their positions to shared memory behind a second
+// named barrier.  The exchange of one half is thus hidden behind the other
+// half's pair loop (and the two halves' exchanges overlap); every CTA
+// integrates the same sums in the same order, so all copies of an agent's
+// state are bit-identical.  Nothing inside the N_k loop touches global
+// memory except the optional trajectory/trace stores.
 #pragma once
 
 #include <math.h>
