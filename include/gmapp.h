@@ -286,8 +286,9 @@ typedef struct {
                           block of 64 obstacles only when one of the block's pairs passes
                           an agent's gate (Alg. 1's branch), so this is a multiple of 64
                           and at least the number of pairs within the gates.  For
-                          accounting only (results do not depend on it); rollout_agents and
-                          rollout_ensemble only (other calls leave it untouched). */
+                          accounting only (results do not depend on it); rollout_agents,
+                          rollout_agents_blockcull and rollout_ensemble only (other calls
+                          leave it untouched). */
 } gmapp_rollout_out;
 
 /* Roll all agents forward N_k steps in ONE launch.  Step k (0-based):
