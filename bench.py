@@ -741,7 +741,12 @@ def bench_ensemble(gm, args, reps=5):
             "proj": lambda: gm.rollout_ensemble(obs, mfi, 0, prm, out=out, tuning=shapes["proj"],
                                                 n_proj=na),
             "three_kinds": lambda: gm.rollout_ensemble(obs, three, n3, prm, out=out,
-                                                       tuning=shapes["three_kinds"], n_proj=n3)}
+                                                       tuning=shapes["three_kinds"], n_proj=n3),
+            # the mixed ensemble culled by the obstacle blocks' bounding boxes
+            # (the same forces bit for bit; reported as time, not interactions)
+            "ensemble_culled": lambda: gm.rollout_ensemble(obs, mixed, n_apf, prm, out=out,
+                                                           tuning=shapes["ensemble"], cull=True)}
+    shapes["ensemble_culled"] = shapes["ensemble"]
     for k, fn in runs.items():   # warm-up launches, one NVTX range each (for ncu)
         torch.cuda.nvtx.range_push(f"warm_{k}")
         fn()
@@ -771,6 +776,7 @@ def bench_ensemble(gm, args, reps=5):
              "three_kinds": pairs * ((na - 2 * n3) * FLOPS_PER_INTERACTION +
                                      n3 * PROJ_FLOPS_PER_INTERACTION +
                                      n3 * APF_FLOPS_PER_INTERACTION)}
+    flops["ensemble_culled"] = flops["ensemble"]
     res = {"workload": f"tabletop 640x480 -> 5 mm voxels (N_O = {n_o}); 256 agents x 500 steps; "
                        f"ensemble = last {n_apf} agents APF (gain x 1e-3), r_d alternating 5/10 cm",
            "tuning": {k: list(v) for k, v in shapes.items()}, "peak_TFLOP_per_s": peak,
@@ -784,6 +790,7 @@ def bench_ensemble(gm, args, reps=5):
             "mfi": FLOPS_PER_INTERACTION, "apf": APF_FLOPS_PER_INTERACTION,
             "proj": PROJ_FLOPS_PER_INTERACTION,
             "three_kinds": flops["three_kinds"] / (pairs * na)}
+    full["ensemble_culled"] = full["ensemble"]
     for k, s in times.items():
         test = BLOCK_TEST_FLOPS + OBSTACLE_NORM_FLOPS * 2.0 / shapes[k][1]
         ex = pairs * na * test + heur[k] * full[k]

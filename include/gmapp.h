@@ -465,6 +465,19 @@ gmapp_status rollout_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *obs,
                               const gmapp_rollout_params *prm, gmapp_rollout_out *out,
                               const gmapp_tuning *tune, gmapp_stream stream);
 
+/* rollout_ensemble with spatial culling over the key-sorted obstacle blocks,
+ * as rollout_agents_blockcull does for MFI agents: every group (MFI, APF,
+ * projected current) visits only the blocks of 128 obstacles whose bounding
+ * box meets a gate of its agents.  Forces, trajectories and path lengths
+ * equal rollout_ensemble's at the same launch shape bit for bit; the
+ * clearance is as for rollout_agents_blockcull.  Arguments and errors as for
+ * rollout_ensemble. */
+gmapp_status rollout_ensemble_blockcull(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                                        const gmapp_agents *agents, int32_t n_proj,
+                                        int32_t n_apf, const gmapp_rollout_params *prm,
+                                        gmapp_rollout_out *out, const gmapp_tuning *tune,
+                                        gmapp_stream stream);
+
 /* gmapp_autotune_rollout for an ensemble (n_proj, n_apf as in
  * rollout_ensemble): ranks the
  * shapes that fit the ensemble (groups split by heuristic), times the best

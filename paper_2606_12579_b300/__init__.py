@@ -395,21 +395,25 @@ def rollout_agents_blockcull(obs: Obstacles, agents: dict, prm, out: dict | None
 
 def rollout_ensemble(obs: Obstacles, agents: dict, n_apf: int, prm, out: dict | None = None,
                      want_traj: bool = True, want_trace: bool = False, want_clear: bool = True,
-                     tuning=None, stream=None, n_proj: int = 0) -> dict:
+                     tuning=None, stream=None, n_proj: int = 0, cull: bool = False) -> dict:
     """Heterogeneous ensemble in one launch: the last ``n_apf`` agents follow
     the APF heuristic (Eq. apf), the ``n_proj`` before them MFI with the
     per-obstacle projected current, the others the MFI field with their own
     current (Eq. mfi); agent groups are homogeneous.  Arguments and outputs
-    as rollout_agents."""
+    as rollout_agents.  ``cull``: rollout_ensemble_blockcull (each group
+    visits only the obstacle blocks whose bounding box meets a gate; the same
+    forces and trajectories bit for bit)."""
     ctx = context()
     na = int(agents["k_r"].numel())
     if out is None:
         out = alloc_rollout_out(na, int(prm.n_steps), want_traj, want_trace, want_clear)
     ob, ag, pr, os_ = obs._struct(), _agents_struct(agents), _params_struct(prm), _out_struct(out)
     t = C.byref(_abi.Tuning(*[int(v) for v in tuning])) if tuning is not None else None
-    check(_abi.load().rollout_ensemble(ctx.handle, C.byref(ob), C.byref(ag), int(n_proj), int(n_apf),
-                                       C.byref(pr), C.byref(os_), t, _stream(stream)),
-          "rollout_ensemble")
+    lib = _abi.load()
+    fn, name = ((lib.rollout_ensemble_blockcull, "rollout_ensemble_blockcull") if cull
+                else (lib.rollout_ensemble, "rollout_ensemble"))
+    check(fn(ctx.handle, C.byref(ob), C.byref(ag), int(n_proj), int(n_apf), C.byref(pr),
+             C.byref(os_), t, _stream(stream)), name)
     return out
 
 

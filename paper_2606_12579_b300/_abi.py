@@ -130,6 +130,9 @@ PROTOTYPES = {
     "rollout_agents_tuned": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
                                        C.POINTER(RolloutParams), C.POINTER(RolloutOut),
                                        C.POINTER(Tuning), P]),
+    "rollout_ensemble_blockcull": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
+                                             C.c_int32, C.c_int32, C.POINTER(RolloutParams),
+                                             C.POINTER(RolloutOut), C.POINTER(Tuning), P]),
     "rollout_agents_blockcull": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
                                            C.POINTER(RolloutParams), C.POINTER(RolloutOut),
                                            C.POINTER(Tuning), P]),

@@ -610,23 +610,23 @@ extern "C" gmapp_status rollout_agents_blockcull(gmapp_ctx *ctx, const gmapp_obs
     return launch(ctx, obs, agents, prm, out, t, stream, Kinds{}, true);
 }
 
-extern "C" gmapp_status rollout_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *obs,
-                                         const gmapp_agents *agents, int32_t n_proj,
-                                         int32_t n_apf,
-                                         const gmapp_rollout_params *prm, gmapp_rollout_out *out,
-                                         const gmapp_tuning *tune, gmapp_stream stream) {
+namespace {
+gmapp_status ensemble_impl(const char *who, gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                           const gmapp_agents *agents, int32_t n_proj, int32_t n_apf,
+                           const gmapp_rollout_params *prm, gmapp_rollout_out *out,
+                           const gmapp_tuning *tune, gmapp_stream stream, bool box_cull) {
     if (!ctx) {
-        set_error("rollout_ensemble: NULL ctx");
+        set_error("%s: NULL ctx", who);
         return GMAPP_ERR_INVALID_ARG;
     }
     gmapp_status st = validate(obs, agents, prm, out);
     if (st != GMAPP_OK) return st;
-    if ((st = check_kinds("rollout_ensemble", agents, n_proj, n_apf, out)) != GMAPP_OK) return st;
+    if ((st = check_kinds(who, agents, n_proj, n_apf, out)) != GMAPP_OK) return st;
     gmapp_tuning t;
     if (tune) {
         if (!(tune->threads == 128 || tune->threads == 256 || tune->threads == 384 ||
               tune->threads == 512)) {
-            set_error("rollout_ensemble: threads must be 128, 256, 384 or 512");
+            set_error("%s: threads must be 128, 256, 384 or 512", who);
             return GMAPP_ERR_INVALID_ARG;
         }
         t = *tune;
@@ -634,5 +634,26 @@ extern "C" gmapp_status rollout_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *
         st = pick_tuning_impl(ctx, obs->cap, agents->n, wants_clear(out), &t, Kinds{n_proj, n_apf});
         if (st != GMAPP_OK) return st;
     }
-    return launch(ctx, obs, agents, prm, out, t, stream, Kinds{n_proj, n_apf});
+    return launch(ctx, obs, agents, prm, out, t, stream, Kinds{n_proj, n_apf}, box_cull);
+}
+}  // namespace
+
+extern "C" gmapp_status rollout_ensemble(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                                         const gmapp_agents *agents, int32_t n_proj,
+                                         int32_t n_apf,
+                                         const gmapp_rollout_params *prm, gmapp_rollout_out *out,
+                                         const gmapp_tuning *tune, gmapp_stream stream) {
+    return ensemble_impl("rollout_ensemble", ctx, obs, agents, n_proj, n_apf, prm, out, tune,
+                         stream, false);
+}
+
+extern "C" gmapp_status rollout_ensemble_blockcull(gmapp_ctx *ctx, const gmapp_obstacles *obs,
+                                                   const gmapp_agents *agents, int32_t n_proj,
+                                                   int32_t n_apf,
+                                                   const gmapp_rollout_params *prm,
+                                                   gmapp_rollout_out *out,
+                                                   const gmapp_tuning *tune,
+                                                   gmapp_stream stream) {
+    return ensemble_impl("rollout_ensemble_blockcull", ctx, obs, agents, n_proj, n_apf, prm, out,
+                         tune, stream, true);
 }

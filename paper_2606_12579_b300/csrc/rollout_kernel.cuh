@@ -71,7 +71,7 @@ struct RolloutArgs {
         *f_trace, *ckpt;
     float *cost_terms;  // [5][N_a] sums of the four-term cost, or NULL
     unsigned long long *heur_pairs;  // pairs whose heuristic terms ran (added), or NULL
-    int32_t box_cull;    // MFI groups visit only the blocks whose bounding box meets a gate
+    int32_t box_cull;    // groups visit only the blocks whose bounding box meets a gate
     float cost_radius;  // r_c of its goal and obstacle terms
     int32_t shard_cap;   // obstacles one CTA can hold (multiple of 128)
     int32_t n_groups;    // agent groups (clusters, or CTA groups with the grid exchange)
@@ -802,13 +802,60 @@ __device__ __forceinline__ bool block_test_exact(f2 ox, f2 oy, f2 oz, const f2 (
 
 // The voting pair loop over the shard (cnt_pad a multiple of 128): terms(ox,
 // oy, oz) evaluates and accumulates the heuristic terms of one packed pair.
-// Returns the number of blocks whose terms ran.
-template <int AG, int NA, int OFF, int NT, bool CLEAR, class Terms>
+// Returns the number of blocks whose terms ran.  With BOX (culled rollouts)
+// a lane tests one block's bounding box (boxes[6 b]) against the half's
+// gates and the warp visits only the blocks whose box meets one, in the
+// same order and lane layout (the clearance then comes from the visited
+// blocks only).
+template <int AG, int NA, int OFF, int NT, bool CLEAR, bool BOX, class Terms>
 __device__ __forceinline__ uint32_t vote_loop(const float *sx, const float *sy, const float *sz,
                                           int cnt_pad, const f2 (&X)[NA], const f2 (&Y)[NA],
                                           const f2 (&Z)[NA], float (&mn)[NA],
                                           const float (&G2a)[AG], float omax2, f2 tiny2,
-                                          Terms &&terms) {
+                                          const float *boxes, Terms &&terms) {
+    if constexpr (BOX) {
+        float TB[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) TB[a] = fmaf(G2a[OFF + a], 1.0f + 0x1p-12f, 1e-12f);
+        constexpr int NWc = NT / 32;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        const int n_it = (cnt_pad / 128 - w + NWc - 1) / NWc;  // blocks w, w + NWc, ...
+        uint32_t blocks = 0;
+        for (int base = 0; base < n_it; base += 32) {
+            const int i = base + lane;
+            bool near = false;
+            if (i < n_it) {
+                const float *bx = boxes + 6 * (w + i * NWc);
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    const float px = lo_of(X[a]), py = lo_of(Y[a]), pz = lo_of(Z[a]);
+                    const float dx = fmaxf(fmaxf(bx[0] - px, px - bx[3]), 0.0f);
+                    const float dy = fmaxf(fmaxf(bx[1] - py, py - bx[4]), 0.0f);
+                    const float dz = fmaxf(fmaxf(bx[2] - pz, pz - bx[5]), 0.0f);
+                    near |= fmaf(dz, dz, fmaf(dy, dy, dx * dx)) <= TB[a];
+                }
+            }
+            uint32_t m = __ballot_sync(0xffffffffu, near);
+            while (m) {
+                const int l = __ffs(m) - 1;
+                m &= m - 1;
+                const int j = (w + (base + l) * NWc) * 128 + 4 * lane;
+                const float4 x4 = *reinterpret_cast<const float4 *>(sx + j);
+                const float4 y4 = *reinterpret_cast<const float4 *>(sy + j);
+                const float4 z4 = *reinterpret_cast<const float4 *>(sz + j);
+                const f2 ox0 = pk(x4.x, x4.y), oy0 = pk(y4.x, y4.y), oz0 = pk(z4.x, z4.y);
+                const f2 ox1 = pk(x4.z, x4.w), oy1 = pk(y4.z, y4.w), oz1 = pk(z4.z, z4.w);
+                if constexpr (CLEAR) {
+                    block_test_exact<AG, NA, OFF>(ox0, oy0, oz0, X, Y, Z, mn, G2a, tiny2);
+                    block_test_exact<AG, NA, OFF>(ox1, oy1, oz1, X, Y, Z, mn, G2a, tiny2);
+                }
+                terms(ox0, oy0, oz0);
+                terms(ox1, oy1, oz1);
+                ++blocks;
+            }
+        }
+        return blocks;
+    }
     f2 QX[NA], QY[NA], QZ[NA];
     float T[NA];
     if constexpr (!CLEAR) block_setup<AG, NA, OFF>(X, Y, Z, G2a, omax2, QX, QY, QZ, T);
@@ -840,12 +887,13 @@ __device__ __forceinline__ uint32_t vote_loop(const float *sx, const float *sy, 
 // partial force sums of this thread's obstacle pairs, reduced over the warp
 // (one transposed butterfly per component) and stored as one record
 // (f_x, f_y, f_z, min |d|^2) per agent at part_slot0[4 (OFF + a)].
-template <int AG, int NA, int OFF, int NT, bool CLEAR, bool VOTE = true>
+template <int AG, int NA, int OFF, int NT, bool CLEAR, bool VOTE = true, bool BOX = false>
 __device__ __forceinline__ void half_step_apf(const float *sx, const float *sy, const float *sz,
                                               int cnt_pad, const float (&cRa)[AG],
                                               const f2 (&ird2)[AG], const float (&G2a)[AG],
                                               float *part_slot0, int lane, const float *pos,
-                                              float omax2, uint32_t *nheur) {
+                                              float omax2, uint32_t *nheur,
+                                              const float *boxes = nullptr) {
     if constexpr (NA > 0) {
         constexpr int P = pow2ceil(NA);
         const int tid = threadIdx.x;
@@ -863,8 +911,8 @@ __device__ __forceinline__ void half_step_apf(const float *sx, const float *sy, 
         const f2 tiny2 = pk(1e-30f, 1e-30f);
         (void)tid;
         if constexpr (VOTE) {
-            *nheur += 2 * NA * vote_loop<AG, NA, OFF, NT, CLEAR>(
-                sx, sy, sz, cnt_pad, X, Y, Z, mn, G2a, omax2, tiny2, [&](f2 ox, f2 oy, f2 oz) {
+            *nheur += 2 * NA * vote_loop<AG, NA, OFF, NT, CLEAR, BOX>(
+                sx, sy, sz, cnt_pad, X, Y, Z, mn, G2a, omax2, tiny2, boxes, [&](f2 ox, f2 oy, f2 oz) {
                     apf_pair_terms<AG, NA, OFF, false>(ox, oy, oz, X, Y, Z, fx, fy, fz, mn, cRa,
                                                        ird2, G2a, tiny2);
                 });
@@ -1065,12 +1113,13 @@ __device__ __forceinline__ void proj_pair_terms(f2 ox, f2 oy, f2 oz, const f2 (&
 // Projected-current counterpart of half_step: positions and velocities of
 // the half's agents from shared memory (pos, vel: [3][AG]); the record
 // (S_x, S_y, S_z, B, min |d|^2, 0) of each agent goes to part_slot0[6 a'].
-template <int AG, int NA, int OFF, int NT, bool CLEAR, bool VOTE = true>
+template <int AG, int NA, int OFF, int NT, bool CLEAR, bool VOTE = true, bool BOX = false>
 __device__ __forceinline__ void half_step_proj(const float *sx, const float *sy, const float *sz,
                                                int cnt_pad, float eps, const f2 (&nR2)[AG],
                                                const float (&G2a)[AG], float *part_slot0,
                                                int lane, const float *pos, const float *vel,
-                                               float omax2, uint32_t *nheur) {
+                                               float omax2, uint32_t *nheur,
+                                               const float *boxes = nullptr) {
     if constexpr (NA > 0) {
         constexpr int P = pow2ceil(NA);
         const int tid = threadIdx.x;
@@ -1092,8 +1141,8 @@ __device__ __forceinline__ void half_step_proj(const float *sx, const float *sy,
         const f2 tiny2 = pk(1e-30f, 1e-30f);
         (void)tid;
         if constexpr (VOTE) {
-            *nheur += 2 * NA * vote_loop<AG, NA, OFF, NT, CLEAR>(
-                sx, sy, sz, cnt_pad, X, Y, Z, mn, G2a, omax2, tiny2, [&](f2 ox, f2 oy, f2 oz) {
+            *nheur += 2 * NA * vote_loop<AG, NA, OFF, NT, CLEAR, BOX>(
+                sx, sy, sz, cnt_pad, X, Y, Z, mn, G2a, omax2, tiny2, boxes, [&](f2 ox, f2 oy, f2 oz) {
                     proj_pair_terms<AG, NA, OFF, false>(ox, oy, oz, X, Y, Z, VX, VY, VZ, ax, ay,
                                                         az, ab, mn, nR2, G2a, eps, tiny2);
                 });
@@ -1460,13 +1509,13 @@ __global__ void __launch_bounds__(NT + 32 * kExchWarps, 1) k_rollout(const Rollo
                 for (int k = 0; k < A.n_steps; ++k) {
                     if (k > 0) named_sync(kPos + 0, kBoth);
                     if constexpr (APF)
-                        half_step_apf<AG, H0, 0, NT, CLEAR, VOTE>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
+                        half_step_apf<AG, H0, 0, NT, CLEAR, VOTE, BOX>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
                                                             part(0) + 4 * (warp * AG), lane, pos,
-                                                            omax2, &nheur);
+                                                            omax2, &nheur, boxes);
                     else if constexpr (PROJ)
-                        half_step_proj<AG, H0, 0, NT, CLEAR, VOTE>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
+                        half_step_proj<AG, H0, 0, NT, CLEAR, VOTE, BOX>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
                                                              part(0) + 6 * (warp * AG), lane, pos,
-                                                             vel, omax2, &nheur);
+                                                             vel, omax2, &nheur, boxes);
                     else
                         half_step<AG, H0, 0, NM0, NT, CLEAR, false, false, true, VOTE, BOX>(
                             sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(0) + 2 * (warp * AG), C,
@@ -1474,13 +1523,13 @@ __global__ void __launch_bounds__(NT + 32 * kExchWarps, 1) k_rollout(const Rollo
                     named_arrive(kPart + 0, kBoth);
                     if (k > 0) named_sync(kPos + 1, kBoth);
                     if constexpr (APF)
-                        half_step_apf<AG, H1, H0, NT, CLEAR, VOTE>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
+                        half_step_apf<AG, H1, H0, NT, CLEAR, VOTE, BOX>(sx, sy, sz, cnt_pad, cRa, ird2, G2s,
                                                              part(1) + 4 * (warp * AG), lane, pos,
-                                                             omax2, &nheur);
+                                                             omax2, &nheur, boxes);
                     else if constexpr (PROJ)
-                        half_step_proj<AG, H1, H0, NT, CLEAR, VOTE>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
+                        half_step_proj<AG, H1, H0, NT, CLEAR, VOTE, BOX>(sx, sy, sz, cnt_pad, eps, nR2, G2a,
                                                               part(1) + 6 * (warp * AG), lane, pos,
-                                                              vel, omax2, &nheur);
+                                                              vel, omax2, &nheur, boxes);
                     else
                         half_step<AG, H1, H0, NM1, NT, CLEAR, false, false, true, VOTE, BOX>(
                             sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(1) + 2 * (warp * AG), C,
@@ -1493,14 +1542,9 @@ __global__ void __launch_bounds__(NT + 32 * kExchWarps, 1) k_rollout(const Rollo
             bool every = false;
 #pragma unroll
             for (int a = 0; a < AG; ++a) every |= (APF ? G2s[a] : G2a[a]) == INFINITY;
-            if (every) {
-                steps(std::false_type{}, std::false_type{});
-            } else if constexpr (!APF && !PROJ) {
-                if (A.box_cull) steps(std::true_type{}, std::true_type{});
-                else steps(std::true_type{}, std::false_type{});
-            } else {
-                steps(std::true_type{}, std::false_type{});
-            }
+            if (every) steps(std::false_type{}, std::false_type{});
+            else if (A.box_cull) steps(std::true_type{}, std::true_type{});
+            else steps(std::true_type{}, std::false_type{});
             if (A.heur_pairs && lane == 0 && nheur)
                 atomicAdd(A.heur_pairs, 64ull * nheur);
             return;

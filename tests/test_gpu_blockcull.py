@@ -125,3 +125,29 @@ def test_four_term_cost_sums_equal_all_pairs(gm):
     gm.sync()
     assert np.array_equal(_bits(outs[0]["cost_terms"]), _bits(outs[1]["cost_terms"]))
     assert int(sels[0]["best"].item()) == int(sels[1]["best"].item())
+
+
+@pytest.mark.parametrize("n_proj,n_apf", [(0, 60), (60, 0), (20, 20)])
+@pytest.mark.parametrize("clear", [False, True])
+def test_ensemble_equals_rollout_ensemble_bit_for_bit(gm, n_proj, n_apf, clear):
+    """APF and projected-current groups (and MFI beside them) culled by the
+    block boxes: forces and trajectories equal rollout_ensemble's."""
+    import torch
+    w = synth.tabletop_workload(n_agents=60, n_steps=200)
+    ag = synth.ensemble_agents(w["agents"], n_apf)
+    obs = gm.filter_cloud(torch.from_numpy(w["xyz"]).cuda(), w["T"], w["workspace"], cap=80000)
+    dev = to_dev_agents(ag)
+    outs = []
+    for cull in (False, True):
+        o = gm.alloc_rollout_out(60, 200, want_traj=True, want_trace=True, want_clear=clear)
+        if not clear:
+            o["m_trace"] = None
+        o["heur_pairs"] = torch.zeros(1, dtype=torch.int64, device="cuda")
+        gm.rollout_ensemble(obs, dev, n_apf, w["params"], out=o, tuning=TABLE, n_proj=n_proj,
+                            cull=cull)
+        outs.append(o)
+    gm.sync()
+    a, b = outs
+    for key in ("w_trace", "f_trace", "traj", "path_len"):
+        assert np.array_equal(_bits(a[key]), _bits(b[key])), key
+    assert int(b["heur_pairs"].item()) < 0.5 * 60 * obs.count() * 200
