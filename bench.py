@@ -724,14 +724,14 @@ def bench_ensemble(gm, args, reps=5):
     three = dev(synth.ensemble_agents(w["agents"], n3))
     out = gm.alloc_rollout_out(na, nk, want_traj=True, want_clear=False)
     shapes = {"ensemble": gm.autotune_ensemble(obs, mixed, n_apf, prm, out=out, candidates=16,
-                                               probe_steps=100)[0],
-              "mfi": gm.autotune_rollout(obs, mfi, prm, out=out, candidates=16, probe_steps=100)[0],
+                                               probe_steps=nk)[0],
+              "mfi": gm.autotune_rollout(obs, mfi, prm, out=out, candidates=16, probe_steps=nk)[0],
               "apf": gm.autotune_ensemble(obs, all_apf, na, prm, out=out, candidates=16,
-                                          probe_steps=100)[0],
+                                          probe_steps=nk)[0],
               "proj": gm.autotune_ensemble(obs, mfi, 0, prm, out=out, candidates=16,
-                                           probe_steps=100, n_proj=na)[0],
+                                           probe_steps=nk, n_proj=na)[0],
               "three_kinds": gm.autotune_ensemble(obs, three, n3, prm, out=out, candidates=16,
-                                                  probe_steps=100, n_proj=n3)[0]}
+                                                  probe_steps=nk, n_proj=n3)[0]}
     cur = torch.cuda.current_stream()
     runs = {"ensemble": lambda: gm.rollout_ensemble(obs, mixed, n_apf, prm, out=out,
                                                     tuning=shapes["ensemble"]),
