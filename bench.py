@@ -941,6 +941,10 @@ def bench_culled(gm, args, n_frames=16, ticks=32):
         plan_all(i)
         plan_block(i)
     gm.sync()
+    torch.cuda.nvtx.range_push("warm_blockcull")   # one launch in a range (for ncu)
+    gm.rollout_agents_blockcull(obs, agents, prm, out=out_b, tuning=tun_b)
+    torch.cuda.nvtx.range_pop()
+    gm.sync()
     t_c = _events(torch, cur, lambda it=iter(range(ticks)): plan_culled(next(it)), ticks)
     t_a = _events(torch, cur, lambda it=iter(range(ticks)): plan_all(next(it)), ticks)
     t_b = _events(torch, cur, lambda it=iter(range(ticks)): plan_block(next(it)), ticks)
