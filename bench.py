@@ -1099,7 +1099,9 @@ def bench_served(gm, args):
     culled = {}
     for rate in (float(r) for r in str(args.serve_cull_rates).split(",")):
         s, p = run_served(True, rate, int(args.serve_cull_chunk)), run_plain(True, rate)
-        culled[f"{rate:g}_per_s"] = {"served": s, "plain": p, "p99_speedup": p["p99_ms"] / s["p99_ms"]}
+        sb = run_served("blocks", rate, int(args.serve_cull_chunk))
+        culled[f"{rate:g}_per_s"] = {"served": s, "plain": p, "p99_speedup": p["p99_ms"] / s["p99_ms"],
+                                     "served_block_culled": sb}
     return {"workload": f"{n_req} requests at 1 kHz: 200k-point tabletop frames + 4 moving spheres, "
                         "1 cm voxels, N_a in {64, 256, 1024}, N_k = 300",
             "offered_per_s": 1000.0, "served": served, "plain": plain,

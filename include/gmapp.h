@@ -665,7 +665,11 @@ typedef struct {
                                 r_d + r_a + r_O (the voxel grid as a neighbour grid, as in
                                 rollout_agents_culled; one agent per work item, 128 threads;
                                 agents_per_item and threads are then unused and every r_d
-                                must be finite); 0: all pairs */
+                                must be finite); 2: block culling in the chunk kernel (a
+                                work item's agents visit only the resident blocks of 128
+                                obstacles whose bounding box meets a gate, as in
+                                rollout_agents_blockcull; results equal culled = 0 bit for
+                                bit); 0: all pairs */
 } gmapp_server_config;
 
 /* A request: HOST cloud and agent arrays (kept alive, unmodified, by the

@@ -729,7 +729,9 @@ def _host_ptr(a):
 class Server:
     """Control-rate request server: requests (host clouds and agents) are
     admitted as arena memory frees up, advanced M steps per tick together in
-    one launch, scored and returned; see include/gmapp.h."""
+    one launch, scored and returned; see include/gmapp.h.  ``culled``:
+    False (all pairs), True (voxel-grid culling, one agent per work item) or
+    "blocks" (block culling in the chunk kernel; results equal all pairs)."""
 
     def __init__(self, max_slots=16, max_agents=1024, max_steps=300, obs_cap=32768,
                  arena_bytes=4 << 30, chunk_steps=50, agents_per_item=8, threads=256,
@@ -737,7 +739,7 @@ class Server:
         ctx = context()
         cfg = _abi.ServerConfig(int(max_slots), int(max_agents), int(max_steps), int(obs_cap),
                                 int(arena_bytes), int(chunk_steps), int(agents_per_item),
-                                int(threads), int(bool(culled)))
+                                int(threads), 2 if culled == "blocks" else int(bool(culled)))
         h = C.c_void_p()
         check(_abi.load().gmapp_server_create(ctx.handle, C.byref(cfg), C.byref(h)),
               "gmapp_server_create")

@@ -61,7 +61,12 @@ struct ChunkArgs {
     uint32_t *err;
 };
 
-template <int AG, int NT>
+// BOX (cfg.culled == 2): the pair loop visits only the resident blocks of 128
+// obstacles whose bounding box meets a gate of the item's agents (in the
+// order and lane layout of the voting loop, so the sums equal the all-pairs
+// server's bit for bit); the obstacles beyond the resident part are still
+// evaluated pair by pair.
+template <int AG, int NT, bool BOX>
 __global__ void __launch_bounds__(NT, 1) ks_chunk(const ChunkArgs A) {
     constexpr int NW = NT / 32;
     constexpr int NM = sfu_agents(AG);
@@ -72,6 +77,7 @@ __global__ void __launch_bounds__(NT, 1) ks_chunk(const ChunkArgs A) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *sx = smem, *sy = smem + A.shard_cap, *sz = smem + 2 * A.shard_cap;
     float *recv = smem + 3 * A.shard_cap;
+    float *boxes = recv + 2 * NW * AG * 2;  // [shard_cap / 128][6] (BOX)
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -163,14 +169,40 @@ __global__ void __launch_bounds__(NT, 1) ks_chunk(const ChunkArgs A) {
             if (lane == 0) atomicMax(&s_om, __float_as_int(m));  // m >= 0: ordered as ints
         }
         __syncthreads();
+        if constexpr (BOX) {
+            // bounding box of every resident block (NaN pads ignored), one warp per block
+            for (int b = warp; b < cnt_pad / 128; b += NW) {
+                float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = b * 128 + 4 * lane + q;
+                    lo[0] = fminf(lo[0], sx[i]);
+                    lo[1] = fminf(lo[1], sy[i]);
+                    lo[2] = fminf(lo[2], sz[i]);
+                    hi[0] = fmaxf(hi[0], sx[i]);
+                    hi[1] = fmaxf(hi[1], sy[i]);
+                    hi[2] = fmaxf(hi[2], sz[i]);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+                        hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+                    }
+                }
+                if (lane < 6) boxes[6 * b + lane] = lane < 3 ? lo[lane] : hi[lane - 3];
+            }
+            __syncthreads();
+        }
         const float omax2 = __int_as_float(s_om);
         const float h = S.vel_half * S.dt * S.inv_mass;
         const float goal[3] = {S.goal[0], S.goal[1], S.goal[2]};
         for (int k = item.k0; k < item.k1; ++k) {
             float *rp = recv + (k & 1) * (NW * AG * 2);
-            half_step<AG, AG, 0, NM, NT, false, true, true, false, true>(
+            half_step<AG, AG, 0, NM, NT, false, true, true, false, true, BOX>(
                 sx, sy, sz, cnt_pad, S.eps, nR2, G2a, p, rp + 2 * (warp * AG), 1u, lane, tail,
-                nullptr, nullptr, omax2);
+                nullptr, nullptr, omax2, boxes);
             __syncthreads();
             float W = 0.0f, md2 = INFINITY;
             half_combine<AG, AG, 0, false>(rp, NW, lane, W, md2);
@@ -300,16 +332,17 @@ __global__ void __launch_bounds__(kServeCullThreads) ks_chunk_culled(const Chunk
 
 using ChunkKernel = void (*)(const ChunkArgs);
 
-ChunkKernel chunk_kernel(int ag, int nt) {
-#define GMAPP_CK(AGV)                                             \
-    case AGV:                                                     \
-        switch (nt) {                                             \
-            case 256: return ks_chunk<AGV, 256>;                  \
-            case 384: return ks_chunk<AGV, 384>;                  \
-            case 512:                                             \
-                if constexpr (AGV <= 8) return ks_chunk<AGV, 512>; \
-                return nullptr;                                   \
-            default: return nullptr;                              \
+template <bool BOX>
+ChunkKernel chunk_kernel_t(int ag, int nt) {
+#define GMAPP_CK(AGV)                                                  \
+    case AGV:                                                          \
+        switch (nt) {                                                  \
+            case 256: return ks_chunk<AGV, 256, BOX>;                  \
+            case 384: return ks_chunk<AGV, 384, BOX>;                  \
+            case 512:                                                  \
+                if constexpr (AGV <= 8) return ks_chunk<AGV, 512, BOX>; \
+                return nullptr;                                        \
+            default: return nullptr;                                   \
         }
     switch (ag) {
         GMAPP_CK(4)
@@ -318,6 +351,10 @@ ChunkKernel chunk_kernel(int ag, int nt) {
         default: return nullptr;
     }
 #undef GMAPP_CK
+}
+
+ChunkKernel chunk_kernel(int ag, int nt, bool box) {
+    return box ? chunk_kernel_t<true>(ag, nt) : chunk_kernel_t<false>(ag, nt);
 }
 
 double now_s() {
@@ -432,7 +469,7 @@ size_t request_bytes(const gmapp_server_config &c, const gmapp_request &r, size_
     add(na * 6 * 4 + na * 4);                          // p_final, v_final, path_len
     add(na * (nk + 1) * 12);                           // trajectories
     add(na * 4 + 4 + (nk + 1) * 12);                   // costs, best, best trajectory
-    if (c.culled) add(gmapp_grid_index_bytes(&r.ws));  // neighbour index
+    if (c.culled == 1) add(gmapp_grid_index_bytes(&r.ws));  // neighbour index
     return b;
 }
 
@@ -463,8 +500,8 @@ gmapp_status admit(gmapp_server *s, ServerReq *q) {
     float *fin = reinterpret_cast<float *>(take(na * 6 * 4 + na * 4));
     q->out.traj = reinterpret_cast<float *>(take(na * (nk + 1) * 12));
     float *sel = reinterpret_cast<float *>(take(na * 4 + 4 + (nk + 1) * 12));
-    const size_t index_bytes = s->cfg.culled ? gmapp_grid_index_bytes(&r.ws) : 0;
-    uint32_t *index = s->cfg.culled ? reinterpret_cast<uint32_t *>(take(index_bytes)) : nullptr;
+    const size_t index_bytes = s->cfg.culled == 1 ? gmapp_grid_index_bytes(&r.ws) : 0;
+    uint32_t *index = s->cfg.culled == 1 ? reinterpret_cast<uint32_t *>(take(index_bytes)) : nullptr;
     q->out.p_final = fin;
     q->out.v_final = fin + 3 * na;
     q->out.path_len = fin + 6 * na;
@@ -564,12 +601,14 @@ extern "C" gmapp_status gmapp_server_create(gmapp_ctx *ctx, const gmapp_server_c
                                             gmapp_server **out) {
     if (!ctx || !cfg || !out || cfg->max_slots < 1 || cfg->arena_bytes < (1 << 20) ||
         cfg->chunk_steps < 1 || cfg->obs_cap < 4 || cfg->obs_cap % 4 ||
-        cfg->max_agents < 1 || cfg->max_steps < 1) {
+        cfg->max_agents < 1 || cfg->max_steps < 1 || cfg->culled < 0 || cfg->culled > 2) {
         set_error("gmapp_server_create: invalid configuration");
         return GMAPP_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    ChunkKernel fn = cfg->culled ? ks_chunk_culled : chunk_kernel(cfg->agents_per_item, cfg->threads);
+    const bool grid_cull = cfg->culled == 1;  // 2: block culling in the chunk kernel
+    ChunkKernel fn = grid_cull ? ks_chunk_culled
+                               : chunk_kernel(cfg->agents_per_item, cfg->threads, cfg->culled == 2);
     if (!fn) {
         set_error("gmapp_server_create: no chunk kernel for %d agents per item, %d threads",
                   cfg->agents_per_item, cfg->threads);
@@ -587,14 +626,18 @@ extern "C" gmapp_status gmapp_server_create(gmapp_ctx *ctx, const gmapp_server_c
         (static_cast<int64_t>(ctx->max_smem_optin) - static_cast<int64_t>(fa.sharedSizeBytes + recv_bytes)) / 12;
     // the culled kernel reads obstacles through the neighbour index (no shard)
     // a multiple of 128: the pair loop tests whole blocks of 128 obstacles
-    s->shard_cap = cfg->culled ? 0
-                               : static_cast<int>(std::min<int64_t>(
-                                     (static_cast<int64_t>(cfg->obs_cap) + 127) & ~int64_t(127),
-                                     room & ~int64_t(127)));
-    s->smem = cfg->culled ? 0 : static_cast<size_t>(s->shard_cap) * 12 + recv_bytes;
-    const int threads = cfg->culled ? kServeCullThreads : cfg->threads;
+    // (block culling: + 6 floats of bounding box per 128 resident obstacles)
+    const int64_t room_b = cfg->culled == 2 ? room * 128 / (128 + 2) : room;
+    s->shard_cap = grid_cull ? 0
+                             : static_cast<int>(std::min<int64_t>(
+                                   (static_cast<int64_t>(cfg->obs_cap) + 127) & ~int64_t(127),
+                                   room_b & ~int64_t(127)));
+    s->smem = grid_cull ? 0
+                        : static_cast<size_t>(s->shard_cap) * 12 + recv_bytes +
+                              (cfg->culled == 2 ? static_cast<size_t>(s->shard_cap / 128) * 24 : 0);
+    const int threads = grid_cull ? kServeCullThreads : cfg->threads;
     const int max_groups =
-        cfg->culled ? cfg->max_agents : (cfg->max_agents + cfg->agents_per_item - 1) / cfg->agents_per_item;
+        grid_cull ? cfg->max_agents : (cfg->max_agents + cfg->agents_per_item - 1) / cfg->agents_per_item;
     s->max_items = cfg->max_slots * max_groups;
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
@@ -739,7 +782,7 @@ extern "C" gmapp_status gmapp_server_tick(gmapp_server *s, int32_t *n_active) {
         const int N = q->req.prm.n_steps;
         const int k1 = std::min(N, q->k + s->cfg.chunk_steps);
         // culled: one agent per item (group = agent index)
-        const int groups = s->cfg.culled
+        const int groups = s->cfg.culled == 1
                                ? q->req.n_agents
                                : (q->req.n_agents + s->cfg.agents_per_item - 1) / s->cfg.agents_per_item;
         for (int g = 0; g < groups; ++g) {
@@ -761,7 +804,7 @@ extern "C" gmapp_status gmapp_server_tick(gmapp_server *s, int32_t *n_active) {
         GMAPP_CHECK_CUDA(cudaMemsetAsync(s->d_head, 0, sizeof(uint32_t), s->compute));
         ChunkArgs A{s->d_slots, s->d_items, n_items, s->d_head, s->shard_cap, s->ctx->d_err};
         const int grid = std::max(1, std::min(n_items, s->resident));
-        s->fn<<<grid, s->cfg.culled ? kServeCullThreads : s->cfg.threads, s->smem, s->compute>>>(A);
+        s->fn<<<grid, s->cfg.culled == 1 ? kServeCullThreads : s->cfg.threads, s->smem, s->compute>>>(A);
         GMAPP_CHECK_CUDA(cudaGetLastError());
     }
     // 4. requests that reached their horizon: score, copy the plan out

@@ -157,3 +157,16 @@ def test_culled_chunk_size_does_not_change_results(gm):
     for x, y in zip(a, b):
         assert np.array_equal(x["best_traj"], y["best_traj"])
         assert np.array_equal(x["costs"], y["costs"])
+
+
+def test_block_culled_server_equals_all_pairs_server(gm):
+    """culled = "blocks": each work item's agents visit only the resident
+    obstacle blocks whose bounding box meets a gate, in the voting loop's
+    order, so every result equals the all-pairs server's bit for bit."""
+    ws = _requests()
+    a, _, _ = _serve(gm, ws, stagger=True)
+    b, _, _ = _serve(gm, ws, stagger=True, culled="blocks")
+    for ra, rb in zip(a, b):
+        assert ra["best"] == rb["best"] and ra["n_obs"] == rb["n_obs"]
+        assert np.array_equal(ra["costs"].view(np.uint32), rb["costs"].view(np.uint32))
+        assert np.array_equal(ra["best_traj"].view(np.uint32), rb["best_traj"].view(np.uint32))
