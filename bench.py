@@ -635,6 +635,14 @@ def bench_batched(gm, args, reps=3):
     with torch.cuda.stream(s):
         t_batch = _events(torch, s, lambda: b.launch_graph(s), reps)
     gm.sync(s)
+    # the same batch with block culling in the rollout kernel (same results;
+    # plans/s only: culled pairs are not interactions)
+    b.set_culling(True)
+    b.launch_graph(s)
+    gm.sync(s)
+    t_cull = _events(torch, s, lambda: b.launch_graph(s), reps)
+    gm.sync(s)
+    b.set_culling(False)
     # plain per-query path
     outs = []
     for sp in specs:
@@ -663,6 +671,7 @@ def bench_batched(gm, args, reps=3):
                         "launches": 7, "graph": True},
             "plain": {"plans_per_s": 64 / t_plain, "interactions_per_s": inter / t_plain,
                       "ms": 1e3 * t_plain, "launches": 64 * LAUNCHES_PER_STEP},
+            "batched_block_culled": {"plans_per_s": 64 / t_cull, "ms": 1e3 * t_cull},
             "speedup": t_plain / t_batch}
 
 

@@ -626,6 +626,14 @@ void gmapp_batch_destroy(gmapp_batch *batch);
 gmapp_status gmapp_batch_set_tuning(gmapp_batch *batch, int32_t agents_per_item,
                                     int32_t threads);
 
+/* on != 0: block culling in the persistent rollout kernel -- a work item's
+ * agents visit only the resident blocks of 128 obstacles whose bounding box
+ * meets one of their gates (as rollout_agents_blockcull); results equal the
+ * unculled batch's bit for bit, except the clearance, which then comes from
+ * the visited obstacles (as for rollout_agents_blockcull).  Discards a
+ * captured graph. */
+gmapp_status gmapp_batch_set_culling(gmapp_batch *batch, int32_t on);
+
 /* Enqueue the whole batch on `stream`: batched filter (5 launches over all
  * queries), the planner (N_O of every query, work items ordered by cost,
  * largest first), ONE persistent rollout launch whose CTAs pop

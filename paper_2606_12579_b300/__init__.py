@@ -702,6 +702,11 @@ class Batch:
         check(_abi.load().gmapp_batch_set_tuning(self.handle, int(agents_per_item), int(threads)),
               "gmapp_batch_set_tuning")
 
+    def set_culling(self, on: bool) -> None:
+        """Block culling in the rollout kernel (results unchanged)."""
+        check(_abi.load().gmapp_batch_set_culling(self.handle, int(bool(on))),
+              "gmapp_batch_set_culling")
+
     def autotune(self, stream=None):
         t = _abi.Tuning()
         ms = C.c_float()

@@ -164,6 +164,7 @@ PROTOTYPES = {
     "gmapp_batch_create": (C.c_int, [P, C.POINTER(Query), C.c_int32, C.POINTER(P)]),
     "gmapp_batch_destroy": (None, [P]),
     "gmapp_batch_set_tuning": (C.c_int, [P, C.c_int32, C.c_int32]),
+    "gmapp_batch_set_culling": (C.c_int, [P, C.c_int32]),
     "rollout_batch": (C.c_int, [P, P]),
     "gmapp_batch_launch_graph": (C.c_int, [P, P]),
     "gmapp_batch_autotune": (C.c_int, [P, P, C.POINTER(Tuning), C.POINTER(C.c_float)]),

@@ -136,7 +136,11 @@ __global__ void __launch_bounds__(1024) kb_plan(const BatchDev B, int32_t agents
     (void)agents_per_item;
 }
 
-template <int AG, int NT, bool CLEAR>
+// BOX (gmapp_batch_set_culling): the pair loop visits only the resident
+// blocks of 128 obstacles whose bounding box meets a gate of the item's
+// agents, in the voting loop's order (results equal the unculled batch's bit
+// for bit); the obstacles beyond the resident part are evaluated pair by pair.
+template <int AG, int NT, bool CLEAR, bool BOX>
 __global__ void __launch_bounds__(NT, 1) kb_rollout(const BatchDev B) {
     constexpr int NW = NT / 32;
     constexpr int NM = sfu_agents(AG);
@@ -147,6 +151,7 @@ __global__ void __launch_bounds__(NT, 1) kb_rollout(const BatchDev B) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *sx = smem, *sy = smem + B.shard_cap, *sz = smem + 2 * B.shard_cap;
     float *recv = smem + 3 * B.shard_cap;  // [2][NW][AG] x (W, min |d|^2)
+    float *boxes = recv + 2 * NW * AG * 2;  // [shard_cap / 128][6] (BOX)
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -238,14 +243,40 @@ __global__ void __launch_bounds__(NT, 1) kb_rollout(const BatchDev B) {
             if (lane == 0) atomicMax(&s_om, __float_as_int(m));  // m >= 0: ordered as ints
         }
         __syncthreads();
+        if constexpr (BOX) {
+            // bounding box of every resident block (NaN pads ignored), one warp per block
+            for (int b = warp; b < cnt_pad / 128; b += NW) {
+                float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = b * 128 + 4 * lane + q;
+                    lo[0] = fminf(lo[0], sx[i]);
+                    lo[1] = fminf(lo[1], sy[i]);
+                    lo[2] = fminf(lo[2], sz[i]);
+                    hi[0] = fmaxf(hi[0], sx[i]);
+                    hi[1] = fmaxf(hi[1], sy[i]);
+                    hi[2] = fmaxf(hi[2], sz[i]);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+                        hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+                    }
+                }
+                if (lane < 6) boxes[6 * b + lane] = lane < 3 ? lo[lane] : hi[lane - 3];
+            }
+            __syncthreads();
+        }
         const float omax2 = __int_as_float(s_om);
         const float h = Q.vel_half * Q.dt * Q.inv_mass;
         const float goal[3] = {Q.goal[0], Q.goal[1], Q.goal[2]};
         for (int k = 0; k < N; ++k) {
             float *rp = recv + (k & 1) * (NW * AG * 2);
-            half_step<AG, AG, 0, NM, NT, CLEAR, true, true, false, true>(
+            half_step<AG, AG, 0, NM, NT, CLEAR, true, true, false, true, BOX>(
                 sx, sy, sz, cnt_pad, Q.eps, nR2, G2a, p, rp + 2 * (warp * AG), 1u, lane, tail,
-                nullptr, nullptr, omax2);
+                nullptr, nullptr, omax2, boxes);
             __syncthreads();
             float W = 0.0f, md2 = INFINITY;
             half_combine<AG, AG, 0, CLEAR>(rp, NW, lane, W, md2);
@@ -298,17 +329,17 @@ __global__ void __launch_bounds__(kScoreThreads) kb_score(const BatchDev B) {
 
 using BatchKernel = void (*)(const BatchDev);
 
-template <bool CLEAR>
+template <bool CLEAR, bool BOX>
 BatchKernel batch_kernel_for(int ag, int nt) {
-#define GMAPP_BK(AGV)                                             \
-    case AGV:                                                     \
-        switch (nt) {                                             \
-            case 256: return kb_rollout<AGV, 256, CLEAR>;         \
-            case 384: return kb_rollout<AGV, 384, CLEAR>;         \
-            case 512:                                             \
-                if constexpr (AGV <= 8) return kb_rollout<AGV, 512, CLEAR>; \
-                return nullptr;                                   \
-            default: return nullptr;                              \
+#define GMAPP_BK(AGV)                                                  \
+    case AGV:                                                          \
+        switch (nt) {                                                  \
+            case 256: return kb_rollout<AGV, 256, CLEAR, BOX>;         \
+            case 384: return kb_rollout<AGV, 384, CLEAR, BOX>;         \
+            case 512:                                                  \
+                if constexpr (AGV <= 8) return kb_rollout<AGV, 512, CLEAR, BOX>; \
+                return nullptr;                                        \
+            default: return nullptr;                                   \
         }
     switch (ag) {
         GMAPP_BK(2)
@@ -322,8 +353,9 @@ BatchKernel batch_kernel_for(int ag, int nt) {
 #undef GMAPP_BK
 }
 
-BatchKernel batch_kernel(int ag, int nt, bool clear) {
-    return clear ? batch_kernel_for<true>(ag, nt) : batch_kernel_for<false>(ag, nt);
+BatchKernel batch_kernel(int ag, int nt, bool clear, bool box) {
+    if (box) return clear ? batch_kernel_for<true, true>(ag, nt) : batch_kernel_for<false, true>(ag, nt);
+    return clear ? batch_kernel_for<true, false>(ag, nt) : batch_kernel_for<false, false>(ag, nt);
 }
 
 }  // namespace
@@ -343,6 +375,7 @@ struct gmapp_batch {
     int32_t pt_blocks = 0, bm_blocks = 0, sb_blocks = 0, n_items = 0, shard_cap = 0;
     int64_t max_cap = 4;  // largest obstacle capacity over the queries
     bool clear = false;
+    bool cull = false;  // block culling in the rollout kernel (gmapp_batch_set_culling)
     int32_t agents_per_item = 8, threads = 256;
     BatchKernel fn = nullptr;
     size_t smem = 0;
@@ -370,7 +403,7 @@ void release(gmapp_batch *b) {
 
 // (Re)build the item list and the kernel choice for a tuning.
 gmapp_status apply_tuning(gmapp_batch *b, int32_t agents_per_item, int32_t threads) {
-    BatchKernel fn = batch_kernel(agents_per_item, threads, b->clear);
+    BatchKernel fn = batch_kernel(agents_per_item, threads, b->clear, b->cull);
     if (!fn) {
         set_error("gmapp_batch: no kernel for %d agents per item and %d threads", agents_per_item,
                   threads);
@@ -382,8 +415,10 @@ gmapp_status apply_tuning(gmapp_batch *b, int32_t agents_per_item, int32_t threa
     GMAPP_CHECK_CUDA(cudaFuncGetAttributes(&fa, reinterpret_cast<const void *>(fn)));
     const size_t recv_bytes =
         static_cast<size_t>(2) * (threads / 32) * agents_per_item * 2 * sizeof(float);
+    // (the obstacles' 12 B each, and with culling 6 floats of bounding box per 128)
     const int64_t room = (static_cast<int64_t>(b->ctx->max_smem_optin) -
-                          static_cast<int64_t>(fa.sharedSizeBytes + recv_bytes)) / 12;
+                          static_cast<int64_t>(fa.sharedSizeBytes + recv_bytes)) * 128 /
+                         (12 * 128 + (b->cull ? 24 : 0));
     // a multiple of 128: the pair loop tests whole blocks of 128 obstacles
     b->shard_cap = static_cast<int32_t>(std::min<int64_t>((b->max_cap + 127) & ~int64_t(127),
                                                           room & ~int64_t(127)));
@@ -391,7 +426,8 @@ gmapp_status apply_tuning(gmapp_batch *b, int32_t agents_per_item, int32_t threa
         set_error("gmapp_batch: no shared memory left for obstacles");
         return GMAPP_ERR_CAPACITY;
     }
-    const size_t smem = static_cast<size_t>(b->shard_cap) * 3 * sizeof(float) + recv_bytes;
+    const size_t smem = static_cast<size_t>(b->shard_cap) * 3 * sizeof(float) + recv_bytes +
+                        (b->cull ? static_cast<size_t>(b->shard_cap / 128) * 24 : 0);
     std::vector<int32_t> items;
     for (int q = 0; q < b->n_q; ++q) {
         const int groups = (b->hq[q].n_agents + agents_per_item - 1) / agents_per_item;
@@ -645,6 +681,18 @@ extern "C" gmapp_status gmapp_batch_set_tuning(gmapp_batch *b, int32_t agents_pe
         return GMAPP_ERR_INVALID_ARG;
     }
     return apply_tuning(b, agents_per_item, threads);
+}
+
+extern "C" gmapp_status gmapp_batch_set_culling(gmapp_batch *b, int32_t on) {
+    if (!b) {
+        set_error("gmapp_batch_set_culling: NULL batch");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    const bool prev = b->cull;
+    b->cull = on != 0;
+    const gmapp_status st = apply_tuning(b, b->agents_per_item, b->threads);
+    if (st != GMAPP_OK) b->cull = prev;
+    return st;
 }
 
 extern "C" gmapp_status rollout_batch(gmapp_batch *b, gmapp_stream stream) {

@@ -167,3 +167,29 @@ def test_obstacle_sets_larger_than_shared_memory(gm):
     obs = np.stack([ref_f["x"], ref_f["y"], ref_f["z"]])
     ref = oracle.rollout(obs, ref_f["r_O"], w["agents"], w["params"])
     assert np.abs(r["out"]["traj"].cpu().numpy() - ref["traj"]).max() <= POS_TOL
+
+
+@pytest.mark.parametrize("clear", [False, True])
+def test_block_culled_batch_equals_unculled(gm, clear):
+    """gmapp_batch_set_culling: the work items visit only the resident
+    obstacle blocks whose bounding box meets a gate; trajectories, path
+    lengths, costs and the selections equal the unculled batch's bit for bit
+    (with the clearance, the costs use the culled clearance, so only the
+    trajectories and path lengths are compared)."""
+    ws_list = _small_queries(seed=11)
+    outs = []
+    for cull in (False, True):
+        b = gm.Batch(_specs(ws_list), want_clear=clear)
+        b.set_culling(cull)
+        b.run()
+        gm.sync()
+        outs.append(b)
+    for q in range(len(ws_list)):
+        a, c = outs[0].results[q], outs[1].results[q]
+        for k in ("traj", "p_final", "v_final", "path_len"):
+            assert np.array_equal(a["out"][k].cpu().numpy().view(np.uint32),
+                                  c["out"][k].cpu().numpy().view(np.uint32)), (q, k)
+        if not clear:
+            assert np.array_equal(a["costs"].cpu().numpy().view(np.uint32),
+                                  c["costs"].cpu().numpy().view(np.uint32)), q
+            assert int(a["best"].item()) == int(c["best"].item())
