@@ -182,12 +182,25 @@ def run_reference(args, ws, rank):
             "data": "synthetic", "impl": "reference",
             "config": _config(base, args, ws),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "cpu_model": _cpu_model(),
                              "sample": f"per step: full-frame filter + {sample} of "
                                        f"{base['agents']['k_r'].size} agents x all obstacles x "
                                        f"{base['params'].n_steps} steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
 
 
 def _config(base, args, ws):
@@ -1144,6 +1157,7 @@ def cpu_baseline(base, frames, n_agents_sample, min_seconds=10.0, max_steps=8):
     finally:
         oracle.set_threads(cores)
     return {"value": inter / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": _cpu_model(),
             "sample": f"{steps} steps on distinct frames, each: full-frame filter + "
                       f"{n_agents_sample} of {base['agents']['k_r'].size} agents x all obstacles x "
                       f"{base['params'].n_steps} steps",
@@ -1160,7 +1174,9 @@ def main():
     ap.add_argument("--frames", type=int, default=48)
     ap.add_argument("--cpu-agents", type=int, default=256,
                     help="agents per step of the oracle's cpu_baseline")
-    ap.add_argument("--ref-agents", type=int, default=8)
+    ap.add_argument("--ref-agents", type=int, default=256,
+                    help="agents per step of the --impl reference arm (all 256 by default, "
+                         "so the oracle's OpenMP threads over agents all have work)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--obs-cap", type=int, default=0,
                     help="obstacle capacity of the S_W buffers (multiple of 4; 0 = from the scene)")

@@ -153,18 +153,25 @@ gmapp_status filter_cloud(gmapp_ctx *ctx, const float *xyz, int64_t n_raw,
  *   - Sizes whose scratch would exceed 16 MiB (see
  *     gmapp_filter_workspace_bytes) are rejected with GMAPP_ERR_CAPACITY
  *     before anything is launched.
- *   - The call allocates and frees nothing.  Its first call on a device
- *     looks up the array's device address (cudaGetSymbolAddress) with that
- *     device current; make that first call before any stream capture.
+ *   - The call allocates and frees nothing.  Every call looks up the
+ *     array's device address (cudaGetSymbolAddress) on the current device;
+ *     the first call on a device loads the library's module there, so make
+ *     it before any stream capture.
  *   - All calls share the one array (the kernels clear what must start at
  *     zero), so calls whose work overlaps on the GPU -- on different streams
  *     or devices' threads racing on one device -- race with each other;
  *     order them on one stream.
- *   - Output overflow is reported through *out->n > out->cap only (there is
- *     no context error word). */
+ *   - Output overflow: *out->n > out->cap, and a capacity flag that
+ *     filter_cloud_noalloc_status reports (there is no context error word). */
 gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, const float T[12],
                                   const gmapp_workspace *ws, gmapp_obstacles *out,
                                   gmapp_stream stream);
+
+/* Status of the latest filter_cloud_noalloc call on the current device:
+ * waits for `stream`, then returns GMAPP_ERR_CAPACITY when that call found
+ * more voxels than out->cap, else GMAPP_OK.  Each filter_cloud_noalloc call
+ * clears the flag first.  Allocates nothing. */
+gmapp_status filter_cloud_noalloc_status(gmapp_stream stream);
 
 /* Batched filter: many clouds (a stream of frames, or several sensors) through
  * one sequence of four launches (Sec. IV-B, Sec. V-A, as filter_cloud).  The

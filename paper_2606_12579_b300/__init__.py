@@ -21,11 +21,11 @@ from . import _abi
 from ._abi import check
 
 __all__ = ["Context", "context", "Obstacles", "filter_cloud", "filter_clouds",
-           "filter_cloud_noalloc",
+           "filter_cloud_noalloc", "filter_cloud_noalloc_status",
            "filter_workspace_bytes", "rollout_agents", "rollout_ensemble", "score_and_select",
            "score_and_select4", "grid_index", "rollout_agents_culled",
            "pick_tuning", "autotune_rollout", "autotune_ensemble", "rollout_adjoint", "GMappRollout", "sync", "GmappError",
-           "FilterBatch", "Batch", "Server"]
+           "FilterBatch", "Batch", "Server", "measure_peaks"]
 
 GmappError = _abi.GmappError
 
@@ -168,6 +168,15 @@ def _ws_struct(ws) -> _abi.Workspace:
     return s
 
 
+def measure_peaks(reps: int = 5) -> dict:
+    """Measured FP32 FMA (packed and scalar) and SFU rates of the current GPU
+    (gmapp_measure_peaks): the denominators of the force kernel's roofline."""
+    context()
+    p = _abi.Peaks()
+    check(_abi.load().gmapp_measure_peaks(int(reps), C.byref(p)), "gmapp_measure_peaks")
+    return {f: getattr(p, f) for f, _ in _abi.Peaks._fields_}
+
+
 def filter_workspace_bytes(n_raw: int, ws) -> int:
     return int(_abi.load().gmapp_filter_workspace_bytes(int(n_raw), C.byref(_ws_struct(ws))))
 
@@ -240,6 +249,12 @@ def filter_cloud_noalloc(xyz, T, ws, out: Obstacles, stream=None) -> Obstacles:
                                            _stream(stream)), "filter_cloud_noalloc")
     out.r_O = float(ob.r_O)
     return out
+
+
+def filter_cloud_noalloc_status(stream=None) -> None:
+    """Waits for ``stream`` and raises GmappError (GMAPP_ERR_CAPACITY) when the
+    latest filter_cloud_noalloc call found more voxels than ``out.cap``."""
+    check(_abi.load().filter_cloud_noalloc_status(_stream(stream)), "filter_cloud_noalloc_status")
 
 
 # ---------------------------------------------------------------------------

@@ -1,4 +1,4 @@
-"""ctypes mirror of include/gmapp.h: structures, status codes, prototypes.
+"""ctypes mirror of include/gmapp.h (and include/gmapp_peaks.h): structures, status codes, prototypes.
 
 Loading the library needs no GPU (the CUDA runtime is linked statically and
 binds to the driver on the first CUDA call); every compute call does.
@@ -103,6 +103,15 @@ class Result(C.Structure):
                 ("t_admit", C.c_double), ("t_done", C.c_double)]
 
 
+class Peaks(C.Structure):
+    """gmapp_peaks (include/gmapp_peaks.h)."""
+    _fields_ = [("fp32_tflops", C.c_double), ("fp32_tflops_scalar", C.c_double),
+                ("fma_lanes_per_clk_sm", C.c_double), ("fma_lanes_per_clk_sm_scalar", C.c_double),
+                ("sfu_lanes_per_clk_sm", C.c_double), ("sfu_gops", C.c_double),
+                ("mix_fma_busy", C.c_double), ("mix_sfu_busy", C.c_double),
+                ("sm_mhz", C.c_double), ("sm_count", C.c_int32)]
+
+
 class ServerStats(C.Structure):
     _fields_ = [("active", C.c_int32), ("pending", C.c_int32), ("completed", C.c_int64),
                 ("arena_free_bytes", C.c_int64), ("shard_cap", C.c_int32)]
@@ -125,6 +134,8 @@ PROTOTYPES = {
                                 C.POINTER(Obstacles), P, C.c_size_t, P]),
     "filter_cloud_noalloc": (C.c_int, [P, C.c_int64, C.POINTER(C.c_float * 12),
                                        C.POINTER(Workspace), C.POINTER(Obstacles), P]),
+    "filter_cloud_noalloc_status": (C.c_int, [P]),
+    "gmapp_measure_peaks": (C.c_int, [C.c_int32, C.POINTER(Peaks)]),
     "rollout_agents": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),
                                  C.POINTER(RolloutParams), C.POINTER(RolloutOut), P]),
     "rollout_agents_tuned": (C.c_int, [P, C.POINTER(Obstacles), C.POINTER(Agents),

@@ -1,7 +1,8 @@
 """Build ``libgmapp.so`` (the C-ABI CUDA library) in-tree for sm_103a.
 
 Each ``csrc/*.cu`` is compiled to an object in ``_build/`` (in parallel),
-then linked into ``paper_2606_12579_b300/libgmapp.so``.  The CUDA runtime is
+then linked into ``paper_2606_12579_b300/libgmapp.so``; an object is
+recompiled only when its source or a header it includes is newer.  The CUDA runtime is
 linked statically, so the library needs only the driver at run time.
 
 ``build(bounds_check=True)`` builds the bounds-checked variant
@@ -15,6 +16,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import os
+import re
 import subprocess
 import sys
 
@@ -38,8 +40,33 @@ def _deps():
         os.path.join(os.path.dirname(HERE), "include", "gmapp.h")]
 
 
-def _compile(src: str, verbose: bool, bdir: str = BUILD, extra=()) -> str:
+_INCLUDE = re.compile(r'^\s*#\s*include\s+"([^"]+)"', re.M)
+
+
+def _closure(src: str, seen=None) -> set:
+    """The file and every quoted include it reaches (transitively)."""
+    seen = set() if seen is None else seen
+    src = os.path.normpath(src)
+    if src in seen or not os.path.exists(src):
+        return seen
+    seen.add(src)
+    with open(src) as f:
+        for inc in _INCLUDE.findall(f.read()):
+            _closure(os.path.join(os.path.dirname(src), inc), seen)
+    return seen
+
+
+def _stale(src: str, obj: str) -> bool:
+    if not os.path.exists(obj):
+        return True
+    t = os.path.getmtime(obj)
+    return any(os.path.getmtime(d) > t for d in _closure(src))
+
+
+def _compile(src: str, verbose: bool, bdir: str = BUILD, extra=(), force: bool = True) -> str:
     obj = os.path.join(bdir, os.path.basename(src) + ".o")
+    if not force and not verbose and not _stale(src, obj):
+        return obj
     cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
@@ -60,7 +87,7 @@ def build(force: bool = False, verbose: bool = False, bounds_check: bool = False
         return lib
     os.makedirs(bdir, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose, bdir, extra), _sources()))
+        objs = list(ex.map(lambda s: _compile(s, verbose, bdir, extra, force), _sources()))
     tmp = lib + ".tmp"
     subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, lib)

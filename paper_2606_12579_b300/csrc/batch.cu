@@ -410,28 +410,33 @@ gmapp_status apply_tuning(gmapp_batch *b, int32_t agents_per_item, int32_t threa
         return GMAPP_ERR_INVALID_ARG;
     }
     // resident part of each obstacle set: as much as shared memory holds
-    // after the receive slots (larger sets stream their remainder from L2)
+    // after the receive slots (larger sets stream their remainder from L2).
+    // The room for the culling boxes (6 floats per 128 obstacles) is kept
+    // whether or not culling is on, so both modes hold the same obstacles in
+    // shared memory and give bit-identical sums.
     cudaFuncAttributes fa;
     GMAPP_CHECK_CUDA(cudaFuncGetAttributes(&fa, reinterpret_cast<const void *>(fn)));
     const size_t recv_bytes =
         static_cast<size_t>(2) * (threads / 32) * agents_per_item * 2 * sizeof(float);
-    // (the obstacles' 12 B each, and with culling 6 floats of bounding box per 128)
     const int64_t room = (static_cast<int64_t>(b->ctx->max_smem_optin) -
                           static_cast<int64_t>(fa.sharedSizeBytes + recv_bytes)) * 128 /
-                         (12 * 128 + (b->cull ? 24 : 0));
+                         (12 * 128 + 24);
     // a multiple of 128: the pair loop tests whole blocks of 128 obstacles
-    b->shard_cap = static_cast<int32_t>(std::min<int64_t>((b->max_cap + 127) & ~int64_t(127),
-                                                          room & ~int64_t(127)));
-    if (b->shard_cap < 128) {
+    const int32_t shard_cap = static_cast<int32_t>(std::min<int64_t>(
+        (b->max_cap + 127) & ~int64_t(127), room & ~int64_t(127)));
+    if (shard_cap < 128) {
         set_error("gmapp_batch: no shared memory left for obstacles");
         return GMAPP_ERR_CAPACITY;
     }
-    const size_t smem = static_cast<size_t>(b->shard_cap) * 3 * sizeof(float) + recv_bytes +
-                        (b->cull ? static_cast<size_t>(b->shard_cap / 128) * 24 : 0);
+    const size_t smem = static_cast<size_t>(shard_cap) * 3 * sizeof(float) + recv_bytes +
+                        (b->cull ? static_cast<size_t>(shard_cap / 128) * 24 : 0);
+    // every check runs before the batch changes: a rejected tuning leaves
+    // the kernel, its shard size and the device item list as they were
+    std::vector<QueryDev> hq = b->hq;
     std::vector<int32_t> items;
     for (int q = 0; q < b->n_q; ++q) {
-        const int groups = (b->hq[q].n_agents + agents_per_item - 1) / agents_per_item;
-        b->hq[q].n_groups = groups;
+        const int groups = (hq[q].n_agents + agents_per_item - 1) / agents_per_item;
+        hq[q].n_groups = groups;
         if (q > 0xffff || groups > 0xffff) {
             set_error("gmapp_batch: too many queries or agent groups");
             return GMAPP_ERR_CAPACITY;
@@ -443,10 +448,6 @@ gmapp_status apply_tuning(gmapp_batch *b, int32_t agents_per_item, int32_t threa
                   items.size(), kMaxItems);
         return GMAPP_ERR_CAPACITY;
     }
-    GMAPP_CHECK_CUDA(cudaMemcpy(b->d_q, b->hq.data(), sizeof(QueryDev) * b->n_q,
-                                cudaMemcpyHostToDevice));
-    GMAPP_CHECK_CUDA(cudaMemcpy(b->d_items_static, items.data(), sizeof(int32_t) * items.size(),
-                                cudaMemcpyHostToDevice));
     GMAPP_CHECK_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           static_cast<int>(smem)));
@@ -460,6 +461,18 @@ gmapp_status apply_tuning(gmapp_batch *b, int32_t agents_per_item, int32_t threa
         set_error("gmapp_batch: rollout kernel cannot be resident");
         return GMAPP_ERR_CAPACITY;
     }
+    // commit: device tables first; if a copy fails the batch refuses to run
+    cudaError_t e = cudaMemcpy(b->d_q, hq.data(), sizeof(QueryDev) * b->n_q,
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_items_static, items.data(), sizeof(int32_t) * items.size(),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        b->fn = nullptr;
+        return cuda_fail(e, "gmapp_batch: tuning tables");
+    }
+    b->hq = std::move(hq);
+    b->shard_cap = shard_cap;
     b->n_items = static_cast<int32_t>(items.size());
     b->grid = std::max(1, std::min(b->n_items, per_sm * b->ctx->sm_count));
     b->fn = fn;
@@ -698,6 +711,10 @@ extern "C" gmapp_status gmapp_batch_set_culling(gmapp_batch *b, int32_t on) {
 extern "C" gmapp_status rollout_batch(gmapp_batch *b, gmapp_stream stream) {
     if (!b) {
         set_error("rollout_batch: NULL batch");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    if (!b->fn) {
+        set_error("rollout_batch: the batch has no usable tuning (a tuning copy failed)");
         return GMAPP_ERR_INVALID_ARG;
     }
     const BatchDev B = dev_view(b);

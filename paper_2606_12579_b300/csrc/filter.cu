@@ -17,7 +17,6 @@
 #include <math.h>
 
 #include <algorithm>
-#include <mutex>
 
 
 #include "filter_device.cuh"
@@ -221,38 +220,27 @@ namespace gmapp {
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
-constexpr int kNoAllocMaxDevices = 64;
-
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+// Capacity flag of the latest call (GMAPP_DEVERR_CAPACITY when more voxels
+// qualified than out->cap); cleared at the start of every call and read by
+// filter_cloud_noalloc_status.
 static __device__ uint32_t g_noalloc_err;
 
-// Device addresses of the two symbols, looked up once per device (host code
-// may not use the symbols' names as addresses).
+// Device addresses of the two symbols on the current device (host code may
+// not use the symbols' names as addresses).  Looked up on every call: the
+// lookup allocates nothing, and a cached address would go stale after a
+// device reset reloads the module.
 struct NoAllocSymbols {
     void *scratch = nullptr;
     uint32_t *err = nullptr;
 };
-NoAllocSymbols g_noalloc_syms[kNoAllocMaxDevices];
-std::mutex g_noalloc_mu;
 
 gmapp_status noalloc_symbols(NoAllocSymbols *out) {
-    int dev = 0;
-    GMAPP_CHECK_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kNoAllocMaxDevices) {
-        set_error("filter_cloud_noalloc: device %d beyond the supported %d", dev,
-                  kNoAllocMaxDevices);
-        return GMAPP_ERR_INVALID_ARG;
-    }
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    NoAllocSymbols &s = g_noalloc_syms[dev];
-    if (!s.scratch) {
-        void *scratch = nullptr, *err = nullptr;
-        GMAPP_CHECK_CUDA(cudaGetSymbolAddress(&scratch, g_noalloc_scratch));
-        GMAPP_CHECK_CUDA(cudaGetSymbolAddress(&err, g_noalloc_err));
-        s.scratch = scratch;
-        s.err = static_cast<uint32_t *>(err);
-    }
-    *out = s;
+    void *scratch = nullptr, *err = nullptr;
+    GMAPP_CHECK_CUDA(cudaGetSymbolAddress(&scratch, g_noalloc_scratch));
+    GMAPP_CHECK_CUDA(cudaGetSymbolAddress(&err, g_noalloc_err));
+    out->scratch = scratch;
+    out->err = static_cast<uint32_t *>(err);
     return GMAPP_OK;
 }
 
@@ -299,6 +287,8 @@ extern "C" gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, co
     NoAllocSymbols sym;
     gmapp_status st = noalloc_symbols(&sym);
     if (st != GMAPP_OK) return st;
+    // the flag reports this call only (a device memset allocates nothing)
+    GMAPP_CHECK_CUDA(cudaMemsetAsync(sym.err, 0, sizeof(uint32_t), stream));
     int dev = 0, sms = 0;
     GMAPP_CHECK_CUDA(cudaGetDevice(&dev));
     GMAPP_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -364,5 +354,20 @@ extern "C" gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, co
             tkeys, tcounts, trep, n_occ, toffsets, ws->min_pts, A, o);
     }
     GMAPP_CHECK_CUDA(cudaGetLastError());
+    return GMAPP_OK;
+}
+
+extern "C" gmapp_status filter_cloud_noalloc_status(gmapp_stream stream) {
+    NoAllocSymbols sym;
+    gmapp_status st = noalloc_symbols(&sym);
+    if (st != GMAPP_OK) return st;
+    uint32_t word = 0;
+    GMAPP_CHECK_CUDA(cudaMemcpyAsync(&word, sym.err, sizeof(word), cudaMemcpyDeviceToHost, stream));
+    GMAPP_CHECK_CUDA(cudaStreamSynchronize(stream));
+    if (word & GMAPP_DEVERR_CAPACITY) {
+        set_error("filter_cloud_noalloc: more voxels qualified than out->cap (*out->n holds "
+                  "the number needed)");
+        return GMAPP_ERR_CAPACITY;
+    }
     return GMAPP_OK;
 }

@@ -625,9 +625,11 @@ extern "C" gmapp_status gmapp_server_create(gmapp_ctx *ctx, const gmapp_server_c
     const int64_t room =
         (static_cast<int64_t>(ctx->max_smem_optin) - static_cast<int64_t>(fa.sharedSizeBytes + recv_bytes)) / 12;
     // the culled kernel reads obstacles through the neighbour index (no shard)
-    // a multiple of 128: the pair loop tests whole blocks of 128 obstacles
-    // (block culling: + 6 floats of bounding box per 128 resident obstacles)
-    const int64_t room_b = cfg->culled == 2 ? room * 128 / (128 + 2) : room;
+    // a multiple of 128: the pair loop tests whole blocks of 128 obstacles.
+    // Room for block culling's boxes (6 floats per 128 resident obstacles) is
+    // kept in both chunk-kernel modes, so the all-pairs and the block-culled
+    // server hold the same obstacles in shared memory and agree bit for bit.
+    const int64_t room_b = room * 128 / (128 + 2);
     s->shard_cap = grid_cull ? 0
                              : static_cast<int>(std::min<int64_t>(
                                    (static_cast<int64_t>(cfg->obs_cap) + 127) & ~int64_t(127),

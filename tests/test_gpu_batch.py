@@ -193,3 +193,56 @@ def test_block_culled_batch_equals_unculled(gm, clear):
             assert np.array_equal(a["costs"].cpu().numpy().view(np.uint32),
                                   c["costs"].cpu().numpy().view(np.uint32)), q
             assert int(a["best"].item()) == int(c["best"].item())
+
+
+def test_rejected_tuning_leaves_batch_unchanged(gm):
+    """A tuning the batch rejects (more work items than the planner holds)
+    leaves the kernel, its shared-memory shard and the item list as they
+    were: the next run gives the same results bit for bit, within tolerance
+    of the oracle.  The obstacle capacity exceeds one CTA's shared memory, so
+    a shard size taken from the rejected tuning would not fit the kernel."""
+    g = np.random.Generator(np.random.PCG64(404))
+    ws_list = [synth.sphere_workload(seed=int(g.integers(1, 1 << 30)), n_raw=3000, voxel=0.01,
+                                     n_agents=1000, n_steps=12) for _ in range(17)]
+    b = gm.Batch(_specs(ws_list, cap=1 << 16), want_traj=False)
+    b.set_tuning(16, 256)
+    b.run()
+    gm.sync()
+    first = [r["out"]["p_final"].cpu().numpy().copy() for r in b.results]
+    with pytest.raises(gm.GmappError) as e:
+        b.set_tuning(2, 256)  # 17 x 500 items > the planner's 8192
+    assert e.value.status == 2
+    b.run()
+    gm.sync()
+    for q, (w, r) in enumerate(zip(ws_list, b.results)):
+        got = r["out"]["p_final"].cpu().numpy()
+        assert np.array_equal(got.view(np.uint32), first[q].view(np.uint32)), q
+        if q % 8 == 0:
+            ref_f = oracle.filter_cloud(w["xyz"], w["T"], w["workspace"])
+            idx = np.array([0, 499, 999])
+            obs = np.stack([ref_f["x"], ref_f["y"], ref_f["z"]])
+            ref = oracle.rollout(obs, ref_f["r_O"], subset_agents(w["agents"], idx), w["params"],
+                                 want_traj=False)
+            assert np.abs(got[:, idx] - ref["p_final"]).max() <= POS_TOL
+
+
+@pytest.mark.parametrize("clear", [False, True])
+def test_block_culled_batch_equals_unculled_beyond_shared_memory(gm, clear):
+    """Obstacle sets larger than one CTA's shared memory (the remainder comes
+    from L2): culled and unculled batches keep the same obstacles resident,
+    so their results are equal bit for bit here too."""
+    ws_list = [synth.sphere_workload(seed=4242, n_raw=120000, voxel=0.003, n_agents=9, n_steps=60),
+               synth.sphere_workload(seed=77, n_raw=150000, voxel=0.0025, n_agents=21, n_steps=40)]
+    outs = []
+    for cull in (False, True):
+        b = gm.Batch(_specs(ws_list, cap=1 << 16), want_clear=clear)
+        b.set_culling(cull)
+        b.run()
+        gm.sync()
+        outs.append(b)
+    assert min(r["obs"].count() for r in outs[0].results) > 19000
+    for q in range(len(ws_list)):
+        a, c = outs[0].results[q], outs[1].results[q]
+        for k in ("traj", "p_final", "v_final", "path_len"):
+            assert np.array_equal(a["out"][k].cpu().numpy().view(np.uint32),
+                                  c["out"][k].cpu().numpy().view(np.uint32)), (q, k)
