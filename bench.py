@@ -284,6 +284,12 @@ def run_ours(args, ws, rank, local):
     for i in range(args.warmup):
         step(i % args.frames)
     torch.cuda.synchronize()
+    # FP32 FMA / SFU rates of this GPU (event-timed probe kernels), the
+    # denominators of the force kernel's roofline
+    peaks_probe = gm.measure_peaks(reps=5)
+    for i in range(args.warmup):
+        step(i % args.frames)
+    torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -398,7 +404,9 @@ def run_ours(args, ws, rank, local):
         props = torch.cuda.get_device_properties(local)
         peaks = _measured_peaks()
         sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2032.0
-        peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        peak_nominal = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        # the faster of the packed and the scalar FMA probe
+        peak_tflops = max(peaks_probe["fp32_tflops"], peaks_probe["fp32_tflops_scalar"])
         mean_roll = statistics.mean(roll_ms) / 1e3
         per_launch_inter = na * statistics.mean(
             [n_obs[(args.warmup + i) % args.frames] for i in range(args.steps)]) * nk
@@ -423,8 +431,16 @@ def run_ours(args, ws, rank, local):
                          "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                          "traffic": _traffic_from_profile(),
                          "flops_per_interaction": FLOPS_PER_INTERACTION,
-                         "peak_source": f"{props.multi_processor_count} SMs x "
-                                        f"{FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                         "peak_source": "measured: gmapp_measure_peaks, the faster of "
+                                        "fma.rn.f32x2 (12 chains) and fma.rn.f32 (16 chains), "
+                                        "4 CTAs x 256 threads per SM, "
+                                        f"at {peaks_probe['sm_mhz']:.0f} MHz",
+                         "peak_nominal": peak_nominal,
+                         "peak_nominal_source": f"{props.multi_processor_count} SMs x "
+                                                f"{FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                                f"{sm_max:.0f} MHz",
+                         "frac_of_nominal": achieved / peak_nominal,
+                         "peaks_measured": peaks_probe,
                          "rollout_ms_mean": 1e3 * mean_roll,
                          "rollout_ms_median": float(np.median(roll_ms)),
                          "executed": {
@@ -447,10 +463,14 @@ def run_ours(args, ws, rank, local):
             "cpu_baseline": cpu,
         }
         result["config"]["obs_cap"] = obs_cap
+        del frames, pinned, wsp, obs, ro, sel
+        torch.cuda.empty_cache()
         if not args.no_patterns:
-            del frames, pinned, wsp, obs, ro, sel
-            torch.cuda.empty_cache()
             result["patterns"] = {name: fn(gm, args) for name, fn in PATTERNS.items()}
+            fs = result["patterns"]["filter_stream"]
+        else:
+            fs = bench_filter_stream(gm, args, with_fused=False)
+        result["roofline_filter"] = _filter_roofline(fs)
         print(json.dumps(result), flush=True)
     if ws > 1:
         dist.barrier()
@@ -473,7 +493,31 @@ def _events(torch, stream, fn, reps):
     return e0.elapsed_time(e1) / 1e3 / reps
 
 
-def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8):
+FILTER_PROFILE = os.path.join(ROOT, "profiles", "filter_stream_tabletop.md")
+
+
+def _filter_roofline(fs: dict) -> dict:
+    """Roofline line of the perception filter (A1-A3) from the filter-stream
+    measurement: algorithmic bytes per frame / device time per frame against
+    the measured HBM copy rate; DRAM traffic per frame from the committed
+    ncu summary (line 'traffic_bytes_per_frame: N'), if present."""
+    best = fs["stream"]
+    traffic = None
+    if os.path.exists(FILTER_PROFILE):
+        with open(FILTER_PROFILE) as f:
+            for line in f:
+                if line.strip().startswith("traffic_bytes_per_frame:"):
+                    v = line.split(":", 1)[1].strip()
+                    traffic = None if v in ("", "null") else float(v)
+    return {"bound": "hbm", "kernel": best.get("kernel", "filter_stream"),
+            "achieved": best["GB_per_s"], "peak": fs["peak_GB_per_s"], "unit": "GB/s",
+            "frac": best["hbm_frac"], "traffic": traffic,
+            "algorithmic_bytes_per_frame": fs["algorithmic_bytes"] / fs["n_frames"],
+            "us_per_frame": best["us_per_frame"], "workload": fs["workload"],
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+
+def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8, with_fused=True):
     """The perception filter alone (A1-A3) over a stream of 256 tabletop
     frames (307,200 points each, 944 MB read in total; 64 distinct frames,
     236 MB, cycled so that no frame is still in L2 when it comes back):
@@ -578,7 +622,10 @@ def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8):
     gm.sync()
     del batches, frames
     torch.cuda.empty_cache()
-    res["fused_2_sensors"] = bench_fused(gm)
+    res["n_frames"] = n_filters
+    res["stream"] = dict(res["batched_32"], kernel="kf_keys/kf_sums/kf_emit/kf_count")
+    if with_fused:
+        res["fused_2_sensors"] = bench_fused(gm)
     return res
 
 

@@ -5,7 +5,7 @@
  * fraction of peak needs the rate those pipes actually sustain on this
  * part.  gmapp_measure_peaks times short event-bracketed probe kernels:
  *
- *   - packed FMA:   fma.rn.f32x2 on 8 independent accumulators per thread
+ *   - packed FMA:   fma.rn.f32x2 on 12 independent accumulators per thread
  *                   (the instruction the pair loop uses);
  *   - scalar FMA:   fma.rn.f32 on 16 independent accumulators per thread;
  *   - SFU:          rsqrt.approx.ftz.f32 on 8 independent chains per thread;

@@ -336,29 +336,37 @@ def grad_vector(adj: dict, i: int) -> np.ndarray:
 def fd_gradient(obs_xyz, r_O, agents: dict, prm, agent_ids, h: float = 1e-6) -> dict:
     """Central finite differences (step h) of each listed agent's cost with
     respect to v0 (3), k_r, k_a and c (3), perturbing one agent parameter at
-    a time on a one-agent rollout (agents are independent).  Returns per
-    agent (gradient[8], valid[8]); an entry is valid only when both
-    perturbed runs have the unperturbed run's branch signature (no clamp,
-    gate or nearest-obstacle change inside +-h: no kink crossed)."""
-    out = {}
-    for i in agent_ids:
+    a time (agents are independent, so every perturbed copy is one more
+    agent of a single oracle run).  Returns per agent (gradient[8],
+    valid[8]); an entry is valid only when both perturbed runs have the
+    unperturbed run's branch signature (no clamp, gate or nearest-obstacle
+    change inside +-h: no kink crossed)."""
+    ids = [int(i) for i in agent_ids]
+    copies = []  # per listed agent: base, then (+h, -h) for each of the 8 parameters
+    for i in ids:
         one = {k: (_f64(v)[:, i:i + 1] if _f64(v).ndim == 2 else _f64(v)[i:i + 1])
                for k, v in agents.items()}
-        base_sig = adjoint(obs_xyz, r_O, one, prm)["sig"][0]
-        g = np.zeros(8)
-        ok = np.zeros(8, bool)
-        for q, (name, ax) in enumerate(GRAD_NAMES):
-            vals, sigs = [], []
+        copies.append(one)
+        for name, ax in GRAD_NAMES:
             for sgn in (+1, -1):
                 a = {k: v.copy() for k, v in one.items()}
                 if ax is None:
                     a[name][0] += sgn * h
                 else:
                     a[name][ax, 0] += sgn * h
-                r = adjoint(obs_xyz, r_O, a, prm)
-                vals.append(r["cost"][0])
-                sigs.append(r["sig"][0])
-            g[q] = (vals[0] - vals[1]) / (2 * h)
-            ok[q] = sigs[0] == base_sig and sigs[1] == base_sig
-        out[int(i)] = (g, ok)
+                copies.append(a)
+    allc = {k: np.ascontiguousarray(np.concatenate([c[k] for c in copies], axis=-1))
+            for k in copies[0]}
+    r = adjoint(obs_xyz, r_O, allc, prm)
+    per = 1 + 2 * len(GRAD_NAMES)
+    out = {}
+    for n, i in enumerate(ids):
+        b = n * per
+        g = np.zeros(8)
+        ok = np.zeros(8, bool)
+        for q in range(len(GRAD_NAMES)):
+            up, dn = b + 1 + 2 * q, b + 2 + 2 * q
+            g[q] = (r["cost"][up] - r["cost"][dn]) / (2 * h)
+            ok[q] = r["sig"][up] == r["sig"][b] and r["sig"][dn] == r["sig"][b]
+        out[i] = (g, ok)
     return out

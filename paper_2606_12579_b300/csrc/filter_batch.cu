@@ -1,18 +1,31 @@
 // filter_cloud_batch: the perception filter of Sec. IV-B / Sec. V-A for many
-// clouds at once.  A single frame is a few MB -- far less than one launch
-// needs to approach HBM bandwidth -- so a stream of frames (or several
-// sensors) goes through ONE sequence of four launches: every launch covers
-// the blocks of all jobs, a block -> job table maps each block to its cloud,
-// and the building blocks are those of filter_cloud (filter_device.cuh), so
-// each job's S_W is bit-identical to filter_cloud on the same cloud.
+// clouds at once (a stream of depth frames, or several sensors).
 //
-//   kf_keys   points -> keys + bitmap bits
+// A single frame is a few MB, far less than a launch needs to approach HBM
+// bandwidth, and a whole stream's scratch (key per point, bitmap over the
+// grid) is far larger than L2.  So the jobs are filtered in WAVES whose
+// scratch fits comfortably in L2 (about 20 MB: a few frames), each wave
+// through four launches, and consecutive waves alternate between the
+// caller's stream and a second stream of the batch, so the latency-bound
+// passes of one wave overlap the bandwidth-bound key pass of the next.  The
+// two streams each own one set of scratch slots, reused wave after wave: the
+// per-point keys and bitmap words a wave writes are read back from L2 and
+// overwritten there by the wave after next, so only the raw points and the
+// obstacle sets move through DRAM.
+//
+//   kf_keys   8 points per thread and iteration (six 16-byte streaming
+//             loads in flight): key per point + bitmap bits
 //   kf_sums   per-block (and per-chunk) popcounts; each job's last block
 //             scans its block sums
-//   kf_emit   ranks, keys, centres; publishes each job's N_O; clears the
-//             bitmap behind it (the scratch is zeroed once at creation, so
-//             no clearing launch is needed)
-//   kf_count  per-voxel point counts and smallest indices
+//   kf_emit   per 32-word chunk: ranks of its words (warp scan), the chunk's
+//             set bits compacted in shared memory, then written 32 obstacles
+//             at a time (coalesced: key, count 0, index ~0, centre); publishes
+//             each job's N_O and clears the bitmap words behind it
+//   kf_count  8 keys per thread and iteration: per-voxel point counts and
+//             smallest point index
+//
+// Every job's S_W is bit-identical to filter_cloud on the same cloud (same
+// key and centre arithmetic, same ranks).
 #include <math.h>
 
 #include <algorithm>
@@ -24,12 +37,38 @@
 namespace gmapp {
 namespace {
 
-constexpr int kMaxPointBlocksPerJob = 64;  // a few 4-point groups per thread
+constexpr int kPointsPerThread = 8;      // kf_keys / kf_count: points per thread per iteration
+constexpr int kPointItersPerThread = 2;  // iterations per thread in a job's block range
+constexpr size_t kWaveL2Bytes = size_t(20) << 20;  // L2-resident scratch per wave
+
+// Division by an invariant divisor d by multiplication (T. Granlund and P. L.
+// Montgomery, "Division by invariant integers using multiplication", PLDI
+// 1994, Sec. 4, unsigned case): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n) and
+// q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0) equals floor(n / d) for
+// every 32-bit n.
+struct DivMagic {
+    uint32_t m, s1, s2;
+};
+
+DivMagic div_magic(uint32_t d) {
+    int l = 0;
+    while ((uint64_t(1) << l) < d) ++l;
+    const uint64_t m = ((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1;
+    return DivMagic{static_cast<uint32_t>(m), static_cast<uint32_t>(std::min(l, 1)),
+                    static_cast<uint32_t>(std::max(l - 1, 0))};
+}
+
+__device__ __forceinline__ uint32_t div_by(uint32_t n, DivMagic g) {
+    const uint32_t t = __umulhi(g.m, n);
+    return (t + ((n - t) >> g.s1)) >> g.s2;
+}
 
 struct FilterJob {
     const float *xyz;
     int64_t n_raw;
     FilterArgs fa;
+    DivMagic dx, dy;  // division by dims_x, dims_y (key -> cell coordinates)
     uint32_t *bitmap, *chunk, *sums, *offsets, *counters, *keys;
     uint2 *pw;
     int32_t pt_blk0, pt_nblk, bm_blk0, bm_nblk, sb_blk0, sb_nblk;
@@ -37,36 +76,191 @@ struct FilterJob {
     int32_t *n_out;
 };
 
-__global__ void __launch_bounds__(kThreads) kf_keys(const FilterJob *J, const int32_t *pt_map) {
-    const FilterJob &Q = J[pt_map[blockIdx.x]];
-    const FilterArgs fa = Q.fa;
-    keys_range(Q.xyz, Q.n_raw, fa, Q.keys, Q.bitmap, blockIdx.x - Q.pt_blk0, Q.pt_nblk);
+// One point -> its linear voxel key, or kInvalid: the binary32 sequence of
+// voxel_key without the explicit finiteness test.  A non-finite coordinate
+// makes every transformed coordinate NaN or infinite (0 x inf is NaN, any
+// other product is infinite or NaN), and a NaN or infinite quotient fails
+// the range test 0 <= q < dims, so the same points are dropped.
+__device__ __forceinline__ uint32_t key_of(float x, float y, float z, const FilterArgs &A,
+                                           float inv_voxel) {
+    uint32_t idx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float t0 = __fmul_rn(A.T[4 * a + 0], x);
+        const float t1 = __fmul_rn(A.T[4 * a + 1], y);
+        const float t2 = __fmul_rn(A.T[4 * a + 2], z);
+        const float w = __fadd_rn(__fadd_rn(__fadd_rn(t0, t1), t2), A.T[4 * a + 3]);
+        const float q = voxel_quotient(__fsub_rn(w, A.lo[a]), A.voxel, inv_voxel);
+        if (!(q >= 0.0f && q < A.dimf[a])) return kInvalid;
+        idx[a] = static_cast<uint32_t>(q);
+    }
+    return (idx[2] * A.ny + idx[1]) * A.nx + idx[0];
 }
 
-__global__ void __launch_bounds__(kBmThreads) kf_sums(const FilterJob *J, const int32_t *sb_map) {
-    const FilterJob &Q = J[sb_map[blockIdx.x]];
-    bitmap_sums_block(Q.bitmap, Q.chunk, Q.sums, Q.offsets, Q.counters, Q.counters + 1,
-                      blockIdx.x - Q.sb_blk0, Q.sb_nblk);
+__global__ void __launch_bounds__(kThreads) kf_keys(const FilterJob *J, const int32_t *pt_map,
+                                                    int32_t blk0) {
+    const int32_t gb = blockIdx.x + blk0;
+    const FilterJob &Q = J[pt_map[gb]];
+    const FilterArgs A = Q.fa;
+    const int64_t n = Q.n_raw, n8 = n / kPointsPerThread;
+    const int64_t blk = gb - Q.pt_blk0, stride = static_cast<int64_t>(Q.pt_nblk) * kThreads;
+    const float inv = __frcp_rn(A.voxel);
+    uint32_t *__restrict__ keys = Q.keys;
+    uint32_t *__restrict__ bitmap = Q.bitmap;
+    const int64_t cells = static_cast<int64_t>(A.nx) * A.ny * A.nz;
+    auto chk = [&](uint32_t k) { return k == kInvalid || bc_ok(k, cells, A.err) ? k : kInvalid; };
+    for (int64_t g = blk * kThreads + threadIdx.x; g < n8; g += stride) {
+        const float4 *src = reinterpret_cast<const float4 *>(Q.xyz) + 6 * g;
+        const float4 a0 = __ldcs(src), a1 = __ldcs(src + 1), a2 = __ldcs(src + 2);
+        const float4 a3 = __ldcs(src + 3), a4 = __ldcs(src + 4), a5 = __ldcs(src + 5);
+        uint4 k, l;
+        k.x = chk(key_of(a0.x, a0.y, a0.z, A, inv));
+        k.y = chk(key_of(a0.w, a1.x, a1.y, A, inv));
+        k.z = chk(key_of(a1.z, a1.w, a2.x, A, inv));
+        k.w = chk(key_of(a2.y, a2.z, a2.w, A, inv));
+        l.x = chk(key_of(a3.x, a3.y, a3.z, A, inv));
+        l.y = chk(key_of(a3.w, a4.x, a4.y, A, inv));
+        l.z = chk(key_of(a4.z, a4.w, a5.x, A, inv));
+        l.w = chk(key_of(a5.y, a5.z, a5.w, A, inv));
+        uint4 *dst = reinterpret_cast<uint4 *>(keys + kPointsPerThread * g);
+        dst[0] = k;
+        dst[1] = l;
+        BitMerge m;
+        m.add(k.x, bitmap);
+        m.add(k.y, bitmap);
+        m.add(k.z, bitmap);
+        m.add(k.w, bitmap);
+        m.add(l.x, bitmap);
+        m.add(l.y, bitmap);
+        m.add(l.z, bitmap);
+        m.add(l.w, bitmap);
+        m.flush(bitmap);
+    }
+    // ragged tail (n % 8 points): the first threads of the job's first block
+    const int64_t t = kPointsPerThread * n8 + blk * kThreads + threadIdx.x;
+    if (t < n) {
+        const uint32_t k = chk(key_of(Q.xyz[3 * t], Q.xyz[3 * t + 1], Q.xyz[3 * t + 2], A, inv));
+        keys[t] = k;
+        if (k != kInvalid) atomicOr(&bitmap[k >> 5], 1u << (k & 31));
+    }
 }
+
+__global__ void __launch_bounds__(kBmThreads) kf_sums(const FilterJob *J, const int32_t *sb_map,
+                                                      int32_t blk0) {
+    const int32_t gb = blockIdx.x + blk0;
+    const FilterJob &Q = J[sb_map[gb]];
+    bitmap_sums_block(Q.bitmap, Q.chunk, Q.sums, Q.offsets, Q.counters, Q.counters + 1,
+                      gb - Q.sb_blk0, Q.sb_nblk);
+}
+
+// Per warp: kChunksPerWarp chunks of 32 words.  For an occupied chunk, each
+// lane ranks its word (warp scan of popcounts on top of the chunk's offset),
+// records (rank, bits) for kf_count, clears the word, and writes the keys of
+// its set bits to the warp's stage in shared memory at their ranks within
+// the chunk; the warp then writes the chunk's obstacles 32 consecutive ranks
+// at a time.
+constexpr int kEmitWarps = kBmThreads / 32;
 
 __global__ void __launch_bounds__(kBmThreads) kf_emit(const FilterJob *J, const int32_t *bm_map,
-                                                      uint32_t *err) {
-    const FilterJob &Q = J[bm_map[blockIdx.x]];
-    const int64_t blk = blockIdx.x - Q.bm_blk0;
+                                                      int32_t blk0, uint32_t *err) {
+    __shared__ uint32_t stage[kEmitWarps][kChunkWords * 32];
+    const int32_t gb = blockIdx.x + blk0;
+    const FilterJob &Q = J[bm_map[gb]];
+    const int64_t blk = gb - Q.bm_blk0;
     const EmitOut o = Q.o;
     if (blk == 0 && threadIdx.x == 0) {
         const uint32_t t = Q.counters[1];
         *Q.n_out = static_cast<int32_t>(t);
         if (t > o.cap) raise_error(err, GMAPP_DEVERR_CAPACITY);
     }
-    const FilterArgs fa = Q.fa;
-    emit_block<kChunksPerWarp>(Q.bitmap, Q.offsets, Q.chunk, Q.pw, fa, o, blk, true);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *st = stage[warp];
+    const FilterArgs A = Q.fa;
+    const DivMagic dx = Q.dx, dy = Q.dy;
+    const int64_t c0 = (blk * kEmitWarps + warp) * kChunksPerWarp;
+    uint32_t w[kChunksPerWarp];
+#pragma unroll
+    for (int j = 0; j < kChunksPerWarp; ++j) w[j] = Q.bitmap[(c0 + j) * kChunkWords + lane];
+#pragma unroll 1
+    for (int j = 0; j < kChunksPerWarp; ++j) {
+        if (!__ballot_sync(0xffffffffu, w[j] != 0u)) continue;
+        const int64_t c = c0 + j;
+        const uint32_t cnt = __popc(w[j]);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t excl = incl - cnt;
+        const uint32_t base = Q.offsets[c / kChunksPerSumBlock] + Q.chunk[c];
+        const uint32_t wv = static_cast<uint32_t>(c * kChunkWords + lane);
+        if (w[j]) {
+            Q.pw[wv] = make_uint2(base + excl, w[j]);
+            Q.bitmap[wv] = 0u;
+        }
+        uint32_t bits = w[j], pos = excl;
+        const uint32_t k0 = wv * 32u;
+        while (bits) {
+            const uint32_t b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            st[pos++] = k0 + b;
+        }
+        __syncwarp();
+        for (uint32_t r = lane; r < total; r += 32) {
+            const uint32_t key = st[r];
+            const uint32_t rank = base + r;
+            if (rank < o.cap) {
+                const uint32_t q1 = div_by(key, dx);
+                const uint32_t ix = key - q1 * A.nx;
+                const uint32_t iz = div_by(q1, dy);
+                const uint32_t iy = q1 - iz * A.ny;
+                float cx, cy, cz;
+                cell_centre(ix, iy, iz, A, cx, cy, cz);
+                o.keys[rank] = key;
+                o.counts[rank] = 0u;
+                o.rep[rank] = kInvalid;
+                o.x[rank] = cx;
+                o.y[rank] = cy;
+                o.z[rank] = cz;
+            }
+        }
+        __syncwarp();
+    }
 }
 
-__global__ void __launch_bounds__(kThreads) kf_count(const FilterJob *J, const int32_t *pt_map) {
-    const FilterJob &Q = J[pt_map[blockIdx.x]];
-    count_range(Q.keys, Q.n_raw, Q.pw, Q.o.counts, Q.o.rep, Q.o.cap,
-                blockIdx.x - Q.pt_blk0, Q.pt_nblk);
+__global__ void __launch_bounds__(kThreads) kf_count(const FilterJob *J, const int32_t *pt_map,
+                                                     int32_t blk0) {
+    const int32_t gb = blockIdx.x + blk0;
+    const FilterJob &Q = J[pt_map[gb]];
+    const int64_t n = Q.n_raw, n8 = n / kPointsPerThread;
+    const int64_t blk = gb - Q.pt_blk0, stride = static_cast<int64_t>(Q.pt_nblk) * kThreads;
+    const uint2 *__restrict__ pw = Q.pw;
+    uint32_t *counts = Q.o.counts, *rep = Q.o.rep;
+    const int64_t cap = Q.o.cap;
+    for (int64_t g = blk * kThreads + threadIdx.x; g < n8; g += stride) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(Q.keys + kPointsPerThread * g);
+        const uint4 k = __ldcs(src), l = __ldcs(src + 1);
+        const uint32_t kk[8] = {k.x, k.y, k.z, k.w, l.x, l.y, l.z, l.w};
+        uint32_t r[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) r[i] = rank_of(kk[i], pw, cap);
+        RankMerge m;
+        const uint32_t i0 = static_cast<uint32_t>(kPointsPerThread * g);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (r[i] != kInvalid) m.add(r[i], i0 + i, counts, rep);
+        m.flush(counts, rep);
+    }
+    const int64_t t = kPointsPerThread * n8 + blk * kThreads + threadIdx.x;
+    if (t < n) {
+        const uint32_t r = rank_of(Q.keys[t], pw, cap);
+        if (r != kInvalid) {
+            atomicAdd(&counts[r], 1u);
+            atomicMin(&rep[r], static_cast<uint32_t>(t));
+        }
+    }
 }
 
 }  // namespace
@@ -79,7 +273,10 @@ struct gmapp_filter_batch {
     FilterJob *d_jobs = nullptr;
     int32_t *d_pt_map = nullptr, *d_bm_map = nullptr, *d_sb_map = nullptr;
     void *d_ws = nullptr;
-    int32_t pt_blocks = 0, bm_blocks = 0, sb_blocks = 0;
+    // per wave: first block and block count of each launch
+    std::vector<int32_t> pt0, ptn, bm0, bmn, sb0, sbn;
+    cudaStream_t side = nullptr;  // odd waves (the caller's stream runs the even ones)
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -90,6 +287,9 @@ void release(gmapp_filter_batch *fb) {
     cudaFree(fb->d_bm_map);
     cudaFree(fb->d_sb_map);
     cudaFree(fb->d_ws);
+    if (fb->fork) cudaEventDestroy(fb->fork);
+    if (fb->join) cudaEventDestroy(fb->join);
+    if (fb->side) cudaStreamDestroy(fb->side);
 }
 
 }  // namespace
@@ -101,10 +301,7 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
         return GMAPP_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    std::vector<FilterJob> hj(n_jobs);
-    std::vector<int32_t> pt_map, bm_map, sb_map;
-    std::vector<size_t> ws_off(n_jobs);
-    size_t ws_total = 0;
+    size_t slot_bytes = 256, touched = 1;
     for (int q = 0; q < n_jobs; ++q) {
         const gmapp_cloud_job &J = jobs[q];
         if (!valid_workspace(&J.ws) || J.ws.min_pts != 1 || J.n_raw < 0 ||
@@ -125,8 +322,23 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
                 return GMAPP_ERR_INVALID_ARG;
             }
         const Layout L = layout(J.n_raw, &J.ws);
-        ws_off[q] = ws_total;
-        ws_total = align_up(ws_total + L.total, 256);
+        slot_bytes = std::max(slot_bytes, align_up(L.total, 256));
+        // scratch a wave keeps in L2: keys, bitmap, the occupied words' ranks
+        touched = std::max(touched, static_cast<size_t>(J.n_raw) * 4 +
+                                        static_cast<size_t>(L.n_words) * 5);
+    }
+    const int W = static_cast<int>(std::max<size_t>(
+        1, std::min<size_t>(n_jobs, kWaveL2Bytes / touched)));
+    const int n_waves = (n_jobs + W - 1) / W;
+    const int n_slots = std::min(n_waves, 2) * W;
+
+    std::vector<FilterJob> hj(n_jobs);
+    std::vector<int32_t> pt_map, bm_map, sb_map;
+    gmapp_filter_batch *fb = new gmapp_filter_batch();
+    fb->ctx = ctx;
+    for (int q = 0; q < n_jobs; ++q) {
+        const gmapp_cloud_job &J = jobs[q];
+        const Layout L = layout(J.n_raw, &J.ws);
         FilterJob &D = hj[q];
         memset(&D, 0, sizeof(D));
         D.xyz = J.xyz;
@@ -141,9 +353,12 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
         D.fa.ny = J.ws.dims[1];
         D.fa.nz = J.ws.dims[2];
         D.fa.err = ctx->d_err;
+        D.dx = div_magic(D.fa.nx);
+        D.dy = div_magic(D.fa.ny);
+        const int64_t n8 = J.n_raw / kPointsPerThread;
         D.pt_blk0 = static_cast<int32_t>(pt_map.size());
         D.pt_nblk = static_cast<int32_t>(std::max<int64_t>(
-            1, std::min<int64_t>((J.n_raw / 4 + kThreads - 1) / kThreads, kMaxPointBlocksPerJob)));
+            1, (n8 + kThreads * kPointItersPerThread - 1) / (kThreads * kPointItersPerThread)));
         for (int i = 0; i < D.pt_nblk; ++i) pt_map.push_back(q);
         D.bm_blk0 = static_cast<int32_t>(bm_map.size());
         D.bm_nblk = static_cast<int32_t>(L.n_blocks);
@@ -151,31 +366,43 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
         D.sb_blk0 = static_cast<int32_t>(sb_map.size());
         D.sb_nblk = static_cast<int32_t>(L.n_sblocks);
         for (int i = 0; i < D.sb_nblk; ++i) sb_map.push_back(q);
-        D.o = EmitOut{o.keys, o.counts, o.rep_idx, o.x, o.y, o.z, o.cap};
-        D.n_out = o.n;
+        D.o = EmitOut{J.out.keys, J.out.counts, J.out.rep_idx, J.out.x, J.out.y, J.out.z,
+                      J.out.cap};
+        D.n_out = J.out.n;
         if (pt_map.size() > 0x7fffffffu || bm_map.size() > 0x7fffffffu) {
+            delete fb;
             set_error("gmapp_filter_batch_create: too many blocks");
             return GMAPP_ERR_CAPACITY;
         }
     }
-    gmapp_filter_batch *fb = new gmapp_filter_batch();
-    fb->ctx = ctx;
-    fb->pt_blocks = static_cast<int32_t>(pt_map.size());
-    fb->bm_blocks = static_cast<int32_t>(bm_map.size());
-    fb->sb_blocks = static_cast<int32_t>(sb_map.size());
-    cudaError_t e = cudaMalloc(&fb->d_ws, std::max<size_t>(ws_total, 256));
+    for (int w = 0; w < n_waves; ++w) {
+        const int q0 = w * W, q1 = std::min(n_jobs, q0 + W) - 1;
+        fb->pt0.push_back(hj[q0].pt_blk0);
+        fb->ptn.push_back(hj[q1].pt_blk0 + hj[q1].pt_nblk - hj[q0].pt_blk0);
+        fb->bm0.push_back(hj[q0].bm_blk0);
+        fb->bmn.push_back(hj[q1].bm_blk0 + hj[q1].bm_nblk - hj[q0].bm_blk0);
+        fb->sb0.push_back(hj[q0].sb_blk0);
+        fb->sbn.push_back(hj[q1].sb_blk0 + hj[q1].sb_nblk - hj[q0].sb_blk0);
+    }
+    const size_t ws_total = static_cast<size_t>(n_slots) * slot_bytes;
+    cudaError_t e = cudaMalloc(&fb->d_ws, ws_total);
     // zero scratch: bitmaps and counters start clear, and each run leaves
     // them clear again
-    if (e == cudaSuccess) e = cudaMemset(fb->d_ws, 0, std::max<size_t>(ws_total, 256));
+    if (e == cudaSuccess) e = cudaMemset(fb->d_ws, 0, ws_total);
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_jobs, sizeof(FilterJob) * n_jobs);
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_pt_map, sizeof(int32_t) * pt_map.size());
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_bm_map, sizeof(int32_t) * bm_map.size());
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_sb_map, sizeof(int32_t) * sb_map.size());
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fb->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fb->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fb->join, cudaEventDisableTiming);
     if (e == cudaSuccess) {
         char *ws = static_cast<char *>(fb->d_ws);
         for (int q = 0; q < n_jobs; ++q) {
+            // wave w = q / W uses slot set w % 2 (its stream's), slot q - w W
+            const int w = q / W, slot = (w % 2) * W + (q - w * W);
             const Layout L = layout(jobs[q].n_raw, &jobs[q].ws);
-            char *base = ws + ws_off[q];
+            char *base = ws + static_cast<size_t>(slot) * slot_bytes;
             FilterJob &D = hj[q];
             D.bitmap = reinterpret_cast<uint32_t *>(base + L.off_bitmap);
             D.pw = reinterpret_cast<uint2 *>(base + L.off_pw);
@@ -209,6 +436,7 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
 
 extern "C" void gmapp_filter_batch_destroy(gmapp_filter_batch *fb) {
     if (!fb) return;
+    if (fb->side) cudaStreamSynchronize(fb->side);
     release(fb);
     delete fb;
 }
@@ -218,10 +446,23 @@ extern "C" gmapp_status filter_cloud_batch(gmapp_filter_batch *fb, gmapp_stream 
         set_error("filter_cloud_batch: NULL batch");
         return GMAPP_ERR_INVALID_ARG;
     }
-    kf_keys<<<fb->pt_blocks, kThreads, 0, stream>>>(fb->d_jobs, fb->d_pt_map);
-    kf_sums<<<fb->sb_blocks, kBmThreads, 0, stream>>>(fb->d_jobs, fb->d_sb_map);
-    kf_emit<<<fb->bm_blocks, kBmThreads, 0, stream>>>(fb->d_jobs, fb->d_bm_map, fb->ctx->d_err);
-    kf_count<<<fb->pt_blocks, kThreads, 0, stream>>>(fb->d_jobs, fb->d_pt_map);
+    const int n_waves = static_cast<int>(fb->pt0.size());
+    if (n_waves > 1) {
+        GMAPP_CHECK_CUDA(cudaEventRecord(fb->fork, stream));
+        GMAPP_CHECK_CUDA(cudaStreamWaitEvent(fb->side, fb->fork, 0));
+    }
+    for (int w = 0; w < n_waves; ++w) {
+        cudaStream_t s = (w % 2 == 0) ? stream : fb->side;
+        kf_keys<<<fb->ptn[w], kThreads, 0, s>>>(fb->d_jobs, fb->d_pt_map, fb->pt0[w]);
+        kf_sums<<<fb->sbn[w], kBmThreads, 0, s>>>(fb->d_jobs, fb->d_sb_map, fb->sb0[w]);
+        kf_emit<<<fb->bmn[w], kBmThreads, 0, s>>>(fb->d_jobs, fb->d_bm_map, fb->bm0[w],
+                                                   fb->ctx->d_err);
+        kf_count<<<fb->ptn[w], kThreads, 0, s>>>(fb->d_jobs, fb->d_pt_map, fb->pt0[w]);
+    }
+    if (n_waves > 1) {
+        GMAPP_CHECK_CUDA(cudaEventRecord(fb->join, fb->side));
+        GMAPP_CHECK_CUDA(cudaStreamWaitEvent(stream, fb->join, 0));
+    }
     GMAPP_CHECK_CUDA(cudaGetLastError());
     return GMAPP_OK;
 }

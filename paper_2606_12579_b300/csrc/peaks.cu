@@ -80,19 +80,19 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_ffma2(int iters, uint32
     ClockMark m;
     m.start();
     const float s0 = 1.0f + 1e-3f * (threadIdx.x & 7);
-    u64 acc[8];
+    u64 acc[12];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] = pack2(s0 + i, s0 - i);
+    for (int i = 0; i < 12; ++i) acc[i] = pack2(s0 + i, s0 - i);
     const u64 a = pack2(0.9999999f, 0.99999994f), b = pack2(1e-7f, 2e-7f);
-#pragma unroll 4
+#pragma unroll 2
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) acc[i] = ffma2(acc[i], a, b);
+        for (int i = 0; i < 12; ++i) acc[i] = ffma2(acc[i], a, b);
     }
     m.stop(clk);
     float s = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) s += sum2(acc[i]);
+    for (int i = 0; i < 12; ++i) s += sum2(acc[i]);
     keep(s, sink);
 }
 
@@ -230,7 +230,7 @@ extern "C" int gmapp_measure_peaks(int32_t reps, gmapp_peaks *out) {
     if (st == GMAPP_OK) st = time_probe(k_probe_mix, grid, it_mix, reps, sink, clk, &tx, &mhzx);
     cudaFree(buf);
     if (st != GMAPP_OK) return st;
-    const double fma2_lanes = threads * it_fma * 16.0 / t2;        // lane-FMAs per second
+    const double fma2_lanes = threads * it_fma * 24.0 / t2;        // lane-FMAs per second
     const double fma1_lanes = threads * (it_fma / 2) * 16.0 / t1;
     const double mufu = threads * it_mufu * 8.0 / tm;             // results per second
     const double mix_fma = threads * it_mix * 16.0 / tx, mix_mufu = threads * it_mix * 2.0 / tx;
