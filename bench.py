@@ -466,7 +466,8 @@ def run_ours(args, ws, rank, local):
         del frames, pinned, wsp, obs, ro, sel
         torch.cuda.empty_cache()
         if not args.no_patterns:
-            result["patterns"] = {name: fn(gm, args) for name, fn in PATTERNS.items()}
+            result["patterns"] = {name: fn(gm, args) for name, fn in PATTERNS.items()
+                                  if name != "filter_batched"}
             fs = result["patterns"]["filter_stream"]
         else:
             fs = bench_filter_stream(gm, args, with_fused=False)
@@ -517,7 +518,8 @@ def _filter_roofline(fs: dict) -> dict:
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
 
-def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8, with_fused=True):
+def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8, with_fused=True,
+                        batched_only=False):
     """The perception filter alone (A1-A3) over a stream of 256 tabletop
     frames (307,200 points each, 944 MB read in total; 64 distinct frames,
     236 MB, cycled so that no frame is still in L2 when it comes back):
@@ -594,9 +596,9 @@ def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8, wit
         return {"ms": 1e3 * t, "us_per_frame": 1e6 * t / n_filters, "GB_per_s": gbs,
                 "hbm_frac": gbs / peak if peak else None}
 
-    # filter_cloud_batch: 32 frames per batch (four launches for all of
-    # them), two batches over the 64 distinct frames, run alternately
-    per = 32
+    # filter_cloud_batch: all 64 distinct frames in one batch (filtered in
+    # L2-sized waves of a few frames on two streams), run four times
+    per = n_distinct
     batches = [gm.FilterBatch([frames[i] for i in range(b, b + per)], w0["T"], w0["workspace"],
                               caps=[131072] * per) for b in range(0, n_distinct, per)]
     cur = torch.cuda.current_stream()
@@ -615,15 +617,41 @@ def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8, wit
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
         best = t if best is None else min(best, t)
-    res["batched_32"] = entry(best)
-    res["batched_32"]["launches"] = 4 * (n_filters // per)
+    res["batched"] = entry(best)
+    res["batched"]["frames_per_batch"] = per
+    # the same runs captured once in a CUDA graph (the batch's two streams
+    # join the capture), so launch latency is off the critical path
+    side = torch.cuda.Stream()
+    side.wait_stream(cur)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        for r in range(n_filters // per):
+            batches[r % len(batches)].run(stream=side)
+    torch.cuda.synchronize()
+    bestg = None
+    for _ in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        graph.replay()
+        e1.record(cur)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        bestg = t if bestg is None else min(bestg, t)
+    for fb, b in zip(batches, range(0, n_distinct, per)):   # results unchanged by the replays
+        assert [o.count() for o in fb.outs] == n_obs[b:b + per]
+    res["batched_graph"] = entry(bestg)
+    res["batched_graph"]["frames_per_batch"] = per
+    res["n_frames"] = n_filters
+    pick = "batched_graph" if bestg < best else "batched"
+    res["stream"] = dict(res[pick], kernel="kf_keys/kf_sums/kf_emit/kf_count", mode=pick)
+    del graph
+    if batched_only:
+        return res
     for ns in (n_streams, 1):
         res[f"per_frame_streams_{ns}"] = entry(run(ns))
     gm.sync()
     del batches, frames
     torch.cuda.empty_cache()
-    res["n_frames"] = n_filters
-    res["stream"] = dict(res["batched_32"], kernel="kf_keys/kf_sums/kf_emit/kf_count")
     if with_fused:
         res["fused_2_sensors"] = bench_fused(gm)
     return res
@@ -1041,48 +1069,69 @@ def bench_culled(gm, args, n_frames=16, ticks=32):
 
 
 def bench_served(gm, args):
-    """1 kHz open-loop request stream (200k-point tabletop frames with 4 moving
-    spheres, 1 cm voxels, N_a in {64, 256, 1024}, N_k = 300) through the
-    continuously batched server vs the same stream served one request at a
-    time through the plain per-query calls, both with all pairs and with
-    spatial culling (each agent visits the obstacles within its reach).
-    Frames come from a pool
-    rendered at evenly spaced times of the stream (each frame serves the
-    requests of its 1/pool-th of the stream)."""
+    """1 kHz open-loop request stream over ``--serve-seconds`` (default 10 s:
+    10,000 requests), each with its own 200k-point frame of the tabletop
+    scene with 4 moving spheres at its arrival time (1 cm voxels, N_a in
+    {64, 256, 1024}, N_k = 300), through the continuously batched server
+    (first-fit admission with an aging bound) vs the same stream served one
+    request at a time through the plain per-query calls.  The frames are
+    rendered on the GPU before the stream starts (synth.stream_frames) and
+    held in pinned host memory, as a sensor would deliver them; every request
+    copies its frame host -> device.  The culled comparisons run the first
+    ``--serve-cull-seconds`` of the same stream at several offered rates."""
     import torch
     import synth
+    from synth.stream_frames import StreamFrames
     dur = float(args.serve_seconds)
     n_req = int(round(dur * 1000))
-    pool = max(4, int(round(dur * 5)))
     arrivals_1k, na_choice, _ = synth.serve_stream(n_requests=n_req)
-    frames, Ts = [], []
-    for i in range(pool):
-        w = synth.tabletop_workload(seed=1005 + i, n_agents=1, n_steps=1, n_points=200000,
-                                    voxel=0.01, spheres_at=float(arrivals_1k[i * n_req // pool]),
-                                    sphere_seed=1005, scene_seed=1005)
-        frames.append(torch.from_numpy(w["xyz"]).pin_memory())
-        Ts.append(w["T"])
-        ws_grid, prm = w["workspace"], w["params"]
+    renderer = StreamFrames(seed=1005, n_points=200000, device="cuda")
+    frame_bytes = 200000 * 12
+    avail = 64 << 30
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    # every request its own frame, as long as host memory holds them (a
+    # quarter of the available memory at most); else frames are reused
+    # cyclically and the output says how many were distinct
+    n_frames = int(max(64, min(n_req, (avail // 4) // frame_bytes)))
+    n_frames = (n_frames // 64) * 64 if n_frames < n_req else n_req
+    frames = torch.empty(n_frames, 200000, 3, dtype=torch.float32, pin_memory=True)
+    for c0 in range(0, n_frames, 512):
+        c1 = min(n_frames, c0 + 512)
+        frames[c0:c1].copy_(renderer.render(arrivals_1k[c0:c1], first=c0))
+    torch.cuda.synchronize()
+    T_cam = renderer.T
+    Ts = [T_cam]
+    base = synth.tabletop_workload(seed=1005, n_agents=1, n_steps=1, n_points=2000, voxel=0.01)
+    ws_grid, prm = base["workspace"], base["params"]
     import dataclasses
     prm = dataclasses.replace(prm, n_steps=300)
     agents = {}
     for na in (64, 256, 1024):
         a = synth.agent_set(na, 77 + na, synth.workloads.TABLE_START, synth.workloads.TABLE_GOAL)
         agents[na] = {k: torch.from_numpy(v).pin_memory() for k, v in a.items()}
-    frame_of = [min(pool - 1, r * pool // n_req) for r in range(n_req)]
+    frame_of = [r % n_frames for r in range(n_req)]
+    Ts = [T_cam] * n_frames
 
     def lat_stats(lat, t_span, inter):
         lat = np.asarray(lat) * 1e3
         return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "plans_per_s": len(lat) / t_span, "interactions_per_s": inter / t_span}
 
-    def run_served(culled, rate=1000.0, chunk=50):
-        """The stream, offered at ``rate`` requests/s, through the continuously
-        batched server (``chunk`` steps of every active plan per tick)."""
+    def run_served(culled, rate=1000.0, chunk=50, n=n_req):
+        """The first ``n`` requests of the stream, offered at ``rate``
+        requests/s, through the continuously batched server (``chunk`` steps
+        of every active plan per tick; first-fit admission, a queued request
+        overtaken at most 64 times)."""
         arrivals = arrivals_1k * (1000.0 / rate)
         srv = gm.Server(max_slots=48, max_agents=1024, max_steps=300, obs_cap=32768,
                         arena_bytes=2 << 30, chunk_steps=chunk, agents_per_item=8, threads=256,
-                        culled=culled)
+                        culled=culled, admit_bypass=64)
         for r in range(4):   # warm up (kernel loading, first admissions)
             t = srv.submit(frames[0], Ts[0], ws_grid, agents[int(na_choice[r])], prm)
             while srv.poll(t) is None:
@@ -1092,9 +1141,9 @@ def bench_served(gm, args):
         outstanding = {}
         t0 = time.perf_counter()
         nxt = 0
-        while done < n_req:
+        while done < n:
             now = time.perf_counter() - t0
-            while nxt < n_req and arrivals[nxt] <= now:
+            while nxt < n and arrivals[nxt] <= now:
                 na = int(na_choice[nxt])
                 tk = srv.submit(frames[frame_of[nxt]], Ts[frame_of[nxt]], ws_grid, agents[na], prm)
                 outstanding[tk] = (nxt, na)
@@ -1138,9 +1187,9 @@ def bench_served(gm, args):
             gm.rollout_agents(obs, dev_agents[na], prm, out=outs[na])
         return gm.score_and_select(outs[na], prm)
 
-    def run_plain(culled, rate=1000.0):
-        """The stream, offered at ``rate`` requests/s, one request at a time
-        through the per-query calls."""
+    def run_plain(culled, rate=1000.0, n=n_req):
+        """The first ``n`` requests of the stream, offered at ``rate``
+        requests/s, one request at a time through the per-query calls."""
         arrivals = arrivals_1k * (1000.0 / rate)
         for na in agents:  # warm up
             gm.filter_cloud(dev_frame.copy_(frames[0]), Ts[0], ws_grid, out=obs, workspace=wsb)
@@ -1148,7 +1197,7 @@ def bench_served(gm, args):
         gm.sync()
         lat, inter = [], 0
         t0 = time.perf_counter()
-        for r in range(n_req):
+        for r in range(n):
             while time.perf_counter() - t0 < arrivals[r]:
                 pass
             na = int(na_choice[r])
@@ -1166,20 +1215,25 @@ def bench_served(gm, args):
 
     served, plain = run_served(False), run_plain(False)
     culled = {}
+    n_cull = min(n_req, int(round(float(args.serve_cull_seconds) * 1000)))
     for rate in (float(r) for r in str(args.serve_cull_rates).split(",")):
-        s, p = run_served(True, rate, int(args.serve_cull_chunk)), run_plain(True, rate)
-        sb = run_served("blocks", rate, int(args.serve_cull_chunk))
+        s = run_served(True, rate, int(args.serve_cull_chunk), n=n_cull)
+        p = run_plain(True, rate, n=n_cull)
+        sb = run_served("blocks", rate, int(args.serve_cull_chunk), n=n_cull)
         culled[f"{rate:g}_per_s"] = {"served": s, "plain": p, "p99_speedup": p["p99_ms"] / s["p99_ms"],
                                      "served_block_culled": sb}
-    return {"workload": f"{n_req} requests at 1 kHz: 200k-point tabletop frames + 4 moving spheres, "
-                        "1 cm voxels, N_a in {64, 256, 1024}, N_k = 300",
+    return {"workload": f"{n_req} requests at 1 kHz over {dur:g} s: each its own 200k-point "
+                        "tabletop frame with 4 moving spheres at its arrival time, 1 cm voxels, "
+                        "N_a in {64, 256, 1024}, N_k = 300",
             "offered_per_s": 1000.0, "served": served, "plain": plain,
             "p99_speedup": plain["p99_ms"] / served["p99_ms"],
+            "plans_per_s_speedup": served["plans_per_s"] / plain["plans_per_s"],
+            "admission": "first fit over the queue, a request overtaken at most 64 times",
             "culled": {"note": "every agent visits only the obstacles within its reach "
-                               "(interactions/s still counts all pairs); the same frames "
-                               "and N_a offered at each rate",
+                               "(interactions/s still counts all pairs); the first "
+                               f"{n_cull} requests of the same stream at each rate",
                        "chunk_steps": int(args.serve_cull_chunk), **culled},
-            "frames_in_pool": pool}
+            "frames_distinct": n_frames, "frames_host_bytes": int(frames.numel() * 4)}
 
 
 def cpu_baseline(base, frames, n_agents_sample, min_seconds=10.0, max_steps=8):
@@ -1233,8 +1287,10 @@ def main():
                     help="offered request rates (Hz) of the culled serving comparison")
     ap.add_argument("--serve-cull-chunk", type=int, default=300,
                     help="steps per tick of the culled server")
-    ap.add_argument("--serve-seconds", type=float, default=3.0,
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the 1 kHz request stream of the served loop")
+    ap.add_argument("--serve-cull-seconds", type=float, default=3.0,
+                    help="length of the stream prefix of the culled serving comparison")
     ap.add_argument("--tuning", default="",
                     help="rollout launch shape 'cluster,agents,threads[,exchange]' "
                          "(default: autotuned)")
@@ -1257,6 +1313,7 @@ def main():
 
 
 PATTERNS = {"filter_stream": lambda gm, a: bench_filter_stream(gm, a),
+            "filter_batched": lambda gm, a: bench_filter_stream(gm, a, batched_only=True),
             "batched": lambda gm, a: bench_batched(gm, a),
             "adjoint": lambda gm, a: bench_adjoint(gm, a),
             "ensemble": lambda gm, a: bench_ensemble(gm, a),

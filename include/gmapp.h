@@ -607,11 +607,18 @@ typedef struct {
     gmapp_cost_weights w;
     gmapp_obstacles obs;      /* S_W buffers of this query (cap >= 4, multiple of 4) */
     gmapp_rollout_out out;    /* p_final, v_final, path_len required; traj,
-                                 clear_pen, min_clear optional; traces and
-                                 checkpoints are not produced in a batch */
+                                 clear_pen, min_clear, cost_terms optional; traces
+                                 and checkpoints are not produced in a batch.  With
+                                 cost_terms set, the query is scored by the paper's
+                                 four-term cost (as score_and_select4, with w4, alpha
+                                 and c_best below; prm.cost_radius > 0) instead of w */
     float *costs;             /* device [N_a] */
     int32_t *best;            /* device [1] */
     float *best_traj;         /* device [(n_steps+1)*3] or NULL */
+    gmapp_cost4 w4;           /* four-term weights (with out.cost_terms) */
+    float alpha;              /* hysteresis of the four-term selection */
+    float *c_best;            /* device float32 C_best of the query's plan (in/out; NaN = none),
+                                 or NULL (plain argmin) */
 } gmapp_query;
 
 typedef struct gmapp_batch gmapp_batch;
@@ -685,6 +692,20 @@ typedef struct {
                                 obstacles whose bounding box meets a gate, as in
                                 rollout_agents_blockcull; results equal culled = 0 bit for
                                 bit); 0: all pairs */
+    int32_t admit_bypass;    /* aging bound of the admission: 0 admits queued requests in
+                                arrival order, stopping at the first that does not fit;
+                                k > 0 admits first fit over the whole queue (a request that
+                                fits is admitted although an older one does not), but once
+                                the oldest queued request has been overtaken k times, no
+                                later request is admitted before it */
+    int32_t four_term;       /* 1: the chunk kernel also computes the clearance and the
+                                sums of the paper's four-term cost (Eq. cost_function), so
+                                requests may ask for cost_mode 1 (slower pair loop: the
+                                exact distance of every pair); 0: plain cost only.  Not with
+                                culled = 1 */
+    int32_t max_plan_streams; /* with four_term: number of request streams whose current plan
+                                cost C_best the server keeps on the device (Sec. IV-A
+                                "Selection Mechanism"); 0 = none */
 } gmapp_server_config;
 
 /* A request: HOST cloud and agent arrays (kept alive, unmodified, by the
@@ -699,12 +720,24 @@ typedef struct {
     const float *k_r, *k_a, *r_d, *r_a;      /* host [n_agents] */
     int32_t n_agents;
     gmapp_rollout_params prm;
-    gmapp_cost_weights w;
+    gmapp_cost_weights w;    /* cost_mode 0: the weighted cost of score_and_select */
+    int32_t cost_mode;       /* 0: score_and_select with w (plain argmin); 1: the paper's
+                                four-term cost with w4 and the selection against C_best, as
+                                score_and_select4 (needs a four_term server and
+                                prm.cost_radius > 0) */
+    gmapp_cost4 w4;          /* cost_mode 1: weights of the four terms */
+    float alpha;             /* cost_mode 1: hysteresis factor of the selection */
+    int32_t plan_stream;     /* cost_mode 1: the request stream (0 <= s < max_plan_streams)
+                                whose C_best the selection compares against and updates;
+                                requests of one stream are scored in the order they were
+                                submitted.  -1: no current plan (plain argmin) */
 } gmapp_request;
 
 typedef struct {
     int32_t done;
-    int32_t best;          /* selected agent i* */
+    int32_t best;          /* selected agent i*; -1 when, with cost_mode 1 and a current plan,
+                              no agent is cheaper than alpha C_best (keep following the
+                              current plan; best_traj is then undefined) */
     float best_cost;
     int32_t n_obs;         /* N_O of the request's S_W */
     const float *best_traj; /* host [(n_steps+1)*3], valid until release */
@@ -735,12 +768,14 @@ gmapp_status gmapp_server_submit(gmapp_server *server, const gmapp_request *req,
 
 /* One scheduling round: waits for the previous round's chunk, retires
  * requests whose plan reached host memory (freeing their bytes), admits
- * queued requests in arrival order while their bytes fit (H2D copies on the
- * copy stream, filter_cloud on the compute stream), advances every active
- * request by up to chunk_steps steps in ONE persistent launch over
- * (request, agent group) items, and scores the requests that reached their
- * horizon (score_and_select, then D2H of i*, the costs and the chosen
- * trajectory).  *n_active (may be NULL) receives the active count. */
+ * queued requests while their bytes fit (in arrival order, or first fit
+ * with the aging bound admit_bypass; H2D copies on the copy stream,
+ * filter_cloud on the compute stream), advances every active request by up
+ * to chunk_steps steps in ONE persistent launch over (request, agent group)
+ * items, and scores the requests that reached their horizon
+ * (score_and_select, or score_and_select4 against the request stream's
+ * C_best, then D2H of i*, the costs and the chosen trajectory).  *n_active
+ * (may be NULL) receives the active count. */
 gmapp_status gmapp_server_tick(gmapp_server *server, int32_t *n_active);
 
 /* Result of a request: GMAPP_ERR_NOT_READY until done.  Identical bit for

@@ -655,7 +655,10 @@ class Batch:
 
     ``queries``: list of dicts with ``xyz`` (device [N, 3] float32), ``T``,
     ``ws``, ``agents`` (device arrays), ``prm`` and optionally ``obs_cap``
-    (default: the raw point count rounded up to 4) and ``want_traj``.
+    (default: the raw point count rounded up to 4), ``want_traj`` and
+    ``cost4`` (score by the paper's four-term cost with prm.w4, prm.a_max,
+    prm.cost_radius; ``alpha`` and ``c_best``, a device float32 tensor [1]
+    holding the current plan's cost, give the selection's hysteresis).
     Outputs are allocated here; ``results[q]`` holds the query's obstacle
     set, rollout outputs, ``costs``, ``best`` and ``best_traj``."""
 
@@ -672,8 +675,9 @@ class Batch:
             cap = int(spec.get("obs_cap", max(4, (int(xyz.shape[0]) + 3) // 4 * 4)))
             obs = Obstacles.empty(cap)
             obs.r_O = 0.5 * float(spec["ws"].voxel)
+            cost4 = bool(spec.get("cost4", False))
             out = alloc_rollout_out(na, int(prm.n_steps), want_traj=spec.get("want_traj", want_traj),
-                                    want_clear=want_clear)
+                                    want_clear=want_clear, want_cost4=cost4)
             dev = xyz.device
             res = {"obs": obs, "out": out, "costs": torch.empty(na, dtype=torch.float32, device=dev),
                    "best": torch.empty(1, dtype=torch.int32, device=dev),
@@ -695,6 +699,13 @@ class Batch:
             Q.costs = res["costs"].data_ptr()
             Q.best = res["best"].data_ptr()
             Q.best_traj = res["best_traj"].data_ptr() if res["best_traj"] is not None else None
+            if cost4:
+                w4 = tuple(float(v) for v in prm.w4)
+                Q.w4 = _abi.Cost4(w4[0], w4[1], w4[2], w4[3], float(prm.a_max))
+                Q.alpha = float(spec.get("alpha", 1.0))
+                cb = spec.get("c_best")
+                Q.c_best = cb.data_ptr() if cb is not None else None
+                self._keep.append(cb)
         h = C.c_void_p()
         check(_abi.load().gmapp_batch_create(ctx.handle, arr, len(queries), C.byref(h)),
               "gmapp_batch_create")
@@ -755,11 +766,17 @@ class Server:
 
     def __init__(self, max_slots=16, max_agents=1024, max_steps=300, obs_cap=32768,
                  arena_bytes=4 << 30, chunk_steps=50, agents_per_item=8, threads=256,
-                 culled=False):
+                 culled=False, admit_bypass=0, four_term=False, max_plan_streams=0):
+        """``admit_bypass``: 0 admits in arrival order; k > 0 first fit over
+        the queue with an aging bound of k overtakes.  ``four_term``: the
+        chunk kernel computes the clearance and the four-term cost sums, so
+        requests may use ``cost4=True``; ``max_plan_streams`` C_best slots
+        on the device for request streams (``plan_stream``)."""
         ctx = context()
         cfg = _abi.ServerConfig(int(max_slots), int(max_agents), int(max_steps), int(obs_cap),
                                 int(arena_bytes), int(chunk_steps), int(agents_per_item),
-                                int(threads), 2 if culled == "blocks" else int(bool(culled)))
+                                int(threads), 2 if culled == "blocks" else int(bool(culled)),
+                                int(admit_bypass), int(bool(four_term)), int(max_plan_streams))
         h = C.c_void_p()
         check(_abi.load().gmapp_server_create(ctx.handle, C.byref(cfg), C.byref(h)),
               "gmapp_server_create")
@@ -772,7 +789,12 @@ class Server:
             _abi._lib.gmapp_server_destroy(h)
             self.handle = None
 
-    def submit(self, xyz, T, ws, agents: dict, prm) -> int:
+    def submit(self, xyz, T, ws, agents: dict, prm, cost4: bool = False, alpha: float = 1.0,
+               plan_stream: int = -1) -> int:
+        """Queue a request.  ``cost4``: score with the paper's four-term cost
+        (weights prm.w4, prm.a_max, radius prm.cost_radius) and select against
+        the C_best of request stream ``plan_stream`` with hysteresis ``alpha``
+        (-1: plain argmin); needs a server created with four_term=True."""
         r = _abi.Request()
         r.xyz = _host_ptr(xyz)
         r.n_raw = int(xyz.shape[0])
@@ -784,6 +806,14 @@ class Server:
         r.n_agents = int(agents["k_r"].shape[0])
         r.prm = _params_struct(prm)
         r.w = _abi.CostWeights(float(prm.w_path), float(prm.w_goal), float(prm.w_clear))
+        r.cost_mode = 1 if cost4 else 0
+        if cost4:
+            w4 = tuple(float(v) for v in prm.w4)
+            r.w4 = _abi.Cost4(w4[0], w4[1], w4[2], w4[3], float(prm.a_max))
+            r.alpha = float(alpha)
+            r.plan_stream = int(plan_stream)
+        else:
+            r.plan_stream = -1
         t = C.c_int64()
         check(_abi.load().gmapp_server_submit(self.handle, C.byref(r), C.byref(t)),
               "gmapp_server_submit")

@@ -81,19 +81,23 @@ class Query(C.Structure):
     _fields_ = [("xyz", P), ("n_raw", C.c_int64), ("T", C.c_float * 12), ("ws", Workspace),
                 ("agents", Agents), ("prm", RolloutParams), ("w", CostWeights),
                 ("obs", Obstacles), ("out", RolloutOut), ("costs", P), ("best", P),
-                ("best_traj", P)]
+                ("best_traj", P), ("w4", Cost4), ("alpha", C.c_float), ("c_best", P)]
 
 
 class ServerConfig(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("max_agents", C.c_int32), ("max_steps", C.c_int32),
                 ("obs_cap", C.c_int64), ("arena_bytes", C.c_int64), ("chunk_steps", C.c_int32),
-                ("agents_per_item", C.c_int32), ("threads", C.c_int32), ("culled", C.c_int32)]
+                ("agents_per_item", C.c_int32), ("threads", C.c_int32), ("culled", C.c_int32),
+                ("admit_bypass", C.c_int32), ("four_term", C.c_int32),
+                ("max_plan_streams", C.c_int32)]
 
 
 class Request(C.Structure):
     _fields_ = [("xyz", P), ("n_raw", C.c_int64), ("T", C.c_float * 12), ("ws", Workspace),
                 ("p0", P), ("v0", P), ("c", P), ("k_r", P), ("k_a", P), ("r_d", P), ("r_a", P),
-                ("n_agents", C.c_int32), ("prm", RolloutParams), ("w", CostWeights)]
+                ("n_agents", C.c_int32), ("prm", RolloutParams), ("w", CostWeights),
+                ("cost_mode", C.c_int32), ("w4", Cost4), ("alpha", C.c_float),
+                ("plan_stream", C.c_int32)]
 
 
 class Result(C.Structure):

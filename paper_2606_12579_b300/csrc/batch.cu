@@ -63,7 +63,18 @@ struct QueryDev {
     float *costs;
     int32_t *best;
     float *best_traj;
+    // four-term cost (out.cost_terms set): the sums [5][n], its radius,
+    // weights, hysteresis and the plan's C_best
+    float *cost_terms;
+    float cost_radius;
+    float w4[4], smooth_scale, alpha;
+    float *c_best;
 };
+
+// Four-term cost accumulators per agent (as k_rollout's cost columns):
+// 0 sum min(|p - goal|, r_c), 1 sum max(r_c - m, 0), 2 the path length before
+// the last segment, 3 the jerk sum, 4 |p_0 - goal|, 5-7 F_{k-1}, 8-10 f_r at k-1.
+constexpr int kCostRows = 11;
 
 struct BatchDev {
     const QueryDev *q;
@@ -272,6 +283,11 @@ __global__ void __launch_bounds__(NT, 1) kb_rollout(const BatchDev B) {
         const float omax2 = __int_as_float(s_om);
         const float h = Q.vel_half * Q.dt * Q.inv_mass;
         const float goal[3] = {Q.goal[0], Q.goal[1], Q.goal[2]};
+        // four-term cost sums (the arithmetic of k_rollout's exchange warps)
+        const bool four = CLEAR && Q.cost_terms != nullptr;  // uniform per item
+        float cv[kCostRows];
+#pragma unroll
+        for (int r = 0; r < kCostRows; ++r) cv[r] = 0.0f;
         for (int k = 0; k < N; ++k) {
             float *rp = recv + (k & 1) * (NW * AG * 2);
             half_step<AG, AG, 0, NM, NT, CLEAR, true, true, false, true, BOX>(
@@ -281,9 +297,38 @@ __global__ void __launch_bounds__(NT, 1) kb_rollout(const BatchDev B) {
             float W = 0.0f, md2 = INFINITY;
             half_combine<AG, AG, 0, CLEAR>(rp, NW, lane, W, md2);
             if (lane < na) {
-                float g[3], kf, m;
+                float g[3], kf, m, F[3];
+                const float vprev[3] = {v[0], v[1], v[2]};
+                if (four) {
+                    const float gx = p[0] - goal[0], gy = p[1] - goal[1], gz = p[2] - goal[2];
+                    const float dg = sqrtf(fmaf(gz, gz, fmaf(gy, gy, gx * gx)));
+                    cv[0] += fminf(dg, Q.cost_radius);
+                    if (k == 0) cv[4] = dg;
+                    if (k == N - 1) cv[2] = L;  // before the last segment
+                }
                 agent_step<CLEAR>(p, v, cc, k_r, k_a, R, goal, h, Q.dt, Q.rho, Q.damping,
-                                  Q.clear_margin, Q.clear_beta, W, md2, L, pen, minc, m, g, kf);
+                                  Q.clear_margin, Q.clear_beta, W, md2, L, pen, minc, m, g, kf, F);
+                if (four) {
+                    float fr[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) fr[d] = kf * g[d];
+                    cv[1] += fmaxf(Q.cost_radius - m, 0.0f);
+                    if (k >= 2 && k <= N - 2) {
+                        float sj = 0.0f;
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            const float dF = fmaf(-k_a * Q.dt, vprev[d],
+                                                  fmaf(-Q.damping * h, cv[5 + d], fr[d] - cv[8 + d]));
+                            sj = fmaf(dF, dF, sj);
+                        }
+                        cv[3] += sj;
+                    }
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        cv[5 + d] = F[d];
+                        cv[8 + d] = fr[d];
+                    }
+                }
                 if (warp == 0 && Q.traj) {
                     float *t = Q.traj + ((size_t)(a0 + lane) * (N + 1) + k + 1) * 3;
                     t[0] = p[0];
@@ -301,6 +346,14 @@ __global__ void __launch_bounds__(NT, 1) kb_rollout(const BatchDev B) {
             Q.path_len[i] = L;
             if (Q.clear_pen) Q.clear_pen[i] = pen;
             if (Q.min_clear) Q.min_clear[i] = minc;
+            if (four) {
+                const float rc = Q.cost_radius, dh = Q.dt * h;
+                Q.cost_terms[i] = cv[0] / rc;
+                Q.cost_terms[n + i] = cv[1] / rc;
+                Q.cost_terms[2 * n + i] = cv[2];
+                Q.cost_terms[3 * n + i] = dh * dh * cv[3];
+                Q.cost_terms[4 * n + i] = cv[4];
+            }
         }
         __syncthreads();  // the next item's bulk copy overwrites the shard
     }
@@ -324,6 +377,13 @@ __global__ void __launch_bounds__(kScoreThreads) kb_score(const BatchDev B) {
     S.costs = Q.costs;
     S.best = Q.best;
     S.best_traj = Q.best_traj;
+    if (Q.cost_terms) {  // the paper's four-term cost and selection against C_best
+        S.terms = Q.cost_terms;
+        for (int j = 0; j < 4; ++j) S.w4[j] = Q.w4[j];
+        S.smooth_scale = Q.smooth_scale;
+        S.alpha = Q.alpha;
+        S.c_best = Q.c_best;
+    }
     score_select_block(S);
 }
 
@@ -548,7 +608,11 @@ extern "C" gmapp_status gmapp_batch_create(gmapp_ctx *ctx, const gmapp_query *qu
         if (a.n < 1 || !a.p0 || !a.v0 || !a.c || !a.k_r || !a.k_a || !a.r_d || !a.r_a ||
             p.n_steps < 1 || !(p.dt > 0.0f) || !(p.eps > 0.0f) || !(p.clear_beta > 0.0f) ||
             !Qh.out.p_final || !Qh.out.v_final || !Qh.out.path_len || !Qh.costs || !Qh.best ||
-            (Qh.best_traj && !Qh.out.traj) || (Qh.w.w_clear != 0.0f && !Qh.out.clear_pen)) {
+            (Qh.best_traj && !Qh.out.traj) || (Qh.w.w_clear != 0.0f && !Qh.out.clear_pen) ||
+            (Qh.out.cost_terms &&
+             (!(Qh.prm.cost_radius > 0.0f) || !(Qh.w4.a_max > 0.0f) || !isfinite(Qh.alpha) ||
+              !isfinite(Qh.w4.w_goal) || !isfinite(Qh.w4.w_obs) || !isfinite(Qh.w4.w_path) ||
+              !isfinite(Qh.w4.w_smooth)))) {
             set_error("gmapp_batch_create: query %d: invalid agents, parameters or outputs", q);
             delete b;
             return GMAPP_ERR_INVALID_ARG;
@@ -626,7 +690,21 @@ extern "C" gmapp_status gmapp_batch_create(gmapp_ctx *ctx, const gmapp_query *qu
         D.costs = Qh.costs;
         D.best = Qh.best;
         D.best_traj = Qh.best_traj;
-        b->clear = b->clear || Qh.out.clear_pen || Qh.out.min_clear;
+        D.cost_terms = Qh.out.cost_terms;
+        D.cost_radius = p.cost_radius;
+        D.w4[0] = Qh.w4.w_goal;
+        D.w4[1] = Qh.w4.w_obs;
+        D.w4[2] = Qh.w4.w_path;
+        D.w4[3] = Qh.w4.w_smooth;
+        {
+            const double dt = p.dt, am = Qh.w4.a_max;
+            D.smooth_scale = Qh.out.cost_terms
+                                 ? static_cast<float>(1.0 / (p.n_steps * dt * dt * dt * dt * am * am))
+                                 : 0.0f;
+        }
+        D.alpha = Qh.alpha;
+        D.c_best = Qh.c_best;
+        b->clear = b->clear || Qh.out.clear_pen || Qh.out.min_clear || Qh.out.cost_terms;
     }
     b->pt_blocks = static_cast<int32_t>(pt_map.size());
     b->bm_blocks = static_cast<int32_t>(bm_map.size());

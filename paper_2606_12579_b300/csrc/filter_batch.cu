@@ -39,7 +39,7 @@ namespace {
 
 constexpr int kPointsPerThread = 8;      // kf_keys / kf_count: points per thread per iteration
 constexpr int kPointItersPerThread = 2;  // iterations per thread in a job's block range
-constexpr size_t kWaveL2Bytes = size_t(20) << 20;  // L2-resident scratch per wave
+constexpr size_t kWaveL2Bytes = size_t(48) << 20;  // L2-resident scratch per wave
 
 // Division by an invariant divisor d by multiplication (T. Granlund and P. L.
 // Montgomery, "Division by invariant integers using multiplication", PLDI
@@ -72,9 +72,12 @@ struct FilterJob {
     uint32_t *bitmap, *chunk, *sums, *offsets, *counters, *keys;
     uint2 *pw;
     int32_t pt_blk0, pt_nblk, bm_blk0, bm_nblk, sb_blk0, sb_nblk;
+    int64_t n_bm_groups;  // groups of kWordsPerBlock bitmap words (kf_emit loops over them)
     EmitOut o;
     int32_t *n_out;
 };
+
+constexpr int kEmitGroupsPerBlock = 4;  // kf_emit: groups of 1024 words per block
 
 // One point -> its linear voxel key, or kInvalid: the binary32 sequence of
 // voxel_key without the explicit finiteness test.  A non-finite coordinate
@@ -109,10 +112,30 @@ __global__ void __launch_bounds__(kThreads) kf_keys(const FilterJob *J, const in
     uint32_t *__restrict__ bitmap = Q.bitmap;
     const int64_t cells = static_cast<int64_t>(A.nx) * A.ny * A.nz;
     auto chk = [&](uint32_t k) { return k == kInvalid || bc_ok(k, cells, A.err) ? k : kInvalid; };
-    for (int64_t g = blk * kThreads + threadIdx.x; g < n8; g += stride) {
-        const float4 *src = reinterpret_cast<const float4 *>(Q.xyz) + 6 * g;
-        const float4 a0 = __ldcs(src), a1 = __ldcs(src + 1), a2 = __ldcs(src + 2);
-        const float4 a3 = __ldcs(src + 3), a4 = __ldcs(src + 4), a5 = __ldcs(src + 5);
+    // software-pipelined: the next group's six loads are issued before this
+    // group's keys are computed
+    const float4 *pts = reinterpret_cast<const float4 *>(Q.xyz);
+    int64_t g = blk * kThreads + threadIdx.x;
+    float4 b0, b1, b2, b3, b4, b5;
+    if (g < n8) {
+        b0 = __ldcs(pts + 6 * g);
+        b1 = __ldcs(pts + 6 * g + 1);
+        b2 = __ldcs(pts + 6 * g + 2);
+        b3 = __ldcs(pts + 6 * g + 3);
+        b4 = __ldcs(pts + 6 * g + 4);
+        b5 = __ldcs(pts + 6 * g + 5);
+    }
+    for (; g < n8; g += stride) {
+        const float4 a0 = b0, a1 = b1, a2 = b2, a3 = b3, a4 = b4, a5 = b5;
+        const int64_t gn = g + stride;
+        if (gn < n8) {
+            b0 = __ldcs(pts + 6 * gn);
+            b1 = __ldcs(pts + 6 * gn + 1);
+            b2 = __ldcs(pts + 6 * gn + 2);
+            b3 = __ldcs(pts + 6 * gn + 3);
+            b4 = __ldcs(pts + 6 * gn + 4);
+            b5 = __ldcs(pts + 6 * gn + 5);
+        }
         uint4 k, l;
         k.x = chk(key_of(a0.x, a0.y, a0.z, A, inv));
         k.y = chk(key_of(a0.w, a1.x, a1.y, A, inv));
@@ -166,9 +189,9 @@ __global__ void __launch_bounds__(kBmThreads) kf_emit(const FilterJob *J, const 
     __shared__ uint32_t stage[kEmitWarps][kChunkWords * 32];
     const int32_t gb = blockIdx.x + blk0;
     const FilterJob &Q = J[bm_map[gb]];
-    const int64_t blk = gb - Q.bm_blk0;
+    const int64_t eb = gb - Q.bm_blk0;
     const EmitOut o = Q.o;
-    if (blk == 0 && threadIdx.x == 0) {
+    if (eb == 0 && threadIdx.x == 0) {
         const uint32_t t = Q.counters[1];
         *Q.n_out = static_cast<int32_t>(t);
         if (t > o.cap) raise_error(err, GMAPP_DEVERR_CAPACITY);
@@ -177,11 +200,25 @@ __global__ void __launch_bounds__(kBmThreads) kf_emit(const FilterJob *J, const 
     uint32_t *st = stage[warp];
     const FilterArgs A = Q.fa;
     const DivMagic dx = Q.dx, dy = Q.dy;
+    // this block's groups of kWordsPerBlock words: eb, eb + nb, eb + 2 nb, ...
+    const int64_t n_groups = Q.n_bm_groups;
+    for (int64_t blk = eb; blk < n_groups; blk += Q.bm_nblk) {
     const int64_t c0 = (blk * kEmitWarps + warp) * kChunksPerWarp;
-    uint32_t w[kChunksPerWarp];
+    uint32_t w[kChunksPerWarp], cbase[kChunksPerWarp];
 #pragma unroll
-    for (int j = 0; j < kChunksPerWarp; ++j) w[j] = Q.bitmap[(c0 + j) * kChunkWords + lane];
-#pragma unroll 1
+    for (int j = 0; j < kChunksPerWarp; ++j) {
+        w[j] = Q.bitmap[(c0 + j) * kChunkWords + lane];
+        // the chunk's first rank, loaded ahead of the scan (lane j fetches chunk j)
+        cbase[j] = 0;
+    }
+    if (lane < kChunksPerWarp) {
+        const int64_t c = c0 + lane;
+        const uint32_t b = Q.offsets[c / kChunksPerSumBlock] + Q.chunk[c];
+#pragma unroll
+        for (int j = 0; j < kChunksPerWarp; ++j)
+            if (lane == j) cbase[j] = b;
+    }
+#pragma unroll
     for (int j = 0; j < kChunksPerWarp; ++j) {
         if (!__ballot_sync(0xffffffffu, w[j] != 0u)) continue;
         const int64_t c = c0 + j;
@@ -194,7 +231,7 @@ __global__ void __launch_bounds__(kBmThreads) kf_emit(const FilterJob *J, const 
         }
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         const uint32_t excl = incl - cnt;
-        const uint32_t base = Q.offsets[c / kChunksPerSumBlock] + Q.chunk[c];
+        const uint32_t base = __shfl_sync(0xffffffffu, cbase[j], j);
         const uint32_t wv = static_cast<uint32_t>(c * kChunkWords + lane);
         if (w[j]) {
             Q.pw[wv] = make_uint2(base + excl, w[j]);
@@ -228,6 +265,7 @@ __global__ void __launch_bounds__(kBmThreads) kf_emit(const FilterJob *J, const 
         }
         __syncwarp();
     }
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) kf_count(const FilterJob *J, const int32_t *pt_map,
@@ -239,9 +277,20 @@ __global__ void __launch_bounds__(kThreads) kf_count(const FilterJob *J, const i
     const uint2 *__restrict__ pw = Q.pw;
     uint32_t *counts = Q.o.counts, *rep = Q.o.rep;
     const int64_t cap = Q.o.cap;
-    for (int64_t g = blk * kThreads + threadIdx.x; g < n8; g += stride) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(Q.keys + kPointsPerThread * g);
-        const uint4 k = __ldcs(src), l = __ldcs(src + 1);
+    const uint4 *ks = reinterpret_cast<const uint4 *>(Q.keys);
+    int64_t g = blk * kThreads + threadIdx.x;
+    uint4 nk0, nk1;
+    if (g < n8) {
+        nk0 = __ldcs(ks + 2 * g);
+        nk1 = __ldcs(ks + 2 * g + 1);
+    }
+    for (; g < n8; g += stride) {
+        const uint4 k = nk0, l = nk1;
+        const int64_t gn = g + stride;
+        if (gn < n8) {
+            nk0 = __ldcs(ks + 2 * gn);
+            nk1 = __ldcs(ks + 2 * gn + 1);
+        }
         const uint32_t kk[8] = {k.x, k.y, k.z, k.w, l.x, l.y, l.z, l.w};
         uint32_t r[8];
 #pragma unroll
@@ -327,9 +376,10 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
         touched = std::max(touched, static_cast<size_t>(J.n_raw) * 4 +
                                         static_cast<size_t>(L.n_words) * 5);
     }
-    const int W = static_cast<int>(std::max<size_t>(
+    const int W_max = static_cast<int>(std::max<size_t>(
         1, std::min<size_t>(n_jobs, kWaveL2Bytes / touched)));
-    const int n_waves = (n_jobs + W - 1) / W;
+    const int n_waves = (n_jobs + W_max - 1) / W_max;
+    const int W = (n_jobs + n_waves - 1) / n_waves;  // balanced waves
     const int n_slots = std::min(n_waves, 2) * W;
 
     std::vector<FilterJob> hj(n_jobs);
@@ -361,7 +411,8 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
             1, (n8 + kThreads * kPointItersPerThread - 1) / (kThreads * kPointItersPerThread)));
         for (int i = 0; i < D.pt_nblk; ++i) pt_map.push_back(q);
         D.bm_blk0 = static_cast<int32_t>(bm_map.size());
-        D.bm_nblk = static_cast<int32_t>(L.n_blocks);
+        D.n_bm_groups = L.n_blocks;
+        D.bm_nblk = static_cast<int32_t>((L.n_blocks + kEmitGroupsPerBlock - 1) / kEmitGroupsPerBlock);
         for (int i = 0; i < D.bm_nblk; ++i) bm_map.push_back(q);
         D.sb_blk0 = static_cast<int32_t>(sb_map.size());
         D.sb_nblk = static_cast<int32_t>(L.n_sblocks);

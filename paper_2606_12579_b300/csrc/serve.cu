@@ -46,7 +46,17 @@ struct SlotDev {
     float *sp, *sv, *sL;       // saved state between chunks: p [3][n], v [3][n], L [n]
     float *traj, *p_final, *v_final, *path_len;
     NeighbourGrid grid;        // culled server: the request's neighbour index
+    // four-term cost (cost_mode 1; CLEAR chunk kernels): outputs [5][n] and the
+    // sums carried between chunks [kCostRows][n]
+    float *cost_terms, *cacc;
+    float cost_radius;
 };
+
+// Four-term cost accumulators per agent (the rows of k_rollout's cost
+// columns): 0 sum min(|p - goal|, r_c), 1 sum max(r_c - m, 0), 2 the path
+// length before the last segment, 3 the jerk sum, 4 |p_0 - goal|, 5-7
+// F_{k-1}, 8-10 f_r at k-1.
+constexpr int kCostRows = 11;
 
 struct ChunkItem {
     int32_t slot, group, k0, k1;
@@ -66,7 +76,7 @@ struct ChunkArgs {
 // order and lane layout of the voting loop, so the sums equal the all-pairs
 // server's bit for bit); the obstacles beyond the resident part are still
 // evaluated pair by pair.
-template <int AG, int NT, bool BOX>
+template <int AG, int NT, bool BOX, bool CLEAR>
 __global__ void __launch_bounds__(NT, 1) ks_chunk(const ChunkArgs A) {
     constexpr int NW = NT / 32;
     constexpr int NM = sfu_agents(AG);
@@ -198,18 +208,55 @@ __global__ void __launch_bounds__(NT, 1) ks_chunk(const ChunkArgs A) {
         const float omax2 = __int_as_float(s_om);
         const float h = S.vel_half * S.dt * S.inv_mass;
         const float goal[3] = {S.goal[0], S.goal[1], S.goal[2]};
+        // four-term cost sums (the arithmetic of k_rollout's exchange warps),
+        // carried between chunks in S.cacc
+        const bool four = CLEAR && S.cost_terms != nullptr;  // uniform per item
+        float cv[kCostRows];
+#pragma unroll
+        for (int r = 0; r < kCostRows; ++r)
+            cv[r] = four && lane < na && item.k0 > 0 ? S.cacc[r * n + a0 + lane] : 0.0f;
         for (int k = item.k0; k < item.k1; ++k) {
             float *rp = recv + (k & 1) * (NW * AG * 2);
-            half_step<AG, AG, 0, NM, NT, false, true, true, false, true, BOX>(
+            half_step<AG, AG, 0, NM, NT, CLEAR, true, true, false, true, BOX>(
                 sx, sy, sz, cnt_pad, S.eps, nR2, G2a, p, rp + 2 * (warp * AG), 1u, lane, tail,
                 nullptr, nullptr, omax2, boxes);
             __syncthreads();
             float W = 0.0f, md2 = INFINITY;
-            half_combine<AG, AG, 0, false>(rp, NW, lane, W, md2);
+            half_combine<AG, AG, 0, CLEAR>(rp, NW, lane, W, md2);
             if (lane < na) {
-                float g[3], kf, m;
-                agent_step<false>(p, v, cc, k_r, k_a, R, goal, h, S.dt, S.rho, S.damping,
-                                  S.clear_margin, S.clear_beta, W, md2, L, pen, minc, m, g, kf);
+                float g[3], kf, m, F[3];
+                const float vprev[3] = {v[0], v[1], v[2]};
+                if (four) {
+                    const float gx = p[0] - goal[0], gy = p[1] - goal[1], gz = p[2] - goal[2];
+                    const float dg = sqrtf(fmaf(gz, gz, fmaf(gy, gy, gx * gx)));
+                    cv[0] += fminf(dg, S.cost_radius);
+                    if (k == 0) cv[4] = dg;
+                    if (k == N - 1) cv[2] = L;  // before the last segment
+                }
+                agent_step<CLEAR>(p, v, cc, k_r, k_a, R, goal, h, S.dt, S.rho, S.damping,
+                                  S.clear_margin, S.clear_beta, W, md2, L, pen, minc, m, g, kf,
+                                  F);
+                if (four) {
+                    float fr[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) fr[d] = kf * g[d];
+                    cv[1] += fmaxf(S.cost_radius - m, 0.0f);
+                    if (k >= 2 && k <= N - 2) {
+                        float sj = 0.0f;
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            const float dF = fmaf(-k_a * S.dt, vprev[d],
+                                                  fmaf(-S.damping * h, cv[5 + d], fr[d] - cv[8 + d]));
+                            sj = fmaf(dF, dF, sj);
+                        }
+                        cv[3] += sj;
+                    }
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        cv[5 + d] = F[d];
+                        cv[8 + d] = fr[d];
+                    }
+                }
                 if (warp == 0 && S.traj) {
                     float *t = S.traj + ((size_t)(a0 + lane) * (N + 1) + k + 1) * 3;
                     t[0] = p[0];
@@ -225,12 +272,24 @@ __global__ void __launch_bounds__(NT, 1) ks_chunk(const ChunkArgs A) {
                 S.sv[d * n + i] = v[d];
             }
             S.sL[i] = L;
+            if (four) {
+#pragma unroll
+                for (int r = 0; r < kCostRows; ++r) S.cacc[r * n + i] = cv[r];
+            }
             if (item.k1 == N) {
                 for (int d = 0; d < 3; ++d) {
                     S.p_final[d * n + i] = p[d];
                     S.v_final[d * n + i] = v[d];
                 }
                 S.path_len[i] = L;
+                if (four) {
+                    const float rc = S.cost_radius, dh = S.dt * h;
+                    S.cost_terms[i] = cv[0] / rc;
+                    S.cost_terms[n + i] = cv[1] / rc;
+                    S.cost_terms[2 * n + i] = cv[2];
+                    S.cost_terms[3 * n + i] = dh * dh * cv[3];
+                    S.cost_terms[4 * n + i] = cv[4];
+                }
             }
         }
         __syncthreads();
@@ -332,15 +391,15 @@ __global__ void __launch_bounds__(kServeCullThreads) ks_chunk_culled(const Chunk
 
 using ChunkKernel = void (*)(const ChunkArgs);
 
-template <bool BOX>
+template <bool BOX, bool CLEAR>
 ChunkKernel chunk_kernel_t(int ag, int nt) {
 #define GMAPP_CK(AGV)                                                  \
     case AGV:                                                          \
         switch (nt) {                                                  \
-            case 256: return ks_chunk<AGV, 256, BOX>;                  \
-            case 384: return ks_chunk<AGV, 384, BOX>;                  \
+            case 256: return ks_chunk<AGV, 256, BOX, CLEAR>;           \
+            case 384: return ks_chunk<AGV, 384, BOX, CLEAR>;           \
             case 512:                                                  \
-                if constexpr (AGV <= 8) return ks_chunk<AGV, 512, BOX>; \
+                if constexpr (AGV <= 8) return ks_chunk<AGV, 512, BOX, CLEAR>; \
                 return nullptr;                                        \
             default: return nullptr;                                   \
         }
@@ -353,8 +412,9 @@ ChunkKernel chunk_kernel_t(int ag, int nt) {
 #undef GMAPP_CK
 }
 
-ChunkKernel chunk_kernel(int ag, int nt, bool box) {
-    return box ? chunk_kernel_t<true>(ag, nt) : chunk_kernel_t<false>(ag, nt);
+ChunkKernel chunk_kernel(int ag, int nt, bool box, bool clear) {
+    if (clear) return box ? chunk_kernel_t<true, true>(ag, nt) : chunk_kernel_t<false, true>(ag, nt);
+    return box ? chunk_kernel_t<true, false>(ag, nt) : chunk_kernel_t<false, false>(ag, nt);
 }
 
 double now_s() {
@@ -413,6 +473,8 @@ struct ServerReq {
     int slot = -1;
     size_t off = 0, bytes = 0;
     int32_t k = 0;  // steps done
+    int64_t seq = 0;       // position in its plan stream (cost_mode 1, plan_stream >= 0)
+    int32_t bypassed = 0;  // later requests admitted while this one waited
     enum { PENDING, ACTIVE, SCORING, DONE } state = PENDING;
     // results, copied out of the slot's pinned staging when the request retires
     int32_t best = -1, n_obs = 0;
@@ -425,6 +487,7 @@ struct ServerReq {
     float *d_costs = nullptr, *d_best_traj = nullptr;
     int32_t *d_best = nullptr;
     gmapp_rollout_out out{};
+    float *d_cacc = nullptr;  // four-term sums carried between chunks
 };
 
 struct gmapp_server {
@@ -453,6 +516,10 @@ struct gmapp_server {
     size_t smem = 0;
     int shard_cap = 0, resident = 0;
     int64_t completed = 0;
+    // per plan stream: the current plan's cost C_best on the device (NaN =
+    // none yet), the next sequence number to hand out and to score
+    float *d_cbest = nullptr;
+    std::vector<int64_t> next_seq, next_score;
 };
 
 namespace {
@@ -470,6 +537,7 @@ size_t request_bytes(const gmapp_server_config &c, const gmapp_request &r, size_
     add(na * (nk + 1) * 12);                           // trajectories
     add(na * 4 + 4 + (nk + 1) * 12);                   // costs, best, best trajectory
     if (c.culled == 1) add(gmapp_grid_index_bytes(&r.ws));  // neighbour index
+    if (r.cost_mode == 1) add(na * (5 + kCostRows) * 4);    // four-term sums and carry
     return b;
 }
 
@@ -502,6 +570,13 @@ gmapp_status admit(gmapp_server *s, ServerReq *q) {
     float *sel = reinterpret_cast<float *>(take(na * 4 + 4 + (nk + 1) * 12));
     const size_t index_bytes = s->cfg.culled == 1 ? gmapp_grid_index_bytes(&r.ws) : 0;
     uint32_t *index = s->cfg.culled == 1 ? reinterpret_cast<uint32_t *>(take(index_bytes)) : nullptr;
+    q->out.cost_terms = nullptr;
+    q->d_cacc = nullptr;
+    if (r.cost_mode == 1) {
+        float *ct = reinterpret_cast<float *>(take(na * (5 + kCostRows) * 4));
+        q->out.cost_terms = ct;
+        q->d_cacc = ct + 5 * na;
+    }
     q->out.p_final = fin;
     q->out.v_final = fin + 3 * na;
     q->out.path_len = fin + 6 * na;
@@ -564,6 +639,9 @@ gmapp_status admit(gmapp_server *s, ServerReq *q) {
     D.p_final = q->out.p_final;
     D.v_final = q->out.v_final;
     D.path_len = q->out.path_len;
+    D.cost_terms = q->out.cost_terms;
+    D.cacc = q->d_cacc;
+    D.cost_radius = r.prm.cost_radius;
     if (index) {
         D.grid.wr = index;
         for (int a = 0; a < 3; ++a) D.grid.lo[a] = r.ws.lo[a];
@@ -601,14 +679,18 @@ extern "C" gmapp_status gmapp_server_create(gmapp_ctx *ctx, const gmapp_server_c
                                             gmapp_server **out) {
     if (!ctx || !cfg || !out || cfg->max_slots < 1 || cfg->arena_bytes < (1 << 20) ||
         cfg->chunk_steps < 1 || cfg->obs_cap < 4 || cfg->obs_cap % 4 ||
-        cfg->max_agents < 1 || cfg->max_steps < 1 || cfg->culled < 0 || cfg->culled > 2) {
+        cfg->max_agents < 1 || cfg->max_steps < 1 || cfg->culled < 0 || cfg->culled > 2 ||
+        cfg->admit_bypass < 0 || cfg->four_term < 0 || cfg->four_term > 1 ||
+        cfg->max_plan_streams < 0 || (cfg->four_term && cfg->culled == 1) ||
+        (cfg->max_plan_streams > 0 && !cfg->four_term)) {
         set_error("gmapp_server_create: invalid configuration");
         return GMAPP_ERR_INVALID_ARG;
     }
     *out = nullptr;
     const bool grid_cull = cfg->culled == 1;  // 2: block culling in the chunk kernel
     ChunkKernel fn = grid_cull ? ks_chunk_culled
-                               : chunk_kernel(cfg->agents_per_item, cfg->threads, cfg->culled == 2);
+                               : chunk_kernel(cfg->agents_per_item, cfg->threads, cfg->culled == 2,
+                                              cfg->four_term == 1);
     if (!fn) {
         set_error("gmapp_server_create: no chunk kernel for %d agents per item, %d threads",
                   cfg->agents_per_item, cfg->threads);
@@ -657,6 +739,13 @@ extern "C" gmapp_status gmapp_server_create(gmapp_ctx *ctx, const gmapp_server_c
     if (e == cudaSuccess) e = cudaMalloc(&s->d_items, sizeof(ChunkItem) * s->max_items);
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_items, sizeof(ChunkItem) * s->max_items);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_head, sizeof(uint32_t));
+    if (e == cudaSuccess && cfg->max_plan_streams > 0) {
+        // C_best of every plan stream starts as NaN (all bits set): no plan yet
+        e = cudaMalloc(&s->d_cbest, sizeof(float) * cfg->max_plan_streams);
+        if (e == cudaSuccess) e = cudaMemset(s->d_cbest, 0xFF, sizeof(float) * cfg->max_plan_streams);
+        s->next_seq.assign(cfg->max_plan_streams, 0);
+        s->next_score.assign(cfg->max_plan_streams, 0);
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->tick_ev, cudaEventDisableTiming);
     const size_t ms = cfg->max_slots;
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_best, sizeof(int32_t) * ms);
@@ -702,6 +791,7 @@ extern "C" void gmapp_server_destroy(gmapp_server *s) {
     cudaFree(s->d_items);
     cudaFreeHost(s->h_items);
     cudaFree(s->d_head);
+    cudaFree(s->d_cbest);
     if (s->compute) cudaStreamDestroy(s->compute);
     if (s->copy) cudaStreamDestroy(s->copy);
     delete s;
@@ -725,6 +815,22 @@ extern "C" gmapp_status gmapp_server_submit(gmapp_server *s, const gmapp_request
         set_error("gmapp_server_submit: invalid voxel grid");
         return GMAPP_ERR_INVALID_ARG;
     }
+    if (r->cost_mode < 0 || r->cost_mode > 1) {
+        set_error("gmapp_server_submit: cost_mode must be 0 or 1");
+        return GMAPP_ERR_INVALID_ARG;
+    }
+    if (r->cost_mode == 1) {
+        const gmapp_cost4 &w = r->w4;
+        if (!s->cfg.four_term || !(r->prm.cost_radius > 0.0f) || !isfinite(w.w_goal) ||
+            !isfinite(w.w_obs) || !isfinite(w.w_path) || !isfinite(w.w_smooth) ||
+            !(w.a_max > 0.0f) || !isfinite(r->alpha) || r->plan_stream < -1 ||
+            r->plan_stream >= s->cfg.max_plan_streams) {
+            set_error("gmapp_server_submit: the four-term cost needs a four_term server, "
+                      "cost_radius > 0, finite weights and alpha, a_max > 0 and -1 <= "
+                      "plan_stream < max_plan_streams");
+            return GMAPP_ERR_INVALID_ARG;
+        }
+    }
     ServerReq *q = new ServerReq();
     q->req = *r;
     q->ticket = s->next_ticket++;
@@ -736,6 +842,7 @@ extern "C" gmapp_status gmapp_server_submit(gmapp_server *s, const gmapp_request
         set_error("gmapp_server_submit: request needs more than the whole arena");
         return GMAPP_ERR_CAPACITY;
     }
+    if (r->cost_mode == 1 && r->plan_stream >= 0) q->seq = s->next_seq[r->plan_stream]++;
     s->reqs[q->ticket] = q;
     s->pending.push_back(q->ticket);
     *ticket = q->ticket;
@@ -759,20 +866,38 @@ extern "C" gmapp_status gmapp_server_tick(gmapp_server *s, int32_t *n_active) {
         if (cudaEventQuery(s->slot_done[q->slot]) != cudaSuccess) continue;
         retire(s, q);
     }
-    // 2. admit pending requests in arrival order while their bytes fit
-    while (!s->pending.empty() && !s->free_slots.empty()) {
-        ServerReq *q = s->reqs[s->pending.front()];
-        size_t off;
-        if (!s->arena.alloc(q->bytes, &off)) break;
-        s->pending.pop_front();
-        q->off = off;
-        q->slot = s->free_slots.back();
-        s->free_slots.pop_back();
-        q->t_admit = now_s();
-        gmapp_status st = admit(s, q);
-        if (st != GMAPP_OK) return st;
-        q->state = ServerReq::ACTIVE;
-        q->k = 0;
+    // 2. admission: pending requests whose bytes fit, in arrival order; with
+    //    admit_bypass > 0 a request that does not fit is passed over (first
+    //    fit), until it has been overtaken admit_bypass times
+    //    (requests of one plan stream keep their order among themselves, so a
+    //    finished request never waits for the score of one still queued)
+    {
+        std::vector<ServerReq *> skipped;
+        std::vector<char> held(s->next_seq.size(), 0);
+        for (auto it = s->pending.begin(); it != s->pending.end() && !s->free_slots.empty();) {
+            ServerReq *q = s->reqs[*it];
+            const int ps = q->req.cost_mode == 1 ? q->req.plan_stream : -1;
+            size_t off;
+            if ((ps >= 0 && held[ps]) || !s->arena.alloc(q->bytes, &off)) {
+                if (s->cfg.admit_bypass == 0 || q->bypassed >= s->cfg.admit_bypass) break;
+                if (ps >= 0) held[ps] = 1;
+                skipped.push_back(q);
+                ++it;
+                continue;
+            }
+            it = s->pending.erase(it);
+            q->off = off;
+            q->slot = s->free_slots.back();
+            s->free_slots.pop_back();
+            q->t_admit = now_s();
+            gmapp_status st = admit(s, q);
+            if (st != GMAPP_OK) return st;
+            q->state = ServerReq::ACTIVE;
+            q->k = 0;
+            bool aged = false;
+            for (ServerReq *o : skipped) aged |= ++o->bypassed >= s->cfg.admit_bypass;
+            if (aged) break;
+        }
     }
     // 3. one chunk of up to M steps for every active request, one launch
     std::vector<std::pair<int64_t, ChunkItem>> items;
@@ -782,6 +907,7 @@ extern "C" gmapp_status gmapp_server_tick(gmapp_server *s, int32_t *n_active) {
         if (q->state != ServerReq::ACTIVE) continue;
         ++active;
         const int N = q->req.prm.n_steps;
+        if (q->k >= N) continue;  // done, waiting for its turn to be scored
         const int k1 = std::min(N, q->k + s->cfg.chunk_steps);
         // culled: one agent per item (group = agent index)
         const int groups = s->cfg.culled == 1
@@ -813,9 +939,20 @@ extern "C" gmapp_status gmapp_server_tick(gmapp_server *s, int32_t *n_active) {
     for (auto &kv : s->reqs) {
         ServerReq *q = kv.second;
         if (q->state != ServerReq::ACTIVE || q->k < q->req.prm.n_steps) continue;
-        gmapp_status st = score_and_select(s->ctx, &q->out, q->req.n_agents, &q->req.prm,
-                                           &q->req.w, NAN, 1.0f, q->d_costs, q->d_best,
-                                           q->d_best_traj, s->compute);
+        gmapp_status st;
+        if (q->req.cost_mode == 1) {
+            // requests of one plan stream are scored in submission order, so
+            // each compares against the plan its predecessor left in C_best
+            const int ps = q->req.plan_stream;
+            if (ps >= 0 && q->seq != s->next_score[ps]) continue;
+            st = score_and_select4(s->ctx, &q->out, q->req.n_agents, &q->req.prm, &q->req.w4,
+                                   ps >= 0 ? s->d_cbest + ps : nullptr, q->req.alpha,
+                                   q->d_costs, q->d_best, q->d_best_traj, s->compute);
+            if (ps >= 0) ++s->next_score[ps];
+        } else {
+            st = score_and_select(s->ctx, &q->out, q->req.n_agents, &q->req.prm, &q->req.w, NAN,
+                                  1.0f, q->d_costs, q->d_best, q->d_best_traj, s->compute);
+        }
         if (st != GMAPP_OK) return st;
         const size_t nk = q->req.prm.n_steps;
         const int sl = q->slot;

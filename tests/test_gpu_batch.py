@@ -246,3 +246,49 @@ def test_block_culled_batch_equals_unculled_beyond_shared_memory(gm, clear):
         for k in ("traj", "p_final", "v_final", "path_len"):
             assert np.array_equal(a["out"][k].cpu().numpy().view(np.uint32),
                                   c["out"][k].cpu().numpy().view(np.uint32)), (q, k)
+
+
+def test_four_term_cost_in_the_batch(gm):
+    """Batched queries scored by the paper's four-term cost (Eq.
+    cost_function) with the selection against each query's C_best on the
+    device: run 1 picks the argmin and stores its cost, run 2 (same scenes)
+    applies i* = argmin {C_i < alpha C_best}.  Costs agree with
+    rollout_agents + score_and_select4 on each query and with the oracle's
+    four_term_costs; selections follow the alpha rule on the batch's costs."""
+    import math
+    import torch
+    ws_list = _small_queries(n=5, seed=61)
+    specs = _specs(ws_list)
+    alpha = 0.999
+    for w, sp in zip(ws_list, specs):
+        w["params"] = dataclasses.replace(w["params"], cost_radius=0.05, a_max=50.0,
+                                          w4=(1.0, 2.0, 1.0, 0.5))
+        sp["prm"] = w["params"]
+        sp["cost4"] = True
+        sp["alpha"] = alpha
+        sp["c_best"] = torch.full((1,), math.nan, dtype=torch.float32, device="cuda")
+    b = gm.Batch(specs)
+    prev = [math.nan] * len(ws_list)
+    for run in range(2):
+        b.run()
+        gm.sync()
+        for q, (w, sp, r) in enumerate(zip(ws_list, specs, b.results)):
+            prm = w["params"]
+            C = r["costs"].cpu().numpy().astype(np.float64)
+            best = int(r["best"].item())
+            assert best == oracle.select(C, prev[q], alpha)
+            if best >= 0:
+                assert float(sp["c_best"].item()) == np.float32(C[best])
+                prev[q] = float(np.float32(C[best]))
+            if run == 0:
+                out = gm.alloc_rollout_out(w["agents"]["k_r"].size, prm.n_steps, want_cost4=True)
+                gm.rollout_agents(r["obs"], to_dev_agents(w["agents"]), prm, out=out)
+                sel = gm.score_and_select4(out, prm)
+                gm.sync()
+                assert np.allclose(C, sel["costs"].cpu().numpy(), rtol=1e-4, atol=1e-5)
+                f = oracle.filter_cloud(w["xyz"], w["T"], w["workspace"])
+                o = np.stack([f["x"], f["y"], f["z"]])
+                ref = oracle.rollout(o, f["r_O"], w["agents"], prm, want_trace=True)
+                want = oracle.four_term_costs(ref["traj"], ref["m_trace"], prm.goal, prm.dt,
+                                              prm.cost_radius, prm.a_max, prm.w4)["C"]
+                assert np.allclose(C, want, rtol=1e-3, atol=1e-3)

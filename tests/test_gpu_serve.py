@@ -254,3 +254,115 @@ def test_served_stream_shape_mix_equals_alone_and_oracle(gm):
         assert r["best"] == oi or abs(c_ref[r["best"]] - c_ref[oi]) < 1e-6
         assert np.allclose(r["costs"], c_ref, rtol=1e-4, atol=1e-4)
         assert np.abs(r["best_traj"] - ref["traj"][r["best"]]).max() <= 1e-3
+
+
+def _four_term_requests():
+    """A plan stream of successive frames (moving spheres) plus plain-cost
+    requests and a four-term request without a stream, interleaved."""
+    import dataclasses
+    ws = _requests(n=8, seed=41)
+    for w in ws:
+        w["params"] = dataclasses.replace(w["params"], cost_radius=0.05, a_max=50.0,
+                                          w4=(1.0, 2.0, 1.0, 0.5))
+    # (request, cost4, plan_stream)
+    kinds = [(0, True, 0), (1, False, -1), (2, True, 0), (3, True, -1), (4, True, 0),
+             (5, False, -1), (6, True, 0), (7, True, 0)]
+    return ws, kinds
+
+
+def _serve4(gm, ws, kinds, alpha, one_at_a_time=False, bypass=4):
+    srv = gm.Server(max_slots=8, max_agents=64, max_steps=200, obs_cap=16384,
+                    arena_bytes=1 << 28, chunk_steps=16, agents_per_item=8,
+                    four_term=True, max_plan_streams=2, admit_bypass=bypass)
+    out, max_active = [], 0
+    tickets = []
+    for r, c4, ps in kinds:
+        w = ws[r]
+        t = srv.submit(w["xyz"], w["T"], w["workspace"], w["agents"], w["params"], cost4=c4,
+                       alpha=alpha, plan_stream=ps)
+        tickets.append(t)
+        if one_at_a_time:
+            res = None
+            while res is None:
+                srv.tick()
+                res = srv.poll(t)
+        else:
+            max_active = max(max_active, srv.tick())
+    done = {}
+    for _ in range(10000):
+        if len(done) == len(tickets):
+            break
+        max_active = max(max_active, srv.tick())
+        for t in tickets:
+            if t not in done:
+                res = srv.poll(t)
+                if res is not None:
+                    done[t] = res
+    return [done[t] for t in tickets], max_active
+
+
+def test_four_term_server_plan_stream(gm):
+    """The paper's four-term cost (Eq. cost_function) and the selection
+    against the current plan (i* = argmin {C_i < alpha C_best}) in the served
+    loop.  A plan stream of five requests shares one device-resident C_best,
+    mixed with plain-cost requests and a four-term request without a
+    stream.  Every result equals the same sequence served one request at a
+    time, bit for bit; each four-term request's costs and selection agree
+    with rollout_agents + score_and_select4 on the same query with its own
+    C_best chain; the selection follows alpha C_best on the server's costs;
+    and the costs and selections agree with the oracle's four_term_costs and
+    select on the oracle's own chain."""
+    import math
+    import torch
+    alpha = 0.95
+    ws, kinds = _four_term_requests()
+    mixed, max_active = _serve4(gm, ws, kinds, alpha)
+    assert max_active >= 2
+    alone, _ = _serve4(gm, ws, kinds, alpha, one_at_a_time=True, bypass=0)
+    for a, b in zip(alone, mixed):
+        assert a["best"] == b["best"]
+        assert np.array_equal(a["costs"].view(np.uint32), b["costs"].view(np.uint32))
+        if b["best"] >= 0:
+            assert np.array_equal(a["best_traj"].view(np.uint32), b["best_traj"].view(np.uint32))
+    c_dev = torch.full((1,), math.nan, dtype=torch.float32, device="cuda")
+    srv_best, ora_best = math.nan, math.nan
+    kept, agree = 0, 0
+    for (r, c4, ps), res in zip(kinds, mixed):
+        w = ws[r]
+        prm = w["params"]
+        if not c4:
+            continue
+        # the same query through the single-query calls
+        obs = gm.filter_cloud(torch.from_numpy(w["xyz"]).cuda(), w["T"], w["workspace"],
+                              cap=16384)
+        out = gm.alloc_rollout_out(w["agents"]["k_r"].size, prm.n_steps, want_cost4=True)
+        gm.rollout_agents(obs, {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda()
+                                for k, v in w["agents"].items()}, prm, out=out)
+        sel = gm.score_and_select4(out, prm, c_best=c_dev if ps == 0 else None, alpha=alpha)
+        gm.sync()
+        direct = sel["costs"].cpu().numpy().astype(np.float64)
+        assert np.allclose(res["costs"], direct, rtol=1e-4, atol=1e-5)
+        # the server's selection follows the alpha rule on its own costs
+        prev = srv_best if ps == 0 else math.nan
+        want = oracle.select(res["costs"].astype(np.float64), prev, alpha)
+        assert res["best"] == want
+        if ps == 0 and res["best"] >= 0:
+            srv_best = float(res["costs"][res["best"]])
+        kept += res["best"] < 0
+        # the oracle on its own chain
+        f = oracle.filter_cloud(w["xyz"], w["T"], w["workspace"])
+        o = np.stack([f["x"], f["y"], f["z"]])
+        ref = oracle.rollout(o, f["r_O"], w["agents"], prm, want_trace=True)
+        C = oracle.four_term_costs(ref["traj"], ref["m_trace"], prm.goal, prm.dt,
+                                   prm.cost_radius, prm.a_max, prm.w4)["C"]
+        assert np.allclose(res["costs"], C, rtol=1e-3, atol=1e-3)
+        oprev = ora_best if ps == 0 else math.nan
+        oi = oracle.select(C, oprev, alpha)
+        if ps == 0 and oi >= 0:
+            ora_best = float(C[oi])
+        gi = res["best"]
+        same = gi == oi or (gi >= 0 and oi >= 0 and abs(C[gi] - C[oi]) < 1e-4)
+        agree += same
+    print(f"four-term server: {kept} requests kept the current plan; {agree} of 6 selections "
+          f"agree with the oracle's chain")
+    assert agree >= 5
