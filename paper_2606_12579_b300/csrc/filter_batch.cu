@@ -4,22 +4,21 @@
 // A single frame is a few MB, far less than a launch needs to approach HBM
 // bandwidth, and a whole stream's scratch (key per point, bitmap over the
 // grid) is far larger than L2.  So the jobs are filtered in WAVES whose
-// scratch fits comfortably in L2 (about 20 MB: a few frames), each wave
-// through four launches, and consecutive waves alternate between the
-// caller's stream and a second stream of the batch, so the latency-bound
-// passes of one wave overlap the bandwidth-bound key pass of the next.  The
-// two streams each own one set of scratch slots, reused wave after wave: the
-// per-point keys and bitmap words a wave writes are read back from L2 and
-// overwritten there by the wave after next, so only the raw points and the
-// obstacle sets move through DRAM.
+// scratch fits in L2 (at most 48 MB of keys and bitmap words: 16 tabletop
+// frames), each wave through four launches, and consecutive waves alternate
+// between the caller's stream and a second stream of the batch, so the
+// passes of one wave overlap those of the next.  The two streams each own
+// one set of scratch slots, reused wave after wave.
 //
 //   kf_keys   8 points per thread and iteration (six 16-byte streaming
 //             loads in flight): key per point + bitmap bits
 //   kf_sums   per-block (and per-chunk) popcounts; each job's last block
-//             scans its block sums
-//   kf_emit   per 32-word chunk: ranks of its words (warp scan), the chunk's
-//             set bits compacted in shared memory, then written 32 obstacles
-//             at a time (coalesced: key, count 0, index ~0, centre); publishes
+//             scans its block sums; the occupied 32-word chunks are appended
+//             to the job's chunk list
+//   kf_emit   persistent over the wave's occupied chunks (empty ones cost
+//             nothing): ranks of a chunk's words (warp scan), its set bits
+//             compacted in shared memory, then written 32 obstacles at a
+//             time (coalesced: key, count 0, index ~0, centre); publishes
 //             each job's N_O and clears the bitmap words behind it
 //   kf_count  8 keys per thread and iteration: per-voxel point counts and
 //             smallest point index
@@ -38,7 +37,7 @@ namespace gmapp {
 namespace {
 
 constexpr int kPointsPerThread = 8;      // kf_keys / kf_count: points per thread per iteration
-constexpr int kPointItersPerThread = 2;  // iterations per thread in a job's block range
+constexpr int kPointItersPerThread = 4;  // kf_keys / kf_count: iterations per thread
 constexpr size_t kWaveL2Bytes = size_t(48) << 20;  // L2-resident scratch per wave
 
 // Division by an invariant divisor d by multiplication (T. Granlund and P. L.
@@ -70,14 +69,13 @@ struct FilterJob {
     FilterArgs fa;
     DivMagic dx, dy;  // division by dims_x, dims_y (key -> cell coordinates)
     uint32_t *bitmap, *chunk, *sums, *offsets, *counters, *keys;
+    uint32_t *chunk_list;  // occupied 32-word chunks (kf_sums appends, kf_emit visits);
+                           // their number in counters[3]
     uint2 *pw;
-    int32_t pt_blk0, pt_nblk, bm_blk0, bm_nblk, sb_blk0, sb_nblk;
-    int64_t n_bm_groups;  // groups of kWordsPerBlock bitmap words (kf_emit loops over them)
+    int32_t pt_blk0, pt_nblk, sb_blk0, sb_nblk;
     EmitOut o;
     int32_t *n_out;
 };
-
-constexpr int kEmitGroupsPerBlock = 4;  // kf_emit: groups of 1024 words per block
 
 // One point -> its linear voxel key, or kInvalid: the binary32 sequence of
 // voxel_key without the explicit finiteness test.  A non-finite coordinate
@@ -100,6 +98,9 @@ __device__ __forceinline__ uint32_t key_of(float x, float y, float z, const Filt
     return (idx[2] * A.ny + idx[1]) * A.nx + idx[0];
 }
 
+// Points -> keys: 8 consecutive points per thread and iteration (six
+// 16-byte streaming loads in flight), key per point stored, bitmap bits
+// merged per thread.
 __global__ void __launch_bounds__(kThreads) kf_keys(const FilterJob *J, const int32_t *pt_map,
                                                     int32_t blk0) {
     const int32_t gb = blockIdx.x + blk0;
@@ -112,30 +113,11 @@ __global__ void __launch_bounds__(kThreads) kf_keys(const FilterJob *J, const in
     uint32_t *__restrict__ bitmap = Q.bitmap;
     const int64_t cells = static_cast<int64_t>(A.nx) * A.ny * A.nz;
     auto chk = [&](uint32_t k) { return k == kInvalid || bc_ok(k, cells, A.err) ? k : kInvalid; };
-    // software-pipelined: the next group's six loads are issued before this
-    // group's keys are computed
-    const float4 *pts = reinterpret_cast<const float4 *>(Q.xyz);
-    int64_t g = blk * kThreads + threadIdx.x;
-    float4 b0, b1, b2, b3, b4, b5;
-    if (g < n8) {
-        b0 = __ldcs(pts + 6 * g);
-        b1 = __ldcs(pts + 6 * g + 1);
-        b2 = __ldcs(pts + 6 * g + 2);
-        b3 = __ldcs(pts + 6 * g + 3);
-        b4 = __ldcs(pts + 6 * g + 4);
-        b5 = __ldcs(pts + 6 * g + 5);
-    }
-    for (; g < n8; g += stride) {
-        const float4 a0 = b0, a1 = b1, a2 = b2, a3 = b3, a4 = b4, a5 = b5;
-        const int64_t gn = g + stride;
-        if (gn < n8) {
-            b0 = __ldcs(pts + 6 * gn);
-            b1 = __ldcs(pts + 6 * gn + 1);
-            b2 = __ldcs(pts + 6 * gn + 2);
-            b3 = __ldcs(pts + 6 * gn + 3);
-            b4 = __ldcs(pts + 6 * gn + 4);
-            b5 = __ldcs(pts + 6 * gn + 5);
-        }
+    if (blk == 0 && threadIdx.x == 0) Q.counters[3] = 0;  // kf_sums refills the chunk list
+    for (int64_t g = blk * kThreads + threadIdx.x; g < n8; g += stride) {
+        const float4 *src = reinterpret_cast<const float4 *>(Q.xyz) + 6 * g;
+        const float4 a0 = __ldcs(src), a1 = __ldcs(src + 1), a2 = __ldcs(src + 2);
+        const float4 a3 = __ldcs(src + 3), a4 = __ldcs(src + 4), a5 = __ldcs(src + 5);
         uint4 k, l;
         k.x = chk(key_of(a0.x, a0.y, a0.z, A, inv));
         k.y = chk(key_of(a0.w, a1.x, a1.y, A, inv));
@@ -173,101 +155,103 @@ __global__ void __launch_bounds__(kBmThreads) kf_sums(const FilterJob *J, const 
     const int32_t gb = blockIdx.x + blk0;
     const FilterJob &Q = J[sb_map[gb]];
     bitmap_sums_block(Q.bitmap, Q.chunk, Q.sums, Q.offsets, Q.counters, Q.counters + 1,
-                      gb - Q.sb_blk0, Q.sb_nblk);
+                      gb - Q.sb_blk0, Q.sb_nblk, Q.chunk_list, Q.counters + 3);
 }
 
-// Per warp: kChunksPerWarp chunks of 32 words.  For an occupied chunk, each
-// lane ranks its word (warp scan of popcounts on top of the chunk's offset),
+// The occupied 32-word chunks of the wave's jobs, one per warp at a time
+// (every warp of the grid strides over each job's chunk list): each lane
+// ranks its word (warp scan of popcounts on top of the chunk's offset),
 // records (rank, bits) for kf_count, clears the word, and writes the keys of
 // its set bits to the warp's stage in shared memory at their ranks within
 // the chunk; the warp then writes the chunk's obstacles 32 consecutive ranks
-// at a time.
+// at a time.  Empty chunks cost nothing here.
 constexpr int kEmitWarps = kBmThreads / 32;
 
-__global__ void __launch_bounds__(kBmThreads) kf_emit(const FilterJob *J, const int32_t *bm_map,
-                                                      int32_t blk0, uint32_t *err) {
+__global__ void __launch_bounds__(kBmThreads) kf_emit(const FilterJob *J, int32_t q0, int32_t q1,
+                                                      uint32_t *err) {
     __shared__ uint32_t stage[kEmitWarps][kChunkWords * 32];
-    const int32_t gb = blockIdx.x + blk0;
-    const FilterJob &Q = J[bm_map[gb]];
-    const int64_t eb = gb - Q.bm_blk0;
-    const EmitOut o = Q.o;
-    if (eb == 0 && threadIdx.x == 0) {
-        const uint32_t t = Q.counters[1];
-        *Q.n_out = static_cast<int32_t>(t);
-        if (t > o.cap) raise_error(err, GMAPP_DEVERR_CAPACITY);
-    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = q0 + static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x); q < q1;
+         q += static_cast<int>(gridDim.x * blockDim.x)) {
+        const uint32_t t = J[q].counters[1];
+        *J[q].n_out = static_cast<int32_t>(t);
+        if (t > J[q].o.cap) raise_error(err, GMAPP_DEVERR_CAPACITY);
+    }
     uint32_t *st = stage[warp];
-    const FilterArgs A = Q.fa;
-    const DivMagic dx = Q.dx, dy = Q.dy;
-    // this block's groups of kWordsPerBlock words: eb, eb + nb, eb + 2 nb, ...
-    const int64_t n_groups = Q.n_bm_groups;
-    for (int64_t blk = eb; blk < n_groups; blk += Q.bm_nblk) {
-    const int64_t c0 = (blk * kEmitWarps + warp) * kChunksPerWarp;
-    uint32_t w[kChunksPerWarp], cbase[kChunksPerWarp];
-#pragma unroll
-    for (int j = 0; j < kChunksPerWarp; ++j) {
-        w[j] = Q.bitmap[(c0 + j) * kChunkWords + lane];
-        // the chunk's first rank, loaded ahead of the scan (lane j fetches chunk j)
-        cbase[j] = 0;
-    }
-    if (lane < kChunksPerWarp) {
-        const int64_t c = c0 + lane;
-        const uint32_t b = Q.offsets[c / kChunksPerSumBlock] + Q.chunk[c];
-#pragma unroll
-        for (int j = 0; j < kChunksPerWarp; ++j)
-            if (lane == j) cbase[j] = b;
-    }
-#pragma unroll
-    for (int j = 0; j < kChunksPerWarp; ++j) {
-        if (!__ballot_sync(0xffffffffu, w[j] != 0u)) continue;
-        const int64_t c = c0 + j;
-        const uint32_t cnt = __popc(w[j]);
-        uint32_t incl = cnt;
+    const uint32_t gw = blockIdx.x * kEmitWarps + warp, tw = gridDim.x * kEmitWarps;
+    // the wave's chunk lists as one index space: lane l holds the number of
+    // occupied chunks of jobs q0 .. q0 + l (inclusive scan), 32 jobs a round
+    for (int qb = q0; qb < q1; qb += 32) {
+        const int qn = min(32, q1 - qb);
+        uint32_t incl = lane < qn ? J[qb + lane].counters[3] : 0u;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= d) incl += y;
         }
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const uint32_t excl = incl - cnt;
-        const uint32_t base = __shfl_sync(0xffffffffu, cbase[j], j);
-        const uint32_t wv = static_cast<uint32_t>(c * kChunkWords + lane);
-        if (w[j]) {
-            Q.pw[wv] = make_uint2(base + excl, w[j]);
-            Q.bitmap[wv] = 0u;
-        }
-        uint32_t bits = w[j], pos = excl;
-        const uint32_t k0 = wv * 32u;
-        while (bits) {
-            const uint32_t b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            st[pos++] = k0 + b;
-        }
-        __syncwarp();
-        for (uint32_t r = lane; r < total; r += 32) {
-            const uint32_t key = st[r];
-            const uint32_t rank = base + r;
-            if (rank < o.cap) {
-                const uint32_t q1 = div_by(key, dx);
-                const uint32_t ix = key - q1 * A.nx;
-                const uint32_t iz = div_by(q1, dy);
-                const uint32_t iy = q1 - iz * A.ny;
-                float cx, cy, cz;
-                cell_centre(ix, iy, iz, A, cx, cy, cz);
-                o.keys[rank] = key;
-                o.counts[rank] = 0u;
-                o.rep[rank] = kInvalid;
-                o.x[rank] = cx;
-                o.y[rank] = cy;
-                o.z[rank] = cz;
+        const uint32_t total_chunks = __shfl_sync(0xffffffffu, incl, 31);
+        for (uint32_t gi = gw; gi < total_chunks; gi += tw) {
+            // job of gi: the first lane whose inclusive count exceeds gi
+            const uint32_t jl = __ffs(__ballot_sync(0xffffffffu, lane < qn && incl > gi)) - 1;
+            const uint32_t prev = __shfl_sync(0xffffffffu, incl, (jl + 31) & 31);  // lane jl - 1
+            const uint32_t li = gi - (jl ? prev : 0u);
+            const FilterJob &Q = J[qb + jl];
+            const EmitOut o = Q.o;
+            const FilterArgs A = Q.fa;
+            const DivMagic dx = Q.dx, dy = Q.dy;
+            const uint32_t c = Q.chunk_list[li];
+            const uint32_t wv = c * kChunkWords + lane;
+            const uint32_t w = Q.bitmap[wv];
+            uint32_t base = 0;
+            if (lane == 0) base = Q.offsets[c / kChunksPerSumBlock] + Q.chunk[c];
+            const uint32_t cnt = __popc(w);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
             }
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t excl = incl - cnt;
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (w) {
+                Q.pw[wv] = make_uint2(base + excl, w);
+                Q.bitmap[wv] = 0u;
+            }
+            uint32_t bits = w, pos = excl;
+            const uint32_t k0 = wv * 32u;
+            while (bits) {
+                const uint32_t b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                st[pos++] = k0 + b;
+            }
+            __syncwarp();
+            for (uint32_t r = lane; r < total; r += 32) {
+                const uint32_t key = st[r];
+                const uint32_t rank = base + r;
+                if (rank < o.cap) {
+                    const uint32_t qy = div_by(key, dx);
+                    const uint32_t ix = key - qy * A.nx;
+                    const uint32_t iz = div_by(qy, dy);
+                    const uint32_t iy = qy - iz * A.ny;
+                    float cx, cy, cz;
+                    cell_centre(ix, iy, iz, A, cx, cy, cz);
+                    o.keys[rank] = key;
+                    o.counts[rank] = 0u;
+                    o.rep[rank] = kInvalid;
+                    o.x[rank] = cx;
+                    o.y[rank] = cy;
+                    o.z[rank] = cz;
+                }
+            }
+            __syncwarp();
         }
-        __syncwarp();
-    }
     }
 }
 
+// Keys -> ranks (the word's rank and bits, pw, from L2) -> counts and
+// smallest indices, 8 consecutive keys per thread and iteration, runs of
+// equal ranks merged per thread.
 __global__ void __launch_bounds__(kThreads) kf_count(const FilterJob *J, const int32_t *pt_map,
                                                      int32_t blk0) {
     const int32_t gb = blockIdx.x + blk0;
@@ -277,20 +261,9 @@ __global__ void __launch_bounds__(kThreads) kf_count(const FilterJob *J, const i
     const uint2 *__restrict__ pw = Q.pw;
     uint32_t *counts = Q.o.counts, *rep = Q.o.rep;
     const int64_t cap = Q.o.cap;
-    const uint4 *ks = reinterpret_cast<const uint4 *>(Q.keys);
-    int64_t g = blk * kThreads + threadIdx.x;
-    uint4 nk0, nk1;
-    if (g < n8) {
-        nk0 = __ldcs(ks + 2 * g);
-        nk1 = __ldcs(ks + 2 * g + 1);
-    }
-    for (; g < n8; g += stride) {
-        const uint4 k = nk0, l = nk1;
-        const int64_t gn = g + stride;
-        if (gn < n8) {
-            nk0 = __ldcs(ks + 2 * gn);
-            nk1 = __ldcs(ks + 2 * gn + 1);
-        }
+    for (int64_t g = blk * kThreads + threadIdx.x; g < n8; g += stride) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(Q.keys + kPointsPerThread * g);
+        const uint4 k = __ldcs(src), l = __ldcs(src + 1);
         const uint32_t kk[8] = {k.x, k.y, k.z, k.w, l.x, l.y, l.z, l.w};
         uint32_t r[8];
 #pragma unroll
@@ -320,10 +293,11 @@ using namespace gmapp;
 struct gmapp_filter_batch {
     gmapp_ctx *ctx = nullptr;
     FilterJob *d_jobs = nullptr;
-    int32_t *d_pt_map = nullptr, *d_bm_map = nullptr, *d_sb_map = nullptr;
+    int32_t *d_pt_map = nullptr, *d_sb_map = nullptr;
     void *d_ws = nullptr;
     // per wave: first block and block count of each launch
-    std::vector<int32_t> pt0, ptn, bm0, bmn, sb0, sbn;
+    std::vector<int32_t> pt0, ptn, sb0, sbn, q0, q1;  // per wave
+    int emit_grid = 0;
     cudaStream_t side = nullptr;  // odd waves (the caller's stream runs the even ones)
     cudaEvent_t fork = nullptr, join = nullptr;
 };
@@ -333,7 +307,6 @@ namespace {
 void release(gmapp_filter_batch *fb) {
     cudaFree(fb->d_jobs);
     cudaFree(fb->d_pt_map);
-    cudaFree(fb->d_bm_map);
     cudaFree(fb->d_sb_map);
     cudaFree(fb->d_ws);
     if (fb->fork) cudaEventDestroy(fb->fork);
@@ -371,7 +344,8 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
                 return GMAPP_ERR_INVALID_ARG;
             }
         const Layout L = layout(J.n_raw, &J.ws);
-        slot_bytes = std::max(slot_bytes, align_up(L.total, 256));
+        slot_bytes = std::max(slot_bytes, align_up(L.total, 256) +
+                                              align_up(static_cast<size_t>(L.n_words / kChunkWords) * 4, 256));
         // scratch a wave keeps in L2: keys, bitmap, the occupied words' ranks
         touched = std::max(touched, static_cast<size_t>(J.n_raw) * 4 +
                                         static_cast<size_t>(L.n_words) * 5);
@@ -383,9 +357,10 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
     const int n_slots = std::min(n_waves, 2) * W;
 
     std::vector<FilterJob> hj(n_jobs);
-    std::vector<int32_t> pt_map, bm_map, sb_map;
+    std::vector<int32_t> pt_map, sb_map;
     gmapp_filter_batch *fb = new gmapp_filter_batch();
     fb->ctx = ctx;
+    fb->emit_grid = ctx->sm_count * 4;  // persistent over the wave's occupied chunks
     for (int q = 0; q < n_jobs; ++q) {
         const gmapp_cloud_job &J = jobs[q];
         const Layout L = layout(J.n_raw, &J.ws);
@@ -410,17 +385,13 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
         D.pt_nblk = static_cast<int32_t>(std::max<int64_t>(
             1, (n8 + kThreads * kPointItersPerThread - 1) / (kThreads * kPointItersPerThread)));
         for (int i = 0; i < D.pt_nblk; ++i) pt_map.push_back(q);
-        D.bm_blk0 = static_cast<int32_t>(bm_map.size());
-        D.n_bm_groups = L.n_blocks;
-        D.bm_nblk = static_cast<int32_t>((L.n_blocks + kEmitGroupsPerBlock - 1) / kEmitGroupsPerBlock);
-        for (int i = 0; i < D.bm_nblk; ++i) bm_map.push_back(q);
         D.sb_blk0 = static_cast<int32_t>(sb_map.size());
         D.sb_nblk = static_cast<int32_t>(L.n_sblocks);
         for (int i = 0; i < D.sb_nblk; ++i) sb_map.push_back(q);
         D.o = EmitOut{J.out.keys, J.out.counts, J.out.rep_idx, J.out.x, J.out.y, J.out.z,
                       J.out.cap};
         D.n_out = J.out.n;
-        if (pt_map.size() > 0x7fffffffu || bm_map.size() > 0x7fffffffu) {
+        if (pt_map.size() > 0x7fffffffu || sb_map.size() > 0x7fffffffu) {
             delete fb;
             set_error("gmapp_filter_batch_create: too many blocks");
             return GMAPP_ERR_CAPACITY;
@@ -430,8 +401,8 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
         const int q0 = w * W, q1 = std::min(n_jobs, q0 + W) - 1;
         fb->pt0.push_back(hj[q0].pt_blk0);
         fb->ptn.push_back(hj[q1].pt_blk0 + hj[q1].pt_nblk - hj[q0].pt_blk0);
-        fb->bm0.push_back(hj[q0].bm_blk0);
-        fb->bmn.push_back(hj[q1].bm_blk0 + hj[q1].bm_nblk - hj[q0].bm_blk0);
+        fb->q0.push_back(q0);
+        fb->q1.push_back(q1 + 1);
         fb->sb0.push_back(hj[q0].sb_blk0);
         fb->sbn.push_back(hj[q1].sb_blk0 + hj[q1].sb_nblk - hj[q0].sb_blk0);
     }
@@ -442,7 +413,6 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
     if (e == cudaSuccess) e = cudaMemset(fb->d_ws, 0, ws_total);
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_jobs, sizeof(FilterJob) * n_jobs);
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_pt_map, sizeof(int32_t) * pt_map.size());
-    if (e == cudaSuccess) e = cudaMalloc(&fb->d_bm_map, sizeof(int32_t) * bm_map.size());
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_sb_map, sizeof(int32_t) * sb_map.size());
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fb->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fb->fork, cudaEventDisableTiming);
@@ -462,15 +432,13 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
             D.offsets = reinterpret_cast<uint32_t *>(base + L.off_offsets);
             D.counters = reinterpret_cast<uint32_t *>(base + L.off_counters);
             D.keys = reinterpret_cast<uint32_t *>(base + L.off_keys);
+            D.chunk_list = reinterpret_cast<uint32_t *>(base + align_up(L.total, 256));
         }
         e = cudaMemcpy(fb->d_jobs, hj.data(), sizeof(FilterJob) * n_jobs,
                        cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess)
         e = cudaMemcpy(fb->d_pt_map, pt_map.data(), sizeof(int32_t) * pt_map.size(),
-                       cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(fb->d_bm_map, bm_map.data(), sizeof(int32_t) * bm_map.size(),
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(fb->d_sb_map, sb_map.data(), sizeof(int32_t) * sb_map.size(),
@@ -506,7 +474,7 @@ extern "C" gmapp_status filter_cloud_batch(gmapp_filter_batch *fb, gmapp_stream 
         cudaStream_t s = (w % 2 == 0) ? stream : fb->side;
         kf_keys<<<fb->ptn[w], kThreads, 0, s>>>(fb->d_jobs, fb->d_pt_map, fb->pt0[w]);
         kf_sums<<<fb->sbn[w], kBmThreads, 0, s>>>(fb->d_jobs, fb->d_sb_map, fb->sb0[w]);
-        kf_emit<<<fb->bmn[w], kBmThreads, 0, s>>>(fb->d_jobs, fb->d_bm_map, fb->bm0[w],
+        kf_emit<<<fb->emit_grid, kBmThreads, 0, s>>>(fb->d_jobs, fb->q0[w], fb->q1[w],
                                                    fb->ctx->d_err);
         kf_count<<<fb->ptn[w], kThreads, 0, s>>>(fb->d_jobs, fb->d_pt_map, fb->pt0[w]);
     }

@@ -222,10 +222,15 @@ __device__ uint32_t scan_block_sums(const uint32_t *sums, uint32_t *offsets, int
 // exclusive popcount prefix within the block (chunk_off) and the block
 // total.  The last block to finish scans all block totals into offsets and
 // publishes the total number of occupied voxels.
+// With `list` (and its counter *n_list), the index of every occupied chunk
+// is also appended to list (in no particular order), so a later pass can
+// visit only those.
 __device__ __forceinline__ void bitmap_sums_block(const uint32_t *__restrict__ bitmap,
                                                   uint32_t *chunk_off, uint32_t *sums,
                                                   uint32_t *offsets, uint32_t *counter,
-                                                  uint32_t *n_occ, int64_t blk, int64_t nblk) {
+                                                  uint32_t *n_occ, int64_t blk, int64_t nblk,
+                                                  uint32_t *list = nullptr,
+                                                  uint32_t *n_list = nullptr) {
     __shared__ uint32_t warp_tot[kBmThreads / 32];
     __shared__ bool is_last;
     const int t = threadIdx.x;
@@ -238,6 +243,16 @@ __device__ __forceinline__ void bitmap_sums_block(const uint32_t *__restrict__ b
     }
     // a chunk is two consecutive threads: the even one carries its sum
     c += __shfl_xor_sync(0xffffffffu, c, 1);
+    if (list) {
+        const bool occ = !(t & 1) && c != 0u;
+        const uint32_t m = __ballot_sync(0xffffffffu, occ);
+        uint32_t at = 0;
+        if ((t & 31) == 0 && m) at = atomicAdd(n_list, static_cast<uint32_t>(__popc(m)));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (occ)
+            list[at + __popc(m & ((1u << (t & 31)) - 1u))] =
+                static_cast<uint32_t>(blk * kChunksPerSumBlock + (t >> 1));
+    }
     uint32_t tot;
     const uint32_t excl = block_exclusive_scan<kBmThreads>((t & 1) ? 0u : c, warp_tot, tot);
     if (!(t & 1)) chunk_off[blk * kChunksPerSumBlock + (t >> 1)] = excl;
