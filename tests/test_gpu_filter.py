@@ -226,3 +226,52 @@ def test_voxel_faces_stress_bit_exact(gm):
         obs = _run(gm, pts, T, ws)
         gm.sync()
         _assert_same(obs, ref)
+
+
+def test_batched_filter_many_waves_matches_filter_cloud(gm):
+    """40 tabletop frames: more than one L2-sized wave (16 tabletop frames), so
+    the batch alternates waves between its two streams and reuses each
+    stream's scratch slots.  Every job's S_W equals filter_cloud's bit for bit,
+    on two runs in a row and through a CUDA-graph replay."""
+    import torch
+    base = [synth.tabletop_workload(frame_seed=9_100_000 + f, n_agents=1, n_steps=1)
+            for f in range(4)]
+    g = np.random.Generator(np.random.PCG64(23))
+    frames = []
+    for i in range(40):
+        x = base[i % 4]["xyz"]
+        frames.append((x + g.normal(0.0, 1e-3, x.shape)).astype(np.float32))
+    T, ws = base[0]["T"], base[0]["workspace"]
+    clouds = [torch.from_numpy(f).cuda() for f in frames]
+    fb = gm.FilterBatch(clouds, T, ws, caps=[131072] * len(clouds))
+    ref = []
+    for c in clouds:
+        o = _run(gm, c.cpu().numpy(), T, ws, cap=131072)
+        gm.sync()
+        n = o.count()
+        ref.append({f: getattr(o, f)[:n].clone() for f in ("x", "y", "z", "keys", "counts",
+                                                            "rep_idx")})
+    def check():
+        for q, r in enumerate(ref):
+            n = fb.outs[q].count()
+            assert n == r["keys"].numel(), q
+            for f, t in r.items():
+                assert torch.equal(getattr(fb.outs[q], f)[:n], t), (q, f)
+    for _ in range(2):
+        fb.run()
+        gm.sync()
+        check()
+    for o in fb.outs:
+        o.counts.fill_(7)
+        o.x.fill_(-1.0)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        fb.run(stream=s)
+    graph.replay()
+    torch.cuda.synchronize()
+    gm.sync()
+    check()
+    # the first frame against the oracle as well
+    _assert_same(fb.outs[0], oracle.filter_cloud(frames[0], T, ws))

@@ -366,3 +366,68 @@ def test_four_term_server_plan_stream(gm):
     print(f"four-term server: {kept} requests kept the current plan; {agree} of 6 selections "
           f"agree with the oracle's chain")
     assert agree >= 5
+
+
+def _admission_case():
+    """A small request, then a large one (a 300k-point frame), then eight
+    small ones, all queued before the first tick."""
+    small = _requests(n=9, seed=71)
+    g = np.random.Generator(np.random.PCG64(72))
+    big = synth.tabletop_workload(seed=int(g.integers(1, 1 << 30)), n_points=300000, voxel=0.01,
+                                  n_agents=17, n_steps=60, spheres_at=0.3, sphere_seed=11,
+                                  scene_seed=99)
+    return [small[0], big] + small[1:]
+
+
+def _bytes_of(gm, w):
+    """Arena bytes the server gives one request (read from its free bytes)."""
+    srv = gm.Server(max_slots=2, max_agents=64, max_steps=200, obs_cap=32768,
+                    arena_bytes=64 << 20, chunk_steps=1, agents_per_item=8)
+    free0 = srv.stats()["arena_free_bytes"]
+    srv.submit(w["xyz"], w["T"], w["workspace"], w["agents"], w["params"])
+    srv.tick()
+    used = free0 - srv.stats()["arena_free_bytes"]
+    while srv.poll(1) is None:
+        srv.tick()
+    return used
+
+
+def test_first_fit_admission_with_aging_bound(gm):
+    """admit_bypass = k: queued requests that fit are admitted past an older
+    one that does not, but once that one has been overtaken k times nothing
+    later is admitted before it.  k = 0 is strict arrival order.  Results do
+    not depend on the order (bit for bit)."""
+    ws = _admission_case()
+    b_small, b_big = _bytes_of(gm, ws[0]), _bytes_of(gm, ws[1])
+    assert b_big >= b_small + 2 * _bytes_of(gm, ws[2])
+    arena = (b_big + 4095) // 4096 * 4096  # the large request fits only alone
+
+    def run(bypass):
+        srv = gm.Server(max_slots=8, max_agents=64, max_steps=200, obs_cap=32768,
+                        arena_bytes=arena, chunk_steps=16, agents_per_item=8,
+                        admit_bypass=bypass)
+        tickets = [srv.submit(w["xyz"], w["T"], w["workspace"], w["agents"], w["params"])
+                   for w in ws]
+        done = {}
+        for _ in range(100000):
+            if len(done) == len(tickets):
+                break
+            srv.tick()
+            for t in tickets:
+                if t not in done:
+                    r = srv.poll(t)
+                    if r is not None:
+                        done[t] = r
+        res = [done[t] for t in tickets]
+        overtook = sum(r["t_admit"] < res[1]["t_admit"] for r in res[2:])
+        return res, overtook
+
+    strict, n0 = run(0)
+    aged, n2 = run(2)
+    free, n64 = run(64)
+    gm.sync()  # no capacity or timeout flag from any of the runs
+    assert n0 == 0 and n2 == 2 and n64 > 2, (n0, n2, n64)
+    for a, b, c in zip(strict, aged, free):
+        assert a["best"] == b["best"] == c["best"]
+        assert np.array_equal(a["costs"], b["costs"]) and np.array_equal(a["costs"], c["costs"])
+        assert np.array_equal(a["best_traj"], b["best_traj"])
