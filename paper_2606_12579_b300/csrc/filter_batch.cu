@@ -37,7 +37,6 @@ namespace gmapp {
 namespace {
 
 constexpr int kPointsPerThread = 8;      // kf_keys / kf_count: points per thread per iteration
-constexpr int kPointItersPerThread = 4;  // kf_keys / kf_count: iterations per thread
 constexpr size_t kWaveL2Bytes = size_t(48) << 20;  // L2-resident scratch per wave
 
 // Division by an invariant divisor d by multiplication (T. Granlund and P. L.
@@ -72,7 +71,7 @@ struct FilterJob {
     uint32_t *chunk_list;  // occupied 32-word chunks (kf_sums appends, kf_emit visits);
                            // their number in counters[3]
     uint2 *pw;
-    int32_t pt_blk0, pt_nblk, sb_blk0, sb_nblk;
+    int32_t pt_blk0, pt_nblk, cp_blk0, cp_nblk, sb_blk0, sb_nblk;  // key, count, sums blocks
     EmitOut o;
     int32_t *n_out;
 };
@@ -252,12 +251,12 @@ __global__ void __launch_bounds__(kBmThreads) kf_emit(const FilterJob *J, int32_
 // Keys -> ranks (the word's rank and bits, pw, from L2) -> counts and
 // smallest indices, 8 consecutive keys per thread and iteration, runs of
 // equal ranks merged per thread.
-__global__ void __launch_bounds__(kThreads) kf_count(const FilterJob *J, const int32_t *pt_map,
+__global__ void __launch_bounds__(kThreads) kf_count(const FilterJob *J, const int32_t *cp_map,
                                                      int32_t blk0) {
     const int32_t gb = blockIdx.x + blk0;
-    const FilterJob &Q = J[pt_map[gb]];
+    const FilterJob &Q = J[cp_map[gb]];
     const int64_t n = Q.n_raw, n8 = n / kPointsPerThread;
-    const int64_t blk = gb - Q.pt_blk0, stride = static_cast<int64_t>(Q.pt_nblk) * kThreads;
+    const int64_t blk = gb - Q.cp_blk0, stride = static_cast<int64_t>(Q.cp_nblk) * kThreads;
     const uint2 *__restrict__ pw = Q.pw;
     uint32_t *counts = Q.o.counts, *rep = Q.o.rep;
     const int64_t cap = Q.o.cap;
@@ -293,10 +292,10 @@ using namespace gmapp;
 struct gmapp_filter_batch {
     gmapp_ctx *ctx = nullptr;
     FilterJob *d_jobs = nullptr;
-    int32_t *d_pt_map = nullptr, *d_sb_map = nullptr;
+    int32_t *d_pt_map = nullptr, *d_cp_map = nullptr, *d_sb_map = nullptr;
     void *d_ws = nullptr;
     // per wave: first block and block count of each launch
-    std::vector<int32_t> pt0, ptn, sb0, sbn, q0, q1;  // per wave
+    std::vector<int32_t> pt0, ptn, cp0, cpn, sb0, sbn, q0, q1;  // per wave
     int emit_grid = 0;
     cudaStream_t side = nullptr;  // odd waves (the caller's stream runs the even ones)
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -307,6 +306,7 @@ namespace {
 void release(gmapp_filter_batch *fb) {
     cudaFree(fb->d_jobs);
     cudaFree(fb->d_pt_map);
+    cudaFree(fb->d_cp_map);
     cudaFree(fb->d_sb_map);
     cudaFree(fb->d_ws);
     if (fb->fork) cudaEventDestroy(fb->fork);
@@ -357,7 +357,19 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
     const int n_slots = std::min(n_waves, 2) * W;
 
     std::vector<FilterJob> hj(n_jobs);
-    std::vector<int32_t> pt_map, sb_map;
+    std::vector<int32_t> pt_map, cp_map, sb_map;
+    // key and count passes: per wave, about one full wave of resident CTAs
+    // (the SM count times the CTAs an SM holds), shared by the wave's jobs
+    int keys_per_sm = 1, count_per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&keys_per_sm, kf_keys, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&count_per_sm, kf_count, kThreads, 0);
+    const int64_t keys_blocks = std::max(1, keys_per_sm) * static_cast<int64_t>(ctx->sm_count);
+    const int64_t count_blocks = std::max(1, count_per_sm) * static_cast<int64_t>(ctx->sm_count);
+    auto blocks_for = [&](int64_t n8, int64_t wave_blocks) {
+        const int64_t per_job = (wave_blocks + W - 1) / W;
+        return static_cast<int32_t>(std::max<int64_t>(
+            1, std::min<int64_t>(per_job, (n8 + kThreads - 1) / kThreads)));
+    };
     gmapp_filter_batch *fb = new gmapp_filter_batch();
     fb->ctx = ctx;
     fb->emit_grid = ctx->sm_count * 4;  // persistent over the wave's occupied chunks
@@ -382,16 +394,19 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
         D.dy = div_magic(D.fa.ny);
         const int64_t n8 = J.n_raw / kPointsPerThread;
         D.pt_blk0 = static_cast<int32_t>(pt_map.size());
-        D.pt_nblk = static_cast<int32_t>(std::max<int64_t>(
-            1, (n8 + kThreads * kPointItersPerThread - 1) / (kThreads * kPointItersPerThread)));
+        D.pt_nblk = blocks_for(n8, keys_blocks);
         for (int i = 0; i < D.pt_nblk; ++i) pt_map.push_back(q);
+        D.cp_blk0 = static_cast<int32_t>(cp_map.size());
+        D.cp_nblk = blocks_for(n8, count_blocks);
+        for (int i = 0; i < D.cp_nblk; ++i) cp_map.push_back(q);
         D.sb_blk0 = static_cast<int32_t>(sb_map.size());
         D.sb_nblk = static_cast<int32_t>(L.n_sblocks);
         for (int i = 0; i < D.sb_nblk; ++i) sb_map.push_back(q);
         D.o = EmitOut{J.out.keys, J.out.counts, J.out.rep_idx, J.out.x, J.out.y, J.out.z,
                       J.out.cap};
         D.n_out = J.out.n;
-        if (pt_map.size() > 0x7fffffffu || sb_map.size() > 0x7fffffffu) {
+        if (pt_map.size() > 0x7fffffffu || cp_map.size() > 0x7fffffffu ||
+            sb_map.size() > 0x7fffffffu) {
             delete fb;
             set_error("gmapp_filter_batch_create: too many blocks");
             return GMAPP_ERR_CAPACITY;
@@ -401,6 +416,8 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
         const int q0 = w * W, q1 = std::min(n_jobs, q0 + W) - 1;
         fb->pt0.push_back(hj[q0].pt_blk0);
         fb->ptn.push_back(hj[q1].pt_blk0 + hj[q1].pt_nblk - hj[q0].pt_blk0);
+        fb->cp0.push_back(hj[q0].cp_blk0);
+        fb->cpn.push_back(hj[q1].cp_blk0 + hj[q1].cp_nblk - hj[q0].cp_blk0);
         fb->q0.push_back(q0);
         fb->q1.push_back(q1 + 1);
         fb->sb0.push_back(hj[q0].sb_blk0);
@@ -413,6 +430,7 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
     if (e == cudaSuccess) e = cudaMemset(fb->d_ws, 0, ws_total);
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_jobs, sizeof(FilterJob) * n_jobs);
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_pt_map, sizeof(int32_t) * pt_map.size());
+    if (e == cudaSuccess) e = cudaMalloc(&fb->d_cp_map, sizeof(int32_t) * cp_map.size());
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_sb_map, sizeof(int32_t) * sb_map.size());
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fb->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fb->fork, cudaEventDisableTiming);
@@ -439,6 +457,9 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
     }
     if (e == cudaSuccess)
         e = cudaMemcpy(fb->d_pt_map, pt_map.data(), sizeof(int32_t) * pt_map.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(fb->d_cp_map, cp_map.data(), sizeof(int32_t) * cp_map.size(),
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(fb->d_sb_map, sb_map.data(), sizeof(int32_t) * sb_map.size(),
@@ -476,7 +497,7 @@ extern "C" gmapp_status filter_cloud_batch(gmapp_filter_batch *fb, gmapp_stream 
         kf_sums<<<fb->sbn[w], kBmThreads, 0, s>>>(fb->d_jobs, fb->d_sb_map, fb->sb0[w]);
         kf_emit<<<fb->emit_grid, kBmThreads, 0, s>>>(fb->d_jobs, fb->q0[w], fb->q1[w],
                                                    fb->ctx->d_err);
-        kf_count<<<fb->ptn[w], kThreads, 0, s>>>(fb->d_jobs, fb->d_pt_map, fb->pt0[w]);
+        kf_count<<<fb->cpn[w], kThreads, 0, s>>>(fb->d_jobs, fb->d_cp_map, fb->cp0[w]);
     }
     if (n_waves > 1) {
         GMAPP_CHECK_CUDA(cudaEventRecord(fb->join, fb->side));
