@@ -1136,15 +1136,21 @@ def bench_served(gm, args):
         return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "plans_per_s": len(lat) / t_span, "interactions_per_s": inter / t_span}
 
-    def run_served(culled, rate=1000.0, chunk=50, n=n_req):
+    def run_served(culled, rate=1000.0, chunk=50, n=n_req, plan_streams=0, alpha=0.95):
         """The first ``n`` requests of the stream, offered at ``rate``
         requests/s, through the continuously batched server (``chunk`` steps
         of every active plan per tick; first-fit admission, a queued request
-        overtaken at most 64 times)."""
+        overtaken at most 64 times).  With ``plan_streams`` > 0 the requests
+        are re-planning ticks of that many robots (request r belongs to
+        stream r mod plan_streams), scored by the paper's four-term cost and
+        selected against their stream's C_best with hysteresis ``alpha``."""
         arrivals = arrivals_1k * (1000.0 / rate)
         srv = gm.Server(max_slots=48, max_agents=1024, max_steps=300, obs_cap=32768,
                         arena_bytes=2 << 30, chunk_steps=chunk, agents_per_item=8, threads=256,
-                        culled=culled, admit_bypass=64)
+                        culled=culled, admit_bypass=64, four_term=plan_streams > 0,
+                        max_plan_streams=plan_streams)
+        c4 = dict(cost4=True, alpha=alpha) if plan_streams else {}
+        kept = 0
         for r in range(4):   # warm up (kernel loading, first admissions)
             t = srv.submit(frames[0], Ts[0], ws_grid, agents[int(na_choice[r])], prm)
             while srv.poll(t) is None:
@@ -1158,7 +1164,10 @@ def bench_served(gm, args):
             now = time.perf_counter() - t0
             while nxt < n and arrivals[nxt] <= now:
                 na = int(na_choice[nxt])
-                tk = srv.submit(frames[frame_of[nxt]], Ts[frame_of[nxt]], ws_grid, agents[na], prm)
+                if plan_streams:
+                    c4["plan_stream"] = nxt % plan_streams
+                tk = srv.submit(frames[frame_of[nxt]], Ts[frame_of[nxt]], ws_grid, agents[na], prm,
+                                **c4)
                 outstanding[tk] = (nxt, na)
                 nxt += 1
             if not outstanding:
@@ -1173,11 +1182,15 @@ def bench_served(gm, args):
                 r, na = outstanding.pop(tk)
                 lat.append(time.perf_counter() - t0 - arrivals[r])
                 inter += na * res["n_obs"] * prm.n_steps
+                kept += res["best"] < 0
                 srv.release(tk)
                 done += 1
         t_span = time.perf_counter() - t0
         del srv
-        return lat_stats(lat, t_span, inter)
+        out = lat_stats(lat, t_span, inter)
+        if plan_streams:
+            out.update(plan_streams=plan_streams, alpha=alpha, kept_current_plan=int(kept))
+        return out
 
     cur = torch.cuda.current_stream()
     dev_frame = torch.empty(200000, 3, device="cuda")
@@ -1227,8 +1240,11 @@ def bench_served(gm, args):
         return lat_stats(lat, t_span, inter)
 
     served, plain = run_served(False), run_plain(False)
-    culled = {}
+    # the re-planning form: 8 robots' plan streams, four-term cost, C_best
+    # per stream on the device (the first --serve-cull-seconds of the stream)
     n_cull = min(n_req, int(round(float(args.serve_cull_seconds) * 1000)))
+    replan = run_served(False, n=n_cull, plan_streams=8)
+    culled = {}
     for rate in (float(r) for r in str(args.serve_cull_rates).split(",")):
         s = run_served(True, rate, int(args.serve_cull_chunk), n=n_cull)
         p = run_plain(True, rate, n=n_cull)
@@ -1241,6 +1257,7 @@ def bench_served(gm, args):
             "offered_per_s": 1000.0, "served": served, "plain": plain,
             "p99_speedup": plain["p99_ms"] / served["p99_ms"],
             "plans_per_s_speedup": served["plans_per_s"] / plain["plans_per_s"],
+            "served_four_term_replanning": dict(replan, requests=n_cull),
             "admission": "first fit over the queue, a request overtaken at most 64 times",
             "culled": {"note": "every agent visits only the obstacles within its reach "
                                "(interactions/s still counts all pairs); the first "

@@ -618,7 +618,8 @@ typedef struct {
     gmapp_cost4 w4;           /* four-term weights (with out.cost_terms) */
     float alpha;              /* hysteresis of the four-term selection */
     float *c_best;            /* device float32 C_best of the query's plan (in/out; NaN = none),
-                                 or NULL (plain argmin) */
+                                 or NULL (plain argmin); the queries of one batch are scored
+                                 concurrently, so each needs its own word */
 } gmapp_query;
 
 typedef struct gmapp_batch gmapp_batch;
