@@ -70,6 +70,7 @@ struct FilterJob {
     uint32_t *bitmap, *chunk, *sums, *offsets, *counters, *keys;
     uint32_t *chunk_list;  // occupied 32-word chunks (kf_sums appends, kf_emit visits);
                            // their number in counters[3]
+    uint32_t n_chunks;     // chunks of the bitmap (the list's capacity)
     uint2 *pw;
     int32_t pt_blk0, pt_nblk, cp_blk0, cp_nblk, sb_blk0, sb_nblk;  // key, count, sums blocks
     EmitOut o;
@@ -199,6 +200,9 @@ __global__ void __launch_bounds__(kBmThreads) kf_emit(const FilterJob *J, int32_
             const FilterArgs A = Q.fa;
             const DivMagic dx = Q.dx, dy = Q.dy;
             const uint32_t c = Q.chunk_list[li];
+            // every rank, output slot and bitmap word below derives from c:
+            // the bounds-checked build checks it (warp-uniform: c is)
+            if (!bc_ok(c, Q.n_chunks, err)) continue;
             const uint32_t wv = c * kChunkWords + lane;
             const uint32_t w = Q.bitmap[wv];
             uint32_t base = 0;
@@ -451,6 +455,7 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
             D.counters = reinterpret_cast<uint32_t *>(base + L.off_counters);
             D.keys = reinterpret_cast<uint32_t *>(base + L.off_keys);
             D.chunk_list = reinterpret_cast<uint32_t *>(base + align_up(L.total, 256));
+            D.n_chunks = static_cast<uint32_t>(L.n_words / kChunkWords);
         }
         e = cudaMemcpy(fb->d_jobs, hj.data(), sizeof(FilterJob) * n_jobs,
                        cudaMemcpyHostToDevice);

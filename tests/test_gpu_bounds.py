@@ -2,8 +2,9 @@
 GMAPP_BOUNDS_CHECK=1): its index checks set GMAPP_DEVERR_BOUNDS in the
 device error word instead of faulting.  The path runs here on small cases
 (N_O <= 64 obstacles, N_a <= 4 agents) compared with the oracle and on the
-full tabletop frame through every rollout form, and the error word must stay
-clean.  The check runs in a child process, which loads the checked library
+full tabletop frame through every rollout form, the stream filter over
+several waves, a four-term batch and four-term served requests; the error
+word must stay clean.  The check runs in a child process, which loads the checked library
 in place of the normal one."""
 
 import os
@@ -54,6 +55,32 @@ gm.rollout_ensemble(obs, dev, 16, t["params"], tuning=(5, 6, 256, 1), n_proj=16)
 b = gm.Batch([{"xyz": cloud, "T": t["T"], "ws": t["workspace"], "agents": dev,
                "prm": t["params"], "obs_cap": 80000}])
 b.run()
+gm.sync()
+
+# the stream filter over several waves, a four-term batch and a four-term
+# served request
+frames = [torch.from_numpy(synth.tabletop_workload(frame_seed=300 + i, n_agents=1,
+                                                   n_steps=1)["xyz"]).cuda() for i in range(20)]
+fb = gm.FilterBatch(frames, t["T"], t["workspace"], caps=[131072] * 20)
+fb.run()
+fb.run()
+gm.sync()
+p4 = dataclasses.replace(t["params"], cost_radius=0.05, a_max=50.0)
+cb = torch.full((1,), float("nan"), device="cuda")
+b4 = gm.Batch([{"xyz": cloud, "T": t["T"], "ws": t["workspace"], "agents": dev, "prm": p4,
+                "obs_cap": 80000, "cost4": True, "alpha": 0.95, "c_best": cb}])
+b4.run()
+b4.run()
+gm.sync()
+s = synth.tabletop_workload(n_agents=20, n_steps=60, n_points=30000, voxel=0.01)
+srv = gm.Server(max_slots=4, max_agents=64, max_steps=100, obs_cap=16384, arena_bytes=1 << 28,
+                chunk_steps=16, agents_per_item=8, four_term=True, max_plan_streams=1,
+                admit_bypass=2)
+tk = [srv.submit(s["xyz"], s["T"], s["workspace"], s["agents"],
+                 dataclasses.replace(s["params"], cost_radius=0.05, a_max=50.0), cost4=True,
+                 alpha=0.95, plan_stream=0) for _ in range(3)]
+while any(srv.poll(x) is None for x in tk):
+    srv.tick()
 gm.sync()
 print("bounds-checked build clean")
 '''
