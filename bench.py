@@ -470,7 +470,7 @@ def run_ours(args, ws, rank, local):
                                   if name != "filter_batched"}
             fs = result["patterns"]["filter_stream"]
         else:
-            fs = bench_filter_stream(gm, args, with_fused=False)
+            fs = bench_filter_stream(gm, args, with_fused=False, batched_only=True)
         result["roofline_filter"] = _filter_roofline(fs)
         print(json.dumps(result), flush=True)
     if ws > 1:
