@@ -48,6 +48,7 @@ APF_FLOPS_PER_INTERACTION = 19
 # projected-current MFI pair: 3 sub, 5 for |d|^2, rsqrt, 2 for s = |d|^2 r - R,
 # rcp, 5 for t = d . v, 3 mul for a = w r^2 t, 4 accumulating FMAs (8)
 PROJ_FLOPS_PER_INTERACTION = 28
+ADJOINT_FLOPS_PER_INTERACTION = 26  # recompute 13 + grad W: 3 mul, 3 FMA, d(1/s) ~ 7
 FP32_LANES_PER_SM = 128
 OBS_CAP = 131072
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "rollout_tabletop_256x500.md")
@@ -802,6 +803,12 @@ def bench_adjoint(gm, args, reps=3):
             "tuning": list(tuning),
             "forward_ms": 1e3 * t_fwd, "adjoint_ms": 1e3 * t_adj, "plain_forward_ms": 1e3 * t_plain,
             "forward_equivalent_interactions_per_s": inter / (t_fwd + t_adj),
+            # raw flops: the forward's 13 per pair, and the adjoint's recompute
+            # with the gradient of W (13 + 3 mul + 3 accumulating FMAs + the
+            # derivative of 1/s, about 26 per pair)
+            "adjoint_TFLOP_per_s": inter * ADJOINT_FLOPS_PER_INTERACTION / t_adj / 1e12,
+            "forward_plus_adjoint_TFLOP_per_s":
+                inter * (FLOPS_PER_INTERACTION + ADJOINT_FLOPS_PER_INTERACTION) / (t_fwd + t_adj) / 1e12,
             "gradient_cost_over_plain_forward": (t_fwd + t_adj) / t_plain,
             "plain_forward_fp32": {"achieved_TFLOP_per_s": fwd_tflops, "peak_TFLOP_per_s": peak,
                                    "frac": fwd_tflops / peak,
