@@ -327,7 +327,16 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
         return GMAPP_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    size_t slot_bytes = 256, touched = 1;
+    size_t touched = 1;
+    // one layout for every slot, sized by the largest cloud and the largest
+    // grid of the batch: a slot serves different jobs wave after wave, and
+    // each region (bitmap, ranks, counters, keys) must sit at the same place
+    // for all of them -- the bitmap stays zero beyond what a job sets and
+    // clears, and no job's keys or ranks land where a later one's bitmap or
+    // counters are
+    int64_t max_raw = 0;
+    int q_cells = 0;
+    uint64_t max_cells = 0;
     for (int q = 0; q < n_jobs; ++q) {
         const gmapp_cloud_job &J = jobs[q];
         if (!valid_workspace(&J.ws) || J.ws.min_pts != 1 || J.n_raw < 0 ||
@@ -348,12 +357,20 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
                 return GMAPP_ERR_INVALID_ARG;
             }
         const Layout L = layout(J.n_raw, &J.ws);
-        slot_bytes = std::max(slot_bytes, align_up(L.total, 256) +
-                                              align_up(static_cast<size_t>(L.n_words / kChunkWords) * 4, 256));
+        const uint64_t cells = static_cast<uint64_t>(J.ws.dims[0]) * J.ws.dims[1] * J.ws.dims[2];
+        if (cells > max_cells) {
+            max_cells = cells;
+            q_cells = q;
+        }
+        max_raw = std::max<int64_t>(max_raw, J.n_raw);
         // scratch a wave keeps in L2: keys, bitmap, the occupied words' ranks
         touched = std::max(touched, static_cast<size_t>(J.n_raw) * 4 +
                                         static_cast<size_t>(L.n_words) * 5);
     }
+    const Layout SL = layout(max_raw, &jobs[q_cells].ws);  // the slots' common layout
+    const size_t list_off = align_up(SL.total, 256);
+    const size_t slot_bytes =
+        list_off + align_up(static_cast<size_t>(SL.n_words / kChunkWords) * 4, 256);
     const int W_max = static_cast<int>(std::max<size_t>(
         1, std::min<size_t>(n_jobs, kWaveL2Bytes / touched)));
     const int n_waves = (n_jobs + W_max - 1) / W_max;
@@ -447,14 +464,14 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
             const Layout L = layout(jobs[q].n_raw, &jobs[q].ws);
             char *base = ws + static_cast<size_t>(slot) * slot_bytes;
             FilterJob &D = hj[q];
-            D.bitmap = reinterpret_cast<uint32_t *>(base + L.off_bitmap);
-            D.pw = reinterpret_cast<uint2 *>(base + L.off_pw);
-            D.chunk = reinterpret_cast<uint32_t *>(base + L.off_chunk);
-            D.sums = reinterpret_cast<uint32_t *>(base + L.off_sums);
-            D.offsets = reinterpret_cast<uint32_t *>(base + L.off_offsets);
-            D.counters = reinterpret_cast<uint32_t *>(base + L.off_counters);
-            D.keys = reinterpret_cast<uint32_t *>(base + L.off_keys);
-            D.chunk_list = reinterpret_cast<uint32_t *>(base + align_up(L.total, 256));
+            D.bitmap = reinterpret_cast<uint32_t *>(base + SL.off_bitmap);
+            D.pw = reinterpret_cast<uint2 *>(base + SL.off_pw);
+            D.chunk = reinterpret_cast<uint32_t *>(base + SL.off_chunk);
+            D.sums = reinterpret_cast<uint32_t *>(base + SL.off_sums);
+            D.offsets = reinterpret_cast<uint32_t *>(base + SL.off_offsets);
+            D.counters = reinterpret_cast<uint32_t *>(base + SL.off_counters);
+            D.keys = reinterpret_cast<uint32_t *>(base + SL.off_keys);
+            D.chunk_list = reinterpret_cast<uint32_t *>(base + list_off);
             D.n_chunks = static_cast<uint32_t>(L.n_words / kChunkWords);
         }
         e = cudaMemcpy(fb->d_jobs, hj.data(), sizeof(FilterJob) * n_jobs,

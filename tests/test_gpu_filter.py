@@ -275,3 +275,49 @@ def test_batched_filter_many_waves_matches_filter_cloud(gm):
     check()
     # the first frame against the oracle as well
     _assert_same(fb.outs[0], oracle.filter_cloud(frames[0], T, ws))
+
+
+def test_batched_filter_mixed_jobs_reuse_slots(gm):
+    """45 jobs of four kinds in turn (a tabletop frame on its 200x200x160 grid,
+    a sphere cloud on its 100x100x80 grid, a ragged 13-point cloud, an empty
+    one): three waves, so the third reuses the first wave's scratch slots
+    with jobs of other sizes and grids.  Every job equals filter_cloud bit for
+    bit on two runs in a row."""
+    import torch
+    tab = synth.tabletop_workload(n_agents=1, n_steps=1)
+    sph = synth.sphere_workload()
+    g = np.random.Generator(np.random.PCG64(29))
+    kinds = [(tab["xyz"], tab["T"], tab["workspace"]), (sph["xyz"], sph["T"], sph["workspace"]),
+             (g.uniform(-0.05, 1.05, (13, 3)).astype(np.float32), tab["T"], tab["workspace"]),
+             (np.zeros((0, 3), np.float32), tab["T"], tab["workspace"])]
+    jobs = []
+    for q in range(45):
+        x, T, ws = kinds[q % 4]
+        if x.shape[0] > 100:
+            x = (x + g.normal(0.0, 1e-3, x.shape)).astype(np.float32)
+        jobs.append((x, T, ws))
+    clouds = [torch.from_numpy(np.ascontiguousarray(x)).cuda() if x.shape[0] else
+              torch.empty(0, 3, device="cuda") for x, _, _ in jobs]
+    caps = [max(4, (x.shape[0] + 3) // 4 * 4) for x, _, _ in jobs]
+    fb = gm.FilterBatch(clouds, [j[1] for j in jobs], [j[2] for j in jobs], caps=caps)
+    refs = []
+    for (x, T, ws), cap in zip(jobs, caps):
+        if x.shape[0]:
+            o = _run(gm, x, T, ws, cap=cap)
+            gm.sync()
+            n = o.count()
+            refs.append({f: getattr(o, f)[:n].clone() for f in ("x", "y", "z", "keys", "counts",
+                                                                "rep_idx")})
+        else:
+            refs.append(None)
+    for _ in range(2):
+        fb.run()
+        gm.sync()
+        for q, r in enumerate(refs):
+            n = fb.outs[q].count()
+            if r is None:
+                assert n == 0, q
+                continue
+            assert n == r["keys"].numel(), q
+            for f, t in r.items():
+                assert torch.equal(getattr(fb.outs[q], f)[:n], t), (q, f)
