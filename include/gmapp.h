@@ -702,8 +702,9 @@ typedef struct {
     int32_t four_term;       /* 1: the chunk kernel also computes the clearance and the
                                 sums of the paper's four-term cost (Eq. cost_function), so
                                 requests may ask for cost_mode 1 (slower pair loop: the
-                                exact distance of every pair); 0: plain cost only.  Not with
-                                culled = 1 */
+                                exact distance of every pair); 0: plain cost only.  With
+                                culled = 1 or 2 the obstacle term uses the culled clearance
+                                (exact within an agent's reach r_d + r_a + r_O) */
     int32_t max_plan_streams; /* with four_term: number of request streams whose current plan
                                 cost C_best the server keeps on the device (Sec. IV-A
                                 "Selection Mechanism"); 0 = none */

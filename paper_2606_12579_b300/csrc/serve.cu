@@ -347,15 +347,61 @@ __global__ void __launch_bounds__(kServeCullThreads) ks_chunk_culled(const Chunk
             t[1] = p[1];
             t[2] = p[2];
         }
+        // four-term cost sums (cost_mode 1), kept by thread 0 and carried
+        // between chunks in S.cacc; the clearance is the culled one (the
+        // nearest obstacle within the agent's reach)
+        const bool four = S.cost_terms != nullptr;  // uniform per item
+        float cv[kCostRows];
+#pragma unroll
+        for (int r = 0; r < kCostRows; ++r)
+            cv[r] = four && tid == 0 && item.k0 > 0 ? S.cacc[r * n + i] : 0.0f;
         for (int k = item.k0; k < item.k1; ++k) {
             float W, md2;
-            culled_terms<NT, false>(p, reach, G2, R, S.eps, S.grid, S.ox, S.oy, S.oz, tid, W,
-                                    md2);
-            culled_reduce<NT, false>(W, md2, s_w, s_m);
+            if (four) {
+                culled_terms<NT, true>(p, reach, G2, R, S.eps, S.grid, S.ox, S.oy, S.oz, tid, W,
+                                       md2);
+                culled_reduce<NT, true>(W, md2, s_w, s_m);
+            } else {
+                culled_terms<NT, false>(p, reach, G2, R, S.eps, S.grid, S.ox, S.oy, S.oz, tid, W,
+                                        md2);
+                culled_reduce<NT, false>(W, md2, s_w, s_m);
+            }
             if (tid == 0) {
-                float g[3], kf, m;
-                agent_step<false>(p, v, cc, k_r, k_a, R, goal, h, S.dt, S.rho, S.damping,
-                                  S.clear_margin, S.clear_beta, W, md2, L, pen, minc, m, g, kf);
+                float g[3], kf, m, F[3];
+                if (four) {
+                    const float vprev[3] = {v[0], v[1], v[2]};
+                    const float gx = p[0] - goal[0], gy = p[1] - goal[1], gz = p[2] - goal[2];
+                    const float dg = sqrtf(fmaf(gz, gz, fmaf(gy, gy, gx * gx)));
+                    cv[0] += fminf(dg, S.cost_radius);
+                    if (k == 0) cv[4] = dg;
+                    if (k == N - 1) cv[2] = L;  // before the last segment
+                    agent_step<true>(p, v, cc, k_r, k_a, R, goal, h, S.dt, S.rho, S.damping,
+                                     S.clear_margin, S.clear_beta, W, md2, L, pen, minc, m, g, kf,
+                                     F);
+                    float fr[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) fr[d] = kf * g[d];
+                    cv[1] += fmaxf(S.cost_radius - m, 0.0f);
+                    if (k >= 2 && k <= N - 2) {
+                        float sj = 0.0f;
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            const float dF = fmaf(-k_a * S.dt, vprev[d],
+                                                  fmaf(-S.damping * h, cv[5 + d], fr[d] - cv[8 + d]));
+                            sj = fmaf(dF, dF, sj);
+                        }
+                        cv[3] += sj;
+                    }
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        cv[5 + d] = F[d];
+                        cv[8 + d] = fr[d];
+                    }
+                } else {
+                    agent_step<false>(p, v, cc, k_r, k_a, R, goal, h, S.dt, S.rho, S.damping,
+                                      S.clear_margin, S.clear_beta, W, md2, L, pen, minc, m, g,
+                                      kf);
+                }
                 s_p[0] = p[0];
                 s_p[1] = p[1];
                 s_p[2] = p[2];
@@ -377,12 +423,24 @@ __global__ void __launch_bounds__(kServeCullThreads) ks_chunk_culled(const Chunk
                 S.sv[d * n + i] = v[d];
             }
             S.sL[i] = L;
+            if (four) {
+#pragma unroll
+                for (int r = 0; r < kCostRows; ++r) S.cacc[r * n + i] = cv[r];
+            }
             if (item.k1 == N) {
                 for (int d = 0; d < 3; ++d) {
                     S.p_final[d * n + i] = p[d];
                     S.v_final[d * n + i] = v[d];
                 }
                 S.path_len[i] = L;
+                if (four) {
+                    const float rc = S.cost_radius, dh = S.dt * h;
+                    S.cost_terms[i] = cv[0] / rc;
+                    S.cost_terms[n + i] = cv[1] / rc;
+                    S.cost_terms[2 * n + i] = cv[2];
+                    S.cost_terms[3 * n + i] = dh * dh * cv[3];
+                    S.cost_terms[4 * n + i] = cv[4];
+                }
             }
         }
     }
@@ -681,7 +739,7 @@ extern "C" gmapp_status gmapp_server_create(gmapp_ctx *ctx, const gmapp_server_c
         cfg->chunk_steps < 1 || cfg->obs_cap < 4 || cfg->obs_cap % 4 ||
         cfg->max_agents < 1 || cfg->max_steps < 1 || cfg->culled < 0 || cfg->culled > 2 ||
         cfg->admit_bypass < 0 || cfg->four_term < 0 || cfg->four_term > 1 ||
-        cfg->max_plan_streams < 0 || (cfg->four_term && cfg->culled == 1) ||
+        cfg->max_plan_streams < 0 ||
         (cfg->max_plan_streams > 0 && !cfg->four_term)) {
         set_error("gmapp_server_create: invalid configuration");
         return GMAPP_ERR_INVALID_ARG;

@@ -270,10 +270,10 @@ def _four_term_requests():
     return ws, kinds
 
 
-def _serve4(gm, ws, kinds, alpha, one_at_a_time=False, bypass=4):
+def _serve4(gm, ws, kinds, alpha, one_at_a_time=False, bypass=4, culled=False):
     srv = gm.Server(max_slots=8, max_agents=64, max_steps=200, obs_cap=16384,
                     arena_bytes=1 << 28, chunk_steps=16, agents_per_item=8,
-                    four_term=True, max_plan_streams=2, admit_bypass=bypass)
+                    four_term=True, max_plan_streams=2, admit_bypass=bypass, culled=culled)
     out, max_active = [], 0
     tickets = []
     for r, c4, ps in kinds:
@@ -301,7 +301,8 @@ def _serve4(gm, ws, kinds, alpha, one_at_a_time=False, bypass=4):
     return [done[t] for t in tickets], max_active
 
 
-def test_four_term_server_plan_stream(gm):
+@pytest.mark.parametrize("culled", [False, True, "blocks"], ids=["all_pairs", "grid", "blocks"])
+def test_four_term_server_plan_stream(gm, culled):
     """The paper's four-term cost (Eq. cost_function) and the selection
     against the current plan (i* = argmin {C_i < alpha C_best}) in the served
     loop.  A plan stream of five requests shares one device-resident C_best,
@@ -311,14 +312,17 @@ def test_four_term_server_plan_stream(gm):
     with rollout_agents + score_and_select4 on the same query with its own
     C_best chain; the selection follows alpha C_best on the server's costs;
     and the costs and selections agree with the oracle's four_term_costs and
-    select on the oracle's own chain."""
+    select on the oracle's own chain.  The culled servers (voxel grid, obstacle
+    blocks) use the culled clearance, which equals the exact one wherever it
+    counts here: the cost radius (5 cm) does not exceed the detection radius,
+    so obstacles beyond an agent's reach add nothing to the obstacle term."""
     import math
     import torch
     alpha = 0.95
     ws, kinds = _four_term_requests()
-    mixed, max_active = _serve4(gm, ws, kinds, alpha)
+    mixed, max_active = _serve4(gm, ws, kinds, alpha, culled=culled)
     assert max_active >= 2
-    alone, _ = _serve4(gm, ws, kinds, alpha, one_at_a_time=True, bypass=0)
+    alone, _ = _serve4(gm, ws, kinds, alpha, one_at_a_time=True, bypass=0, culled=culled)
     for a, b in zip(alone, mixed):
         assert a["best"] == b["best"]
         assert np.array_equal(a["costs"].view(np.uint32), b["costs"].view(np.uint32))
