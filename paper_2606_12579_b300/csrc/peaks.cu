@@ -223,7 +223,7 @@ extern "C" int gmapp_measure_peaks(int32_t reps, gmapp_peaks *out) {
     }
     // iteration counts: a few milliseconds per probe on a 148-SM part
     const int it_fma = 1 << 16, it_mufu = 1 << 13, it_mix = 1 << 14;
-    double t2, t1, tm, tx, mhz2, mhz1, mhzm, mhzx;
+    double t2 = 0, t1 = 0, tm = 0, tx = 0, mhz2 = 0, mhz1 = 0, mhzm = 0, mhzx = 0;
     gmapp_status st = time_probe(k_probe_ffma2, grid, it_fma, reps, sink, clk, &t2, &mhz2);
     if (st == GMAPP_OK) st = time_probe(k_probe_ffma, grid, it_fma / 2, reps, sink, clk, &t1, &mhz1);
     if (st == GMAPP_OK) st = time_probe(k_probe_mufu, grid, it_mufu, reps, sink, clk, &tm, &mhzm);
