@@ -644,7 +644,7 @@ def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8, wit
     res["batched_graph"]["frames_per_batch"] = per
     res["n_frames"] = n_filters
     pick = "batched_graph" if bestg < best else "batched"
-    res["stream"] = dict(res[pick], kernel="kf_keys/kf_sums/kf_emit/kf_count", mode=pick)
+    res["stream"] = dict(res[pick], kernel="kf_points/kf_sums/kf_emit", mode=pick)
     del graph
     if batched_only:
         return res

@@ -173,11 +173,12 @@ gmapp_status filter_cloud_noalloc(const float *xyz, int64_t n_raw, const float T
  * clears the flag first.  Allocates nothing. */
 gmapp_status filter_cloud_noalloc_status(gmapp_stream stream);
 
-/* Batched filter: many clouds (a stream of frames, or several sensors) through
- * one sequence of four launches (Sec. IV-B, Sec. V-A, as filter_cloud).  The
- * jobs are fixed at creation (their device pointers are kept); each run
- * filters every job's cloud into its obstacle buffers with results
- * bit-identical to filter_cloud on the same cloud. */
+/* Batched filter: many clouds (a stream of frames, or several sensors) in
+ * waves of jobs whose scratch fits in L2, three launches per wave
+ * (Sec. IV-B, Sec. V-A, as filter_cloud).  The jobs are fixed at creation
+ * (their device pointers are kept); each run filters every job's cloud into
+ * its obstacle buffers with results bit-identical to filter_cloud on the
+ * same cloud. */
 typedef struct {
     const float *xyz;     /* device, n_raw x 3 float32 AoS, 16-byte aligned */
     int64_t n_raw;        /* >= 0 points */
@@ -190,13 +191,17 @@ typedef struct gmapp_filter_batch gmapp_filter_batch;
 
 /* Checks every job (GMAPP_ERR_INVALID_ARG names the first bad one), keeps the
  * job table on the device and allocates the jobs' scratch once (the library
- * owns it; freed by gmapp_filter_batch_destroy).  Synchronous. */
+ * owns it; freed by gmapp_filter_batch_destroy).  Scratch: two sets of wave
+ * slots, each slot 8 bytes per cell of the largest grid (a point count and a
+ * smallest index per cell) plus the bitmap (about 51 MB for a 200x200x160
+ * grid).  Synchronous. */
 gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cloud_job *jobs,
                                        int32_t n_jobs, gmapp_filter_batch **out);
 void gmapp_filter_batch_destroy(gmapp_filter_batch *fb);
 
-/* Filters every job's cloud: four launches on `stream` whatever the number of
- * jobs (graph-capturable; allocates nothing).  Output overflow of a job sets
+/* Filters every job's cloud: three launches per wave, the waves alternating
+ * between `stream` and a second stream of the batch that joins `stream` at
+ * the end (graph-capturable; allocates nothing).  Output overflow of a job sets
  * GMAPP_DEVERR_CAPACITY and its out.n > out.cap. */
 gmapp_status filter_cloud_batch(gmapp_filter_batch *fb, gmapp_stream stream);
 

@@ -2,29 +2,36 @@
 // clouds at once (a stream of depth frames, or several sensors).
 //
 // A single frame is a few MB, far less than a launch needs to approach HBM
-// bandwidth, and a whole stream's scratch (key per point, bitmap over the
-// grid) is far larger than L2.  So the jobs are filtered in WAVES whose
-// scratch fits in L2 (at most 48 MB of keys and bitmap words: 16 tabletop
-// frames), each wave through four launches, and consecutive waves alternate
-// between the caller's stream and a second stream of the batch, so the
-// passes of one wave overlap those of the next.  The two streams each own
-// one set of scratch slots, reused wave after wave.
+// bandwidth, and a whole stream's scratch is far larger than L2.  So the
+// jobs are filtered in WAVES whose touched scratch fits in L2 (at most 48 MB:
+// about 15 tabletop frames), each wave through three launches, and
+// consecutive waves alternate between the caller's stream and a second
+// stream of the batch, so the passes of one wave overlap those of the next.
+// The two streams each own one set of scratch slots, reused wave after wave.
 //
-//   kf_keys   8 points per thread and iteration (six 16-byte streaming
-//             loads in flight): key per point + bitmap bits
+// Each slot holds, besides the bitmap over the grid, one 8-byte record per
+// grid cell (point count, complement of the smallest point index).  The
+// records start at zero and the emit pass puts every record it reads back
+// to zero, so no pass clears them and only occupied cells are ever touched.
+//
+//   kf_points 8 points per thread and iteration (six 16-byte streaming
+//             loads in flight): key per point, bitmap bits, and per run of
+//             equal keys one reduction into the cell's count and one into
+//             its smallest index (reductions return nothing: the thread
+//             never waits on them)
 //   kf_sums   per-block (and per-chunk) popcounts; each job's last block
 //             scans its block sums; the occupied 32-word chunks are appended
 //             to the job's chunk list
 //   kf_emit   persistent over the wave's occupied chunks (empty ones cost
 //             nothing): ranks of a chunk's words (warp scan), its set bits
 //             compacted in shared memory, then written 32 obstacles at a
-//             time (coalesced: key, count 0, index ~0, centre); publishes
-//             each job's N_O and clears the bitmap words behind it
-//   kf_count  8 keys per thread and iteration: per-voxel point counts and
-//             smallest point index
+//             time (coalesced: key, count, smallest index, centre, the
+//             records read and cleared); publishes each job's N_O and
+//             clears the bitmap words behind it
 //
 // Every job's S_W is bit-identical to filter_cloud on the same cloud (same
-// key and centre arithmetic, same ranks).
+// key and centre arithmetic, same ranks; a count is a sum and the smallest
+// index a minimum, whatever the order of the reductions).
 #include <math.h>
 
 #include <algorithm>
@@ -36,7 +43,7 @@
 namespace gmapp {
 namespace {
 
-constexpr int kPointsPerThread = 8;      // kf_keys / kf_count: points per thread per iteration
+constexpr int kPointsPerThread = 8;      // kf_points: points per thread per iteration
 constexpr size_t kWaveL2Bytes = size_t(48) << 20;  // L2-resident scratch per wave
 
 // Division by an invariant divisor d by multiplication (T. Granlund and P. L.
@@ -67,12 +74,12 @@ struct FilterJob {
     int64_t n_raw;
     FilterArgs fa;
     DivMagic dx, dy;  // division by dims_x, dims_y (key -> cell coordinates)
-    uint32_t *bitmap, *chunk, *sums, *offsets, *counters, *keys;
+    uint32_t *bitmap, *chunk, *sums, *offsets, *counters;
     uint32_t *chunk_list;  // occupied 32-word chunks (kf_sums appends, kf_emit visits);
                            // their number in counters[3]
     uint32_t n_chunks;     // chunks of the bitmap (the list's capacity)
-    uint2 *pw;
-    int32_t pt_blk0, pt_nblk, cp_blk0, cp_nblk, sb_blk0, sb_nblk;  // key, count, sums blocks
+    uint2 *rec;            // per grid cell: (points, ~smallest point index); zero when unused
+    int32_t pt_blk0, pt_nblk, sb_blk0, sb_nblk;  // point-pass and sums blocks
     EmitOut o;
     int32_t *n_out;
 };
@@ -98,55 +105,134 @@ __device__ __forceinline__ uint32_t key_of(float x, float y, float z, const Filt
     return (idx[2] * A.ny + idx[1]) * A.nx + idx[0];
 }
 
-// Points -> keys: 8 consecutive points per thread and iteration (six
-// 16-byte streaming loads in flight), key per point stored, bitmap bits
-// merged per thread.
-__global__ void __launch_bounds__(kThreads) kf_keys(const FilterJob *J, const int32_t *pt_map,
-                                                    int32_t blk0) {
+// Reductions into global memory that return nothing (the issuing thread
+// never waits for them).
+__device__ __forceinline__ void red_add(uint32_t *p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_max(uint32_t *p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.max.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// BitMerge with a reduction: bits of consecutive points in one 32-cell word
+// OR-ed into the bitmap at once.
+struct BitMergeRed {
+    uint32_t word = kInvalid, bits = 0;
+    __device__ __forceinline__ void add(uint32_t key, uint32_t *bitmap) {
+        if (key == kInvalid) return;
+        const uint32_t w = key >> 5, b = 1u << (key & 31);
+        if (w == word) {
+            bits |= b;
+            return;
+        }
+        flush(bitmap);
+        word = w;
+        bits = b;
+    }
+    __device__ __forceinline__ void flush(uint32_t *bitmap) {
+        if (word != kInvalid) red_or(&bitmap[word], bits);
+        word = kInvalid;
+    }
+};
+
+// Runs of equal keys among one thread's consecutive points: one reduction
+// into the cell's count (the run's length) and one into its smallest index
+// (the run's first point: a thread visits its points in ascending order),
+// the index stored complemented so that zero means "none" and the largest
+// complement is the smallest index.
+struct CellMerge {
+    uint32_t key = kInvalid, n = 0, first = 0;
+    __device__ __forceinline__ void add(uint32_t k, uint32_t idx, uint2 *rec) {
+        if (k == kInvalid) return;
+        if (k == key) {
+            ++n;
+            return;
+        }
+        flush(rec);
+        key = k;
+        n = 1;
+        first = idx;
+    }
+    __device__ __forceinline__ void flush(uint2 *rec) {
+        if (key == kInvalid) return;
+        red_add(&rec[key].x, n);
+        red_max(&rec[key].y, ~first);
+        key = kInvalid;
+    }
+};
+
+// Points -> keys -> bitmap bits and cell records: 8 consecutive points per
+// thread and iteration, bits merged per thread by word, records by run of
+// equal keys.  A warp's 256 points (3 KB) come in as six coalesced 16-byte
+// loads per lane (512 contiguous bytes per instruction) and are handed to
+// their threads through the warp's tile in shared memory.
+__global__ void __launch_bounds__(kThreads, 4) kf_points(const FilterJob *J, const int32_t *pt_map,
+                                                      int32_t blk0) {
+    __shared__ float4 tile[kThreads / 32][6 * 32];
+    const int lane = threadIdx.x & 31;
+    float4 *tw = tile[threadIdx.x >> 5];
     const int32_t gb = blockIdx.x + blk0;
     const FilterJob &Q = J[pt_map[gb]];
     const FilterArgs A = Q.fa;
     const int64_t n = Q.n_raw, n8 = n / kPointsPerThread;
     const int64_t blk = gb - Q.pt_blk0, stride = static_cast<int64_t>(Q.pt_nblk) * kThreads;
     const float inv = __frcp_rn(A.voxel);
-    uint32_t *__restrict__ keys = Q.keys;
+    // the job's pointers in registers: the reductions below are memory
+    // clobbers, after which fields read through Q would be loaded again
     uint32_t *__restrict__ bitmap = Q.bitmap;
+    uint2 *__restrict__ rec = Q.rec;
+    const float *__restrict__ xyz = Q.xyz;
     const int64_t cells = static_cast<int64_t>(A.nx) * A.ny * A.nz;
     auto chk = [&](uint32_t k) { return k == kInvalid || bc_ok(k, cells, A.err) ? k : kInvalid; };
     if (blk == 0 && threadIdx.x == 0) Q.counters[3] = 0;  // kf_sums refills the chunk list
-    for (int64_t g = blk * kThreads + threadIdx.x; g < n8; g += stride) {
-        const float4 *src = reinterpret_cast<const float4 *>(Q.xyz) + 6 * g;
-        const float4 a0 = __ldcs(src), a1 = __ldcs(src + 1), a2 = __ldcs(src + 2);
-        const float4 a3 = __ldcs(src + 3), a4 = __ldcs(src + 4), a5 = __ldcs(src + 5);
-        uint4 k, l;
-        k.x = chk(key_of(a0.x, a0.y, a0.z, A, inv));
-        k.y = chk(key_of(a0.w, a1.x, a1.y, A, inv));
-        k.z = chk(key_of(a1.z, a1.w, a2.x, A, inv));
-        k.w = chk(key_of(a2.y, a2.z, a2.w, A, inv));
-        l.x = chk(key_of(a3.x, a3.y, a3.z, A, inv));
-        l.y = chk(key_of(a3.w, a4.x, a4.y, A, inv));
-        l.z = chk(key_of(a4.z, a4.w, a5.x, A, inv));
-        l.w = chk(key_of(a5.y, a5.z, a5.w, A, inv));
-        uint4 *dst = reinterpret_cast<uint4 *>(keys + kPointsPerThread * g);
-        dst[0] = k;
-        dst[1] = l;
-        BitMerge m;
-        m.add(k.x, bitmap);
-        m.add(k.y, bitmap);
-        m.add(k.z, bitmap);
-        m.add(k.w, bitmap);
-        m.add(l.x, bitmap);
-        m.add(l.y, bitmap);
-        m.add(l.z, bitmap);
-        m.add(l.w, bitmap);
+    for (int64_t gw = blk * kThreads + (threadIdx.x & ~31); gw < n8; gw += stride) {
+        // the warp's groups gw .. gw + 31 (the last warp of a job may hold fewer)
+        const float4 *src = reinterpret_cast<const float4 *>(xyz) + 6 * gw;
+        const int64_t lim = 6 * (n8 - gw);
+        float4 v[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+            if (32 * j + lane < lim) v[j] = __ldcs(src + 32 * j + lane);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) tw[32 * j + lane] = v[j];
+        __syncwarp();
+        const float4 a0 = tw[6 * lane], a1 = tw[6 * lane + 1], a2 = tw[6 * lane + 2];
+        const float4 a3 = tw[6 * lane + 3], a4 = tw[6 * lane + 4], a5 = tw[6 * lane + 5];
+        __syncwarp();
+        const int64_t g = gw + lane;
+        if (g >= n8) continue;
+        uint32_t k[8];
+        k[0] = chk(key_of(a0.x, a0.y, a0.z, A, inv));
+        k[1] = chk(key_of(a0.w, a1.x, a1.y, A, inv));
+        k[2] = chk(key_of(a1.z, a1.w, a2.x, A, inv));
+        k[3] = chk(key_of(a2.y, a2.z, a2.w, A, inv));
+        k[4] = chk(key_of(a3.x, a3.y, a3.z, A, inv));
+        k[5] = chk(key_of(a3.w, a4.x, a4.y, A, inv));
+        k[6] = chk(key_of(a4.z, a4.w, a5.x, A, inv));
+        k[7] = chk(key_of(a5.y, a5.z, a5.w, A, inv));
+        const uint32_t i0 = static_cast<uint32_t>(kPointsPerThread * g);
+        BitMergeRed m;
+        CellMerge c;
+#pragma unroll
+        for (int i = 0; i < kPointsPerThread; ++i) {
+            m.add(k[i], bitmap);
+            c.add(k[i], i0 + i, rec);
+        }
         m.flush(bitmap);
+        c.flush(rec);
     }
     // ragged tail (n % 8 points): the first threads of the job's first block
     const int64_t t = kPointsPerThread * n8 + blk * kThreads + threadIdx.x;
     if (t < n) {
-        const uint32_t k = chk(key_of(Q.xyz[3 * t], Q.xyz[3 * t + 1], Q.xyz[3 * t + 2], A, inv));
-        keys[t] = k;
-        if (k != kInvalid) atomicOr(&bitmap[k >> 5], 1u << (k & 31));
+        const uint32_t k = chk(key_of(xyz[3 * t], xyz[3 * t + 1], xyz[3 * t + 2], A, inv));
+        if (k != kInvalid) {
+            red_or(&bitmap[k >> 5], 1u << (k & 31));
+            red_add(&rec[k].x, 1u);
+            red_max(&rec[k].y, ~static_cast<uint32_t>(t));
+        }
     }
 }
 
@@ -161,11 +247,13 @@ __global__ void __launch_bounds__(kBmThreads) kf_sums(const FilterJob *J, const 
 // The occupied 32-word chunks of the wave's jobs, one per warp at a time
 // (every warp of the grid strides over each job's chunk list): each lane
 // ranks its word (warp scan of popcounts on top of the chunk's offset),
-// records (rank, bits) for kf_count, clears the word, and writes the keys of
-// its set bits to the warp's stage in shared memory at their ranks within
-// the chunk; the warp then writes the chunk's obstacles 32 consecutive ranks
-// at a time.  Empty chunks cost nothing here.
+// clears the word, and writes the keys of its set bits to the warp's stage
+// in shared memory at their ranks within the chunk; the warp then writes the
+// chunk's obstacles 32 consecutive ranks at a time, each with its cell's
+// record, which it puts back to zero (also beyond the output's capacity).
+// Empty chunks cost nothing here.
 constexpr int kEmitWarps = kBmThreads / 32;
+constexpr int kEmitLoads = 8;  // record loads a lane keeps in flight
 
 __global__ void __launch_bounds__(kBmThreads) kf_emit(const FilterJob *J, int32_t q0, int32_t q1,
                                                       uint32_t *err) {
@@ -217,10 +305,7 @@ __global__ void __launch_bounds__(kBmThreads) kf_emit(const FilterJob *J, int32_
             const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
             const uint32_t excl = incl - cnt;
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (w) {
-                Q.pw[wv] = make_uint2(base + excl, w);
-                Q.bitmap[wv] = 0u;
-            }
+            if (w) Q.bitmap[wv] = 0u;
             uint32_t bits = w, pos = excl;
             const uint32_t k0 = wv * 32u;
             while (bits) {
@@ -229,61 +314,39 @@ __global__ void __launch_bounds__(kBmThreads) kf_emit(const FilterJob *J, int32_
                 st[pos++] = k0 + b;
             }
             __syncwarp();
-            for (uint32_t r = lane; r < total; r += 32) {
-                const uint32_t key = st[r];
-                const uint32_t rank = base + r;
-                if (rank < o.cap) {
-                    const uint32_t qy = div_by(key, dx);
-                    const uint32_t ix = key - qy * A.nx;
-                    const uint32_t iz = div_by(qy, dy);
-                    const uint32_t iy = qy - iz * A.ny;
-                    float cx, cy, cz;
-                    cell_centre(ix, iy, iz, A, cx, cy, cz);
-                    o.keys[rank] = key;
-                    o.counts[rank] = 0u;
-                    o.rep[rank] = kInvalid;
-                    o.x[rank] = cx;
-                    o.y[rank] = cy;
-                    o.z[rank] = cz;
+            // kEmitLoads rounds of 32 at a time: their record loads are
+            // issued together, then each entry is written
+            for (uint32_t r0 = 0; r0 < total; r0 += 32 * kEmitLoads) {
+                uint32_t key[kEmitLoads];
+                uint2 rc[kEmitLoads];
+#pragma unroll
+                for (int j = 0; j < kEmitLoads; ++j) {
+                    const uint32_t r = r0 + 32 * j + lane;
+                    key[j] = r < total ? st[r] : kInvalid;
+                    rc[j] = key[j] != kInvalid ? Q.rec[key[j]] : make_uint2(0u, 0u);
+                }
+#pragma unroll
+                for (int j = 0; j < kEmitLoads; ++j) {
+                    if (key[j] == kInvalid) continue;
+                    Q.rec[key[j]] = make_uint2(0u, 0u);
+                    const uint32_t rank = base + r0 + 32 * j + lane;
+                    if (rank < o.cap) {
+                        const uint32_t qy = div_by(key[j], dx);
+                        const uint32_t ix = key[j] - qy * A.nx;
+                        const uint32_t iz = div_by(qy, dy);
+                        const uint32_t iy = qy - iz * A.ny;
+                        float cx, cy, cz;
+                        cell_centre(ix, iy, iz, A, cx, cy, cz);
+                        o.keys[rank] = key[j];
+                        o.counts[rank] = rc[j].x;
+                        o.rep[rank] = ~rc[j].y;
+                        o.x[rank] = cx;
+                        o.y[rank] = cy;
+                        o.z[rank] = cz;
+                    }
                 }
             }
             __syncwarp();
-        }
-    }
-}
-
-// Keys -> ranks (the word's rank and bits, pw, from L2) -> counts and
-// smallest indices, 8 consecutive keys per thread and iteration, runs of
-// equal ranks merged per thread.
-__global__ void __launch_bounds__(kThreads) kf_count(const FilterJob *J, const int32_t *cp_map,
-                                                     int32_t blk0) {
-    const int32_t gb = blockIdx.x + blk0;
-    const FilterJob &Q = J[cp_map[gb]];
-    const int64_t n = Q.n_raw, n8 = n / kPointsPerThread;
-    const int64_t blk = gb - Q.cp_blk0, stride = static_cast<int64_t>(Q.cp_nblk) * kThreads;
-    const uint2 *__restrict__ pw = Q.pw;
-    uint32_t *counts = Q.o.counts, *rep = Q.o.rep;
-    const int64_t cap = Q.o.cap;
-    for (int64_t g = blk * kThreads + threadIdx.x; g < n8; g += stride) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(Q.keys + kPointsPerThread * g);
-        const uint4 k = __ldcs(src), l = __ldcs(src + 1);
-        const uint32_t kk[8] = {k.x, k.y, k.z, k.w, l.x, l.y, l.z, l.w};
-        uint32_t r[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) r[i] = rank_of(kk[i], pw, cap);
-        RankMerge m;
-        const uint32_t i0 = static_cast<uint32_t>(kPointsPerThread * g);
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-            if (r[i] != kInvalid) m.add(r[i], i0 + i, counts, rep);
-        m.flush(counts, rep);
-    }
-    const int64_t t = kPointsPerThread * n8 + blk * kThreads + threadIdx.x;
-    if (t < n) {
-        const uint32_t r = rank_of(Q.keys[t], pw, cap);
-        if (r != kInvalid) {
-            atomicAdd(&counts[r], 1u);
-            atomicMin(&rep[r], static_cast<uint32_t>(t));
         }
     }
 }
@@ -296,10 +359,10 @@ using namespace gmapp;
 struct gmapp_filter_batch {
     gmapp_ctx *ctx = nullptr;
     FilterJob *d_jobs = nullptr;
-    int32_t *d_pt_map = nullptr, *d_cp_map = nullptr, *d_sb_map = nullptr;
+    int32_t *d_pt_map = nullptr, *d_sb_map = nullptr;
     void *d_ws = nullptr;
-    // per wave: first block and block count of each launch
-    std::vector<int32_t> pt0, ptn, cp0, cpn, sb0, sbn, q0, q1;  // per wave
+    // per wave: first block and block count of each launch, first and last job
+    std::vector<int32_t> pt0, ptn, sb0, sbn, q0, q1;
     int emit_grid = 0;
     cudaStream_t side = nullptr;  // odd waves (the caller's stream runs the even ones)
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -310,12 +373,42 @@ namespace {
 void release(gmapp_filter_batch *fb) {
     cudaFree(fb->d_jobs);
     cudaFree(fb->d_pt_map);
-    cudaFree(fb->d_cp_map);
     cudaFree(fb->d_sb_map);
     cudaFree(fb->d_ws);
     if (fb->fork) cudaEventDestroy(fb->fork);
     if (fb->join) cudaEventDestroy(fb->join);
     if (fb->side) cudaStreamDestroy(fb->side);
+}
+
+// One slot's scratch: the bitmap over the grid (padded to whole kf_sums
+// blocks), per-chunk and per-block popcount offsets, counters, the occupied
+// chunk list and one record per (padded) cell.
+struct SlotLayout {
+    int64_t n_words, n_sblocks;
+    size_t off_bitmap, off_chunk, off_sums, off_offsets, off_counters, off_list, off_rec;
+    size_t total;
+};
+
+SlotLayout slot_layout(uint64_t cells) {
+    SlotLayout L{};
+    const int64_t words = static_cast<int64_t>((cells + 31) / 32);
+    L.n_sblocks = (words + kWordsPerSumBlock - 1) / kWordsPerSumBlock;
+    L.n_words = L.n_sblocks * kWordsPerSumBlock;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    L.off_bitmap = take(L.n_words * 4);
+    L.off_chunk = take(L.n_words / kChunkWords * 4);
+    L.off_sums = take(L.n_sblocks * 4);
+    L.off_offsets = take(L.n_sblocks * 4);
+    L.off_counters = take(64);
+    L.off_list = take(L.n_words / kChunkWords * 4);
+    L.off_rec = take(static_cast<size_t>(L.n_words) * 32 * sizeof(uint2));
+    L.total = off;
+    return L;
 }
 
 }  // namespace
@@ -328,14 +421,11 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
     }
     *out = nullptr;
     size_t touched = 1;
-    // one layout for every slot, sized by the largest cloud and the largest
-    // grid of the batch: a slot serves different jobs wave after wave, and
-    // each region (bitmap, ranks, counters, keys) must sit at the same place
-    // for all of them -- the bitmap stays zero beyond what a job sets and
-    // clears, and no job's keys or ranks land where a later one's bitmap or
-    // counters are
-    int64_t max_raw = 0;
-    int q_cells = 0;
+    // one layout for every slot, sized by the largest grid of the batch: a
+    // slot serves different jobs wave after wave, and each region (bitmap,
+    // offsets, counters, records) must sit at the same place for all of them
+    // -- the bitmap and the records stay zero beyond what a job sets and
+    // clears
     uint64_t max_cells = 0;
     for (int q = 0; q < n_jobs; ++q) {
         const gmapp_cloud_job &J = jobs[q];
@@ -356,21 +446,16 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
                 set_error("gmapp_filter_batch_create: job %d: transform not finite", q);
                 return GMAPP_ERR_INVALID_ARG;
             }
-        const Layout L = layout(J.n_raw, &J.ws);
         const uint64_t cells = static_cast<uint64_t>(J.ws.dims[0]) * J.ws.dims[1] * J.ws.dims[2];
-        if (cells > max_cells) {
-            max_cells = cells;
-            q_cells = q;
-        }
-        max_raw = std::max<int64_t>(max_raw, J.n_raw);
-        // scratch a wave keeps in L2: keys, bitmap, the occupied words' ranks
-        touched = std::max(touched, static_cast<size_t>(J.n_raw) * 4 +
-                                        static_cast<size_t>(L.n_words) * 5);
+        max_cells = std::max(max_cells, cells);
+        // scratch a wave keeps in L2: the bitmap and, at most, one record
+        // per point (a point touches one cell)
+        touched = std::max(touched, static_cast<size_t>((cells + 31) / 32) * 4 +
+                                        static_cast<size_t>(std::min<uint64_t>(
+                                            cells, static_cast<uint64_t>(J.n_raw))) * 8);
     }
-    const Layout SL = layout(max_raw, &jobs[q_cells].ws);  // the slots' common layout
-    const size_t list_off = align_up(SL.total, 256);
-    const size_t slot_bytes =
-        list_off + align_up(static_cast<size_t>(SL.n_words / kChunkWords) * 4, 256);
+    const SlotLayout SL = slot_layout(max_cells);
+    const size_t slot_bytes = SL.total;
     const int W_max = static_cast<int>(std::max<size_t>(
         1, std::min<size_t>(n_jobs, kWaveL2Bytes / touched)));
     const int n_waves = (n_jobs + W_max - 1) / W_max;
@@ -378,14 +463,12 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
     const int n_slots = std::min(n_waves, 2) * W;
 
     std::vector<FilterJob> hj(n_jobs);
-    std::vector<int32_t> pt_map, cp_map, sb_map;
-    // key and count passes: per wave, about one full wave of resident CTAs
-    // (the SM count times the CTAs an SM holds), shared by the wave's jobs
-    int keys_per_sm = 1, count_per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&keys_per_sm, kf_keys, kThreads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&count_per_sm, kf_count, kThreads, 0);
-    const int64_t keys_blocks = std::max(1, keys_per_sm) * static_cast<int64_t>(ctx->sm_count);
-    const int64_t count_blocks = std::max(1, count_per_sm) * static_cast<int64_t>(ctx->sm_count);
+    std::vector<int32_t> pt_map, sb_map;
+    // point pass: per wave, about one full wave of resident CTAs (the SM
+    // count times the CTAs an SM holds), shared by the wave's jobs
+    int pts_per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pts_per_sm, kf_points, kThreads, 0);
+    const int64_t pts_blocks = std::max(1, pts_per_sm) * static_cast<int64_t>(ctx->sm_count);
     auto blocks_for = [&](int64_t n8, int64_t wave_blocks) {
         const int64_t per_job = (wave_blocks + W - 1) / W;
         return static_cast<int32_t>(std::max<int64_t>(
@@ -393,10 +476,12 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
     };
     gmapp_filter_batch *fb = new gmapp_filter_batch();
     fb->ctx = ctx;
-    fb->emit_grid = ctx->sm_count * 4;  // persistent over the wave's occupied chunks
+    // emit: persistent over the wave's occupied chunks, one wave of resident CTAs
+    int emit_per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&emit_per_sm, kf_emit, kBmThreads, 0);
+    fb->emit_grid = std::max(1, emit_per_sm) * ctx->sm_count;
     for (int q = 0; q < n_jobs; ++q) {
         const gmapp_cloud_job &J = jobs[q];
-        const Layout L = layout(J.n_raw, &J.ws);
         FilterJob &D = hj[q];
         memset(&D, 0, sizeof(D));
         D.xyz = J.xyz;
@@ -413,21 +498,20 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
         D.fa.err = ctx->d_err;
         D.dx = div_magic(D.fa.nx);
         D.dy = div_magic(D.fa.ny);
+        const uint64_t cells = static_cast<uint64_t>(J.ws.dims[0]) * J.ws.dims[1] * J.ws.dims[2];
+        const SlotLayout L = slot_layout(cells);
         const int64_t n8 = J.n_raw / kPointsPerThread;
         D.pt_blk0 = static_cast<int32_t>(pt_map.size());
-        D.pt_nblk = blocks_for(n8, keys_blocks);
+        D.pt_nblk = blocks_for(n8, pts_blocks);
         for (int i = 0; i < D.pt_nblk; ++i) pt_map.push_back(q);
-        D.cp_blk0 = static_cast<int32_t>(cp_map.size());
-        D.cp_nblk = blocks_for(n8, count_blocks);
-        for (int i = 0; i < D.cp_nblk; ++i) cp_map.push_back(q);
         D.sb_blk0 = static_cast<int32_t>(sb_map.size());
         D.sb_nblk = static_cast<int32_t>(L.n_sblocks);
         for (int i = 0; i < D.sb_nblk; ++i) sb_map.push_back(q);
+        D.n_chunks = static_cast<uint32_t>(L.n_words / kChunkWords);
         D.o = EmitOut{J.out.keys, J.out.counts, J.out.rep_idx, J.out.x, J.out.y, J.out.z,
                       J.out.cap};
         D.n_out = J.out.n;
-        if (pt_map.size() > 0x7fffffffu || cp_map.size() > 0x7fffffffu ||
-            sb_map.size() > 0x7fffffffu) {
+        if (pt_map.size() > 0x7fffffffu || sb_map.size() > 0x7fffffffu) {
             delete fb;
             set_error("gmapp_filter_batch_create: too many blocks");
             return GMAPP_ERR_CAPACITY;
@@ -437,8 +521,6 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
         const int q0 = w * W, q1 = std::min(n_jobs, q0 + W) - 1;
         fb->pt0.push_back(hj[q0].pt_blk0);
         fb->ptn.push_back(hj[q1].pt_blk0 + hj[q1].pt_nblk - hj[q0].pt_blk0);
-        fb->cp0.push_back(hj[q0].cp_blk0);
-        fb->cpn.push_back(hj[q1].cp_blk0 + hj[q1].cp_nblk - hj[q0].cp_blk0);
         fb->q0.push_back(q0);
         fb->q1.push_back(q1 + 1);
         fb->sb0.push_back(hj[q0].sb_blk0);
@@ -446,12 +528,11 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
     }
     const size_t ws_total = static_cast<size_t>(n_slots) * slot_bytes;
     cudaError_t e = cudaMalloc(&fb->d_ws, ws_total);
-    // zero scratch: bitmaps and counters start clear, and each run leaves
-    // them clear again
+    // zero scratch: bitmaps, records and counters start clear, and each run
+    // leaves them clear again
     if (e == cudaSuccess) e = cudaMemset(fb->d_ws, 0, ws_total);
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_jobs, sizeof(FilterJob) * n_jobs);
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_pt_map, sizeof(int32_t) * pt_map.size());
-    if (e == cudaSuccess) e = cudaMalloc(&fb->d_cp_map, sizeof(int32_t) * cp_map.size());
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_sb_map, sizeof(int32_t) * sb_map.size());
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fb->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fb->fork, cudaEventDisableTiming);
@@ -461,27 +542,21 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
         for (int q = 0; q < n_jobs; ++q) {
             // wave w = q / W uses slot set w % 2 (its stream's), slot q - w W
             const int w = q / W, slot = (w % 2) * W + (q - w * W);
-            const Layout L = layout(jobs[q].n_raw, &jobs[q].ws);
             char *base = ws + static_cast<size_t>(slot) * slot_bytes;
             FilterJob &D = hj[q];
             D.bitmap = reinterpret_cast<uint32_t *>(base + SL.off_bitmap);
-            D.pw = reinterpret_cast<uint2 *>(base + SL.off_pw);
             D.chunk = reinterpret_cast<uint32_t *>(base + SL.off_chunk);
             D.sums = reinterpret_cast<uint32_t *>(base + SL.off_sums);
             D.offsets = reinterpret_cast<uint32_t *>(base + SL.off_offsets);
             D.counters = reinterpret_cast<uint32_t *>(base + SL.off_counters);
-            D.keys = reinterpret_cast<uint32_t *>(base + SL.off_keys);
-            D.chunk_list = reinterpret_cast<uint32_t *>(base + list_off);
-            D.n_chunks = static_cast<uint32_t>(L.n_words / kChunkWords);
+            D.chunk_list = reinterpret_cast<uint32_t *>(base + SL.off_list);
+            D.rec = reinterpret_cast<uint2 *>(base + SL.off_rec);
         }
         e = cudaMemcpy(fb->d_jobs, hj.data(), sizeof(FilterJob) * n_jobs,
                        cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess)
         e = cudaMemcpy(fb->d_pt_map, pt_map.data(), sizeof(int32_t) * pt_map.size(),
-                       cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(fb->d_cp_map, cp_map.data(), sizeof(int32_t) * cp_map.size(),
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(fb->d_sb_map, sb_map.data(), sizeof(int32_t) * sb_map.size(),
@@ -515,11 +590,10 @@ extern "C" gmapp_status filter_cloud_batch(gmapp_filter_batch *fb, gmapp_stream 
     }
     for (int w = 0; w < n_waves; ++w) {
         cudaStream_t s = (w % 2 == 0) ? stream : fb->side;
-        kf_keys<<<fb->ptn[w], kThreads, 0, s>>>(fb->d_jobs, fb->d_pt_map, fb->pt0[w]);
+        kf_points<<<fb->ptn[w], kThreads, 0, s>>>(fb->d_jobs, fb->d_pt_map, fb->pt0[w]);
         kf_sums<<<fb->sbn[w], kBmThreads, 0, s>>>(fb->d_jobs, fb->d_sb_map, fb->sb0[w]);
         kf_emit<<<fb->emit_grid, kBmThreads, 0, s>>>(fb->d_jobs, fb->q0[w], fb->q1[w],
                                                    fb->ctx->d_err);
-        kf_count<<<fb->cpn[w], kThreads, 0, s>>>(fb->d_jobs, fb->d_cp_map, fb->cp0[w]);
     }
     if (n_waves > 1) {
         GMAPP_CHECK_CUDA(cudaEventRecord(fb->join, fb->side));
