@@ -191,17 +191,17 @@ typedef struct gmapp_filter_batch gmapp_filter_batch;
 
 /* Checks every job (GMAPP_ERR_INVALID_ARG names the first bad one), keeps the
  * job table on the device and allocates the jobs' scratch once (the library
- * owns it; freed by gmapp_filter_batch_destroy).  Scratch: two sets of wave
- * slots, each slot 8 bytes per cell of the largest grid (a point count and a
- * smallest index per cell) plus the bitmap (about 51 MB for a 200x200x160
- * grid).  Synchronous. */
+ * owns it; freed by gmapp_filter_batch_destroy).  Scratch: three sets of
+ * wave slots, each slot 8 bytes per cell of the largest grid (a point count
+ * and a smallest index per cell) plus the bitmap (about 52 MB for a
+ * 200x200x160 grid).  Synchronous. */
 gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cloud_job *jobs,
                                        int32_t n_jobs, gmapp_filter_batch **out);
 void gmapp_filter_batch_destroy(gmapp_filter_batch *fb);
 
-/* Filters every job's cloud: three launches per wave, the waves alternating
- * between `stream` and a second stream of the batch that joins `stream` at
- * the end (graph-capturable; allocates nothing).  Output overflow of a job sets
+/* Filters every job's cloud: three launches per wave, the waves going
+ * round-robin to `stream` and two streams of the batch that fork from and
+ * join back into `stream` (graph-capturable; allocates nothing).  Output overflow of a job sets
  * GMAPP_DEVERR_CAPACITY and its out.n > out.cap. */
 gmapp_status filter_cloud_batch(gmapp_filter_batch *fb, gmapp_stream stream);
 

@@ -5,20 +5,21 @@
 // bandwidth, and a whole stream's scratch is far larger than L2.  So the
 // jobs are filtered in WAVES whose touched scratch fits in L2 (at most 48 MB:
 // about 15 tabletop frames), each wave through three launches, and
-// consecutive waves alternate between the caller's stream and a second
-// stream of the batch, so the passes of one wave overlap those of the next.
-// The two streams each own one set of scratch slots, reused wave after wave.
+// consecutive waves go round-robin to three streams (the caller's and two
+// of the batch's own), so the latency-bound passes of three waves overlap.
+// Each stream owns one set of scratch slots, reused wave after wave.
 //
 // Each slot holds, besides the bitmap over the grid, one 8-byte record per
 // grid cell (point count, complement of the smallest point index).  The
 // records start at zero and the emit pass puts every record it reads back
 // to zero, so no pass clears them and only occupied cells are ever touched.
 //
-//   kf_points 8 points per thread and iteration (six 16-byte streaming
-//             loads in flight): key per point, bitmap bits, and per run of
-//             equal keys one reduction into the cell's count and one into
-//             its smallest index (reductions return nothing: the thread
-//             never waits on them)
+//   kf_points 8 points per thread and iteration (a warp's 256 points come
+//             in by coalesced streaming loads through shared memory): key
+//             per point, bitmap bits, and per run of equal keys one
+//             reduction into the cell's count and one into its smallest
+//             index (reductions return nothing: the thread never waits on
+//             them)
 //   kf_sums   per-block (and per-chunk) popcounts; each job's last block
 //             scans its block sums; the occupied 32-word chunks are appended
 //             to the job's chunk list
@@ -45,6 +46,7 @@ namespace {
 
 constexpr int kPointsPerThread = 8;      // kf_points: points per thread per iteration
 constexpr size_t kWaveL2Bytes = size_t(48) << 20;  // L2-resident scratch per wave
+constexpr int kWaveStreams = 3;  // waves in flight: streams (the caller's + side ones), slot sets
 
 // Division by an invariant divisor d by multiplication (T. Granlund and P. L.
 // Montgomery, "Division by invariant integers using multiplication", PLDI
@@ -364,8 +366,11 @@ struct gmapp_filter_batch {
     // per wave: first block and block count of each launch, first and last job
     std::vector<int32_t> pt0, ptn, sb0, sbn, q0, q1;
     int emit_grid = 0;
-    cudaStream_t side = nullptr;  // odd waves (the caller's stream runs the even ones)
-    cudaEvent_t fork = nullptr, join = nullptr;
+    // wave w runs on stream w mod kWaveStreams: 0 is the caller's, the
+    // others are the batch's own side streams, forked from and joined back
+    // into the caller's stream by events
+    cudaStream_t side[kWaveStreams - 1] = {};
+    cudaEvent_t fork = nullptr, join[kWaveStreams - 1] = {};
 };
 
 namespace {
@@ -376,8 +381,10 @@ void release(gmapp_filter_batch *fb) {
     cudaFree(fb->d_sb_map);
     cudaFree(fb->d_ws);
     if (fb->fork) cudaEventDestroy(fb->fork);
-    if (fb->join) cudaEventDestroy(fb->join);
-    if (fb->side) cudaStreamDestroy(fb->side);
+    for (int i = 0; i < kWaveStreams - 1; ++i) {
+        if (fb->join[i]) cudaEventDestroy(fb->join[i]);
+        if (fb->side[i]) cudaStreamDestroy(fb->side[i]);
+    }
 }
 
 // One slot's scratch: the bitmap over the grid (padded to whole kf_sums
@@ -460,7 +467,7 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
         1, std::min<size_t>(n_jobs, kWaveL2Bytes / touched)));
     const int n_waves = (n_jobs + W_max - 1) / W_max;
     const int W = (n_jobs + n_waves - 1) / n_waves;  // balanced waves
-    const int n_slots = std::min(n_waves, 2) * W;
+    const int n_slots = std::min(n_waves, kWaveStreams) * W;
 
     std::vector<FilterJob> hj(n_jobs);
     std::vector<int32_t> pt_map, sb_map;
@@ -534,14 +541,16 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_jobs, sizeof(FilterJob) * n_jobs);
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_pt_map, sizeof(int32_t) * pt_map.size());
     if (e == cudaSuccess) e = cudaMalloc(&fb->d_sb_map, sizeof(int32_t) * sb_map.size());
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fb->side, cudaStreamNonBlocking);
+    for (int i = 0; i < kWaveStreams - 1; ++i) {
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fb->side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fb->join[i], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fb->fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fb->join, cudaEventDisableTiming);
     if (e == cudaSuccess) {
         char *ws = static_cast<char *>(fb->d_ws);
         for (int q = 0; q < n_jobs; ++q) {
-            // wave w = q / W uses slot set w % 2 (its stream's), slot q - w W
-            const int w = q / W, slot = (w % 2) * W + (q - w * W);
+            // wave w = q / W uses slot set w mod kWaveStreams (its stream's), slot q - w W
+            const int w = q / W, slot = (w % kWaveStreams) * W + (q - w * W);
             char *base = ws + static_cast<size_t>(slot) * slot_bytes;
             FilterJob &D = hj[q];
             D.bitmap = reinterpret_cast<uint32_t *>(base + SL.off_bitmap);
@@ -573,7 +582,8 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
 
 extern "C" void gmapp_filter_batch_destroy(gmapp_filter_batch *fb) {
     if (!fb) return;
-    if (fb->side) cudaStreamSynchronize(fb->side);
+    for (int i = 0; i < kWaveStreams - 1; ++i)
+        if (fb->side[i]) cudaStreamSynchronize(fb->side[i]);
     release(fb);
     delete fb;
 }
@@ -584,20 +594,23 @@ extern "C" gmapp_status filter_cloud_batch(gmapp_filter_batch *fb, gmapp_stream 
         return GMAPP_ERR_INVALID_ARG;
     }
     const int n_waves = static_cast<int>(fb->pt0.size());
-    if (n_waves > 1) {
+    const int n_side = std::min(n_waves, kWaveStreams) - 1;  // side streams in use
+    if (n_side > 0) {
         GMAPP_CHECK_CUDA(cudaEventRecord(fb->fork, stream));
-        GMAPP_CHECK_CUDA(cudaStreamWaitEvent(fb->side, fb->fork, 0));
+        for (int i = 0; i < n_side; ++i)
+            GMAPP_CHECK_CUDA(cudaStreamWaitEvent(fb->side[i], fb->fork, 0));
     }
     for (int w = 0; w < n_waves; ++w) {
-        cudaStream_t s = (w % 2 == 0) ? stream : fb->side;
+        const int l = w % kWaveStreams;
+        cudaStream_t s = l == 0 ? stream : fb->side[l - 1];
         kf_points<<<fb->ptn[w], kThreads, 0, s>>>(fb->d_jobs, fb->d_pt_map, fb->pt0[w]);
         kf_sums<<<fb->sbn[w], kBmThreads, 0, s>>>(fb->d_jobs, fb->d_sb_map, fb->sb0[w]);
         kf_emit<<<fb->emit_grid, kBmThreads, 0, s>>>(fb->d_jobs, fb->q0[w], fb->q1[w],
                                                    fb->ctx->d_err);
     }
-    if (n_waves > 1) {
-        GMAPP_CHECK_CUDA(cudaEventRecord(fb->join, fb->side));
-        GMAPP_CHECK_CUDA(cudaStreamWaitEvent(stream, fb->join, 0));
+    for (int i = 0; i < n_side; ++i) {
+        GMAPP_CHECK_CUDA(cudaEventRecord(fb->join[i], fb->side[i]));
+        GMAPP_CHECK_CUDA(cudaStreamWaitEvent(stream, fb->join[i], 0));
     }
     GMAPP_CHECK_CUDA(cudaGetLastError());
     return GMAPP_OK;
