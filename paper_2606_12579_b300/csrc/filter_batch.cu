@@ -16,10 +16,11 @@
 //
 //   kf_points 8 points per thread and iteration (a warp's 256 points come
 //             in by coalesced streaming loads through shared memory): key
-//             per point, bitmap bits, and per run of equal keys one
-//             reduction into the cell's count and one into its smallest
-//             index (reductions return nothing: the thread never waits on
-//             them)
+//             per point; per run of equal keys one reduction into the
+//             cell's count and one into its smallest index; the bitmap bits
+//             gathered per warp and word in shared memory, one reduction per
+//             word and tile (reductions return nothing: the thread never
+//             waits on them)
 //   kf_sums   per-block (and per-chunk) popcounts; each job's last block
 //             scans its block sums; the occupied 32-word chunks are appended
 //             to the job's chunk list
@@ -121,21 +122,57 @@ __device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
 
 // BitMerge with a reduction: bits of consecutive points in one 32-cell word
 // OR-ed into the bitmap at once.
-struct BitMergeRed {
+// A warp's words of the bitmap, gathered in shared memory while it keys
+// its 256 points (64 slots, open addressing on the word index): each word
+// then goes to the bitmap in one reduction per tile instead of one per run;
+// a word that finds no slot within 8 probes goes to the bitmap at once.
+constexpr int kWordSlots = 64;
+struct WordTable {
+    uint32_t *key, *bits;  // this warp's slots; key kInvalid = empty
+    __device__ __forceinline__ void add(uint32_t word, uint32_t b, uint32_t *bitmap) {
+        uint32_t h = (word * 2654435761u) >> 26;
+        for (int probe = 0; probe < 8; ++probe) {
+            const uint32_t old = atomicCAS(&key[h], kInvalid, word);
+            if (old == kInvalid || old == word) {
+                atomicOr(&bits[h], b);
+                return;
+            }
+            h = (h + 1) & (kWordSlots - 1);
+        }
+        red_or(&bitmap[word], b);
+    }
+    // the whole warp: every gathered word to the bitmap, slots emptied
+    __device__ __forceinline__ void flush(uint32_t *bitmap, int lane) {
+        __syncwarp();
+#pragma unroll
+        for (int s = lane; s < kWordSlots; s += 32) {
+            const uint32_t w = key[s];
+            if (w != kInvalid) {
+                red_or(&bitmap[w], bits[s]);
+                key[s] = kInvalid;
+                bits[s] = 0u;
+            }
+        }
+        __syncwarp();
+    }
+};
+
+// Bits of one thread's consecutive points merged while they share a word.
+struct BitMerge8 {
     uint32_t word = kInvalid, bits = 0;
-    __device__ __forceinline__ void add(uint32_t key, uint32_t *bitmap) {
+    __device__ __forceinline__ void add(uint32_t key, WordTable &t, uint32_t *bitmap) {
         if (key == kInvalid) return;
         const uint32_t w = key >> 5, b = 1u << (key & 31);
         if (w == word) {
             bits |= b;
             return;
         }
-        flush(bitmap);
+        flush(t, bitmap);
         word = w;
         bits = b;
     }
-    __device__ __forceinline__ void flush(uint32_t *bitmap) {
-        if (word != kInvalid) red_or(&bitmap[word], bits);
+    __device__ __forceinline__ void flush(WordTable &t, uint32_t *bitmap) {
+        if (word != kInvalid) t.add(word, bits, bitmap);
         word = kInvalid;
     }
 };
@@ -167,15 +204,22 @@ struct CellMerge {
 };
 
 // Points -> keys -> bitmap bits and cell records: 8 consecutive points per
-// thread and iteration, bits merged per thread by word, records by run of
-// equal keys.  A warp's 256 points (3 KB) come in as six coalesced 16-byte
+// thread and iteration, bits merged per thread by word and then per warp in
+// its word table, records by run of equal keys.  A warp's 256 points (3 KB) come in as six coalesced 16-byte
 // loads per lane (512 contiguous bytes per instruction) and are handed to
 // their threads through the warp's tile in shared memory.
 __global__ void __launch_bounds__(kThreads, 4) kf_points(const FilterJob *J, const int32_t *pt_map,
                                                       int32_t blk0) {
     __shared__ float4 tile[kThreads / 32][6 * 32];
+    __shared__ uint32_t wkey[kThreads / 32][kWordSlots], wbits[kThreads / 32][kWordSlots];
     const int lane = threadIdx.x & 31;
     float4 *tw = tile[threadIdx.x >> 5];
+    WordTable table{wkey[threadIdx.x >> 5], wbits[threadIdx.x >> 5]};
+    for (int s = lane; s < kWordSlots; s += 32) {
+        table.key[s] = kInvalid;
+        table.bits[s] = 0u;
+    }
+    __syncwarp();
     const int32_t gb = blockIdx.x + blk0;
     const FilterJob &Q = J[pt_map[gb]];
     const FilterArgs A = Q.fa;
@@ -205,26 +249,28 @@ __global__ void __launch_bounds__(kThreads, 4) kf_points(const FilterJob *J, con
         const float4 a3 = tw[6 * lane + 3], a4 = tw[6 * lane + 4], a5 = tw[6 * lane + 5];
         __syncwarp();
         const int64_t g = gw + lane;
-        if (g >= n8) continue;
-        uint32_t k[8];
-        k[0] = chk(key_of(a0.x, a0.y, a0.z, A, inv));
-        k[1] = chk(key_of(a0.w, a1.x, a1.y, A, inv));
-        k[2] = chk(key_of(a1.z, a1.w, a2.x, A, inv));
-        k[3] = chk(key_of(a2.y, a2.z, a2.w, A, inv));
-        k[4] = chk(key_of(a3.x, a3.y, a3.z, A, inv));
-        k[5] = chk(key_of(a3.w, a4.x, a4.y, A, inv));
-        k[6] = chk(key_of(a4.z, a4.w, a5.x, A, inv));
-        k[7] = chk(key_of(a5.y, a5.z, a5.w, A, inv));
-        const uint32_t i0 = static_cast<uint32_t>(kPointsPerThread * g);
-        BitMergeRed m;
-        CellMerge c;
+        if (g < n8) {
+            uint32_t k[8];
+            k[0] = chk(key_of(a0.x, a0.y, a0.z, A, inv));
+            k[1] = chk(key_of(a0.w, a1.x, a1.y, A, inv));
+            k[2] = chk(key_of(a1.z, a1.w, a2.x, A, inv));
+            k[3] = chk(key_of(a2.y, a2.z, a2.w, A, inv));
+            k[4] = chk(key_of(a3.x, a3.y, a3.z, A, inv));
+            k[5] = chk(key_of(a3.w, a4.x, a4.y, A, inv));
+            k[6] = chk(key_of(a4.z, a4.w, a5.x, A, inv));
+            k[7] = chk(key_of(a5.y, a5.z, a5.w, A, inv));
+            const uint32_t i0 = static_cast<uint32_t>(kPointsPerThread * g);
+            BitMerge8 m;
+            CellMerge c;
 #pragma unroll
-        for (int i = 0; i < kPointsPerThread; ++i) {
-            m.add(k[i], bitmap);
-            c.add(k[i], i0 + i, rec);
+            for (int i = 0; i < kPointsPerThread; ++i) {
+                m.add(k[i], table, bitmap);
+                c.add(k[i], i0 + i, rec);
+            }
+            m.flush(table, bitmap);
+            c.flush(rec);
         }
-        m.flush(bitmap);
-        c.flush(rec);
+        table.flush(bitmap, lane);
     }
     // ragged tail (n % 8 points): the first threads of the job's first block
     const int64_t t = kPointsPerThread * n8 + blk * kThreads + threadIdx.x;
