@@ -165,19 +165,31 @@ def test_repeat_determinism(gm):
 def test_batched_filter_matches_filter_cloud_and_oracle(gm):
     """filter_cloud_batch over uneven clouds (a full tabletop frame, a sphere
     cloud on its own grid, a ragged tiny cloud, an empty one, one that
-    overflows its capacity) gives each job the result of filter_cloud on
-    the same cloud, bit for bit, and the oracle's; a second run repeats it."""
+    overflows its capacity, points scattered over the whole grid so that a
+    warp's 256 points touch more bitmap words than its word table holds, and
+    20,003 points in one voxel, one long run of equal keys) gives each job
+    the result of filter_cloud on the same cloud, bit for bit, and the
+    oracle's; a second run repeats it."""
     import torch
     tab = synth.tabletop_workload(n_agents=1, n_steps=1)
     sph = synth.sphere_workload()
     g = np.random.Generator(np.random.PCG64(17))
     tiny = g.uniform(-0.05, 1.05, (13, 3)).astype(np.float32)
     empty = np.zeros((0, 3), np.float32)
+    ws_t = tab["workspace"]
+    I = np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], np.float32)
+    lo, hi = np.asarray(ws_t.lo, np.float64), np.asarray(ws_t.lo, np.float64) + \
+        np.asarray(ws_t.dims, np.float64) * ws_t.voxel
+    scattered = g.uniform(lo, hi, (50000, 3)).astype(np.float32)
+    centre = lo + (np.array([17, 33, 9]) + 0.5) * ws_t.voxel
+    one_voxel = (centre + g.uniform(-0.4, 0.4, (20003, 3)) * ws_t.voxel).astype(np.float32)
     jobs = [(tab["xyz"], tab["T"], tab["workspace"], None),
             (sph["xyz"], sph["T"], sph["workspace"], None),
             (tiny, tab["T"], tab["workspace"], None),
             (empty, tab["T"], tab["workspace"], None),
-            (tab["xyz"], tab["T"], tab["workspace"], 1000)]
+            (tab["xyz"], tab["T"], tab["workspace"], 1000),
+            (scattered, I, ws_t, None),
+            (one_voxel, I, ws_t, None)]
     clouds = [torch.from_numpy(np.ascontiguousarray(x)).cuda() if x.shape[0] else
               torch.empty(0, 3, device="cuda") for x, _, _, _ in jobs]
     caps = [c if c is not None else max(4, (x.shape[0] + 3) // 4 * 4) for x, _, _, c in jobs]
@@ -229,9 +241,9 @@ def test_voxel_faces_stress_bit_exact(gm):
 
 
 def test_batched_filter_many_waves_matches_filter_cloud(gm):
-    """40 tabletop frames: more than one L2-sized wave (16 tabletop frames), so
-    the batch alternates waves between its two streams and reuses each
-    stream's scratch slots.  Every job's S_W equals filter_cloud's bit for bit,
+    """40 tabletop frames: more than one L2-sized wave (about 15 tabletop
+    frames), so the batch deals its waves round-robin to its streams and
+    reuses each stream's scratch slots.  Every job's S_W equals filter_cloud's bit for bit,
     on two runs in a row and through a CUDA-graph replay."""
     import torch
     base = [synth.tabletop_workload(frame_seed=9_100_000 + f, n_agents=1, n_steps=1)
