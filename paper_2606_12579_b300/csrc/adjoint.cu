@@ -120,7 +120,9 @@ __device__ __forceinline__ float and_bits(float v, uint32_t m) {
 // jg, jg + 1) for NA agents: W += [gate] u, grad += [gate, unclamped]
 // u^2/|d| (p - o) (negated later), nearest obstacle.  TAIL: the pair holds
 // the shard's odd last obstacle twice and its hi lane counts for nothing.
-template <int NA, int NM, bool TAIL, bool ARGMIN = true, bool MASKD = false>
+// OPEN: every agent of the half is without a gate (r_d = inf) and the pair
+// is a real obstacle, so every gate test passes and is not evaluated.
+template <int NA, int NM, bool TAIL, bool ARGMIN = true, bool MASKD = false, bool OPEN = false>
 __device__ __forceinline__ void adj_pair(f2 ox, f2 oy, f2 oz, int jg, const f2 (&X)[NA],
                                          const f2 (&Y)[NA], const f2 (&Z)[NA],
                                          const f2 (&nR2)[NA], const float (&G2)[NA], float eps,
@@ -136,7 +138,8 @@ __device__ __forceinline__ void adj_pair(f2 ox, f2 oy, f2 oz, int jg, const f2 (
         const float s0l = lo_of(s), s0h = hi_of(s);
         const float sl = fmaxf(s0l, eps), sh = fmaxf(s0h, eps);
         // gate (s <= r_d, as |d|^2 <= (r_d + R)^2); gradient: gate AND unclamped
-        const uint32_t gl = le_bits(d2l, G2[a]), gh = TAIL ? 0u : le_bits(d2h, G2[a]);
+        const uint32_t gl = OPEN ? ~0u : le_bits(d2l, G2[a]);
+        const uint32_t gh = TAIL ? 0u : OPEN ? ~0u : le_bits(d2h, G2[a]);
         const uint32_t ql = gl & gt_bits(s0l, eps), qh = gh & gt_bits(s0h, eps);
         f2 u;  // 1/s (SFU agents) or -1/s (Newton-Raphson agents)
         if (sfu_agent(a, NM, NA)) {
@@ -144,7 +147,10 @@ __device__ __forceinline__ void adj_pair(f2 ox, f2 oy, f2 oz, int jg, const f2 (
         } else {
             u = neg_rcp2(pk(sl, sh), sl, sh, one2);
         }
-        W[a] = add2(W[a], pk(and_bits(lo_of(u), gl), and_bits(hi_of(u), gh)));
+        if (OPEN && !TAIL)
+            W[a] = add2(W[a], u);
+        else
+            W[a] = add2(W[a], pk(and_bits(lo_of(u), gl), and_bits(hi_of(u), gh)));
         const f2 t = mul2(mul2(u, u), r);  // u^2 / |d|
         const f2 q = pk(and_bits(lo_of(t), ql), and_bits(hi_of(t), qh));
         if (MASKD) {
@@ -233,20 +239,36 @@ __device__ __forceinline__ void adj_half(const float *sx, const float *sy, const
         // never become the nearest obstacle
         const int cnt_pad = (cnt + 127) & ~127;
         // an agent without a gate (r_d = inf) passes every block: then every
-        // block's terms run without the test
-        bool every = false;
+        // block's terms run without the test (and when no agent of the half
+        // has a gate, without the gate masks)
+        bool every = false, open = true;
 #pragma unroll
-        for (int a = 0; a < NA; ++a) every |= G2[a] == INFINITY;
+        for (int a = 0; a < NA; ++a) {
+            every |= G2[a] == INFINITY;
+            open &= G2[a] == INFINITY;
+        }
         if (every) {
             // the real obstacles only (no NaN pads): pairs, then an odd last one
             const int cnt_even = cnt & ~1;
+            if (open) {
 #pragma unroll 2
-            for (int j = 2 * tid; j < cnt_even; j += 2 * NT) {
-                const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
-                const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
-                const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
-                adj_pair<NA, NM, false>(ox, oy, oz, j0 + j, X, Y, Z, nR2, G2, eps, one2, W, GX,
-                                        GY, GZ, bd, bj);
+                for (int j = 2 * tid; j < cnt_even; j += 2 * NT) {
+                    const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
+                    const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
+                    const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
+                    adj_pair<NA, NM, false, true, false, true>(ox, oy, oz, j0 + j, X, Y, Z, nR2,
+                                                               G2, eps, one2, W, GX, GY, GZ, bd,
+                                                               bj);
+                }
+            } else {
+#pragma unroll 2
+                for (int j = 2 * tid; j < cnt_even; j += 2 * NT) {
+                    const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
+                    const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
+                    const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
+                    adj_pair<NA, NM, false>(ox, oy, oz, j0 + j, X, Y, Z, nR2, G2, eps, one2, W,
+                                            GX, GY, GZ, bd, bj);
+                }
             }
             if ((cnt & 1) && tid == (cnt_even / 2) % NT) {
                 const float x = sx[cnt_even], y = sy[cnt_even], z = sz[cnt_even];
