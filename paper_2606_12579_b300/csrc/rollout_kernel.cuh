@@ -292,33 +292,36 @@ __device__ __forceinline__ bool pair_dist(f2 ox, f2 oy, f2 oz, const f2 (&X)[NA]
     return hit;
 }
 
-template <int AG, int NA, int OFF, int NM>
+// OPEN: no agent of the half has a gate (r_d = inf) and both obstacles of
+// the pair are real, so every gate mask is 1 and is not formed.
+template <int AG, int NA, int OFF, int NM, bool OPEN = false>
 __device__ __forceinline__ void pair_heur(const f2 (&d2)[NA], f2 (&acc)[NA], const f2 (&nR2)[AG],
                                           const float (&G2a)[AG], float eps, f2 one2) {
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
         const float d2l = lo_of(d2[a]), d2h = hi_of(d2[a]);
-        const f2 mask = pk(le_mask(d2l, G2a[OFF + a]), le_mask(d2h, G2a[OFF + a]));
         const f2 r = pk(rsqrt_approx(d2l), rsqrt_approx(d2h));
         const f2 s = fma2(d2[a], r, nR2[OFF + a]);  // |d| - R (NaN when d = 0)
         const float sl = fmaxf(lo_of(s), eps), sh = fmaxf(hi_of(s), eps);
-        if (sfu_agent(a, NM, NA)) {
-            acc[a] = fma2(mask, pk(rcp_approx(sl), rcp_approx(sh)), acc[a]);
+        const f2 y = sfu_agent(a, NM, NA) ? pk(rcp_approx(sl), rcp_approx(sh))
+                                          : neg_rcp2(pk(sl, sh), sl, sh, one2);
+        if constexpr (OPEN) {
+            acc[a] = add2(y, acc[a]);
         } else {
-            const f2 y = neg_rcp2(pk(sl, sh), sl, sh, one2);
+            const f2 mask = pk(le_mask(d2l, G2a[OFF + a]), le_mask(d2h, G2a[OFF + a]));
             acc[a] = fma2(mask, y, acc[a]);
         }
     }
 }
 
-template <int AG, int NA, int OFF, int NM, bool CLEAR>
+template <int AG, int NA, int OFF, int NM, bool CLEAR, bool OPEN = false>
 __device__ __forceinline__ void pair_terms(f2 ox, f2 oy, f2 oz, const f2 (&X)[NA],
                                            const f2 (&Y)[NA], const f2 (&Z)[NA], f2 (&acc)[NA],
                                            float (&mn)[NA], const f2 (&nR2)[AG],
                                            const float (&G2a)[AG], float eps, f2 one2) {
     f2 d2[NA];
     pair_dist<AG, NA, OFF, CLEAR>(ox, oy, oz, X, Y, Z, d2, mn, G2a);
-    pair_heur<AG, NA, OFF, NM>(d2, acc, nR2, G2a, eps, one2);
+    pair_heur<AG, NA, OFF, NM, OPEN>(d2, acc, nR2, G2a, eps, one2);
 }
 
 // Obstacles beyond what shared memory holds, read from global memory
@@ -355,7 +358,7 @@ __device__ __forceinline__ void half_step(const float *sx, const float *sy, cons
                                           GlobalTail tail = GlobalTail{},
                                           const float *pos = nullptr,
                                           uint32_t *nheur = nullptr, float omax2 = 0.0f,
-                                          const float *boxes = nullptr) {
+                                          const float *boxes = nullptr, int cnt_real = -1) {
     if constexpr (NA > 0) {
         constexpr int P = pow2ceil(NA);
         const int tid = threadIdx.x;
@@ -482,8 +485,27 @@ __device__ __forceinline__ void half_step(const float *sx, const float *sy, cons
             if (nheur) *nheur += 2 * blocks * NA;  // blocks of 128 obstacles
         } else {
             uint32_t its = 0;
+            // with no gate in the half, the real obstacles' pairs run without
+            // the gate masks (a NaN pad needs its mask of 0): up to the last
+            // whole pair of real obstacles, then the rest masked
+            bool open = cnt_real >= 0;
+#pragma unroll
+            for (int a = 0; a < NA; ++a) open &= G2a[OFF + a] == INFINITY;
+            int j = 2 * tid;
+            if (open) {
+                const int cnt_even = cnt_real & ~1;
 #pragma unroll 3
-            for (int j = 2 * tid; j < cnt_pad; j += 2 * NT) {
+                for (; j < cnt_even; j += 2 * NT) {
+                    const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
+                    const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
+                    const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
+                    pair_terms<AG, NA, OFF, NM, CLEAR, true>(ox, oy, oz, X, Y, Z, acc, mn, nR2,
+                                                             G2a, eps, one2);
+                    ++its;
+                }
+            }
+#pragma unroll 3
+            for (; j < cnt_pad; j += 2 * NT) {
                 const f2 ox = *reinterpret_cast<const f2 *>(sx + j);
                 const f2 oy = *reinterpret_cast<const f2 *>(sy + j);
                 const f2 oz = *reinterpret_cast<const f2 *>(sz + j);
@@ -1519,7 +1541,7 @@ __global__ void __launch_bounds__(NT + 32 * kExchWarps, 1) k_rollout(const Rollo
                     else
                         half_step<AG, H0, 0, NM0, NT, CLEAR, false, false, true, VOTE, BOX>(
                             sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(0) + 2 * (warp * AG), C,
-                            lane, GlobalTail{}, pos, &nheur, omax2, boxes);
+                            lane, GlobalTail{}, pos, &nheur, omax2, boxes, cnt);
                     named_arrive(kPart + 0, kBoth);
                     if (k > 0) named_sync(kPos + 1, kBoth);
                     if constexpr (APF)
@@ -1533,7 +1555,7 @@ __global__ void __launch_bounds__(NT + 32 * kExchWarps, 1) k_rollout(const Rollo
                     else
                         half_step<AG, H1, H0, NM1, NT, CLEAR, false, false, true, VOTE, BOX>(
                             sx, sy, sz, cnt_pad, eps, nR2, G2a, p, part(1) + 2 * (warp * AG), C,
-                            lane, GlobalTail{}, pos, &nheur, omax2, boxes);
+                            lane, GlobalTail{}, pos, &nheur, omax2, boxes, cnt);
                     named_arrive(kPart + 1, kBoth);
                 }
             };
