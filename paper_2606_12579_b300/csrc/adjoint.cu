@@ -165,13 +165,19 @@ __device__ __forceinline__ void adj_pair(f2 ox, f2 oy, f2 oz, int jg, const f2 (
             GZ[a] = fma2(q, dz, GZ[a]);
         }
         if (ARGMIN) {
-            if (d2l < bd[a]) {  // ascending index per thread: strict < keeps the lowest
-                bd[a] = d2l;
-                bj[a] = jg;
-            }
-            if (!TAIL && d2h < bd[a]) {
-                bd[a] = d2h;
-                bj[a] = jg + 1;
+            // ascending index per thread: strict < keeps the lowest (and the
+            // lo lane on a tie within the pair)
+            if (TAIL) {
+                if (d2l < bd[a]) {
+                    bd[a] = d2l;
+                    bj[a] = jg;
+                }
+            } else {
+                const float m = fminf(d2l, d2h);  // NaN lanes never win
+                if (m < bd[a]) {
+                    bj[a] = d2h < d2l ? jg + 1 : jg;
+                    bd[a] = m;
+                }
             }
         }
     }
@@ -192,14 +198,11 @@ __device__ __forceinline__ bool adj_test(f2 ox, f2 oy, f2 oz, int jg, const f2 (
         const f2 dx = sub2(X[a], ox), dy = sub2(Y[a], oy), dz = sub2(Z[a], oz);
         const f2 d2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
         const float d2l = lo_of(d2), d2h = hi_of(d2);
-        hit |= fminf(d2l, d2h) <= G2[a];
-        if (d2l < bd[a]) {
-            bd[a] = d2l;
-            bj[a] = jg;
-        }
-        if (d2h < bd[a]) {
-            bd[a] = d2h;
-            bj[a] = jg + 1;
+        const float m = fminf(d2l, d2h);  // NaN lanes never win
+        hit |= m <= G2[a];
+        if (m < bd[a]) {  // ascending index: strict < keeps the lowest (lo lane on a tie)
+            bj[a] = d2h < d2l ? jg + 1 : jg;
+            bd[a] = m;
         }
     }
     return hit;
