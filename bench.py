@@ -524,7 +524,7 @@ def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8, wit
     """The perception filter alone (A1-A3) over a stream of 256 tabletop
     frames (307,200 points each, 944 MB read in total; 64 distinct frames,
     236 MB, cycled so that no frame is still in L2 when it comes back):
-    through filter_cloud_batch, 32 frames per batch; and frame by frame
+    through filter_cloud_batch, all 64 in one batch; and frame by frame
     through filter_cloud, on 8 CUDA streams with a workspace and an output
     each, and on one stream back to back (both graph-captured).  Algorithmic
     bytes per frame: 12 B per raw point read + 24 B per obstacle written
@@ -598,7 +598,7 @@ def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8, wit
                 "hbm_frac": gbs / peak if peak else None}
 
     # filter_cloud_batch: all 64 distinct frames in one batch (filtered in
-    # L2-sized waves of a few frames on two streams), run four times
+    # L2-sized waves of a few frames on three streams), run four times
     per = n_distinct
     batches = [gm.FilterBatch([frames[i] for i in range(b, b + per)], w0["T"], w0["workspace"],
                               caps=[131072] * per) for b in range(0, n_distinct, per)]
@@ -620,7 +620,7 @@ def bench_filter_stream(gm, args, n_filters=256, n_distinct=64, n_streams=8, wit
         best = t if best is None else min(best, t)
     res["batched"] = entry(best)
     res["batched"]["frames_per_batch"] = per
-    # the same runs captured once in a CUDA graph (the batch's two streams
+    # the same runs captured once in a CUDA graph (the batch's side streams
     # join the capture), so launch latency is off the critical path
     side = torch.cuda.Stream()
     side.wait_stream(cur)
