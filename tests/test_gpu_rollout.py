@@ -157,12 +157,18 @@ def test_launch_shapes(gm, shape):
     _compare_rollout(out, ref)
 
 
+@pytest.mark.parametrize("gated", [True, False])
 @pytest.mark.parametrize("n_obs", [0, 1, 2, 3, 5, 17, 1001])
-def test_small_obstacle_counts(gm, n_obs):
+def test_small_obstacle_counts(gm, n_obs, gated):
+    """Shards of every size and parity (one to many CTAs per group), with and
+    without a detection gate (r_d = inf: the pair loop without the gate
+    masks over the real obstacles, the masked loop for an odd last one)."""
     g = np.random.Generator(np.random.PCG64(n_obs))
     obs = np.stack([g.uniform(0.35, 0.45, n_obs), g.uniform(-0.03, 0.03, n_obs),
                     g.uniform(0.37, 0.43, n_obs)]).astype(np.float32)
     w = synth.sphere_workload(n_agents=5, n_steps=150)
+    if not gated:
+        w["agents"] = dict(w["agents"], r_d=np.full(5, np.inf, np.float32))
     ref = oracle.rollout(obs, 0.005, w["agents"], w["params"])
     for shape in ((1, 5, 128), (4, 2, 256), (16, 3, 128), (4, 2, 256, 1), (16, 3, 128, 1)):
         out = gm.rollout_agents(_gpu_obstacles(gm, obs, 0.005, cap=1024), to_dev_agents(w["agents"]),
