@@ -694,15 +694,18 @@ __device__ __forceinline__ bool exchange_half_grid(const float *part, uint64_t *
         if (p < npairs) {
             const int r = p / NA, a = OFF + p % NA;
             const uint64_t *src = xs + 2 * (r * AG + a);
-            for (uint32_t it = 0; ok && static_cast<uint32_t>(vw[j] >> 32) != tag; ++it) {
-                if (it == limit) ok = false;
-                else vw[j] = ld_relaxed_u64(src);
-            }
-            if (CLEAR) {
-                for (uint32_t it = 0; ok && static_cast<uint32_t>(vm[j] >> 32) != tag; ++it) {
-                    if (it == limit) ok = false;
-                    else vm[j] = ld_relaxed_u64(src + 1);
+            // both words of the pair are reloaded together while either is
+            // stale: one round trip per poll, not one per word
+            for (uint32_t it = 0; ok; ++it) {
+                const bool fw = static_cast<uint32_t>(vw[j] >> 32) == tag;
+                const bool fm = !CLEAR || static_cast<uint32_t>(vm[j] >> 32) == tag;
+                if (fw && fm) break;
+                if (it == limit) {
+                    ok = false;
+                    break;
                 }
+                if (!fw) vw[j] = ld_relaxed_u64(src);
+                if (!fm) vm[j] = ld_relaxed_u64(src + 1);
             }
             *reinterpret_cast<float2 *>(slot + 2 * (r * AG + a)) =
                 make_float2(__uint_as_float(static_cast<uint32_t>(vw[j])),
@@ -1075,14 +1078,24 @@ __device__ __forceinline__ bool exchange_half_grid_rec(const float *part, uint64
             const int r = p / NA, a = OFF + p % NA;
             const uint64_t *src = xs + RS * (r * AG + a);
             float *dst = slot + RS * (r * AG + a);
+            // the record's stale words are reloaded together: one round trip
+            // per poll, not one per word
+            for (uint32_t it = 0; ok; ++it) {
+                bool fresh = true;
 #pragma unroll
-            for (int c = 0; c < NV; ++c) {
-                for (uint32_t it = 0; ok && static_cast<uint32_t>(w[j][c] >> 32) != tag; ++it) {
-                    if (it == limit) ok = false;
-                    else w[j][c] = ld_relaxed_u64(src + c);
+                for (int c = 0; c < NV; ++c)
+                    fresh = fresh && static_cast<uint32_t>(w[j][c] >> 32) == tag;
+                if (fresh) break;
+                if (it == limit) {
+                    ok = false;
+                    break;
                 }
-                dst[c] = __uint_as_float(static_cast<uint32_t>(w[j][c]));
+#pragma unroll
+                for (int c = 0; c < NV; ++c)
+                    if (static_cast<uint32_t>(w[j][c] >> 32) != tag) w[j][c] = ld_relaxed_u64(src + c);
             }
+#pragma unroll
+            for (int c = 0; c < NV; ++c) dst[c] = __uint_as_float(static_cast<uint32_t>(w[j][c]));
         }
     }
     __syncwarp();
