@@ -606,8 +606,9 @@ def __getattr__(name):
 # ---------------------------------------------------------------------------
 
 class FilterBatch:
-    """Many clouds through one batched filter (four launches for all of them,
-    results bit-identical to filter_cloud per cloud).  ``clouds``: list of
+    """Many clouds through one batched filter (waves of clouds whose scratch
+    fits in L2, three launches per wave on the batch's streams; results
+    bit-identical to filter_cloud per cloud).  ``clouds``: list of
     device [N, 3] float32 tensors (kept, not copied: refill them in place
     between runs); ``T`` and ``ws`` are shared by all clouds, or lists of one
     per cloud.  ``outs[q]`` is cloud q's obstacle set after run()."""
