@@ -13,14 +13,66 @@
 //   k_emit          per word: prefix rank; per set bit (one lane per bit of a
 //                   word, warp-cooperative): key, centre; publishes N_O
 //   k_count         points -> rank -> count (atomicAdd), smallest index (atomicMin)
+//   (several sensors: k_keys_fused / k_count_fused, one launch for up to 8
+//   sensors, each sensor's blocks with its own transform and index base)
 //   k_keep_sums / k_keep_emit   only when min_pts > 1: order-preserving compaction
 #include <math.h>
 
 #include <algorithm>
-
+#include <vector>
 
 #include "filter_device.cuh"
 
+
+namespace gmapp {
+namespace {
+
+// Several sensors' key and count passes in one launch each: sensor q owns
+// blocks [blk0, blk0 + nblk) of the grid (ascending blk0), its transform, its
+// key slot and the index of its first point.
+constexpr int kFuseMax = 8;
+struct SensorRange {
+    const float *xyz;
+    int64_t n, slot;
+    float T[12];
+    uint32_t idx0;
+    int32_t blk0, nblk;
+};
+struct SensorSet {
+    SensorRange s[kFuseMax];
+    int32_t n;
+};
+
+// The sensor of this block (the last one whose first block is at or before
+// it), read with compile-time indices only.
+__device__ __forceinline__ void sensor_of_block(const SensorSet &S, SensorRange &R) {
+#pragma unroll
+    for (int t = 0; t < kFuseMax; ++t)
+        if (t < S.n && static_cast<int32_t>(blockIdx.x) >= S.s[t].blk0) R = S.s[t];
+}
+
+__global__ void __launch_bounds__(kThreads) k_keys_fused(const SensorSet S, FilterArgs A,
+                                                         uint32_t *__restrict__ keys,
+                                                         uint32_t *__restrict__ bitmap) {
+    SensorRange R = S.s[0];
+    sensor_of_block(S, R);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) A.T[i] = R.T[i];
+    keys_range(R.xyz, R.n, A, keys + R.slot, bitmap, blockIdx.x - R.blk0, R.nblk);
+}
+
+__global__ void __launch_bounds__(kThreads) k_count_fused(const SensorSet S,
+                                                          const uint32_t *__restrict__ keys,
+                                                          const uint2 *__restrict__ pw,
+                                                          uint32_t *counts, uint32_t *rep,
+                                                          int64_t cap) {
+    SensorRange R = S.s[0];
+    sensor_of_block(S, R);
+    count_range(keys + R.slot, R.n, pw, counts, rep, cap, blockIdx.x - R.blk0, R.nblk, R.idx0);
+}
+
+}  // namespace
+}  // namespace gmapp
 
 using namespace gmapp;
 
@@ -123,26 +175,50 @@ gmapp_status filter_impl(const char *who, gmapp_ctx *ctx, const gmapp_sensor_clo
 
     k_zero<<<grid_zero, kThreads, 0, stream>>>(reinterpret_cast<uint4 *>(bitmap), L.n_words / 4,
                                                counters, 16);
+    // sensors in groups of up to kFuseMax, one key launch (and later one
+    // count launch) per group; a single cloud launches the plain kernels
+    std::vector<SensorSet> sets;
+    std::vector<int32_t> set_blocks;  // blocks of each group's launch
     {
-        int64_t slot = 0;
+        int64_t slot = 0, idx0 = 0;
         for (int32_t s = 0; s < n_sensors; ++s) {
-            for (int i = 0; i < 12; ++i) A.T[i] = clouds[s].T[i];
-            k_keys<<<grid_for(clouds[s].n_raw), kThreads, 0, stream>>>(
-                clouds[s].xyz, clouds[s].n_raw, A, keys + slot, bitmap);
+            if (s % kFuseMax == 0) {
+                sets.push_back(SensorSet{});
+                set_blocks.push_back(0);
+            }
+            SensorSet &S = sets.back();
+            SensorRange &R = S.s[S.n++];
+            R.xyz = clouds[s].xyz;
+            R.n = clouds[s].n_raw;
+            R.slot = slot;
+            for (int i = 0; i < 12; ++i) R.T[i] = clouds[s].T[i];
+            R.idx0 = static_cast<uint32_t>(idx0);
+            R.nblk = grid_for(clouds[s].n_raw);
+            R.blk0 = set_blocks.back();
+            set_blocks.back() += R.nblk;
             slot += (clouds[s].n_raw + 3) & ~int64_t(3);
+            idx0 += clouds[s].n_raw;
         }
+    }
+    if (n_sensors == 1) {
+        for (int i = 0; i < 12; ++i) A.T[i] = clouds[0].T[i];
+        k_keys<<<grid_for(clouds[0].n_raw), kThreads, 0, stream>>>(clouds[0].xyz, clouds[0].n_raw,
+                                                                   A, keys, bitmap);
+    } else {
+        for (size_t g = 0; g < sets.size(); ++g)
+            k_keys_fused<<<set_blocks[g], kThreads, 0, stream>>>(sets[g], A, keys, bitmap);
     }
     k_bitmap_sums<<<static_cast<int>(L.n_sblocks), kBmThreads, 0, stream>>>(bitmap, chunk, sums, offsets,
                                                                           counters, n_occ);
     // per-sensor counts: points of sensor s carry the indices idx0 + i
     auto count_all = [&](uint32_t *cnt, uint32_t *rep, int64_t cap) {
-        int64_t slot = 0, idx0 = 0;
-        for (int32_t s = 0; s < n_sensors; ++s) {
-            k_count<<<grid_for(clouds[s].n_raw), kThreads, 0, stream>>>(
-                keys + slot, clouds[s].n_raw, pw, cnt, rep, cap, static_cast<uint32_t>(idx0));
-            slot += (clouds[s].n_raw + 3) & ~int64_t(3);
-            idx0 += clouds[s].n_raw;
+        if (n_sensors == 1) {
+            k_count<<<grid_for(clouds[0].n_raw), kThreads, 0, stream>>>(keys, clouds[0].n_raw, pw,
+                                                                        cnt, rep, cap, 0u);
+            return;
         }
+        for (size_t g = 0; g < sets.size(); ++g)
+            k_count_fused<<<set_blocks[g], kThreads, 0, stream>>>(sets[g], keys, pw, cnt, rep, cap);
     };
     if (ws->min_pts == 1) {
         EmitOut o{out->keys, out->counts, out->rep_idx, out->x, out->y, out->z, out->cap};
