@@ -1,8 +1,9 @@
 """GPU filter_clouds vs the oracle: several depth sensors fused into one
 obstacle set (Sec. IV-B), bit-exact keys, counts, smallest global indices
 and voxel centres -- two 848x480 cameras at full frame size, three cameras
-with ragged cloud sizes and an empty one, min_pts > 1, one sensor equal to
-filter_cloud, repeats, invalid arguments."""
+with ragged cloud sizes and an empty one, eleven sensors (two fused launch
+groups), min_pts > 1, one sensor equal to filter_cloud, repeats, invalid
+arguments."""
 
 import dataclasses
 
@@ -63,6 +64,19 @@ def test_three_ragged_clouds_and_an_empty_one(gm, voxel):
     ws = dataclasses.replace(m["workspace"], voxel=voxel, dims=dims)
     ref = oracle.filter_clouds(clouds, ws)
     obs = gm.filter_clouds(_dev(clouds), ws, cap=60000)
+    gm.sync()
+    _assert_same(obs, ref)
+
+
+def test_eleven_sensors_two_launch_groups(gm):
+    """More sensors than one fused key launch takes (8): eleven ragged
+    clouds (one empty) go through two key and two count launches; the index
+    bases run across both groups."""
+    m = synth.multi_sensor_frames(n_sensors=3, n_points=9001)
+    sizes = [9001, 17, 4096, 0, 333, 9000, 1, 2048, 5555, 8191, 64]
+    clouds = [(m["clouds"][i % 3][0][:n], m["clouds"][i % 3][1]) for i, n in enumerate(sizes)]
+    ref = oracle.filter_clouds(clouds, m["workspace"])
+    obs = gm.filter_clouds(_dev(clouds), m["workspace"], cap=60000)
     gm.sync()
     _assert_same(obs, ref)
 
