@@ -120,8 +120,6 @@ __device__ __forceinline__ void red_or(uint32_t *p, uint32_t v) {
     asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// BitMerge with a reduction: bits of consecutive points in one 32-cell word
-// OR-ed into the bitmap at once.
 // A warp's words of the bitmap, gathered in shared memory while it keys
 // its 256 points (64 slots, open addressing on the word index): each word
 // then goes to the bitmap in one reduction per tile instead of one per run;
