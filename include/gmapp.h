@@ -194,7 +194,8 @@ typedef struct gmapp_filter_batch gmapp_filter_batch;
  * owns it; freed by gmapp_filter_batch_destroy).  Scratch: three sets of
  * wave slots, each slot 8 bytes per cell of the largest grid (a point count
  * and a smallest index per cell) plus the bitmap (about 52 MB for a
- * 200x200x160 grid).  Synchronous. */
+ * 200x200x160 grid); waves hold fewer jobs when the slot sets would take
+ * more than half of the device memory free at creation.  Synchronous. */
 gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cloud_job *jobs,
                                        int32_t n_jobs, gmapp_filter_batch **out);
 void gmapp_filter_batch_destroy(gmapp_filter_batch *fb);

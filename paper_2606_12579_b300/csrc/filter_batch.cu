@@ -507,8 +507,18 @@ extern "C" gmapp_status gmapp_filter_batch_create(gmapp_ctx *ctx, const gmapp_cl
     }
     const SlotLayout SL = slot_layout(max_cells);
     const size_t slot_bytes = SL.total;
-    const int W_max = static_cast<int>(std::max<size_t>(
+    int W_max = static_cast<int>(std::max<size_t>(
         1, std::min<size_t>(n_jobs, kWaveL2Bytes / touched)));
+    // the slot sets take at most half of the device memory free now (a
+    // large grid makes a slot large): fewer jobs per wave otherwise
+    size_t free_bytes = 0, total_bytes = 0;
+    if (cudaMemGetInfo(&free_bytes, &total_bytes) == cudaSuccess) {
+        const size_t per_wave_job = static_cast<size_t>(kWaveStreams) * slot_bytes;
+        const size_t fit = free_bytes / 2 / std::max<size_t>(1, per_wave_job);
+        W_max = static_cast<int>(std::max<size_t>(1, std::min<size_t>(W_max, fit)));
+    } else {
+        cudaGetLastError();  // no memory figure: keep the L2-sized waves
+    }
     const int n_waves = (n_jobs + W_max - 1) / W_max;
     const int W = (n_jobs + n_waves - 1) / n_waves;  // balanced waves
     const int n_slots = std::min(n_waves, kWaveStreams) * W;
