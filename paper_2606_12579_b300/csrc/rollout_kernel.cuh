@@ -1811,9 +1811,12 @@ RolloutKernel rollout_kernel_ens3_grid_clear(int ag, int nt);
 // SFU share of the reciprocals: NM of AG agents use rcp.approx, the rest the
 // Newton-Raphson path.  Per obstacle pair an SFU agent costs 8 FMA-pipe
 // lane-ops and 2 SFU ops, a Newton-Raphson agent 14 and 1; with 128 FMA
-// lanes and 16 SFU lanes per SM clock the two pipes balance near NM/AG = 1/2
-// (measured best on B300); tiny groups stay on the SFU, where latency
-// matters more.
-constexpr int sfu_agents(int ag) { return ag <= 2 ? ag : (ag + 1) / 2; }
+// lanes and 16 SFU lanes per SM clock the two pipes balance near NM/AG = 1/2.
+// Measured on B300: one SFU agent more than half of an even group (dense
+// 50k x 512 x 1000 forward at AG = 14: 11.9 ms with 8 SFU agents, 12.3 ms
+// with 7 or 9); odd groups keep (AG + 1) / 2 (the tabletop query at AG = 9:
+// 2.67 ms with 5, 2.73 ms with 4).  Tiny groups stay on the SFU, where
+// latency matters more.
+constexpr int sfu_agents(int ag) { return ag <= 2 ? ag : (ag + 2) / 2; }
 
 }  // namespace gmapp
