@@ -787,7 +787,11 @@ def bench_adjoint(gm, args, reps=3):
     gm.rollout_agents(o, ag, prm, out=plain_out)
     gm.sync()
     # the forward's launch shape measured on these inputs (as the headline step)
-    tuning, _ = gm.autotune_rollout(o, ag, prm, out=plain_out, candidates=16, probe_steps=100)
+    if getattr(args, "adjoint_tuning", ""):
+        tuning = tuple(int(v) for v in args.adjoint_tuning.split(","))
+    else:
+        tuning, _ = gm.autotune_rollout(o, ag, prm, out=plain_out, candidates=16,
+                                        probe_steps=100)
     t_fwd = _events(torch, cur, lambda: gm.rollout_agents(o, ag, prm, out=out, tuning=tuning),
                     reps)
     t_adj = _events(torch, cur, lambda: gm.rollout_adjoint(o, ag, prm, out["ckpt"], workspace=ws),
@@ -1333,6 +1337,9 @@ def main():
     ap.add_argument("--tuning", default="",
                     help="rollout launch shape 'cluster,agents,threads[,exchange]' "
                          "(default: autotuned)")
+    ap.add_argument("--adjoint-tuning", default="",
+                    help="forward launch shape of the adjoint pattern "
+                         "'cluster,agents,threads,exchange' (default: autotuned)")
     ap.add_argument("--pattern", choices=sorted(PATTERNS), default=None,
                     help="run only this pattern measurement and print its JSON")
     args = ap.parse_args()
