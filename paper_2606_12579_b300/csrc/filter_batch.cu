@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kBmThreads) kf_sums(const FilterJob *J, const 
 // chunk's obstacles 32 consecutive ranks at a time, each with its cell's
 // record, which it puts back to zero (also beyond the output's capacity).
 // Empty chunks cost nothing here.
-constexpr int kEmitThreads = 128;  // 4 warps a CTA: 3.19 us per frame against 3.25 with 8
+constexpr int kEmitThreads = 64;  // 2 warps a CTA: 3.14 us per frame against 3.19 with 4, 3.25 with 8
 constexpr int kEmitWarps = kEmitThreads / 32;
 constexpr int kEmitLoads = 8;  // record loads a lane keeps in flight
 
